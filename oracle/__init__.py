@@ -1,0 +1,203 @@
+"""CPU oracle for the ABFT-protected GEMM (FT-BLAS, Zhai et al., ICS '21, Sections II.A and V).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU-baseline
+leg may import this package; the library itself never does. The C source next to this
+file (``ftgemm_oracle.c``) is plain binary64 code compiled with ``-ffp-contract=off``; it
+shares no code with the CUDA path. Buffers are flat numpy float64 arrays in BLAS storage
+with explicit leading dimensions, exactly as the C ABI takes them.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+ROW_MAJOR, COL_MAJOR = 101, 102
+NO_TRANS, TRANS = 111, 112
+SITE_ACCUM, SITE_OUTPUT, SITE_CHECKSUM = 1, 2, 3
+MODE_BITFLIP, MODE_ADD_REL = 0, 1
+KIND_CORRECTED, KIND_CHECKSUM_ONLY, KIND_UNCORRECTABLE, KIND_INPUT_NONFINITE = 1, 2, 3, 4
+MAX_RECORDS = 256
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ftgemm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class Problem(C.Structure):
+    _fields_ = [
+        ("layout", C.c_int32), ("transa", C.c_int32), ("transb", C.c_int32), ("pad_", C.c_int32),
+        ("M", C.c_int64), ("N", C.c_int64), ("K", C.c_int64),
+        ("alpha", C.c_double),
+        ("A", C.c_void_p), ("lda", C.c_int64),
+        ("B", C.c_void_p), ("ldb", C.c_int64),
+        ("beta", C.c_double),
+        ("Cin", C.c_void_p), ("ldc", C.c_int64),
+        ("tile_m", C.c_int64), ("tile_n", C.c_int64),
+        ("bk", C.c_int64),
+    ]
+
+
+class Injection(C.Structure):
+    _fields_ = [
+        ("i", C.c_int64), ("j", C.c_int64),
+        ("site", C.c_int32), ("mode", C.c_int32), ("bit", C.c_int32),
+        ("rel_log2", C.c_int32), ("sign", C.c_int32), ("pad_", C.c_int32),
+    ]
+
+
+class Record(C.Structure):
+    _fields_ = [
+        ("tile_row", C.c_int64), ("tile_col", C.c_int64), ("i", C.c_int64), ("j", C.c_int64),
+        ("delta_row", C.c_double), ("delta_col", C.c_double),
+        ("tau_row", C.c_double), ("tau_col", C.c_double),
+        ("value_before", C.c_double), ("value_after", C.c_double), ("value_subtracted", C.c_double),
+        ("kind", C.c_int32), ("rows_flagged", C.c_int32), ("cols_flagged", C.c_int32), ("pad_", C.c_int32),
+    ]
+
+
+class Report(C.Structure):
+    _fields_ = [
+        ("tiles_checked", C.c_uint64), ("detected", C.c_uint64), ("corrected", C.c_uint64),
+        ("uncorrectable", C.c_uint64), ("checksum_only", C.c_uint64), ("input_nonfinite", C.c_uint64),
+        ("n_records", C.c_uint32), ("pad_", C.c_uint32),
+        ("rec", Record * MAX_RECORDS),
+    ]
+
+    def records(self):
+        return [self.rec[q] for q in range(min(self.n_records, MAX_RECORDS))]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C, -ffp-contract=off). Returns the library path."""
+    with _lock:
+        if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+            return _LIB_PATH
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+               "-fopenmp", "-Wall", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+        return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        # ORACLE_LIB points the tests at a deliberately broken build (mutation tests).
+        path = os.environ.get("ORACLE_LIB") or build()
+        L = C.CDLL(path)
+        L.oracle_gemm.argtypes = [C.POINTER(Problem), C.c_void_p]
+        L.oracle_gemm.restype = C.c_int
+        L.oracle_gemm_rows.argtypes = [C.POINTER(Problem), C.c_int64, C.c_void_p, C.c_void_p]
+        L.oracle_gemm_rows.restype = C.c_int
+        L.oracle_ft_gemm.argtypes = [C.POINTER(Problem), C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                                     C.c_void_p, C.POINTER(Report)]
+        L.oracle_ft_gemm.restype = C.c_int
+        L.oracle_draw_injections.argtypes = [C.c_uint64, C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                             C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                             C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_void_p]
+        L.oracle_draw_injections.restype = C.c_int64
+        L.oracle_num_threads.argtypes = []
+        L.oracle_num_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def num_threads() -> int:
+    return int(lib().oracle_num_threads())
+
+
+def _f64(x):
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    return a
+
+
+def make_problem(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc,
+                 tile_m=128, tile_n=128, bk=16, keep=None):
+    """Fill a Problem; ``keep`` (a list) receives the arrays that must outlive the call."""
+    A = _f64(A); B = _f64(B)
+    Cin = _f64(Cin) if Cin is not None else np.zeros(1)
+    if keep is not None:
+        keep.extend([A, B, Cin])
+    p = Problem(layout=layout, transa=transa, transb=transb, pad_=0, M=M, N=N, K=K, alpha=alpha,
+                A=A.ctypes.data, lda=lda, B=B.ctypes.data, ldb=ldb, beta=beta,
+                Cin=Cin.ctypes.data, ldc=ldc, tile_m=tile_m, tile_n=tile_n, bk=bk)
+    return p
+
+
+def gemm(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc):
+    """Plain C = alpha*op(A)*op(B) + beta*C_in (the GEMM definition). Returns a new buffer."""
+    keep = []
+    p = make_problem(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc, keep=keep)
+    out = np.array(keep[2], copy=True) if Cin is not None else np.zeros(max(1, ldc * (N if layout == COL_MAJOR else M)))
+    rc = lib().oracle_gemm(C.byref(p), out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_gemm: bad arguments")
+    return out
+
+
+def gemm_rows(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc, rows):
+    """Rows ``rows`` of the plain product, as an array of shape (len(rows), N)."""
+    keep = []
+    p = make_problem(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc, keep=keep)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.zeros((len(rows), N), dtype=np.float64)
+    lib().oracle_gemm_rows(C.byref(p), len(rows), rows.ctypes.data, out.ctypes.data)
+    return out
+
+
+def injections_array(points):
+    """``points``: iterable of dicts/tuples (i, j, site, mode, bit, rel_log2, sign)."""
+    pts = list(points)
+    arr = (Injection * max(1, len(pts)))()
+    for q, pt in enumerate(pts):
+        if isinstance(pt, dict):
+            pt = (pt["i"], pt["j"], pt.get("site", SITE_ACCUM), pt.get("mode", MODE_BITFLIP),
+                  pt.get("bit", 0), pt.get("rel_log2", 0), pt.get("sign", 1))
+        i, j, site, mode, bit, rel, sign = pt
+        arr[q] = Injection(i=i, j=j, site=site, mode=mode, bit=bit, rel_log2=rel, sign=sign, pad_=0)
+    return arr, len(pts)
+
+
+def ft_gemm(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc,
+            tile_m, tile_n, bk, injections=(), tiles=None, out=None):
+    """ABFT-protected GEMM. Returns ``(Cout_buffer, Report)``.
+
+    ``tiles``: None for all tiles, else tile numbers t = tile_row + tile_col * n_tile_rows
+    (only those tiles of the output are written; ``out`` may carry the rest).
+    """
+    keep = []
+    p = make_problem(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc,
+                     tile_m, tile_n, bk, keep=keep)
+    if out is None:
+        n_store = max(1, ldc * (N if layout == COL_MAJOR else M))
+        out = np.array(keep[2], copy=True) if Cin is not None and beta != 0.0 else np.zeros(n_store)
+    inj, n_inj = injections_array(injections)
+    rep = Report()
+    if tiles is None:
+        rc = lib().oracle_ft_gemm(C.byref(p), n_inj, C.addressof(inj), 0, None, out.ctypes.data, C.byref(rep))
+    else:
+        t = np.ascontiguousarray(tiles, dtype=np.int64)
+        rc = lib().oracle_ft_gemm(C.byref(p), n_inj, C.addressof(inj), len(t), t.ctypes.data, out.ctypes.data,
+                                  C.byref(rep))
+    if rc != 0:
+        raise ValueError("oracle_ft_gemm: bad arguments")
+    return out, rep
+
+
+def draw_injections(seed, launch, every_n, per_launch, site, mode, bit_lo, bit_hi, log2_lo, log2_hi,
+                    M, N, tile_m, tile_n, cap=256):
+    """The seeded injection draw of one launch (the oracle's own SplitMix64)."""
+    arr = (Injection * cap)()
+    n = lib().oracle_draw_injections(seed, launch, every_n, per_launch, site, mode, bit_lo, bit_hi,
+                                     log2_lo, log2_hi, M, N, tile_m, tile_n, cap, C.addressof(arr))
+    return [dict(i=arr[q].i, j=arr[q].j, site=arr[q].site, mode=arr[q].mode, bit=arr[q].bit,
+                 rel_log2=arr[q].rel_log2, sign=arr[q].sign) for q in range(n)]

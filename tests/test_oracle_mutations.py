@@ -1,0 +1,41 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake in a copy of the oracle's C source (never in the real one),
+builds it, and runs the pin tests against that build; they must fail.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "ftgemm_oracle.c")
+
+MUTATIONS = {
+    "delta_sign": ("dr[ii] = Cr_ref - Cr;", "dr[ii] = Cr - Cr_ref;"),
+    "dropped_beta_term": ("if (p->beta != 0.0) Cr = Cr + p->beta * cin_sum;", ""),
+    "transposed_operand": ("int64_t p = (trans == OR_TRANS) ? c : r;", "int64_t p = (trans == OR_NO_TRANS) ? c : r;"),
+    "injection_point_off_by_one_tile": ("const int64_t kstar = p->bk * (nk / 2);", "const int64_t kstar = p->bk * ((nk + 1) / 2);"),
+    "wrong_located_column": ("r.j = (fc >= 0) ? j0 + fc : -1;", "r.j = (fc >= 0) ? j0 + (fc + 1) % nJ : -1;"),
+    "dropped_term_in_Be": ("for (int64_t j = j0; j < j0 + nJ; ++j) { double b = b_elem(p, k, j); s = s + b;",
+                           "for (int64_t j = j0 + 1; j < j0 + nJ; ++j) { double b = b_elem(p, k, j); s = s + b;"),
+    "missing_alpha_in_prediction": ("double Cc = p->alpha * dotp;", "double Cc = dotp;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found once"
+    mutated = tmp_path / "mutant.c"
+    mutated.write_text(src.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
+                    "-o", str(lib), str(mutated), "-lm"], check=True, capture_output=True)
+    env = dict(os.environ, ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch mutation {name}:\n{r.stdout[-2000:]}"

@@ -1,0 +1,346 @@
+"""Pins for the CPU oracle: facts fixed by the mathematics and the paper, not by the oracle.
+
+FT-BLAS Section II.A defines the checksum relations e^T C = (e^T A) B and C e = A (B e),
+Section V.A/V.B the detect/locate scheme with beta*C folded in, and Section VI.C the
+correction of an injected error by its located magnitude. Each test below checks the
+oracle against something independent of its own code: closed-form products of integer
+matrices (exact in binary64), special cases that reduce to textbook results, a library
+matmul within the standard rounding bound, brute-force injection on tiny inputs with the
+faulty value recomputed here in plain Python floats, and exact checksum differences on
+integer data.
+"""
+import math
+import struct
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth as S
+
+U = 2.0 ** -53
+LAYOUTS = [O.COL_MAJOR, O.ROW_MAJOR]
+TRANS = [O.NO_TRANS, O.TRANS]
+COMBOS = [(l, a, b) for l in LAYOUTS for a in TRANS for b in TRANS]
+
+
+def gamma(n):
+    return n * U / (1 - n * U)
+
+
+def stored(layout, trans, logical, pad=3):
+    """BLAS storage of X such that op(X) == logical."""
+    X = logical if trans == O.NO_TRANS else logical.T
+    ld = (X.shape[0] if layout == O.COL_MAJOR else X.shape[1]) + pad
+    return S.store(X, layout, ld=max(1, ld))
+
+
+def c_store(layout, C_log, pad=2):
+    ld = (C_log.shape[0] if layout == O.COL_MAJOR else C_log.shape[1]) + pad
+    return S.store(C_log, layout, ld=max(1, ld))
+
+
+def plain(layout, ta, tb, A_log, B_log, alpha=1.0, beta=0.0, C_log=None):
+    M, K = A_log.shape
+    N = B_log.shape[1]
+    a, lda = stored(layout, ta, A_log)
+    b, ldb = stored(layout, tb, B_log)
+    if C_log is None:
+        C_log = np.zeros((M, N))
+    c, ldc = c_store(layout, C_log)
+    out = O.gemm(layout, ta, tb, M, N, K, alpha, a, lda, b, ldb, beta, c, ldc)
+    return S.load(out, layout, M, N, ldc)
+
+
+def ft(layout, ta, tb, A_log, B_log, alpha=1.0, beta=0.0, C_log=None, tile=(4, 4), bk=2, inj=(), tiles=None):
+    M, K = A_log.shape
+    N = B_log.shape[1]
+    a, lda = stored(layout, ta, A_log)
+    b, ldb = stored(layout, tb, B_log)
+    if C_log is None:
+        C_log = np.zeros((M, N))
+    c, ldc = c_store(layout, C_log)
+    out, rep = O.ft_gemm(layout, ta, tb, M, N, K, alpha, a, lda, b, ldb, beta, c, ldc,
+                         tile[0], tile[1], bk, injections=inj, tiles=tiles)
+    return S.load(out, layout, M, N, ldc), rep
+
+
+def flip(x, bit):
+    (u,) = struct.unpack("<Q", struct.pack("<d", x))
+    return struct.unpack("<d", struct.pack("<Q", u ^ (1 << bit)))[0]
+
+
+# ------------------------------------------------------------------------------------
+# The product itself
+# ------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("layout,ta,tb", COMBOS)
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (7, 5, 9), (33, 17, 64)])
+def test_closed_form_linear_operands(layout, ta, tb, M, N, K):
+    """A(i,k) = i + k, B(k,j) = k + j  =>  C(i,j) = K i j + (i + j) S1 + S2, exactly."""
+    i = np.arange(M)[:, None]
+    j = np.arange(N)[None, :]
+    k = np.arange(K)
+    A = (np.arange(M)[:, None] + k[None, :]).astype(np.float64)
+    B = (k[:, None] + np.arange(N)[None, :]).astype(np.float64)
+    S1 = K * (K - 1) // 2
+    S2 = (K - 1) * K * (2 * K - 1) // 6
+    expect = (K * i * j + (i + j) * S1 + S2).astype(np.float64)
+    assert np.array_equal(plain(layout, ta, tb, A, B), expect)
+    # alpha, beta with exact dyadic values and an integer C_in
+    Cin = (i - 2 * j).astype(np.float64)
+    got = plain(layout, ta, tb, A, B, alpha=0.5, beta=-2.0, C_log=Cin)
+    assert np.array_equal(got, 0.5 * expect - 2.0 * Cin)
+
+
+@pytest.mark.parametrize("layout,ta,tb", COMBOS)
+def test_identity_and_ones(layout, ta, tb):
+    K, N = 6, 5
+    B = S.uniform_matrix(3, 1, K, N)
+    assert np.array_equal(plain(layout, ta, tb, np.eye(K), B), B)
+    Bi = S.randint(3, 2, K * N, -9, 9).reshape(K, N).astype(np.float64)
+    ones = np.ones((4, K))
+    expect = np.tile(Bi.sum(axis=0), (4, 1))  # integer column sums, exact
+    assert np.array_equal(plain(layout, ta, tb, ones, Bi), expect)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_library_matmul_within_rounding_bound(seed):
+    M, N, K = 23, 19, 71
+    A = S.uniform_matrix(seed, 0, M, K)
+    B = S.uniform_matrix(seed, 1, K, N)
+    got = plain(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B)
+    bound = 2 * gamma(K) * (np.abs(A) @ np.abs(B))
+    assert np.all(np.abs(got - A @ B) <= bound)
+
+
+def test_storage_variants_give_identical_bits():
+    """op() and layout change only where elements are read, never the order of a sum."""
+    M, N, K = 13, 11, 29
+    A = S.uniform_matrix(5, 0, M, K)
+    B = S.uniform_matrix(5, 1, K, N)
+    Cin = S.uniform_matrix(5, 2, M, N)
+    ref = plain(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B, 1.5, 0.5, Cin)
+    for layout, ta, tb in COMBOS:
+        assert np.array_equal(plain(layout, ta, tb, A, B, 1.5, 0.5, Cin), ref)
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+def test_checksum_invariants_of_the_product(seed):
+    """Section II.A: e^T C = (e^T A) B and C e = A (B e), within rounding."""
+    M, N, K = 40, 30, 50
+    A = S.uniform_matrix(seed, 0, M, K)
+    B = S.uniform_matrix(seed, 1, K, N)
+    Cm = plain(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B)
+    absprod = np.abs(A) @ np.abs(B)
+    col_lhs = np.array([math.fsum(Cm[:, j]) for j in range(N)])
+    col_rhs = np.array([math.fsum(A.sum(axis=0) * B[:, j]) for j in range(N)])
+    row_lhs = np.array([math.fsum(Cm[i, :]) for i in range(M)])
+    row_rhs = np.array([math.fsum(A[i, :] * B.sum(axis=1)) for i in range(M)])
+    g = gamma(K + max(M, N) + 2)
+    assert np.all(np.abs(col_lhs - col_rhs) <= 2 * g * absprod.sum(axis=0))
+    assert np.all(np.abs(row_lhs - row_rhs) <= 2 * g * absprod.sum(axis=1))
+
+
+# ------------------------------------------------------------------------------------
+# The fault-tolerant path
+# ------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("layout,ta,tb", COMBOS)
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (1.5, 0.5), (-0.75, 2.0)])
+def test_clean_runs_never_flag_and_match_plain(layout, ta, tb, alpha, beta):
+    M, N, K = 37, 29, 45
+    A = S.uniform_matrix(21, 0, M, K)
+    B = S.uniform_matrix(21, 1, K, N)
+    Cin = S.uniform_matrix(21, 2, M, N)
+    for tile, bk in [((16, 8), 4), ((4, 4), 3), ((37, 29), 16), ((1, 29), 1)]:
+        got, rep = ft(layout, ta, tb, A, B, alpha, beta, Cin, tile=tile, bk=bk)
+        assert rep.detected == 0 and rep.input_nonfinite == 0
+        assert rep.tiles_checked == math.ceil(M / tile[0]) * math.ceil(N / tile[1])
+        assert np.array_equal(got, plain(layout, ta, tb, A, B, alpha, beta, Cin))
+
+
+def test_clean_soak_structured_magnitudes():
+    """Rows of A and columns of B scaled by 2^u, u in [-8, 8]: no false alarm."""
+    for seed in range(6):
+        M, N, K = 48, 40, 96
+        A = S.normal_matrix(seed, 0, M, K) * S.pow2_row_scales(seed, 5, M)[:, None]
+        B = S.normal_matrix(seed, 1, K, N) * S.pow2_row_scales(seed, 6, N)[None, :]
+        Cin = S.normal_matrix(seed, 2, M, N)
+        _, rep = ft(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B, 1.5, 0.5, Cin, tile=(16, 16), bk=8)
+        assert rep.detected == 0
+
+
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")
+@pytest.mark.parametrize("tile", [(2, 2), (4, 4), (3, 2), (1, 5), (4, 5)])
+@pytest.mark.parametrize("bk", [1, 2])
+def test_bruteforce_accumulator_bitflips_tiny(tile, bk):
+    """Every element and every bit 40..62 of a 4x5x3 product: the flipped element is
+    located exactly and the corrected output equals the fault-free output bit for bit."""
+    M, N, K = 4, 5, 3
+    A = S.uniform_matrix(7, 0, M, K)
+    B = S.uniform_matrix(7, 1, K, N)
+    clean = plain(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B)
+    nk = -(-K // bk)
+    kstar = bk * (nk // 2)
+    for i in range(M):
+        for j in range(N):
+            for bit in range(40, 63):
+                acc = 0.0
+                for k in range(K):
+                    if k == kstar:
+                        acc = flip(acc, bit)
+                    acc = acc + A[i, k] * B[k, j]
+                bad = acc  # alpha = 1, beta = 0
+                err = bad - clean[i, j]
+                if math.isfinite(err) and abs(err) < 1e-9:
+                    continue  # below any plausible threshold: not a detection case
+                got, rep = ft(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B, tile=tile, bk=bk,
+                              inj=[dict(i=i, j=j, site=O.SITE_ACCUM, bit=bit)])
+                assert (rep.detected, rep.corrected, rep.uncorrectable, rep.checksum_only) == (1, 1, 0, 0)
+                r = rep.records()[0]
+                assert (r.i, r.j, r.kind) == (i, j, O.KIND_CORRECTED)
+                assert struct.pack("<d", r.value_before) == struct.pack("<d", bad)
+                assert np.array_equal(got, clean)
+
+
+@pytest.mark.parametrize("layout,ta,tb", COMBOS)
+def test_delta_is_the_injected_magnitude_on_integer_data(layout, ta, tb):
+    """Integer operands make every checksum exact, so C^r_ref - C^r and C^c_ref - C^c
+    equal the injected error e exactly, and subtracting it (Section VI.C) restores C."""
+    M, N, K = 9, 7, 12
+    A = S.randint(31, 0, M * K, -4, 4).reshape(M, K).astype(np.float64)
+    B = S.randint(31, 1, K * N, -4, 4).reshape(K, N).astype(np.float64)
+    Cin = S.randint(31, 2, M * N, -9, 9).reshape(M, N).astype(np.float64)
+    clean = plain(layout, ta, tb, A, B, 1.0, 1.0, Cin)
+    for (i, j, p, s) in [(0, 0, 0, 1), (8, 6, -3, -1), (4, 3, 2, 1), (5, 1, -7, -1)]:
+        if clean[i, j] == 0:
+            continue
+        e = s * 2.0 ** p * abs(clean[i, j])
+        got, rep = ft(layout, ta, tb, A, B, 1.0, 1.0, Cin, tile=(9, 7), bk=4,
+                      inj=[dict(i=i, j=j, site=O.SITE_OUTPUT, mode=O.MODE_ADD_REL, rel_log2=p, sign=s)])
+        r = rep.records()[0]
+        assert (r.i, r.j, rep.corrected) == (i, j, 1)
+        assert r.delta_row == e and r.delta_col == e
+        assert r.value_before == clean[i, j] + e
+        assert r.value_subtracted == clean[i, j]
+        assert np.array_equal(got, clean)
+
+
+def test_classification_multiple_and_checksum_faults():
+    M, N, K = 16, 16, 20
+    A = S.randint(41, 0, M * K, -3, 3).reshape(M, K).astype(np.float64)
+    B = S.randint(41, 1, K * N, -3, 3).reshape(K, N).astype(np.float64)
+    clean = plain(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B)
+    add = lambda i, j, p=2: dict(i=i, j=j, site=O.SITE_OUTPUT, mode=O.MODE_ADD_REL, rel_log2=p, sign=1)
+    nz = [(i, j) for i in range(M) for j in range(N) if clean[i, j] != 0]
+    # two errors in one 8x8 tile, different rows and columns: uncorrectable, C kept as computed
+    (i1, j1), (i2, j2) = [(i, j) for (i, j) in nz if i < 8 and j < 8][0], (7, 7)
+    if clean[7, 7] == 0:
+        pytest.skip("degenerate draw")
+    got, rep = ft(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B, tile=(8, 8), inj=[add(i1, j1), add(i2, j2)])
+    assert (rep.detected, rep.uncorrectable, rep.corrected) == (1, 1, 0)
+    assert got[i1, j1] != clean[i1, j1]
+    # two errors in one row of one tile: one row, two columns flagged -> uncorrectable
+    row_pair = [(i, j) for (i, j) in nz if i == 9 and j >= 8][:2]
+    _, rep = ft(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B, tile=(8, 8), inj=[add(*row_pair[0]), add(*row_pair[1])])
+    assert (rep.detected, rep.uncorrectable) == (1, 1)
+    r = rep.records()[0]
+    assert (r.rows_flagged, r.cols_flagged) == (1, 2)
+    # one error in each of two tiles: both corrected
+    got, rep = ft(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B, tile=(8, 8),
+                  inj=[add(*nz[0]), add(*[(i, j) for (i, j) in nz if i >= 8 and j >= 8][0])])
+    assert (rep.detected, rep.corrected, rep.tiles_checked) == (2, 2, 4)
+    assert np.array_equal(got, clean)
+    # a fault in the predicted row checksum only: checksum-only, C untouched
+    i_cs = [i for i in range(8) if clean[i, :8].sum() != 0][0]
+    got, rep = ft(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B, tile=(8, 8),
+                  inj=[dict(i=i_cs, j=0, site=O.SITE_CHECKSUM, mode=O.MODE_ADD_REL, rel_log2=0, sign=1)])
+    assert (rep.detected, rep.checksum_only, rep.corrected) == (1, 1, 0)
+    assert rep.records()[0].i == i_cs and rep.records()[0].j == -1
+    assert np.array_equal(got, clean)
+
+
+def test_quick_returns_and_beta_zero_ignores_nan():
+    M, N, K = 6, 5, 4
+    A = S.uniform_matrix(1, 0, M, K)
+    B = S.uniform_matrix(1, 1, K, N)
+    Cin = S.uniform_matrix(1, 2, M, N)
+    # K = 0 and alpha = 0: C = beta * C, nothing checked
+    for (Kq, alpha) in [(0, 1.0), (K, 0.0)]:
+        Aq = A[:, :Kq]
+        Bq = B[:Kq, :]
+        got, rep = ft(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, Aq, Bq, alpha, 0.5, Cin)
+        assert np.array_equal(got, 0.5 * Cin) and rep.tiles_checked == 0
+    # beta = 0: C_in is never read, NaN there does not propagate
+    nanC = np.full((M, N), np.nan)
+    got, rep = ft(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B, 1.0, 0.0, nanC)
+    assert np.all(np.isfinite(got)) and rep.detected == 0
+    got, rep = ft(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B, 0.0, 0.0, nanC)
+    assert np.array_equal(got, np.zeros((M, N)))
+
+
+def test_nonfinite_input_is_reported_not_corrected():
+    M, N, K = 8, 8, 8
+    A = S.uniform_matrix(2, 0, M, K)
+    A[3, 2] = np.inf
+    B = S.uniform_matrix(2, 1, K, N)
+    _, rep = ft(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B, tile=(4, 4))
+    assert rep.input_nonfinite == 2 and rep.corrected == 0  # tiles of row block 0
+
+
+def test_exponent_flip_to_nonfinite_is_corrected():
+    """A flip of bit 62 that makes the running sum infinite or huge is still located and
+    recomputed (the paper's subtraction cannot restore a non-finite value)."""
+    M, N, K = 8, 8, 16
+    A = S.uniform_matrix(9, 0, M, K)
+    B = S.uniform_matrix(9, 1, K, N)
+    clean = plain(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B)
+    got, rep = ft(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B, tile=(8, 8), bk=4,
+                  inj=[dict(i=2, j=5, site=O.SITE_ACCUM, bit=62)])
+    assert rep.corrected == 1 and np.array_equal(got, clean)
+
+
+def test_ragged_tiles_and_injection_in_last_tile():
+    M, N, K = 37, 29, 33
+    A = S.uniform_matrix(4, 0, M, K)
+    B = S.uniform_matrix(4, 1, K, N)
+    Cin = S.uniform_matrix(4, 2, M, N)
+    clean = plain(O.ROW_MAJOR, O.TRANS, O.NO_TRANS, A, B, 1.5, 0.5, Cin)
+    got, rep = ft(O.ROW_MAJOR, O.TRANS, O.NO_TRANS, A, B, 1.5, 0.5, Cin, tile=(16, 8), bk=8,
+                  inj=[dict(i=36, j=28, site=O.SITE_ACCUM, bit=55), dict(i=0, j=0, site=O.SITE_ACCUM, bit=51)])
+    assert rep.tiles_checked == 3 * 4 and rep.corrected == 2
+    assert sorted((r.i, r.j) for r in rep.records()) == [(0, 0), (36, 28)]
+    assert np.array_equal(got, clean)
+
+
+def test_selected_tiles_only():
+    M, N, K = 32, 32, 16
+    A = S.uniform_matrix(6, 0, M, K)
+    B = S.uniform_matrix(6, 1, K, N)
+    clean = plain(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B)
+    got, rep = ft(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B, tile=(8, 8), tiles=[0, 5, 15])
+    assert rep.tiles_checked == 3
+    for t in [0, 5, 15]:
+        r0, c0 = (t % 4) * 8, (t // 4) * 8
+        assert np.array_equal(got[r0:r0 + 8, c0:c0 + 8], clean[r0:r0 + 8, c0:c0 + 8])
+    assert np.all(got[8:16, 0:8] == 0)
+
+
+def test_seeded_draw_properties():
+    M, N, tm, tn = 300, 260, 128, 64
+    n_tiles = 3 * 5
+    seen_launches = []
+    for launch in range(30):
+        pts = O.draw_injections(12345, launch, 10, 4, O.SITE_ACCUM, O.MODE_BITFLIP, 40, 62, -20, 4, M, N, tm, tn)
+        if not pts:
+            continue
+        seen_launches.append(launch)
+        tiles = {(p["i"] // tm, p["j"] // tn) for p in pts}
+        assert len(pts) == 4 and len(tiles) == 4
+        for p in pts:
+            assert 0 <= p["i"] < M and 0 <= p["j"] < N and 40 <= p["bit"] <= 62 and -20 <= p["rel_log2"] <= 4
+        assert pts == O.draw_injections(12345, launch, 10, 4, O.SITE_ACCUM, O.MODE_BITFLIP, 40, 62, -20, 4, M, N, tm, tn)
+    assert seen_launches == [5, 15, 25]  # 12345 % 10 == 5
+    pts = O.draw_injections(1, 0, 1, 100, O.SITE_ACCUM, O.MODE_BITFLIP, 40, 62, 0, 0, M, N, tm, tn)
+    assert len(pts) == n_tiles
