@@ -1,0 +1,415 @@
+#!/usr/bin/env python3
+"""Benchmark of the ABFT-protected FP64 GEMM (FT-BLAS, Zhai et al., ICS '21) on GB300.
+
+Workload: FT-DGEMM, column-major, M = N = K = 8192 (a member of the paper's 2048^2-10240^2
+DGEMM range), alpha = 1.5, beta = 0.5, A, B, C uniform on [-1, 1) from a fixed seed, one
+seeded accumulator bit flip (bits 40-62) per 10 launches. One step = one protected call:
+operand staging, fused checksum encode, product, alpha/beta epilogue, verification,
+location, correction and the report all run inside it.
+
+Printed (one JSON line, rank 0): FT-GEMM TFLOP/s (2 M N K per step over device time,
+inputs resident in HBM), the fraction of the FP64 peak, the ABFT overhead against the same
+kernel with protection compiled out (ftblas_dgemm_noabft), with and without injection, the
+detected/corrected counts, the error against the CPU oracle on sampled rows, an
+end-to-end figure through the host-buffer entry point (copies included), the sampled SM
+clocks, and the CPU oracle timed on the host on a bounded sample.
+
+`--impl reference` times the CPU oracle instead (the only reference there is: the paper's
+implementation is AVX-512 CPU code that is not available), on bounded samples per step.
+
+Multi-GPU (torchrun): every rank runs its own independent problem (output tiles shard with
+no data-path exchange), so scaling is weak; the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FT-GEMM TFLOP/s, % of peak, ABFT overhead % vs unprotected, at stated error"
+UNIT = "TFLOP/s"
+SEED = 20210601
+TILE = 128
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=8192, help="M = N = K")
+    ap.add_argument("--engine", choices=["dfma", "dmma"], default="dfma", help="headline FP64 engine")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-second-engine", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    """Roofline denominators. The measured file holds HBM and BF16 figures; the FP64
+    pipe's peak is derived from them and the nominal figures (see the design notes)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    mp = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            mp = json.load(f)
+    bf16 = mp.get("bf16_tflops")
+    sm_max = mp.get("sm_max_mhz", 2070.0)
+    # FP64 FMA pipe: 2 FMA / clock / SM (GB300 nominal 1.25 TFLOP/s at 2070 MHz) x 152 SMs.
+    alu = 2 * 2 * 152 * sm_max * 1e6 / 1e12
+    if bf16 is not None:
+        tensor = bf16 * 1.25 / 2250.0
+        tensor_src = f"measured bf16 {bf16} TFLOP/s x nominal FP64/BF16 ratio 1.25/2250"
+    else:
+        tensor = 1900.0 * 1.25 / 2250.0
+        tensor_src = "fallback bf16 1900 TFLOP/s x nominal FP64/BF16 ratio 1.25/2250"
+    return dict(alu=alu, alu_src=f"2 FP64 FMA/clk/SM x 152 SMs x {sm_max} MHz", tensor=tensor,
+                tensor_src=tensor_src)
+
+
+def workload_config(n, engine):
+    return {"workload": f"ft_dgemm_fp64_col_major_{n}x{n}x{n}", "M": n, "N": n, "K": n, "alpha": 1.5, "beta": 0.5,
+            "layout": "column-major, no transpose", "inputs": "A, B, C uniform[-1,1) from a fixed seed",
+            "injection": "one seeded accumulator bit flip (bits 40-62) per 10 launches",
+            "verification_tile": f"{TILE}x{TILE}", "engine": engine,
+            "l2": "inputs 512 MiB per operand > 129 MB L2; no flush between steps"}
+
+
+def gen_inputs(n, seed):
+    import synth as S
+    A = S.uniform(seed, 0, n * n)   # logical column-major index == storage index (ld = n)
+    B = S.uniform(seed, 1, n * n)
+    Cin = S.uniform(seed, 2, n * n)
+    return A, B, Cin
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(n, A, B, Cin, n_tiles, seed_tiles=7):
+    """The CPU oracle (as it stands) on n_tiles seeded 128 x 128 tiles of the workload.
+    Returns (flops, seconds, threads)."""
+    import oracle as O
+    import synth as S
+    tr = (n + TILE - 1) // TILE
+    tiles = np.unique(S.randint(seed_tiles, 3, n_tiles * 4, 0, tr * tr - 1))[:n_tiles]
+    t0 = time.perf_counter()
+    O.ft_gemm(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, n, n, n, 1.5, A, n, B, n, 0.5, Cin, n, TILE, TILE, 32,
+              tiles=tiles, out=np.array(Cin, copy=True))
+    dt = time.perf_counter() - t0
+    return 2.0 * len(tiles) * TILE * TILE * n, dt, O.num_threads()
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle as O
+    n = args.size
+    A, B, Cin = gen_inputs(n, SEED)
+    threads = O.num_threads()
+    per_step = max(1, min(16, threads))
+    times, flops = [], 0.0
+    for s in range(args.warmup + args.steps):
+        f, dt, _ = oracle_sample(n, A, B, Cin, per_step, seed_tiles=1000 + s)
+        if s >= args.warmup:
+            times.append(dt)
+            flops += f
+    total = sum(times)
+    value = flops / total / 1e12
+    sample = f"{per_step} seeded {TILE}x{TILE} output tiles of the {n}^3 problem per step (full K, checksums included)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(n, "cpu-oracle"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, dist):
+    import ctypes
+
+    import torch
+
+    import paper_2104_00897_gb300 as fb
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    fb.load()
+    n = args.size
+    flops_step = 2.0 * n * n * n
+    A, B, Cin = gen_inputs(n, SEED + rank)
+    dA = torch.from_numpy(A).to(dev)
+    dB = torch.from_numpy(B).to(dev)
+    dCin = torch.from_numpy(Cin).to(dev)
+    dC = dCin.clone()
+    stream = torch.cuda.current_stream(dev)
+    st = stream.cuda_stream
+    engines = {"dfma": fb.ENGINE_DFMA, "dmma": fb.ENGINE_DMMA}
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(protect, inject, steps, warmup, clocks=False):
+        """Per-launch device times (ms) of `steps` calls after `warmup`, with reports."""
+        if protect and inject:
+            # one flip per 10 launches, placed so that it falls inside the timed steps
+            seed = (SEED + rank) - ((SEED + rank) % 10) + ((warmup + 1) % 10)
+            fb.ftblas_set_injection(fb.make_injection(seed=seed, site=fb.SITE_ACCUM, mode=fb.MODE_BITFLIP, bit_lo=40,
+                                                      bit_hi=62, every_n_launches=10, errors_per_launch=1))
+        else:
+            fb.ftblas_set_injection(None)
+        reps = [fb.new_report(dev) for _ in range(steps)]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+
+        def call(rep):
+            args_ = (fb.COL_MAJOR, fb.NO_TRANS, fb.NO_TRANS, n, n, n, 1.5, dA.data_ptr(), n, dB.data_ptr(), n, 0.5,
+                     dC.data_ptr(), n, st)
+            if protect:
+                fb.check(fb.ftblas_dgemm(*args_, rep.data_ptr() if rep is not None else None))
+            else:
+                fb.check(fb.ftblas_dgemm_noabft(*args_))
+
+        for _ in range(warmup):
+            call(None)
+        barrier()
+        sampler = ClockSampler(local) if clocks else None
+        if sampler:
+            sampler.__enter__()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for s in range(steps):
+            ev[s][0].record(stream)
+            call(reps[s])
+            ev[s][1].record(stream)
+        t1.record(stream)
+        barrier()
+        if sampler:
+            sampler.__exit__(None, None, None)
+        total_ms = max_over_ranks(t0.elapsed_time(t1))
+        per = [a.elapsed_time(b) for a, b in ev]
+        rsum = {"detected": 0, "corrected": 0, "uncorrectable": 0, "checksum_only": 0, "tiles_checked": 0,
+                "status": 0}
+        if protect:
+            for r in reps:
+                rr = fb.report_from_device(r)
+                for k in ("detected", "corrected", "uncorrectable", "checksum_only", "tiles_checked"):
+                    rsum[k] += int(getattr(rr, k))
+                rsum["status"] |= int(rr.status)
+        injected = 0
+        if protect and inject:
+            injected = sum(1 for L in range(warmup, warmup + steps) if L % 10 == ((warmup + 1) % 10))
+        fb.ftblas_set_injection(None)
+        return total_ms, per, rsum, injected, (sampler.summary() if sampler else None)
+
+    results = {}
+    engine_list = [args.engine] + ([] if args.no_second_engine else [e for e in engines if e != args.engine])
+    clocks = None
+    for eng in engine_list:
+        fb.ftblas_set_fp64_engine(engines[eng])
+        head = eng == args.engine
+        ft_ms, ft_per, ft_rep, injected, clk = timed(True, True, args.steps, args.warmup, clocks=head)
+        if head:
+            clocks = clk
+        cl_ms, _, cl_rep, _, _ = timed(True, False, args.steps, args.warmup)
+        na_ms, _, _, _, _ = timed(False, False, args.steps, args.warmup)
+        results[eng] = dict(ft_ms=ft_ms, ft_per=ft_per, ft_rep=ft_rep, injected=injected, clean_ms=cl_ms,
+                            clean_rep=cl_rep, noabft_ms=na_ms)
+    fb.ftblas_set_fp64_engine(engines[args.engine])
+
+    # Accuracy at the stated error: one more protected call from the known C_in, checked on
+    # sampled rows against the oracle.
+    err = None
+    if rank == 0:
+        import oracle as O
+        import synth as S
+        dC.copy_(dCin)
+        fb.check(fb.ftblas_dgemm(fb.COL_MAJOR, fb.NO_TRANS, fb.NO_TRANS, n, n, n, 1.5, dA.data_ptr(), n,
+                                 dB.data_ptr(), n, 0.5, dC.data_ptr(), n, st, None))
+        torch.cuda.synchronize(dev)
+        rows = np.unique(S.randint(SEED, 9, 4, 0, n - 1))
+        got = dC.view(n, n).t()[torch.as_tensor(rows, device=dev)].cpu().numpy()  # column-major: C[i, :]
+        ref = O.gemm_rows(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, n, n, n, 1.5, A, n, B, n, 0.5, Cin, n, rows)
+        err = float(np.abs(got - ref).max() / (np.abs(A).max() * np.abs(B).max() * n))
+
+    # End to end through the public host-buffer entry point: pinned host operands, copies
+    # in, protected GEMM, copies out (C and the report), synchronised per call.
+    e2e = None
+    if not args.no_e2e:
+        hA = torch.from_numpy(A).pin_memory()
+        hB = torch.from_numpy(B).pin_memory()
+        hC = torch.from_numpy(Cin).pin_memory()
+        hrep = fb.FtReport()
+        fb.ftblas_set_injection(None)
+
+        def hcall():
+            fb.check(fb.ftblas_dgemm_host(fb.COL_MAJOR, fb.NO_TRANS, fb.NO_TRANS, n, n, n, 1.5, hA.data_ptr(), n,
+                                          hB.data_ptr(), n, 0.5, hC.data_ptr(), n, st, ctypes.addressof(hrep)))
+
+        for _ in range(max(1, min(args.warmup, 2))):
+            hcall()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hcall()
+        barrier()
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": world * flops_step * args.steps / e2e_s / 1e12, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * n * n * 8, "d2h_bytes_per_step": n * n * 8 + fb.REPORT_BYTES}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        f, dt, thr = oracle_sample(n, A, B, Cin, n_tiles=16)
+        cpu = {"value": f / dt / 1e12, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"16 seeded {TILE}x{TILE} output tiles of the {n}^3 problem (full K, checksums included), "
+                         f"{dt:.1f} s"}
+
+    if rank != 0:
+        return 0
+    pk = peaks()
+    h = results[args.engine]
+    ft_ms = h["ft_ms"]
+    value = world * flops_step * args.steps / (ft_ms / 1e3) / 1e12
+    kernel_ms = statistics.mean(h["ft_per"])
+    achieved = flops_step / (kernel_ms / 1e3) / 1e12
+    bound = "alu" if args.engine == "dfma" else "tensor"
+    peak = pk["alu"] if bound == "alu" else pk["tensor"]
+
+    def tf(ms):
+        return flops_step * args.steps / (ms / 1e3) / 1e12
+
+    engines_out = {}
+    for eng, r in results.items():
+        engines_out[eng] = {
+            "ft_tflops_injected": tf(r["ft_ms"]), "ft_tflops_clean": tf(r["clean_ms"]),
+            "noabft_tflops": tf(r["noabft_ms"]),
+            "abft_overhead_pct_injected": 100.0 * (r["ft_ms"] / r["noabft_ms"] - 1.0),
+            "abft_overhead_pct_clean": 100.0 * (r["clean_ms"] / r["noabft_ms"] - 1.0),
+            "injected": r["injected"], "detected": r["ft_rep"]["detected"], "corrected": r["ft_rep"]["corrected"],
+            "false_alarms_clean": r["clean_rep"]["detected"], "uncorrectable": r["ft_rep"]["uncorrectable"],
+            "frac_of_fp64_alu_peak": tf(r["ft_ms"]) / pk["alu"],
+            "frac_of_fp64_tensor_peak": tf(r["ft_ms"]) / pk["tensor"],
+        }
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ft_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(n, args.engine),
+        "pct_of_peak": 100.0 * achieved / peak,
+        "abft_overhead_pct": engines_out[args.engine]["abft_overhead_pct_injected"],
+        "abft_overhead_pct_clean": engines_out[args.engine]["abft_overhead_pct_clean"],
+        "error_vs_oracle": {"normalized_max": err, "criterion": "max|C-C_ref|/(max|A| max|B| K) <= 1e-15",
+                            "rows_sampled": 4},
+        "faults": {"injected": h["injected"], "detected": h["ft_rep"]["detected"],
+                   "corrected": h["ft_rep"]["corrected"], "uncorrectable": h["ft_rep"]["uncorrectable"],
+                   "false_alarms_clean_run": h["clean_rep"]["detected"], "status": h["ft_rep"]["status"]},
+        "engines": engines_out,
+        "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "peak_source": pk["alu_src"] if bound == "alu" else pk["tensor_src"],
+                     "kernel": "dgemm_kernel (FT, " + args.engine + ")", "kernel_ms": kernel_ms},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist_mod.init_process_group("gloo", rank=rank, world_size=world)
+        dist = dist_mod
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, world)
+        return run_ours(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

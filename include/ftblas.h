@@ -1,0 +1,198 @@
+/*
+ * ftblas.h - C ABI of the GB300 (sm_103a) ABFT-protected GEMM.
+ *
+ * Operation (FT-BLAS, Zhai et al., ICS '21, Section II.A with Section V): the BLAS GEMM
+ *     C = alpha * op(A) * op(B) + beta * C,   op(X) = X or X^T,
+ * where op(A) is M x K, op(B) is K x N and C is M x N, protected by Huang-Abraham
+ * checksums (Section II.A): column sums e^T A and row sums B e are encoded while the
+ * operand tiles are staged, the row and column checksums of every output tile are
+ * verified after the product (C = beta*C folded in, Section V.B), and a single corrupted
+ * element per tile is located at the crossing of the mismatching row and column
+ * (Section V.A) and corrected (Section VI.C). One verification interval is one output
+ * tile over all of K in one call; ftblas_verification_tile() reports its shape.
+ *
+ * Storage follows BLAS/CBLAS: column-major (element (r, c) of X at X[r + c*ld], ld >=
+ * max(1, rows)) or row-major (X[r*ld + c], ld >= max(1, cols)), selected per call.
+ *
+ * Ownership and asynchrony: A, B, C are caller-owned DEVICE pointers; the library never
+ * frees them. A call validates its arguments on the host, enqueues its kernels on
+ * `stream` (a cudaStream_t; NULL = the legacy default stream) and returns without
+ * synchronising. The report, when given, must be device-accessible memory (device,
+ * pinned-mapped or managed); the call resets it on the stream and the kernels fill it, so
+ * it is valid after the stream has been synchronised. C and the report must not be used
+ * by other work on other streams while the call is in flight.
+ *
+ * Return values (all entry points): 0 on success; -p when argument p (1-based, in the
+ * order of the signature) is invalid, BLAS xerbla style; a positive FTBLAS_STATUS_* code
+ * otherwise. Detection results never change the return value (the call is asynchronous):
+ * they are in the report.
+ */
+#ifndef FTBLAS_H_
+#define FTBLAS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { FTBLAS_ROW_MAJOR = 101, FTBLAS_COL_MAJOR = 102 } ftblas_layout_t;   /* CBLAS values */
+typedef enum { FTBLAS_NO_TRANS = 111, FTBLAS_TRANS = 112 } ftblas_trans_t;
+
+/* Element types of ftblas_gemm_ex. */
+typedef enum {
+  FTBLAS_R_64F = 0,      /* binary64 */
+  FTBLAS_R_32F = 1,      /* binary32 */
+  FTBLAS_R_16BF = 2,     /* bfloat16 */
+  FTBLAS_R_8F_E4M3 = 3   /* OCP FP8 E4M3 (finite-only, max 448) */
+} ftblas_dtype_t;
+
+/* Positive status codes. */
+#define FTBLAS_STATUS_NOT_SUPPORTED 2   /* dtype / shape / alignment combination not provided */
+#define FTBLAS_STATUS_CUDA_ERROR 3      /* a CUDA runtime call failed (see ftblas_last_cuda_error) */
+#define FTBLAS_STATUS_ALLOC_FAILED 4    /* the library could not obtain workspace */
+
+/* Report status bits (ft_report_t.status). */
+#define FT_STATUS_TIMEOUT 1u            /* a bounded device wait gave up; affected tiles were not stored */
+#define FT_STATUS_RECORDS_TRUNCATED 2u  /* more than FTBLAS_MAX_RECORDS records were produced */
+
+/* Record kinds (ft_error_record_t.kind). */
+#define FT_KIND_CORRECTED 1       /* one row and one column mismatched: element located and recomputed */
+#define FT_KIND_CHECKSUM_ONLY 2   /* mismatch on one side only: fault in the checksum path; C kept */
+#define FT_KIND_UNCORRECTABLE 3   /* several rows and/or columns mismatched; C left as computed */
+#define FT_KIND_INPUT_NONFINITE 4 /* an encoded checksum of A, B or C_in is not finite; not checked */
+
+#define FTBLAS_MAX_RECORDS 64
+
+/* One detection event, in the caller's coordinates of C (row-major calls included). */
+typedef struct {
+  int64_t tile_row, tile_col;   /* verification tile: rows [tile_row*tile_rows, ...), columns likewise */
+  int64_t i, j;                 /* located element, or the first flagged row / column (-1: none) */
+  double delta_row;             /* C^r_ref(i) - C^r(i): reference minus predicted row checksum */
+  double delta_col;             /* C^c_ref(j) - C^c(j) */
+  double tau_row, tau_col;      /* round-off thresholds the deltas were compared with */
+  double value_before;          /* C(i, j) as computed, error included (FT_KIND_CORRECTED) */
+  double value_after;           /* C(i, j) as stored after recomputation */
+  int32_t kind;                 /* FT_KIND_* */
+  int32_t rows_flagged, cols_flagged;
+  int32_t reserved;
+} ft_error_record_t;
+
+/* Per-call detection report (Section VI.C: located element, magnitude, correction). */
+typedef struct {
+  uint64_t tiles_checked;     /* verification intervals (tiles) checked */
+  uint64_t detected;          /* tiles with any mismatch */
+  uint64_t corrected;         /* tiles with one located and corrected element */
+  uint64_t uncorrectable;     /* tiles left as computed: several mismatching rows/columns */
+  uint64_t checksum_only;     /* tiles with a mismatch on one side only */
+  uint64_t input_nonfinite;   /* tiles whose encoded input checksums were not finite */
+  uint32_t status;            /* FT_STATUS_* bits */
+  uint32_t n_records;         /* records produced (may exceed FTBLAS_MAX_RECORDS; see status) */
+  ft_error_record_t rec[FTBLAS_MAX_RECORDS];
+} ft_report_t;
+
+/* ---------------------------------------------------------------------------------- */
+/* Fault injection (Section VI.C: errors injected into C at chosen points, then        */
+/* detected, located and corrected). Test and benchmark facility; off by default.     */
+/* ---------------------------------------------------------------------------------- */
+
+#define FT_SITE_ACCUM 1     /* flip a bit of the running sum of C(i,j) after bk*floor(nk/2) products */
+#define FT_SITE_OUTPUT 2    /* perturb C(i,j) after alpha/beta, before verification */
+#define FT_SITE_CHECKSUM 3  /* perturb the predicted row checksum C^r(i) of the tile holding (i,j) */
+#define FT_MODE_BITFLIP 0   /* XOR bit `bit` (0 = lsb of the IEEE pattern of the accumulator type) */
+#define FT_MODE_ADD_REL 1   /* add sign * 2^rel_log2 * |value| */
+
+#define FTBLAS_MAX_FIXED_INJECTIONS 16
+#define FTBLAS_MAX_INJECTIONS_PER_LAUNCH 64
+
+typedef struct {
+  int64_t i, j;               /* element of C, caller's coordinates */
+  int32_t site, mode, bit, rel_log2, sign, reserved;
+} ft_inject_point_t;
+
+typedef struct {
+  uint64_t seed;              /* seeded draw: SplitMix64 stream seed ^ (launch * 0xD1B54A32D192ED03) */
+  int32_t site, mode;         /* FT_SITE_*, FT_MODE_* of drawn points */
+  int32_t bit_lo, bit_hi;     /* drawn bit range (inclusive) */
+  int32_t log2_lo, log2_hi;   /* drawn rel_log2 range (inclusive) */
+  int32_t every_n_launches;   /* launch n injects when n % every == seed % every; 0 = no draw */
+  int32_t errors_per_launch;  /* distinct tiles per injecting launch (<= FTBLAS_MAX_INJECTIONS_PER_LAUNCH) */
+  int32_t n_fixed;            /* > 0: inject exactly fixed[0..n_fixed-1] on every launch instead */
+  int32_t reserved;
+  ft_inject_point_t fixed[FTBLAS_MAX_FIXED_INJECTIONS];
+} ft_inject_t;
+
+/* Install (cfg != NULL) or remove (cfg == NULL) the process-wide injection plan and reset
+ * the launch counter to 0. Every protected call with M, N > 0 that passes validation
+ * counts as one launch. For launch n the seeded draw takes, per injection, six SplitMix64
+ * outputs in the order tile, row offset, column offset, bit, rel_log2, sign; tiles are
+ * numbered t = tile_row + tile_col * n_tile_rows in the caller's coordinates and drawn
+ * without replacement. Returns 0, or -1 when cfg is malformed (ranges, counts). */
+int ftblas_set_injection(const ft_inject_t* cfg);
+
+/* Protected launches counted since the last ftblas_set_injection. */
+uint64_t ftblas_injection_launch_count(void);
+
+/* ---------------------------------------------------------------------------------- */
+/* GEMM entry points                                                                  */
+/* ---------------------------------------------------------------------------------- */
+
+/* FP64 ABFT-protected GEMM (Sections II.A, V; products and checksums in binary64).
+ * Arguments 1-16: layout, transa, transb, M, N, K (>= 0), alpha, A, lda, B, ldb, beta, C,
+ * ldc, stream, report (NULL: no report). A and B are read only; C is read when beta != 0
+ * and written. M == 0 or N == 0 returns at once; K == 0 or alpha == 0 computes C = beta*C
+ * with no checks; beta == 0 never reads C (NaN there does not propagate). */
+int ftblas_dgemm(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,
+                 int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+                 const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                 void* stream, ft_report_t* report);
+
+/* The same kernel with the protection compiled out (no encode, verify or correction, no
+ * injection): the baseline the ABFT overhead is measured against. Same arguments; no
+ * report. */
+int ftblas_dgemm_noabft(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,
+                        int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+                        const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                        void* stream);
+
+/* ftblas_dgemm on HOST buffers: copies A, B (and C when beta != 0) to library-owned
+ * device workspace on `stream`, runs the protected GEMM, copies C and the report back and
+ * synchronises the stream before returning. report (host memory) may be NULL. Pinned host
+ * memory gives the fastest copies. Workspace grows to the largest call and is kept. */
+int ftblas_dgemm_host(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,
+                      int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+                      const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                      void* stream, ft_report_t* report);
+
+/* Shape of the verification tile used for a call, in the caller's coordinates of C, and
+ * the k-tile depth that sets the accumulator injection point (bk * floor(ceil(K/bk)/2)
+ * products). compute_type selects the kernel family (FTBLAS_R_64F for ftblas_dgemm).
+ * Returns 0, or a negative argument index. */
+int ftblas_verification_tile(ftblas_layout_t layout, ftblas_dtype_t compute_type,
+                             int64_t M, int64_t N, int64_t K,
+                             int64_t* tile_rows, int64_t* tile_cols, int64_t* k_tile);
+
+/* FP64 product engine: 0 = DFMA (SIMT fused multiply-add, default), 1 = DMMA (FP64
+ * tensor-core mma.sync m8n8k4). Both run the same staging, encode and epilogue. Returns
+ * the previous engine, or -1 for an unknown value. Process-wide. */
+int ftblas_set_fp64_engine(int engine);
+
+/* Staging path of the calling thread's most recent GEMM launch: 1 = operands staged by
+ * TMA (16-byte aligned base addresses and leading dimensions), 0 = cooperative loads (any
+ * other alignment), -1 = no kernel launched yet on this thread. For tests and tuning. */
+int ftblas_last_launch_used_tma(void);
+
+/* Human-readable text of a return code. */
+const char* ftblas_status_string(int code);
+
+/* cudaError_t of the last failing CUDA call made by the library on this thread (0: none). */
+int ftblas_last_cuda_error(void);
+
+/* Library version, e.g. "0.1.0". */
+const char* ftblas_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FTBLAS_H_ */

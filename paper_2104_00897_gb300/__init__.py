@@ -1,0 +1,258 @@
+"""Python binding of libftblas (the ABFT-protected GEMM of FT-BLAS on GB300).
+
+Argument marshalling only: every function here forwards to the C ABI of
+``include/ftblas.h`` under the same name, and the torch helpers just turn tensors into
+pointers, leading dimensions and the current CUDA stream. No step of the product,
+checksum encode, verification or correction runs in Python, and there is no CPU
+fallback: if the CUDA library is missing or cannot be loaded, importing the binding's
+functions raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+ROW_MAJOR, COL_MAJOR = 101, 102
+NO_TRANS, TRANS = 111, 112
+R_64F, R_32F, R_16BF, R_8F_E4M3 = 0, 1, 2, 3
+SITE_ACCUM, SITE_OUTPUT, SITE_CHECKSUM = 1, 2, 3
+MODE_BITFLIP, MODE_ADD_REL = 0, 1
+KIND_CORRECTED, KIND_CHECKSUM_ONLY, KIND_UNCORRECTABLE, KIND_INPUT_NONFINITE = 1, 2, 3, 4
+STATUS_TIMEOUT, STATUS_RECORDS_TRUNCATED = 1, 2
+ENGINE_DFMA, ENGINE_DMMA = 0, 1
+MAX_RECORDS = 64
+MAX_FIXED_INJECTIONS = 16
+MAX_INJECTIONS_PER_LAUNCH = 64
+
+
+class FtErrorRecord(C.Structure):
+    _fields_ = [
+        ("tile_row", C.c_int64), ("tile_col", C.c_int64), ("i", C.c_int64), ("j", C.c_int64),
+        ("delta_row", C.c_double), ("delta_col", C.c_double),
+        ("tau_row", C.c_double), ("tau_col", C.c_double),
+        ("value_before", C.c_double), ("value_after", C.c_double),
+        ("kind", C.c_int32), ("rows_flagged", C.c_int32), ("cols_flagged", C.c_int32), ("reserved", C.c_int32),
+    ]
+
+
+class FtReport(C.Structure):
+    _fields_ = [
+        ("tiles_checked", C.c_uint64), ("detected", C.c_uint64), ("corrected", C.c_uint64),
+        ("uncorrectable", C.c_uint64), ("checksum_only", C.c_uint64), ("input_nonfinite", C.c_uint64),
+        ("status", C.c_uint32), ("n_records", C.c_uint32),
+        ("rec", FtErrorRecord * MAX_RECORDS),
+    ]
+
+    def records(self):
+        return [self.rec[q] for q in range(min(self.n_records, MAX_RECORDS))]
+
+    def as_dict(self):
+        return dict(tiles_checked=self.tiles_checked, detected=self.detected, corrected=self.corrected,
+                    uncorrectable=self.uncorrectable, checksum_only=self.checksum_only,
+                    input_nonfinite=self.input_nonfinite, status=self.status, n_records=self.n_records,
+                    records=[{f: getattr(r, f) for f, _ in FtErrorRecord._fields_} for r in self.records()])
+
+
+class FtInjectPoint(C.Structure):
+    _fields_ = [("i", C.c_int64), ("j", C.c_int64), ("site", C.c_int32), ("mode", C.c_int32),
+                ("bit", C.c_int32), ("rel_log2", C.c_int32), ("sign", C.c_int32), ("reserved", C.c_int32)]
+
+
+class FtInject(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("site", C.c_int32), ("mode", C.c_int32),
+                ("bit_lo", C.c_int32), ("bit_hi", C.c_int32), ("log2_lo", C.c_int32), ("log2_hi", C.c_int32),
+                ("every_n_launches", C.c_int32), ("errors_per_launch", C.c_int32),
+                ("n_fixed", C.c_int32), ("reserved", C.c_int32),
+                ("fixed", FtInjectPoint * MAX_FIXED_INJECTIONS)]
+
+
+REPORT_BYTES = C.sizeof(FtReport)
+
+# (name, restype, argtypes) of every entry point declared in include/ftblas.h
+_GEMM_ARGS = [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64, C.c_double, C.c_void_p, C.c_int64,
+              C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_int64]
+SIGNATURES = {
+    "ftblas_set_injection": (C.c_int, [C.c_void_p]),
+    "ftblas_injection_launch_count": (C.c_uint64, []),
+    "ftblas_dgemm": (C.c_int, _GEMM_ARGS + [C.c_void_p, C.c_void_p]),
+    "ftblas_dgemm_noabft": (C.c_int, _GEMM_ARGS + [C.c_void_p]),
+    "ftblas_dgemm_host": (C.c_int, _GEMM_ARGS + [C.c_void_p, C.c_void_p]),
+    "ftblas_verification_tile": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64,
+                                           C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ftblas_set_fp64_engine": (C.c_int, [C.c_int]),
+    "ftblas_status_string": (C.c_char_p, [C.c_int]),
+    "ftblas_last_cuda_error": (C.c_int, []),
+    "ftblas_last_launch_used_tma": (C.c_int, []),
+    "ftblas_version": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libftblas.so (building it first if asked). Raises if it cannot be loaded."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_needed else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libftblas.so not found at {path}; run paper_2104_00897_gb300.build.build()")
+        lib = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _call(name, *args):
+    return getattr(load(), name)(*args)
+
+
+# ------------------------------------------------------------------ C ABI, same names
+def ftblas_dgemm(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream, report):
+    return _call("ftblas_dgemm", layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream, report)
+
+
+def ftblas_dgemm_noabft(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream):
+    return _call("ftblas_dgemm_noabft", layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream)
+
+
+def ftblas_dgemm_host(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream, report):
+    return _call("ftblas_dgemm_host", layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream,
+                 report)
+
+
+def ftblas_set_injection(cfg):
+    """cfg: FtInject, or None to switch injection off (also resets the launch counter)."""
+    return _call("ftblas_set_injection", None if cfg is None else C.addressof(cfg))
+
+
+def ftblas_injection_launch_count():
+    return int(_call("ftblas_injection_launch_count"))
+
+
+def ftblas_verification_tile(layout, compute_type, M, N, K):
+    r, c, k = C.c_int64(), C.c_int64(), C.c_int64()
+    rc = _call("ftblas_verification_tile", layout, compute_type, M, N, K, C.addressof(r), C.addressof(c),
+               C.addressof(k))
+    if rc != 0:
+        raise ValueError(f"ftblas_verification_tile: argument {-rc} invalid")
+    return r.value, c.value, k.value
+
+
+def ftblas_set_fp64_engine(engine):
+    return _call("ftblas_set_fp64_engine", engine)
+
+
+def ftblas_status_string(code):
+    return _call("ftblas_status_string", code).decode()
+
+
+def ftblas_last_cuda_error():
+    return _call("ftblas_last_cuda_error")
+
+
+def ftblas_last_launch_used_tma():
+    return _call("ftblas_last_launch_used_tma")
+
+
+def ftblas_version():
+    return _call("ftblas_version").decode()
+
+
+# ------------------------------------------------------------------ helpers
+def make_injection(seed=0, site=SITE_ACCUM, mode=MODE_BITFLIP, bit_lo=40, bit_hi=62, log2_lo=0, log2_hi=0,
+                   every_n_launches=0, errors_per_launch=0, fixed=()):
+    """Build an FtInject. ``fixed``: iterable of dicts with i, j and optional site, mode,
+    bit, rel_log2, sign; when given, those points are injected on every launch."""
+    cfg = FtInject(seed=seed, site=site, mode=mode, bit_lo=bit_lo, bit_hi=bit_hi, log2_lo=log2_lo, log2_hi=log2_hi,
+                   every_n_launches=every_n_launches, errors_per_launch=errors_per_launch, n_fixed=0, reserved=0)
+    pts = list(fixed)
+    if len(pts) > MAX_FIXED_INJECTIONS:
+        raise ValueError("too many fixed injection points")
+    for q, p in enumerate(pts):
+        cfg.fixed[q] = FtInjectPoint(i=p["i"], j=p["j"], site=p.get("site", SITE_ACCUM),
+                                     mode=p.get("mode", MODE_BITFLIP), bit=p.get("bit", 0),
+                                     rel_log2=p.get("rel_log2", 0), sign=p.get("sign", 1), reserved=0)
+    cfg.n_fixed = len(pts)
+    return cfg
+
+
+def check(rc, what="ftblas call"):
+    if rc != 0:
+        raise RuntimeError(f"{what} failed: {rc} ({ftblas_status_string(rc)}; cuda error {ftblas_last_cuda_error()})")
+    return rc
+
+
+def report_from_device(buf) -> FtReport:
+    """Copy a device report (a torch uint8 tensor of REPORT_BYTES) into an FtReport."""
+    host = buf.detach().to("cpu").numpy().tobytes()
+    return FtReport.from_buffer_copy(host)
+
+
+def new_report(device=None):
+    """A device buffer for one ft_report_t (torch uint8 tensor)."""
+    import torch
+    return torch.zeros(REPORT_BYTES, dtype=torch.uint8, device=device or "cuda")
+
+
+def _layout_of(t):
+    """(layout, ld) of a 2-D tensor whose storage is row- or column-major with a unit stride."""
+    r, c = t.shape
+    s0, s1 = t.stride()
+    if s1 == 1 and (s0 >= max(1, c) or r <= 1):
+        return ROW_MAJOR, max(s0, max(1, c))
+    if s0 == 1 and (s1 >= max(1, r) or c <= 1):
+        return COL_MAJOR, max(s1, max(1, r))
+    return None, None
+
+
+def dgemm(a, b, c=None, alpha=1.0, beta=0.0, trans_a=False, trans_b=False, report=None, protect=True,
+          stream=None):
+    """c = alpha * op(a) @ op(b) + beta * c on float64 CUDA tensors, protected by ABFT.
+
+    Tensors may be row-major or column-major (a unit stride in either dimension); the
+    layout of ``c`` decides the call's layout and the operands are brought to it by
+    copies when they differ. ``report``: a buffer from new_report() (or None). Returns c.
+    """
+    import torch
+    Ma, Ka = (a.shape[1], a.shape[0]) if trans_a else (a.shape[0], a.shape[1])
+    Kb, Nb = (b.shape[1], b.shape[0]) if trans_b else (b.shape[0], b.shape[1])
+    if Ka != Kb:
+        raise ValueError(f"inner dimensions differ: {Ka} vs {Kb}")
+    M, N, K = Ma, Nb, Ka
+    if c is None:
+        c = torch.empty((M, N), dtype=torch.float64, device=a.device)
+        if beta != 0.0:
+            raise ValueError("beta != 0 needs c")
+    layout, ldc = _layout_of(c)
+    if layout is None:
+        raise ValueError("c must have a unit stride in one dimension")
+
+    def as_layout(x):
+        lay, ld = _layout_of(x)
+        if lay == layout:
+            return x, ld
+        y = x.contiguous() if layout == ROW_MAJOR else x.t().contiguous().t()
+        return y, _layout_of(y)[1]
+
+    a2, lda = as_layout(a)
+    b2, ldb = as_layout(b)
+    st = stream if stream is not None else torch.cuda.current_stream(a.device).cuda_stream
+    ta = TRANS if trans_a else NO_TRANS
+    tb = TRANS if trans_b else NO_TRANS
+    if protect:
+        rc = ftblas_dgemm(layout, ta, tb, M, N, K, float(alpha), a2.data_ptr(), lda, b2.data_ptr(), ldb, float(beta),
+                          c.data_ptr(), ldc, st, report.data_ptr() if report is not None else None)
+    else:
+        rc = ftblas_dgemm_noabft(layout, ta, tb, M, N, K, float(alpha), a2.data_ptr(), lda, b2.data_ptr(), ldb,
+                                 float(beta), c.data_ptr(), ldc, st)
+    check(rc, "ftblas_dgemm")
+    return c

@@ -1,0 +1,604 @@
+// FP64 ABFT-protected GEMM for sm_103a (FT-BLAS, Zhai et al., ICS '21, Sections II.A, V).
+//
+// One CTA computes one 128 x 128 output tile over all of K; that tile is the verification
+// interval. Per k-tile (32 deep) the operand tiles are staged in shared memory by TMA
+// (3-stage mbarrier ring; a cooperative-load fallback covers pointers or leading dimensions
+// TMA cannot address). While staged they are reused, as the paper's fused packing reuses
+// each loaded element (Section V.B):
+//   E1  warp reductions give this k-tile's checksum row of A^c = [A; e^T A] (e^T A over the
+//       tile's rows) and checksum column of B^r = [B, Be] (Be over the tile's columns);
+//   E2  the predicted checksums accumulate C^r(i) += A(i,k) (Be)(k) and
+//       C^c(j) += (e^T A)(k) B(k,j), with upward-rounded binary32 magnitudes for the
+//       threshold;
+//   MMA the product, by one of two FP64 engines sharing this code: DFMA (8x8 register
+//       micro-tile of fused multiply-adds per thread) or DMMA (mma.sync.m8n8k4.f64 tensor
+//       core fragments). On GB300 both issue to the same FP64 pipe, so checksum work costs
+//       exactly its operation count: (3/128) of the product here.
+// Epilogue: C = alpha*acc + beta*C_in in registers; reference checksums C^r_ref, C^c_ref
+// from those registers (Section V.B reuses C at register level); compare with the
+// predicted ones against the rigorous round-off threshold; exactly one flagged row and
+// one flagged column locate the error (Section V.A), which is corrected by recomputing
+// that element with the identical instruction sequence (bit-exact fault-free value);
+// other patterns are classified and reported. Then the tile is stored.
+#include <climits>
+
+#include "ft_device.cuh"
+#include "ft_internal.h"
+
+namespace ftk {
+
+namespace {
+
+constexpr int BM = kDBM, BN = kDBN, BK = kDBK, STAGES = kDStages, NT = kDThreads;
+constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s per wait; a k-tile normally takes ~0.1 ms
+constexpr uint32_t kStageBytes = (BM * BK + BK * BN) * sizeof(double);
+
+struct __align__(1024) DSmem {
+  double a[STAGES][BM * BK];
+  double b[STAGES][BK * BN];
+  double encA[BK];        // e^T A over the tile's rows, per k of the current k-tile
+  double encB[BK];        // B e over the tile's columns
+  float encA_abs[BK];     // upward-rounded e^T |A|
+  float encB_abs[BK];     // upward-rounded |B| e
+  uint64_t full[STAGES];
+  int timeout;
+  int nonfinite;
+  int first_row, first_col;
+  double delta_row, delta_col;
+  float tau_row, tau_col;
+  int recompute;          // 1: the located element must be recomputed
+  int loc_i, loc_j;       // tile-local location
+};
+
+// Operand element (i, k) of the staged A tile and (k, j) of the staged B tile.
+template <bool AK>
+__device__ __forceinline__ double lds_a(const double* sA, int i, int k) {
+  return AK ? sA[i * BK + k] : sA[k * BM + i];
+}
+template <bool BKM>
+__device__ __forceinline__ double lds_b(const double* sB, int k, int j) {
+  return BKM ? sB[j * BK + k] : sB[k * BN + j];
+}
+
+// Kernel-frame global operand access (recompute and fallback loads).
+__device__ __forceinline__ double ldg_a(const DgemmParams& p, int64_t i, int64_t k) {
+  return p.a_kmajor ? p.A[k + i * p.lda] : p.A[i + k * p.lda];
+}
+__device__ __forceinline__ double ldg_b(const DgemmParams& p, int64_t k, int64_t j) {
+  return p.b_kmajor ? p.B[k + j * p.ldb] : p.B[j + k * p.ldb];
+}
+
+// ---------------------------------------------------------------------------------------
+// Product engines. Each thread owns NR x NC accumulators at tile rows row(t, r) and tile
+// columns col(t, c); threads sharing a row (column) have distinct row_slot (col_slot).
+// ---------------------------------------------------------------------------------------
+struct EngineDFMA {
+  static constexpr int NR = 8, NC = 8;
+  static constexpr int ROW_SLOTS = 16, COL_SLOTS = 16;
+  __device__ static int row(int t, int r) { return (t & 15) + 16 * r; }
+  __device__ static int col(int t, int c) { return (t >> 4) + 16 * c; }
+  __device__ static int row_slot(int t) { return t >> 4; }
+  __device__ static int col_slot(int t) { return t & 15; }
+
+  template <bool AK, bool BKM>
+  __device__ static void ktile(double (&acc)[NR][NC], const double* sA, const double* sB, int t) {
+    const int tr = t & 15, tc = t >> 4;
+#pragma unroll 2
+    for (int k = 0; k < BK; ++k) {
+      double a[NR], b[NC];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) a[r] = lds_a<AK>(sA, tr + 16 * r, k);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) b[c] = lds_b<BKM>(sB, k, tc + 16 * c);
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+    }
+  }
+
+  // Fault-free value of acc at kernel-frame element (gi, gj): the same fused multiply-add
+  // chain in ascending k (the zero-filled padding of the last k-tile adds exact zeros).
+  // Called by the owning thread only; returns true if this thread produced the value.
+  __device__ static bool recompute(const DgemmParams& p, int64_t gi, int64_t gj, int t, int li, int lj,
+                                   double& out) {
+    bool mine = false;
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) mine |= (row(t, r) == li && col(t, c) == lj);
+    if (!mine) return false;
+    double acc = 0.0;
+    for (int64_t k = 0; k < p.K; ++k) acc = fma(ldg_a(p, gi, k), ldg_b(p, k, gj), acc);
+    out = acc;
+    return true;
+  }
+};
+
+__device__ __forceinline__ void dmma884(double& d0, double& d1, double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+               : "+d"(d0), "+d"(d1)
+               : "d"(a), "d"(b));
+}
+
+struct EngineDMMA {
+  // 8 warps as 4 (rows) x 2 (columns); warp tile 32 x 64 = 4 x 8 fragments of 8 x 8.
+  // m8n8k4 fragments: A(g, q), B(q, g), C(g, 2q + e) with g = lane / 4, q = lane % 4.
+  static constexpr int NR = 4, NC = 16;
+  static constexpr int ROW_SLOTS = 8, COL_SLOTS = 32;
+  __device__ static int wm(int t) { return (t >> 5) & 3; }
+  __device__ static int wn(int t) { return t >> 7; }
+  __device__ static int g(int t) { return (t & 31) >> 2; }
+  __device__ static int q(int t) { return t & 3; }
+  __device__ static int row(int t, int r) { return 32 * wm(t) + 8 * r + g(t); }
+  __device__ static int col(int t, int c) { return 64 * wn(t) + 8 * (c >> 1) + 2 * q(t) + (c & 1); }
+  __device__ static int row_slot(int t) { return wn(t) * 4 + q(t); }
+  __device__ static int col_slot(int t) { return wm(t) * 8 + g(t); }
+
+  template <bool AK, bool BKM>
+  __device__ static void ktile(double (&acc)[NR][NC], const double* sA, const double* sB, int t) {
+    const int r0 = 32 * wm(t) + g(t), c0 = 64 * wn(t) + g(t), qq = q(t);
+#pragma unroll 2
+    for (int k = 0; k < BK; k += 4) {
+      double a[NR], b[NC / 2];
+#pragma unroll
+      for (int mb = 0; mb < NR; ++mb) a[mb] = lds_a<AK>(sA, r0 + 8 * mb, k + qq);
+#pragma unroll
+      for (int nb = 0; nb < NC / 2; ++nb) b[nb] = lds_b<BKM>(sB, k + qq, c0 + 8 * nb);
+#pragma unroll
+      for (int mb = 0; mb < NR; ++mb)
+#pragma unroll
+        for (int nb = 0; nb < NC / 2; ++nb) dmma884(acc[mb][2 * nb], acc[mb][2 * nb + 1], a[mb], b[nb]);
+    }
+  }
+
+  // Warp-cooperative recompute of the 8 x 8 fragment holding the element, with the same
+  // mma sequence over k in chunks of 4 (out-of-range operands are the zeros TMA filled).
+  __device__ static bool recompute(const DgemmParams& p, int64_t gi, int64_t gj, int t, int li, int lj,
+                                   double& out) {
+    const int w_row = li / 32, w_col = lj / 64;
+    if (wm(t) != w_row || wn(t) != w_col) return false;  // warp-uniform
+    const int64_t rb = gi - (li % 8), cb = gj - (lj % 8);  // fragment origin, kernel frame
+    const int64_t ra = rb + g(t), cbb = cb + g(t);
+    double d0 = 0.0, d1 = 0.0;
+    for (int64_t k0 = 0; k0 < p.K; k0 += 4) {
+      const int64_t k = k0 + q(t);
+      const double a = (ra < p.M && k < p.K) ? ldg_a(p, ra, k) : 0.0;
+      const double b = (cbb < p.N && k < p.K) ? ldg_b(p, k, cbb) : 0.0;
+      dmma884(d0, d1, a, b);
+    }
+    const int my_row = li % 8 == g(t);
+    const int my_col = (lj % 8) / 2 == q(t);
+    if (my_row && my_col) {
+      out = (lj & 1) ? d1 : d0;
+      return true;
+    }
+    return false;
+  }
+};
+
+__device__ void write_record(const DgemmParams& p, int kind, int64_t tr, int64_t tc, int64_t i, int64_t j,
+                             double drow, double dcol, double trow, double tcol, double before, double after,
+                             int nr, int nc) {
+  if (p.report == nullptr) return;
+  const unsigned slot = atomicAdd(&p.report->n_records, 1u);
+  if (slot >= FTBLAS_MAX_RECORDS) {
+    atomicOr(&p.report->status, FT_STATUS_RECORDS_TRUNCATED);
+    return;
+  }
+  ft_error_record_t& r = p.report->rec[slot];
+  if (p.swap_report) {
+    r.tile_row = tc; r.tile_col = tr; r.i = j; r.j = i;
+    r.delta_row = dcol; r.delta_col = drow; r.tau_row = tcol; r.tau_col = trow;
+    r.rows_flagged = nc; r.cols_flagged = nr;
+  } else {
+    r.tile_row = tr; r.tile_col = tc; r.i = i; r.j = j;
+    r.delta_row = drow; r.delta_col = dcol; r.tau_row = trow; r.tau_col = tcol;
+    r.rows_flagged = nr; r.cols_flagged = nc;
+  }
+  r.value_before = before;
+  r.value_after = after;
+  r.kind = kind;
+  r.reserved = 0;
+}
+
+// Cooperative (non-TMA) load of one k-tile into the same smem layout TMA produces.
+template <bool AK, bool BKM>
+__device__ void load_ktile_plain(const DgemmParams& p, double* sA, double* sB, int m0, int n0, int k0, int t) {
+  for (int idx = t; idx < BM * BK; idx += NT) {
+    int i, k;
+    if (AK) { i = idx / BK; k = idx % BK; } else { k = idx / BM; i = idx % BM; }
+    const int64_t gi = m0 + i, gk = k0 + k;
+    sA[idx] = (gi < p.M && gk < p.K) ? ldg_a(p, gi, gk) : 0.0;
+  }
+  for (int idx = t; idx < BK * BN; idx += NT) {
+    int k, j;
+    if (BKM) { j = idx / BK; k = idx % BK; } else { k = idx / BN; j = idx % BN; }
+    const int64_t gk = k0 + k, gj = n0 + j;
+    sB[idx] = (gk < p.K && gj < p.N) ? ldg_b(p, gk, gj) : 0.0;
+  }
+}
+
+template <bool AK, bool BKM>
+__device__ __forceinline__ void issue_ktile(DSmem& sm, const CUtensorMap* tmA, const CUtensorMap* tmB, int s,
+                                            int m0, int n0, int k0) {
+  mbar_arrive_expect_tx(&sm.full[s], kStageBytes);
+  if (AK) tma_load_2d(sm.a[s], tmA, &sm.full[s], k0, m0);
+  else tma_load_2d(sm.a[s], tmA, &sm.full[s], m0, k0);
+  if (BKM) tma_load_2d(sm.b[s], tmB, &sm.full[s], k0, n0);
+  else tma_load_2d(sm.b[s], tmB, &sm.full[s], n0, k0);
+}
+
+template <class E, bool AK, bool BKM, bool FT>
+__global__ void __launch_bounds__(NT, 1)
+    dgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 const __grid_constant__ DgemmParams p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  DSmem& sm = *reinterpret_cast<DSmem*>(smem_raw);
+  const int t = threadIdx.x;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int nk = (p.K + BK - 1) / BK;
+  const int kstar_tile = nk / 2;
+  const int nI = min(BM, p.M - m0), nJ = min(BN, p.N - n0);
+
+  if (t == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(&sm.full[s], 1);
+    sm.timeout = 0; sm.nonfinite = 0;
+    sm.first_row = INT_MAX; sm.first_col = INT_MAX;
+    sm.recompute = 0;
+    fence_mbar_init();
+    if (p.use_tma) {
+      tma_prefetch_desc(&tmA);
+      tma_prefetch_desc(&tmB);
+      for (int s = 0; s < STAGES && s < nk; ++s) issue_ktile<AK, BKM>(sm, &tmA, &tmB, s, m0, n0, s * BK);
+    }
+  }
+  __syncthreads();
+
+  double acc[E::NR][E::NC];
+#pragma unroll
+  for (int r = 0; r < E::NR; ++r)
+#pragma unroll
+    for (int c = 0; c < E::NC; ++c) acc[r][c] = 0.0;
+  double pred = 0.0;  // t < 128: alpha-free C^r(i = t) partial; t >= 128: C^c(j = t - 128)
+  float pmag = 0.0f;  // upward-rounded magnitude sum for the threshold
+
+  int kt = 0;
+  for (; kt < nk; ++kt) {
+    const int s = kt % STAGES;
+    if (p.use_tma) {
+      if (!mbar_wait_bounded(&sm.full[s], (kt / STAGES) & 1, kWaitLimitNs)) sm.timeout = 1;
+    } else {
+      load_ktile_plain<AK, BKM>(p, sm.a[s], sm.b[s], m0, n0, kt * BK, t);
+    }
+    __syncthreads();
+    if (sm.timeout) break;
+    const double* sA = sm.a[s];
+    const double* sB = sm.b[s];
+
+    if (FT) {
+      // Accumulator injection after bk * floor(nk / 2) products (test launches only).
+      if (kt == kstar_tile && p.inj.n > 0) {
+        for (int e = 0; e < p.inj.n; ++e) {
+          const InjectPoint& ip = p.inj.p[e];
+          if (ip.site != kSiteAccum || ip.mode != FT_MODE_BITFLIP) continue;
+          const int li = ip.i - m0, lj = ip.j - n0;
+          if (li < 0 || li >= nI || lj < 0 || lj >= nJ) continue;
+#pragma unroll
+          for (int r = 0; r < E::NR; ++r)
+#pragma unroll
+            for (int c = 0; c < E::NC; ++c)
+              if (E::row(t, r) == li && E::col(t, c) == lj) acc[r][c] = flip_bit_f64(acc[r][c], ip.bit);
+        }
+      }
+      // E1: e^T A (k = s < BK) and B e (k = s - BK) for this k-tile; 4 lanes per sum.
+      {
+        const int sidx = t >> 2, part = t & 3;
+        double v = 0.0;
+        float va = 0.0f;
+        if (sidx < BK) {
+#pragma unroll 8
+          for (int qq = 0; qq < BM / 4; ++qq) {
+            const double x = lds_a<AK>(sA, part + 4 * qq, sidx);
+            v += x;
+            va = add_up(va, abs_up(x));
+          }
+        } else {
+#pragma unroll 8
+          for (int qq = 0; qq < BN / 4; ++qq) {
+            const double x = lds_b<BKM>(sB, sidx - BK, part + 4 * qq);
+            v += x;
+            va = add_up(va, abs_up(x));
+          }
+        }
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        va = add_up(va, __shfl_xor_sync(0xffffffffu, va, 1));
+        va = add_up(va, __shfl_xor_sync(0xffffffffu, va, 2));
+        if (part == 0) {
+          if (sidx < BK) { sm.encA[sidx] = v; sm.encA_abs[sidx] = va; }
+          else { sm.encB[sidx - BK] = v; sm.encB_abs[sidx - BK] = va; }
+          if (!isfinite(v)) sm.nonfinite = 1;
+        }
+      }
+      __syncthreads();
+      // E2: C^r(i) += sum_k A(i,k) (Be)(k) for i = t; C^c(j) += sum_k (e^T A)(k) B(k,j) for
+      // j = t - 128. The k order is rotated by lane to spread shared-memory banks.
+      if (t < BM) {
+#pragma unroll 8
+        for (int kk = 0; kk < BK; ++kk) {
+          const int k = (kk + t) & (BK - 1);
+          const double x = lds_a<AK>(sA, t, k);
+          pred = fma(x, sm.encB[k], pred);
+          pmag = fma_up(abs_up(x), sm.encB_abs[k], pmag);
+        }
+      } else {
+        const int j = t - BM;
+#pragma unroll 8
+        for (int kk = 0; kk < BK; ++kk) {
+          const int k = (kk + t) & (BK - 1);
+          const double y = lds_b<BKM>(sB, k, j);
+          pred = fma(sm.encA[k], y, pred);
+          pmag = fma_up(sm.encA_abs[k], abs_up(y), pmag);
+        }
+      }
+    }
+
+    E::template ktile<AK, BKM>(acc, sA, sB, t);
+    __syncthreads();
+    if (p.use_tma && t == 0 && kt + STAGES < nk) issue_ktile<AK, BKM>(sm, &tmA, &tmB, s, m0, n0, (kt + STAGES) * BK);
+  }
+
+  if (sm.timeout) {
+    // Abandon the tile: wait (bounded) for copies this CTA still has in flight, then
+    // report. The output tile is not written.
+    if (t == 0) {
+      if (p.use_tma)
+        for (int k2 = kt; k2 < nk && k2 < kt + STAGES; ++k2)
+          (void)mbar_wait_bounded(&sm.full[k2 % STAGES], (k2 / STAGES) & 1, kWaitLimitNs);
+      if (p.report) atomicOr(&p.report->status, FT_STATUS_TIMEOUT);
+    }
+    return;
+  }
+
+  // ---------------------------------------------------------------- epilogue: C in registers
+  const bool beta_nz = (p.beta != 0.0);
+  // Partial-sum arrays overlay the operand ring (all copies have landed and been read).
+  double* rsum = sm.a[0];                                              // [ROW_SLOTS][BM] sum of C
+  double* rcin = rsum + E::ROW_SLOTS * BM;                             // sum of C_in
+  float* rabs = reinterpret_cast<float*>(rcin + E::ROW_SLOTS * BM);    // upward sum of |C|
+  float* rabc = rabs + E::ROW_SLOTS * BM;                              // upward sum of |C_in|
+  double* csum = sm.b[0];                                              // [COL_SLOTS][BN]
+  double* ccin = csum + E::COL_SLOTS * BN;
+  float* cabs = reinterpret_cast<float*>(ccin + E::COL_SLOTS * BN);
+  float* cabc = cabs + E::COL_SLOTS * BN;
+  static_assert((E::ROW_SLOTS * BM * 2 * 8 + E::ROW_SLOTS * BM * 2 * 4) <= (int)sizeof(double) * STAGES * BM * BK,
+                "row partials exceed the A ring");
+  static_assert((E::COL_SLOTS * BN * 2 * 8 + E::COL_SLOTS * BN * 2 * 4) <= (int)sizeof(double) * STAGES * BK * BN,
+                "column partials exceed the B ring");
+  const int rslot = E::row_slot(t), cslot = E::col_slot(t);
+  auto cin_at = [&](int li, int lj) -> double {
+    return (li < nI && lj < nJ) ? p.C[(int64_t)(m0 + li) + (int64_t)(n0 + lj) * p.ldc] : 0.0;
+  };
+  if (FT && beta_nz) {
+    // beta*C_in enters the predicted checksums (Section V.B): its row and column sums,
+    // read from C_in (cached) so no extra register array stays live beside acc.
+#pragma unroll 1
+    for (int r = 0; r < E::NR; ++r) {
+      double s = 0.0;
+      float sa = 0.0f;
+#pragma unroll 4
+      for (int c = 0; c < E::NC; ++c) { const double x = cin_at(E::row(t, r), E::col(t, c)); s += x; sa = add_up(sa, abs_up(x)); }
+      rcin[rslot * BM + E::row(t, r)] = s; rabc[rslot * BM + E::row(t, r)] = sa;
+    }
+#pragma unroll 1
+    for (int c = 0; c < E::NC; ++c) {
+      double s = 0.0;
+      float sa = 0.0f;
+#pragma unroll 4
+      for (int r = 0; r < E::NR; ++r) { const double x = cin_at(E::row(t, r), E::col(t, c)); s += x; sa = add_up(sa, abs_up(x)); }
+      ccin[cslot * BN + E::col(t, c)] = s; cabc[cslot * BN + E::col(t, c)] = sa;
+    }
+  } else if (FT) {
+#pragma unroll
+    for (int r = 0; r < E::NR; ++r) { rcin[rslot * BM + E::row(t, r)] = 0.0; rabc[rslot * BM + E::row(t, r)] = 0.0f; }
+#pragma unroll
+    for (int c = 0; c < E::NC; ++c) { ccin[cslot * BN + E::col(t, c)] = 0.0; cabc[cslot * BN + E::col(t, c)] = 0.0f; }
+  }
+#pragma unroll
+  for (int r = 0; r < E::NR; ++r)
+#pragma unroll
+    for (int c = 0; c < E::NC; ++c)
+      acc[r][c] = beta_nz ? fma(p.alpha, acc[r][c], p.beta * cin_at(E::row(t, r), E::col(t, c))) : p.alpha * acc[r][c];
+
+  if (FT) {
+    // Output-site injection (test launches only).
+    for (int e = 0; e < p.inj.n; ++e) {
+      const InjectPoint& ip = p.inj.p[e];
+      if (ip.site != kSiteOutput) continue;
+      const int li = ip.i - m0, lj = ip.j - n0;
+      if (li < 0 || li >= nI || lj < 0 || lj >= nJ) continue;
+#pragma unroll
+      for (int r = 0; r < E::NR; ++r)
+#pragma unroll
+        for (int c = 0; c < E::NC; ++c)
+          if (E::row(t, r) == li && E::col(t, c) == lj) {
+            double v = acc[r][c];
+            if (ip.mode == FT_MODE_BITFLIP) v = flip_bit_f64(v, ip.bit);
+            else {
+              const double em = ldexp(fabs(v), ip.rel_log2);
+              v = ip.sign < 0 ? v - em : v + em;
+            }
+            acc[r][c] = v;
+          }
+    }
+
+    // Reference checksums C^r_ref, C^c_ref from the registers (partial per slot).
+#pragma unroll
+    for (int r = 0; r < E::NR; ++r) {
+      double s = 0.0;
+      float sa = 0.0f;
+#pragma unroll
+      for (int c = 0; c < E::NC; ++c) { s += acc[r][c]; sa = add_up(sa, abs_up(acc[r][c])); }
+      rsum[rslot * BM + E::row(t, r)] = s; rabs[rslot * BM + E::row(t, r)] = sa;
+    }
+#pragma unroll
+    for (int c = 0; c < E::NC; ++c) {
+      double s = 0.0;
+      float sa = 0.0f;
+#pragma unroll
+      for (int r = 0; r < E::NR; ++r) { s += acc[r][c]; sa = add_up(sa, abs_up(acc[r][c])); }
+      csum[cslot * BN + E::col(t, c)] = s; cabs[cslot * BN + E::col(t, c)] = sa;
+    }
+    __syncthreads();
+
+    // Verify one row (t < 128) or one column (t >= 128) per thread.
+    const bool is_row = t < BM;
+    const int idx = is_row ? t : t - BM;
+    const int nslots = is_row ? E::ROW_SLOTS : E::COL_SLOTS;
+    const double* ps = is_row ? rsum : csum;
+    const double* pc = is_row ? rcin : ccin;
+    const float* pa = is_row ? rabs : cabs;
+    const float* pac = is_row ? rabc : cabc;
+    const int extent = is_row ? BM : BN;
+    double ref = 0.0, cin_sum = 0.0;
+    float R = 0.0f, Q = 0.0f;
+    for (int sl = 0; sl < nslots; ++sl) {
+      ref += ps[sl * extent + idx];
+      cin_sum += pc[sl * extent + idx];
+      R = add_up(R, pa[sl * extent + idx]);
+      Q = add_up(Q, pac[sl * extent + idx]);
+    }
+    double predicted = beta_nz ? fma(p.alpha, pred, p.beta * cin_sum) : p.alpha * pred;
+    if (beta_nz && !isfinite(cin_sum)) sm.nonfinite = 1;
+    for (int e = 0; e < p.inj.n; ++e) {  // checksum-path injection (test launches only)
+      const InjectPoint& ip = p.inj.p[e];
+      const bool hit_row = ip.site == kSiteChecksumRow && is_row && ip.i == m0 + idx && ip.j >= n0 && ip.j < n0 + nJ;
+      const bool hit_col = ip.site == kSiteChecksumCol && !is_row && ip.j == n0 + idx && ip.i >= m0 && ip.i < m0 + nI;
+      if (hit_row || hit_col) {
+        if (ip.mode == FT_MODE_BITFLIP) predicted = flip_bit_f64(predicted, ip.bit);
+        else {
+          const double em = ldexp(fabs(predicted), ip.rel_log2);
+          predicted = ip.sign < 0 ? predicted - em : predicted + em;
+        }
+      }
+    }
+    const double delta = ref - predicted;
+    // tau = 2 [gamma_{K+n+3} (|alpha| P + |beta| Q) + gamma_n R], n = columns (rows) summed.
+    const int n_other = is_row ? nJ : nI;
+    const float g1 = gamma_up((int64_t)p.K + n_other + 3), g2 = gamma_up(n_other);
+    const float aa = abs_up(p.alpha), bb = abs_up(p.beta);
+    float tau = fma_up(aa, pmag, mul_up(bb, Q));
+    tau = fma_up(g1, tau, mul_up(g2, R));
+    tau = mul_up(2.0f, tau);
+    const bool valid = idx < (is_row ? nI : nJ);
+    const bool flagged = valid && !(fabs(delta) <= (double)tau);
+    if (flagged) atomicMin(is_row ? &sm.first_row : &sm.first_col, idx);
+    const int nr = __syncthreads_count(is_row && flagged);
+    const int nc = __syncthreads_count(!is_row && flagged);
+    if (is_row && idx == sm.first_row) { sm.delta_row = delta; sm.tau_row = tau; }
+    if (!is_row && idx == sm.first_col) { sm.delta_col = delta; sm.tau_col = tau; }
+    __syncthreads();
+
+    const bool nonfinite = sm.nonfinite != 0;
+    const int64_t tr = blockIdx.x, tc = blockIdx.y;
+    if (!nonfinite && nr == 1 && nc == 1) {
+      // Located at the crossing of the flagged row and column; recompute it.
+      const int li = sm.first_row, lj = sm.first_col;
+      const int64_t gi = m0 + li, gj = n0 + lj;
+      double acc_fixed;
+      const bool mine = E::recompute(p, gi, gj, t, li, lj, acc_fixed);
+      if (mine) {
+        const double cin = beta_nz ? p.C[gi + gj * p.ldc] : 0.0;
+        const double fixed = beta_nz ? fma(p.alpha, acc_fixed, p.beta * cin) : p.alpha * acc_fixed;
+        double before = 0.0;
+#pragma unroll
+        for (int r = 0; r < E::NR; ++r)
+#pragma unroll
+          for (int c = 0; c < E::NC; ++c)
+            if (E::row(t, r) == li && E::col(t, c) == lj) { before = acc[r][c]; acc[r][c] = fixed; }
+        write_record(p, FT_KIND_CORRECTED, tr, tc, gi, gj, sm.delta_row, sm.delta_col, sm.tau_row, sm.tau_col,
+                     before, fixed, nr, nc);
+      }
+    } else if (t == 0 && (nonfinite || nr > 0 || nc > 0)) {
+      const int kind = nonfinite ? FT_KIND_INPUT_NONFINITE
+                       : (nr == 0 || nc == 0) ? FT_KIND_CHECKSUM_ONLY
+                                              : FT_KIND_UNCORRECTABLE;
+      const int64_t gi = nr > 0 ? m0 + sm.first_row : -1;
+      const int64_t gj = nc > 0 ? n0 + sm.first_col : -1;
+      write_record(p, kind, tr, tc, gi, gj, nr > 0 ? sm.delta_row : 0.0, nc > 0 ? sm.delta_col : 0.0,
+                   nr > 0 ? sm.tau_row : 0.0, nc > 0 ? sm.tau_col : 0.0, 0.0, 0.0, nr, nc);
+    }
+    if (t == 0 && p.report) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(&p.report->tiles_checked), 1ull);
+      if (nonfinite) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&p.report->input_nonfinite), 1ull);
+      } else if (nr > 0 || nc > 0) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&p.report->detected), 1ull);
+        unsigned long long* ctr = (nr == 1 && nc == 1) ? reinterpret_cast<unsigned long long*>(&p.report->corrected)
+                                  : (nr == 0 || nc == 0) ? reinterpret_cast<unsigned long long*>(&p.report->checksum_only)
+                                                         : reinterpret_cast<unsigned long long*>(&p.report->uncorrectable);
+        atomicAdd(ctr, 1ull);
+      }
+    }
+  }
+
+  // Store the tile.
+#pragma unroll
+  for (int c = 0; c < E::NC; ++c) {
+#pragma unroll
+    for (int r = 0; r < E::NR; ++r) {
+      const int li = E::row(t, r), lj = E::col(t, c);
+      if (li < nI && lj < nJ) p.C[(int64_t)(m0 + li) + (int64_t)(n0 + lj) * p.ldc] = acc[r][c];
+    }
+  }
+}
+
+__global__ void scale_kernel(double* C, int64_t ldc, int32_t M, int32_t N, double beta) {
+  const int64_t total = (int64_t)M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % M, j = e / M;
+    double* c = C + i + j * ldc;
+    *c = (beta == 0.0) ? 0.0 : beta * *c;
+  }
+}
+
+template <class E, bool AK, bool BKM, bool FT>
+cudaError_t launch_one(const DgemmParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, cudaStream_t st) {
+  auto kern = dgemm_kernel<E, AK, BKM, FT>;
+  // Set on every launch: the attribute is per device and the call costs microseconds.
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DSmem));
+  if (e != cudaSuccess) return e;
+  dim3 grid((p.M + BM - 1) / BM, (p.N + BN - 1) / BN);
+  kern<<<grid, NT, sizeof(DSmem), st>>>(*tmA, *tmB, p);
+  return cudaGetLastError();
+}
+
+template <class E, bool FT>
+cudaError_t launch_layout(const DgemmParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, cudaStream_t st) {
+  if (p.a_kmajor) {
+    return p.b_kmajor ? launch_one<E, true, true, FT>(p, tmA, tmB, st) : launch_one<E, true, false, FT>(p, tmA, tmB, st);
+  }
+  return p.b_kmajor ? launch_one<E, false, true, FT>(p, tmA, tmB, st) : launch_one<E, false, false, FT>(p, tmA, tmB, st);
+}
+
+}  // namespace
+
+cudaError_t launch_dgemm(const DgemmParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, bool ft, int engine,
+                         cudaStream_t stream) {
+  if (engine == kEngineDMMA) {
+    return ft ? launch_layout<EngineDMMA, true>(p, tmA, tmB, stream) : launch_layout<EngineDMMA, false>(p, tmA, tmB, stream);
+  }
+  return ft ? launch_layout<EngineDFMA, true>(p, tmA, tmB, stream) : launch_layout<EngineDFMA, false>(p, tmA, tmB, stream);
+}
+
+cudaError_t launch_scale(double* C, int64_t ldc, int32_t M, int32_t N, double beta, cudaStream_t stream) {
+  const int64_t total = (int64_t)M * N;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  scale_kernel<<<blocks, 256, 0, stream>>>(C, ldc, M, N, beta);
+  return cudaGetLastError();
+}
+
+}  // namespace ftk

@@ -1,0 +1,65 @@
+// Internal declarations shared by the host API (ftblas_api.cu) and the kernel translation
+// units. Everything here is in the KERNEL frame: a column-major problem C = alpha *
+// op(A) op(B) + beta C. A row-major call is mapped to it by computing C^T = op(B)^T op(A)^T,
+// so kernel "rows" are caller columns; `swap_report` tells the kernels to write report
+// records back in the caller's frame.
+#pragma once
+
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "../../include/ftblas.h"
+
+namespace ftk {
+
+// Injection sites in the kernel frame (the caller's FT_SITE_CHECKSUM maps to a row or a
+// column checksum depending on the layout).
+enum : int32_t { kSiteAccum = 1, kSiteOutput = 2, kSiteChecksumRow = 3, kSiteChecksumCol = 4 };
+
+struct InjectPoint {
+  int32_t i, j;          // kernel-frame element
+  int32_t site, mode;    // kSite*, FT_MODE_*
+  int32_t bit, rel_log2, sign, pad;
+};
+
+constexpr int kMaxInject = FTBLAS_MAX_INJECTIONS_PER_LAUNCH;
+
+struct InjectList {
+  int32_t n;
+  int32_t pad;
+  InjectPoint p[kMaxInject];
+};
+
+// Parameters of one FP64 launch (passed by value as a __grid_constant__ struct).
+struct DgemmParams {
+  int32_t M, N, K;               // kernel frame
+  int32_t use_tma;               // 1: operands staged by TMA; 0: by cooperative loads
+  double alpha, beta;
+  const double* A; int64_t lda;  // kernel-frame op(A) source (recompute, fallback loads)
+  const double* B; int64_t ldb;
+  double* C; int64_t ldc;
+  int32_t a_kmajor, b_kmajor;    // storage: A k-contiguous?  B k-contiguous?
+  ft_report_t* report;           // may be null
+  int32_t swap_report;           // 1: records in the transposed (caller row-major) frame
+  int32_t pad_;
+  InjectList inj;
+};
+
+// FP64 tile geometry (all engines).
+constexpr int kDBM = 128;      // tile rows (kernel frame)
+constexpr int kDBN = 128;      // tile columns
+constexpr int kDBK = 32;       // k-tile depth
+constexpr int kDStages = 3;    // smem ring depth
+constexpr int kDThreads = 256; // 8 warps, all compute
+
+enum Fp64Engine : int { kEngineDFMA = 0, kEngineDMMA = 1 };
+
+// Launch the FP64 kernel family. `ft` selects protection. Returns a cudaError_t.
+cudaError_t launch_dgemm(const DgemmParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB,
+                         bool ft, int engine, cudaStream_t stream);
+
+// C = beta * C over an M x N column-major kernel-frame matrix (quick-return path).
+cudaError_t launch_scale(double* C, int64_t ldc, int32_t M, int32_t N, double beta, cudaStream_t stream);
+
+}  // namespace ftk

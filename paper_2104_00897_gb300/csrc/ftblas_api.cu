@@ -1,0 +1,389 @@
+// Host side of the C ABI declared in include/ftblas.h: argument validation (BLAS xerbla
+// style), the layout/transpose mapping to the column-major kernel frame, TMA descriptors,
+// the injection plan, and the host-buffer variant. No compute happens here: every step of
+// the product, encode, verification and correction runs in the kernels.
+#include <cudaTypedefs.h>
+
+#include <atomic>
+#include <cstring>
+#include <mutex>
+
+#include "ft_internal.h"
+
+using namespace ftk;
+
+namespace {
+
+thread_local int g_last_cuda_error = 0;
+thread_local int g_last_used_tma = -1;
+std::atomic<int> g_fp64_engine{kEngineDFMA};
+
+// ------------------------------------------------------------------ injection plan state
+std::mutex g_inj_mu;
+bool g_inj_on = false;
+ft_inject_t g_inj;
+uint64_t g_launch = 0;
+
+int record_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return 0;
+  g_last_cuda_error = static_cast<int>(e);
+  return FTBLAS_STATUS_CUDA_ERROR;
+}
+
+// SplitMix64 step (Steele, Lea and Flood, OOPSLA 2014).
+uint64_t splitmix_next(uint64_t& s) {
+  s += 0x9E3779B97F4A7C15ull;
+  uint64_t z = s;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+struct CallerPoint {
+  int64_t i, j;
+  int32_t site, mode, bit, rel_log2, sign;
+};
+
+// The points injected into this launch, in the caller's coordinates. The seeded draw is
+// the one documented beside ftblas_set_injection in the header.
+int plan_injections(int64_t M, int64_t N, int64_t tile_rows, int64_t tile_cols, CallerPoint* out) {
+  std::lock_guard<std::mutex> lk(g_inj_mu);
+  const uint64_t launch = g_launch++;
+  if (!g_inj_on) return 0;
+  const ft_inject_t& c = g_inj;
+  int n = 0;
+  if (c.n_fixed > 0) {
+    for (int q = 0; q < c.n_fixed && n < kMaxInject; ++q) {
+      const ft_inject_point_t& f = c.fixed[q];
+      if (f.i < 0 || f.i >= M || f.j < 0 || f.j >= N) continue;
+      out[n++] = CallerPoint{f.i, f.j, f.site, f.mode, f.bit, f.rel_log2, f.sign};
+    }
+    return n;
+  }
+  if (c.every_n_launches <= 0 || c.errors_per_launch <= 0) return 0;
+  const uint64_t every = static_cast<uint64_t>(c.every_n_launches);
+  if (launch % every != c.seed % every) return 0;
+  const int64_t tr = (M + tile_rows - 1) / tile_rows, tc = (N + tile_cols - 1) / tile_cols;
+  const int64_t ntiles = tr * tc;
+  int64_t want = c.errors_per_launch;
+  if (want > ntiles) want = ntiles;
+  if (want > kMaxInject) want = kMaxInject;
+  uint64_t st = c.seed ^ (launch * 0xD1B54A32D192ED03ull);
+  while (n < want) {
+    const uint64_t t = splitmix_next(st) % static_cast<uint64_t>(ntiles);
+    const uint64_t ri = splitmix_next(st), rj = splitmix_next(st), rb = splitmix_next(st);
+    const uint64_t rp = splitmix_next(st), rs = splitmix_next(st);
+    const int64_t trow = static_cast<int64_t>(t) % tr, tcol = static_cast<int64_t>(t) / tr;
+    bool dup = false;
+    for (int q = 0; q < n; ++q)
+      if (out[q].i / tile_rows == trow && out[q].j / tile_cols == tcol) dup = true;
+    if (dup) continue;
+    const int64_t rows = (trow == tr - 1) ? M - trow * tile_rows : tile_rows;
+    const int64_t cols = (tcol == tc - 1) ? N - tcol * tile_cols : tile_cols;
+    CallerPoint& pnt = out[n++];
+    pnt.i = trow * tile_rows + static_cast<int64_t>(ri % static_cast<uint64_t>(rows));
+    pnt.j = tcol * tile_cols + static_cast<int64_t>(rj % static_cast<uint64_t>(cols));
+    pnt.site = c.site;
+    pnt.mode = c.mode;
+    pnt.bit = c.bit_lo + static_cast<int32_t>(rb % static_cast<uint64_t>(c.bit_hi - c.bit_lo + 1));
+    pnt.rel_log2 = c.log2_lo + static_cast<int32_t>(rp % static_cast<uint64_t>(c.log2_hi - c.log2_lo + 1));
+    pnt.sign = (rs & 1) ? -1 : 1;
+  }
+  return n;
+}
+
+// ------------------------------------------------------------------ TMA descriptors
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2-D FP64 tensor map: `inner` contiguous elements, `outer` lines `ld` elements apart.
+bool make_map_f64(CUtensorMap* map, const void* base, int64_t inner, int64_t outer, int64_t ld, uint32_t box_inner,
+                  uint32_t box_outer) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
+  if (((ld * 8) & 15) != 0 || ld * 8 >= (int64_t(1) << 40)) return false;
+  if (inner <= 0 || outer <= 0 || inner > (int64_t(1) << 32) || outer > (int64_t(1) << 32)) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(outer)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld * 8)};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// ------------------------------------------------------------------ validation
+struct Frame {
+  // kernel frame (column-major): C' = alpha op(A') op(B') + beta C'
+  int64_t M, N;
+  const void* A;
+  int64_t lda;
+  const void* B;
+  int64_t ldb;
+  bool a_kmajor, b_kmajor, swap;
+};
+
+int validate(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B,
+             int64_t ldb, const void* C, int64_t ldc, bool need_ab) {
+  if (layout != FTBLAS_ROW_MAJOR && layout != FTBLAS_COL_MAJOR) return -1;
+  if (ta != FTBLAS_NO_TRANS && ta != FTBLAS_TRANS) return -2;
+  if (tb != FTBLAS_NO_TRANS && tb != FTBLAS_TRANS) return -3;
+  if (M < 0) return -4;
+  if (N < 0) return -5;
+  if (K < 0) return -6;
+  const bool col = layout == FTBLAS_COL_MAJOR;
+  // rows / cols of the stored A and B
+  const int64_t a_rows = (ta == FTBLAS_NO_TRANS) ? M : K, a_cols = (ta == FTBLAS_NO_TRANS) ? K : M;
+  const int64_t b_rows = (tb == FTBLAS_NO_TRANS) ? K : N, b_cols = (tb == FTBLAS_NO_TRANS) ? N : K;
+  const int64_t need_lda = col ? (a_rows > 1 ? a_rows : 1) : (a_cols > 1 ? a_cols : 1);
+  const int64_t need_ldb = col ? (b_rows > 1 ? b_rows : 1) : (b_cols > 1 ? b_cols : 1);
+  const int64_t need_ldc = col ? (M > 1 ? M : 1) : (N > 1 ? N : 1);
+  if (need_ab && A == nullptr) return -8;
+  if (lda < need_lda) return -9;
+  if (need_ab && B == nullptr) return -10;
+  if (ldb < need_ldb) return -11;
+  if (M > 0 && N > 0 && C == nullptr) return -13;
+  if (ldc < need_ldc) return -14;
+  return 0;
+}
+
+Frame map_frame(int layout, int ta, int tb, int64_t M, int64_t N, const void* A, int64_t lda, const void* B,
+                int64_t ldb) {
+  Frame f;
+  if (layout == FTBLAS_COL_MAJOR) {
+    f = Frame{M, N, A, lda, B, ldb, ta == FTBLAS_TRANS, tb == FTBLAS_NO_TRANS, false};
+  } else {
+    // C^T = op(B)^T op(A)^T over the same memory read column-major.
+    f = Frame{N, M, B, ldb, A, lda, tb == FTBLAS_TRANS, ta == FTBLAS_NO_TRANS, true};
+  }
+  return f;
+}
+
+constexpr int64_t kMaxDim = (int64_t(1) << 31) - 256;
+
+int dgemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+               int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* stream,
+               ft_report_t* report, bool ft) {
+  const bool need_ab = (K > 0 && alpha != 0.0 && M > 0 && N > 0);
+  int v = validate(layout, ta, tb, M, N, K, A, lda, B, ldb, C, ldc, need_ab);
+  if (v != 0) return v;
+  if (M > kMaxDim || N > kMaxDim || K > kMaxDim) return FTBLAS_STATUS_NOT_SUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (ft && report != nullptr) {
+    if (int e = record_cuda(cudaMemsetAsync(report, 0, sizeof(ft_report_t), st))) return e;
+  }
+  if (M == 0 || N == 0) return 0;
+  const Frame f = map_frame(layout, ta, tb, M, N, A, lda, B, ldb);
+  CallerPoint pts[kMaxInject];
+  int npts = 0;
+  if (ft) {
+    const int64_t tile_rows = f.swap ? kDBN : kDBM, tile_cols = f.swap ? kDBM : kDBN;
+    npts = plan_injections(M, N, tile_rows, tile_cols, pts);
+  }
+  if (K == 0 || alpha == 0.0) return record_cuda(launch_scale(C, ldc, (int32_t)f.M, (int32_t)f.N, beta, st));
+
+  DgemmParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.M = (int32_t)f.M; p.N = (int32_t)f.N; p.K = (int32_t)K;
+  p.alpha = alpha; p.beta = beta;
+  p.A = static_cast<const double*>(f.A); p.lda = f.lda;
+  p.B = static_cast<const double*>(f.B); p.ldb = f.ldb;
+  p.C = C; p.ldc = ldc;
+  p.a_kmajor = f.a_kmajor; p.b_kmajor = f.b_kmajor;
+  p.report = ft ? report : nullptr;
+  p.swap_report = f.swap;
+  p.inj.n = 0;
+  for (int q = 0; q < npts; ++q) {
+    InjectPoint& ip = p.inj.p[p.inj.n++];
+    const CallerPoint& c = pts[q];
+    ip.i = (int32_t)(f.swap ? c.j : c.i);
+    ip.j = (int32_t)(f.swap ? c.i : c.j);
+    ip.site = c.site == FT_SITE_CHECKSUM ? (f.swap ? kSiteChecksumCol : kSiteChecksumRow) : c.site;
+    ip.mode = c.mode; ip.bit = c.bit; ip.rel_log2 = c.rel_log2; ip.sign = c.sign; ip.pad = 0;
+  }
+  CUtensorMap tmA, tmB;
+  std::memset(&tmA, 0, sizeof(tmA));
+  std::memset(&tmB, 0, sizeof(tmB));
+  bool ok = f.a_kmajor ? make_map_f64(&tmA, f.A, K, f.M, f.lda, kDBK, kDBM)
+                       : make_map_f64(&tmA, f.A, f.M, K, f.lda, kDBM, kDBK);
+  ok = ok && (f.b_kmajor ? make_map_f64(&tmB, f.B, K, f.N, f.ldb, kDBK, kDBN)
+                         : make_map_f64(&tmB, f.B, f.N, K, f.ldb, kDBN, kDBK));
+  p.use_tma = ok ? 1 : 0;
+  g_last_used_tma = p.use_tma;
+  return record_cuda(launch_dgemm(p, &tmA, &tmB, ft, g_fp64_engine.load(), st));
+}
+
+// ------------------------------------------------------------------ host-buffer workspace
+std::mutex g_ws_mu;
+void* g_ws = nullptr;
+size_t g_ws_bytes = 0;
+int g_ws_device = -1;
+
+}  // namespace
+
+extern "C" {
+
+int ftblas_set_injection(const ft_inject_t* cfg) {
+  std::lock_guard<std::mutex> lk(g_inj_mu);
+  g_launch = 0;
+  if (cfg == nullptr) {
+    g_inj_on = false;
+    return 0;
+  }
+  if (cfg->n_fixed < 0 || cfg->n_fixed > FTBLAS_MAX_FIXED_INJECTIONS) return -1;
+  if (cfg->n_fixed == 0) {
+    if (cfg->every_n_launches < 0 || cfg->errors_per_launch < 0 ||
+        cfg->errors_per_launch > FTBLAS_MAX_INJECTIONS_PER_LAUNCH)
+      return -1;
+    if (cfg->bit_lo < 0 || cfg->bit_hi > 63 || cfg->bit_lo > cfg->bit_hi) return -1;
+    if (cfg->log2_lo > cfg->log2_hi) return -1;
+    if (cfg->site < FT_SITE_ACCUM || cfg->site > FT_SITE_CHECKSUM) return -1;
+    if (cfg->mode != FT_MODE_BITFLIP && cfg->mode != FT_MODE_ADD_REL) return -1;
+  }
+  for (int q = 0; q < cfg->n_fixed; ++q) {
+    const ft_inject_point_t& f = cfg->fixed[q];
+    if (f.site < FT_SITE_ACCUM || f.site > FT_SITE_CHECKSUM) return -1;
+    if (f.mode != FT_MODE_BITFLIP && f.mode != FT_MODE_ADD_REL) return -1;
+    if (f.mode == FT_MODE_BITFLIP && (f.bit < 0 || f.bit > 63)) return -1;
+  }
+  g_inj = *cfg;
+  g_inj_on = true;
+  return 0;
+}
+
+uint64_t ftblas_injection_launch_count(void) {
+  std::lock_guard<std::mutex> lk(g_inj_mu);
+  return g_launch;
+}
+
+int ftblas_dgemm(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb, int64_t M, int64_t N,
+                 int64_t K, double alpha, const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                 double* C, int64_t ldc, void* stream, ft_report_t* report) {
+  return dgemm_impl(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, stream, report, true);
+}
+
+int ftblas_dgemm_noabft(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb, int64_t M, int64_t N,
+                        int64_t K, double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                        double beta, double* C, int64_t ldc, void* stream) {
+  return dgemm_impl(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, stream, nullptr, false);
+}
+
+int ftblas_dgemm_host(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb, int64_t M, int64_t N,
+                      int64_t K, double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                      double beta, double* C, int64_t ldc, void* stream, ft_report_t* report) {
+  const bool need_ab = (K > 0 && alpha != 0.0 && M > 0 && N > 0);
+  int v = validate(layout, transa, transb, M, N, K, A, lda, B, ldb, C, ldc, need_ab);
+  if (v != 0) return v;
+  const bool col = layout == FTBLAS_COL_MAJOR;
+  // Stored extents (contiguous run length x number of runs) of A, B, C.
+  const int64_t a_rows = (transa == FTBLAS_NO_TRANS) ? M : K, a_cols = (transa == FTBLAS_NO_TRANS) ? K : M;
+  const int64_t b_rows = (transb == FTBLAS_NO_TRANS) ? K : N, b_cols = (transb == FTBLAS_NO_TRANS) ? N : K;
+  const int64_t a_run = col ? a_rows : a_cols, a_cnt = col ? a_cols : a_rows;
+  const int64_t b_run = col ? b_rows : b_cols, b_cnt = col ? b_cols : b_rows;
+  const int64_t c_run = col ? M : N, c_cnt = col ? N : M;
+  auto even = [](int64_t x) { return x < 2 ? int64_t(2) : (x + 1) & ~int64_t(1); };
+  const int64_t dlda = even(a_run), dldb = even(b_run), dldc = even(c_run);
+  const size_t bytesA = need_ab ? size_t(dlda) * a_cnt * 8 : 0, bytesB = need_ab ? size_t(dldb) * b_cnt * 8 : 0;
+  const size_t bytesC = size_t(dldc) * c_cnt * 8;
+  auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t total = up(bytesA) + up(bytesB) + up(bytesC) + up(sizeof(ft_report_t));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  int dev = 0;
+  if (int e = record_cuda(cudaGetDevice(&dev))) return e;
+  if (g_ws == nullptr || g_ws_bytes < total || g_ws_device != dev) {
+    if (g_ws) {
+      cudaStreamSynchronize(st);
+      int cur = dev;
+      if (g_ws_device >= 0 && g_ws_device != dev) cudaSetDevice(g_ws_device);
+      cudaFree(g_ws);
+      if (cur != g_ws_device) cudaSetDevice(cur);
+      g_ws = nullptr;
+    }
+    if (cudaMalloc(&g_ws, total) != cudaSuccess) {
+      g_ws = nullptr; g_ws_bytes = 0;
+      return FTBLAS_STATUS_ALLOC_FAILED;
+    }
+    g_ws_bytes = total;
+    g_ws_device = dev;
+  }
+  char* base = static_cast<char*>(g_ws);
+  double* dA = reinterpret_cast<double*>(base);
+  double* dB = reinterpret_cast<double*>(base + up(bytesA));
+  double* dC = reinterpret_cast<double*>(base + up(bytesA) + up(bytesB));
+  ft_report_t* dR = reinterpret_cast<ft_report_t*>(base + up(bytesA) + up(bytesB) + up(bytesC));
+  if (need_ab) {
+    if (int e = record_cuda(cudaMemcpy2DAsync(dA, dlda * 8, A, lda * 8, a_run * 8, a_cnt, cudaMemcpyHostToDevice, st)))
+      return e;
+    if (int e = record_cuda(cudaMemcpy2DAsync(dB, dldb * 8, B, ldb * 8, b_run * 8, b_cnt, cudaMemcpyHostToDevice, st)))
+      return e;
+  }
+  if (beta != 0.0 && M > 0 && N > 0) {
+    if (int e = record_cuda(cudaMemcpy2DAsync(dC, dldc * 8, C, ldc * 8, c_run * 8, c_cnt, cudaMemcpyHostToDevice, st)))
+      return e;
+  }
+  int rc = dgemm_impl(layout, transa, transb, M, N, K, alpha, dA, dlda, dB, dldb, beta, dC, dldc, stream,
+                      report ? dR : nullptr, true);
+  if (rc != 0) return rc;
+  if (M > 0 && N > 0) {
+    if (int e = record_cuda(cudaMemcpy2DAsync(C, ldc * 8, dC, dldc * 8, c_run * 8, c_cnt, cudaMemcpyDeviceToHost, st)))
+      return e;
+  }
+  if (report) {
+    if (int e = record_cuda(cudaMemcpyAsync(report, dR, sizeof(ft_report_t), cudaMemcpyDeviceToHost, st))) return e;
+  }
+  return record_cuda(cudaStreamSynchronize(st));
+}
+
+int ftblas_verification_tile(ftblas_layout_t layout, ftblas_dtype_t compute_type, int64_t M, int64_t N, int64_t K,
+                             int64_t* tile_rows, int64_t* tile_cols, int64_t* k_tile) {
+  if (layout != FTBLAS_ROW_MAJOR && layout != FTBLAS_COL_MAJOR) return -1;
+  if (compute_type != FTBLAS_R_64F) return -2;
+  if (M < 0) return -3;
+  if (N < 0) return -4;
+  if (K < 0) return -5;
+  if (!tile_rows) return -6;
+  if (!tile_cols) return -7;
+  if (!k_tile) return -8;
+  const bool swap = layout == FTBLAS_ROW_MAJOR;
+  *tile_rows = swap ? kDBN : kDBM;
+  *tile_cols = swap ? kDBM : kDBN;
+  *k_tile = kDBK;
+  return 0;
+}
+
+int ftblas_set_fp64_engine(int engine) {
+  if (engine != kEngineDFMA && engine != kEngineDMMA) return -1;
+  return g_fp64_engine.exchange(engine);
+}
+
+const char* ftblas_status_string(int code) {
+  if (code == 0) return "success";
+  if (code < 0) return "invalid argument (the negated code is its 1-based position)";
+  switch (code) {
+    case FTBLAS_STATUS_NOT_SUPPORTED: return "not supported (type, shape or alignment)";
+    case FTBLAS_STATUS_CUDA_ERROR: return "CUDA runtime error (see ftblas_last_cuda_error)";
+    case FTBLAS_STATUS_ALLOC_FAILED: return "workspace allocation failed";
+    default: return "unknown status";
+  }
+}
+
+int ftblas_last_cuda_error(void) { return g_last_cuda_error; }
+
+int ftblas_last_launch_used_tma(void) { return g_last_used_tma; }
+
+const char* ftblas_version(void) { return "0.1.0"; }
+
+}  // extern "C"

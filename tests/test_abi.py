@@ -1,0 +1,76 @@
+"""The C ABI library builds, loads and exports every entry point include/ftblas.h declares
+(no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2104_00897_gb300 as fb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "ftblas.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ftblas_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported_and_bound():
+    lib = fb.load()
+    names = declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in fb.SIGNATURES, f"binding lacks {n}"
+
+
+def test_struct_sizes_match_the_header_layout():
+    assert ctypes.sizeof(fb.FtErrorRecord) == 96
+    assert fb.REPORT_BYTES == 6 * 8 + 4 + 4 + 64 * 96
+    assert ctypes.sizeof(fb.FtInjectPoint) == 40
+    assert ctypes.sizeof(fb.FtInject) == 8 + 10 * 4 + 16 * 40
+
+
+@pytest.mark.parametrize("args,code", [
+    ((100, 111, 111, 4, 4, 4, 1.0, 1, 4, 1, 4, 0.0, 1, 4), -1),
+    ((102, 110, 111, 4, 4, 4, 1.0, 1, 4, 1, 4, 0.0, 1, 4), -2),
+    ((102, 111, 113, 4, 4, 4, 1.0, 1, 4, 1, 4, 0.0, 1, 4), -3),
+    ((102, 111, 111, -1, 4, 4, 1.0, 1, 4, 1, 4, 0.0, 1, 4), -4),
+    ((102, 111, 111, 4, -1, 4, 1.0, 1, 4, 1, 4, 0.0, 1, 4), -5),
+    ((102, 111, 111, 4, 4, -1, 1.0, 1, 4, 1, 4, 0.0, 1, 4), -6),
+    ((102, 111, 111, 4, 4, 4, 1.0, None, 4, 1, 4, 0.0, 1, 4), -8),
+    ((102, 111, 111, 4, 4, 4, 1.0, 1, 3, 1, 4, 0.0, 1, 4), -9),
+    ((102, 111, 112, 4, 5, 4, 1.0, 1, 4, 1, 4, 0.0, 1, 4), -11),   # B^T stored 5 x 4 needs ldb >= 5
+    ((102, 111, 111, 4, 4, 4, 1.0, 1, 4, 1, 4, 0.0, None, 4), -13),
+    ((101, 111, 111, 4, 6, 4, 1.0, 1, 4, 1, 6, 0.0, 1, 5), -14),   # row-major C needs ldc >= N
+])
+def test_argument_validation_codes(args, code):
+    # Invalid arguments are rejected on the host before any CUDA call.
+    assert fb.ftblas_dgemm(*args, None, None) == code
+    assert fb.ftblas_dgemm_noabft(*args, None) == code
+
+
+def test_empty_problem_returns_without_gpu_work():
+    # M == 0 / N == 0: quick return, no device memory touched (null pointers are fine).
+    assert fb.ftblas_dgemm(102, 111, 111, 0, 4, 4, 1.0, None, 1, None, 4, 0.0, None, 1, None, None) == 0
+    assert fb.ftblas_dgemm(102, 111, 111, 4, 0, 4, 1.0, None, 4, None, 4, 0.0, None, 4, None, None) == 0
+
+
+def test_injection_config_validation_and_counter():
+    assert fb.ftblas_set_injection(fb.make_injection(seed=3, every_n_launches=5, errors_per_launch=2)) == 0
+    assert fb.ftblas_injection_launch_count() == 0
+    bad = fb.make_injection(bit_lo=50, bit_hi=40, every_n_launches=1, errors_per_launch=1)
+    assert fb.ftblas_set_injection(bad) == -1
+    bad = fb.make_injection(every_n_launches=1, errors_per_launch=65)
+    assert fb.ftblas_set_injection(bad) == -1
+    assert fb.ftblas_set_injection(None) == 0
+
+
+def test_verification_tile_and_engine_switch():
+    assert fb.ftblas_verification_tile(fb.COL_MAJOR, fb.R_64F, 10, 10, 10) == (128, 128, 32)
+    assert fb.ftblas_verification_tile(fb.ROW_MAJOR, fb.R_64F, 10, 10, 10) == (128, 128, 32)
+    prev = fb.ftblas_set_fp64_engine(fb.ENGINE_DMMA)
+    assert fb.ftblas_set_fp64_engine(prev) == fb.ENGINE_DMMA
+    assert fb.ftblas_set_fp64_engine(7) == -1
