@@ -405,12 +405,13 @@ static void ft_tile(const oracle_problem_t* p, int64_t tr, int64_t tc,
     if (p->beta != 0.0 && !isfinite_d(cin_sum)) nonfinite_input = 1;
   }
 
-  /* Verify: an entry is flagged when |delta| > tau or delta (or tau) is not finite. */
+  /* Verify: an entry is flagged when |delta| > tau, or when delta is not finite (NaN, or
+   * infinite even when an infinite C entry has made tau infinite too). */
   int64_t nr = 0, nc = 0, fr = -1, fc = -1;
   for (int64_t ii = 0; ii < nI; ++ii)
-    if (!(fabs(dr[ii]) <= tr_tau[ii])) { if (fr < 0) fr = ii; ++nr; }
+    if (!(fabs(dr[ii]) <= tr_tau[ii]) || isinf(dr[ii])) { if (fr < 0) fr = ii; ++nr; }
   for (int64_t jj = 0; jj < nJ; ++jj)
-    if (!(fabs(dc[jj]) <= tc_tau[jj])) { if (fc < 0) fc = jj; ++nc; }
+    if (!(fabs(dc[jj]) <= tc_tau[jj]) || isinf(dc[jj])) { if (fc < 0) fc = jj; ++nc; }
 
   oracle_record_t r;
   memset(&r, 0, sizeof(r));

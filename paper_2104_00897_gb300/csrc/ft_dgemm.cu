@@ -45,7 +45,7 @@ struct __align__(1024) DSmem {
   int nonfinite;
   int first_row, first_col;
   double delta_row, delta_col;
-  float tau_row, tau_col;
+  double tau_row, tau_col;
   int recompute;          // 1: the located element must be recomputed
   int loc_i, loc_j;       // tile-local location
 };
@@ -74,11 +74,14 @@ __device__ __forceinline__ double ldg_b(const DgemmParams& p, int64_t k, int64_t
 // ---------------------------------------------------------------------------------------
 struct EngineDFMA {
   static constexpr int NR = 8, NC = 8;
-  static constexpr int ROW_SLOTS = 16, COL_SLOTS = 16;
+  // Lanes l and l^16 share rows (reduced by one xor shuffle); the 8 warps then hold 8
+  // partials per row. A column belongs to one half-warp (xor 1, 2, 4, 8): one partial.
+  static constexpr int ROW_SLOTS = 8, COL_SLOTS = 1;
+  static constexpr int ROW_XOR = 16, COL_XOR = 15;  // lane bits over which to reduce
   __device__ static int row(int t, int r) { return (t & 15) + 16 * r; }
   __device__ static int col(int t, int c) { return (t >> 4) + 16 * c; }
-  __device__ static int row_slot(int t) { return t >> 4; }
-  __device__ static int col_slot(int t) { return t & 15; }
+  __device__ static int row_slot(int t) { return t >> 5; }
+  __device__ static int col_slot(int t) { return 0; }
 
   template <bool AK, bool BKM>
   __device__ static void ktile(double (&acc)[NR][NC], const double* sA, const double* sB, int t) {
@@ -125,15 +128,18 @@ struct EngineDMMA {
   // 8 warps as 4 (rows) x 2 (columns); warp tile 32 x 64 = 4 x 8 fragments of 8 x 8.
   // m8n8k4 fragments: A(g, q), B(q, g), C(g, 2q + e) with g = lane / 4, q = lane % 4.
   static constexpr int NR = 4, NC = 16;
-  static constexpr int ROW_SLOTS = 8, COL_SLOTS = 32;
+  // Rows are shared by the 4 lanes with equal g (xor 1, 2) and by the 2 column warps;
+  // columns by the 8 lanes with equal q (xor 4, 8, 16) and by the 4 row warps.
+  static constexpr int ROW_SLOTS = 2, COL_SLOTS = 4;
+  static constexpr int ROW_XOR = 3, COL_XOR = 28;
   __device__ static int wm(int t) { return (t >> 5) & 3; }
   __device__ static int wn(int t) { return t >> 7; }
   __device__ static int g(int t) { return (t & 31) >> 2; }
   __device__ static int q(int t) { return t & 3; }
   __device__ static int row(int t, int r) { return 32 * wm(t) + 8 * r + g(t); }
   __device__ static int col(int t, int c) { return 64 * wn(t) + 8 * (c >> 1) + 2 * q(t) + (c & 1); }
-  __device__ static int row_slot(int t) { return wn(t) * 4 + q(t); }
-  __device__ static int col_slot(int t) { return wm(t) * 8 + g(t); }
+  __device__ static int row_slot(int t) { return wn(t); }
+  __device__ static int col_slot(int t) { return wm(t); }
 
   template <bool AK, bool BKM>
   __device__ static void ktile(double (&acc)[NR][NC], const double* sA, const double* sB, int t) {
@@ -176,6 +182,47 @@ struct EngineDMMA {
     return false;
   }
 };
+
+
+// Butterfly sum over the lane bits in `mask` (plain and upward-rounded).
+__device__ __forceinline__ void xor_reduce(double& s, double& a, int mask) {
+#pragma unroll
+  for (int b = 1; b < 32; b <<= 1) {
+    if (mask & b) {
+      s += __shfl_xor_sync(0xffffffffu, s, b);
+      a = __dadd_ru(a, __shfl_xor_sync(0xffffffffu, a, b));
+    }
+  }
+}
+
+// Row and column sums (and upward-rounded sums of magnitudes) of val(r, c) over the
+// tile, written as per-slot partials: srow/arow[ROW_SLOTS][BM], scol/acol[COL_SLOTS][BN].
+template <class E, class F>
+__device__ __forceinline__ void tile_sums(F val, int t, double* srow, double* arow, double* scol, double* acol) {
+  const int lane = t & 31;
+#pragma unroll
+  for (int r = 0; r < E::NR; ++r) {
+    double s = 0.0, a = 0.0;
+#pragma unroll
+    for (int c = 0; c < E::NC; ++c) { const double x = val(r, c); s += x; a = __dadd_ru(a, fabs(x)); }
+    xor_reduce(s, a, E::ROW_XOR);
+    if ((lane & E::ROW_XOR) == 0) { srow[E::row_slot(t) * BM + E::row(t, r)] = s; arow[E::row_slot(t) * BM + E::row(t, r)] = a; }
+  }
+#pragma unroll
+  for (int c = 0; c < E::NC; ++c) {
+    double s = 0.0, a = 0.0;
+#pragma unroll
+    for (int r = 0; r < E::NR; ++r) { const double x = val(r, c); s += x; a = __dadd_ru(a, fabs(x)); }
+    xor_reduce(s, a, E::COL_XOR);
+    if ((lane & E::COL_XOR) == 0) { scol[E::col_slot(t) * BN + E::col(t, c)] = s; acol[E::col_slot(t) * BN + E::col(t, c)] = a; }
+  }
+}
+
+// Upward-rounded gamma_n = n u / (1 - n u), u = 2^-53, in binary64.
+__device__ __forceinline__ double gamma_up64(int64_t n) {
+  const double nu = __dmul_ru((double)n, 0x1p-53);
+  return __ddiv_ru(nu, __dsub_rd(1.0, nu));
+}
 
 __device__ void write_record(const DgemmParams& p, int kind, int64_t tr, int64_t tc, int64_t i, int64_t j,
                              double drow, double dcol, double trow, double tcol, double before, double after,
@@ -363,47 +410,29 @@ __global__ void __launch_bounds__(NT, 1)
 
   // ---------------------------------------------------------------- epilogue: C in registers
   const bool beta_nz = (p.beta != 0.0);
-  // Partial-sum arrays overlay the operand ring (all copies have landed and been read).
-  double* rsum = sm.a[0];                                              // [ROW_SLOTS][BM] sum of C
-  double* rcin = rsum + E::ROW_SLOTS * BM;                             // sum of C_in
-  float* rabs = reinterpret_cast<float*>(rcin + E::ROW_SLOTS * BM);    // upward sum of |C|
-  float* rabc = rabs + E::ROW_SLOTS * BM;                              // upward sum of |C_in|
-  double* csum = sm.b[0];                                              // [COL_SLOTS][BN]
-  double* ccin = csum + E::COL_SLOTS * BN;
-  float* cabs = reinterpret_cast<float*>(ccin + E::COL_SLOTS * BN);
-  float* cabc = cabs + E::COL_SLOTS * BN;
-  static_assert((E::ROW_SLOTS * BM * 2 * 8 + E::ROW_SLOTS * BM * 2 * 4) <= (int)sizeof(double) * STAGES * BM * BK,
-                "row partials exceed the A ring");
-  static_assert((E::COL_SLOTS * BN * 2 * 8 + E::COL_SLOTS * BN * 2 * 4) <= (int)sizeof(double) * STAGES * BK * BN,
-                "column partials exceed the B ring");
-  const int rslot = E::row_slot(t), cslot = E::col_slot(t);
   auto cin_at = [&](int li, int lj) -> double {
     return (li < nI && lj < nJ) ? p.C[(int64_t)(m0 + li) + (int64_t)(n0 + lj) * p.ldc] : 0.0;
   };
-  if (FT && beta_nz) {
-    // beta*C_in enters the predicted checksums (Section V.B): its row and column sums,
-    // read from C_in (cached) so no extra register array stays live beside acc.
-#pragma unroll 1
-    for (int r = 0; r < E::NR; ++r) {
-      double s = 0.0;
-      float sa = 0.0f;
-#pragma unroll 4
-      for (int c = 0; c < E::NC; ++c) { const double x = cin_at(E::row(t, r), E::col(t, c)); s += x; sa = add_up(sa, abs_up(x)); }
-      rcin[rslot * BM + E::row(t, r)] = s; rabc[rslot * BM + E::row(t, r)] = sa;
+  // Partial-sum arrays overlay the operand ring (every copy has landed and been read).
+  double* rsum = sm.a[0];                 // [ROW_SLOTS][BM]  sum of C over the row
+  double* rabs = rsum + E::ROW_SLOTS * BM;  //                  upward sum of |C|
+  double* rcin = rabs + E::ROW_SLOTS * BM;  //                  sum of C_in
+  double* rabc = rcin + E::ROW_SLOTS * BM;  //                  upward sum of |C_in|
+  double* csum = rabc + E::ROW_SLOTS * BM;  // [COL_SLOTS][BN]
+  double* cabs = csum + E::COL_SLOTS * BN;
+  double* ccin = cabs + E::COL_SLOTS * BN;
+  double* cabc = ccin + E::COL_SLOTS * BN;
+  double* slow = cabc + E::COL_SLOTS * BN;  // [2][kSlowChunk] threshold slow path
+  constexpr int kSlowChunk = 1024;
+  static_assert(4 * (E::ROW_SLOTS * BM + E::COL_SLOTS * BN) + 2 * kSlowChunk <= STAGES * BM * BK,
+                "epilogue scratch exceeds the A ring");
+  if (FT) {
+    // beta*C_in enters the predicted checksums (Section V.B): its row and column sums.
+    if (beta_nz) {
+      tile_sums<E>([&](int r, int c) { return cin_at(E::row(t, r), E::col(t, c)); }, t, rcin, rabc, ccin, cabc);
+    } else {
+      tile_sums<E>([&](int, int) { return 0.0; }, t, rcin, rabc, ccin, cabc);
     }
-#pragma unroll 1
-    for (int c = 0; c < E::NC; ++c) {
-      double s = 0.0;
-      float sa = 0.0f;
-#pragma unroll 4
-      for (int r = 0; r < E::NR; ++r) { const double x = cin_at(E::row(t, r), E::col(t, c)); s += x; sa = add_up(sa, abs_up(x)); }
-      ccin[cslot * BN + E::col(t, c)] = s; cabc[cslot * BN + E::col(t, c)] = sa;
-    }
-  } else if (FT) {
-#pragma unroll
-    for (int r = 0; r < E::NR; ++r) { rcin[rslot * BM + E::row(t, r)] = 0.0; rabc[rslot * BM + E::row(t, r)] = 0.0f; }
-#pragma unroll
-    for (int c = 0; c < E::NC; ++c) { ccin[cslot * BN + E::col(t, c)] = 0.0; cabc[cslot * BN + E::col(t, c)] = 0.0f; }
   }
 #pragma unroll
   for (int r = 0; r < E::NR; ++r)
@@ -432,42 +461,51 @@ __global__ void __launch_bounds__(NT, 1)
             acc[r][c] = v;
           }
     }
-
-    // Reference checksums C^r_ref, C^c_ref from the registers (partial per slot).
-#pragma unroll
-    for (int r = 0; r < E::NR; ++r) {
-      double s = 0.0;
-      float sa = 0.0f;
-#pragma unroll
-      for (int c = 0; c < E::NC; ++c) { s += acc[r][c]; sa = add_up(sa, abs_up(acc[r][c])); }
-      rsum[rslot * BM + E::row(t, r)] = s; rabs[rslot * BM + E::row(t, r)] = sa;
-    }
-#pragma unroll
-    for (int c = 0; c < E::NC; ++c) {
-      double s = 0.0;
-      float sa = 0.0f;
-#pragma unroll
-      for (int r = 0; r < E::NR; ++r) { s += acc[r][c]; sa = add_up(sa, abs_up(acc[r][c])); }
-      csum[cslot * BN + E::col(t, c)] = s; cabs[cslot * BN + E::col(t, c)] = sa;
-    }
+    // Reference checksums C^r_ref, C^c_ref from the registers (Section V.B).
+    tile_sums<E>([&](int r, int c) { return acc[r][c]; }, t, rsum, rabs, csum, cabs);
     __syncthreads();
 
-    // Verify one row (t < 128) or one column (t >= 128) per thread.
+    // One row (t < 128) or one column (t >= 128) per thread.
     const bool is_row = t < BM;
     const int idx = is_row ? t : t - BM;
     const int nslots = is_row ? E::ROW_SLOTS : E::COL_SLOTS;
-    const double* ps = is_row ? rsum : csum;
-    const double* pc = is_row ? rcin : ccin;
-    const float* pa = is_row ? rabs : cabs;
-    const float* pac = is_row ? rabc : cabc;
     const int extent = is_row ? BM : BN;
-    double ref = 0.0, cin_sum = 0.0;
-    float R = 0.0f, Q = 0.0f;
+    const double* ps = is_row ? rsum : csum;
+    const double* pa = is_row ? rabs : cabs;
+    const double* pc = is_row ? rcin : ccin;
+    const double* pac = is_row ? rabc : cabc;
+    double ref = 0.0, cin_sum = 0.0, R = 0.0, Q = 0.0;
     for (int sl = 0; sl < nslots; ++sl) {
       ref += ps[sl * extent + idx];
       cin_sum += pc[sl * extent + idx];
-      R = add_up(R, pa[sl * extent + idx]);
-      Q = add_up(Q, pac[sl * extent + idx]);
+      R = __dadd_ru(R, pa[sl * extent + idx]);
+      Q = __dadd_ru(Q, pac[sl * extent + idx]);
+    }
+    // The binary32 magnitude sum from the mainloop overflows only for huge operands; then
+    // the tile recomputes it in binary64 (upward) from global memory.
+    double P = (double)pmag;
+    if (__syncthreads_or(!isfinite(pmag))) {
+      double* sabsB = slow;               // upward sum_{j in tile} |B(k, j)|
+      double* sabsA = slow + kSlowChunk;  // upward sum_{i in tile} |A(i, k)|
+      P = 0.0;
+      for (int64_t k0 = 0; k0 < p.K; k0 += kSlowChunk) {
+        const int kc = (int)((p.K - k0) < kSlowChunk ? (p.K - k0) : kSlowChunk);
+        for (int kk = t; kk < kc; kk += NT) {
+          double sb = 0.0, sa = 0.0;
+          for (int j = 0; j < nJ; ++j) sb = __dadd_ru(sb, fabs(ldg_b(p, k0 + kk, n0 + j)));
+          for (int i = 0; i < nI; ++i) sa = __dadd_ru(sa, fabs(ldg_a(p, m0 + i, k0 + kk)));
+          sabsB[kk] = sb;
+          sabsA[kk] = sa;
+        }
+        __syncthreads();
+        if (idx < (is_row ? nI : nJ)) {
+          for (int kk = 0; kk < kc; ++kk) {
+            const double x = is_row ? fabs(ldg_a(p, m0 + idx, k0 + kk)) : fabs(ldg_b(p, k0 + kk, n0 + idx));
+            P = __fma_ru(x, is_row ? sabsB[kk] : sabsA[kk], P);
+          }
+        }
+        __syncthreads();
+      }
     }
     double predicted = beta_nz ? fma(p.alpha, pred, p.beta * cin_sum) : p.alpha * pred;
     if (beta_nz && !isfinite(cin_sum)) sm.nonfinite = 1;
@@ -484,15 +522,16 @@ __global__ void __launch_bounds__(NT, 1)
       }
     }
     const double delta = ref - predicted;
-    // tau = 2 [gamma_{K+n+3} (|alpha| P + |beta| Q) + gamma_n R], n = columns (rows) summed.
+    // tau = 2 [gamma_{K+n+3} (|alpha| P + |beta| Q) + gamma_n R], n = entries summed, all
+    // rounded upward: a rigorous bound on |delta| for an error-free tile.
     const int n_other = is_row ? nJ : nI;
-    const float g1 = gamma_up((int64_t)p.K + n_other + 3), g2 = gamma_up(n_other);
-    const float aa = abs_up(p.alpha), bb = abs_up(p.beta);
-    float tau = fma_up(aa, pmag, mul_up(bb, Q));
-    tau = fma_up(g1, tau, mul_up(g2, R));
-    tau = mul_up(2.0f, tau);
+    const double g1 = gamma_up64((int64_t)p.K + n_other + 3), g2 = gamma_up64(n_other);
+    double tau = __fma_ru(fabs(p.alpha), P, __dmul_ru(fabs(p.beta), Q));
+    tau = __fma_ru(g1, tau, __dmul_ru(g2, R));
+    tau = __dmul_ru(2.0, tau);
     const bool valid = idx < (is_row ? nI : nJ);
-    const bool flagged = valid && !(fabs(delta) <= (double)tau);
+    // Flagged: |delta| > tau, or delta not finite (NaN, or infinite even against tau = inf).
+    const bool flagged = valid && (!(fabs(delta) <= tau) || isinf(delta));
     if (flagged) atomicMin(is_row ? &sm.first_row : &sm.first_col, idx);
     const int nr = __syncthreads_count(is_row && flagged);
     const int nc = __syncthreads_count(!is_row && flagged);

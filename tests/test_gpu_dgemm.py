@@ -163,6 +163,49 @@ def test_output_checksum_and_multiple_error_sites(engine):
             assert np.array_equal(got.view(np.uint64), clean.view(np.uint64))
 
 
+@pytest.mark.parametrize("engine", ENGINES)
+def test_infinite_output_flagged_against_infinite_threshold(engine):
+    """An output flipped to +inf makes its row/column sums and thresholds infinite; it is
+    still located and recomputed (same data as the oracle's pin)."""
+    fb.ftblas_set_fp64_engine(engine)
+    P = Problem(8, 8, 8, alpha=1.0, beta=0.0, seed=51, pad="even")
+    P.A = np.eye(8)
+    P.B = S.randint(51, 0, 64, 2, 5).reshape(8, 8).astype(np.float64)
+    P.B[3, 5] = 1.0
+    P.a, P.lda = S.store(P.A, O.COL_MAJOR, ld=8)
+    P.b, P.ldb = S.store(P.B, O.COL_MAJOR, ld=8)
+    clean, _ = run_gpu(P)
+    pt = dict(i=3, j=5, site=fb.SITE_OUTPUT, mode=fb.MODE_BITFLIP, bit=62)
+    fb.ftblas_set_injection(fb.make_injection(fixed=[pt]))
+    got, rep = run_gpu(P)
+    _, orep = P.oracle_ft(*tile_of(P), injections=[pt])
+    assert report_summary(rep) == report_summary(orep) == (1, 1, 1, 0, 0, 0)
+    assert record_set(rep) == record_set(orep) == [(3, 5, fb.KIND_CORRECTED)]
+    assert np.array_equal(got, clean)
+
+
+def test_huge_operands_use_the_binary64_threshold_path():
+    """Operands near 1e20 overflow the binary32 magnitude sums of the mainloop; the tile
+    then recomputes its threshold in binary64 and still matches the oracle."""
+    P = Problem(200, 136, 64, alpha=1.0, beta=0.5, seed=61, pad="even")
+    scale = 2.0 ** 70
+    P.A = P.A * scale
+    P.B = P.B * scale
+    P.a, P.lda = S.store(P.A, O.COL_MAJOR, ld=P.lda)
+    P.b, P.ldb = S.store(P.B, O.COL_MAJOR, ld=P.ldb)
+    tr, tc, bk = tile_of(P)
+    clean, rep = run_gpu(P)
+    ref, orep = P.oracle_ft(tr, tc, bk)
+    assert report_summary(rep) == report_summary(orep) and rep.detected == 0
+    assert P.normalized_error(clean, ref) <= TOL
+    pt = dict(i=150, j=100, site=fb.SITE_ACCUM, bit=44)
+    fb.ftblas_set_injection(fb.make_injection(fixed=[pt]))
+    got, rep = run_gpu(P)
+    _, orep = P.oracle_ft(tr, tc, bk, injections=[pt])
+    assert record_set(rep) == record_set(orep) == [(150, 100, fb.KIND_CORRECTED)]
+    assert np.array_equal(got.view(np.uint64), clean.view(np.uint64))
+
+
 def test_quick_returns_on_gpu():
     P = Problem(70, 50, 0, alpha=1.0, beta=0.5, seed=3)
     got, rep = run_gpu(P)

@@ -301,6 +301,24 @@ def test_exponent_flip_to_nonfinite_is_corrected():
     assert rep.corrected == 1 and np.array_equal(got, clean)
 
 
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")
+def test_infinite_output_is_flagged_against_infinite_threshold():
+    """C(3,5) == 1.0 exactly; flipping bit 62 of it gives +inf, which makes the row sum,
+    the column sum and both thresholds infinite. It must still be located and recomputed."""
+    M = N = K = 8
+    A = np.eye(8)
+    B = S.randint(51, 0, K * N, 2, 5).reshape(K, N).astype(np.float64)
+    B[3, 5] = 1.0
+    clean = plain(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B)
+    assert clean[3, 5] == 1.0 and flip(1.0, 62) == math.inf
+    got, rep = ft(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, A, B, tile=(8, 8), bk=4,
+                  inj=[dict(i=3, j=5, site=O.SITE_OUTPUT, mode=O.MODE_BITFLIP, bit=62)])
+    r = rep.records()[0]
+    assert (rep.corrected, r.i, r.j) == (1, 3, 5)
+    assert math.isinf(r.delta_row) and math.isinf(r.tau_row)
+    assert np.array_equal(got, clean)
+
+
 def test_ragged_tiles_and_injection_in_last_tile():
     M, N, K = 37, 29, 33
     A = S.uniform_matrix(4, 0, M, K)
