@@ -75,7 +75,23 @@ __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
 // Upward-rounded binary32 arithmetic. Every operation rounds toward +infinity, so sums and
 // products of non-negative values computed this way are upper bounds of the exact values.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ float abs_up(double x) { return __double2float_ru(fabs(x)); }
+// Upper bound of |x| as a binary32 value, built from the high word of x with integer
+// operations only (no FP64-pipe instruction: on GB300 that pipe is the bottleneck, and a
+// binary64 -> binary32 conversion issues to it). The high word holds the sign, the 11-bit
+// exponent e and the top 20 significand bits; re-biasing e to 8 bits and adding one unit
+// in the 20th significand bit bounds the dropped low bits from above. |x| < 2^-126 maps
+// to 2^-126, |x| >= 2^128 to +inf (the caller's overflow path).
+__device__ __forceinline__ double abs_int(double x) {
+  return __hiloint2double(__double2hiint(x) & 0x7fffffff, __double2loint(x));
+}
+__device__ __forceinline__ float abs_up(double x) {
+  const uint32_t hi = static_cast<uint32_t>(__double2hiint(x)) & 0x7fffffffu;
+  const uint32_t e = hi >> 20;
+  uint32_t b = ((hi - (896u << 20)) << 3) + 8u;
+  b = (e < 897u) ? 0x00800000u : b;
+  b = (e > 1150u) ? 0x7f800000u : b;
+  return __uint_as_float(b);
+}
 __device__ __forceinline__ float add_up(float a, float b) { return __fadd_ru(a, b); }
 __device__ __forceinline__ float fma_up(float a, float b, float c) { return __fmaf_ru(a, b, c); }
 __device__ __forceinline__ float mul_up(float a, float b) { return __fmul_ru(a, b); }
