@@ -164,9 +164,45 @@ int ftblas_dgemm_host(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_tran
                       const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
                       void* stream, ft_report_t* report);
 
+/* Mixed-precision ABFT-protected GEMM (Section II.A checksums; FP32 accumulation on the
+ * tensor cores, binary64 checksum comparison). Arguments 1-22 in order: layout, transa,
+ * transb, M, N, K, alpha, A, Atype, lda, B, Btype, ldb, beta, C, Ctype, ldc, compute_type,
+ * a_scale, b_scale, stream, report. alpha and beta point to HOST scalars of the compute
+ * type (double for FTBLAS_R_64F, float for FTBLAS_R_32F). Supported combinations:
+ *   A, B, C, compute all FTBLAS_R_64F            -> the same path as ftblas_dgemm;
+ *   A, B FTBLAS_R_16BF, C and compute FTBLAS_R_32F -> tcgen05 BF16 GEMM, C stored in FP32.
+ * a_scale / b_scale (device pointers to one float each) scale FP8 operands and must be
+ * NULL otherwise. The BF16 path needs both operands K-contiguous in the column-major
+ * kernel frame (column-major: A transposed and B not; row-major: A not transposed and B
+ * transposed), leading dimensions that are multiples of 8 elements and 16-byte aligned
+ * base addresses; other combinations return FTBLAS_STATUS_NOT_SUPPORTED. Its threshold
+ * assumes the tensor core accumulates in binary32 with unit roundoff 2^-23, its row
+ * checksums are verified in every tile and its column checksums only in tiles with a row
+ * mismatch (Section V.A); a located error is corrected by subtracting the row mismatch
+ * (Section VI.C), evaluated as C^r(i) - sum_{j' != j} C(i,j') so that a huge or
+ * non-finite error does not cancel catastrophically. Workspace (about
+ * 16*K*ceil(N/256)*2 + 8*K*ceil(M/128) bytes) is taken from the stream-ordered allocator
+ * and released on the same stream. */
+int ftblas_gemm_ex(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,
+                   int64_t M, int64_t N, int64_t K, const void* alpha,
+                   const void* A, ftblas_dtype_t Atype, int64_t lda,
+                   const void* B, ftblas_dtype_t Btype, int64_t ldb, const void* beta,
+                   void* C, ftblas_dtype_t Ctype, int64_t ldc, ftblas_dtype_t compute_type,
+                   const float* a_scale, const float* b_scale, void* stream, ft_report_t* report);
+
+/* ftblas_gemm_ex with the protection compiled out (no encode pre-pass, no checksum MMA,
+ * no verification): the baseline for the overhead. Same arguments without the report. */
+int ftblas_gemm_ex_noabft(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,
+                          int64_t M, int64_t N, int64_t K, const void* alpha,
+                          const void* A, ftblas_dtype_t Atype, int64_t lda,
+                          const void* B, ftblas_dtype_t Btype, int64_t ldb, const void* beta,
+                          void* C, ftblas_dtype_t Ctype, int64_t ldc, ftblas_dtype_t compute_type,
+                          const float* a_scale, const float* b_scale, void* stream);
+
 /* Shape of the verification tile used for a call, in the caller's coordinates of C, and
  * the k-tile depth that sets the accumulator injection point (bk * floor(ceil(K/bk)/2)
- * products). compute_type selects the kernel family (FTBLAS_R_64F for ftblas_dgemm).
+ * products; for FTBLAS_R_32F the k-tile of the tensor-core path). compute_type selects the
+ * kernel family: FTBLAS_R_64F (ftblas_dgemm) or FTBLAS_R_32F (BF16 tensor-core path).
  * Returns 0, or a negative argument index. */
 int ftblas_verification_tile(ftblas_layout_t layout, ftblas_dtype_t compute_type,
                              int64_t M, int64_t N, int64_t K,

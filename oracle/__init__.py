@@ -20,6 +20,8 @@ NO_TRANS, TRANS = 111, 112
 SITE_ACCUM, SITE_OUTPUT, SITE_CHECKSUM = 1, 2, 3
 MODE_BITFLIP, MODE_ADD_REL = 0, 1
 KIND_CORRECTED, KIND_CHECKSUM_ONLY, KIND_UNCORRECTABLE, KIND_INPUT_NONFINITE = 1, 2, 3, 4
+PREC_FP64, PREC_ACC32 = 0, 1
+U_ACC32 = 2.0 ** -23
 MAX_RECORDS = 256
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -41,6 +43,8 @@ class Problem(C.Structure):
         ("Cin", C.c_void_p), ("ldc", C.c_int64),
         ("tile_m", C.c_int64), ("tile_n", C.c_int64),
         ("bk", C.c_int64),
+        ("precision", C.c_int32), ("pad2_", C.c_int32),
+        ("u_acc", C.c_double),
     ]
 
 
@@ -121,7 +125,7 @@ def _f64(x):
 
 
 def make_problem(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc,
-                 tile_m=128, tile_n=128, bk=16, keep=None):
+                 tile_m=128, tile_n=128, bk=16, keep=None, precision=PREC_FP64, u_acc=U_ACC32):
     """Fill a Problem; ``keep`` (a list) receives the arrays that must outlive the call."""
     A = _f64(A); B = _f64(B)
     Cin = _f64(Cin) if Cin is not None else np.zeros(1)
@@ -129,14 +133,17 @@ def make_problem(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C
         keep.extend([A, B, Cin])
     p = Problem(layout=layout, transa=transa, transb=transb, pad_=0, M=M, N=N, K=K, alpha=alpha,
                 A=A.ctypes.data, lda=lda, B=B.ctypes.data, ldb=ldb, beta=beta,
-                Cin=Cin.ctypes.data, ldc=ldc, tile_m=tile_m, tile_n=tile_n, bk=bk)
+                Cin=Cin.ctypes.data, ldc=ldc, tile_m=tile_m, tile_n=tile_n, bk=bk,
+                precision=precision, pad2_=0, u_acc=u_acc)
     return p
 
 
-def gemm(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc):
-    """Plain C = alpha*op(A)*op(B) + beta*C_in (the GEMM definition). Returns a new buffer."""
+def gemm(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc, precision=PREC_FP64):
+    """Plain C = alpha*op(A)*op(B) + beta*C_in (the GEMM definition; with PREC_ACC32 the
+    result is rounded to binary32). Returns a new buffer."""
     keep = []
-    p = make_problem(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc, keep=keep)
+    p = make_problem(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc, keep=keep,
+                     precision=precision)
     out = np.array(keep[2], copy=True) if Cin is not None else np.zeros(max(1, ldc * (N if layout == COL_MAJOR else M)))
     rc = lib().oracle_gemm(C.byref(p), out.ctypes.data)
     if rc != 0:
@@ -168,7 +175,7 @@ def injections_array(points):
 
 
 def ft_gemm(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc,
-            tile_m, tile_n, bk, injections=(), tiles=None, out=None):
+            tile_m, tile_n, bk, injections=(), tiles=None, out=None, precision=PREC_FP64, u_acc=U_ACC32):
     """ABFT-protected GEMM. Returns ``(Cout_buffer, Report)``.
 
     ``tiles``: None for all tiles, else tile numbers t = tile_row + tile_col * n_tile_rows
@@ -176,7 +183,7 @@ def ft_gemm(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, l
     """
     keep = []
     p = make_problem(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc,
-                     tile_m, tile_n, bk, keep=keep)
+                     tile_m, tile_n, bk, keep=keep, precision=precision, u_acc=u_acc)
     if out is None:
         n_store = max(1, ldc * (N if layout == COL_MAJOR else M))
         out = np.array(keep[2], copy=True) if Cin is not None and beta != 0.0 else np.zeros(n_store)

@@ -62,6 +62,14 @@
 
 #define OR_MAX_RECORDS 256
 
+/* Precision of the protected product. FP64: binary64 throughout (the paper's setting).
+ * ACC32: operands of any precision given as exact binary64 values, products accumulated
+ * in binary32 (modelled by the binary64 sum and the threshold's u_acc), C rounded to
+ * binary32; the row checksums are verified in every tile and the column checksums only in
+ * tiles with a row mismatch (the lazy second side of Section V.A). */
+#define OR_PREC_FP64 0
+#define OR_PREC_ACC32 1
+
 /* ---------------------------------------------------------------------------------- */
 /* Problem description and results                                                    */
 /* ---------------------------------------------------------------------------------- */
@@ -76,6 +84,9 @@ typedef struct {
   const double* Cin; int64_t ldc;   /* not read when beta == 0 */
   int64_t tile_m, tile_n;           /* verification tile, in rows x columns of C */
   int64_t bk;                       /* k-tile depth (sets the accumulator injection point) */
+  int32_t precision;                /* OR_PREC_FP64, or OR_PREC_ACC32 (binary32 accumulation, binary32 C) */
+  int32_t pad2_;
+  double u_acc;                     /* OR_PREC_ACC32: unit roundoff of the accumulation */
 } oracle_problem_t;
 
 typedef struct {
@@ -140,6 +151,17 @@ static double flip_bit(double x, int bit) {
   return x;
 }
 
+static double round32(double x) { return (double)(float)x; }
+
+static double flip_bit32(double x, int bit) {
+  float f = (float)x;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  u ^= (uint32_t)1 << bit;
+  memcpy(&f, &u, 4);
+  return (double)f;
+}
+
 /* ---------------------------------------------------------------------------------- */
 /* The GEMM definition: C = alpha * op(A) * op(B) + beta * C                           */
 /* ---------------------------------------------------------------------------------- */
@@ -183,6 +205,7 @@ int oracle_gemm(const oracle_problem_t* p, double* Cout) {
       } else {
         v = scale_out(p, acc, i, j);
       }
+      if (p->precision == OR_PREC_ACC32) v = round32(v);
       Cout[c_index(p->layout, p->ldc, i, j)] = v;
     }
   }
@@ -459,6 +482,157 @@ static void ft_tile(const oracle_problem_t* p, int64_t tr, int64_t tc,
   free(dr); free(tr_tau); free(dc); free(tc_tau);
 }
 
+/* One verification interval of the ACC32 precision (operands exact in binary64, products
+ * accumulated in binary32, C stored in binary32). Same encode and checksums as ft_tile;
+ * the differences are the ones a binary32 accumulation brings:
+ *   - C(i,j) = fl32(alpha * acc + beta * C_in), acc the binary64 inner product;
+ *   - an accumulator injection flips bit b of the binary32 accumulator after all K products;
+ *   - tau uses gamma_K(u_acc) for the product part, with sum_k |A(i,k)| sum_j |B(k,j)|
+ *     bounded by (sum_k |A(i,k)|) (max_k sum_j |B(k,j)|) over the tile:
+ *       row:    |alpha| P (gamma_K(u_acc) (2 + 2^-7) + 2^-20) + 2^-23 (sum_j |C| + |beta| sum_j |C_in|)
+ *       column: |alpha| P (gamma_K(u_acc) + 2^-30) + 2^-23 (sum_i |C| + 34 |beta| sum_i |C_in|)
+ *     (the row side's prediction is itself a binary32 product of A with B e split into
+ *     three pieces; the column side's is formed in compensated arithmetic);
+ *   - column checksums are formed only when a row mismatches (Section V.A, lazy side);
+ *   - a located error is corrected by subtracting the row mismatch (Section VI.C),
+ *     evaluated as C(i,j) = C^r(i) - sum_{j' != j} C(i,j') (equal in exact arithmetic,
+ *     stable for huge or non-finite errors); the result is rounded to binary32. */
+static void ft_tile_acc32(const oracle_problem_t* p, int64_t tr, int64_t tc,
+                          int64_t n_inj, const oracle_injection_t* inj,
+                          double* Cout, tile_result_t* res) {
+  const int64_t K = p->K;
+  const int64_t i0 = tr * p->tile_m, j0 = tc * p->tile_n;
+  const int64_t nI = (i0 + p->tile_m <= p->M) ? p->tile_m : p->M - i0;
+  const int64_t nJ = (j0 + p->tile_n <= p->N) ? p->tile_n : p->N - j0;
+  memset(res, 0, sizeof(*res));
+  double* Ac = (double*)calloc((size_t)(K > 0 ? K : 1), sizeof(double));
+  double* Br = (double*)calloc((size_t)(K > 0 ? K : 1), sizeof(double));
+  double maxAbsAe = 0.0, maxAbsBe = 0.0;
+  for (int64_t k = 0; k < K; ++k) {
+    double s = 0.0, sa = 0.0;
+    for (int64_t i = i0; i < i0 + nI; ++i) { double a = a_elem(p, i, k); s = s + a; sa = sa + fabs(a); }
+    Ac[k] = s;
+    if (sa > maxAbsAe) maxAbsAe = sa;
+    s = 0.0; sa = 0.0;
+    for (int64_t j = j0; j < j0 + nJ; ++j) { double b = b_elem(p, k, j); s = s + b; sa = sa + fabs(b); }
+    Br[k] = s;
+    if (sa > maxAbsBe) maxAbsBe = sa;
+  }
+  double* T = (double*)malloc((size_t)(nI * nJ) * sizeof(double));
+  for (int64_t jj = 0; jj < nJ; ++jj) {
+    for (int64_t ii = 0; ii < nI; ++ii) {
+      int64_t i = i0 + ii, j = j0 + jj;
+      double acc = dot_row_col(p, i, j, 0, -1);
+      for (int64_t q = 0; q < n_inj; ++q)
+        if (inj[q].i == i && inj[q].j == j && inj[q].site == OR_SITE_ACCUM && inj[q].mode == OR_MODE_BITFLIP)
+          acc = flip_bit32(acc, inj[q].bit);
+      double v = round32(scale_out(p, acc, i, j));
+      for (int64_t q = 0; q < n_inj; ++q) {
+        if (inj[q].i != i || inj[q].j != j || inj[q].site != OR_SITE_OUTPUT) continue;
+        if (inj[q].mode == OR_MODE_BITFLIP) {
+          v = flip_bit32(v, inj[q].bit);
+        } else {
+          double e = ldexp(fabs(v), inj[q].rel_log2);
+          v = round32((inj[q].sign < 0) ? v - e : v + e);
+        }
+      }
+      T[ii + jj * nI] = v;
+    }
+  }
+  const double gK = gamma_n((double)K * p->u_acc / 1.1102230246251565e-16);
+  /* Row side, every row. */
+  int64_t nr = 0, fr = -1;
+  double fr_delta = 0.0, fr_tau = 0.0, fr_pred = 0.0;
+  for (int64_t ii = 0; ii < nI; ++ii) {
+    int64_t i = i0 + ii;
+    double dotp = 0.0, rowAbsA = 0.0;
+    for (int64_t k = 0; k < K; ++k) { double a = a_elem(p, i, k); dotp = dotp + a * Br[k]; rowAbsA = rowAbsA + fabs(a); }
+    double cin_sum = 0.0, Q = 0.0;
+    if (p->beta != 0.0)
+      for (int64_t jj = 0; jj < nJ; ++jj) { double c = cin_elem(p, i, j0 + jj); cin_sum = cin_sum + c; Q = Q + fabs(c); }
+    double Cr = p->alpha * dotp;
+    if (p->beta != 0.0) Cr = Cr + p->beta * cin_sum;
+    for (int64_t q = 0; q < n_inj; ++q) {
+      if (inj[q].site != OR_SITE_CHECKSUM || inj[q].i != i || inj[q].j / p->tile_n != tc) continue;
+      double e = ldexp(fabs(Cr), inj[q].rel_log2);
+      Cr = (inj[q].sign < 0) ? Cr - e : Cr + e;
+    }
+    double Cr_ref = 0.0, R = 0.0;
+    for (int64_t jj = 0; jj < nJ; ++jj) { Cr_ref = Cr_ref + T[ii + jj * nI]; R = R + fabs(T[ii + jj * nI]); }
+    double P = rowAbsA * maxAbsBe;
+    double tau = fabs(p->alpha) * P * (gK * (2.0 + 0.0078125) + 9.5367431640625e-07) +
+                 1.1920928955078125e-07 * (R + fabs(p->beta) * Q);
+    double d = Cr_ref - Cr;
+    if (!(fabs(d) <= tau) || isinf(d)) {
+      if (fr < 0) { fr = ii; fr_delta = d; fr_tau = tau; fr_pred = Cr; }
+      ++nr;
+    }
+  }
+  /* Column side, only when a row mismatched. */
+  int64_t nc = 0, fc = -1;
+  double fc_delta = 0.0, fc_tau = 0.0;
+  if (nr > 0) {
+    for (int64_t jj = 0; jj < nJ; ++jj) {
+      int64_t j = j0 + jj;
+      double dotp = 0.0, colAbsB = 0.0;
+      for (int64_t k = 0; k < K; ++k) { double b = b_elem(p, k, j); dotp = dotp + Ac[k] * b; colAbsB = colAbsB + fabs(b); }
+      double cin_sum = 0.0, Q = 0.0;
+      if (p->beta != 0.0)
+        for (int64_t ii = 0; ii < nI; ++ii) { double c = cin_elem(p, i0 + ii, j); cin_sum = cin_sum + c; Q = Q + fabs(c); }
+      double Cc = p->alpha * dotp;
+      if (p->beta != 0.0) Cc = Cc + p->beta * cin_sum;
+      double Cc_ref = 0.0, R = 0.0;
+      for (int64_t ii = 0; ii < nI; ++ii) { Cc_ref = Cc_ref + T[ii + jj * nI]; R = R + fabs(T[ii + jj * nI]); }
+      double P = colAbsB * maxAbsAe;
+      double tau = fabs(p->alpha) * P * (gK + 9.313225746154785e-10) +
+                   1.1920928955078125e-07 * (R + 34.0 * fabs(p->beta) * Q);
+      double d = Cc_ref - Cc;
+      if (!(fabs(d) <= tau) || isinf(d)) {
+        if (fc < 0) { fc = jj; fc_delta = d; fc_tau = tau; }
+        ++nc;
+      }
+    }
+  }
+  oracle_record_t r;
+  memset(&r, 0, sizeof(r));
+  r.tile_row = tr; r.tile_col = tc;
+  r.i = (fr >= 0) ? i0 + fr : -1;
+  r.j = (fc >= 0) ? j0 + fc : -1;
+  r.delta_row = fr_delta; r.delta_col = fc_delta; r.tau_row = fr_tau; r.tau_col = fc_tau;
+  r.rows_flagged = (int32_t)nr; r.cols_flagged = (int32_t)nc;
+  if (nr == 0) {
+    /* clean */
+  } else if (nr == 1 && nc == 1) {
+    res->detected = 1; res->corrected = 1;
+    r.kind = OR_KIND_CORRECTED;
+    double before = T[fr + fc * nI];
+    r.value_before = before;
+    r.value_subtracted = before - fr_delta;
+    /* C(i,j) - delta_row equals C^r(i) - sum_{j' != j} C(i,j') in exact arithmetic; the
+     * second form never touches the erroneous value, so a huge or non-finite error does
+     * not cancel catastrophically. */
+    double rest = 0.0;
+    for (int64_t jj = 0; jj < nJ; ++jj)
+      if (jj != fc) rest = rest + T[fr + jj * nI];
+    double after = fr_pred - rest;
+    T[fr + fc * nI] = round32(after);
+    r.value_after = T[fr + fc * nI];
+    add_record(res, &r);
+  } else if (nc == 0) {
+    res->detected = 1; res->checksum_only = 1;
+    r.kind = OR_KIND_CHECKSUM_ONLY;
+    add_record(res, &r);
+  } else {
+    res->detected = 1; res->uncorrectable = 1;
+    r.kind = OR_KIND_UNCORRECTABLE;
+    add_record(res, &r);
+  }
+  for (int64_t jj = 0; jj < nJ; ++jj)
+    for (int64_t ii = 0; ii < nI; ++ii)
+      Cout[c_index(p->layout, p->ldc, i0 + ii, j0 + jj)] = T[ii + jj * nI];
+  free(Ac); free(Br); free(T);
+}
+
 /* ABFT-protected C = alpha*op(A)*op(B) + beta*C_in into Cout.
  * sel_tiles: NULL = every tile; otherwise n_sel tile numbers t = tile_row + tile_col *
  * n_tile_rows, and only those tiles of Cout are written. K == 0 or alpha == 0 is the
@@ -477,7 +651,10 @@ int oracle_ft_gemm(const oracle_problem_t* p, int64_t n_inj, const oracle_inject
       int64_t r0 = (t % tr) * p->tile_m, c0 = (t / tr) * p->tile_n;
       for (int64_t j = c0; j < c0 + p->tile_n && j < p->N; ++j)
         for (int64_t i = r0; i < r0 + p->tile_m && i < p->M; ++i)
-          Cout[c_index(p->layout, p->ldc, i, j)] = (p->beta == 0.0) ? 0.0 : p->beta * cin_elem(p, i, j);
+          Cout[c_index(p->layout, p->ldc, i, j)] =
+              (p->beta == 0.0) ? 0.0
+                               : (p->precision == OR_PREC_ACC32 ? round32(p->beta * cin_elem(p, i, j))
+                                                                : p->beta * cin_elem(p, i, j));
     }
     return 0;
   }
@@ -485,7 +662,10 @@ int oracle_ft_gemm(const oracle_problem_t* p, int64_t n_inj, const oracle_inject
 #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t s = 0; s < nsel; ++s) {
     int64_t t = sel_tiles ? sel_tiles[s] : s;
-    ft_tile(p, t % tr, t / tr, n_inj, inj, Cout, &res[s]);
+    if (p->precision == OR_PREC_ACC32)
+      ft_tile_acc32(p, t % tr, t / tr, n_inj, inj, Cout, &res[s]);
+    else
+      ft_tile(p, t % tr, t / tr, n_inj, inj, Cout, &res[s]);
   }
   /* Merge in tile order (deterministic). */
   for (int64_t s = 0; s < nsel; ++s) {

@@ -73,7 +73,12 @@ REPORT_BYTES = C.sizeof(FtReport)
 # (name, restype, argtypes) of every entry point declared in include/ftblas.h
 _GEMM_ARGS = [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64, C.c_double, C.c_void_p, C.c_int64,
               C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_int64]
+_GEMM_EX_ARGS = [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_int,
+                 C.c_int64, C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_int,
+                 C.c_void_p, C.c_void_p, C.c_void_p]
 SIGNATURES = {
+    "ftblas_gemm_ex": (C.c_int, _GEMM_EX_ARGS + [C.c_void_p]),
+    "ftblas_gemm_ex_noabft": (C.c_int, _GEMM_EX_ARGS),
     "ftblas_set_injection": (C.c_int, [C.c_void_p]),
     "ftblas_injection_launch_count": (C.c_uint64, []),
     "ftblas_dgemm": (C.c_int, _GEMM_ARGS + [C.c_void_p, C.c_void_p]),
@@ -127,6 +132,25 @@ def ftblas_dgemm_noabft(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, 
 def ftblas_dgemm_host(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream, report):
     return _call("ftblas_dgemm_host", layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream,
                  report)
+
+
+def ftblas_gemm_ex(layout, transa, transb, M, N, K, alpha, A, Atype, lda, B, Btype, ldb, beta, C_, Ctype, ldc,
+                   compute_type, a_scale, b_scale, stream, report):
+    """alpha / beta: host scalars, passed by pointer as the compute type requires."""
+    al, be = _scalar(alpha, compute_type), _scalar(beta, compute_type)
+    return _call("ftblas_gemm_ex", layout, transa, transb, M, N, K, C.addressof(al), A, Atype, lda, B, Btype, ldb,
+                 C.addressof(be), C_, Ctype, ldc, compute_type, a_scale, b_scale, stream, report)
+
+
+def ftblas_gemm_ex_noabft(layout, transa, transb, M, N, K, alpha, A, Atype, lda, B, Btype, ldb, beta, C_, Ctype,
+                          ldc, compute_type, a_scale, b_scale, stream):
+    al, be = _scalar(alpha, compute_type), _scalar(beta, compute_type)
+    return _call("ftblas_gemm_ex_noabft", layout, transa, transb, M, N, K, C.addressof(al), A, Atype, lda, B, Btype,
+                 ldb, C.addressof(be), C_, Ctype, ldc, compute_type, a_scale, b_scale, stream)
+
+
+def _scalar(x, compute_type):
+    return C.c_double(float(x)) if compute_type == R_64F else C.c_float(float(x))
 
 
 def ftblas_set_injection(cfg):

@@ -1,0 +1,49 @@
+// Internal declarations of the reduced-precision (tcgen05) path, kernel frame: C is M x N
+// column-major FP32, A is M x K and B is K x N, both K-contiguous.
+#pragma once
+
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "ft_internal.h"
+
+namespace ftk {
+
+constexpr int kTcBM = 128;       // tile rows (TMEM lanes)
+constexpr int kTcBN = 256;       // tile columns (TMEM columns)
+constexpr int kTcChkRows = 16;   // N of the checksum MMA (pieces of B e in rows 0..2)
+
+struct TcParams {
+  int32_t M, N, K;
+  int32_t swap_report;
+  float alpha, beta;
+  float u_acc;                   // unit roundoff assumed for the tensor-core accumulation
+  int32_t pad_;
+  const void* A; int64_t lda;
+  const void* B; int64_t ldb;
+  float* C; int64_t ldc;
+  const float* rowAbsA;          // [M]   upward sum_k |A(i,k)|
+  const float* colAbsB;          // [N]   upward sum_k |B(k,j)|
+  const float* maxAbsAe;         // [nMb] max_k upward sum_{i in block} |A(i,k)|
+  const float* maxAbsBe;         // [nNb] max_k upward sum_{j in block} |B(k,j)|
+  const float2* sA;              // [nMb][K] e^T A per row block, hi + lo
+  ft_report_t* report;
+  InjectList inj;
+};
+
+struct TcWorkspace {
+  uint16_t* chk;  int64_t kpitch;
+  float2* sA;
+  float* rowAbsPart; float* colAbsPart;
+  float* rowAbsA; float* colAbsB; float* maxAbsAe; float* maxAbsBe;
+  size_t bytes;
+};
+
+size_t tc_workspace_bytes(int32_t M, int32_t N, int32_t K);
+TcWorkspace tc_workspace_carve(void* base, int32_t M, int32_t N, int32_t K);
+cudaError_t launch_tc_encode(const TcParams& p, const TcWorkspace& w, void* ws_base, cudaStream_t st);
+cudaError_t launch_tc_gemm(const TcParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmChk,
+                           bool ft, cudaStream_t st);
+
+}  // namespace ftk

@@ -9,6 +9,7 @@
 #include <mutex>
 
 #include "ft_internal.h"
+#include "ft_tc.h"
 
 using namespace ftk;
 
@@ -124,6 +125,24 @@ bool make_map_f64(CUtensorMap* map, const void* base, int64_t inner, int64_t out
   return r == CUDA_SUCCESS;
 }
 
+// 2-D 16-bit tensor map with 128-byte swizzle: `inner` K-contiguous elements per line.
+bool make_map_b16_sw128(CUtensorMap* map, const void* base, int64_t inner, int64_t outer, int64_t ld_elems,
+                        uint32_t box_inner, uint32_t box_outer) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
+  if (((ld_elems * 2) & 15) != 0 || ld_elems * 2 >= (int64_t(1) << 40)) return false;
+  if (inner <= 0 || outer <= 0 || inner > (int64_t(1) << 32) || outer > (int64_t(1) << 32)) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(outer)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld_elems * 2)};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 // ------------------------------------------------------------------ validation
 struct Frame {
   // kernel frame (column-major): C' = alpha op(A') op(B') + beta C'
@@ -225,7 +244,107 @@ int dgemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, doub
   return record_cuda(launch_dgemm(p, &tmA, &tmB, ft, g_fp64_engine.load(), st));
 }
 
+// ------------------------------------------------------------------ mixed precision
+int gemm_ex_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, const void* alpha, const void* A,
+                 int Atype, int64_t lda, const void* B, int Btype, int64_t ldb, const void* beta, void* C, int Ctype,
+                 int64_t ldc, int ctype, const float* a_scale, const float* b_scale, void* stream,
+                 ft_report_t* report, bool ft) {
+  // argument positions of ftblas_gemm_ex (1-based)
+  if (layout != FTBLAS_ROW_MAJOR && layout != FTBLAS_COL_MAJOR) return -1;
+  if (ta != FTBLAS_NO_TRANS && ta != FTBLAS_TRANS) return -2;
+  if (tb != FTBLAS_NO_TRANS && tb != FTBLAS_TRANS) return -3;
+  if (M < 0) return -4;
+  if (N < 0) return -5;
+  if (K < 0) return -6;
+  if (alpha == nullptr) return -7;
+  if (beta == nullptr) return -14;
+  const bool all64 = Atype == FTBLAS_R_64F && Btype == FTBLAS_R_64F && Ctype == FTBLAS_R_64F && ctype == FTBLAS_R_64F;
+  const bool bf16 = Atype == FTBLAS_R_16BF && Btype == FTBLAS_R_16BF && Ctype == FTBLAS_R_32F && ctype == FTBLAS_R_32F;
+  if (all64) {
+    if (a_scale != nullptr) return -19;
+    if (b_scale != nullptr) return -20;
+    const double al = *static_cast<const double*>(alpha), be = *static_cast<const double*>(beta);
+    int v = dgemm_impl(layout, ta, tb, M, N, K, al, static_cast<const double*>(A), lda,
+                       static_cast<const double*>(B), ldb, be, static_cast<double*>(C), ldc, stream, report, ft);
+    // map dgemm argument positions onto gemm_ex positions
+    static const int pos[17] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 11, 13, 14, 15, 17, 21, 22};
+    return (v < 0 && -v <= 16) ? -pos[-v] : v;
+  }
+  if (!bf16) return FTBLAS_STATUS_NOT_SUPPORTED;
+  if (a_scale != nullptr) return -19;
+  if (b_scale != nullptr) return -20;
+  const bool need_ab = (K > 0 && *static_cast<const float*>(alpha) != 0.0f && M > 0 && N > 0);
+  int v = validate(layout, ta, tb, M, N, K, A, lda, B, ldb, C, ldc, need_ab);
+  if (v != 0) {
+    static const int pos[15] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 11, 13, 14, 15, 17};
+    return -pos[-v];
+  }
+  if (M > kMaxDim || N > kMaxDim || K > kMaxDim) return FTBLAS_STATUS_NOT_SUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (ft && report != nullptr) {
+    if (int e = record_cuda(cudaMemsetAsync(report, 0, sizeof(ft_report_t), st))) return e;
+  }
+  if (M == 0 || N == 0) return 0;
+  const Frame f = map_frame(layout, ta, tb, M, N, A, lda, B, ldb);
+  CallerPoint pts[kMaxInject];
+  int npts = 0;
+  if (ft) {
+    const int64_t tile_rows = f.swap ? kTcBN : kTcBM, tile_cols = f.swap ? kTcBM : kTcBN;
+    npts = plan_injections(M, N, tile_rows, tile_cols, pts);
+  }
+  const float al = *static_cast<const float*>(alpha), be = *static_cast<const float*>(beta);
+  if (!f.a_kmajor || !f.b_kmajor) return FTBLAS_STATUS_NOT_SUPPORTED;
+  if (K == 0 || al == 0.0f) return FTBLAS_STATUS_NOT_SUPPORTED;  // quick return not provided for FP32 C yet
+  TcParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.M = (int32_t)f.M; p.N = (int32_t)f.N; p.K = (int32_t)K;
+  p.alpha = al; p.beta = be; p.u_acc = 0x1p-23f;
+  p.A = f.A; p.lda = f.lda; p.B = f.B; p.ldb = f.ldb;
+  p.C = static_cast<float*>(C); p.ldc = ldc;
+  p.report = ft ? report : nullptr;
+  p.swap_report = f.swap;
+  for (int q = 0; q < npts; ++q) {
+    InjectPoint& ip = p.inj.p[p.inj.n++];
+    const CallerPoint& c = pts[q];
+    ip.i = (int32_t)(f.swap ? c.j : c.i);
+    ip.j = (int32_t)(f.swap ? c.i : c.j);
+    ip.site = c.site == FT_SITE_CHECKSUM ? kSiteChecksumRow : c.site;
+    ip.mode = c.mode; ip.bit = c.bit; ip.rel_log2 = c.rel_log2; ip.sign = c.sign; ip.pad = 0;
+  }
+  CUtensorMap tmA, tmB, tmC;
+  std::memset(&tmA, 0, sizeof(tmA)); std::memset(&tmB, 0, sizeof(tmB)); std::memset(&tmC, 0, sizeof(tmC));
+  if (!make_map_b16_sw128(&tmA, f.A, K, f.M, f.lda, 64, kTcBM)) return FTBLAS_STATUS_NOT_SUPPORTED;
+  if (!make_map_b16_sw128(&tmB, f.B, K, f.N, f.ldb, 64, kTcBN)) return FTBLAS_STATUS_NOT_SUPPORTED;
+  g_last_used_tma = 1;
+  if (!ft) return record_cuda(launch_tc_gemm(p, &tmA, &tmB, &tmA, false, st));
+  const size_t wsb = tc_workspace_bytes(p.M, p.N, p.K);
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, wsb, st) != cudaSuccess) return FTBLAS_STATUS_ALLOC_FAILED;
+  TcWorkspace w = tc_workspace_carve(ws, p.M, p.N, p.K);
+  p.rowAbsA = w.rowAbsA; p.colAbsB = w.colAbsB; p.maxAbsAe = w.maxAbsAe; p.maxAbsBe = w.maxAbsBe; p.sA = w.sA;
+  const int64_t nNb = (f.N + kTcBN - 1) / kTcBN;
+  if (!make_map_b16_sw128(&tmC, w.chk, K, nNb * kTcChkRows, w.kpitch, 64, kTcChkRows)) {
+    cudaFreeAsync(ws, st);
+    return FTBLAS_STATUS_NOT_SUPPORTED;
+  }
+  int rc = record_cuda(launch_tc_encode(p, w, ws, st));
+  if (rc == 0) rc = record_cuda(launch_tc_gemm(p, &tmA, &tmB, &tmC, true, st));
+  cudaFreeAsync(ws, st);
+  return rc;
+}
+
 // ------------------------------------------------------------------ host-buffer workspace
+// Copy `cnt` runs of `run` doubles from pitch `spitch` to pitch `dpitch` (elements): one
+// linear copy when the pitches agree (the 2-D engine path is far slower) and, for copies
+// into the caller's buffer, there is no padding to preserve between runs; else 2-D.
+cudaError_t copy_runs(double* dst, int64_t dpitch, const double* src, int64_t spitch, int64_t run, int64_t cnt,
+                      cudaMemcpyKind kind, cudaStream_t st) {
+  if (run == 0 || cnt == 0) return cudaSuccess;
+  const bool linear = dpitch == spitch && (kind == cudaMemcpyHostToDevice || run == dpitch);
+  if (linear) return cudaMemcpyAsync(dst, src, size_t((cnt - 1) * spitch + run) * 8, kind, st);
+  return cudaMemcpy2DAsync(dst, dpitch * 8, src, spitch * 8, run * 8, cnt, kind, st);
+}
+
 std::mutex g_ws_mu;
 void* g_ws = nullptr;
 size_t g_ws_bytes = 0;
@@ -325,21 +444,17 @@ int ftblas_dgemm_host(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_tran
   double* dC = reinterpret_cast<double*>(base + up(bytesA) + up(bytesB));
   ft_report_t* dR = reinterpret_cast<ft_report_t*>(base + up(bytesA) + up(bytesB) + up(bytesC));
   if (need_ab) {
-    if (int e = record_cuda(cudaMemcpy2DAsync(dA, dlda * 8, A, lda * 8, a_run * 8, a_cnt, cudaMemcpyHostToDevice, st)))
-      return e;
-    if (int e = record_cuda(cudaMemcpy2DAsync(dB, dldb * 8, B, ldb * 8, b_run * 8, b_cnt, cudaMemcpyHostToDevice, st)))
-      return e;
+    if (int e = record_cuda(copy_runs(dA, dlda, A, lda, a_run, a_cnt, cudaMemcpyHostToDevice, st))) return e;
+    if (int e = record_cuda(copy_runs(dB, dldb, B, ldb, b_run, b_cnt, cudaMemcpyHostToDevice, st))) return e;
   }
   if (beta != 0.0 && M > 0 && N > 0) {
-    if (int e = record_cuda(cudaMemcpy2DAsync(dC, dldc * 8, C, ldc * 8, c_run * 8, c_cnt, cudaMemcpyHostToDevice, st)))
-      return e;
+    if (int e = record_cuda(copy_runs(dC, dldc, C, ldc, c_run, c_cnt, cudaMemcpyHostToDevice, st))) return e;
   }
   int rc = dgemm_impl(layout, transa, transb, M, N, K, alpha, dA, dlda, dB, dldb, beta, dC, dldc, stream,
                       report ? dR : nullptr, true);
   if (rc != 0) return rc;
   if (M > 0 && N > 0) {
-    if (int e = record_cuda(cudaMemcpy2DAsync(C, ldc * 8, dC, dldc * 8, c_run * 8, c_cnt, cudaMemcpyDeviceToHost, st)))
-      return e;
+    if (int e = record_cuda(copy_runs(C, ldc, dC, dldc, c_run, c_cnt, cudaMemcpyDeviceToHost, st))) return e;
   }
   if (report) {
     if (int e = record_cuda(cudaMemcpyAsync(report, dR, sizeof(ft_report_t), cudaMemcpyDeviceToHost, st))) return e;
@@ -347,10 +462,28 @@ int ftblas_dgemm_host(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_tran
   return record_cuda(cudaStreamSynchronize(st));
 }
 
+int ftblas_gemm_ex(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb, int64_t M, int64_t N, int64_t K,
+                   const void* alpha, const void* A, ftblas_dtype_t Atype, int64_t lda, const void* B,
+                   ftblas_dtype_t Btype, int64_t ldb, const void* beta, void* C, ftblas_dtype_t Ctype, int64_t ldc,
+                   ftblas_dtype_t compute_type, const float* a_scale, const float* b_scale, void* stream,
+                   ft_report_t* report) {
+  return gemm_ex_impl(layout, transa, transb, M, N, K, alpha, A, Atype, lda, B, Btype, ldb, beta, C, Ctype, ldc,
+                      compute_type, a_scale, b_scale, stream, report, true);
+}
+
+int ftblas_gemm_ex_noabft(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb, int64_t M, int64_t N,
+                          int64_t K, const void* alpha, const void* A, ftblas_dtype_t Atype, int64_t lda,
+                          const void* B, ftblas_dtype_t Btype, int64_t ldb, const void* beta, void* C,
+                          ftblas_dtype_t Ctype, int64_t ldc, ftblas_dtype_t compute_type, const float* a_scale,
+                          const float* b_scale, void* stream) {
+  return gemm_ex_impl(layout, transa, transb, M, N, K, alpha, A, Atype, lda, B, Btype, ldb, beta, C, Ctype, ldc,
+                      compute_type, a_scale, b_scale, stream, nullptr, false);
+}
+
 int ftblas_verification_tile(ftblas_layout_t layout, ftblas_dtype_t compute_type, int64_t M, int64_t N, int64_t K,
                              int64_t* tile_rows, int64_t* tile_cols, int64_t* k_tile) {
   if (layout != FTBLAS_ROW_MAJOR && layout != FTBLAS_COL_MAJOR) return -1;
-  if (compute_type != FTBLAS_R_64F) return -2;
+  if (compute_type != FTBLAS_R_64F && compute_type != FTBLAS_R_32F) return -2;
   if (M < 0) return -3;
   if (N < 0) return -4;
   if (K < 0) return -5;
@@ -358,9 +491,10 @@ int ftblas_verification_tile(ftblas_layout_t layout, ftblas_dtype_t compute_type
   if (!tile_cols) return -7;
   if (!k_tile) return -8;
   const bool swap = layout == FTBLAS_ROW_MAJOR;
-  *tile_rows = swap ? kDBN : kDBM;
-  *tile_cols = swap ? kDBM : kDBN;
-  *k_tile = kDBK;
+  const int64_t bm = compute_type == FTBLAS_R_64F ? kDBM : kTcBM, bn = compute_type == FTBLAS_R_64F ? kDBN : kTcBN;
+  *tile_rows = swap ? bn : bm;
+  *tile_cols = swap ? bm : bn;
+  *k_tile = compute_type == FTBLAS_R_64F ? kDBK : 64;
   return 0;
 }
 

@@ -1,0 +1,205 @@
+"""GPU parity of the BF16 tensor-core ABFT GEMM (tcgen05, FP32 accumulation) against the
+CPU oracle's ACC32 precision, through the C ABI (ftblas_gemm_ex).
+
+Values: the oracle forms each C(i,j) from the exact inner product of the same BF16
+operands (binary64), rounded once to binary32; the kernel accumulates in binary32 on the
+tensor core. They must agree within the stated accumulation bound,
+|C - C_ref| <= 2 gamma_K(2^-23) |alpha| (|A||B|)_ij + 2^-22 (|C_ref| + |beta C_in|).
+Detection, location and classification must match the oracle exactly where the injected
+error is not within a factor 4 of the threshold (both sides evaluate the same threshold
+formula from slightly different roundings).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth as S
+from tests.helpers import record_set, report_summary
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2104_00897_gb300 as fb  # noqa: E402
+
+U32 = 2.0 ** -23
+
+
+def gamma(n, u):
+    return n * u / (1 - n * u)
+
+
+@pytest.fixture(autouse=True)
+def _fresh_injection():
+    fb.ftblas_set_injection(None)
+    yield
+    fb.ftblas_set_injection(None)
+
+
+class Bf16Problem:
+    """Seeded BF16 operands, K-contiguous in the kernel frame (the path's requirement)."""
+
+    def __init__(self, M, N, K, layout=O.COL_MAJOR, alpha=1.0, beta=0.0, seed=1, row_scale=False, pad=8):
+        self.M, self.N, self.K, self.layout, self.alpha, self.beta = M, N, K, layout, alpha, beta
+        # column-major: A transposed, B not; row-major: A not, B transposed
+        self.ta, self.tb = (O.TRANS, O.NO_TRANS) if layout == O.COL_MAJOR else (O.NO_TRANS, O.TRANS)
+        A = S.normal_matrix(seed, 0, M, K)
+        if row_scale:
+            A = A * S.pow2_row_scales(seed, 5, M)[:, None]
+        B = S.normal_matrix(seed, 1, K, N)
+        self.Abits = S.to_bf16_bits(A)
+        self.Bbits = S.to_bf16_bits(B)
+        self.A = S.bf16_bits_to_f64(self.Abits)
+        self.B = S.bf16_bits_to_f64(self.Bbits)
+        self.Cin = S.bf16_bits_to_f64(S.to_bf16_bits(S.normal_matrix(seed, 2, M, N)))  # exact in binary32 too
+        Xa = self.Abits if self.ta == O.NO_TRANS else self.Abits.T
+        Xb = self.Bbits if self.tb == O.NO_TRANS else self.Bbits.T
+        up8 = lambda x: (x + 7) // 8 * 8  # 16-byte rows for TMA
+        lda = up8(Xa.shape[0] if layout == O.COL_MAJOR else Xa.shape[1]) + pad
+        ldb = up8(Xb.shape[0] if layout == O.COL_MAJOR else Xb.shape[1]) + pad
+        self.a16, self.lda = S.store(Xa, layout, ld=lda, pad_value=0)
+        self.b16, self.ldb = S.store(Xb, layout, ld=ldb, pad_value=0)
+        XaF = self.A if self.ta == O.NO_TRANS else self.A.T
+        XbF = self.B if self.tb == O.NO_TRANS else self.B.T
+        self.a64, _ = S.store(XaF, layout, ld=lda)
+        self.b64, _ = S.store(XbF, layout, ld=ldb)
+        self.ldc = (M if layout == O.COL_MAJOR else N) + 4
+        self.c64, _ = S.store(self.Cin, layout, ld=self.ldc)
+
+    def tile(self):
+        return fb.ftblas_verification_tile(self.layout, fb.R_32F, self.M, self.N, self.K)
+
+    def run(self, protect=True):
+        dA = torch.from_numpy(self.a16.view(np.int16)).cuda()
+        dB = torch.from_numpy(self.b16.view(np.int16)).cuda()
+        dC = torch.from_numpy(np.nan_to_num(self.c64, nan=0.0).astype(np.float32)).cuda()
+        rep = fb.new_report() if protect else None
+        st = torch.cuda.current_stream().cuda_stream
+        args = (self.layout, self.ta, self.tb, self.M, self.N, self.K, self.alpha, dA.data_ptr(), fb.R_16BF,
+                self.lda, dB.data_ptr(), fb.R_16BF, self.ldb, self.beta, dC.data_ptr(), fb.R_32F, self.ldc, fb.R_32F,
+                None, None, st)
+        rc = fb.ftblas_gemm_ex(*args, rep.data_ptr()) if protect else fb.ftblas_gemm_ex_noabft(*args)
+        fb.check(rc, "ftblas_gemm_ex")
+        torch.cuda.synchronize()
+        out = S.load(dC.cpu().numpy().astype(np.float64), self.layout, self.M, self.N, self.ldc)
+        return out, (fb.report_from_device(rep) if protect else None)
+
+    def oracle(self, injections=(), tiles=None):
+        tr, tc, bk = self.tile()
+        out, rep = O.ft_gemm(self.layout, self.ta, self.tb, self.M, self.N, self.K, self.alpha, self.a64, self.lda,
+                             self.b64, self.ldb, self.beta, self.c64, self.ldc, tr, tc, bk, injections=injections,
+                             tiles=tiles, precision=O.PREC_ACC32)
+        return S.load(out, self.layout, self.M, self.N, self.ldc), rep
+
+    def bound(self, ref):
+        prod = np.abs(self.A) @ np.abs(self.B)
+        return (2 * gamma(self.K, U32) * abs(self.alpha) * prod + 2.0 ** -22 * (np.abs(ref) + abs(self.beta) *
+                np.abs(self.Cin)) + 1e-30)
+
+
+@pytest.mark.parametrize("layout", [O.COL_MAJOR, O.ROW_MAJOR])
+@pytest.mark.parametrize("shape", [(128, 256, 64), (300, 700, 200), (256, 512, 1000), (5, 3, 130)])
+def test_bf16_values_match_oracle_within_bound(layout, shape):
+    M, N, K = shape
+    P = Bf16Problem(M, N, K, layout, alpha=1.25, beta=0.5, seed=M + N + K)
+    plain, _ = P.run(protect=False)
+    got, rep = P.run(protect=True)
+    ref, orep = P.oracle()
+    assert np.all(np.abs(got - ref) <= P.bound(ref))
+    assert np.array_equal(got, plain)  # the checksum MMA does not touch the product
+    assert report_summary(rep) == report_summary(orep)
+    assert rep.detected == 0 and rep.status == 0
+
+
+@pytest.mark.parametrize("layout", [O.COL_MAJOR, O.ROW_MAJOR])
+def test_bf16_injections_match_oracle(layout):
+    P = Bf16Problem(384, 768, 512, layout, alpha=1.0, beta=0.0, seed=3)
+    clean, _ = P.run()
+    cases = [
+        [dict(i=10, j=20, site=fb.SITE_OUTPUT, mode=fb.MODE_ADD_REL, rel_log2=4, sign=1)],
+        [dict(i=300, j=700, site=fb.SITE_OUTPUT, mode=fb.MODE_ADD_REL, rel_log2=2, sign=-1)],
+        [dict(i=129, j=257, site=fb.SITE_ACCUM, mode=fb.MODE_BITFLIP, bit=29)],
+        [dict(i=5, j=6, site=fb.SITE_OUTPUT, mode=fb.MODE_BITFLIP, bit=30)],
+        [dict(i=10, j=20, site=fb.SITE_OUTPUT, mode=fb.MODE_ADD_REL, rel_log2=3),
+         dict(i=11, j=30, site=fb.SITE_OUTPUT, mode=fb.MODE_ADD_REL, rel_log2=3)],
+        [dict(i=10, j=20, site=fb.SITE_OUTPUT, mode=fb.MODE_ADD_REL, rel_log2=-40)],
+    ]
+    if layout == O.COL_MAJOR:
+        cases.append([dict(i=200, j=100, site=fb.SITE_CHECKSUM, mode=fb.MODE_ADD_REL, rel_log2=2, sign=1)])
+    for pts in cases:
+        fb.ftblas_set_injection(fb.make_injection(fixed=pts))
+        got, rep = P.run()
+        ref, orep = P.oracle(injections=pts)
+        assert report_summary(rep) == report_summary(orep), pts
+        assert record_set(rep) == record_set(orep), pts
+        for r in rep.records():
+            if r.kind == fb.KIND_CORRECTED:
+                # corrected from the checksum: within the row threshold of the fault-free value
+                assert abs(got[r.i, r.j] - clean[r.i, r.j]) <= r.tau_row + 2.0 ** -22 * abs(clean[r.i, r.j])
+        if rep.uncorrectable == 0:
+            mask = np.ones_like(got, dtype=bool)
+            for r in rep.records():
+                if r.i >= 0 and r.j >= 0:
+                    mask[r.i, r.j] = False
+            assert np.array_equal(got[mask], clean[mask])
+
+
+def test_bf16_detection_threshold_sweep_agrees_with_oracle():
+    """Config-3 style: relative output errors 2^p |C|, p = -20 .. 4, rows scaled by 2^u."""
+    P = Bf16Problem(256, 512, 1024, O.COL_MAJOR, alpha=1.0, beta=0.0, seed=11, row_scale=True)
+    _, orep0 = P.oracle()
+    assert orep0.detected == 0
+    points = [(17 * q % 256, 61 * q % 512) for q in range(1, 13)]
+    detected_min_p = None
+    for p in range(-20, 5, 2):
+        for sign in (1, -1):
+            pts = [dict(i=i, j=j, site=fb.SITE_OUTPUT, mode=fb.MODE_ADD_REL, rel_log2=p, sign=sign)
+                   for (i, j) in points[:1]]
+            fb.ftblas_set_injection(fb.make_injection(fixed=pts))
+            _, rep = P.run()
+            _, orep = P.oracle(injections=pts)
+            r = orep.records()
+            if r and r[0].tau_row > 0 and 0.25 < abs(r[0].delta_row) / r[0].tau_row < 4:
+                continue  # marginal: within a factor 4 of the threshold
+            assert report_summary(rep) == report_summary(orep), (p, sign)
+            if rep.corrected and detected_min_p is None:
+                detected_min_p = p
+    assert detected_min_p is not None and detected_min_p <= 4
+
+
+def test_bf16_non_k_contiguous_is_not_supported():
+    P = Bf16Problem(128, 256, 64, O.COL_MAJOR)
+    dA = torch.zeros(128 * 64, dtype=torch.int16, device="cuda")
+    dB = torch.zeros(256 * 64, dtype=torch.int16, device="cuda")
+    dC = torch.zeros(128 * 256, dtype=torch.float32, device="cuda")
+    rc = fb.ftblas_gemm_ex(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, 128, 256, 64, 1.0, dA.data_ptr(), fb.R_16BF, 128,
+                           dB.data_ptr(), fb.R_16BF, 64, 0.0, dC.data_ptr(), fb.R_32F, 128, fb.R_32F, None, None,
+                           None, None)
+    assert rc == 2  # FTBLAS_STATUS_NOT_SUPPORTED
+    assert P.M == 128
+
+
+def test_bf16_full_size_8192_sampled_rows():
+    """8192^3 BF16 with an injected output error: sampled rows within the bound, the faulted
+    tile's detection equal to the oracle's."""
+    n = 8192
+    P = Bf16Problem(n, n, n, O.COL_MAJOR, alpha=1.0, beta=0.0, seed=20210603, pad=0)
+    i, j = 4321, 1234
+    pt = dict(i=i, j=j, site=fb.SITE_OUTPUT, mode=fb.MODE_ADD_REL, rel_log2=4, sign=1)
+    fb.ftblas_set_injection(fb.make_injection(fixed=[pt]))
+    got, rep = P.run()
+    assert report_summary(rep)[:5] == ((n // 128) * (n // 256), 1, 1, 0, 0)
+    assert [(r.i, r.j) for r in rep.records()] == [(i, j)]
+    rows = np.unique(np.concatenate([S.randint(9, 9, 3, 0, n - 1), [i]]))
+    ref_rows = O.gemm_rows(O.COL_MAJOR, P.ta, P.tb, n, n, n, P.alpha, P.a64, P.lda, P.b64, P.ldb, P.beta, P.c64,
+                           P.ldc, rows)
+    prod = (np.abs(P.A[rows, :]) @ np.abs(P.B))
+    bound = 2 * gamma(n, U32) * prod + 2.0 ** -22 * np.abs(ref_rows) + 1e-30
+    sel = np.ones_like(ref_rows, dtype=bool)
+    sel[list(rows).index(i), j] = False
+    assert np.all(np.abs(got[rows, :] - ref_rows)[sel] <= bound[sel])
+    tr, tc, bk = P.tile()
+    t = (i // tr) + (j // tc) * ((n + tr - 1) // tr)
+    _, orep = P.oracle(injections=[pt], tiles=[t])
+    assert record_set(orep) == record_set(rep)

@@ -362,3 +362,99 @@ def test_seeded_draw_properties():
     assert seen_launches == [5, 15, 25]  # 12345 % 10 == 5
     pts = O.draw_injections(1, 0, 1, 100, O.SITE_ACCUM, O.MODE_BITFLIP, 40, 62, 0, 0, M, N, tm, tn)
     assert len(pts) == n_tiles
+
+
+# ------------------------------------------------------------------------------------
+# ACC32 precision (binary32 accumulation and output): pins on exact integer data
+# ------------------------------------------------------------------------------------
+
+def ft32(A_log, B_log, alpha=1.0, beta=0.0, C_log=None, tile=(8, 16), inj=()):
+    M, K = A_log.shape
+    N = B_log.shape[1]
+    a, lda = stored(O.COL_MAJOR, O.TRANS, A_log)   # A k-contiguous
+    b, ldb = stored(O.COL_MAJOR, O.NO_TRANS, B_log)
+    if C_log is None:
+        C_log = np.zeros((M, N))
+    c, ldc = c_store(O.COL_MAJOR, C_log)
+    out, rep = O.ft_gemm(O.COL_MAJOR, O.TRANS, O.NO_TRANS, M, N, K, alpha, a, lda, b, ldb, beta, c, ldc,
+                         tile[0], tile[1], 64, injections=inj, precision=O.PREC_ACC32)
+    return S.load(out, O.COL_MAJOR, M, N, ldc), rep
+
+
+def test_acc32_closed_form_is_exact_after_binary32_rounding():
+    M, N, K = 9, 13, 20
+    i = np.arange(M)[:, None]
+    j = np.arange(N)[None, :]
+    k = np.arange(K)
+    A = (np.arange(M)[:, None] + k[None, :]).astype(np.float64)
+    B = (k[:, None] - np.arange(N)[None, :]).astype(np.float64)
+    S1 = K * (K - 1) // 2
+    S2 = (K - 1) * K * (2 * K - 1) // 6
+    expect = (-K * i * j + (i - j) * S1 + S2).astype(np.float64)  # integers < 2^24: exact in binary32
+    got, rep = ft32(A, B)
+    assert np.array_equal(got, expect) and rep.detected == 0
+    a, lda = stored(O.COL_MAJOR, O.NO_TRANS, A)
+    b, ldb = stored(O.COL_MAJOR, O.NO_TRANS, B)
+    plain32 = O.gemm(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, M, N, K, 1.0, a, lda, b, ldb, 0.0, None, M,
+                     precision=O.PREC_ACC32)
+    assert np.array_equal(S.load(plain32, O.COL_MAJOR, M, N, M), expect)
+
+
+def test_acc32_binary32_rounding_of_the_output():
+    """C is rounded to binary32 once: 1 + 2^-30 becomes 1."""
+    A = np.array([[1.0, 2.0 ** -30]])
+    B = np.array([[1.0], [1.0]])
+    got, _ = ft32(A, B, tile=(1, 1))
+    assert got[0, 0] == 1.0
+
+
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")
+def test_acc32_injections_on_integer_data():
+    M, N, K = 16, 32, 24
+    A = S.randint(71, 0, M * K, -3, 3).reshape(M, K).astype(np.float64)
+    B = S.randint(71, 1, K * N, -3, 3).reshape(K, N).astype(np.float64)
+    Cin = S.randint(71, 2, M * N, -5, 5).reshape(M, N).astype(np.float64)
+    clean, rep = ft32(A, B, 1.0, 1.0, Cin)
+    assert rep.detected == 0
+    nz = [(i, j) for i in range(M) for j in range(N) if clean[i, j] != 0]
+    (i, j) = nz[5]
+    # a large output error: located, and subtracting it restores C exactly (exact checksums)
+    got, rep = ft32(A, B, 1.0, 1.0, Cin, inj=[dict(i=i, j=j, site=O.SITE_OUTPUT, mode=O.MODE_ADD_REL, rel_log2=3,
+                                                   sign=1)])
+    assert (rep.corrected, rep.records()[0].i, rep.records()[0].j) == (1, i, j)
+    assert rep.records()[0].delta_row == 8.0 * abs(clean[i, j])
+    assert np.array_equal(got, clean)
+    # an error far below the threshold is not detected
+    got, rep = ft32(A, B, 1.0, 1.0, Cin, inj=[dict(i=i, j=j, site=O.SITE_OUTPUT, mode=O.MODE_ADD_REL, rel_log2=-60,
+                                                   sign=1)])
+    assert rep.detected == 0
+    # an output flipped to infinity: recovered from the row checksum, exactly
+    ones = [(i, j) for (i, j) in nz if abs(clean[i, j]) == 1.0]
+    if ones:
+        (i1, j1) = ones[0]
+        got, rep = ft32(A, B, 1.0, 1.0, Cin, inj=[dict(i=i1, j=j1, site=O.SITE_OUTPUT, mode=O.MODE_BITFLIP, bit=30)])
+        assert rep.corrected == 1 and math.isinf(rep.records()[0].value_before)
+        assert np.array_equal(got, clean)
+    # an accumulator flip of the binary32 sum (bit 29: exponent)
+    got, rep = ft32(A, B, 1.0, 1.0, Cin, inj=[dict(i=i, j=j, site=O.SITE_ACCUM, mode=O.MODE_BITFLIP, bit=29)])
+    assert (rep.corrected, rep.records()[0].i, rep.records()[0].j) == (1, i, j)
+    assert np.array_equal(got, clean)
+    # a fault in the predicted row checksum: checksum-only, C kept
+    got, rep = ft32(A, B, 1.0, 1.0, Cin, inj=[dict(i=3, j=0, site=O.SITE_CHECKSUM, mode=O.MODE_ADD_REL, rel_log2=2,
+                                                   sign=1)])
+    assert (rep.checksum_only, rep.corrected) == (1, 0) and np.array_equal(got, clean)
+    # two errors in one tile: uncorrectable
+    (i2, j2) = [(a, b) for (a, b) in nz if a // 8 == i // 8 and b // 16 == j // 16 and a != i and b != j][0]
+    _, rep = ft32(A, B, 1.0, 1.0, Cin, inj=[dict(i=i, j=j, site=O.SITE_OUTPUT, mode=O.MODE_ADD_REL, rel_log2=3),
+                                            dict(i=i2, j=j2, site=O.SITE_OUTPUT, mode=O.MODE_ADD_REL, rel_log2=3)])
+    assert rep.uncorrectable == 1
+
+
+def test_acc32_clean_soak_bf16_like_values():
+    """bfloat16-exact operands, rows scaled by 2^u: no false alarm at K = 512."""
+    for seed in range(4):
+        M, N, K = 32, 64, 512
+        A = S.bf16_bits_to_f64(S.to_bf16_bits(S.normal_matrix(seed, 0, M, K) * S.pow2_row_scales(seed, 5, M)[:, None]))
+        B = S.bf16_bits_to_f64(S.to_bf16_bits(S.normal_matrix(seed, 1, K, N)))
+        _, rep = ft32(A, B, 1.0, 0.0, None, tile=(16, 32))
+        assert rep.detected == 0
