@@ -154,7 +154,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     sm.nonfinite = 0;
     fence_mbar_init();
   }
-  if (warp == 1) tmem_alloc(&sm.tmem_base, TMEM_COLS);
+  if (warp == 1) {
+    __syncwarp();
+    tmem_alloc(&sm.tmem_base, TMEM_COLS);
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -207,7 +210,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const bool row_ok = row < nI;
     const int ew = warp - 2;                // epilogue warp index 0..3
     const uint32_t trow = tmem + (static_cast<uint32_t>(q * 32) << 16);
-    const bool got = mbar_wait_bounded(&sm.accum, 0, kWaitLimitNs);
+    // tcgen05.ld is warp-collective (.sync.aligned): every TMEM load below is executed by all
+    // 32 lanes of the warp, whatever their row; `got` is made warp-uniform for that reason.
+    const bool got = __all_sync(0xffffffffu, mbar_wait_bounded(&sm.accum, 0, kWaitLimitNs));
     if (!got) sm.timeout = 1;
     tc_fence_after();
     const bool beta_nz = p.beta != 0.0f;
@@ -216,6 +221,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (got) {
       for (int ch = 0; ch < BN / 32; ++ch) {
         uint32_t v[32];
+        __syncwarp();  // reconverge after the previous chunk's per-lane branches
         tmem_ld32(trow + ch * 32, v);
         tmem_ld_wait();
         float cinv[32];
@@ -271,10 +277,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // -------------------------------------------------------- row verification
       double delta = 0.0, tau = 0.0, predicted = 0.0;
       bool flagged = false;
-      if (got && row_ok) {
-        uint32_t w4[4];
+      uint32_t w4[4] = {0u, 0u, 0u, 0u};
+      if (got) {  // warp-uniform
+        __syncwarp();
         tmem_ld4(trow + kChkCol, w4);
         tmem_ld_wait();
+      }
+      if (got && row_ok) {
         const double pr = (double)__uint_as_float(w4[0]) + (double)__uint_as_float(w4[1]) +
                           (double)__uint_as_float(w4[2]);
         const double cin_sum = (double)cs + (double)cc;
@@ -400,6 +409,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   if (t == 0 && sm.timeout && p.report) atomicOr(&p.report->status, FT_STATUS_TIMEOUT);
   if (warp == 1) {
+    __syncwarp();  // tcgen05.dealloc is warp-collective: reconverge after the divergent MMA issue
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
   }
