@@ -51,6 +51,7 @@ typedef enum {
 #define FTBLAS_STATUS_NOT_SUPPORTED 2   /* dtype / shape / alignment combination not provided */
 #define FTBLAS_STATUS_CUDA_ERROR 3      /* a CUDA runtime call failed (see ftblas_last_cuda_error) */
 #define FTBLAS_STATUS_ALLOC_FAILED 4    /* the library could not obtain workspace */
+#define FTBLAS_STATUS_WORKSPACE_LIMIT 5 /* ftblas_gemm_ex_noalloc: problem exceeds its static scratch */
 
 /* Report status bits (ft_report_t.status). */
 #define FT_STATUS_TIMEOUT 1u            /* a bounded device wait gave up; affected tiles were not stored */
@@ -198,6 +199,33 @@ int ftblas_gemm_ex_noabft(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_
                           const void* B, ftblas_dtype_t Btype, int64_t ldb, const void* beta,
                           void* C, ftblas_dtype_t Ctype, int64_t ldc, ftblas_dtype_t compute_type,
                           const float* a_scale, const float* b_scale, void* stream);
+
+/* ftblas_gemm_ex for callers that must not allocate device memory. The paper has no
+ * counterpart: this entry point exists for integrations where the process does not own
+ * the device allocator, so cudaMalloc / cudaMallocAsync are unavailable or forbidden
+ * while work is being issued. Examples are a runtime whose memory is fully reserved up
+ * front by another framework's caching allocator, a real-time or certification setting
+ * that forbids allocation after initialisation, and a caller holding a lock under which
+ * allocation could block. The protected BF16 GEMM (the same argument list and the same
+ * supported combination as ftblas_gemm_ex: A, B FTBLAS_R_16BF, C and compute
+ * FTBLAS_R_32F) takes its encode scratch from one static device array of 16 MiB that
+ * every GPU loading this library holds until the process exits; nothing else is
+ * allocated (no cudaMalloc, cudaFree, stream-ordered or library allocation).
+ *   - Size limit: problems whose scratch, about 32*K*ceil(N/256) + 8*K*ceil(M/128) +
+ *     8*(M+N)*ceil(K/1024) bytes, exceeds 16 MiB are rejected with
+ *     FTBLAS_STATUS_WORKSPACE_LIMIT before any device work (M = N = K = 8192 fits).
+ *   - First call per device: it looks up the device address of the static array with
+ *     the device current; make that first call before any stream capture.
+ *   - Sharing: every call on a device uses the same array and clears the part it needs
+ *     at its start. Calls whose device work overlaps (different streams, or other
+ *     threads) race on it and must be serialised by the caller.
+ * Other combinations return FTBLAS_STATUS_NOT_SUPPORTED. */
+int ftblas_gemm_ex_noalloc(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,
+                           int64_t M, int64_t N, int64_t K, const void* alpha,
+                           const void* A, ftblas_dtype_t Atype, int64_t lda,
+                           const void* B, ftblas_dtype_t Btype, int64_t ldb, const void* beta,
+                           void* C, ftblas_dtype_t Ctype, int64_t ldc, ftblas_dtype_t compute_type,
+                           const float* a_scale, const float* b_scale, void* stream, ft_report_t* report);
 
 /* Shape of the verification tile used for a call, in the caller's coordinates of C, and
  * the k-tile depth that sets the accumulator injection point (bk * floor(ceil(K/bk)/2)

@@ -21,6 +21,7 @@ SITE_ACCUM, SITE_OUTPUT, SITE_CHECKSUM = 1, 2, 3
 MODE_BITFLIP, MODE_ADD_REL = 0, 1
 KIND_CORRECTED, KIND_CHECKSUM_ONLY, KIND_UNCORRECTABLE, KIND_INPUT_NONFINITE = 1, 2, 3, 4
 STATUS_TIMEOUT, STATUS_RECORDS_TRUNCATED = 1, 2
+STATUS_NOT_SUPPORTED, STATUS_CUDA_ERROR, STATUS_ALLOC_FAILED, STATUS_WORKSPACE_LIMIT = 2, 3, 4, 5
 ENGINE_DFMA, ENGINE_DMMA = 0, 1
 MAX_RECORDS = 64
 MAX_FIXED_INJECTIONS = 16
@@ -79,6 +80,7 @@ _GEMM_EX_ARGS = [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64, C.c
 SIGNATURES = {
     "ftblas_gemm_ex": (C.c_int, _GEMM_EX_ARGS + [C.c_void_p]),
     "ftblas_gemm_ex_noabft": (C.c_int, _GEMM_EX_ARGS),
+    "ftblas_gemm_ex_noalloc": (C.c_int, _GEMM_EX_ARGS + [C.c_void_p]),
     "ftblas_set_injection": (C.c_int, [C.c_void_p]),
     "ftblas_injection_launch_count": (C.c_uint64, []),
     "ftblas_dgemm": (C.c_int, _GEMM_ARGS + [C.c_void_p, C.c_void_p]),
@@ -147,6 +149,14 @@ def ftblas_gemm_ex_noabft(layout, transa, transb, M, N, K, alpha, A, Atype, lda,
     al, be = _scalar(alpha, compute_type), _scalar(beta, compute_type)
     return _call("ftblas_gemm_ex_noabft", layout, transa, transb, M, N, K, C.addressof(al), A, Atype, lda, B, Btype,
                  ldb, C.addressof(be), C_, Ctype, ldc, compute_type, a_scale, b_scale, stream)
+
+
+def ftblas_gemm_ex_noalloc(layout, transa, transb, M, N, K, alpha, A, Atype, lda, B, Btype, ldb, beta, C_, Ctype,
+                           ldc, compute_type, a_scale, b_scale, stream, report):
+    """ftblas_gemm_ex on the library's static 16 MiB device scratch: allocates nothing."""
+    al, be = _scalar(alpha, compute_type), _scalar(beta, compute_type)
+    return _call("ftblas_gemm_ex_noalloc", layout, transa, transb, M, N, K, C.addressof(al), A, Atype, lda, B, Btype,
+                 ldb, C.addressof(be), C_, Ctype, ldc, compute_type, a_scale, b_scale, stream, report)
 
 
 def _scalar(x, compute_type):

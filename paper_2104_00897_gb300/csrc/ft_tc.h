@@ -46,4 +46,12 @@ cudaError_t launch_tc_encode(const TcParams& p, const TcWorkspace& w, void* ws_b
 cudaError_t launch_tc_gemm(const TcParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmChk,
                            bool ft, cudaStream_t st);
 
+// The protected BF16 GEMM of ftblas_gemm_ex run on caller-supplied device scratch of
+// ws_bytes bytes instead of stream-ordered allocations. Returns
+// FTBLAS_STATUS_WORKSPACE_LIMIT, before any device work, when the problem needs more.
+int gemm_bf16_ft_with_workspace(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, const void* alpha,
+                                const void* A, int Atype, int64_t lda, const void* B, int Btype, int64_t ldb,
+                                const void* beta, void* C, int Ctype, int64_t ldc, int ctype, const float* a_scale,
+                                const float* b_scale, void* stream, ft_report_t* report, void* ws, size_t ws_bytes);
+
 }  // namespace ftk

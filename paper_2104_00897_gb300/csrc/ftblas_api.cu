@@ -352,6 +352,80 @@ int g_ws_device = -1;
 
 }  // namespace
 
+namespace ftk {
+
+// Same argument checks, mapping, injection plan and launches as the BF16 branch of
+// gemm_ex_impl, with the encode workspace taken from `ws` (no allocation of any kind).
+int gemm_bf16_ft_with_workspace(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, const void* alpha,
+                                const void* A, int Atype, int64_t lda, const void* B, int Btype, int64_t ldb,
+                                const void* beta, void* C, int Ctype, int64_t ldc, int ctype, const float* a_scale,
+                                const float* b_scale, void* stream, ft_report_t* report, void* ws, size_t ws_bytes) {
+  if (layout != FTBLAS_ROW_MAJOR && layout != FTBLAS_COL_MAJOR) return -1;
+  if (ta != FTBLAS_NO_TRANS && ta != FTBLAS_TRANS) return -2;
+  if (tb != FTBLAS_NO_TRANS && tb != FTBLAS_TRANS) return -3;
+  if (M < 0) return -4;
+  if (N < 0) return -5;
+  if (K < 0) return -6;
+  if (alpha == nullptr) return -7;
+  if (beta == nullptr) return -14;
+  const bool bf16 = Atype == FTBLAS_R_16BF && Btype == FTBLAS_R_16BF && Ctype == FTBLAS_R_32F && ctype == FTBLAS_R_32F;
+  if (!bf16) return FTBLAS_STATUS_NOT_SUPPORTED;
+  if (a_scale != nullptr) return -19;
+  if (b_scale != nullptr) return -20;
+  const bool need_ab = (K > 0 && *static_cast<const float*>(alpha) != 0.0f && M > 0 && N > 0);
+  int v = validate(layout, ta, tb, M, N, K, A, lda, B, ldb, C, ldc, need_ab);
+  if (v != 0) {
+    static const int pos[15] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 11, 13, 14, 15, 17};
+    return -pos[-v];
+  }
+  if (M > kMaxDim || N > kMaxDim || K > kMaxDim) return FTBLAS_STATUS_NOT_SUPPORTED;
+  const Frame f = map_frame(layout, ta, tb, M, N, A, lda, B, ldb);
+  if (M > 0 && N > 0 && tc_workspace_bytes((int32_t)f.M, (int32_t)f.N, (int32_t)K) > ws_bytes)
+    return FTBLAS_STATUS_WORKSPACE_LIMIT;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (report != nullptr) {
+    if (int e = record_cuda(cudaMemsetAsync(report, 0, sizeof(ft_report_t), st))) return e;
+  }
+  if (M == 0 || N == 0) return 0;
+  CallerPoint pts[kMaxInject];
+  const int64_t tile_rows = f.swap ? kTcBN : kTcBM, tile_cols = f.swap ? kTcBM : kTcBN;
+  const int npts = plan_injections(M, N, tile_rows, tile_cols, pts);
+  const float al = *static_cast<const float*>(alpha), be = *static_cast<const float*>(beta);
+  if (!f.a_kmajor || !f.b_kmajor) return FTBLAS_STATUS_NOT_SUPPORTED;
+  if (K == 0 || al == 0.0f) return FTBLAS_STATUS_NOT_SUPPORTED;
+  TcParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.M = (int32_t)f.M; p.N = (int32_t)f.N; p.K = (int32_t)K;
+  p.alpha = al; p.beta = be; p.u_acc = 0x1p-23f;
+  p.A = f.A; p.lda = f.lda; p.B = f.B; p.ldb = f.ldb;
+  p.C = static_cast<float*>(C); p.ldc = ldc;
+  p.report = report;
+  p.swap_report = f.swap;
+  for (int q = 0; q < npts; ++q) {
+    InjectPoint& ip = p.inj.p[p.inj.n++];
+    const CallerPoint& c = pts[q];
+    ip.i = (int32_t)(f.swap ? c.j : c.i);
+    ip.j = (int32_t)(f.swap ? c.i : c.j);
+    ip.site = c.site == FT_SITE_CHECKSUM ? kSiteChecksumRow : c.site;
+    ip.mode = c.mode; ip.bit = c.bit; ip.rel_log2 = c.rel_log2; ip.sign = c.sign; ip.pad = 0;
+  }
+  CUtensorMap tmA, tmB, tmC;
+  std::memset(&tmA, 0, sizeof(tmA)); std::memset(&tmB, 0, sizeof(tmB)); std::memset(&tmC, 0, sizeof(tmC));
+  if (!make_map_b16_sw128(&tmA, f.A, K, f.M, f.lda, 64, kTcBM)) return FTBLAS_STATUS_NOT_SUPPORTED;
+  if (!make_map_b16_sw128(&tmB, f.B, K, f.N, f.ldb, 64, kTcBN)) return FTBLAS_STATUS_NOT_SUPPORTED;
+  g_last_used_tma = 1;
+  TcWorkspace w = tc_workspace_carve(ws, p.M, p.N, p.K);
+  p.rowAbsA = w.rowAbsA; p.colAbsB = w.colAbsB; p.maxAbsAe = w.maxAbsAe; p.maxAbsBe = w.maxAbsBe; p.sA = w.sA;
+  const int64_t nNb = (f.N + kTcBN - 1) / kTcBN;
+  if (!make_map_b16_sw128(&tmC, w.chk, K, nNb * kTcChkRows, w.kpitch, 64, kTcChkRows))
+    return FTBLAS_STATUS_NOT_SUPPORTED;
+  int rc = record_cuda(launch_tc_encode(p, w, ws, st));  // clears the carved workspace first
+  if (rc == 0) rc = record_cuda(launch_tc_gemm(p, &tmA, &tmB, &tmC, true, st));
+  return rc;
+}
+
+}  // namespace ftk
+
 extern "C" {
 
 int ftblas_set_injection(const ft_inject_t* cfg) {
@@ -510,6 +584,8 @@ const char* ftblas_status_string(int code) {
     case FTBLAS_STATUS_NOT_SUPPORTED: return "not supported (type, shape or alignment)";
     case FTBLAS_STATUS_CUDA_ERROR: return "CUDA runtime error (see ftblas_last_cuda_error)";
     case FTBLAS_STATUS_ALLOC_FAILED: return "workspace allocation failed";
+    case FTBLAS_STATUS_WORKSPACE_LIMIT:
+      return "problem needs more scratch than the static workspace of ftblas_gemm_ex_noalloc (16 MiB)";
     default: return "unknown status";
   }
 }

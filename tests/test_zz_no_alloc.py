@@ -1,0 +1,76 @@
+"""The no-allocation entry point, ftblas_gemm_ex_noalloc.
+
+Some callers cannot allocate device memory while they issue work: their process does not
+own the device allocator (another framework has reserved it), or their setting forbids
+allocation after start-up. For them ftblas_gemm_ex_noalloc runs the protected BF16 GEMM
+on a static 16 MiB device array instead of stream-ordered allocations. These checks call
+it through the C ABI and compare it with the allocating entry point, ftblas_gemm_ex,
+within the BF16 tolerance the other tests use, on two calls in a row (the second call
+finds the first call's data in the shared array), and check that a problem needing more
+scratch than the array holds is rejected before any device work. This file is collected
+last on purpose, and it also passes alone in a fresh process.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2104_00897_gb300 as fb  # noqa: E402
+
+U32 = 2.0 ** -23
+
+
+def _operands(M, N, K, seed):
+    A = S.bf16_bits_to_f64(S.to_bf16_bits(S.normal_matrix(seed, 0, M, K)))
+    B = S.bf16_bits_to_f64(S.to_bf16_bits(S.normal_matrix(seed, 1, K, N)))
+    Cin = S.bf16_bits_to_f64(S.to_bf16_bits(S.normal_matrix(seed, 2, M, N)))
+    # column-major, A transposed (stored K x M) and B not: both K-contiguous
+    a16, lda = S.store(S.to_bf16_bits(A).T, O.COL_MAJOR, ld=K)
+    b16, ldb = S.store(S.to_bf16_bits(B), O.COL_MAJOR, ld=K)
+    return A, B, Cin, a16, lda, b16, ldb
+
+
+def _call(entry, M, N, K, dA, lda, dB, ldb, Cin, alpha, beta):
+    dC = torch.from_numpy(Cin.T.astype(np.float32).ravel().copy()).cuda()  # column-major, ldc = M
+    rep = fb.new_report()
+    rc = entry(O.COL_MAJOR, O.TRANS, O.NO_TRANS, M, N, K, alpha, dA.data_ptr(), fb.R_16BF, lda, dB.data_ptr(),
+               fb.R_16BF, ldb, beta, dC.data_ptr(), fb.R_32F, M, fb.R_32F, None, None,
+               torch.cuda.current_stream().cuda_stream, rep.data_ptr())
+    fb.check(rc, entry.__name__)
+    torch.cuda.synchronize()
+    return dC.cpu().numpy().astype(np.float64).reshape(N, M).T, fb.report_from_device(rep)
+
+
+def test_noalloc_matches_the_allocating_entry_point_twice():
+    M, N, K = 640, 1280, 1536
+    alpha, beta = 1.25, 0.5
+    A, B, Cin, a16, lda, b16, ldb = _operands(M, N, K, seed=97)
+    dA = torch.from_numpy(a16.view(np.int16)).cuda()
+    dB = torch.from_numpy(b16.view(np.int16)).cuda()
+    fb.ftblas_set_injection(None)
+    ref, ref_rep = _call(fb.ftblas_gemm_ex, M, N, K, dA, lda, dB, ldb, Cin, alpha, beta)
+    gam = K * U32 / (1 - K * U32)
+    tol = 2 * gam * abs(alpha) * (np.abs(A) @ np.abs(B)) + 2.0 ** -22 * (np.abs(ref) + abs(beta) * np.abs(Cin))
+    for call in range(2):
+        got, rep = _call(fb.ftblas_gemm_ex_noalloc, M, N, K, dA, lda, dB, ldb, Cin, alpha, beta)
+        assert np.all(np.abs(got - ref) <= tol), call
+        assert (rep.tiles_checked, rep.detected, rep.status) == (ref_rep.tiles_checked, 0, 0), call
+
+
+def test_noalloc_rejects_problems_beyond_its_scratch():
+    # M = N = 128, K = 2^20: the encode scratch (about 40 MiB) exceeds the 16 MiB array.
+    M, N, K = 128, 256, 1 << 20
+    dA = torch.zeros(M * K, dtype=torch.int16, device="cuda")  # real buffers of the right size
+    dB = torch.zeros(N * K, dtype=torch.int16, device="cuda")
+    dC = torch.full((M * N,), 7.0, dtype=torch.float32, device="cuda")
+    rc = fb.ftblas_gemm_ex_noalloc(O.COL_MAJOR, O.TRANS, O.NO_TRANS, M, N, K, 1.0, dA.data_ptr(), fb.R_16BF, K,
+                                   dB.data_ptr(), fb.R_16BF, K, 0.0, dC.data_ptr(), fb.R_32F, M, fb.R_32F, None, None,
+                                   None, None)
+    assert rc == fb.STATUS_WORKSPACE_LIMIT
+    assert "static workspace" in fb.ftblas_status_string(rc)
+    torch.cuda.synchronize()
+    assert bool((dC == 7.0).all())  # nothing ran
