@@ -54,6 +54,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-second-engine", action="store_true")
+    ap.add_argument("--no-bf16", action="store_true", help="skip the BF16 tensor-core measurement")
+    ap.add_argument("--bf16-only", action="store_true",
+                    help="measure only the BF16 tensor-core form (for profiling); prints its own JSON line")
     return ap.parse_args()
 
 
@@ -163,6 +166,103 @@ def oracle_sample(n, A, B, Cin, n_tiles, seed_tiles=7):
     return 2.0 * len(tiles) * TILE * TILE * n, dt, O.num_threads()
 
 
+# ------------------------------------------------------------------ BF16 tensor-core form
+def run_bf16(args, dev, n, steps, warmup, fp64_tflops):
+    """The BF16 form (config 3): A, B N(0,1) with rows of A scaled by 2^u, u in [-8, 8],
+    FP32 accumulation on the tensor cores, FP32 C, FP64 checksum comparison. Reports FT and
+    unprotected TFLOP/s, the speedup over FP64 FT-DGEMM, the error against the FP64 product
+    on sampled rows, and the fraction of injected output errors 2^p |C| detected per p."""
+    import torch
+
+    import oracle as O
+    import paper_2104_00897_gb300 as fb
+    import synth as S
+
+    seed = SEED + 3
+    A = S.normal_matrix(seed, 0, n, n) * S.pow2_row_scales(seed, 5, n)[:, None]
+    B = S.normal_matrix(seed, 1, n, n)
+    abits = S.to_bf16_bits(A)
+    bbits = S.to_bf16_bits(B)
+    # column-major call with A transposed (stored K x M) and B not: both K-contiguous
+    dA = torch.from_numpy(np.ascontiguousarray(abits).view(np.int16).ravel()).to(dev)       # A^T col-major == A row-major
+    dB = torch.from_numpy(np.ascontiguousarray(bbits.T).view(np.int16).ravel()).to(dev)     # B col-major
+    dC = torch.zeros(n * n, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    flops = 2.0 * n ** 3
+
+    def call(protect, rep=None):
+        a = (O.COL_MAJOR, O.TRANS, O.NO_TRANS, n, n, n, 1.0, dA.data_ptr(), fb.R_16BF, n, dB.data_ptr(), fb.R_16BF, n,
+             0.0, dC.data_ptr(), fb.R_32F, n, fb.R_32F, None, None, st)
+        if protect:
+            fb.check(fb.ftblas_gemm_ex(*a, rep.data_ptr() if rep is not None else None), "ftblas_gemm_ex")
+        else:
+            fb.check(fb.ftblas_gemm_ex_noabft(*a), "ftblas_gemm_ex_noabft")
+
+    def timed(protect, inject):
+        if inject:
+            fb.ftblas_set_injection(fb.make_injection(seed=seed, site=fb.SITE_OUTPUT, mode=fb.MODE_ADD_REL, log2_lo=8,
+                                                      log2_hi=12, every_n_launches=1, errors_per_launch=1))
+        else:
+            fb.ftblas_set_injection(None)
+        reps = [fb.new_report(dev) for _ in range(steps)]
+        for _ in range(warmup):
+            call(protect)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for s_ in range(steps):
+            call(protect, reps[s_])
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        corr = sum(int(fb.report_from_device(r).corrected) for r in reps) if protect else 0
+        det = sum(int(fb.report_from_device(r).detected) for r in reps) if protect else 0
+        fb.ftblas_set_injection(None)
+        return ms, det, corr
+
+    ms_na, _, _ = timed(False, False)
+    ms_ft, det0, _ = timed(True, False)
+    ms_inj, det_inj, corr_inj = timed(True, True)
+    # accuracy against the FP64 product of the same BF16 values, on sampled rows
+    call(True)
+    torch.cuda.synchronize(dev)
+    rows = np.unique(S.randint(seed, 9, 4, 0, n - 1))
+    C = dC.view(n, n).t()[torch.as_tensor(rows, device=dev)].double().cpu().numpy()
+    A64 = S.bf16_bits_to_f64(abits[rows, :])
+    B64 = S.bf16_bits_to_f64(bbits)
+    ref = A64 @ B64
+    scale = np.abs(A64) @ np.abs(B64)
+    err_norm = float(np.max(np.abs(C - ref) / scale))
+    err_rel = float(np.median(np.abs(C - ref) / np.maximum(np.abs(ref), 1e-30)))
+    # detection map over p (config 3): one output error 2^p |C(i,j)| per launch at a seeded element
+    det_map = {}
+    for p in range(-20, 13, 2):
+        hits = 0
+        trials = 4
+        for t in range(trials):
+            fb.ftblas_set_injection(fb.make_injection(seed=seed + 1000 * p + t, site=fb.SITE_OUTPUT,
+                                                      mode=fb.MODE_ADD_REL, log2_lo=p, log2_hi=p, every_n_launches=1,
+                                                      errors_per_launch=1))
+            rep = fb.new_report(dev)
+            call(True, rep)
+            torch.cuda.synchronize(dev)
+            hits += int(fb.report_from_device(rep).corrected)
+        det_map[str(p)] = hits / trials
+    fb.ftblas_set_injection(None)
+    return {
+        "workload": f"ft_gemm_bf16_fp32acc_{n}x{n}x{n}, A rows scaled by 2^u (u in [-8, 8]), N(0,1)",
+        "ft_tflops": flops / ms_ft / 1e9, "ft_tflops_injected": flops / ms_inj / 1e9,
+        "noabft_tflops": flops / ms_na / 1e9,
+        "abft_overhead_pct": 100.0 * (ms_ft / ms_na - 1.0),
+        "speedup_over_fp64_ft": (flops / ms_ft / 1e9) / fp64_tflops if fp64_tflops else None,
+        "false_alarms_clean": det0, "injected": steps, "corrected": corr_inj, "detected": det_inj,
+        "error_vs_fp64": {"max_over_sum_abs_ab": err_norm, "median_rel": err_rel, "rows_sampled": int(len(rows)),
+                          "note": "C - (A B computed in binary64 from the same BF16 values)"},
+        "detection_map_rel_log2": det_map,
+        "threshold": "rigorous: gamma_K(2^-23) |alpha| (sum_k|A(i,k)|)(max_k sum_j|B(k,j)|) + 2^-23 (sum|C|)",
+    }
+
+
 # ------------------------------------------------------------------ reference arm (the oracle)
 def run_reference(args, rank, world):
     if rank != 0:
@@ -204,6 +304,10 @@ def run_ours(args, rank, world, dist):
     dev = torch.device("cuda", local)
     fb.load()
     n = args.size
+    if args.bf16_only:
+        if rank == 0:
+            print(json.dumps({"bf16": run_bf16(args, dev, n, args.steps, args.warmup, None)}), flush=True)
+        return 0
     flops_step = 2.0 * n * n * n
     A, B, Cin = gen_inputs(n, SEED + rank)
     dA = torch.from_numpy(A).to(dev)
@@ -341,6 +445,11 @@ def run_ours(args, rank, world, dist):
                "sample": f"16 seeded {TILE}x{TILE} output tiles of the {n}^3 problem (full K, checksums included), "
                          f"{dt:.1f} s"}
 
+    bf16 = None
+    if not args.no_bf16 and rank == 0:
+        fp64_ft = flops_step * args.steps / (results[args.engine]["ft_ms"] / 1e3) / 1e12
+        bf16 = run_bf16(args, dev, n, args.steps, args.warmup, fp64_ft)
+
     if rank != 0:
         return 0
     pk = peaks()
@@ -384,6 +493,7 @@ def run_ours(args, rank, world, dist):
                      "traffic": None, "peak_source": pk["alu_src"] if bound == "alu" else pk["tensor_src"],
                      "kernel": "dgemm_kernel (FT, " + args.engine + ")", "kernel_ms": kernel_ms},
         "cpu_baseline": cpu,
+        "bf16": bf16,
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clocks,

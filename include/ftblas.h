@@ -177,12 +177,15 @@ int ftblas_dgemm_host(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_tran
  * kernel frame (column-major: A transposed and B not; row-major: A not transposed and B
  * transposed), leading dimensions that are multiples of 8 elements and 16-byte aligned
  * base addresses; other combinations return FTBLAS_STATUS_NOT_SUPPORTED. Its threshold
- * assumes the tensor core accumulates in binary32 with unit roundoff 2^-23, its row
- * checksums are verified in every tile and its column checksums only in tiles with a row
- * mismatch (Section V.A); a located error is corrected by subtracting the row mismatch
+ * assumes the tensor core accumulates in binary32 with unit roundoff 2^-23 (measured on
+ * GB300: truncating accumulation). Protected tiles hold 128 x 240 outputs: B^r = [B, Be]
+ * (Section II.A) fills the 256-column MMA. Row checksums are verified in every tile and
+ * column checksums only in tiles with a row mismatch (Section V.A); when those flag no
+ * column (rows of very different scale) and beta == 0, the mismatching row is recomputed
+ * and compared element by element; a located error is corrected by subtracting the row mismatch
  * (Section VI.C), evaluated as C^r(i) - sum_{j' != j} C(i,j') so that a huge or
  * non-finite error does not cancel catastrophically. Workspace (about
- * 16*K*ceil(N/256)*2 + 8*K*ceil(M/128) bytes) is taken from the stream-ordered allocator
+ * 32*K*ceil(N/240) + 8*K*ceil(M/128) bytes) is taken from the stream-ordered allocator
  * and released on the same stream. */
 int ftblas_gemm_ex(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,
                    int64_t M, int64_t N, int64_t K, const void* alpha,
@@ -211,7 +214,7 @@ int ftblas_gemm_ex_noabft(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_
  * FTBLAS_R_32F) takes its encode scratch from one static device array of 16 MiB that
  * every GPU loading this library holds until the process exits; nothing else is
  * allocated (no cudaMalloc, cudaFree, stream-ordered or library allocation).
- *   - Size limit: problems whose scratch, about 32*K*ceil(N/256) + 8*K*ceil(M/128) +
+ *   - Size limit: problems whose scratch, about 32*K*ceil(N/240) + 8*K*ceil(M/128) +
  *     8*(M+N)*ceil(K/1024) bytes, exceeds 16 MiB are rejected with
  *     FTBLAS_STATUS_WORKSPACE_LIMIT before any device work (M = N = K = 8192 fits).
  *   - First call per device: it looks up the device address of the static array with

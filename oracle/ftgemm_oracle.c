@@ -490,10 +490,14 @@ static void ft_tile(const oracle_problem_t* p, int64_t tr, int64_t tc,
  *   - tau uses gamma_K(u_acc) for the product part, with sum_k |A(i,k)| sum_j |B(k,j)|
  *     bounded by (sum_k |A(i,k)|) (max_k sum_j |B(k,j)|) over the tile:
  *       row:    |alpha| P (gamma_K(u_acc) (2 + 2^-7) + 2^-20) + 2^-23 (sum_j |C| + |beta| sum_j |C_in|)
- *       column: |alpha| P (gamma_K(u_acc) + 2^-30) + 2^-23 (sum_i |C| + 34 |beta| sum_i |C_in|)
+ *       column: |alpha| P_c (gamma_K(u_acc) + gamma_K(2^-24) + 2^-22) + 2^-23 (sum_i |C| + 34 |beta| sum_i |C_in|),
+ *               P_c = sum_k (sum_{i in tile} |A(i,k)|) |B(k,j)| (exact: it is formed only in the
+ *               rare tiles with a row mismatch)
  *     (the row side's prediction is itself a binary32 product of A with B e split into
- *     three pieces; the column side's is formed in compensated arithmetic);
+ *     three pieces; the column side's is a binary32 dot product of the rounded e^T A with B);
  *   - column checksums are formed only when a row mismatches (Section V.A, lazy side);
+ *     when they flag no column and beta == 0, the mismatching row is recomputed and each
+ *     element compared with its own bound (locates errors in rows of small scale);
  *   - a located error is corrected by subtracting the row mismatch (Section VI.C),
  *     evaluated as C(i,j) = C^r(i) - sum_{j' != j} C(i,j') (equal in exact arithmetic,
  *     stable for huge or non-finite errors); the result is rounded to binary32. */
@@ -506,13 +510,14 @@ static void ft_tile_acc32(const oracle_problem_t* p, int64_t tr, int64_t tc,
   const int64_t nJ = (j0 + p->tile_n <= p->N) ? p->tile_n : p->N - j0;
   memset(res, 0, sizeof(*res));
   double* Ac = (double*)calloc((size_t)(K > 0 ? K : 1), sizeof(double));
+  double* Ac_abs = (double*)calloc((size_t)(K > 0 ? K : 1), sizeof(double));
   double* Br = (double*)calloc((size_t)(K > 0 ? K : 1), sizeof(double));
-  double maxAbsAe = 0.0, maxAbsBe = 0.0;
+  double maxAbsBe = 0.0;
   for (int64_t k = 0; k < K; ++k) {
     double s = 0.0, sa = 0.0;
     for (int64_t i = i0; i < i0 + nI; ++i) { double a = a_elem(p, i, k); s = s + a; sa = sa + fabs(a); }
     Ac[k] = s;
-    if (sa > maxAbsAe) maxAbsAe = sa;
+    Ac_abs[k] = sa;
     s = 0.0; sa = 0.0;
     for (int64_t j = j0; j < j0 + nJ; ++j) { double b = b_elem(p, k, j); s = s + b; sa = sa + fabs(b); }
     Br[k] = s;
@@ -540,6 +545,7 @@ static void ft_tile_acc32(const oracle_problem_t* p, int64_t tr, int64_t tc,
     }
   }
   const double gK = gamma_n((double)K * p->u_acc / 1.1102230246251565e-16);
+  const double g24 = gamma_n((double)K * 5.9604644775390625e-08 / 1.1102230246251565e-16);  /* gamma_K(2^-24) */
   /* Row side, every row. */
   int64_t nr = 0, fr = -1;
   double fr_delta = 0.0, fr_tau = 0.0, fr_pred = 0.0;
@@ -574,8 +580,8 @@ static void ft_tile_acc32(const oracle_problem_t* p, int64_t tr, int64_t tc,
   if (nr > 0) {
     for (int64_t jj = 0; jj < nJ; ++jj) {
       int64_t j = j0 + jj;
-      double dotp = 0.0, colAbsB = 0.0;
-      for (int64_t k = 0; k < K; ++k) { double b = b_elem(p, k, j); dotp = dotp + Ac[k] * b; colAbsB = colAbsB + fabs(b); }
+      double dotp = 0.0, P = 0.0;
+      for (int64_t k = 0; k < K; ++k) { double b = b_elem(p, k, j); dotp = dotp + Ac[k] * b; P = P + Ac_abs[k] * fabs(b); }
       double cin_sum = 0.0, Q = 0.0;
       if (p->beta != 0.0)
         for (int64_t ii = 0; ii < nI; ++ii) { double c = cin_elem(p, i0 + ii, j); cin_sum = cin_sum + c; Q = Q + fabs(c); }
@@ -583,8 +589,7 @@ static void ft_tile_acc32(const oracle_problem_t* p, int64_t tr, int64_t tc,
       if (p->beta != 0.0) Cc = Cc + p->beta * cin_sum;
       double Cc_ref = 0.0, R = 0.0;
       for (int64_t ii = 0; ii < nI; ++ii) { Cc_ref = Cc_ref + T[ii + jj * nI]; R = R + fabs(T[ii + jj * nI]); }
-      double P = colAbsB * maxAbsAe;
-      double tau = fabs(p->alpha) * P * (gK + 9.313225746154785e-10) +
+      double tau = fabs(p->alpha) * P * (gK + g24 + 2.384185791015625e-07) +
                    1.1920928955078125e-07 * (R + 34.0 * fabs(p->beta) * Q);
       double d = Cc_ref - Cc;
       if (!(fabs(d) <= tau) || isinf(d)) {
@@ -593,19 +598,49 @@ static void ft_tile_acc32(const oracle_problem_t* p, int64_t tr, int64_t tc,
       }
     }
   }
+  /* Row-recompute locator: one mismatching row and no mismatching column (the column
+   * checksums of a tile whose rows differ greatly in scale cannot resolve an error in a
+   * small row), beta == 0. Each element of that row is compared with its own recomputed
+   * value against |alpha| (gamma_K(u_acc) + 2^-30) sum_k |A(i,k)||B(k,j)| + 2^-23 |C(i,j)|. */
+  int64_t ne = 0, fe = -1;
+  const int recompute_row = (nr == 1 && nc == 0 && p->beta == 0.0);
+  if (recompute_row) {
+    int64_t i = i0 + fr;
+    for (int64_t jj = 0; jj < nJ; ++jj) {
+      int64_t j = j0 + jj;
+      double rec = 0.0, S = 0.0;
+      for (int64_t k = 0; k < K; ++k) {
+        double a = a_elem(p, i, k), b = b_elem(p, k, j);
+        rec = rec + a * b;
+        S = S + fabs(a) * fabs(b);
+      }
+      rec = p->alpha * rec;
+      double cij = T[fr + jj * nI];
+      double te = fabs(p->alpha) * S * (gK + g24 + 9.313225746154785e-10) + 1.1920928955078125e-07 * fabs(cij);
+      double d = cij - rec;
+      if (!(fabs(d) <= te) || isinf(d)) {
+        if (fe < 0) fe = jj;
+        ++ne;
+      }
+    }
+  }
+  int64_t located = -1;
+  if (nr == 1 && nc == 1) located = fc;
+  else if (recompute_row && ne == 1) located = fe;
   oracle_record_t r;
   memset(&r, 0, sizeof(r));
   r.tile_row = tr; r.tile_col = tc;
   r.i = (fr >= 0) ? i0 + fr : -1;
-  r.j = (fc >= 0) ? j0 + fc : -1;
+  r.j = (fc >= 0) ? j0 + fc : (located >= 0 ? j0 + located : -1);
   r.delta_row = fr_delta; r.delta_col = fc_delta; r.tau_row = fr_tau; r.tau_col = fc_tau;
-  r.rows_flagged = (int32_t)nr; r.cols_flagged = (int32_t)nc;
+  r.rows_flagged = (int32_t)nr; r.cols_flagged = (int32_t)(nc > 0 ? nc : (recompute_row ? ne : 0));
   if (nr == 0) {
     /* clean */
-  } else if (nr == 1 && nc == 1) {
+  } else if (located >= 0) {
     res->detected = 1; res->corrected = 1;
     r.kind = OR_KIND_CORRECTED;
-    double before = T[fr + fc * nI];
+    const int64_t fcl = located;
+    double before = T[fr + fcl * nI];
     r.value_before = before;
     r.value_subtracted = before - fr_delta;
     /* C(i,j) - delta_row equals C^r(i) - sum_{j' != j} C(i,j') in exact arithmetic; the
@@ -613,12 +648,12 @@ static void ft_tile_acc32(const oracle_problem_t* p, int64_t tr, int64_t tc,
      * not cancel catastrophically. */
     double rest = 0.0;
     for (int64_t jj = 0; jj < nJ; ++jj)
-      if (jj != fc) rest = rest + T[fr + jj * nI];
+      if (jj != fcl) rest = rest + T[fr + jj * nI];
     double after = fr_pred - rest;
-    T[fr + fc * nI] = round32(after);
-    r.value_after = T[fr + fc * nI];
+    T[fr + fcl * nI] = round32(after);
+    r.value_after = T[fr + fcl * nI];
     add_record(res, &r);
-  } else if (nc == 0) {
+  } else if (nc == 0 && (!recompute_row || ne == 0)) {
     res->detected = 1; res->checksum_only = 1;
     r.kind = OR_KIND_CHECKSUM_ONLY;
     add_record(res, &r);
@@ -630,7 +665,7 @@ static void ft_tile_acc32(const oracle_problem_t* p, int64_t tr, int64_t tc,
   for (int64_t jj = 0; jj < nJ; ++jj)
     for (int64_t ii = 0; ii < nI; ++ii)
       Cout[c_index(p->layout, p->ldc, i0 + ii, j0 + jj)] = T[ii + jj * nI];
-  free(Ac); free(Br); free(T);
+  free(Ac); free(Ac_abs); free(Br); free(T);
 }
 
 /* ABFT-protected C = alpha*op(A)*op(B) + beta*C_in into Cout.

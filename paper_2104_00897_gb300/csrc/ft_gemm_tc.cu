@@ -5,23 +5,26 @@
 // of Section II.A, the lazy second side that of Section V.A, and C = beta*C is folded into
 // the checksums as in Section V.B.
 //
-// Structure (one 128 x 256 output tile per CTA, 192 threads):
-//   warp 0      TMA producer: A (128 x 64), B (256 x 64) and the checksum operand (16 x 64)
-//               k-tiles into a 4-stage ring, 128-byte swizzled, K-major;
-//   warp 1      TMEM allocation and MMA issue (one thread): per k-tile 4 x
-//               tcgen05.mma M128 N256 K16 into TMEM columns [0, 256) and, when protected,
-//               4 x M128 N16 K16 of A against the checksum operand into columns [256, 272):
-//               the row checksum C^r = A (B e) is produced by the tensor core itself;
-//   warps 2..5  epilogue, one TMEM lane (= output row) per thread: C = alpha acc + beta C_in,
-//               stored in FP32; the reference row checksum C^r_ref(i) = sum_j C(i,j) in
-//               compensated binary32; compared in binary64 with the predicted checksum;
-//               only when a row mismatches, the column checksums of the tile are formed
-//               (C^c_ref from the stored tile, C^c = (e^T A) B from global memory in
-//               compensated binary32) to locate the error, which is then corrected from
-//               the row checksum.
-// The checksum operand holds B e of the tile's 256 columns, split into three BF16 pieces
-// (hi, mid, lo), prepared by a bandwidth-bound pre-pass that also forms the magnitude
-// bounds for the threshold and e^T A per 128-row block for the column side.
+// Structure (persistent: one CTA of 192 threads per SM loops over output tiles; the
+// tensor-core tile is 128 x 256 and the TMEM accumulator is double-buffered):
+//   warp 0      TMA producer: A (128 x 64) and B (N_data x 64) k-tiles into a 4-stage ring,
+//               128-byte swizzled, K-major. Protected launches put the checksum column of
+//               B^r = [B, Be] (Section II.A) into rows 240..255 of the same B stage: Be over
+//               the tile's 240 data columns, split into three BF16 pieces (hi, mid, lo) by a
+//               bandwidth-bound encode pre-pass.
+//   warp 1      TMEM allocation and MMA issue (one thread): 4 x tcgen05.mma M128 N256 K16 per
+//               k-tile into one of two 256-column TMEM buffers, so the next tile's product
+//               overlaps the previous tile's epilogue. With the checksum column appended, the
+//               tensor core produces C^r = A (B e) in columns 240..242 with the product
+//               itself, at no extra instruction (6.7 % fewer data columns per tile).
+//   warps 2..5  epilogue, one TMEM lane (= output row) per thread: C = alpha acc + beta C_in
+//               stored in FP32; C^r_ref(i) = sum_j C(i,j) in compensated binary32, compared
+//               in binary64 with the predicted checksum against a rigorous bound. Only in a
+//               tile with a mismatching row are the column checksums formed (C^c_ref from
+//               the stored tile, C^c = (e^T A) B from global memory in binary32)
+//               to locate the error; when the columns cannot locate it (rows of very
+//               different scale), the mismatching row is recomputed and compared element by
+//               element. The located element is corrected from the row checksum.
 #include <climits>
 
 #include <cuda_bf16.h>
@@ -34,31 +37,36 @@ namespace ftk {
 
 namespace {
 
-constexpr int BM = kTcBM, BN = kTcBN, BKB = 128;  // BKB: k-tile depth in bytes (64 BF16)
+constexpr int BM = kTcBM;            // 128 tile rows (TMEM lanes)
+constexpr int BNM = 256;             // MMA N = TMEM columns = B stage rows
+constexpr int BKB = 128;             // k-tile depth in bytes (64 BF16)
 constexpr int STAGES = 4;
 constexpr int NTHREADS = 192;
-constexpr int CHK_ROWS = kTcChkRows;
-constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t kChkCol = 256;                  // TMEM column of the checksum accumulators
-constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per wait; a whole tile takes ~0.1 ms
+constexpr int CHK_ROWS = kTcChkRows;  // 16
+constexpr uint32_t TMEM_COLS = 512;   // two accumulator buffers of 256 columns
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait; a whole tile takes ~0.1 ms
+
+template <bool FT>
+struct TcGeom {
+  static constexpr int BN = FT ? kTcBNProt : BNM;  // data columns per tile
+};
 
 struct __align__(1024) TcSmem {
   uint8_t a[STAGES][BM * BKB];
-  uint8_t b[STAGES][BN * BKB];
-  uint8_t chk[STAGES][CHK_ROWS * BKB];
+  uint8_t b[STAGES][BNM * BKB];
   uint64_t full[STAGES];
   uint64_t empty[STAGES];
-  uint64_t accum;
+  uint64_t tfull[2];             // accumulator buffer b holds a finished tile
+  uint64_t tempty[2];            // accumulator buffer b has been read by the 4 epilogue warps
   uint32_t tmem_base;
   int timeout;
-  int nflag_rows, first_row, nflag_cols, first_col;
-  int nonfinite;
+  int nflag_rows, first_row, nflag_cols, first_col, nflag_elem, first_elem;
   double delta_row, tau_row, delta_col, tau_col;
   double pred_row;               // predicted row checksum of the first flagged row
-  float cin_col[4][BN];          // per-warp partial column sums of C_in (beta != 0)
-  float cin_col_abs[4][BN];
-  double col_delta[BN];          // lazy column side: C^c_ref - C^c and tau per column
-  double col_tau[BN];
+  float cin_col[4][BNM];         // per-warp partial column sums of C_in (beta != 0)
+  float cin_col_abs[4][BNM];
+  double col_delta[BNM];         // lazy column side: C^c_ref - C^c and tau per column
+  double col_tau[BNM];
 };
 
 __device__ __forceinline__ float bf16_to_f32(uint16_t b) { return __uint_as_float(static_cast<uint32_t>(b) << 16); }
@@ -70,46 +78,50 @@ __device__ __forceinline__ void neumaier(float& s, float& c, float x) {
   s = t;
 }
 
-// Error-free product a*b = p + e (binary32, via fused multiply-add).
-__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
-  p = a * b;
-  e = fmaf(a, b, -p);
+__device__ __forceinline__ double warp_sum_f64(double x) {
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) x += __shfl_xor_sync(0xffffffffu, x, w);
+  return x;
+}
+__device__ __forceinline__ float warp_sum_up(float x) {
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) x = __fadd_ru(x, __shfl_xor_sync(0xffffffffu, x, w));
+  return x;
 }
 
-// Warp transpose-reduction: lane l ends with sum over lanes of v[l] (31 shuffles).
-__device__ __forceinline__ float warp_column_sum(float (&v)[32], int lane) {
+__device__ __forceinline__ float warp_sum_plain(float x) {
 #pragma unroll
-  for (int w = 16; w >= 1; w >>= 1) {
-#pragma unroll
-    for (int i = 0; i < w; ++i) {
-      const bool up = (lane & w) != 0;
-      const float send = up ? v[i] : v[i + w];
-      const float keep = up ? v[i + w] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
-    }
-  }
-  return v[0];
+  for (int w = 16; w >= 1; w >>= 1) x += __shfl_xor_sync(0xffffffffu, x, w);
+  return x;
 }
-__device__ __forceinline__ float warp_column_sum_up(float (&v)[32], int lane) {
-#pragma unroll
-  for (int w = 16; w >= 1; w >>= 1) {
-#pragma unroll
-    for (int i = 0; i < w; ++i) {
-      const bool up = (lane & w) != 0;
-      const float send = up ? v[i] : v[i + w];
-      const float keep = up ? v[i + w] : v[i];
-      v[i] = __fadd_ru(keep, __shfl_xor_sync(0xffffffffu, send, w));
+
+// alpha * acc + beta * C_in with the accumulator- and output-site injections of the current
+// plan applied (test launches only; kept out of line).
+__device__ __noinline__ float inject_element(const TcParams& p, int64_t gi, int64_t gj, float acc, float cin,
+                                             bool beta_nz) {
+  for (int e = 0; e < p.inj.n; ++e) {
+    const InjectPoint& ip = p.inj.p[e];
+    if (ip.i == gi && ip.j == gj && ip.site == kSiteAccum && ip.mode == FT_MODE_BITFLIP)
+      acc = __uint_as_float(__float_as_uint(acc) ^ (1u << ip.bit));
+  }
+  float out = beta_nz ? fmaf(p.alpha, acc, p.beta * cin) : p.alpha * acc;
+  for (int e = 0; e < p.inj.n; ++e) {
+    const InjectPoint& ip = p.inj.p[e];
+    if (ip.i != gi || ip.j != gj || ip.site != kSiteOutput) continue;
+    if (ip.mode == FT_MODE_BITFLIP) {
+      out = __uint_as_float(__float_as_uint(out) ^ (1u << ip.bit));
+    } else {
+      const float em = ldexpf(fabsf(out), ip.rel_log2);
+      out = ip.sign < 0 ? out - em : out + em;
     }
   }
-  return v[0];
+  return out;
 }
 
 __device__ __forceinline__ float gamma32_up(float n, float u) {
   const float nu = __fmul_ru(n, u);
   return __fdiv_ru(nu, __fsub_rd(1.0f, nu));
 }
-
-__device__ __forceinline__ float ldg_bf16(const uint16_t* p, int64_t idx) { return bf16_to_f32(p[idx]); }
 
 __device__ void tc_record(const TcParams& p, int kind, int64_t tr, int64_t tc, int64_t i, int64_t j, double drow,
                           double dcol, double trow, double tcol, double before, double after, int nr, int nc) {
@@ -135,23 +147,38 @@ __device__ void tc_record(const TcParams& p, int kind, int64_t tr, int64_t tc, i
   r.reserved = 0;
 }
 
+// Persistent-tile order: groups of kGroupM row tiles sweep all column tiles, so the CTAs
+// resident at one time share A row panels and B column panels in L2.
+constexpr int kGroupM = 16;
+__device__ __forceinline__ void tile_coords(int t, int nMb, int nNb, int& mt, int& nt) {
+  const int group = t / (kGroupM * nNb);
+  const int first_m = group * kGroupM;
+  const int gsize = min(kGroupM, nMb - first_m);
+  const int in_group = t - group * kGroupM * nNb;
+  mt = first_m + in_group % gsize;
+  nt = in_group / gsize;
+}
+
+// Persistent kernel: one CTA per SM loops over output tiles. The TMEM accumulator is double
+// buffered (2 x 256 columns): while the epilogue warps verify and store tile t from one
+// buffer, the MMA warp accumulates tile t+1 into the other.
 template <bool FT>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmChk, const __grid_constant__ TcParams p) {
+  constexpr int BN = TcGeom<FT>::BN;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TcSmem& sm = *reinterpret_cast<TcSmem*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int nI = min(BM, p.M - m0), nJ = min(BN, p.N - n0);
   const int bk_elems = BKB / 2;
   const int nk = (p.K + bk_elems - 1) / bk_elems;
+  const int nMb = (p.M + BM - 1) / BM, nNb = (p.N + BN - 1) / BN;
+  const int ntiles = nMb * nNb;
 
   if (t == 0) {
     for (int s = 0; s < STAGES; ++s) { mbar_init(&sm.full[s], 1); mbar_init(&sm.empty[s], 1); }
-    mbar_init(&sm.accum, 1);
-    sm.timeout = 0; sm.nflag_rows = 0; sm.first_row = INT_MAX; sm.nflag_cols = 0; sm.first_col = INT_MAX;
-    sm.nonfinite = 0;
+    for (int b = 0; b < 2; ++b) { mbar_init(&sm.tfull[b], 1); mbar_init(&sm.tempty[b], 4); }
+    sm.timeout = 0;
     fence_mbar_init();
   }
   if (warp == 1) {
@@ -170,119 +197,132 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tma_prefetch_desc(&tmB);
       if (FT) tma_prefetch_desc(&tmChk);
       const uint32_t bytes = (BM + BN + (FT ? CHK_ROWS : 0)) * BKB;
-      for (int kt = 0; kt < nk; ++kt) {
-        const int s = kt % STAGES, u = kt / STAGES;
-        if (u > 0 && !mbar_wait_bounded(&sm.empty[s], (u - 1) & 1, kWaitLimitNs)) { sm.timeout = 1; break; }
-        mbar_arrive_expect_tx(&sm.full[s], bytes);
-        const int k0 = kt * bk_elems;
-        tma_load_2d(sm.a[s], &tmA, &sm.full[s], k0, m0);
-        tma_load_2d(sm.b[s], &tmB, &sm.full[s], k0, n0);
-        if (FT) tma_load_2d(sm.chk[s], &tmChk, &sm.full[s], k0, blockIdx.y * CHK_ROWS);
+      uint32_t it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        int mt, nt;
+        tile_coords(tile, nMb, nNb, mt, nt);
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const uint32_t s = it % STAGES, u = it / STAGES;
+          if (u > 0 && !mbar_wait_bounded(&sm.empty[s], (u - 1) & 1, kWaitLimitNs)) { sm.timeout = 1; ok = false; break; }
+          mbar_arrive_expect_tx(&sm.full[s], bytes);
+          const int k0 = kt * bk_elems;
+          tma_load_2d(sm.a[s], &tmA, &sm.full[s], k0, mt * BM);
+          tma_load_2d(sm.b[s], &tmB, &sm.full[s], k0, nt * BN);
+          if (FT) tma_load_2d(sm.b[s] + BN * BKB, &tmChk, &sm.full[s], k0, nt * CHK_ROWS);
+        }
       }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
-      const uint32_t idesc = umma_idesc(1, 1, BM, BN);
-      const uint32_t idesc_chk = umma_idesc(1, 1, BM, CHK_ROWS);
-      int kt = 0;
-      for (; kt < nk; ++kt) {
-        const int s = kt % STAGES, u = kt / STAGES;
-        if (!mbar_wait_bounded(&sm.full[s], u & 1, kWaitLimitNs)) { sm.timeout = 1; break; }
+      const uint32_t idesc = umma_idesc(1, 1, BM, BNM);
+      uint32_t it = 0, lt = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
+        const uint32_t b = lt & 1, ub = lt >> 1;
+        if (ub > 0 && !mbar_wait_bounded(&sm.tempty[b], (ub - 1) & 1, kWaitLimitNs)) { sm.timeout = 1; break; }
         tc_fence_after();
-        const uint32_t a0 = smem_addr(sm.a[s]), b0 = smem_addr(sm.b[s]), c0 = smem_addr(sm.chk[s]);
+        const uint32_t dcol = tmem + b * BNM;
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const uint32_t s = it % STAGES, u = it / STAGES;
+          if (!mbar_wait_bounded(&sm.full[s], u & 1, kWaitLimitNs)) { sm.timeout = 1; ok = false; break; }
+          tc_fence_after();
+          const uint32_t a0 = smem_addr(sm.a[s]), b0 = smem_addr(sm.b[s]);
 #pragma unroll
-        for (int kk = 0; kk < BKB / 32; ++kk) {
-          const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
-          const uint64_t ad = umma_desc_sw128(a0 + kk * 32);
-          umma_bf16(tmem, ad, umma_desc_sw128(b0 + kk * 32), idesc, acc);
-          if (FT) umma_bf16(tmem + kChkCol, ad, umma_desc_sw128(c0 + kk * 32), idesc_chk, acc);
+          for (int kk = 0; kk < BKB / 32; ++kk)
+            umma_bf16(dcol, umma_desc_sw128(a0 + kk * 32), umma_desc_sw128(b0 + kk * 32), idesc,
+                      (kt > 0 || kk > 0) ? 1u : 0u);
+          umma_commit(&sm.empty[s]);
         }
-        umma_commit(&sm.empty[s]);
+        umma_commit(&sm.tfull[b]);
       }
-      umma_commit(&sm.accum);
     }
   } else {
     // ------------------------------------------------------------ epilogue (warps 2..5)
     const int q = warp & 3;                 // TMEM lane quarter of this warp
     const int row = q * 32 + lane;          // tile row = TMEM lane
-    const int64_t gi = m0 + row;
-    const bool row_ok = row < nI;
     const int ew = warp - 2;                // epilogue warp index 0..3
-    const uint32_t trow = tmem + (static_cast<uint32_t>(q * 32) << 16);
-    // tcgen05.ld is warp-collective (.sync.aligned): every TMEM load below is executed by all
-    // 32 lanes of the warp, whatever their row; `got` is made warp-uniform for that reason.
-    const bool got = __all_sync(0xffffffffu, mbar_wait_bounded(&sm.accum, 0, kWaitLimitNs));
-    if (!got) sm.timeout = 1;
-    tc_fence_after();
+    const int et = t - 64;                  // epilogue thread index 0..127
     const bool beta_nz = p.beta != 0.0f;
-    float rs = 0.f, rc = 0.f, rabs = 0.f;   // compensated sum of C over the row, upward |C| sum
-    float cs = 0.f, cc = 0.f, cabs = 0.f;   // same for C_in
-    if (got) {
-      for (int ch = 0; ch < BN / 32; ++ch) {
-        uint32_t v[32];
-        __syncwarp();  // reconverge after the previous chunk's per-lane branches
-        tmem_ld32(trow + ch * 32, v);
-        tmem_ld_wait();
-        float cinv[32];
+    uint32_t lt = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+      int mt, nt;
+      tile_coords(tile, nMb, nNb, mt, nt);
+      const int m0 = mt * BM, n0 = nt * BN;
+      const int nI = min(BM, p.M - m0), nJ = min(BN, p.N - n0);
+      const int64_t gi = m0 + row;
+      const bool row_ok = row < nI;
+      const uint32_t b = lt & 1, ub = lt >> 1;
+      // tcgen05.ld is warp-collective (.sync.aligned): every TMEM load below is executed by
+      // all 32 lanes of the warp, whatever their row; `got` is made warp-uniform for that.
+      const bool got = __all_sync(0xffffffffu, mbar_wait_bounded(&sm.tfull[b], ub & 1, kWaitLimitNs));
+      if (!got) sm.timeout = 1;
+      tc_fence_after();
+      const uint32_t trow = tmem + b * BNM + (static_cast<uint32_t>(q * 32) << 16);
+      float rs = 0.f, rc = 0.f, rabs = 0.f;   // compensated sum of C over the row, upward |C| sum
+      float cs = 0.f, cc = 0.f, cabs = 0.f;   // same for C_in
+      uint32_t w4[4] = {0u, 0u, 0u, 0u};
+      // Injection points in this tile (test launches only): the per-element injection code
+      // is kept out of the hot loop so the epilogue stays small in the instruction cache,
+      // which it shares with the producer and MMA warps.
+      bool tile_inj = false;
+      if (FT)
+        for (int e = 0; e < p.inj.n; ++e)
+          tile_inj |= p.inj.p[e].i >= m0 && p.inj.p[e].i < m0 + nI && p.inj.p[e].j >= n0 && p.inj.p[e].j < n0 + nJ;
+      if (got) {
+#pragma unroll 1
+        for (int ch = 0; ch < (BN + 7) / 8; ++ch) {
+          uint32_t v[8];
+          __syncwarp();  // reconverge after the previous chunk's per-lane branches
+          tmem_ld8(trow + ch * 8, v);
+          tmem_ld_wait();
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = ch * 32 + j;
-          const int64_t gj = n0 + col;
-          const bool ok = row_ok && col < nJ;
-          float acc = __uint_as_float(v[j]);
-          float cin = 0.f;
-          if (beta_nz && ok) cin = p.C[gi + gj * p.ldc];
-          if (FT && p.inj.n > 0) {
-            for (int e = 0; e < p.inj.n; ++e) {
-              const InjectPoint& ip = p.inj.p[e];
-              if (ip.i == gi && ip.j == gj && ip.site == kSiteAccum && ip.mode == FT_MODE_BITFLIP)
-                acc = __uint_as_float(__float_as_uint(acc) ^ (1u << ip.bit));
-            }
-          }
-          float out = beta_nz ? fmaf(p.alpha, acc, p.beta * cin) : p.alpha * acc;
-          if (FT && p.inj.n > 0) {
-            for (int e = 0; e < p.inj.n; ++e) {
-              const InjectPoint& ip = p.inj.p[e];
-              if (ip.i != gi || ip.j != gj || ip.site != kSiteOutput) continue;
-              if (ip.mode == FT_MODE_BITFLIP) out = __uint_as_float(__float_as_uint(out) ^ (1u << ip.bit));
-              else {
-                const float em = ldexpf(fabsf(out), ip.rel_log2);
-                out = ip.sign < 0 ? out - em : out + em;
+          for (int j = 0; j < 8; ++j) {
+            const int col = ch * 8 + j;
+            const int64_t gj = n0 + col;
+            const bool ok = row_ok && col < nJ;
+            float acc = __uint_as_float(v[j]);
+            float cin = 0.f;
+            if (beta_nz && ok) cin = p.C[gi + gj * p.ldc];
+            float out;
+            if (FT && tile_inj) out = inject_element(p, gi, gj, acc, cin, beta_nz);
+            else out = beta_nz ? fmaf(p.alpha, acc, p.beta * cin) : p.alpha * acc;
+            if (ok) p.C[gi + gj * p.ldc] = out;
+            if (FT) {
+              const float o = ok ? out : 0.f;
+              neumaier(rs, rc, o);
+              rabs = __fadd_ru(rabs, fabsf(o));
+              if (beta_nz) {
+                neumaier(cs, cc, cin);
+                cabs = __fadd_ru(cabs, fabsf(cin));
+                // column sums of C_in over this warp's 32 rows, for the lazy column side
+                const float csum = warp_sum_plain(ok ? cin : 0.f);
+                const float cabsum = warp_sum_up(fabsf(ok ? cin : 0.f));
+                if (lane == 0 && col < BNM) { sm.cin_col[ew][col] = csum; sm.cin_col_abs[ew][col] = cabsum; }
               }
             }
           }
-          if (ok) p.C[gi + gj * p.ldc] = out;
-          if (FT) {
-            const float o = ok ? out : 0.f;
-            neumaier(rs, rc, o);
-            rabs = __fadd_ru(rabs, fabsf(o));
-            if (beta_nz) { neumaier(cs, cc, cin); cabs = __fadd_ru(cabs, fabsf(cin)); }
-          }
-          cinv[j] = cin;
         }
-        if (FT && beta_nz) {
-          // per-warp column sums of C_in for the lazy column side
-          float w1[32], w2[32];
-#pragma unroll
-          for (int j = 0; j < 32; ++j) { w1[j] = cinv[j]; w2[j] = fabsf(cinv[j]); }
-          const float colsum = warp_column_sum(w1, lane);
-          const float colabs = warp_column_sum_up(w2, lane);
-          sm.cin_col[ew][ch * 32 + lane] = colsum;
-          sm.cin_col_abs[ew][ch * 32 + lane] = colabs;
+        if (FT) {
+          __syncwarp();
+          tmem_ld4(trow + BN, w4);  // C^r pieces from the checksum column of B^r
+          tmem_ld_wait();
         }
       }
-    }
-    if (FT) {
+      // The accumulator buffer is free for the MMA warp's next-but-one tile.
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.tempty[b]);
+      if (!FT) continue;
+
       // -------------------------------------------------------- row verification
-      double delta = 0.0, tau = 0.0, predicted = 0.0;
-      bool flagged = false;
-      uint32_t w4[4] = {0u, 0u, 0u, 0u};
-      if (got) {  // warp-uniform
-        __syncwarp();
-        tmem_ld4(trow + kChkCol, w4);
-        tmem_ld_wait();
+      if (et == 0) {
+        sm.nflag_rows = 0; sm.first_row = INT_MAX; sm.nflag_cols = 0; sm.first_col = INT_MAX;
+        sm.nflag_elem = 0; sm.first_elem = INT_MAX;
       }
+      named_bar(1, 128);
+      double delta = 0.0, tau = 0.0, predicted = 0.0;
       if (got && row_ok) {
         const double pr = (double)__uint_as_float(w4[0]) + (double)__uint_as_float(w4[1]) +
                           (double)__uint_as_float(w4[2]);
@@ -299,13 +339,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         delta = ref - predicted;
         // tau = |alpha| P (gamma_K(u_acc) (2 + 2^-7) + 2^-20) + 2 u32 (sum|C| + |beta| sum|C_in|), P an
         // upper bound of sum_k |A(i,k)| sum_{j in tile} |B(k,j)|.
-        const float P = __fmul_ru(p.rowAbsA[gi], p.maxAbsBe[blockIdx.y]);
+        const float P = __fmul_ru(p.rowAbsA[gi], p.maxAbsBe[nt]);
         const float g = gamma32_up((float)p.K, p.u_acc);
         const float prod = __fmul_ru(__fmul_ru(fabsf(p.alpha), P), __fadd_ru(__fmul_ru(g, 2.0078125f), 0x1p-20f));
         const float outp = __fmul_ru(0x1p-23f, __fadd_ru(rabs, __fmul_ru(fabsf(p.beta), cabs)));
         tau = (double)__fadd_ru(prod, outp);
-        flagged = !(fabs(delta) <= tau) || isinf(delta);
-        if (flagged) {
+        if (!(fabs(delta) <= tau) || isinf(delta)) {
           atomicAdd(&sm.nflag_rows, 1);
           atomicMin(&sm.first_row, row);
         }
@@ -315,64 +354,127 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       __threadfence_block();
       named_bar(1, 128);
       const int nr = sm.nflag_rows;
-      const int64_t trr = blockIdx.x, tcc = blockIdx.y;
       if (nr > 0) {
         // ------------------------------------------------------ lazy column side (Section V.A)
-        for (int cidx = t - 64; cidx < BN; cidx += 128) {
-          if (cidx >= nJ) continue;
+        // Each warp takes columns ew, ew + 4, ...; its lanes split the rows (C^c_ref) and K
+        // (C^c = alpha (e^T A) B(:, j), compensated); partial results are summed in binary64.
+        const uint16_t* Bp = static_cast<const uint16_t*>(p.B);
+        const float2* sAI = p.sA + (int64_t)mt * p.K;
+        const float* absAI = p.absSA + (int64_t)mt * p.K;
+        const float g = gamma32_up((float)p.K, p.u_acc);
+        const float g24 = gamma32_up((float)p.K, 0x1p-24f);
+        for (int cidx = ew; cidx < nJ; cidx += 4) {
           const int64_t gj = n0 + cidx;
           float s = 0.f, c = 0.f, a = 0.f;
-          for (int i = 0; i < nI; ++i) {
+          for (int i = lane; i < nI; i += 32) {
             const float x = p.C[(int64_t)(m0 + i) + gj * p.ldc];
             neumaier(s, c, x);
             a = __fadd_ru(a, fabsf(x));
           }
-          // C^c(j) = alpha sum_k (e^T A)(k) B(k, j): compensated dot product (Dot2).
-          const uint16_t* bcol = static_cast<const uint16_t*>(p.B) + gj * p.ldb;
-          float ds = 0.f, dc = 0.f;
-          for (int k = 0; k < p.K; ++k) {
-            const float2 sa = p.sA[(int64_t)blockIdx.x * p.K + k];
-            const float b = ldg_bf16(bcol, k);
-            float p1, e1, p2, e2;
-            two_prod(sa.x, b, p1, e1);
-            two_prod(sa.y, b, p2, e2);
-            neumaier(ds, dc, p1);
-            dc += e1 + p2 + e2;
+          const double cref = warp_sum_f64((double)s + (double)c);
+          const float cref_abs = warp_sum_up(a);
+          // binary32 dot products with two independent accumulators (their rounding enters
+          // the threshold as gamma_K(2^-24) P_c, next to the accumulation's gamma_K(u_acc) P_c)
+          const uint16_t* bcol = Bp + gj * p.ldb;
+          float d0 = 0.f, d1 = 0.f, pc0 = 0.f, pc1 = 0.f;
+          int k = lane;
+          for (; k + 32 < p.K; k += 64) {
+            const float b0 = bf16_to_f32(bcol[k]), b1 = bf16_to_f32(bcol[k + 32]);
+            d0 = fmaf(sAI[k].x, b0, d0);
+            d1 = fmaf(sAI[k + 32].x, b1, d1);
+            pc0 = __fmaf_ru(absAI[k], fabsf(b0), pc0);  // sum_k (sum_i |A(i,k)|) |B(k,j)|, upward
+            pc1 = __fmaf_ru(absAI[k + 32], fabsf(b1), pc1);
           }
-          double cpred = (double)p.alpha * ((double)ds + (double)dc);
+          if (k < p.K) {
+            const float b0 = bf16_to_f32(bcol[k]);
+            d0 = fmaf(sAI[k].x, b0, d0);
+            pc0 = __fmaf_ru(absAI[k], fabsf(b0), pc0);
+          }
+          double cpred = (double)p.alpha * warp_sum_f64((double)d0 + (double)d1);
+          const float Pc = warp_sum_up(__fadd_ru(pc0, pc1));
           float cin_abs = 0.f;
           if (beta_nz) {
             double cin_sum = 0.0;
             for (int w = 0; w < 4; ++w) { cin_sum += (double)sm.cin_col[w][cidx]; cin_abs = __fadd_ru(cin_abs, sm.cin_col_abs[w][cidx]); }
             cpred += (double)p.beta * cin_sum;
           }
-          const double dcol = ((double)s + (double)c) - cpred;
-          const float P = __fmul_ru(p.colAbsB[gj], p.maxAbsAe[blockIdx.x]);
-          const float g = gamma32_up((float)p.K, p.u_acc);
-          // C^c is formed in compensated arithmetic here; the C^c_ref side carries the
-          // accumulation error, the partial C_in sums carry gamma_31 (binary32).
-          const float prod = __fmul_ru(__fmul_ru(fabsf(p.alpha), P), __fadd_ru(g, 0x1p-30f));
-          const float outp = __fmul_ru(0x1p-23f, __fadd_ru(a, __fmul_ru(__fmul_ru(fabsf(p.beta), cin_abs), 34.0f)));
-          const double tauc = (double)__fadd_ru(prod, outp);
-          const bool fl = !(fabs(dcol) <= tauc) || isinf(dcol);
-          sm.col_delta[cidx] = dcol;
-          sm.col_tau[cidx] = tauc;
-          if (fl) {
-            atomicAdd(&sm.nflag_cols, 1);
-            atomicMin(&sm.first_col, cidx);
+          if (lane == 0) {
+            const double dcol = cref - cpred;
+            // C^c_ref carries the accumulation error gamma_K(u_acc) P_c; C^c (binary32 dot of
+            // the rounded e^T A with B) adds gamma_K(2^-24) P_c + 2^-23 P_c; the per-warp C_in
+            // partial sums carry gamma_31 (binary32).
+            const float prod = __fmul_ru(__fmul_ru(fabsf(p.alpha), Pc), __fadd_ru(__fadd_ru(g, g24), 0x1p-22f));
+            const float outp =
+                __fmul_ru(0x1p-23f, __fadd_ru(cref_abs, __fmul_ru(__fmul_ru(fabsf(p.beta), cin_abs), 34.0f)));
+            const double tauc = (double)__fadd_ru(prod, outp);
+            sm.col_delta[cidx] = dcol;
+            sm.col_tau[cidx] = tauc;
+            if (!(fabs(dcol) <= tauc) || isinf(dcol)) {
+              atomicAdd(&sm.nflag_cols, 1);
+              atomicMin(&sm.first_col, cidx);
+            }
           }
         }
         __threadfence_block();
         named_bar(1, 128);
-        if (sm.first_col < BN) { sm.delta_col = sm.col_delta[sm.first_col]; sm.tau_col = sm.col_tau[sm.first_col]; }
         const int nc = sm.nflag_cols;
-        if (t == 64) {
+        if (nc > 0 && et == 0) { sm.delta_col = sm.col_delta[sm.first_col]; sm.tau_col = sm.col_tau[sm.first_col]; }
+        // ------------------------------------------------------ row-recompute locator
+        // One mismatching row and no mismatching column: the column checksums of a tile
+        // whose rows differ greatly in scale cannot resolve an error in a small row. Then
+        // recompute that row and compare each element with its own bound
+        // |alpha| (gamma_K(u_acc) + gamma_K(2^-24) + 2^-30) sum_k |A(i,k)||B(k,j)| + 2^-23 |C(i,j)|.
+        const bool recompute_row = (nr == 1 && nc == 0 && !beta_nz);
+        if (recompute_row) {
+          const int64_t gr = m0 + sm.first_row;
+          const uint16_t* arow = static_cast<const uint16_t*>(p.A) + gr * p.lda;
+          for (int cidx = ew; cidx < nJ; cidx += 4) {
+            const int64_t gj = n0 + cidx;
+            const uint16_t* bcol = Bp + gj * p.ldb;
+            float d0 = 0.f, d1 = 0.f, s0 = 0.f, s1 = 0.f;
+            int k = lane;
+            for (; k + 32 < p.K; k += 64) {
+              const float a0 = bf16_to_f32(arow[k]), b0 = bf16_to_f32(bcol[k]);
+              const float a1 = bf16_to_f32(arow[k + 32]), b1 = bf16_to_f32(bcol[k + 32]);
+              d0 = fmaf(a0, b0, d0);
+              d1 = fmaf(a1, b1, d1);
+              s0 = __fmaf_ru(fabsf(a0), fabsf(b0), s0);
+              s1 = __fmaf_ru(fabsf(a1), fabsf(b1), s1);
+            }
+            if (k < p.K) {
+              const float a0 = bf16_to_f32(arow[k]), b0 = bf16_to_f32(bcol[k]);
+              d0 = fmaf(a0, b0, d0);
+              s0 = __fmaf_ru(fabsf(a0), fabsf(b0), s0);
+            }
+            const double rec = (double)p.alpha * warp_sum_f64((double)d0 + (double)d1);
+            const float S = warp_sum_up(__fadd_ru(s0, s1));
+            if (lane == 0) {
+              const double cij = (double)p.C[gr + gj * p.ldc];
+              // the recomputation is a binary32 dot product: its rounding, gamma_K(2^-24) S,
+              // joins the accumulation's gamma_K(u_acc) S
+              const float te = __fadd_ru(__fmul_ru(__fmul_ru(fabsf(p.alpha), S), __fadd_ru(__fadd_ru(g, g24), 0x1p-30f)),
+                                         __fmul_ru(0x1p-23f, (float)fabs(cij)));
+              const double d = cij - rec;
+              if (!(fabs(d) <= (double)te) || isinf(d)) {
+                atomicAdd(&sm.nflag_elem, 1);
+                atomicMin(&sm.first_elem, cidx);
+              }
+            }
+          }
+          __threadfence_block();
+          named_bar(1, 128);
+        }
+        if (et == 0) {
           int kind;
           double before = 0.0, after = 0.0;
-          int64_t gi2 = nr > 0 ? m0 + sm.first_row : -1;
-          int64_t gj2 = nc > 0 ? n0 + sm.first_col : -1;
-          if (nr == 1 && nc == 1) {
+          const int64_t gi2 = m0 + sm.first_row;
+          int located_col = -1;
+          if (nr == 1 && nc == 1) located_col = sm.first_col;
+          else if (recompute_row && sm.nflag_elem == 1) located_col = sm.first_elem;
+          int64_t gj2 = (nc > 0) ? n0 + sm.first_col : -1;
+          if (located_col >= 0) {
             kind = FT_KIND_CORRECTED;
+            gj2 = n0 + located_col;
             float* cp = p.C + gi2 + gj2 * p.ldc;
             before = (double)*cp;
             // The paper's correction, C(i,j) - delta_row, evaluated as
@@ -384,23 +486,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             after = sm.pred_row - rest;
             *cp = (float)after;
             after = (double)*cp;
-          } else if (nc == 0) {
+          } else if (nc == 0 && (!recompute_row || sm.nflag_elem == 0)) {
             kind = FT_KIND_CHECKSUM_ONLY;
           } else {
             kind = FT_KIND_UNCORRECTABLE;
           }
-          tc_record(p, kind, trr, tcc, gi2, gj2, sm.delta_row, nc > 0 ? sm.delta_col : 0.0, sm.tau_row,
-                    nc > 0 ? sm.tau_col : 0.0, before, after, nr, nc);
+          const int ncols_rep = nc > 0 ? nc : (recompute_row ? sm.nflag_elem : 0);
+          tc_record(p, kind, mt, nt, gi2, gj2, sm.delta_row, nc > 0 ? sm.delta_col : 0.0, sm.tau_row,
+                    nc > 0 ? sm.tau_col : 0.0, before, after, nr, ncols_rep);
           if (p.report) {
             atomicAdd(reinterpret_cast<unsigned long long*>(&p.report->detected), 1ull);
-            unsigned long long* ctr = (nr == 1 && nc == 1) ? reinterpret_cast<unsigned long long*>(&p.report->corrected)
-                                      : (nc == 0) ? reinterpret_cast<unsigned long long*>(&p.report->checksum_only)
-                                                  : reinterpret_cast<unsigned long long*>(&p.report->uncorrectable);
+            unsigned long long* ctr = (kind == FT_KIND_CORRECTED)
+                                          ? reinterpret_cast<unsigned long long*>(&p.report->corrected)
+                                      : (kind == FT_KIND_CHECKSUM_ONLY)
+                                          ? reinterpret_cast<unsigned long long*>(&p.report->checksum_only)
+                                          : reinterpret_cast<unsigned long long*>(&p.report->uncorrectable);
             atomicAdd(ctr, 1ull);
           }
         }
       }
-      if (t == 64 && p.report) atomicAdd(reinterpret_cast<unsigned long long*>(&p.report->tiles_checked), 1ull);
+      if (et == 0 && p.report) atomicAdd(reinterpret_cast<unsigned long long*>(&p.report->tiles_checked), 1ull);
+      named_bar(1, 128);  // every epilogue thread is done with this tile's shared state
     }
   }
 
@@ -417,75 +523,98 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 // ---------------------------------------------------------------------------------------
 // Encode pre-pass (bandwidth-bound). Kernel-frame A is M x K and B is K x N, both
-// K-contiguous (row i of A at A + i*lda, column j of B at B + j*ldb).
+// K-contiguous (row i of A at A + i*lda, column j of B at B + j*ldb). One thread per pair
+// of consecutive k; loads are 4-byte BF16 pairs, coalesced along k.
 // ---------------------------------------------------------------------------------------
+constexpr int ENC_KC = 512;   // k per CTA (256 threads x 2)
 
-// Per 128-row block I and 1024-wide k chunk: e^T A over the block for each k (as an
-// unevaluated hi + lo binary32 pair, compensated), the upward sum of |A| over the block
-// (max over k -> maxAbsAe[I]) and per-row upward partial sums of |A| over the chunk.
-constexpr int ENC_KC = 1024;
-
-__global__ void __launch_bounds__(256) encode_rows_kernel(const uint16_t* A, int64_t lda, int32_t M, int32_t K,
-                                                           float2* sA, float* rowAbsPart, float* maxAbsAe) {
-  const int I = blockIdx.x, kc = blockIdx.y;
-  const int m0 = I * BM, k0 = kc * ENC_KC;
-  const int nI = min(BM, M - m0), kn = min(ENC_KC, K - k0);
-  __shared__ float tile[BM][65];
-  float rowabs = 0.f;    // thread t < 128: row t
-  float colmax = 0.f;
-  for (int kb = 0; kb < kn; kb += 64) {
-    const int kw = min(64, kn - kb);
-    for (int idx = threadIdx.x; idx < BM * 64; idx += 256) {
-      const int r = idx / 64, kk = idx % 64;
-      tile[r][kk] = (r < nI && kk < kw) ? bf16_to_f32(A[(int64_t)(m0 + r) * lda + k0 + kb + kk]) : 0.f;
-    }
-    __syncthreads();
-    if (threadIdx.x < BM) {
-      for (int kk = 0; kk < 64; ++kk) rowabs = __fadd_ru(rowabs, fabsf(tile[threadIdx.x][kk]));
-    } else if (threadIdx.x < BM + 64) {
-      const int kk = threadIdx.x - BM;
-      if (kk < kw) {
-        float s = 0.f, c = 0.f, a = 0.f;
-        for (int r = 0; r < BM; ++r) { neumaier(s, c, tile[r][kk]); a = __fadd_ru(a, fabsf(tile[r][kk])); }
-        const float hi = s + c;
-        const float lo = c - (hi - s);
-        sA[(int64_t)I * K + k0 + kb + kk] = make_float2(hi, lo);
-        colmax = fmaxf(colmax, a);
-      }
-    }
-    __syncthreads();
+__device__ __forceinline__ void load_pair(const uint16_t* row, int64_t k, int32_t K, float& x0, float& x1) {
+  // k is even; the pair (k, k+1) is 4-byte aligned because leading dimensions are multiples
+  // of 8 elements and base addresses are 16-byte aligned.
+  if (k + 1 < K) {
+    const uint32_t w = *reinterpret_cast<const uint32_t*>(row + k);
+    x0 = __uint_as_float(w << 16);
+    x1 = __uint_as_float(w & 0xffff0000u);
+  } else {
+    x0 = (k < K) ? bf16_to_f32(row[k]) : 0.f;
+    x1 = 0.f;
   }
-  if (threadIdx.x < BM && threadIdx.x < nI) rowAbsPart[(int64_t)kc * M + m0 + threadIdx.x] = rowabs;
-  if (threadIdx.x >= BM && threadIdx.x < BM + 64)
-    atomicMax(reinterpret_cast<unsigned int*>(&maxAbsAe[I]), __float_as_uint(colmax));
 }
 
-// Per 256-column block J and k chunk: B e over the block for each k, split into three
-// BF16 pieces written to rows J*16 + {0, 1, 2} of the checksum operand (K-contiguous,
-// pitch kpitch); the upward |B| sum over the block (max over k -> maxAbsBe[J]); per-column
-// upward partial sums of |B| over the chunk.
-__global__ void __launch_bounds__(256) encode_cols_kernel(const uint16_t* B, int64_t ldb, int32_t N, int32_t K,
-                                                           uint16_t* chk, int64_t kpitch, float* colAbsPart,
-                                                           float* maxAbsBe) {
-  const int J = blockIdx.x, kc = blockIdx.y;
-  const int n0 = J * BN, k0 = kc * ENC_KC;
-  const int nJ = min(BN, N - n0), kn = min(ENC_KC, K - k0);
-  __shared__ float tile[BN][33];
-  float colabs = 0.f;  // thread t: column t (256 threads = 256 columns)
-  float kmax = 0.f;
-  for (int kb = 0; kb < kn; kb += 32) {
-    const int kw = min(32, kn - kb);
-    for (int idx = threadIdx.x; idx < BN * 32; idx += 256) {
-      const int c = idx / 32, kk = idx % 32;
-      tile[c][kk] = (c < nJ && kk < kw) ? bf16_to_f32(B[(int64_t)(n0 + c) * ldb + k0 + kb + kk]) : 0.f;
+// Per 128-row block I: e^T A over the block for each k (hi + lo binary32 pair,
+// compensated) and the upward sum of |A| over the block for each k. Streaming, one thread
+// per pair of k, no cross-thread reduction.
+__global__ void __launch_bounds__(256) encode_rows_kernel(const uint16_t* A, int64_t lda, int32_t M, int32_t K,
+                                                           float2* sA, float* absSA) {
+  const int I = blockIdx.x;
+  const int m0 = I * BM;
+  const int nI = min(BM, M - m0);
+  const int64_t k = (int64_t)blockIdx.y * ENC_KC + 2 * threadIdx.x;
+  if (k >= K) return;
+  float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, a0 = 0.f, a1 = 0.f;
+  for (int i = 0; i < nI; ++i) {
+    float x0, x1;
+    load_pair(A + (int64_t)(m0 + i) * lda, k, K, x0, x1);
+    neumaier(s0, c0, x0);
+    neumaier(s1, c1, x1);
+    a0 = __fadd_ru(a0, fabsf(x0));
+    a1 = __fadd_ru(a1, fabsf(x1));
+  }
+  float h = s0 + c0;
+  sA[(int64_t)I * K + k] = make_float2(h, c0 - (h - s0));
+  absSA[(int64_t)I * K + k] = a0;
+  if (k + 1 < K) {
+    h = s1 + c1;
+    sA[(int64_t)I * K + k + 1] = make_float2(h, c1 - (h - s1));
+    absSA[(int64_t)I * K + k + 1] = a1;
+  }
+}
+
+// Upward sum_k |A(i,k)| per row: one warp per row, 16-byte loads along the row.
+__global__ void __launch_bounds__(256) row_abs_kernel(const uint16_t* A, int64_t lda, int32_t M, int32_t K,
+                                                       float* rowAbsA) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+  if (i >= M) return;
+  const uint16_t* row = A + i * lda;
+  float a = 0.f;
+  const int K8 = K & ~7;
+  for (int k = lane * 8; k < K8; k += 256) {
+    const uint4 w = *reinterpret_cast<const uint4*>(row + k);  // rows are 16-byte aligned
+    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      a = __fadd_ru(a, fabsf(__uint_as_float(ws[h] << 16)));
+      a = __fadd_ru(a, fabsf(__uint_as_float(ws[h] & 0xffff0000u)));
     }
-    __syncthreads();
-    for (int kk = 0; kk < 32; ++kk) colabs = __fadd_ru(colabs, fabsf(tile[threadIdx.x][kk]));
-    if (threadIdx.x < 32 && threadIdx.x < kw) {
-      const int kk = threadIdx.x;
-      float s = 0.f, c = 0.f, a = 0.f;
-      for (int col = 0; col < BN; ++col) { neumaier(s, c, tile[col][kk]); a = __fadd_ru(a, fabsf(tile[col][kk])); }
-      // split s + c into three bfloat16 pieces, each the nearest bfloat16 of the remainder
+  }
+  for (int k = K8 + lane; k < K; k += 32) a = __fadd_ru(a, fabsf(bf16_to_f32(row[k])));
+  a = warp_sum_up(a);
+  if (lane == 0) rowAbsA[i] = a;
+}
+
+// Per block J of `bn` columns: B e over the block for each k, split into three BF16 pieces
+// written to rows J*16 + {0, 1, 2} of the checksum operand (K-contiguous, pitch kpitch),
+// and max_k of the upward |B| sum over the block (maxAbsBe[J]). Streaming, one thread per
+// pair of k.
+__global__ void __launch_bounds__(256) encode_cols_kernel(const uint16_t* B, int64_t ldb, int32_t N, int32_t K,
+                                                           int32_t bn, uint16_t* chk, int64_t kpitch, float* maxAbsBe) {
+  const int J = blockIdx.x;
+  const int n0 = J * bn;
+  const int nJ = min(bn, N - n0);
+  const int64_t k = (int64_t)blockIdx.y * ENC_KC + 2 * threadIdx.x;
+  float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, a0 = 0.f, a1 = 0.f;
+  if (k < K) {
+    for (int j = 0; j < nJ; ++j) {
+      float x0, x1;
+      load_pair(B + (int64_t)(n0 + j) * ldb, k, K, x0, x1);
+      neumaier(s0, c0, x0);
+      neumaier(s1, c1, x1);
+      a0 = __fadd_ru(a0, fabsf(x0));
+      a1 = __fadd_ru(a1, fabsf(x1));
+    }
+    auto split_store = [&](float s, float c, int64_t kk) {
+      // three bfloat16 pieces, each the nearest bfloat16 of the remainder of s + c
       const float x = s + c;
       const float xr = c - (x - s);
       const __nv_bfloat16 h = __float2bfloat16_rn(x);
@@ -493,39 +622,30 @@ __global__ void __launch_bounds__(256) encode_cols_kernel(const uint16_t* B, int
       const __nv_bfloat16 m = __float2bfloat16_rn(r1);
       const float r2 = r1 - __bfloat162float(m);
       const __nv_bfloat16 l = __float2bfloat16_rn(r2);
-      const int64_t k = k0 + kb + kk;
-      chk[(int64_t)(J * CHK_ROWS + 0) * kpitch + k] = __bfloat16_as_ushort(h);
-      chk[(int64_t)(J * CHK_ROWS + 1) * kpitch + k] = __bfloat16_as_ushort(m);
-      chk[(int64_t)(J * CHK_ROWS + 2) * kpitch + k] = __bfloat16_as_ushort(l);
-      kmax = fmaxf(kmax, a);
-    }
-    __syncthreads();
+      chk[(int64_t)(J * CHK_ROWS + 0) * kpitch + kk] = __bfloat16_as_ushort(h);
+      chk[(int64_t)(J * CHK_ROWS + 1) * kpitch + kk] = __bfloat16_as_ushort(m);
+      chk[(int64_t)(J * CHK_ROWS + 2) * kpitch + kk] = __bfloat16_as_ushort(l);
+    };
+    split_store(s0, c0, k);
+    if (k + 1 < K) split_store(s1, c1, k + 1);
   }
-  if (threadIdx.x < nJ) colAbsPart[(int64_t)kc * N + n0 + threadIdx.x] = colabs;
-  if (threadIdx.x < 32) atomicMax(reinterpret_cast<unsigned int*>(&maxAbsBe[J]), __float_as_uint(kmax));
-}
-
-// Upward sum of the per-chunk partials.
-__global__ void finalize_abs_kernel(const float* part, int nparts, int32_t n, float* out) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int c = 0; c < nparts; ++c) s = __fadd_ru(s, part[(int64_t)c * n + i]);
-    out[i] = s;
-  }
+  float mx = fmaxf(k < K ? a0 : 0.f, k + 1 < K ? a1 : 0.f);
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, w));
+  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned int*>(&maxAbsBe[J]), __float_as_uint(mx));
 }
 
 }  // namespace
 
 size_t tc_workspace_bytes(int32_t M, int32_t N, int32_t K) {
-  const int64_t nMb = (M + BM - 1) / BM, nNb = (N + BN - 1) / BN, nkc = (K + ENC_KC - 1) / ENC_KC;
+  const int64_t nMb = (M + BM - 1) / BM, nNb = (N + kTcBNProt - 1) / kTcBNProt;
   const int64_t kpitch = (K + 7) / 8 * 8;
   auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
-  return up(nNb * CHK_ROWS * kpitch * 2) + up(nMb * (int64_t)K * 8) + up(nkc * (int64_t)M * 4) + up(nkc * (int64_t)N * 4) +
-         up(M * 4) + up(N * 4) + up(nMb * 4) + up(nNb * 4);
+  return up(nNb * CHK_ROWS * kpitch * 2) + up(nMb * (int64_t)K * 8) + up(nMb * (int64_t)K * 4) + up(M * 4) + up(nNb * 4);
 }
 
 TcWorkspace tc_workspace_carve(void* base, int32_t M, int32_t N, int32_t K) {
-  const int64_t nMb = (M + BM - 1) / BM, nNb = (N + BN - 1) / BN, nkc = (K + ENC_KC - 1) / ENC_KC;
+  const int64_t nMb = (M + BM - 1) / BM, nNb = (N + kTcBNProt - 1) / kTcBNProt;
   const int64_t kpitch = (K + 7) / 8 * 8;
   auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
   char* c = static_cast<char*>(base);
@@ -533,39 +653,43 @@ TcWorkspace tc_workspace_carve(void* base, int32_t M, int32_t N, int32_t K) {
   w.chk = reinterpret_cast<uint16_t*>(c); c += up(nNb * CHK_ROWS * kpitch * 2);
   w.kpitch = kpitch;
   w.sA = reinterpret_cast<float2*>(c); c += up(nMb * (int64_t)K * 8);
-  w.rowAbsPart = reinterpret_cast<float*>(c); c += up(nkc * (int64_t)M * 4);
-  w.colAbsPart = reinterpret_cast<float*>(c); c += up(nkc * (int64_t)N * 4);
+  w.absSA = reinterpret_cast<float*>(c); c += up(nMb * (int64_t)K * 4);
   w.rowAbsA = reinterpret_cast<float*>(c); c += up(M * 4);
-  w.colAbsB = reinterpret_cast<float*>(c); c += up(N * 4);
-  w.maxAbsAe = reinterpret_cast<float*>(c); c += up(nMb * 4);
   w.maxAbsBe = reinterpret_cast<float*>(c); c += up(nNb * 4);
   w.bytes = static_cast<size_t>(c - static_cast<char*>(base));
   return w;
 }
 
 cudaError_t launch_tc_encode(const TcParams& p, const TcWorkspace& w, void* ws_base, cudaStream_t st) {
-  const int nMb = (p.M + BM - 1) / BM, nNb = (p.N + BN - 1) / BN, nkc = (p.K + ENC_KC - 1) / ENC_KC;
-  cudaError_t e = cudaMemsetAsync(ws_base, 0, w.bytes, st);  // zero pieces rows 3..15 and the maxima
+  const int nMb = (p.M + BM - 1) / BM, nNb = (p.N + kTcBNProt - 1) / kTcBNProt, nkc = (p.K + ENC_KC - 1) / ENC_KC;
+  // zero the checksum operand (its rows 3..15 stay zero) and the block maxima
+  cudaError_t e = cudaMemsetAsync(ws_base, 0, w.bytes, st);
   if (e != cudaSuccess) return e;
   encode_rows_kernel<<<dim3(nMb, nkc), 256, 0, st>>>(static_cast<const uint16_t*>(p.A), p.lda, p.M, p.K, w.sA,
-                                                      w.rowAbsPart, w.maxAbsAe);
-  encode_cols_kernel<<<dim3(nNb, nkc), 256, 0, st>>>(static_cast<const uint16_t*>(p.B), p.ldb, p.N, p.K, w.chk,
-                                                      w.kpitch, w.colAbsPart, w.maxAbsBe);
-  finalize_abs_kernel<<<(p.M + 255) / 256, 256, 0, st>>>(w.rowAbsPart, nkc, p.M, w.rowAbsA);
-  finalize_abs_kernel<<<(p.N + 255) / 256, 256, 0, st>>>(w.colAbsPart, nkc, p.N, w.colAbsB);
+                                                      w.absSA);
+  row_abs_kernel<<<(p.M + 7) / 8, 256, 0, st>>>(static_cast<const uint16_t*>(p.A), p.lda, p.M, p.K, w.rowAbsA);
+  encode_cols_kernel<<<dim3(nNb, nkc), 256, 0, st>>>(static_cast<const uint16_t*>(p.B), p.ldb, p.N, p.K, kTcBNProt,
+                                                      w.chk, w.kpitch, w.maxAbsBe);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_gemm(const TcParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmChk,
                            bool ft, cudaStream_t st) {
-  dim3 grid((p.M + BM - 1) / BM, (p.N + BN - 1) / BN);
   const size_t smem = sizeof(TcSmem);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int bn = ft ? kTcBNProt : BNM;
+  const long long tiles = (long long)((p.M + BM - 1) / BM) * ((p.N + bn - 1) / bn);
+  const int grid = (int)(tiles < sms ? tiles : sms);
   if (ft) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     tc_gemm_kernel<true><<<grid, NTHREADS, smem, st>>>(*tmA, *tmB, *tmChk, p);
   } else {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     tc_gemm_kernel<false><<<grid, NTHREADS, smem, st>>>(*tmA, *tmB, *tmChk, p);
   }

@@ -11,8 +11,9 @@
 namespace ftk {
 
 constexpr int kTcBM = 128;       // tile rows (TMEM lanes)
-constexpr int kTcBN = 256;       // tile columns (TMEM columns)
-constexpr int kTcChkRows = 16;   // N of the checksum MMA (pieces of B e in rows 0..2)
+constexpr int kTcBN = 256;       // data columns per tile, unprotected (= MMA N)
+constexpr int kTcBNProt = 240;   // data columns per tile, protected: B^r = [B, Be] fills N = 256
+constexpr int kTcChkRows = 16;   // rows of the checksum operand per column block (pieces of B e in 0..2)
 
 struct TcParams {
   int32_t M, N, K;
@@ -23,11 +24,10 @@ struct TcParams {
   const void* A; int64_t lda;
   const void* B; int64_t ldb;
   float* C; int64_t ldc;
-  const float* rowAbsA;          // [M]   upward sum_k |A(i,k)|
-  const float* colAbsB;          // [N]   upward sum_k |B(k,j)|
-  const float* maxAbsAe;         // [nMb] max_k upward sum_{i in block} |A(i,k)|
-  const float* maxAbsBe;         // [nNb] max_k upward sum_{j in block} |B(k,j)|
-  const float2* sA;              // [nMb][K] e^T A per row block, hi + lo
+  const float* rowAbsA;          // [M]        upward sum_k |A(i,k)|
+  const float* maxAbsBe;         // [nNb]      max_k upward sum_{j in block} |B(k,j)|
+  const float2* sA;              // [nMb][K]   e^T A per 128-row block, hi + lo
+  const float* absSA;            // [nMb][K]   upward sum_{i in block} |A(i,k)|
   ft_report_t* report;
   InjectList inj;
 };
@@ -35,8 +35,9 @@ struct TcParams {
 struct TcWorkspace {
   uint16_t* chk;  int64_t kpitch;
   float2* sA;
-  float* rowAbsPart; float* colAbsPart;
-  float* rowAbsA; float* colAbsB; float* maxAbsAe; float* maxAbsBe;
+  float* absSA;
+  float* rowAbsA;
+  float* maxAbsBe;
   size_t bytes;
 };
 

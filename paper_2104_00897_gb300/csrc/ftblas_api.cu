@@ -289,7 +289,7 @@ int gemm_ex_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   CallerPoint pts[kMaxInject];
   int npts = 0;
   if (ft) {
-    const int64_t tile_rows = f.swap ? kTcBN : kTcBM, tile_cols = f.swap ? kTcBM : kTcBN;
+    const int64_t tile_rows = f.swap ? kTcBNProt : kTcBM, tile_cols = f.swap ? kTcBM : kTcBNProt;
     npts = plan_injections(M, N, tile_rows, tile_cols, pts);
   }
   const float al = *static_cast<const float*>(alpha), be = *static_cast<const float*>(beta);
@@ -314,15 +314,15 @@ int gemm_ex_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   CUtensorMap tmA, tmB, tmC;
   std::memset(&tmA, 0, sizeof(tmA)); std::memset(&tmB, 0, sizeof(tmB)); std::memset(&tmC, 0, sizeof(tmC));
   if (!make_map_b16_sw128(&tmA, f.A, K, f.M, f.lda, 64, kTcBM)) return FTBLAS_STATUS_NOT_SUPPORTED;
-  if (!make_map_b16_sw128(&tmB, f.B, K, f.N, f.ldb, 64, kTcBN)) return FTBLAS_STATUS_NOT_SUPPORTED;
+  if (!make_map_b16_sw128(&tmB, f.B, K, f.N, f.ldb, 64, ft ? kTcBNProt : kTcBN)) return FTBLAS_STATUS_NOT_SUPPORTED;
   g_last_used_tma = 1;
   if (!ft) return record_cuda(launch_tc_gemm(p, &tmA, &tmB, &tmA, false, st));
   const size_t wsb = tc_workspace_bytes(p.M, p.N, p.K);
   void* ws = nullptr;
   if (cudaMallocAsync(&ws, wsb, st) != cudaSuccess) return FTBLAS_STATUS_ALLOC_FAILED;
   TcWorkspace w = tc_workspace_carve(ws, p.M, p.N, p.K);
-  p.rowAbsA = w.rowAbsA; p.colAbsB = w.colAbsB; p.maxAbsAe = w.maxAbsAe; p.maxAbsBe = w.maxAbsBe; p.sA = w.sA;
-  const int64_t nNb = (f.N + kTcBN - 1) / kTcBN;
+  p.rowAbsA = w.rowAbsA; p.maxAbsBe = w.maxAbsBe; p.sA = w.sA; p.absSA = w.absSA;
+  const int64_t nNb = (f.N + kTcBNProt - 1) / kTcBNProt;
   if (!make_map_b16_sw128(&tmC, w.chk, K, nNb * kTcChkRows, w.kpitch, 64, kTcChkRows)) {
     cudaFreeAsync(ws, st);
     return FTBLAS_STATUS_NOT_SUPPORTED;
@@ -388,7 +388,7 @@ int gemm_bf16_ft_with_workspace(int layout, int ta, int tb, int64_t M, int64_t N
   }
   if (M == 0 || N == 0) return 0;
   CallerPoint pts[kMaxInject];
-  const int64_t tile_rows = f.swap ? kTcBN : kTcBM, tile_cols = f.swap ? kTcBM : kTcBN;
+  const int64_t tile_rows = f.swap ? kTcBNProt : kTcBM, tile_cols = f.swap ? kTcBM : kTcBNProt;
   const int npts = plan_injections(M, N, tile_rows, tile_cols, pts);
   const float al = *static_cast<const float*>(alpha), be = *static_cast<const float*>(beta);
   if (!f.a_kmajor || !f.b_kmajor) return FTBLAS_STATUS_NOT_SUPPORTED;
@@ -412,11 +412,11 @@ int gemm_bf16_ft_with_workspace(int layout, int ta, int tb, int64_t M, int64_t N
   CUtensorMap tmA, tmB, tmC;
   std::memset(&tmA, 0, sizeof(tmA)); std::memset(&tmB, 0, sizeof(tmB)); std::memset(&tmC, 0, sizeof(tmC));
   if (!make_map_b16_sw128(&tmA, f.A, K, f.M, f.lda, 64, kTcBM)) return FTBLAS_STATUS_NOT_SUPPORTED;
-  if (!make_map_b16_sw128(&tmB, f.B, K, f.N, f.ldb, 64, kTcBN)) return FTBLAS_STATUS_NOT_SUPPORTED;
+  if (!make_map_b16_sw128(&tmB, f.B, K, f.N, f.ldb, 64, kTcBNProt)) return FTBLAS_STATUS_NOT_SUPPORTED;
   g_last_used_tma = 1;
   TcWorkspace w = tc_workspace_carve(ws, p.M, p.N, p.K);
-  p.rowAbsA = w.rowAbsA; p.colAbsB = w.colAbsB; p.maxAbsAe = w.maxAbsAe; p.maxAbsBe = w.maxAbsBe; p.sA = w.sA;
-  const int64_t nNb = (f.N + kTcBN - 1) / kTcBN;
+  p.rowAbsA = w.rowAbsA; p.maxAbsBe = w.maxAbsBe; p.sA = w.sA; p.absSA = w.absSA;
+  const int64_t nNb = (f.N + kTcBNProt - 1) / kTcBNProt;
   if (!make_map_b16_sw128(&tmC, w.chk, K, nNb * kTcChkRows, w.kpitch, 64, kTcChkRows))
     return FTBLAS_STATUS_NOT_SUPPORTED;
   int rc = record_cuda(launch_tc_encode(p, w, ws, st));  // clears the carved workspace first
@@ -565,7 +565,7 @@ int ftblas_verification_tile(ftblas_layout_t layout, ftblas_dtype_t compute_type
   if (!tile_cols) return -7;
   if (!k_tile) return -8;
   const bool swap = layout == FTBLAS_ROW_MAJOR;
-  const int64_t bm = compute_type == FTBLAS_R_64F ? kDBM : kTcBM, bn = compute_type == FTBLAS_R_64F ? kDBN : kTcBN;
+  const int64_t bm = compute_type == FTBLAS_R_64F ? kDBM : kTcBM, bn = compute_type == FTBLAS_R_64F ? kDBN : kTcBNProt;
   *tile_rows = swap ? bn : bm;
   *tile_cols = swap ? bm : bn;
   *k_tile = compute_type == FTBLAS_R_64F ? kDBK : 64;

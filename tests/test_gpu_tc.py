@@ -206,7 +206,8 @@ def test_bf16_full_size_8192_sampled_rows():
     pt = dict(i=i, j=j, site=fb.SITE_OUTPUT, mode=fb.MODE_ADD_REL, rel_log2=12, sign=1)
     fb.ftblas_set_injection(fb.make_injection(fixed=[pt]))
     got, rep = P.run()
-    assert report_summary(rep)[:5] == ((n // 128) * (n // 256), 1, 1, 0, 0)
+    tr, tc, _ = P.tile()
+    assert report_summary(rep)[:5] == (-(-n // tr) * -(-n // tc), 1, 1, 0, 0)
     assert [(r.i, r.j) for r in rep.records()] == [(i, j)]
     rows = np.unique(np.concatenate([S.randint(9, 9, 3, 0, n - 1), [i]]))
     ref_rows = O.gemm_rows(O.COL_MAJOR, P.ta, P.tb, n, n, n, P.alpha, P.a64, P.lda, P.b64, P.ldb, P.beta, P.c64,
