@@ -185,7 +185,7 @@ int ftblas_dgemm_host(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_tran
  * and compared element by element; a located error is corrected by subtracting the row mismatch
  * (Section VI.C), evaluated as C^r(i) - sum_{j' != j} C(i,j') so that a huge or
  * non-finite error does not cancel catastrophically. Workspace (about
- * 32*K*ceil(N/240) + 8*K*ceil(M/128) bytes) is taken from the stream-ordered allocator
+ * 32*K*ceil(N/240) + 8*K*ceil(M/128) + 4*M*ceil(K/256) bytes) is taken from the stream-ordered allocator
  * and released on the same stream. */
 int ftblas_gemm_ex(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,
                    int64_t M, int64_t N, int64_t K, const void* alpha,
@@ -215,12 +215,12 @@ int ftblas_gemm_ex_noabft(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_
  * every GPU loading this library holds until the process exits; nothing else is
  * allocated (no cudaMalloc, cudaFree, stream-ordered or library allocation).
  *   - Size limit: problems whose scratch, about 32*K*ceil(N/240) + 8*K*ceil(M/128) +
- *     8*(M+N)*ceil(K/1024) bytes, exceeds 16 MiB are rejected with
+ *     4*M*ceil(K/256) bytes, exceeds 16 MiB are rejected with
  *     FTBLAS_STATUS_WORKSPACE_LIMIT before any device work (M = N = K = 8192 fits).
  *   - First call per device: it looks up the device address of the static array with
  *     the device current; make that first call before any stream capture.
- *   - Sharing: every call on a device uses the same array and clears the part it needs
- *     at its start. Calls whose device work overlaps (different streams, or other
+ *   - Sharing: every call on a device uses the same array and its encode pass writes
+ *     every scratch entry its GEMM reads. Calls whose device work overlaps (different streams, or other
  *     threads) race on it and must be serialised by the caller.
  * Other combinations return FTBLAS_STATUS_NOT_SUPPORTED. */
 int ftblas_gemm_ex_noalloc(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,

@@ -489,12 +489,16 @@ static void ft_tile(const oracle_problem_t* p, int64_t tr, int64_t tc,
  *   - an accumulator injection flips bit b of the binary32 accumulator after all K products;
  *   - tau uses gamma_K(u_acc) for the product part, with sum_k |A(i,k)| sum_j |B(k,j)|
  *     bounded by (sum_k |A(i,k)|) (max_k sum_j |B(k,j)|) over the tile:
- *       row:    |alpha| P (gamma_K(u_acc) (2 + 2^-7) + 2^-20) + 2^-23 (sum_j |C| + |beta| sum_j |C_in|)
- *       column: |alpha| P_c (gamma_K(u_acc) + gamma_K(2^-24) + 2^-22) + 2^-23 (sum_i |C| + 34 |beta| sum_i |C_in|),
+ *       row:    |alpha| P (gamma_K(u_acc) (2 + 2^-7) + 2^-20 + gamma_{tile_n}(2^-24))
+ *               + 2^-23 (sum_j |C| + |beta| sum_j |C_in|)
+ *       column: |alpha| P_c (gamma_K(u_acc) + gamma_K(2^-24) + 2^-22 + gamma_{tile_m}(2^-24))
+ *               + 2^-23 (sum_i |C| + 34 |beta| sum_i |C_in|),
  *               P_c = sum_k (sum_{i in tile} |A(i,k)|) |B(k,j)| (exact: it is formed only in the
  *               rare tiles with a row mismatch)
  *     (the row side's prediction is itself a binary32 product of A with B e split into
- *     three pieces; the column side's is a binary32 dot product of the rounded e^T A with B);
+ *     three pieces; the column side's is a binary32 dot product of e^T A with B; B e and
+ *     e^T A are binary32 sums over the tile, whose rounding in any order is at most
+ *     gamma_n(2^-24) times the sum of magnitudes, n the tile width);
  *   - column checksums are formed only when a row mismatches (Section V.A, lazy side);
  *     when they flag no column and beta == 0, the mismatching row is recomputed and each
  *     element compared with its own bound (locates errors in rows of small scale);
@@ -546,6 +550,9 @@ static void ft_tile_acc32(const oracle_problem_t* p, int64_t tr, int64_t tc,
   }
   const double gK = gamma_n((double)K * p->u_acc / 1.1102230246251565e-16);
   const double g24 = gamma_n((double)K * 5.9604644775390625e-08 / 1.1102230246251565e-16);  /* gamma_K(2^-24) */
+  /* gamma_{tile_n}(2^-24) and gamma_{tile_m}(2^-24): rounding of the binary32 sums B e and e^T A */
+  const double genc_r = gamma_n((double)p->tile_n * 5.9604644775390625e-08 / 1.1102230246251565e-16);
+  const double genc_c = gamma_n((double)p->tile_m * 5.9604644775390625e-08 / 1.1102230246251565e-16);
   /* Row side, every row. */
   int64_t nr = 0, fr = -1;
   double fr_delta = 0.0, fr_tau = 0.0, fr_pred = 0.0;
@@ -566,7 +573,7 @@ static void ft_tile_acc32(const oracle_problem_t* p, int64_t tr, int64_t tc,
     double Cr_ref = 0.0, R = 0.0;
     for (int64_t jj = 0; jj < nJ; ++jj) { Cr_ref = Cr_ref + T[ii + jj * nI]; R = R + fabs(T[ii + jj * nI]); }
     double P = rowAbsA * maxAbsBe;
-    double tau = fabs(p->alpha) * P * (gK * (2.0 + 0.0078125) + 9.5367431640625e-07) +
+    double tau = fabs(p->alpha) * P * (gK * (2.0 + 0.0078125) + 9.5367431640625e-07 + genc_r) +
                  1.1920928955078125e-07 * (R + fabs(p->beta) * Q);
     double d = Cr_ref - Cr;
     if (!(fabs(d) <= tau) || isinf(d)) {
@@ -589,7 +596,7 @@ static void ft_tile_acc32(const oracle_problem_t* p, int64_t tr, int64_t tc,
       if (p->beta != 0.0) Cc = Cc + p->beta * cin_sum;
       double Cc_ref = 0.0, R = 0.0;
       for (int64_t ii = 0; ii < nI; ++ii) { Cc_ref = Cc_ref + T[ii + jj * nI]; R = R + fabs(T[ii + jj * nI]); }
-      double tau = fabs(p->alpha) * P * (gK + g24 + 2.384185791015625e-07) +
+      double tau = fabs(p->alpha) * P * (gK + g24 + 2.384185791015625e-07 + genc_c) +
                    1.1920928955078125e-07 * (R + 34.0 * fabs(p->beta) * Q);
       double d = Cc_ref - Cc;
       if (!(fabs(d) <= tau) || isinf(d)) {

@@ -26,6 +26,7 @@
 //               different scale), the mismatching row is recomputed and compared element by
 //               element. The located element is corrected from the row checksum.
 #include <climits>
+#include <cstring>
 
 #include <cuda_bf16.h>
 
@@ -60,13 +61,11 @@ struct __align__(1024) TcSmem {
   uint64_t tempty[2];            // accumulator buffer b has been read by the 4 epilogue warps
   uint32_t tmem_base;
   int timeout;
-  int nflag_rows, first_row, nflag_cols, first_col, nflag_elem, first_elem;
-  double delta_row, tau_row, delta_col, tau_col;
+  int nflag_rows, first_row, pend_slot;
+  double delta_row, tau_row;
   double pred_row;               // predicted row checksum of the first flagged row
   float cin_col[4][BNM];         // per-warp partial column sums of C_in (beta != 0)
   float cin_col_abs[4][BNM];
-  double col_delta[BNM];         // lazy column side: C^c_ref - C^c and tau per column
-  double col_tau[BNM];
 };
 
 __device__ __forceinline__ float bf16_to_f32(uint16_t b) { return __uint_as_float(static_cast<uint32_t>(b) << 16); }
@@ -118,6 +117,19 @@ __device__ __noinline__ float inject_element(const TcParams& p, int64_t gi, int6
   return out;
 }
 
+// Smallest tile column > after (tile-local) where row gi holds an accumulator- or output-site
+// injection point, INT_MAX if none (test launches only; kept out of line).
+__device__ __noinline__ int next_inj_col(const TcParams& p, int64_t gi, int n0, int nJ, int after) {
+  int best = INT_MAX;
+  for (int e = 0; e < p.inj.n; ++e) {
+    const InjectPoint& ip = p.inj.p[e];
+    if (ip.i != gi || (ip.site != kSiteAccum && ip.site != kSiteOutput)) continue;
+    const int c = ip.j - n0;
+    if (c > after && c < nJ && c < best) best = c;
+  }
+  return best;
+}
+
 __device__ __forceinline__ float gamma32_up(float n, float u) {
   const float nu = __fmul_ru(n, u);
   return __fdiv_ru(nu, __fsub_rd(1.0f, nu));
@@ -145,6 +157,17 @@ __device__ void tc_record(const TcParams& p, int kind, int64_t tr, int64_t tc, i
   r.value_after = after;
   r.kind = kind;
   r.reserved = 0;
+}
+
+__device__ void count_kind(const TcParams& p, int kind) {
+  if (p.report == nullptr) return;
+  atomicAdd(reinterpret_cast<unsigned long long*>(&p.report->detected), 1ull);
+  unsigned long long* ctr = (kind == FT_KIND_CORRECTED)
+                                ? reinterpret_cast<unsigned long long*>(&p.report->corrected)
+                            : (kind == FT_KIND_CHECKSUM_ONLY)
+                                ? reinterpret_cast<unsigned long long*>(&p.report->checksum_only)
+                                : reinterpret_cast<unsigned long long*>(&p.report->uncorrectable);
+  atomicAdd(ctr, 1ull);
 }
 
 // Persistent-tile order: groups of kGroupM row tiles sweep all column tiles, so the CTAs
@@ -266,10 +289,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // Injection points in this tile (test launches only): the per-element injection code
       // is kept out of the hot loop so the epilogue stays small in the instruction cache,
       // which it shares with the producer and MMA warps.
-      bool tile_inj = false;
-      if (FT)
-        for (int e = 0; e < p.inj.n; ++e)
-          tile_inj |= p.inj.p[e].i >= m0 && p.inj.p[e].i < m0 + nI && p.inj.p[e].j >= n0 && p.inj.p[e].j < n0 + nJ;
+      int inj_c = INT_MAX;  // next tile column of this row holding an injection point
+      if (FT && p.inj.n > 0) inj_c = next_inj_col(p, gi, n0, nJ, -1);
       if (got) {
 #pragma unroll 1
         for (int ch = 0; ch < (BN + 7) / 8; ++ch) {
@@ -286,8 +307,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             float cin = 0.f;
             if (beta_nz && ok) cin = p.C[gi + gj * p.ldc];
             float out;
-            if (FT && tile_inj) out = inject_element(p, gi, gj, acc, cin, beta_nz);
-            else out = beta_nz ? fmaf(p.alpha, acc, p.beta * cin) : p.alpha * acc;
+            if (FT && col == inj_c) {
+              out = inject_element(p, gi, gj, acc, cin, beta_nz);
+              inj_c = next_inj_col(p, gi, n0, nJ, col);
+            } else {
+              out = beta_nz ? fmaf(p.alpha, acc, p.beta * cin) : p.alpha * acc;
+            }
             if (ok) p.C[gi + gj * p.ldc] = out;
             if (FT) {
               const float o = ok ? out : 0.f;
@@ -317,10 +342,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (!FT) continue;
 
       // -------------------------------------------------------- row verification
-      if (et == 0) {
-        sm.nflag_rows = 0; sm.first_row = INT_MAX; sm.nflag_cols = 0; sm.first_col = INT_MAX;
-        sm.nflag_elem = 0; sm.first_elem = INT_MAX;
-      }
+      if (et == 0) { sm.nflag_rows = 0; sm.first_row = INT_MAX; }
       named_bar(1, 128);
       double delta = 0.0, tau = 0.0, predicted = 0.0;
       if (got && row_ok) {
@@ -337,11 +359,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         const double ref = (double)rs + (double)rc;
         delta = ref - predicted;
-        // tau = |alpha| P (gamma_K(u_acc) (2 + 2^-7) + 2^-20) + 2 u32 (sum|C| + |beta| sum|C_in|), P an
-        // upper bound of sum_k |A(i,k)| sum_{j in tile} |B(k,j)|.
+        // tau = |alpha| P (gamma_K(u_acc) (2 + 2^-7) + 2^-20 + gamma_240(2^-24)) + 2 u32 (sum|C| +
+        // |beta| sum|C_in|), P an upper bound of sum_k |A(i,k)| sum_{j in tile} |B(k,j)|; the
+        // gamma_240(2^-24) term is the rounding of B e, a binary32 sum over the tile's columns.
         const float P = __fmul_ru(p.rowAbsA[gi], p.maxAbsBe[nt]);
         const float g = gamma32_up((float)p.K, p.u_acc);
-        const float prod = __fmul_ru(__fmul_ru(fabsf(p.alpha), P), __fadd_ru(__fmul_ru(g, 2.0078125f), 0x1p-20f));
+        const float genc = gamma32_up((float)kTcBNProt, 0x1p-24f);
+        const float prod = __fmul_ru(__fmul_ru(fabsf(p.alpha), P),
+                                     __fadd_ru(__fadd_ru(__fmul_ru(g, 2.0078125f), 0x1p-20f), genc));
         const float outp = __fmul_ru(0x1p-23f, __fadd_ru(rabs, __fmul_ru(fabsf(p.beta), cabs)));
         tau = (double)__fadd_ru(prod, outp);
         if (!(fabs(delta) <= tau) || isinf(delta)) {
@@ -355,154 +380,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       named_bar(1, 128);
       const int nr = sm.nflag_rows;
       if (nr > 0) {
-        // ------------------------------------------------------ lazy column side (Section V.A)
-        // Each warp takes columns ew, ew + 4, ...; its lanes split the rows (C^c_ref) and K
-        // (C^c = alpha (e^T A) B(:, j), compensated); partial results are summed in binary64.
-        const uint16_t* Bp = static_cast<const uint16_t*>(p.B);
-        const float2* sAI = p.sA + (int64_t)mt * p.K;
-        const float* absAI = p.absSA + (int64_t)mt * p.K;
-        const float g = gamma32_up((float)p.K, p.u_acc);
-        const float g24 = gamma32_up((float)p.K, 0x1p-24f);
-        for (int cidx = ew; cidx < nJ; cidx += 4) {
-          const int64_t gj = n0 + cidx;
-          float s = 0.f, c = 0.f, a = 0.f;
-          for (int i = lane; i < nI; i += 32) {
-            const float x = p.C[(int64_t)(m0 + i) + gj * p.ldc];
-            neumaier(s, c, x);
-            a = __fadd_ru(a, fabsf(x));
-          }
-          const double cref = warp_sum_f64((double)s + (double)c);
-          const float cref_abs = warp_sum_up(a);
-          // binary32 dot products with two independent accumulators (their rounding enters
-          // the threshold as gamma_K(2^-24) P_c, next to the accumulation's gamma_K(u_acc) P_c)
-          const uint16_t* bcol = Bp + gj * p.ldb;
-          float d0 = 0.f, d1 = 0.f, pc0 = 0.f, pc1 = 0.f;
-          int k = lane;
-          for (; k + 32 < p.K; k += 64) {
-            const float b0 = bf16_to_f32(bcol[k]), b1 = bf16_to_f32(bcol[k + 32]);
-            d0 = fmaf(sAI[k].x, b0, d0);
-            d1 = fmaf(sAI[k + 32].x, b1, d1);
-            pc0 = __fmaf_ru(absAI[k], fabsf(b0), pc0);  // sum_k (sum_i |A(i,k)|) |B(k,j)|, upward
-            pc1 = __fmaf_ru(absAI[k + 32], fabsf(b1), pc1);
-          }
-          if (k < p.K) {
-            const float b0 = bf16_to_f32(bcol[k]);
-            d0 = fmaf(sAI[k].x, b0, d0);
-            pc0 = __fmaf_ru(absAI[k], fabsf(b0), pc0);
-          }
-          double cpred = (double)p.alpha * warp_sum_f64((double)d0 + (double)d1);
-          const float Pc = warp_sum_up(__fadd_ru(pc0, pc1));
-          float cin_abs = 0.f;
-          if (beta_nz) {
-            double cin_sum = 0.0;
-            for (int w = 0; w < 4; ++w) { cin_sum += (double)sm.cin_col[w][cidx]; cin_abs = __fadd_ru(cin_abs, sm.cin_col_abs[w][cidx]); }
-            cpred += (double)p.beta * cin_sum;
-          }
-          if (lane == 0) {
-            const double dcol = cref - cpred;
-            // C^c_ref carries the accumulation error gamma_K(u_acc) P_c; C^c (binary32 dot of
-            // the rounded e^T A with B) adds gamma_K(2^-24) P_c + 2^-23 P_c; the per-warp C_in
-            // partial sums carry gamma_31 (binary32).
-            const float prod = __fmul_ru(__fmul_ru(fabsf(p.alpha), Pc), __fadd_ru(__fadd_ru(g, g24), 0x1p-22f));
-            const float outp =
-                __fmul_ru(0x1p-23f, __fadd_ru(cref_abs, __fmul_ru(__fmul_ru(fabsf(p.beta), cin_abs), 34.0f)));
-            const double tauc = (double)__fadd_ru(prod, outp);
-            sm.col_delta[cidx] = dcol;
-            sm.col_tau[cidx] = tauc;
-            if (!(fabs(dcol) <= tauc) || isinf(dcol)) {
-              atomicAdd(&sm.nflag_cols, 1);
-              atomicMin(&sm.first_col, cidx);
-            }
-          }
-        }
-        __threadfence_block();
+        // A row mismatch. The column checksums that locate it (Section V.A, lazy side) are
+        // formed by the resolve pass after every tile is stored, spread over many CTAs; this
+        // CTA only hands the tile over (with the column sums of C_in, which it overwrote).
+        if (et == 0) sm.pend_slot = (int)atomicAdd(&p.pend->count, 1u);
         named_bar(1, 128);
-        const int nc = sm.nflag_cols;
-        if (nc > 0 && et == 0) { sm.delta_col = sm.col_delta[sm.first_col]; sm.tau_col = sm.col_tau[sm.first_col]; }
-        // ------------------------------------------------------ row-recompute locator
-        // One mismatching row and no mismatching column: the column checksums of a tile
-        // whose rows differ greatly in scale cannot resolve an error in a small row. Then
-        // recompute that row and compare each element with its own bound
-        // |alpha| (gamma_K(u_acc) + gamma_K(2^-24) + 2^-30) sum_k |A(i,k)||B(k,j)| + 2^-23 |C(i,j)|.
-        const bool recompute_row = (nr == 1 && nc == 0 && !beta_nz);
-        if (recompute_row) {
-          const int64_t gr = m0 + sm.first_row;
-          const uint16_t* arow = static_cast<const uint16_t*>(p.A) + gr * p.lda;
-          for (int cidx = ew; cidx < nJ; cidx += 4) {
-            const int64_t gj = n0 + cidx;
-            const uint16_t* bcol = Bp + gj * p.ldb;
-            float d0 = 0.f, d1 = 0.f, s0 = 0.f, s1 = 0.f;
-            int k = lane;
-            for (; k + 32 < p.K; k += 64) {
-              const float a0 = bf16_to_f32(arow[k]), b0 = bf16_to_f32(bcol[k]);
-              const float a1 = bf16_to_f32(arow[k + 32]), b1 = bf16_to_f32(bcol[k + 32]);
-              d0 = fmaf(a0, b0, d0);
-              d1 = fmaf(a1, b1, d1);
-              s0 = __fmaf_ru(fabsf(a0), fabsf(b0), s0);
-              s1 = __fmaf_ru(fabsf(a1), fabsf(b1), s1);
-            }
-            if (k < p.K) {
-              const float a0 = bf16_to_f32(arow[k]), b0 = bf16_to_f32(bcol[k]);
-              d0 = fmaf(a0, b0, d0);
-              s0 = __fmaf_ru(fabsf(a0), fabsf(b0), s0);
-            }
-            const double rec = (double)p.alpha * warp_sum_f64((double)d0 + (double)d1);
-            const float S = warp_sum_up(__fadd_ru(s0, s1));
-            if (lane == 0) {
-              const double cij = (double)p.C[gr + gj * p.ldc];
-              // the recomputation is a binary32 dot product: its rounding, gamma_K(2^-24) S,
-              // joins the accumulation's gamma_K(u_acc) S
-              const float te = __fadd_ru(__fmul_ru(__fmul_ru(fabsf(p.alpha), S), __fadd_ru(__fadd_ru(g, g24), 0x1p-30f)),
-                                         __fmul_ru(0x1p-23f, (float)fabs(cij)));
-              const double d = cij - rec;
-              if (!(fabs(d) <= (double)te) || isinf(d)) {
-                atomicAdd(&sm.nflag_elem, 1);
-                atomicMin(&sm.first_elem, cidx);
-              }
-            }
+        const int slot = sm.pend_slot;
+        if (slot < kTcPendCap) {
+          TcPendingEntry& pe = p.pend->e[slot];
+          if (et == 0) {
+            pe.mt = mt; pe.nt = nt; pe.nr = nr; pe.first_row = sm.first_row;
+            pe.delta_row = sm.delta_row; pe.tau_row = sm.tau_row; pe.pred_row = sm.pred_row; pe.done = 0u;
           }
-          __threadfence_block();
-          named_bar(1, 128);
-        }
-        if (et == 0) {
-          int kind;
-          double before = 0.0, after = 0.0;
-          const int64_t gi2 = m0 + sm.first_row;
-          int located_col = -1;
-          if (nr == 1 && nc == 1) located_col = sm.first_col;
-          else if (recompute_row && sm.nflag_elem == 1) located_col = sm.first_elem;
-          int64_t gj2 = (nc > 0) ? n0 + sm.first_col : -1;
-          if (located_col >= 0) {
-            kind = FT_KIND_CORRECTED;
-            gj2 = n0 + located_col;
-            float* cp = p.C + gi2 + gj2 * p.ldc;
-            before = (double)*cp;
-            // The paper's correction, C(i,j) - delta_row, evaluated as
-            // C^r(i) - sum_{j' != j} C(i,j'): equal in exact arithmetic, and it never touches
-            // the erroneous value (no cancellation against a huge or non-finite error).
-            double rest = 0.0;
-            for (int j = 0; j < nJ; ++j)
-              if (n0 + j != gj2) rest += (double)p.C[gi2 + (int64_t)(n0 + j) * p.ldc];
-            after = sm.pred_row - rest;
-            *cp = (float)after;
-            after = (double)*cp;
-          } else if (nc == 0 && (!recompute_row || sm.nflag_elem == 0)) {
-            kind = FT_KIND_CHECKSUM_ONLY;
-          } else {
-            kind = FT_KIND_UNCORRECTABLE;
-          }
-          const int ncols_rep = nc > 0 ? nc : (recompute_row ? sm.nflag_elem : 0);
-          tc_record(p, kind, mt, nt, gi2, gj2, sm.delta_row, nc > 0 ? sm.delta_col : 0.0, sm.tau_row,
-                    nc > 0 ? sm.tau_col : 0.0, before, after, nr, ncols_rep);
-          if (p.report) {
-            atomicAdd(reinterpret_cast<unsigned long long*>(&p.report->detected), 1ull);
-            unsigned long long* ctr = (kind == FT_KIND_CORRECTED)
-                                          ? reinterpret_cast<unsigned long long*>(&p.report->corrected)
-                                      : (kind == FT_KIND_CHECKSUM_ONLY)
-                                          ? reinterpret_cast<unsigned long long*>(&p.report->checksum_only)
-                                          : reinterpret_cast<unsigned long long*>(&p.report->uncorrectable);
-            atomicAdd(ctr, 1ull);
-          }
+          if (beta_nz)
+            for (int c = et; c < nJ; c += 128) {
+              double cs2 = 0.0;
+              float ca = 0.f;
+              for (int w = 0; w < 4; ++w) { cs2 += (double)sm.cin_col[w][c]; ca = __fadd_ru(ca, sm.cin_col_abs[w][c]); }
+              pe.cin_sum[c] = cs2;
+              pe.cin_abs[c] = ca;
+            }
+        } else if (et == 0) {
+          // more mismatching tiles in this call than the resolve pass holds: detected, not located
+          tc_record(p, FT_KIND_UNCORRECTABLE, mt, nt, m0 + sm.first_row, -1, sm.delta_row, 0.0, sm.tau_row, 0.0,
+                    0.0, 0.0, nr, 0);
+          count_kind(p, FT_KIND_UNCORRECTABLE);
         }
       }
       if (et == 0 && p.report) atomicAdd(reinterpret_cast<unsigned long long*>(&p.report->tiles_checked), 1ull);
@@ -522,154 +424,419 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // ---------------------------------------------------------------------------------------
-// Encode pre-pass (bandwidth-bound). Kernel-frame A is M x K and B is K x N, both
-// K-contiguous (row i of A at A + i*lda, column j of B at B + j*ldb). One thread per pair
-// of consecutive k; loads are 4-byte BF16 pairs, coalesced along k.
+// Resolve pass: locate and correct the errors of the tiles whose row checksums mismatched
+// (run after the GEMM on the same stream; with no such tile every CTA returns at once).
+// A work item is (mismatching tile, group of 8 columns); warp w of the CTA takes column
+// j = 8 g + w of the tile and forms
+//   C^c_ref(j) = sum_i C(i,j) over the stored tile (compensated, warp sum in binary64),
+//   C^c(j)     = alpha sum_k (e^T A)(k) B(k,j) [+ beta sum_i C_in(i,j)] (binary32 dot),
+//   P_c(j)     = sum_k (sum_i |A(i,k)|) |B(k,j)| (upward),
+// and, when exactly one row mismatched and beta == 0, that row's element recomputed,
+// alpha sum_k A(i,k) B(k,j), with S = sum_k |A(i,k)||B(k,j)|. The CTA that finishes a
+// tile's last group classifies the tile and corrects it.
 // ---------------------------------------------------------------------------------------
-constexpr int ENC_KC = 512;   // k per CTA (256 threads x 2)
+constexpr int kResolveWarps = 8;
+constexpr int kResolveItems = kTcBNProt;  // one column per work item
 
-__device__ __forceinline__ void load_pair(const uint16_t* row, int64_t k, int32_t K, float& x0, float& x1) {
-  // k is even; the pair (k, k+1) is 4-byte aligned because leading dimensions are multiples
-  // of 8 elements and base addresses are 16-byte aligned.
-  if (k + 1 < K) {
-    const uint32_t w = *reinterpret_cast<const uint32_t*>(row + k);
-    x0 = __uint_as_float(w << 16);
-    x1 = __uint_as_float(w & 0xffff0000u);
-  } else {
-    x0 = (k < K) ? bf16_to_f32(row[k]) : 0.f;
-    x1 = 0.f;
+__device__ __forceinline__ void bf16x8(const uint4 w, float (&x)[8]) {
+  const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    x[2 * h] = __uint_as_float(ws[h] << 16);
+    x[2 * h + 1] = __uint_as_float(ws[h] & 0xffff0000u);
   }
 }
 
-// Per 128-row block I: e^T A over the block for each k (hi + lo binary32 pair,
-// compensated) and the upward sum of |A| over the block for each k. Streaming, one thread
-// per pair of k, no cross-thread reduction.
-__global__ void __launch_bounds__(256) encode_rows_kernel(const uint16_t* A, int64_t lda, int32_t M, int32_t K,
-                                                           float2* sA, float* absSA) {
-  const int I = blockIdx.x;
-  const int m0 = I * BM;
-  const int nI = min(BM, M - m0);
-  const int64_t k = (int64_t)blockIdx.y * ENC_KC + 2 * threadIdx.x;
-  if (k >= K) return;
-  float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, a0 = 0.f, a1 = 0.f;
-  for (int i = 0; i < nI; ++i) {
-    float x0, x1;
-    load_pair(A + (int64_t)(m0 + i) * lda, k, K, x0, x1);
-    neumaier(s0, c0, x0);
-    neumaier(s1, c1, x1);
-    a0 = __fadd_ru(a0, fabsf(x0));
-    a1 = __fadd_ru(a1, fabsf(x1));
-  }
-  float h = s0 + c0;
-  sA[(int64_t)I * K + k] = make_float2(h, c0 - (h - s0));
-  absSA[(int64_t)I * K + k] = a0;
-  if (k + 1 < K) {
-    h = s1 + c1;
-    sA[(int64_t)I * K + k + 1] = make_float2(h, c1 - (h - s1));
-    absSA[(int64_t)I * K + k + 1] = a1;
-  }
-}
+struct ResolveShared {
+  int last, first_col, first_elem;
+  double part_d[kResolveWarps], part_r[kResolveWarps];
+  float part_pc[kResolveWarps], part_S[kResolveWarps];
+  double cref;
+  float cref_abs;
+};
 
-// Upward sum_k |A(i,k)| per row: one warp per row, 16-byte loads along the row.
-__global__ void __launch_bounds__(256) row_abs_kernel(const uint16_t* A, int64_t lda, int32_t M, int32_t K,
-                                                       float* rowAbsA) {
+// One column j of a mismatching tile, the eight warps splitting K in blocks of 256
+// (lane l loads k .. k + 7 of a block with 16-byte loads: B and A rows are 16-byte aligned,
+// leading dimensions being multiples of 8; e^T A rows are 32-byte aligned, pitch a multiple
+// of 8). Partial sums meet in shared memory; thread 0 forms the comparisons.
+template <bool kRecompute>
+__device__ void resolve_column(const TcParams& p, TcPendingEntry& pe, ResolveShared& sh, int mt, int m0, int n0,
+                               int nI, int cidx, bool beta_nz) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * 8 + warp;
-  if (i >= M) return;
-  const uint16_t* row = A + i * lda;
-  float a = 0.f;
-  const int K8 = K & ~7;
-  for (int k = lane * 8; k < K8; k += 256) {
-    const uint4 w = *reinterpret_cast<const uint4*>(row + k);  // rows are 16-byte aligned
-    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+  const int64_t gj = n0 + cidx;
+  const int64_t gi = m0 + pe.first_row;
+  if (warp == 0) {
+    float s = 0.f, c = 0.f, a = 0.f;
+    for (int i = lane; i < nI; i += 32) {
+      const float x = p.C[(int64_t)(m0 + i) + gj * p.ldc];
+      neumaier(s, c, x);
+      a = __fadd_ru(a, fabsf(x));
+    }
+    const double cref = warp_sum_f64((double)s + (double)c);
+    const float cref_abs = warp_sum_up(a);
+    if (lane == 0) { sh.cref = cref; sh.cref_abs = cref_abs; }
+  }
+  const uint16_t* bcol = static_cast<const uint16_t*>(p.B) + gj * p.ldb;
+  const uint16_t* arow = static_cast<const uint16_t*>(p.A) + gi * p.lda;
+  const float* sAI = p.sA + (int64_t)mt * p.sa_pitch;
+  const float* absAI = p.absSA + (int64_t)mt * p.sa_pitch;
+  const int K = p.K, K8 = p.K & ~7;
+  float d = 0.f, pc = 0.f, r = 0.f, S = 0.f;
+#pragma unroll 2
+  for (int k = warp * 256 + lane * 8; k < K8; k += kResolveWarps * 256) {
+    float bx[8];
+    bf16x8(*reinterpret_cast<const uint4*>(bcol + k), bx);
+    const float4 s0 = *reinterpret_cast<const float4*>(sAI + k), s1 = *reinterpret_cast<const float4*>(sAI + k + 4);
+    const float4 u0 = *reinterpret_cast<const float4*>(absAI + k), u1 = *reinterpret_cast<const float4*>(absAI + k + 4);
+    const float sv[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+    const float uv[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      a = __fadd_ru(a, fabsf(__uint_as_float(ws[h] << 16)));
-      a = __fadd_ru(a, fabsf(__uint_as_float(ws[h] & 0xffff0000u)));
+    for (int q = 0; q < 8; ++q) {
+      d = fmaf(sv[q], bx[q], d);
+      pc = __fmaf_ru(uv[q], fabsf(bx[q]), pc);
+    }
+    if (kRecompute) {
+      float ax[8];
+      bf16x8(*reinterpret_cast<const uint4*>(arow + k), ax);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        r = fmaf(ax[q], bx[q], r);
+        S = __fmaf_ru(fabsf(ax[q]), fabsf(bx[q]), S);
+      }
     }
   }
-  for (int k = K8 + lane; k < K; k += 32) a = __fadd_ru(a, fabsf(bf16_to_f32(row[k])));
-  a = warp_sum_up(a);
-  if (lane == 0) rowAbsA[i] = a;
+  if (warp == kResolveWarps - 1 && K8 + lane < K) {  // ragged end of K, one element per lane
+    const int k = K8 + lane;
+    const float bx = bf16_to_f32(bcol[k]);
+    d = fmaf(sAI[k], bx, d);
+    pc = __fmaf_ru(absAI[k], fabsf(bx), pc);
+    if (kRecompute) {
+      const float ax = bf16_to_f32(arow[k]);
+      r = fmaf(ax, bx, r);
+      S = __fmaf_ru(fabsf(ax), fabsf(bx), S);
+    }
+  }
+  const double wd = warp_sum_f64((double)d);
+  const float wpc = warp_sum_up(pc);
+  double wr = 0.0;
+  float wS = 0.f;
+  if (kRecompute) { wr = warp_sum_f64((double)r); wS = warp_sum_up(S); }
+  if (lane == 0) { sh.part_d[warp] = wd; sh.part_pc[warp] = wpc; sh.part_r[warp] = wr; sh.part_S[warp] = wS; }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double dsum = 0.0, rsum = 0.0;
+  float Pc = 0.f, Sx = 0.f;
+  for (int w = 0; w < kResolveWarps; ++w) {
+    dsum += sh.part_d[w]; rsum += sh.part_r[w];
+    Pc = __fadd_ru(Pc, sh.part_pc[w]); Sx = __fadd_ru(Sx, sh.part_S[w]);
+  }
+  const float g = gamma32_up((float)K, p.u_acc);
+  const float g24 = gamma32_up((float)K, 0x1p-24f);
+  const float genc = gamma32_up((float)BM, 0x1p-24f);  // rounding of e^T A, a binary32 sum over 128 rows
+  double cpred = (double)p.alpha * dsum;
+  float cin_abs = 0.f;
+  if (beta_nz) {
+    cpred += (double)p.beta * pe.cin_sum[cidx];
+    cin_abs = pe.cin_abs[cidx];
+  }
+  const double dcol = sh.cref - cpred;
+  // C^c_ref carries the accumulation error gamma_K(u_acc) P_c; C^c (binary32 dot of e^T A
+  // with B) adds gamma_K(2^-24) P_c + 2^-22 P_c, and e^T A itself, a binary32 sum,
+  // gamma_128(2^-24) P_c; the per-warp C_in partial sums carry gamma_31 (binary32).
+  const float prod = __fmul_ru(__fmul_ru(fabsf(p.alpha), Pc), __fadd_ru(__fadd_ru(__fadd_ru(g, g24), 0x1p-22f), genc));
+  const float outp = __fmul_ru(0x1p-23f, __fadd_ru(sh.cref_abs, __fmul_ru(__fmul_ru(fabsf(p.beta), cin_abs), 34.0f)));
+  const double tauc = (double)__fadd_ru(prod, outp);
+  pe.col_delta[cidx] = dcol;
+  pe.col_tau[cidx] = tauc;
+  pe.col_flag[cidx] = (!(fabs(dcol) <= tauc) || isinf(dcol)) ? 1 : 0;
+  if (kRecompute) {
+    const double rec = (double)p.alpha * rsum;
+    const double cij = (double)p.C[gi + gj * p.ldc];
+    // the recomputation is a binary32 dot product: its rounding, gamma_K(2^-24) S, joins the
+    // accumulation's gamma_K(u_acc) S
+    const float te = __fadd_ru(__fmul_ru(__fmul_ru(fabsf(p.alpha), Sx), __fadd_ru(__fadd_ru(g, g24), 0x1p-30f)),
+                               __fmul_ru(0x1p-23f, (float)fabs(cij)));
+    const double dd = cij - rec;
+    pe.elem_flag[cidx] = (!(fabs(dd) <= (double)te) || isinf(dd)) ? 1 : 0;
+  }
 }
 
-// Per block J of `bn` columns: B e over the block for each k, split into three BF16 pieces
-// written to rows J*16 + {0, 1, 2} of the checksum operand (K-contiguous, pitch kpitch),
-// and max_k of the upward |B| sum over the block (maxAbsBe[J]). Streaming, one thread per
-// pair of k.
-__global__ void __launch_bounds__(256) encode_cols_kernel(const uint16_t* B, int64_t ldb, int32_t N, int32_t K,
-                                                           int32_t bn, uint16_t* chk, int64_t kpitch, float* maxAbsBe) {
-  const int J = blockIdx.x;
-  const int n0 = J * bn;
-  const int nJ = min(bn, N - n0);
-  const int64_t k = (int64_t)blockIdx.y * ENC_KC + 2 * threadIdx.x;
-  float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, a0 = 0.f, a1 = 0.f;
-  if (k < K) {
-    for (int j = 0; j < nJ; ++j) {
-      float x0, x1;
-      load_pair(B + (int64_t)(n0 + j) * ldb, k, K, x0, x1);
-      neumaier(s0, c0, x0);
-      neumaier(s1, c1, x1);
-      a0 = __fadd_ru(a0, fabsf(x0));
-      a1 = __fadd_ru(a1, fabsf(x1));
-    }
-    auto split_store = [&](float s, float c, int64_t kk) {
-      // three bfloat16 pieces, each the nearest bfloat16 of the remainder of s + c
-      const float x = s + c;
-      const float xr = c - (x - s);
-      const __nv_bfloat16 h = __float2bfloat16_rn(x);
-      const float r1 = (x - __bfloat162float(h)) + xr;
-      const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-      const float r2 = r1 - __bfloat162float(m);
-      const __nv_bfloat16 l = __float2bfloat16_rn(r2);
-      chk[(int64_t)(J * CHK_ROWS + 0) * kpitch + kk] = __bfloat16_as_ushort(h);
-      chk[(int64_t)(J * CHK_ROWS + 1) * kpitch + kk] = __bfloat16_as_ushort(m);
-      chk[(int64_t)(J * CHK_ROWS + 2) * kpitch + kk] = __bfloat16_as_ushort(l);
-    };
-    split_store(s0, c0, k);
-    if (k + 1 < K) split_store(s1, c1, k + 1);
+// Classification of one mismatching tile (Section V.A locate, Section VI.C correct):
+// one row and one column mismatching locate the error; one row and no column with beta == 0
+// falls back to the row recompute; no column otherwise means a fault in the checksum path
+// (C kept); anything else is uncorrectable. The located element is corrected from the row
+// checksum, C(i,j) = C^r(i) - sum_{j' != j} C(i,j'): equal to C(i,j) - delta_row in exact
+// arithmetic, and it never touches the erroneous value.
+__device__ void resolve_tile(const TcParams& p, TcPendingEntry& pe, ResolveShared& sh, int mt, int nt, int m0,
+                             int n0, int nJ, bool beta_nz) {
+  const int c = threadIdx.x, lane = threadIdx.x & 31;
+  if (c == 0) { sh.first_col = INT_MAX; sh.first_elem = INT_MAX; }
+  __syncthreads();
+  const bool cf = c < nJ && __ldcg(&pe.col_flag[c]) != 0;
+  if (cf) atomicMin(&sh.first_col, c);
+  const int nc = __syncthreads_count(cf);
+  const int nr = pe.nr;
+  const bool recompute_row = nr == 1 && nc == 0 && !beta_nz;
+  const bool ef = recompute_row && c < nJ && __ldcg(&pe.elem_flag[c]) != 0;
+  if (ef) atomicMin(&sh.first_elem, c);
+  const int ne = __syncthreads_count(ef);
+  int located = -1;
+  if (nr == 1 && nc == 1) located = sh.first_col;
+  else if (recompute_row && ne == 1) located = sh.first_elem;
+  if (c >= 32) return;
+  const int64_t gi = m0 + pe.first_row;
+  double rest = 0.0;
+  if (located >= 0)
+    for (int j = lane; j < nJ; j += 32)
+      if (j != located) rest += (double)__ldcg(&p.C[gi + (int64_t)(n0 + j) * p.ldc]);
+  rest = warp_sum_f64(rest);
+  if (lane != 0) return;
+  int kind;
+  double before = 0.0, after = 0.0, dcol = 0.0, tcol = 0.0;
+  int64_t gj = -1;
+  if (nc > 0) {
+    gj = n0 + sh.first_col;
+    dcol = __ldcg(&pe.col_delta[sh.first_col]);
+    tcol = __ldcg(&pe.col_tau[sh.first_col]);
   }
-  float mx = fmaxf(k < K ? a0 : 0.f, k + 1 < K ? a1 : 0.f);
+  if (located >= 0) {
+    kind = FT_KIND_CORRECTED;
+    gj = n0 + located;
+    float* cp = p.C + gi + gj * p.ldc;
+    before = (double)__ldcg(cp);
+    const float fixed = (float)(pe.pred_row - rest);
+    *cp = fixed;
+    after = (double)fixed;
+  } else if (nc == 0 && (!recompute_row || ne == 0)) {
+    kind = FT_KIND_CHECKSUM_ONLY;
+  } else {
+    kind = FT_KIND_UNCORRECTABLE;
+  }
+  const int ncols_rep = nc > 0 ? nc : (recompute_row ? ne : 0);
+  tc_record(p, kind, mt, nt, gi, gj, pe.delta_row, dcol, pe.tau_row, tcol, before, after, nr, ncols_rep);
+  count_kind(p, kind);
+}
+
+__global__ void __launch_bounds__(kResolveWarps * 32) tc_resolve_kernel(const __grid_constant__ TcParams p) {
+  __shared__ ResolveShared sh;
+  const unsigned npend = min(*reinterpret_cast<volatile const unsigned*>(&p.pend->count), (unsigned)kTcPendCap);
+  const int items = (int)npend * kResolveItems;
+  const bool beta_nz = p.beta != 0.0f;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    TcPendingEntry& pe = p.pend->e[item / kResolveItems];
+    const int cidx = item % kResolveItems;
+    const int mt = pe.mt, nt = pe.nt;
+    const int m0 = mt * BM, n0 = nt * kTcBNProt;
+    const int nI = min(BM, p.M - m0), nJ = min(kTcBNProt, p.N - n0);
+    if (cidx < nJ) {
+      if (pe.nr == 1 && !beta_nz) resolve_column<true>(p, pe, sh, mt, m0, n0, nI, cidx, beta_nz);
+      else resolve_column<false>(p, pe, sh, mt, m0, n0, nI, cidx, beta_nz);
+    }
+    if (threadIdx.x == 0) {
+      __threadfence();  // this column's results before the arrival on the tile counter
+      sh.last = (atomicAdd(&pe.done, 1u) == (unsigned)(kResolveItems - 1)) ? 1 : 0;
+    }
+    __syncthreads();
+    if (sh.last) {
+      __threadfence();
+      resolve_tile(p, pe, sh, mt, nt, m0, n0, nJ, beta_nz);
+    }
+    __syncthreads();  // the shared state is reused by the next item
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Encode pre-pass (bandwidth-bound): one read of A and one read of B. Kernel-frame A is
+// M x K and B is K x N, both K-contiguous, so each is a set of K-contiguous lines: the
+// rows of A, the columns of B. A CTA takes a block of L lines (the 128 rows of a tile of
+// A, the 240 columns of a tile of B) and ENC_KC consecutive k. Lane l of warp w loads
+// k0 + 8l .. k0 + 8l + 7 (one 16-byte load per line) of lines w, w + 8, w + 16, ...; the
+// eight warps' partial sums meet in shared memory.
+// Sums over a block are plain binary32 sums: their rounding, at most gamma_L(2^-24) times
+// the sum of magnitudes in any order, is a term of the thresholds. Sums of magnitudes round
+// upward, so they bound the exact sums.
+// ---------------------------------------------------------------------------------------
+constexpr int ENC_KC = 256;   // k per CTA: 32 lanes x 8
+constexpr int ENC_WARPS = 8;
+
+// Eight consecutive bfloat16 of one line from k (a multiple of 8), zero at and beyond K.
+// The 16-byte load is aligned: leading dimensions are multiples of 8 elements and base
+// addresses 16-byte aligned (both required by the tensor maps).
+__device__ __forceinline__ uint4 load8_bf16(const uint16_t* line, int64_t k, int32_t K) {
+  if (k + 8 <= K) return *reinterpret_cast<const uint4*>(line + k);
+  uint32_t w[4] = {0u, 0u, 0u, 0u};
+  for (int q = 0; q < 8; ++q)
+    if (k + q < K) w[q >> 1] |= (uint32_t)line[k + q] << (16 * (q & 1));
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Lane l holds la[u], a partial sum for line u of a group of 8 lines. Returns the upward
+// sum over the 32 lanes of line (l >> 2): recursive halving, 9 shuffles.
+__device__ __forceinline__ float reduce_scatter8_up(const float (&la)[8], int lane) {
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+  float v4[4], v2[2];
 #pragma unroll
-  for (int w = 16; w >= 1; w >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, w));
-  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned int*>(&maxAbsBe[J]), __float_as_uint(mx));
+  for (int j = 0; j < 4; ++j) {
+    const float keep = h16 ? la[4 + j] : la[j], send = h16 ? la[j] : la[4 + j];
+    v4[j] = __fadd_ru(keep, __shfl_xor_sync(0xffffffffu, send, 16));
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const float keep = h8 ? v4[2 + j] : v4[j], send = h8 ? v4[j] : v4[2 + j];
+    v2[j] = __fadd_ru(keep, __shfl_xor_sync(0xffffffffu, send, 8));
+  }
+  float v = __fadd_ru(h4 ? v2[1] : v2[0], __shfl_xor_sync(0xffffffffu, h4 ? v2[0] : v2[1], 4));
+  v = __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, 2));
+  return __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, 1));
+}
+
+struct EncArgs {
+  const uint16_t* X; int64_t ld;
+  int32_t nlines, K, L;
+  int32_t nclear;          // rows pass: entries of maxAbsBe to zero before the columns pass
+  float* sum;              // rows pass: [nblocks][pitch] e^T A per block
+  float* abs_sum;          // rows pass: [nblocks][pitch] upward sum_{i in block} |A(i,k)|
+  int64_t pitch;
+  TcPending* pend;         // rows pass: its tile count is zeroed before the GEMM
+  float* line_part;        // rows pass: [nkc][M] upward sum of |A(i,k)| over one k-chunk
+  float* maxAbsBe;         // [nblocks of B]
+  uint16_t* chk; int64_t kpitch;  // columns pass: pieces of B e, rows J*16 + {0, 1, 2}; rows 3..15 zero
+};
+
+template <bool kRowsOfA>
+__global__ void __launch_bounds__(256) encode_kernel(EncArgs g) {
+  __shared__ float red_s[ENC_WARPS][ENC_KC];
+  __shared__ float red_a[ENC_WARPS][ENC_KC];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int blk = blockIdx.x, kc = blockIdx.y;
+  const int64_t line0 = (int64_t)blk * g.L;
+  const int nI = (int)min((int64_t)g.L, (int64_t)g.nlines - line0);
+  const int64_t k = (int64_t)kc * ENC_KC + lane * 8;
+  float s[8], a[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) { s[q] = 0.f; a[q] = 0.f; }
+  const int T = (nI + ENC_WARPS - 1) / ENC_WARPS;  // lines per warp, rounded up
+  for (int t0 = 0; t0 < T; t0 += 8) {
+    uint4 raw[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int l = warp + ENC_WARPS * (t0 + u);
+      raw[u] = (l < nI && k < g.K) ? load8_bf16(g.X + (line0 + l) * g.ld, k, g.K) : make_uint4(0u, 0u, 0u, 0u);
+    }
+    float la[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const uint32_t ws[4] = {raw[u].x, raw[u].y, raw[u].z, raw[u].w};
+      float lsum = 0.f;
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const float x0 = __uint_as_float(ws[h] << 16), x1 = __uint_as_float(ws[h] & 0xffff0000u);
+        s[2 * h] += x0;
+        s[2 * h + 1] += x1;
+        a[2 * h] = __fadd_ru(a[2 * h], fabsf(x0));
+        a[2 * h + 1] = __fadd_ru(a[2 * h + 1], fabsf(x1));
+        if (kRowsOfA) lsum = __fadd_ru(lsum, __fadd_ru(fabsf(x0), fabsf(x1)));
+      }
+      la[u] = lsum;
+    }
+    if (kRowsOfA) {
+      const float v = reduce_scatter8_up(la, lane);
+      const int l = warp + ENC_WARPS * (t0 + (lane >> 2));
+      if ((lane & 3) == 0 && l < nI) g.line_part[(int64_t)kc * g.nlines + line0 + l] = v;
+    }
+  }
+  *reinterpret_cast<float4*>(&red_s[warp][lane * 8]) = make_float4(s[0], s[1], s[2], s[3]);
+  *reinterpret_cast<float4*>(&red_s[warp][lane * 8 + 4]) = make_float4(s[4], s[5], s[6], s[7]);
+  *reinterpret_cast<float4*>(&red_a[warp][lane * 8]) = make_float4(a[0], a[1], a[2], a[3]);
+  *reinterpret_cast<float4*>(&red_a[warp][lane * 8 + 4]) = make_float4(a[4], a[5], a[6], a[7]);
+  __syncthreads();
+  const int tk = threadIdx.x;
+  float S = 0.f, Aab = 0.f;
+#pragma unroll
+  for (int w = 0; w < ENC_WARPS; ++w) { S += red_s[w][tk]; Aab = __fadd_ru(Aab, red_a[w][tk]); }
+  const int64_t kk = (int64_t)kc * ENC_KC + tk;
+  if (kRowsOfA) {
+    if (kk < g.K) {
+      g.sum[(int64_t)blk * g.pitch + kk] = S;
+      g.abs_sum[(int64_t)blk * g.pitch + kk] = Aab;
+    }
+    if (blk == 0 && kc == 0) {
+      for (int j = tk; j < g.nclear; j += blockDim.x) g.maxAbsBe[j] = 0.f;
+      if (tk == 0) g.pend->count = 0u;
+    }
+  } else {
+    if (kk < g.K) {
+      // three bfloat16 pieces, each the nearest bfloat16 of what the previous ones leave:
+      // together they hold the binary32 sum exactly (8 + 8 + 8 significand bits)
+      const __nv_bfloat16 h = __float2bfloat16_rn(S);
+      const float r1 = S - __bfloat162float(h);
+      const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(m));
+      uint16_t* col = g.chk + (int64_t)blk * CHK_ROWS * g.kpitch + kk;
+      col[0] = __bfloat16_as_ushort(h);
+      col[g.kpitch] = __bfloat16_as_ushort(m);
+      col[2 * g.kpitch] = __bfloat16_as_ushort(lo);
+#pragma unroll
+      for (int r = 3; r < CHK_ROWS; ++r) col[r * g.kpitch] = 0;
+    }
+    float mx = kk < g.K ? Aab : 0.f;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, w));
+    if (lane == 0) atomicMax(reinterpret_cast<unsigned int*>(&g.maxAbsBe[blk]), __float_as_uint(mx));
+  }
+}
+
+// rowAbsA[i] = upward sum over the k-chunks of the per-chunk partial sums.
+__global__ void __launch_bounds__(256) row_abs_finalize_kernel(const float* line_part, int32_t M, int32_t nkc,
+                                                                float* rowAbsA) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  float a = 0.f;
+  for (int c = 0; c < nkc; ++c) a = __fadd_ru(a, line_part[(int64_t)c * M + i]);
+  rowAbsA[i] = a;
 }
 
 }  // namespace
 
 size_t tc_workspace_bytes(int32_t M, int32_t N, int32_t K) {
   const int64_t nMb = (M + BM - 1) / BM, nNb = (N + kTcBNProt - 1) / kTcBNProt;
-  const int64_t kpitch = (K + 7) / 8 * 8;
+  const int64_t kpitch = (K + 7) / 8 * 8, nkc = (K + ENC_KC - 1) / ENC_KC;
   auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
-  return up(nNb * CHK_ROWS * kpitch * 2) + up(nMb * (int64_t)K * 8) + up(nMb * (int64_t)K * 4) + up(M * 4) + up(nNb * 4);
+  return up(nNb * CHK_ROWS * kpitch * 2) + up(nMb * kpitch * 4) + up(nMb * kpitch * 4) + up(M * 4) +
+         up(nNb * 4) + up(nkc * M * 4) + up((int64_t)sizeof(TcPending));
 }
 
 TcWorkspace tc_workspace_carve(void* base, int32_t M, int32_t N, int32_t K) {
   const int64_t nMb = (M + BM - 1) / BM, nNb = (N + kTcBNProt - 1) / kTcBNProt;
-  const int64_t kpitch = (K + 7) / 8 * 8;
+  const int64_t kpitch = (K + 7) / 8 * 8, nkc = (K + ENC_KC - 1) / ENC_KC;
   auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
   char* c = static_cast<char*>(base);
   TcWorkspace w;
   w.chk = reinterpret_cast<uint16_t*>(c); c += up(nNb * CHK_ROWS * kpitch * 2);
   w.kpitch = kpitch;
-  w.sA = reinterpret_cast<float2*>(c); c += up(nMb * (int64_t)K * 8);
-  w.absSA = reinterpret_cast<float*>(c); c += up(nMb * (int64_t)K * 4);
+  w.sA = reinterpret_cast<float*>(c); c += up(nMb * kpitch * 4);
+  w.absSA = reinterpret_cast<float*>(c); c += up(nMb * kpitch * 4);
   w.rowAbsA = reinterpret_cast<float*>(c); c += up(M * 4);
   w.maxAbsBe = reinterpret_cast<float*>(c); c += up(nNb * 4);
+  w.rowPart = reinterpret_cast<float*>(c); c += up(nkc * M * 4);
+  w.pend = reinterpret_cast<TcPending*>(c); c += up((int64_t)sizeof(TcPending));
   w.bytes = static_cast<size_t>(c - static_cast<char*>(base));
   return w;
 }
 
-cudaError_t launch_tc_encode(const TcParams& p, const TcWorkspace& w, void* ws_base, cudaStream_t st) {
+cudaError_t launch_tc_encode(const TcParams& p, const TcWorkspace& w, cudaStream_t st) {
   const int nMb = (p.M + BM - 1) / BM, nNb = (p.N + kTcBNProt - 1) / kTcBNProt, nkc = (p.K + ENC_KC - 1) / ENC_KC;
-  // zero the checksum operand (its rows 3..15 stay zero) and the block maxima
-  cudaError_t e = cudaMemsetAsync(ws_base, 0, w.bytes, st);
-  if (e != cudaSuccess) return e;
-  encode_rows_kernel<<<dim3(nMb, nkc), 256, 0, st>>>(static_cast<const uint16_t*>(p.A), p.lda, p.M, p.K, w.sA,
-                                                      w.absSA);
-  row_abs_kernel<<<(p.M + 7) / 8, 256, 0, st>>>(static_cast<const uint16_t*>(p.A), p.lda, p.M, p.K, w.rowAbsA);
-  encode_cols_kernel<<<dim3(nNb, nkc), 256, 0, st>>>(static_cast<const uint16_t*>(p.B), p.ldb, p.N, p.K, kTcBNProt,
-                                                      w.chk, w.kpitch, w.maxAbsBe);
+  EncArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.X = static_cast<const uint16_t*>(p.A); g.ld = p.lda; g.nlines = p.M; g.K = p.K; g.L = BM;
+  g.nclear = nNb; g.sum = w.sA; g.abs_sum = w.absSA; g.line_part = w.rowPart; g.maxAbsBe = w.maxAbsBe;
+  g.pitch = w.kpitch; g.pend = w.pend;
+  encode_kernel<true><<<dim3(nMb, nkc), ENC_WARPS * 32, 0, st>>>(g);
+  row_abs_finalize_kernel<<<(p.M + 255) / 256, 256, 0, st>>>(w.rowPart, p.M, nkc, w.rowAbsA);
+  std::memset(&g, 0, sizeof(g));
+  g.X = static_cast<const uint16_t*>(p.B); g.ld = p.ldb; g.nlines = p.N; g.K = p.K; g.L = kTcBNProt;
+  g.maxAbsBe = w.maxAbsBe; g.chk = w.chk; g.kpitch = w.kpitch;
+  encode_kernel<false><<<dim3(nNb, nkc), ENC_WARPS * 32, 0, st>>>(g);
   return cudaGetLastError();
 }
 
@@ -688,6 +855,9 @@ cudaError_t launch_tc_gemm(const TcParams& p, const CUtensorMap* tmA, const CUte
     e = cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     tc_gemm_kernel<true><<<grid, NTHREADS, smem, st>>>(*tmA, *tmB, *tmChk, p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    tc_resolve_kernel<<<2 * sms, kResolveWarps * 32, 0, st>>>(p);
   } else {
     e = cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -15,6 +15,28 @@ constexpr int kTcBN = 256;       // data columns per tile, unprotected (= MMA N)
 constexpr int kTcBNProt = 240;   // data columns per tile, protected: B^r = [B, Be] fills N = 256
 constexpr int kTcChkRows = 16;   // rows of the checksum operand per column block (pieces of B e in 0..2)
 
+// A tile whose row checksums mismatch, handed from the GEMM's epilogue to the resolve pass
+// (lazy column side, row recompute, classification and correction), which runs after
+// every tile is stored. Per-column results are written by the resolve pass.
+constexpr int kTcPendCap = 64;   // mismatching tiles per call the resolve pass can locate
+struct TcPendingEntry {
+  int32_t mt, nt, nr, first_row;
+  double delta_row, tau_row, pred_row;
+  uint32_t done;                 // column groups finished (the last one classifies)
+  int32_t pad_;
+  double cin_sum[kTcBNProt];     // beta != 0: sum_i C_in(i,j) over the tile (C_in is overwritten)
+  float cin_abs[kTcBNProt];      //            upward sum_i |C_in(i,j)|
+  double col_delta[kTcBNProt];   // C^c_ref - C^c per column
+  double col_tau[kTcBNProt];
+  uint8_t col_flag[kTcBNProt];   // column mismatches
+  uint8_t elem_flag[kTcBNProt];  // row recompute: element mismatches of the flagged row
+};
+struct TcPending {
+  uint32_t count;                // tiles pushed (may exceed kTcPendCap; the rest are not located)
+  uint32_t pad_[63];
+  TcPendingEntry e[kTcPendCap];
+};
+
 struct TcParams {
   int32_t M, N, K;
   int32_t swap_report;
@@ -26,24 +48,28 @@ struct TcParams {
   float* C; int64_t ldc;
   const float* rowAbsA;          // [M]        upward sum_k |A(i,k)|
   const float* maxAbsBe;         // [nNb]      max_k upward sum_{j in block} |B(k,j)|
-  const float2* sA;              // [nMb][K]   e^T A per 128-row block, hi + lo
-  const float* absSA;            // [nMb][K]   upward sum_{i in block} |A(i,k)|
+  const float* sA;               // [nMb][sa_pitch] e^T A per 128-row block (binary32 sum)
+  const float* absSA;            // [nMb][sa_pitch] upward sum_{i in block} |A(i,k)|
+  int64_t sa_pitch;              // multiple of 8 (32-byte aligned rows)
+  TcPending* pend;
   ft_report_t* report;
   InjectList inj;
 };
 
 struct TcWorkspace {
   uint16_t* chk;  int64_t kpitch;
-  float2* sA;
+  float* sA;
   float* absSA;
   float* rowAbsA;
   float* maxAbsBe;
+  float* rowPart;                // [nkc][M] per-k-chunk partial sums of |A(i,k)|
+  TcPending* pend;
   size_t bytes;
 };
 
 size_t tc_workspace_bytes(int32_t M, int32_t N, int32_t K);
 TcWorkspace tc_workspace_carve(void* base, int32_t M, int32_t N, int32_t K);
-cudaError_t launch_tc_encode(const TcParams& p, const TcWorkspace& w, void* ws_base, cudaStream_t st);
+cudaError_t launch_tc_encode(const TcParams& p, const TcWorkspace& w, cudaStream_t st);
 cudaError_t launch_tc_gemm(const TcParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmChk,
                            bool ft, cudaStream_t st);
 

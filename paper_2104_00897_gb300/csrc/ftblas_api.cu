@@ -322,12 +322,13 @@ int gemm_ex_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   if (cudaMallocAsync(&ws, wsb, st) != cudaSuccess) return FTBLAS_STATUS_ALLOC_FAILED;
   TcWorkspace w = tc_workspace_carve(ws, p.M, p.N, p.K);
   p.rowAbsA = w.rowAbsA; p.maxAbsBe = w.maxAbsBe; p.sA = w.sA; p.absSA = w.absSA;
+  p.sa_pitch = w.kpitch; p.pend = w.pend;
   const int64_t nNb = (f.N + kTcBNProt - 1) / kTcBNProt;
   if (!make_map_b16_sw128(&tmC, w.chk, K, nNb * kTcChkRows, w.kpitch, 64, kTcChkRows)) {
     cudaFreeAsync(ws, st);
     return FTBLAS_STATUS_NOT_SUPPORTED;
   }
-  int rc = record_cuda(launch_tc_encode(p, w, ws, st));
+  int rc = record_cuda(launch_tc_encode(p, w, st));
   if (rc == 0) rc = record_cuda(launch_tc_gemm(p, &tmA, &tmB, &tmC, true, st));
   cudaFreeAsync(ws, st);
   return rc;
@@ -416,10 +417,11 @@ int gemm_bf16_ft_with_workspace(int layout, int ta, int tb, int64_t M, int64_t N
   g_last_used_tma = 1;
   TcWorkspace w = tc_workspace_carve(ws, p.M, p.N, p.K);
   p.rowAbsA = w.rowAbsA; p.maxAbsBe = w.maxAbsBe; p.sA = w.sA; p.absSA = w.absSA;
+  p.sa_pitch = w.kpitch; p.pend = w.pend;
   const int64_t nNb = (f.N + kTcBNProt - 1) / kTcBNProt;
   if (!make_map_b16_sw128(&tmC, w.chk, K, nNb * kTcChkRows, w.kpitch, 64, kTcChkRows))
     return FTBLAS_STATUS_NOT_SUPPORTED;
-  int rc = record_cuda(launch_tc_encode(p, w, ws, st));  // clears the carved workspace first
+  int rc = record_cuda(launch_tc_encode(p, w, st));  // writes every workspace entry the GEMM reads
   if (rc == 0) rc = record_cuda(launch_tc_gemm(p, &tmA, &tmB, &tmC, true, st));
   return rc;
 }
