@@ -55,8 +55,12 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-second-engine", action="store_true")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16 tensor-core measurement")
+    ap.add_argument("--no-fp8", action="store_true", help="skip the FP8 (E4M3) tensor-core measurement")
+    ap.add_argument("--fp8-size", type=int, default=16384, help="M = N = K of the FP8 measurement")
     ap.add_argument("--bf16-only", action="store_true",
                     help="measure only the BF16 tensor-core form (for profiling); prints its own JSON line")
+    ap.add_argument("--fp8-only", action="store_true",
+                    help="measure only the FP8 tensor-core form (for profiling); prints its own JSON line")
     return ap.parse_args()
 
 
@@ -167,32 +171,53 @@ def oracle_sample(n, A, B, Cin, n_tiles, seed_tiles=7):
 
 
 # ------------------------------------------------------------------ BF16 tensor-core form
-def run_bf16(args, dev, n, steps, warmup, fp64_tflops):
-    """The BF16 form (config 3): A, B N(0,1) with rows of A scaled by 2^u, u in [-8, 8],
-    FP32 accumulation on the tensor cores, FP32 C, FP64 checksum comparison. Reports FT and
-    unprotected TFLOP/s, the speedup over FP64 FT-DGEMM, the error against the FP64 product
-    on sampled rows, and the fraction of injected output errors 2^p |C| detected per p."""
+def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
+    """The tensor-core forms. kind "bf16" (config 3): A, B N(0,1) with rows of A scaled by
+    2^u, u in [-8, 8], BF16. kind "fp8" (config 5b): A, B N(0,1) quantised per tensor to
+    E4M3 (scale = amax / 448). Both accumulate in FP32 on the tensor cores, store FP32 C and
+    compare checksums in FP64. Reports FT and unprotected TFLOP/s, the speedup over FP64
+    FT-DGEMM, the error against the FP64 product of the same operands on a sampled block, and
+    the fraction of injected output errors 2^p |C| corrected per p."""
     import torch
 
     import oracle as O
     import paper_2104_00897_gb300 as fb
     import synth as S
 
-    seed = SEED + 3
-    A = S.normal_matrix(seed, 0, n, n) * S.pow2_row_scales(seed, 5, n)[:, None]
-    B = S.normal_matrix(seed, 1, n, n)
-    abits = S.to_bf16_bits(A)
-    bbits = S.to_bf16_bits(B)
-    # column-major call with A transposed (stored K x M) and B not: both K-contiguous
-    dA = torch.from_numpy(np.ascontiguousarray(abits).view(np.int16).ravel()).to(dev)       # A^T col-major == A row-major
-    dB = torch.from_numpy(np.ascontiguousarray(bbits.T).view(np.int16).ravel()).to(dev)     # B col-major
+    threads = max(1, min(16, os.cpu_count() or 1))
+    fp8 = kind == "fp8"
+    seed = SEED + (5 if fp8 else 3)
+    A = S.normal_matrix(seed, 0, n, n, threads=threads)
+    if not fp8:
+        A *= S.pow2_row_scales(seed, 5, n)[:, None]
+    B = S.normal_matrix(seed, 1, n, n, threads=threads)
+    if fp8:
+        sa = float(np.float32(np.max(np.abs(A)) / 448.0))
+        sb = float(np.float32(np.max(np.abs(B)) / 448.0))
+        # column-major call with A transposed (stored K x M, i.e. A row-major) and B not
+        abits = S.map_elementwise(lambda x: S.to_e4m3_bits(x / sa), A, np.uint8, threads)
+        bbits_t = S.map_elementwise(lambda x: S.to_e4m3_bits(x / sb), np.ascontiguousarray(B.T), np.uint8, threads)
+        dA = torch.from_numpy(abits.ravel()).to(dev)
+        dB = torch.from_numpy(bbits_t.ravel()).to(dev)
+        dS = torch.tensor([sa, sb], dtype=torch.float32, device=dev)
+        dtype, sa_ptr, sb_ptr = fb.R_8F_E4M3, dS.data_ptr(), dS.data_ptr() + 4
+        deq = lambda bits, sc: sc * S.e4m3_bits_to_f64(bits)
+    else:
+        abits = S.map_elementwise(S.to_bf16_bits, A, np.uint16, threads)
+        bbits_t = S.map_elementwise(S.to_bf16_bits, np.ascontiguousarray(B.T), np.uint16, threads)
+        dA = torch.from_numpy(abits.view(np.int16).ravel()).to(dev)
+        dB = torch.from_numpy(bbits_t.view(np.int16).ravel()).to(dev)
+        dtype, sa_ptr, sb_ptr = fb.R_16BF, None, None
+        deq = lambda bits, sc: S.bf16_bits_to_f64(bits)
+        sa = sb = 1.0
+    del A, B
     dC = torch.zeros(n * n, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream(dev).cuda_stream
     flops = 2.0 * n ** 3
 
     def call(protect, rep=None):
-        a = (O.COL_MAJOR, O.TRANS, O.NO_TRANS, n, n, n, 1.0, dA.data_ptr(), fb.R_16BF, n, dB.data_ptr(), fb.R_16BF, n,
-             0.0, dC.data_ptr(), fb.R_32F, n, fb.R_32F, None, None, st)
+        a = (O.COL_MAJOR, O.TRANS, O.NO_TRANS, n, n, n, 1.0, dA.data_ptr(), dtype, n, dB.data_ptr(), dtype, n,
+             0.0, dC.data_ptr(), fb.R_32F, n, fb.R_32F, sa_ptr, sb_ptr, st)
         if protect:
             fb.check(fb.ftblas_gemm_ex(*a, rep.data_ptr() if rep is not None else None), "ftblas_gemm_ex")
         else:
@@ -200,8 +225,11 @@ def run_bf16(args, dev, n, steps, warmup, fp64_tflops):
 
     def timed(protect, inject):
         if inject:
-            fb.ftblas_set_injection(fb.make_injection(seed=seed, site=fb.SITE_OUTPUT, mode=fb.MODE_ADD_REL, log2_lo=8,
-                                                      log2_hi=12, every_n_launches=1, errors_per_launch=1))
+            # output errors of 2^p |C|, p above the rigorous threshold's reach (2^8 for BF16 at
+            # K = 8192; 2^12 for FP8 at K = 16384, whose accumulation unit is taken as 2^-22)
+            lo = 12 if fp8 else 8
+            fb.ftblas_set_injection(fb.make_injection(seed=seed, site=fb.SITE_OUTPUT, mode=fb.MODE_ADD_REL, log2_lo=lo,
+                                                      log2_hi=lo + 4, every_n_launches=1, errors_per_launch=1))
         else:
             fb.ftblas_set_injection(None)
         reps = [fb.new_report(dev) for _ in range(steps)]
@@ -223,13 +251,15 @@ def run_bf16(args, dev, n, steps, warmup, fp64_tflops):
     ms_na, _, _ = timed(False, False)
     ms_ft, det0, _ = timed(True, False)
     ms_inj, det_inj, corr_inj = timed(True, True)
-    # accuracy against the FP64 product of the same BF16 values, on sampled rows
+    # accuracy against the FP64 product of the same operands, on a sampled 4 x 64 block
     call(True)
     torch.cuda.synchronize(dev)
     rows = np.unique(S.randint(seed, 9, 4, 0, n - 1))
-    C = dC.view(n, n).t()[torch.as_tensor(rows, device=dev)].double().cpu().numpy()
-    A64 = S.bf16_bits_to_f64(abits[rows, :])
-    B64 = S.bf16_bits_to_f64(bbits)
+    cols = np.unique(S.randint(seed, 10, 64, 0, n - 1))
+    Cfull = dC.view(n, n).t()
+    C = Cfull[torch.as_tensor(rows, device=dev)][:, torch.as_tensor(cols, device=dev)].double().cpu().numpy()
+    A64 = deq(abits[rows, :], sa)
+    B64 = deq(bbits_t[cols, :], sb).T
     ref = A64 @ B64
     scale = np.abs(A64) @ np.abs(B64)
     err_norm = float(np.max(np.abs(C - ref) / scale))
@@ -249,17 +279,21 @@ def run_bf16(args, dev, n, steps, warmup, fp64_tflops):
             hits += int(fb.report_from_device(rep).corrected)
         det_map[str(p)] = hits / trials
     fb.ftblas_set_injection(None)
+    u = "2^-22" if fp8 else "2^-23"
+    values = ("N(0,1) quantised per tensor to E4M3 (scale = amax/448)" if fp8
+              else "N(0,1), A rows scaled by 2^u (u in [-8, 8])")
     return {
-        "workload": f"ft_gemm_bf16_fp32acc_{n}x{n}x{n}, A rows scaled by 2^u (u in [-8, 8]), N(0,1)",
+        "workload": f"ft_gemm_{kind}_fp32acc_{n}x{n}x{n}, {values}",
         "ft_tflops": flops / ms_ft / 1e9, "ft_tflops_injected": flops / ms_inj / 1e9,
         "noabft_tflops": flops / ms_na / 1e9,
         "abft_overhead_pct": 100.0 * (ms_ft / ms_na - 1.0),
         "speedup_over_fp64_ft": (flops / ms_ft / 1e9) / fp64_tflops if fp64_tflops else None,
         "false_alarms_clean": det0, "injected": steps, "corrected": corr_inj, "detected": det_inj,
-        "error_vs_fp64": {"max_over_sum_abs_ab": err_norm, "median_rel": err_rel, "rows_sampled": int(len(rows)),
-                          "note": "C - (A B computed in binary64 from the same BF16 values)"},
+        "error_vs_fp64": {"max_over_sum_abs_ab": err_norm, "median_rel": err_rel,
+                          "sampled": f"{len(rows)} rows x {len(cols)} columns",
+                          "note": f"C - (A B computed in binary64 from the same {kind.upper()} operands)"},
         "detection_map_rel_log2": det_map,
-        "threshold": "rigorous: gamma_K(2^-23) |alpha| (sum_k|A(i,k)|)(max_k sum_j|B(k,j)|) + 2^-23 (sum|C|)",
+        "threshold": f"rigorous: gamma_K({u}) |alpha| (sum_k|A(i,k)|)(max_k sum_j|B(k,j)|) (1 + s) + 2^-23 (sum|C|)",
     }
 
 
@@ -304,9 +338,11 @@ def run_ours(args, rank, world, dist):
     dev = torch.device("cuda", local)
     fb.load()
     n = args.size
-    if args.bf16_only:
+    if args.bf16_only or args.fp8_only:
         if rank == 0:
-            print(json.dumps({"bf16": run_bf16(args, dev, n, args.steps, args.warmup, None)}), flush=True)
+            kind = "bf16" if args.bf16_only else "fp8"
+            size = n if args.bf16_only else args.fp8_size
+            print(json.dumps({kind: run_tc(args, dev, kind, size, args.steps, args.warmup, None)}), flush=True)
         return 0
     flops_step = 2.0 * n * n * n
     A, B, Cin = gen_inputs(n, SEED + rank)
@@ -445,10 +481,12 @@ def run_ours(args, rank, world, dist):
                "sample": f"16 seeded {TILE}x{TILE} output tiles of the {n}^3 problem (full K, checksums included), "
                          f"{dt:.1f} s"}
 
-    bf16 = None
+    bf16 = fp8 = None
+    fp64_ft = flops_step * args.steps / (results[args.engine]["ft_ms"] / 1e3) / 1e12
     if not args.no_bf16 and rank == 0:
-        fp64_ft = flops_step * args.steps / (results[args.engine]["ft_ms"] / 1e3) / 1e12
-        bf16 = run_bf16(args, dev, n, args.steps, args.warmup, fp64_ft)
+        bf16 = run_tc(args, dev, "bf16", n, args.steps, args.warmup, fp64_ft)
+    if not args.no_fp8 and rank == 0:
+        fp8 = run_tc(args, dev, "fp8", args.fp8_size, args.steps, args.warmup, fp64_ft)
 
     if rank != 0:
         return 0
@@ -494,6 +532,7 @@ def run_ours(args, rank, world, dist):
                      "kernel": "dgemm_kernel (FT, " + args.engine + ")", "kernel_ms": kernel_ms},
         "cpu_baseline": cpu,
         "bf16": bf16,
+        "fp8_e4m3": fp8,
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clocks,

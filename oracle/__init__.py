@@ -20,7 +20,7 @@ NO_TRANS, TRANS = 111, 112
 SITE_ACCUM, SITE_OUTPUT, SITE_CHECKSUM = 1, 2, 3
 MODE_BITFLIP, MODE_ADD_REL = 0, 1
 KIND_CORRECTED, KIND_CHECKSUM_ONLY, KIND_UNCORRECTABLE, KIND_INPUT_NONFINITE = 1, 2, 3, 4
-PREC_FP64, PREC_ACC32 = 0, 1
+PREC_FP64, PREC_ACC32, PREC_ACC32_E4M3 = 0, 1, 2
 U_ACC32 = 2.0 ** -23
 MAX_RECORDS = 256
 

@@ -69,6 +69,11 @@
  * tiles with a row mismatch (the lazy second side of Section V.A). */
 #define OR_PREC_FP64 0
 #define OR_PREC_ACC32 1
+/* ACC32 for FP8 (E4M3) operands: the same arithmetic, with the row checksum's prediction
+ * formed from B e split into sixteen e4m3 pieces instead of three bfloat16 ones, whose
+ * magnitudes sum to at most 1.25 |B e| (1 + 2^-7 for the bfloat16 pieces). */
+#define OR_PREC_ACC32_E4M3 2
+#define IS_ACC32(p) ((p)->precision == OR_PREC_ACC32 || (p)->precision == OR_PREC_ACC32_E4M3)
 
 /* ---------------------------------------------------------------------------------- */
 /* Problem description and results                                                    */
@@ -84,7 +89,8 @@ typedef struct {
   const double* Cin; int64_t ldc;   /* not read when beta == 0 */
   int64_t tile_m, tile_n;           /* verification tile, in rows x columns of C */
   int64_t bk;                       /* k-tile depth (sets the accumulator injection point) */
-  int32_t precision;                /* OR_PREC_FP64, or OR_PREC_ACC32 (binary32 accumulation, binary32 C) */
+  int32_t precision;                /* OR_PREC_FP64, OR_PREC_ACC32 or OR_PREC_ACC32_E4M3 (binary32
+                                       accumulation, binary32 C) */
   int32_t pad2_;
   double u_acc;                     /* OR_PREC_ACC32: unit roundoff of the accumulation */
 } oracle_problem_t;
@@ -205,7 +211,7 @@ int oracle_gemm(const oracle_problem_t* p, double* Cout) {
       } else {
         v = scale_out(p, acc, i, j);
       }
-      if (p->precision == OR_PREC_ACC32) v = round32(v);
+      if (IS_ACC32(p)) v = round32(v);
       Cout[c_index(p->layout, p->ldc, i, j)] = v;
     }
   }
@@ -489,14 +495,15 @@ static void ft_tile(const oracle_problem_t* p, int64_t tr, int64_t tc,
  *   - an accumulator injection flips bit b of the binary32 accumulator after all K products;
  *   - tau uses gamma_K(u_acc) for the product part, with sum_k |A(i,k)| sum_j |B(k,j)|
  *     bounded by (sum_k |A(i,k)|) (max_k sum_j |B(k,j)|) over the tile:
- *       row:    |alpha| P (gamma_K(u_acc) (2 + 2^-7) + 2^-20 + gamma_{tile_n}(2^-24))
+ *       row:    |alpha| P (gamma_K(u_acc) (1 + s) + 2^-20 + gamma_{tile_n}(2^-24))
  *               + 2^-23 (sum_j |C| + |beta| sum_j |C_in|)
  *       column: |alpha| P_c (gamma_K(u_acc) + gamma_K(2^-24) + 2^-22 + gamma_{tile_m}(2^-24))
  *               + 2^-23 (sum_i |C| + 34 |beta| sum_i |C_in|),
  *               P_c = sum_k (sum_{i in tile} |A(i,k)|) |B(k,j)| (exact: it is formed only in the
  *               rare tiles with a row mismatch)
  *     (the row side's prediction is itself a binary32 product of A with B e split into
- *     three pieces; the column side's is a binary32 dot product of e^T A with B; B e and
+ *     pieces whose magnitudes sum to at most s |B e|: s = 1 + 2^-7 for three bfloat16
+ *     pieces, 1.25 for sixteen e4m3 pieces; the column side's is a binary32 dot product of e^T A with B; B e and
  *     e^T A are binary32 sums over the tile, whose rounding in any order is at most
  *     gamma_n(2^-24) times the sum of magnitudes, n the tile width);
  *   - column checksums are formed only when a row mismatches (Section V.A, lazy side);
@@ -553,6 +560,7 @@ static void ft_tile_acc32(const oracle_problem_t* p, int64_t tr, int64_t tc,
   /* gamma_{tile_n}(2^-24) and gamma_{tile_m}(2^-24): rounding of the binary32 sums B e and e^T A */
   const double genc_r = gamma_n((double)p->tile_n * 5.9604644775390625e-08 / 1.1102230246251565e-16);
   const double genc_c = gamma_n((double)p->tile_m * 5.9604644775390625e-08 / 1.1102230246251565e-16);
+  const double piece_sum = (p->precision == OR_PREC_ACC32_E4M3) ? 1.25 : 1.0078125;
   /* Row side, every row. */
   int64_t nr = 0, fr = -1;
   double fr_delta = 0.0, fr_tau = 0.0, fr_pred = 0.0;
@@ -573,7 +581,7 @@ static void ft_tile_acc32(const oracle_problem_t* p, int64_t tr, int64_t tc,
     double Cr_ref = 0.0, R = 0.0;
     for (int64_t jj = 0; jj < nJ; ++jj) { Cr_ref = Cr_ref + T[ii + jj * nI]; R = R + fabs(T[ii + jj * nI]); }
     double P = rowAbsA * maxAbsBe;
-    double tau = fabs(p->alpha) * P * (gK * (2.0 + 0.0078125) + 9.5367431640625e-07 + genc_r) +
+    double tau = fabs(p->alpha) * P * (gK * (1.0 + piece_sum) + 9.5367431640625e-07 + genc_r) +
                  1.1920928955078125e-07 * (R + fabs(p->beta) * Q);
     double d = Cr_ref - Cr;
     if (!(fabs(d) <= tau) || isinf(d)) {
@@ -695,7 +703,7 @@ int oracle_ft_gemm(const oracle_problem_t* p, int64_t n_inj, const oracle_inject
         for (int64_t i = r0; i < r0 + p->tile_m && i < p->M; ++i)
           Cout[c_index(p->layout, p->ldc, i, j)] =
               (p->beta == 0.0) ? 0.0
-                               : (p->precision == OR_PREC_ACC32 ? round32(p->beta * cin_elem(p, i, j))
+                               : (IS_ACC32(p) ? round32(p->beta * cin_elem(p, i, j))
                                                                 : p->beta * cin_elem(p, i, j));
     }
     return 0;
@@ -704,7 +712,7 @@ int oracle_ft_gemm(const oracle_problem_t* p, int64_t n_inj, const oracle_inject
 #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t s = 0; s < nsel; ++s) {
     int64_t t = sel_tiles ? sel_tiles[s] : s;
-    if (p->precision == OR_PREC_ACC32)
+    if (IS_ACC32(p))
       ft_tile_acc32(p, t % tr, t / tr, n_inj, inj, Cout, &res[s]);
     else
       ft_tile(p, t % tr, t / tr, n_inj, inj, Cout, &res[s]);

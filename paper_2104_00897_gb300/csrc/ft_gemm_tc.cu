@@ -29,6 +29,7 @@
 #include <cstring>
 
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "ft_device.cuh"
 #include "ft_internal.h"
@@ -40,7 +41,7 @@ namespace {
 
 constexpr int BM = kTcBM;            // 128 tile rows (TMEM lanes)
 constexpr int BNM = 256;             // MMA N = TMEM columns = B stage rows
-constexpr int BKB = 128;             // k-tile depth in bytes (64 BF16)
+constexpr int BKB = 128;             // k-tile depth in bytes (64 BF16 or 128 E4M3)
 constexpr int STAGES = 4;
 constexpr int NTHREADS = 192;
 constexpr int CHK_ROWS = kTcChkRows;  // 16
@@ -70,6 +71,87 @@ struct __align__(1024) TcSmem {
 
 __device__ __forceinline__ float bf16_to_f32(uint16_t b) { return __uint_as_float(static_cast<uint32_t>(b) << 16); }
 
+__device__ __forceinline__ float e4m3_to_f32(uint8_t b) {
+  return __half2float(__half(__nv_cvt_fp8_to_halfraw(static_cast<__nv_fp8_storage_t>(b), __NV_E4M3)));
+}
+
+// Input element kinds of the tensor-core path.
+//   kBytes     storage bytes per element
+//   kPieces    checksum columns holding the pieces of B e (rows 0 .. kPieces-1 of a block)
+//   kPieceSum  bound of sum_p |piece_p| / |B e| (for the threshold's prediction part)
+// BF16: B e as hi + mid + lo bfloat16 (exact for a binary32 value), scale 1.
+// E4M3: B e as 16 e4m3 pieces with fixed scales 2^(9 - 4p): each piece is the nearest e4m3
+//   of what the previous ones leave (subnormals flushed and carried), so |B e| <= 240 * 448
+//   fits the first piece and the pieces hold B e to far below binary32 resolution.
+template <int KIND> struct Elem;
+template <> struct Elem<0> {
+  static constexpr int kBytes = 2, kPieces = 3;
+  static constexpr float kPieceSum = 1.0078125f;
+  // Eight consecutive elements of one K-contiguous line from k (a multiple of 8), zero
+  // at and beyond K; one 16-byte load (aligned: ld is a multiple of 8 elements, bases
+  // 16-byte aligned).
+  using Raw = uint4;
+  static __device__ __forceinline__ Raw zero() { return make_uint4(0u, 0u, 0u, 0u); }
+  static __device__ __forceinline__ Raw load_raw(const void* line, int64_t k, int32_t K) {
+    const uint16_t* l = static_cast<const uint16_t*>(line);
+    if (k + 8 <= K) return *reinterpret_cast<const uint4*>(l + k);
+    uint32_t t[4] = {0u, 0u, 0u, 0u};
+    for (int q = 0; q < 8; ++q)
+      if (k + q < K) t[q >> 1] |= (uint32_t)l[k + q] << (16 * (q & 1));
+    return make_uint4(t[0], t[1], t[2], t[3]);
+  }
+  static __device__ __forceinline__ void load8(const void* line, int64_t k, int32_t K, float (&x)[8]) {
+    unpack(load_raw(line, k, K), x);
+  }
+  static __device__ __forceinline__ void unpack(const Raw w, float (&x)[8]) {
+    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      x[2 * h] = __uint_as_float(ws[h] << 16);
+      x[2 * h + 1] = __uint_as_float(ws[h] & 0xffff0000u);
+    }
+  }
+  static __device__ __forceinline__ float at(const void* line, int64_t k) {
+    return bf16_to_f32(static_cast<const uint16_t*>(line)[k]);
+  }
+};
+template <> struct Elem<1> {
+  static constexpr int kBytes = 1, kPieces = 16;
+  static constexpr float kPieceSum = 1.25f;
+  // as above with one 8-byte load (ld a multiple of 16 elements)
+  using Raw = uint2;
+  static __device__ __forceinline__ Raw zero() { return make_uint2(0u, 0u); }
+  static __device__ __forceinline__ Raw load_raw(const void* line, int64_t k, int32_t K) {
+    const uint8_t* l = static_cast<const uint8_t*>(line);
+    if (k + 8 <= K) return *reinterpret_cast<const uint2*>(l + k);
+    uint32_t t[2] = {0u, 0u};
+    for (int q = 0; q < 8; ++q)
+      if (k + q < K) t[q >> 2] |= (uint32_t)l[k + q] << (8 * (q & 3));
+    return make_uint2(t[0], t[1]);
+  }
+  static __device__ __forceinline__ void load8(const void* line, int64_t k, int32_t K, float (&x)[8]) {
+    unpack(load_raw(line, k, K), x);
+  }
+  static __device__ __forceinline__ void unpack(const Raw w, float (&x)[8]) {
+    const uint32_t ws[2] = {w.x, w.y};
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) x[4 * h + b] = e4m3_to_f32(static_cast<uint8_t>(ws[h] >> (8 * b)));
+  }
+  static __device__ __forceinline__ float at(const void* line, int64_t k) {
+    return e4m3_to_f32(static_cast<const uint8_t*>(line)[k]);
+  }
+};
+
+// alpha times the per-tensor scales of FP8 operands (device values; absent scales are 1)
+__device__ __forceinline__ float alpha_eff(const TcParams& p) {
+  float a = p.alpha;
+  if (p.a_scale != nullptr) a *= *p.a_scale;
+  if (p.b_scale != nullptr) a *= *p.b_scale;
+  return a;
+}
+
 // Neumaier's compensated summation step (binary32).
 __device__ __forceinline__ void neumaier(float& s, float& c, float x) {
   const float t = s + x;
@@ -96,14 +178,14 @@ __device__ __forceinline__ float warp_sum_plain(float x) {
 
 // alpha * acc + beta * C_in with the accumulator- and output-site injections of the current
 // plan applied (test launches only; kept out of line).
-__device__ __noinline__ float inject_element(const TcParams& p, int64_t gi, int64_t gj, float acc, float cin,
-                                             bool beta_nz) {
+__device__ __noinline__ float inject_element(const TcParams& p, float alpha, int64_t gi, int64_t gj, float acc,
+                                             float cin, bool beta_nz) {
   for (int e = 0; e < p.inj.n; ++e) {
     const InjectPoint& ip = p.inj.p[e];
     if (ip.i == gi && ip.j == gj && ip.site == kSiteAccum && ip.mode == FT_MODE_BITFLIP)
       acc = __uint_as_float(__float_as_uint(acc) ^ (1u << ip.bit));
   }
-  float out = beta_nz ? fmaf(p.alpha, acc, p.beta * cin) : p.alpha * acc;
+  float out = beta_nz ? fmaf(alpha, acc, p.beta * cin) : alpha * acc;
   for (int e = 0; e < p.inj.n; ++e) {
     const InjectPoint& ip = p.inj.p[e];
     if (ip.i != gi || ip.j != gj || ip.site != kSiteOutput) continue;
@@ -185,7 +267,7 @@ __device__ __forceinline__ void tile_coords(int t, int nMb, int nNb, int& mt, in
 // Persistent kernel: one CTA per SM loops over output tiles. The TMEM accumulator is double
 // buffered (2 x 256 columns): while the epilogue warps verify and store tile t from one
 // buffer, the MMA warp accumulates tile t+1 into the other.
-template <bool FT>
+template <bool FT, int KIND>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmChk, const __grid_constant__ TcParams p) {
@@ -193,7 +275,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TcSmem& sm = *reinterpret_cast<TcSmem*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int bk_elems = BKB / 2;
+  using E = Elem<KIND>;
+  const int bk_elems = BKB / E::kBytes;
   const int nk = (p.K + bk_elems - 1) / bk_elems;
   const int nMb = (p.M + BM - 1) / BM, nNb = (p.N + BN - 1) / BN;
   const int ntiles = nMb * nNb;
@@ -239,7 +322,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
-      const uint32_t idesc = umma_idesc(1, 1, BM, BNM);
+      // kind::f16 with BF16 operands (format 1), or kind::f8f6f4 with E4M3 operands (format 0)
+      const uint32_t idesc = KIND == 0 ? umma_idesc(1, 1, BM, BNM) : umma_idesc(0, 0, BM, BNM);
       uint32_t it = 0, lt = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
@@ -253,9 +337,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           tc_fence_after();
           const uint32_t a0 = smem_addr(sm.a[s]), b0 = smem_addr(sm.b[s]);
 #pragma unroll
-          for (int kk = 0; kk < BKB / 32; ++kk)
-            umma_bf16(dcol, umma_desc_sw128(a0 + kk * 32), umma_desc_sw128(b0 + kk * 32), idesc,
+          for (int kk = 0; kk < BKB / 32; ++kk) {  // one MMA per 32 bytes of K
+            if (KIND == 0)
+              umma_bf16(dcol, umma_desc_sw128(a0 + kk * 32), umma_desc_sw128(b0 + kk * 32), idesc,
+                        (kt > 0 || kk > 0) ? 1u : 0u);
+            else
+              umma_f8(dcol, umma_desc_sw128(a0 + kk * 32), umma_desc_sw128(b0 + kk * 32), idesc,
                       (kt > 0 || kk > 0) ? 1u : 0u);
+          }
           umma_commit(&sm.empty[s]);
         }
         umma_commit(&sm.tfull[b]);
@@ -268,6 +357,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int ew = warp - 2;                // epilogue warp index 0..3
     const int et = t - 64;                  // epilogue thread index 0..127
     const bool beta_nz = p.beta != 0.0f;
+    const float alpha = alpha_eff(p);
     uint32_t lt = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
       int mt, nt;
@@ -285,7 +375,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const uint32_t trow = tmem + b * BNM + (static_cast<uint32_t>(q * 32) << 16);
       float rs = 0.f, rc = 0.f, rabs = 0.f;   // compensated sum of C over the row, upward |C| sum
       float cs = 0.f, cc = 0.f, cabs = 0.f;   // same for C_in
-      uint32_t w4[4] = {0u, 0u, 0u, 0u};
+      uint32_t wp[16];  // checksum columns: the pieces' products
+#pragma unroll
+      for (int q2 = 0; q2 < 16; ++q2) wp[q2] = 0u;
       // Injection points in this tile (test launches only): the per-element injection code
       // is kept out of the hot loop so the epilogue stays small in the instruction cache,
       // which it shares with the producer and MMA warps.
@@ -308,10 +400,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (beta_nz && ok) cin = p.C[gi + gj * p.ldc];
             float out;
             if (FT && col == inj_c) {
-              out = inject_element(p, gi, gj, acc, cin, beta_nz);
+              out = inject_element(p, alpha, gi, gj, acc, cin, beta_nz);
               inj_c = next_inj_col(p, gi, n0, nJ, col);
             } else {
-              out = beta_nz ? fmaf(p.alpha, acc, p.beta * cin) : p.alpha * acc;
+              out = beta_nz ? fmaf(alpha, acc, p.beta * cin) : alpha * acc;
             }
             if (ok) p.C[gi + gj * p.ldc] = out;
             if (FT) {
@@ -329,10 +421,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
           }
         }
-        if (FT) {
-          __syncwarp();
-          tmem_ld4(trow + BN, w4);  // C^r pieces from the checksum column of B^r
-          tmem_ld_wait();
+        if (FT) {  // C^r pieces from the checksum columns of B^r
+#pragma unroll
+          for (int h = 0; h < (E::kPieces + 7) / 8; ++h) {
+            uint32_t v8[8];
+            __syncwarp();
+            tmem_ld8(trow + BN + 8 * h, v8);
+            tmem_ld_wait();
+#pragma unroll
+            for (int q2 = 0; q2 < 8; ++q2) wp[8 * h + q2] = v8[q2];
+          }
         }
       }
       // The accumulator buffer is free for the MMA warp's next-but-one tile.
@@ -346,10 +444,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       named_bar(1, 128);
       double delta = 0.0, tau = 0.0, predicted = 0.0;
       if (got && row_ok) {
-        const double pr = (double)__uint_as_float(w4[0]) + (double)__uint_as_float(w4[1]) +
-                          (double)__uint_as_float(w4[2]);
+        double pr;
+        if (KIND == 0) {
+          pr = (double)__uint_as_float(wp[0]) + (double)__uint_as_float(wp[1]) + (double)__uint_as_float(wp[2]);
+        } else {
+          pr = 0.0;
+          double sc = 512.0;  // piece scale 2^(9 - 4p)
+#pragma unroll
+          for (int q2 = 0; q2 < E::kPieces; ++q2, sc *= 0.0625) pr += sc * (double)__uint_as_float(wp[q2]);
+        }
         const double cin_sum = (double)cs + (double)cc;
-        predicted = (double)p.alpha * pr + (beta_nz ? (double)p.beta * cin_sum : 0.0);
+        predicted = (double)alpha * pr + (beta_nz ? (double)p.beta * cin_sum : 0.0);
         for (int e = 0; e < p.inj.n; ++e) {
           const InjectPoint& ip = p.inj.p[e];
           if (ip.site == kSiteChecksumRow && ip.i == gi && ip.j >= n0 && ip.j < n0 + nJ) {
@@ -359,14 +464,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         const double ref = (double)rs + (double)rc;
         delta = ref - predicted;
-        // tau = |alpha| P (gamma_K(u_acc) (2 + 2^-7) + 2^-20 + gamma_240(2^-24)) + 2 u32 (sum|C| +
-        // |beta| sum|C_in|), P an upper bound of sum_k |A(i,k)| sum_{j in tile} |B(k,j)|; the
-        // gamma_240(2^-24) term is the rounding of B e, a binary32 sum over the tile's columns.
+        // tau = |alpha| P (gamma_K(u_acc) (1 + s) + 2^-20 + gamma_240(2^-24)) + 2 u32 (sum|C| +
+        // |beta| sum|C_in|), P an upper bound of sum_k |A(i,k)| sum_{j in tile} |B(k,j)|, s the
+        // bound of sum_p |piece_p| / |B e| (the prediction's accumulation error; the
+        // reference row sum's is gamma_K(u_acc) P); the gamma_240(2^-24) term is the
+        // rounding of B e, a binary32 sum over the tile's columns.
         const float P = __fmul_ru(p.rowAbsA[gi], p.maxAbsBe[nt]);
         const float g = gamma32_up((float)p.K, p.u_acc);
         const float genc = gamma32_up((float)kTcBNProt, 0x1p-24f);
-        const float prod = __fmul_ru(__fmul_ru(fabsf(p.alpha), P),
-                                     __fadd_ru(__fadd_ru(__fmul_ru(g, 2.0078125f), 0x1p-20f), genc));
+        const float prod = __fmul_ru(__fmul_ru(fabsf(alpha), P),
+                                     __fadd_ru(__fadd_ru(__fmul_ru(g, 1.0f + E::kPieceSum), 0x1p-20f), genc));
         const float outp = __fmul_ru(0x1p-23f, __fadd_ru(rabs, __fmul_ru(fabsf(p.beta), cabs)));
         tau = (double)__fadd_ru(prod, outp);
         if (!(fabs(delta) <= tau) || isinf(delta)) {
@@ -438,15 +545,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 constexpr int kResolveWarps = 8;
 constexpr int kResolveItems = kTcBNProt;  // one column per work item
 
-__device__ __forceinline__ void bf16x8(const uint4 w, float (&x)[8]) {
-  const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-  for (int h = 0; h < 4; ++h) {
-    x[2 * h] = __uint_as_float(ws[h] << 16);
-    x[2 * h + 1] = __uint_as_float(ws[h] & 0xffff0000u);
-  }
-}
-
 struct ResolveShared {
   int last, first_col, first_elem;
   double part_d[kResolveWarps], part_r[kResolveWarps];
@@ -459,9 +557,10 @@ struct ResolveShared {
 // (lane l loads k .. k + 7 of a block with 16-byte loads: B and A rows are 16-byte aligned,
 // leading dimensions being multiples of 8; e^T A rows are 32-byte aligned, pitch a multiple
 // of 8). Partial sums meet in shared memory; thread 0 forms the comparisons.
-template <bool kRecompute>
-__device__ void resolve_column(const TcParams& p, TcPendingEntry& pe, ResolveShared& sh, int mt, int m0, int n0,
-                               int nI, int cidx, bool beta_nz) {
+template <bool kRecompute, int KIND>
+__device__ void resolve_column(const TcParams& p, float alpha, TcPendingEntry& pe, ResolveShared& sh, int mt, int m0,
+                               int n0, int nI, int cidx, bool beta_nz) {
+  using E = Elem<KIND>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t gj = n0 + cidx;
   const int64_t gi = m0 + pe.first_row;
@@ -476,8 +575,8 @@ __device__ void resolve_column(const TcParams& p, TcPendingEntry& pe, ResolveSha
     const float cref_abs = warp_sum_up(a);
     if (lane == 0) { sh.cref = cref; sh.cref_abs = cref_abs; }
   }
-  const uint16_t* bcol = static_cast<const uint16_t*>(p.B) + gj * p.ldb;
-  const uint16_t* arow = static_cast<const uint16_t*>(p.A) + gi * p.lda;
+  const void* bcol = static_cast<const uint8_t*>(p.B) + gj * p.ldb * E::kBytes;
+  const void* arow = static_cast<const uint8_t*>(p.A) + gi * p.lda * E::kBytes;
   const float* sAI = p.sA + (int64_t)mt * p.sa_pitch;
   const float* absAI = p.absSA + (int64_t)mt * p.sa_pitch;
   const int K = p.K, K8 = p.K & ~7;
@@ -485,7 +584,7 @@ __device__ void resolve_column(const TcParams& p, TcPendingEntry& pe, ResolveSha
 #pragma unroll 2
   for (int k = warp * 256 + lane * 8; k < K8; k += kResolveWarps * 256) {
     float bx[8];
-    bf16x8(*reinterpret_cast<const uint4*>(bcol + k), bx);
+    E::load8(bcol, k, K, bx);
     const float4 s0 = *reinterpret_cast<const float4*>(sAI + k), s1 = *reinterpret_cast<const float4*>(sAI + k + 4);
     const float4 u0 = *reinterpret_cast<const float4*>(absAI + k), u1 = *reinterpret_cast<const float4*>(absAI + k + 4);
     const float sv[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
@@ -497,7 +596,7 @@ __device__ void resolve_column(const TcParams& p, TcPendingEntry& pe, ResolveSha
     }
     if (kRecompute) {
       float ax[8];
-      bf16x8(*reinterpret_cast<const uint4*>(arow + k), ax);
+      E::load8(arow, k, K, ax);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         r = fmaf(ax[q], bx[q], r);
@@ -507,11 +606,11 @@ __device__ void resolve_column(const TcParams& p, TcPendingEntry& pe, ResolveSha
   }
   if (warp == kResolveWarps - 1 && K8 + lane < K) {  // ragged end of K, one element per lane
     const int k = K8 + lane;
-    const float bx = bf16_to_f32(bcol[k]);
+    const float bx = E::at(bcol, k);
     d = fmaf(sAI[k], bx, d);
     pc = __fmaf_ru(absAI[k], fabsf(bx), pc);
     if (kRecompute) {
-      const float ax = bf16_to_f32(arow[k]);
+      const float ax = E::at(arow, k);
       r = fmaf(ax, bx, r);
       S = __fmaf_ru(fabsf(ax), fabsf(bx), S);
     }
@@ -533,7 +632,7 @@ __device__ void resolve_column(const TcParams& p, TcPendingEntry& pe, ResolveSha
   const float g = gamma32_up((float)K, p.u_acc);
   const float g24 = gamma32_up((float)K, 0x1p-24f);
   const float genc = gamma32_up((float)BM, 0x1p-24f);  // rounding of e^T A, a binary32 sum over 128 rows
-  double cpred = (double)p.alpha * dsum;
+  double cpred = (double)alpha * dsum;
   float cin_abs = 0.f;
   if (beta_nz) {
     cpred += (double)p.beta * pe.cin_sum[cidx];
@@ -543,18 +642,18 @@ __device__ void resolve_column(const TcParams& p, TcPendingEntry& pe, ResolveSha
   // C^c_ref carries the accumulation error gamma_K(u_acc) P_c; C^c (binary32 dot of e^T A
   // with B) adds gamma_K(2^-24) P_c + 2^-22 P_c, and e^T A itself, a binary32 sum,
   // gamma_128(2^-24) P_c; the per-warp C_in partial sums carry gamma_31 (binary32).
-  const float prod = __fmul_ru(__fmul_ru(fabsf(p.alpha), Pc), __fadd_ru(__fadd_ru(__fadd_ru(g, g24), 0x1p-22f), genc));
+  const float prod = __fmul_ru(__fmul_ru(fabsf(alpha), Pc), __fadd_ru(__fadd_ru(__fadd_ru(g, g24), 0x1p-22f), genc));
   const float outp = __fmul_ru(0x1p-23f, __fadd_ru(sh.cref_abs, __fmul_ru(__fmul_ru(fabsf(p.beta), cin_abs), 34.0f)));
   const double tauc = (double)__fadd_ru(prod, outp);
   pe.col_delta[cidx] = dcol;
   pe.col_tau[cidx] = tauc;
   pe.col_flag[cidx] = (!(fabs(dcol) <= tauc) || isinf(dcol)) ? 1 : 0;
   if (kRecompute) {
-    const double rec = (double)p.alpha * rsum;
+    const double rec = (double)alpha * rsum;
     const double cij = (double)p.C[gi + gj * p.ldc];
     // the recomputation is a binary32 dot product: its rounding, gamma_K(2^-24) S, joins the
     // accumulation's gamma_K(u_acc) S
-    const float te = __fadd_ru(__fmul_ru(__fmul_ru(fabsf(p.alpha), Sx), __fadd_ru(__fadd_ru(g, g24), 0x1p-30f)),
+    const float te = __fadd_ru(__fmul_ru(__fmul_ru(fabsf(alpha), Sx), __fadd_ru(__fadd_ru(g, g24), 0x1p-30f)),
                                __fmul_ru(0x1p-23f, (float)fabs(cij)));
     const double dd = cij - rec;
     pe.elem_flag[cidx] = (!(fabs(dd) <= (double)te) || isinf(dd)) ? 1 : 0;
@@ -617,8 +716,10 @@ __device__ void resolve_tile(const TcParams& p, TcPendingEntry& pe, ResolveShare
   count_kind(p, kind);
 }
 
+template <int KIND>
 __global__ void __launch_bounds__(kResolveWarps * 32) tc_resolve_kernel(const __grid_constant__ TcParams p) {
   __shared__ ResolveShared sh;
+  const float alpha = alpha_eff(p);
   const unsigned npend = min(*reinterpret_cast<volatile const unsigned*>(&p.pend->count), (unsigned)kTcPendCap);
   const int items = (int)npend * kResolveItems;
   const bool beta_nz = p.beta != 0.0f;
@@ -629,8 +730,8 @@ __global__ void __launch_bounds__(kResolveWarps * 32) tc_resolve_kernel(const __
     const int m0 = mt * BM, n0 = nt * kTcBNProt;
     const int nI = min(BM, p.M - m0), nJ = min(kTcBNProt, p.N - n0);
     if (cidx < nJ) {
-      if (pe.nr == 1 && !beta_nz) resolve_column<true>(p, pe, sh, mt, m0, n0, nI, cidx, beta_nz);
-      else resolve_column<false>(p, pe, sh, mt, m0, n0, nI, cidx, beta_nz);
+      if (pe.nr == 1 && !beta_nz) resolve_column<true, KIND>(p, alpha, pe, sh, mt, m0, n0, nI, cidx, beta_nz);
+      else resolve_column<false, KIND>(p, alpha, pe, sh, mt, m0, n0, nI, cidx, beta_nz);
     }
     if (threadIdx.x == 0) {
       __threadfence();  // this column's results before the arrival on the tile counter
@@ -650,25 +751,14 @@ __global__ void __launch_bounds__(kResolveWarps * 32) tc_resolve_kernel(const __
 // M x K and B is K x N, both K-contiguous, so each is a set of K-contiguous lines: the
 // rows of A, the columns of B. A CTA takes a block of L lines (the 128 rows of a tile of
 // A, the 240 columns of a tile of B) and ENC_KC consecutive k. Lane l of warp w loads
-// k0 + 8l .. k0 + 8l + 7 (one 16-byte load per line) of lines w, w + 8, w + 16, ...; the
-// eight warps' partial sums meet in shared memory.
+// k0 + 8l .. k0 + 8l + 7 (one 16- or 8-byte load per line) of lines w, w + 8, w + 16, ...;
+// the eight warps' partial sums meet in shared memory.
 // Sums over a block are plain binary32 sums: their rounding, at most gamma_L(2^-24) times
 // the sum of magnitudes in any order, is a term of the thresholds. Sums of magnitudes round
 // upward, so they bound the exact sums.
 // ---------------------------------------------------------------------------------------
 constexpr int ENC_KC = 256;   // k per CTA: 32 lanes x 8
 constexpr int ENC_WARPS = 8;
-
-// Eight consecutive bfloat16 of one line from k (a multiple of 8), zero at and beyond K.
-// The 16-byte load is aligned: leading dimensions are multiples of 8 elements and base
-// addresses 16-byte aligned (both required by the tensor maps).
-__device__ __forceinline__ uint4 load8_bf16(const uint16_t* line, int64_t k, int32_t K) {
-  if (k + 8 <= K) return *reinterpret_cast<const uint4*>(line + k);
-  uint32_t w[4] = {0u, 0u, 0u, 0u};
-  for (int q = 0; q < 8; ++q)
-    if (k + q < K) w[q >> 1] |= (uint32_t)line[k + q] << (16 * (q & 1));
-  return make_uint4(w[0], w[1], w[2], w[3]);
-}
 
 // Lane l holds la[u], a partial sum for line u of a group of 8 lines. Returns the upward
 // sum over the 32 lanes of line (l >> 2): recursive halving, 9 shuffles.
@@ -691,20 +781,21 @@ __device__ __forceinline__ float reduce_scatter8_up(const float (&la)[8], int la
 }
 
 struct EncArgs {
-  const uint16_t* X; int64_t ld;
+  const void* X; int64_t ld;
   int32_t nlines, K, L;
   int32_t nclear;          // rows pass: entries of maxAbsBe to zero before the columns pass
   float* sum;              // rows pass: [nblocks][pitch] e^T A per block
   float* abs_sum;          // rows pass: [nblocks][pitch] upward sum_{i in block} |A(i,k)|
-  int64_t pitch;
+  int64_t pitch;           // also the checksum operand's row pitch (elements)
   TcPending* pend;         // rows pass: its tile count is zeroed before the GEMM
   float* line_part;        // rows pass: [nkc][M] upward sum of |A(i,k)| over one k-chunk
   float* maxAbsBe;         // [nblocks of B]
-  uint16_t* chk; int64_t kpitch;  // columns pass: pieces of B e, rows J*16 + {0, 1, 2}; rows 3..15 zero
+  void* chk;               // columns pass: pieces of B e in rows J*16 + p (unused rows zero)
 };
 
-template <bool kRowsOfA>
+template <bool kRowsOfA, int KIND>
 __global__ void __launch_bounds__(256) encode_kernel(EncArgs g) {
+  using E = Elem<KIND>;
   __shared__ float red_s[ENC_WARPS][ENC_KC];
   __shared__ float red_a[ENC_WARPS][ENC_KC];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -712,30 +803,29 @@ __global__ void __launch_bounds__(256) encode_kernel(EncArgs g) {
   const int64_t line0 = (int64_t)blk * g.L;
   const int nI = (int)min((int64_t)g.L, (int64_t)g.nlines - line0);
   const int64_t k = (int64_t)kc * ENC_KC + lane * 8;
+  const uint8_t* X = static_cast<const uint8_t*>(g.X);
   float s[8], a[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) { s[q] = 0.f; a[q] = 0.f; }
   const int T = (nI + ENC_WARPS - 1) / ENC_WARPS;  // lines per warp, rounded up
   for (int t0 = 0; t0 < T; t0 += 8) {
-    uint4 raw[8];
+    typename E::Raw raw[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int l = warp + ENC_WARPS * (t0 + u);
-      raw[u] = (l < nI && k < g.K) ? load8_bf16(g.X + (line0 + l) * g.ld, k, g.K) : make_uint4(0u, 0u, 0u, 0u);
+      raw[u] = (l < nI && k < g.K) ? E::load_raw(X + (line0 + l) * g.ld * E::kBytes, k, g.K) : E::zero();
     }
     float la[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const uint32_t ws[4] = {raw[u].x, raw[u].y, raw[u].z, raw[u].w};
+      float x[8];
+      E::unpack(raw[u], x);
       float lsum = 0.f;
 #pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const float x0 = __uint_as_float(ws[h] << 16), x1 = __uint_as_float(ws[h] & 0xffff0000u);
-        s[2 * h] += x0;
-        s[2 * h + 1] += x1;
-        a[2 * h] = __fadd_ru(a[2 * h], fabsf(x0));
-        a[2 * h + 1] = __fadd_ru(a[2 * h + 1], fabsf(x1));
-        if (kRowsOfA) lsum = __fadd_ru(lsum, __fadd_ru(fabsf(x0), fabsf(x1)));
+      for (int q = 0; q < 8; ++q) {
+        s[q] += x[q];
+        a[q] = __fadd_ru(a[q], fabsf(x[q]));
+        if (kRowsOfA) lsum = __fadd_ru(lsum, fabsf(x[q]));
       }
       la[u] = lsum;
     }
@@ -766,18 +856,35 @@ __global__ void __launch_bounds__(256) encode_kernel(EncArgs g) {
     }
   } else {
     if (kk < g.K) {
-      // three bfloat16 pieces, each the nearest bfloat16 of what the previous ones leave:
-      // together they hold the binary32 sum exactly (8 + 8 + 8 significand bits)
-      const __nv_bfloat16 h = __float2bfloat16_rn(S);
-      const float r1 = S - __bfloat162float(h);
-      const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-      const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(m));
-      uint16_t* col = g.chk + (int64_t)blk * CHK_ROWS * g.kpitch + kk;
-      col[0] = __bfloat16_as_ushort(h);
-      col[g.kpitch] = __bfloat16_as_ushort(m);
-      col[2 * g.kpitch] = __bfloat16_as_ushort(lo);
+      if (KIND == 0) {
+        // three bfloat16 pieces, each the nearest bfloat16 of what the previous ones leave:
+        // together they hold the binary32 sum exactly (8 + 8 + 8 significand bits)
+        const __nv_bfloat16 h = __float2bfloat16_rn(S);
+        const float r1 = S - __bfloat162float(h);
+        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(m));
+        uint16_t* col = static_cast<uint16_t*>(g.chk) + (int64_t)blk * CHK_ROWS * g.pitch + kk;
+        col[0] = __bfloat16_as_ushort(h);
+        col[g.pitch] = __bfloat16_as_ushort(m);
+        col[2 * g.pitch] = __bfloat16_as_ushort(lo);
 #pragma unroll
-      for (int r = 3; r < CHK_ROWS; ++r) col[r * g.kpitch] = 0;
+        for (int r = 3; r < CHK_ROWS; ++r) col[r * g.pitch] = 0;
+      } else {
+        // sixteen e4m3 pieces with scales 2^(9 - 4p): piece p is the nearest e4m3 of
+        // r / 2^(9 - 4p), r what the previous pieces leave; a subnormal piece is flushed to
+        // zero and its value carried. |S| <= 240 * 448 < 256 * 2^9, and each remainder is at
+        // most half an e4m3 unit of the piece before, so every r / 2^(9 - 4p) stays within
+        // +-256, and r - piece is exact (the two are within a factor of two).
+        uint8_t* col = static_cast<uint8_t*>(g.chk) + (int64_t)blk * CHK_ROWS * g.pitch + kk;
+        float r = S, inv = 0x1p-9f, sc = 0x1p9f;
+#pragma unroll
+        for (int pc = 0; pc < Elem<1>::kPieces; ++pc, inv *= 16.f, sc *= 0.0625f) {
+          __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(r * inv, __NV_SATFINITE, __NV_E4M3);
+          if ((q & 0x78u) == 0) q = 0;
+          col[pc * g.pitch] = q;
+          r -= e4m3_to_f32(q) * sc;
+        }
+      }
     }
     float mx = kk < g.K ? Aab : 0.f;
 #pragma unroll
@@ -796,23 +903,37 @@ __global__ void __launch_bounds__(256) row_abs_finalize_kernel(const float* line
   rowAbsA[i] = a;
 }
 
+// C = beta C over an M x N column-major FP32 matrix (beta == 0 writes zeros: C is not read).
+__global__ void scale_f32_kernel(float* C, int64_t ldc, int32_t M, int32_t N, float beta) {
+  const int64_t total = (int64_t)M * N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % M, j = e / M;
+    float* c = C + i + j * ldc;
+    *c = beta == 0.0f ? 0.0f : beta * *c;
+  }
+}
+
 }  // namespace
 
-size_t tc_workspace_bytes(int32_t M, int32_t N, int32_t K) {
+int64_t tc_kpitch(int32_t K) { return (K + 15) / 16 * 16; }
+
+size_t tc_workspace_bytes(int32_t M, int32_t N, int32_t K, int kind) {
   const int64_t nMb = (M + BM - 1) / BM, nNb = (N + kTcBNProt - 1) / kTcBNProt;
-  const int64_t kpitch = (K + 7) / 8 * 8, nkc = (K + ENC_KC - 1) / ENC_KC;
+  const int64_t kpitch = tc_kpitch(K), nkc = (K + ENC_KC - 1) / ENC_KC;
+  const int64_t eb = kind == 0 ? 2 : 1;
   auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
-  return up(nNb * CHK_ROWS * kpitch * 2) + up(nMb * kpitch * 4) + up(nMb * kpitch * 4) + up(M * 4) +
+  return up(nNb * CHK_ROWS * kpitch * eb) + up(nMb * kpitch * 4) + up(nMb * kpitch * 4) + up(M * 4) +
          up(nNb * 4) + up(nkc * M * 4) + up((int64_t)sizeof(TcPending));
 }
 
-TcWorkspace tc_workspace_carve(void* base, int32_t M, int32_t N, int32_t K) {
+TcWorkspace tc_workspace_carve(void* base, int32_t M, int32_t N, int32_t K, int kind) {
   const int64_t nMb = (M + BM - 1) / BM, nNb = (N + kTcBNProt - 1) / kTcBNProt;
-  const int64_t kpitch = (K + 7) / 8 * 8, nkc = (K + ENC_KC - 1) / ENC_KC;
+  const int64_t kpitch = tc_kpitch(K), nkc = (K + ENC_KC - 1) / ENC_KC;
+  const int64_t eb = kind == 0 ? 2 : 1;
   auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
   char* c = static_cast<char*>(base);
   TcWorkspace w;
-  w.chk = reinterpret_cast<uint16_t*>(c); c += up(nNb * CHK_ROWS * kpitch * 2);
+  w.chk = c; c += up(nNb * CHK_ROWS * kpitch * eb);
   w.kpitch = kpitch;
   w.sA = reinterpret_cast<float*>(c); c += up(nMb * kpitch * 4);
   w.absSA = reinterpret_cast<float*>(c); c += up(nMb * kpitch * 4);
@@ -824,46 +945,63 @@ TcWorkspace tc_workspace_carve(void* base, int32_t M, int32_t N, int32_t K) {
   return w;
 }
 
-cudaError_t launch_tc_encode(const TcParams& p, const TcWorkspace& w, cudaStream_t st) {
+template <int KIND>
+static void launch_encode_kind(const TcParams& p, const TcWorkspace& w, cudaStream_t st) {
   const int nMb = (p.M + BM - 1) / BM, nNb = (p.N + kTcBNProt - 1) / kTcBNProt, nkc = (p.K + ENC_KC - 1) / ENC_KC;
   EncArgs g;
   std::memset(&g, 0, sizeof(g));
-  g.X = static_cast<const uint16_t*>(p.A); g.ld = p.lda; g.nlines = p.M; g.K = p.K; g.L = BM;
+  g.X = p.A; g.ld = p.lda; g.nlines = p.M; g.K = p.K; g.L = BM;
   g.nclear = nNb; g.sum = w.sA; g.abs_sum = w.absSA; g.line_part = w.rowPart; g.maxAbsBe = w.maxAbsBe;
   g.pitch = w.kpitch; g.pend = w.pend;
-  encode_kernel<true><<<dim3(nMb, nkc), ENC_WARPS * 32, 0, st>>>(g);
+  encode_kernel<true, KIND><<<dim3(nMb, nkc), ENC_WARPS * 32, 0, st>>>(g);
   row_abs_finalize_kernel<<<(p.M + 255) / 256, 256, 0, st>>>(w.rowPart, p.M, nkc, w.rowAbsA);
   std::memset(&g, 0, sizeof(g));
-  g.X = static_cast<const uint16_t*>(p.B); g.ld = p.ldb; g.nlines = p.N; g.K = p.K; g.L = kTcBNProt;
-  g.maxAbsBe = w.maxAbsBe; g.chk = w.chk; g.kpitch = w.kpitch;
-  encode_kernel<false><<<dim3(nNb, nkc), ENC_WARPS * 32, 0, st>>>(g);
+  g.X = p.B; g.ld = p.ldb; g.nlines = p.N; g.K = p.K; g.L = kTcBNProt;
+  g.maxAbsBe = w.maxAbsBe; g.chk = w.chk; g.pitch = w.kpitch;
+  encode_kernel<false, KIND><<<dim3(nNb, nkc), ENC_WARPS * 32, 0, st>>>(g);
+}
+
+cudaError_t launch_tc_encode(const TcParams& p, const TcWorkspace& w, cudaStream_t st) {
+  if (p.kind == 0) launch_encode_kind<0>(p, w, st);
+  else launch_encode_kind<1>(p, w, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_f32(float* C, int64_t ldc, int64_t M, int64_t N, float beta, cudaStream_t st) {
+  if (M == 0 || N == 0) return cudaSuccess;
+  const int64_t total = M * N;
+  const int64_t blocks = (total + 255) / 256;
+  scale_f32_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(C, ldc, (int32_t)M, (int32_t)N, beta);
+  return cudaGetLastError();
+}
+
+template <bool FT, int KIND>
+static cudaError_t launch_gemm_kind(const TcParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB,
+                                    const CUtensorMap* tmChk, int sms, cudaStream_t st) {
+  const size_t smem = sizeof(TcSmem);
+  const int bn = FT ? kTcBNProt : BNM;
+  const long long tiles = (long long)((p.M + BM - 1) / BM) * ((p.N + bn - 1) / bn);
+  const int grid = (int)(tiles < sms ? tiles : sms);
+  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<FT, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  tc_gemm_kernel<FT, KIND><<<grid, NTHREADS, smem, st>>>(*tmA, *tmB, *tmChk, p);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !FT) return e;
+  tc_resolve_kernel<KIND><<<2 * sms, kResolveWarps * 32, 0, st>>>(p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_gemm(const TcParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmChk,
                            bool ft, cudaStream_t st) {
-  const size_t smem = sizeof(TcSmem);
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const int bn = ft ? kTcBNProt : BNM;
-  const long long tiles = (long long)((p.M + BM - 1) / BM) * ((p.N + bn - 1) / bn);
-  const int grid = (int)(tiles < sms ? tiles : sms);
-  if (ft) {
-    e = cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    tc_gemm_kernel<true><<<grid, NTHREADS, smem, st>>>(*tmA, *tmB, *tmChk, p);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    tc_resolve_kernel<<<2 * sms, kResolveWarps * 32, 0, st>>>(p);
-  } else {
-    e = cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    tc_gemm_kernel<false><<<grid, NTHREADS, smem, st>>>(*tmA, *tmB, *tmChk, p);
-  }
-  return cudaGetLastError();
+  if (p.kind == 0) return ft ? launch_gemm_kind<true, 0>(p, tmA, tmB, tmChk, sms, st)
+                             : launch_gemm_kind<false, 0>(p, tmA, tmB, tmChk, sms, st);
+  return ft ? launch_gemm_kind<true, 1>(p, tmA, tmB, tmChk, sms, st)
+            : launch_gemm_kind<false, 1>(p, tmA, tmB, tmChk, sms, st);
 }
 
 }  // namespace ftk

@@ -13,7 +13,7 @@ namespace ftk {
 constexpr int kTcBM = 128;       // tile rows (TMEM lanes)
 constexpr int kTcBN = 256;       // data columns per tile, unprotected (= MMA N)
 constexpr int kTcBNProt = 240;   // data columns per tile, protected: B^r = [B, Be] fills N = 256
-constexpr int kTcChkRows = 16;   // rows of the checksum operand per column block (pieces of B e in 0..2)
+constexpr int kTcChkRows = 16;   // rows of the checksum operand per column block (pieces of B e)
 
 // A tile whose row checksums mismatch, handed from the GEMM's epilogue to the resolve pass
 // (lazy column side, row recompute, classification and correction), which runs after
@@ -42,7 +42,9 @@ struct TcParams {
   int32_t swap_report;
   float alpha, beta;
   float u_acc;                   // unit roundoff assumed for the tensor-core accumulation
-  int32_t pad_;
+  int32_t kind;                  // 0: BF16 operands, 1: FP8 E4M3 operands
+  const float* a_scale;          // FP8 per-tensor scales (device values), or null
+  const float* b_scale;
   const void* A; int64_t lda;
   const void* B; int64_t ldb;
   float* C; int64_t ldc;
@@ -57,7 +59,7 @@ struct TcParams {
 };
 
 struct TcWorkspace {
-  uint16_t* chk;  int64_t kpitch;
+  void* chk;  int64_t kpitch;    // checksum operand, [nNb * 16][kpitch] elements of the input kind
   float* sA;
   float* absSA;
   float* rowAbsA;
@@ -67,8 +69,10 @@ struct TcWorkspace {
   size_t bytes;
 };
 
-size_t tc_workspace_bytes(int32_t M, int32_t N, int32_t K);
-TcWorkspace tc_workspace_carve(void* base, int32_t M, int32_t N, int32_t K);
+int64_t tc_kpitch(int32_t K);
+size_t tc_workspace_bytes(int32_t M, int32_t N, int32_t K, int kind);
+TcWorkspace tc_workspace_carve(void* base, int32_t M, int32_t N, int32_t K, int kind);
+cudaError_t launch_scale_f32(float* C, int64_t ldc, int64_t M, int64_t N, float beta, cudaStream_t st);
 cudaError_t launch_tc_encode(const TcParams& p, const TcWorkspace& w, cudaStream_t st);
 cudaError_t launch_tc_gemm(const TcParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmChk,
                            bool ft, cudaStream_t st);

@@ -126,18 +126,22 @@ bool make_map_f64(CUtensorMap* map, const void* base, int64_t inner, int64_t out
 }
 
 // 2-D 16-bit tensor map with 128-byte swizzle: `inner` K-contiguous elements per line.
-bool make_map_b16_sw128(CUtensorMap* map, const void* base, int64_t inner, int64_t outer, int64_t ld_elems,
-                        uint32_t box_inner, uint32_t box_outer) {
+// 2-D map of 2-byte (BF16) or 1-byte (FP8) elements, 128-byte swizzle: the box's inner
+// extent is 128 bytes (one swizzle row). Leading dimensions must be a multiple of 16 bytes
+// and the base 16-byte aligned (else false: the caller reports FTBLAS_STATUS_NOT_SUPPORTED).
+bool make_map_sw128(CUtensorMap* map, int elem_bytes, const void* base, int64_t inner, int64_t outer,
+                    int64_t ld_elems, uint32_t box_outer) {
   auto fn = encode_fn();
   if (!fn) return false;
   if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
-  if (((ld_elems * 2) & 15) != 0 || ld_elems * 2 >= (int64_t(1) << 40)) return false;
+  if (((ld_elems * elem_bytes) & 15) != 0 || ld_elems * elem_bytes >= (int64_t(1) << 40)) return false;
   if (inner <= 0 || outer <= 0 || inner > (int64_t(1) << 32) || outer > (int64_t(1) << 32)) return false;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(outer)};
-  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld_elems * 2)};
-  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld_elems * elem_bytes)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / elem_bytes), box_outer};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+  const CUtensorMapDataType dt = elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -245,6 +249,94 @@ int dgemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, doub
 }
 
 // ------------------------------------------------------------------ mixed precision
+// The tensor-core path (A, B BF16 or FP8 E4M3; C and compute FP32) behind ftblas_gemm_ex,
+// ftblas_gemm_ex_noabft and ftblas_gemm_ex_noalloc. Workspace: from the stream-ordered
+// allocator when ws is null, else the caller's ws_bytes bytes (checked before any device
+// work). Argument checks follow ftblas_gemm_ex's positions.
+int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, const void* alpha, const void* A,
+                 int Atype, int64_t lda, const void* B, int Btype, int64_t ldb, const void* beta, void* C, int Ctype,
+                 int64_t ldc, int ctype, const float* a_scale, const float* b_scale, void* stream, ft_report_t* report,
+                 bool ft, void* ws, size_t ws_bytes, bool allow_fp8) {
+  if (layout != FTBLAS_ROW_MAJOR && layout != FTBLAS_COL_MAJOR) return -1;
+  if (ta != FTBLAS_NO_TRANS && ta != FTBLAS_TRANS) return -2;
+  if (tb != FTBLAS_NO_TRANS && tb != FTBLAS_TRANS) return -3;
+  if (M < 0) return -4;
+  if (N < 0) return -5;
+  if (K < 0) return -6;
+  if (alpha == nullptr) return -7;
+  if (beta == nullptr) return -14;
+  const bool c32 = Ctype == FTBLAS_R_32F && ctype == FTBLAS_R_32F;
+  const bool bf16 = c32 && Atype == FTBLAS_R_16BF && Btype == FTBLAS_R_16BF;
+  const bool fp8 = c32 && allow_fp8 && Atype == FTBLAS_R_8F_E4M3 && Btype == FTBLAS_R_8F_E4M3;
+  if (!bf16 && !fp8) return FTBLAS_STATUS_NOT_SUPPORTED;
+  if (bf16 && a_scale != nullptr) return -19;
+  if (bf16 && b_scale != nullptr) return -20;
+  const int kind = fp8 ? 1 : 0;
+  const float al = *static_cast<const float*>(alpha), be = *static_cast<const float*>(beta);
+  const bool need_ab = (K > 0 && al != 0.0f && M > 0 && N > 0);
+  int v = validate(layout, ta, tb, M, N, K, A, lda, B, ldb, C, ldc, need_ab);
+  if (v != 0) {
+    static const int pos[15] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 11, 13, 14, 15, 17};
+    return -pos[-v];
+  }
+  if (M > kMaxDim || N > kMaxDim || K > kMaxDim) return FTBLAS_STATUS_NOT_SUPPORTED;
+  const Frame f = map_frame(layout, ta, tb, M, N, A, lda, B, ldb);
+  if (need_ab && (!f.a_kmajor || !f.b_kmajor)) return FTBLAS_STATUS_NOT_SUPPORTED;
+  const size_t wsb = (ft && need_ab) ? tc_workspace_bytes((int32_t)f.M, (int32_t)f.N, (int32_t)K, kind) : 0;
+  if (ws != nullptr && wsb > ws_bytes) return FTBLAS_STATUS_WORKSPACE_LIMIT;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (ft && report != nullptr) {
+    if (int e = record_cuda(cudaMemsetAsync(report, 0, sizeof(ft_report_t), st))) return e;
+  }
+  if (M == 0 || N == 0) return 0;
+  if (!need_ab) return record_cuda(launch_scale_f32(static_cast<float*>(C), ldc, f.M, f.N, be, st));  // C = beta C
+  CallerPoint pts[kMaxInject];
+  int npts = 0;
+  if (ft) {
+    const int64_t tile_rows = f.swap ? kTcBNProt : kTcBM, tile_cols = f.swap ? kTcBM : kTcBNProt;
+    npts = plan_injections(M, N, tile_rows, tile_cols, pts);
+  }
+  TcParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.M = (int32_t)f.M; p.N = (int32_t)f.N; p.K = (int32_t)K;
+  // accumulation unit: kind::f16 truncates to binary32 (2^-23); kind::f8f6f4 also aligns each
+  // group of 32 products to its largest term and truncates every product, taken as 2^-22
+  p.alpha = al; p.beta = be; p.u_acc = fp8 ? 0x1p-22f : 0x1p-23f;
+  p.kind = kind;
+  p.a_scale = fp8 ? (f.swap ? b_scale : a_scale) : nullptr;
+  p.b_scale = fp8 ? (f.swap ? a_scale : b_scale) : nullptr;
+  p.A = f.A; p.lda = f.lda; p.B = f.B; p.ldb = f.ldb;
+  p.C = static_cast<float*>(C); p.ldc = ldc;
+  p.report = ft ? report : nullptr;
+  p.swap_report = f.swap;
+  for (int q = 0; q < npts; ++q) {
+    InjectPoint& ip = p.inj.p[p.inj.n++];
+    const CallerPoint& c = pts[q];
+    ip.i = (int32_t)(f.swap ? c.j : c.i);
+    ip.j = (int32_t)(f.swap ? c.i : c.j);
+    ip.site = c.site == FT_SITE_CHECKSUM ? kSiteChecksumRow : c.site;
+    ip.mode = c.mode; ip.bit = c.bit; ip.rel_log2 = c.rel_log2; ip.sign = c.sign; ip.pad = 0;
+  }
+  const int eb = fp8 ? 1 : 2;
+  CUtensorMap tmA, tmB, tmC;
+  std::memset(&tmA, 0, sizeof(tmA)); std::memset(&tmB, 0, sizeof(tmB)); std::memset(&tmC, 0, sizeof(tmC));
+  if (!make_map_sw128(&tmA, eb, f.A, K, f.M, f.lda, kTcBM)) return FTBLAS_STATUS_NOT_SUPPORTED;
+  if (!make_map_sw128(&tmB, eb, f.B, K, f.N, f.ldb, ft ? kTcBNProt : kTcBN)) return FTBLAS_STATUS_NOT_SUPPORTED;
+  g_last_used_tma = 1;
+  if (!ft) return record_cuda(launch_tc_gemm(p, &tmA, &tmB, &tmA, false, st));
+  const bool own = ws == nullptr;
+  if (own && cudaMallocAsync(&ws, wsb, st) != cudaSuccess) return FTBLAS_STATUS_ALLOC_FAILED;
+  TcWorkspace w = tc_workspace_carve(ws, p.M, p.N, p.K, kind);
+  p.rowAbsA = w.rowAbsA; p.maxAbsBe = w.maxAbsBe; p.sA = w.sA; p.absSA = w.absSA;
+  p.sa_pitch = w.kpitch; p.pend = w.pend;
+  const int64_t nNb = (f.N + kTcBNProt - 1) / kTcBNProt;
+  int rc = make_map_sw128(&tmC, eb, w.chk, K, nNb * kTcChkRows, w.kpitch, kTcChkRows) ? 0 : FTBLAS_STATUS_NOT_SUPPORTED;
+  if (rc == 0) rc = record_cuda(launch_tc_encode(p, w, st));  // writes every workspace entry the GEMM reads
+  if (rc == 0) rc = record_cuda(launch_tc_gemm(p, &tmA, &tmB, &tmC, true, st));
+  if (own) cudaFreeAsync(ws, st);
+  return rc;
+}
+
 int gemm_ex_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, const void* alpha, const void* A,
                  int Atype, int64_t lda, const void* B, int Btype, int64_t ldb, const void* beta, void* C, int Ctype,
                  int64_t ldc, int ctype, const float* a_scale, const float* b_scale, void* stream,
@@ -259,7 +351,6 @@ int gemm_ex_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   if (alpha == nullptr) return -7;
   if (beta == nullptr) return -14;
   const bool all64 = Atype == FTBLAS_R_64F && Btype == FTBLAS_R_64F && Ctype == FTBLAS_R_64F && ctype == FTBLAS_R_64F;
-  const bool bf16 = Atype == FTBLAS_R_16BF && Btype == FTBLAS_R_16BF && Ctype == FTBLAS_R_32F && ctype == FTBLAS_R_32F;
   if (all64) {
     if (a_scale != nullptr) return -19;
     if (b_scale != nullptr) return -20;
@@ -270,68 +361,8 @@ int gemm_ex_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
     static const int pos[17] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 11, 13, 14, 15, 17, 21, 22};
     return (v < 0 && -v <= 16) ? -pos[-v] : v;
   }
-  if (!bf16) return FTBLAS_STATUS_NOT_SUPPORTED;
-  if (a_scale != nullptr) return -19;
-  if (b_scale != nullptr) return -20;
-  const bool need_ab = (K > 0 && *static_cast<const float*>(alpha) != 0.0f && M > 0 && N > 0);
-  int v = validate(layout, ta, tb, M, N, K, A, lda, B, ldb, C, ldc, need_ab);
-  if (v != 0) {
-    static const int pos[15] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 11, 13, 14, 15, 17};
-    return -pos[-v];
-  }
-  if (M > kMaxDim || N > kMaxDim || K > kMaxDim) return FTBLAS_STATUS_NOT_SUPPORTED;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (ft && report != nullptr) {
-    if (int e = record_cuda(cudaMemsetAsync(report, 0, sizeof(ft_report_t), st))) return e;
-  }
-  if (M == 0 || N == 0) return 0;
-  const Frame f = map_frame(layout, ta, tb, M, N, A, lda, B, ldb);
-  CallerPoint pts[kMaxInject];
-  int npts = 0;
-  if (ft) {
-    const int64_t tile_rows = f.swap ? kTcBNProt : kTcBM, tile_cols = f.swap ? kTcBM : kTcBNProt;
-    npts = plan_injections(M, N, tile_rows, tile_cols, pts);
-  }
-  const float al = *static_cast<const float*>(alpha), be = *static_cast<const float*>(beta);
-  if (!f.a_kmajor || !f.b_kmajor) return FTBLAS_STATUS_NOT_SUPPORTED;
-  if (K == 0 || al == 0.0f) return FTBLAS_STATUS_NOT_SUPPORTED;  // quick return not provided for FP32 C yet
-  TcParams p;
-  std::memset(&p, 0, sizeof(p));
-  p.M = (int32_t)f.M; p.N = (int32_t)f.N; p.K = (int32_t)K;
-  p.alpha = al; p.beta = be; p.u_acc = 0x1p-23f;
-  p.A = f.A; p.lda = f.lda; p.B = f.B; p.ldb = f.ldb;
-  p.C = static_cast<float*>(C); p.ldc = ldc;
-  p.report = ft ? report : nullptr;
-  p.swap_report = f.swap;
-  for (int q = 0; q < npts; ++q) {
-    InjectPoint& ip = p.inj.p[p.inj.n++];
-    const CallerPoint& c = pts[q];
-    ip.i = (int32_t)(f.swap ? c.j : c.i);
-    ip.j = (int32_t)(f.swap ? c.i : c.j);
-    ip.site = c.site == FT_SITE_CHECKSUM ? kSiteChecksumRow : c.site;
-    ip.mode = c.mode; ip.bit = c.bit; ip.rel_log2 = c.rel_log2; ip.sign = c.sign; ip.pad = 0;
-  }
-  CUtensorMap tmA, tmB, tmC;
-  std::memset(&tmA, 0, sizeof(tmA)); std::memset(&tmB, 0, sizeof(tmB)); std::memset(&tmC, 0, sizeof(tmC));
-  if (!make_map_b16_sw128(&tmA, f.A, K, f.M, f.lda, 64, kTcBM)) return FTBLAS_STATUS_NOT_SUPPORTED;
-  if (!make_map_b16_sw128(&tmB, f.B, K, f.N, f.ldb, 64, ft ? kTcBNProt : kTcBN)) return FTBLAS_STATUS_NOT_SUPPORTED;
-  g_last_used_tma = 1;
-  if (!ft) return record_cuda(launch_tc_gemm(p, &tmA, &tmB, &tmA, false, st));
-  const size_t wsb = tc_workspace_bytes(p.M, p.N, p.K);
-  void* ws = nullptr;
-  if (cudaMallocAsync(&ws, wsb, st) != cudaSuccess) return FTBLAS_STATUS_ALLOC_FAILED;
-  TcWorkspace w = tc_workspace_carve(ws, p.M, p.N, p.K);
-  p.rowAbsA = w.rowAbsA; p.maxAbsBe = w.maxAbsBe; p.sA = w.sA; p.absSA = w.absSA;
-  p.sa_pitch = w.kpitch; p.pend = w.pend;
-  const int64_t nNb = (f.N + kTcBNProt - 1) / kTcBNProt;
-  if (!make_map_b16_sw128(&tmC, w.chk, K, nNb * kTcChkRows, w.kpitch, 64, kTcChkRows)) {
-    cudaFreeAsync(ws, st);
-    return FTBLAS_STATUS_NOT_SUPPORTED;
-  }
-  int rc = record_cuda(launch_tc_encode(p, w, st));
-  if (rc == 0) rc = record_cuda(launch_tc_gemm(p, &tmA, &tmB, &tmC, true, st));
-  cudaFreeAsync(ws, st);
-  return rc;
+  return tc_gemm_impl(layout, ta, tb, M, N, K, alpha, A, Atype, lda, B, Btype, ldb, beta, C, Ctype, ldc, ctype, a_scale,
+                      b_scale, stream, report, ft, nullptr, 0, true);
 }
 
 // ------------------------------------------------------------------ host-buffer workspace
@@ -355,75 +386,15 @@ int g_ws_device = -1;
 
 namespace ftk {
 
-// Same argument checks, mapping, injection plan and launches as the BF16 branch of
-// gemm_ex_impl, with the encode workspace taken from `ws` (no allocation of any kind).
+// The protected BF16 GEMM of ftblas_gemm_ex with the encode workspace taken from `ws`
+// (no allocation of any kind).
 int gemm_bf16_ft_with_workspace(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, const void* alpha,
                                 const void* A, int Atype, int64_t lda, const void* B, int Btype, int64_t ldb,
                                 const void* beta, void* C, int Ctype, int64_t ldc, int ctype, const float* a_scale,
                                 const float* b_scale, void* stream, ft_report_t* report, void* ws, size_t ws_bytes) {
-  if (layout != FTBLAS_ROW_MAJOR && layout != FTBLAS_COL_MAJOR) return -1;
-  if (ta != FTBLAS_NO_TRANS && ta != FTBLAS_TRANS) return -2;
-  if (tb != FTBLAS_NO_TRANS && tb != FTBLAS_TRANS) return -3;
-  if (M < 0) return -4;
-  if (N < 0) return -5;
-  if (K < 0) return -6;
-  if (alpha == nullptr) return -7;
-  if (beta == nullptr) return -14;
-  const bool bf16 = Atype == FTBLAS_R_16BF && Btype == FTBLAS_R_16BF && Ctype == FTBLAS_R_32F && ctype == FTBLAS_R_32F;
-  if (!bf16) return FTBLAS_STATUS_NOT_SUPPORTED;
-  if (a_scale != nullptr) return -19;
-  if (b_scale != nullptr) return -20;
-  const bool need_ab = (K > 0 && *static_cast<const float*>(alpha) != 0.0f && M > 0 && N > 0);
-  int v = validate(layout, ta, tb, M, N, K, A, lda, B, ldb, C, ldc, need_ab);
-  if (v != 0) {
-    static const int pos[15] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 11, 13, 14, 15, 17};
-    return -pos[-v];
-  }
-  if (M > kMaxDim || N > kMaxDim || K > kMaxDim) return FTBLAS_STATUS_NOT_SUPPORTED;
-  const Frame f = map_frame(layout, ta, tb, M, N, A, lda, B, ldb);
-  if (M > 0 && N > 0 && tc_workspace_bytes((int32_t)f.M, (int32_t)f.N, (int32_t)K) > ws_bytes)
-    return FTBLAS_STATUS_WORKSPACE_LIMIT;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (report != nullptr) {
-    if (int e = record_cuda(cudaMemsetAsync(report, 0, sizeof(ft_report_t), st))) return e;
-  }
-  if (M == 0 || N == 0) return 0;
-  CallerPoint pts[kMaxInject];
-  const int64_t tile_rows = f.swap ? kTcBNProt : kTcBM, tile_cols = f.swap ? kTcBM : kTcBNProt;
-  const int npts = plan_injections(M, N, tile_rows, tile_cols, pts);
-  const float al = *static_cast<const float*>(alpha), be = *static_cast<const float*>(beta);
-  if (!f.a_kmajor || !f.b_kmajor) return FTBLAS_STATUS_NOT_SUPPORTED;
-  if (K == 0 || al == 0.0f) return FTBLAS_STATUS_NOT_SUPPORTED;
-  TcParams p;
-  std::memset(&p, 0, sizeof(p));
-  p.M = (int32_t)f.M; p.N = (int32_t)f.N; p.K = (int32_t)K;
-  p.alpha = al; p.beta = be; p.u_acc = 0x1p-23f;
-  p.A = f.A; p.lda = f.lda; p.B = f.B; p.ldb = f.ldb;
-  p.C = static_cast<float*>(C); p.ldc = ldc;
-  p.report = report;
-  p.swap_report = f.swap;
-  for (int q = 0; q < npts; ++q) {
-    InjectPoint& ip = p.inj.p[p.inj.n++];
-    const CallerPoint& c = pts[q];
-    ip.i = (int32_t)(f.swap ? c.j : c.i);
-    ip.j = (int32_t)(f.swap ? c.i : c.j);
-    ip.site = c.site == FT_SITE_CHECKSUM ? kSiteChecksumRow : c.site;
-    ip.mode = c.mode; ip.bit = c.bit; ip.rel_log2 = c.rel_log2; ip.sign = c.sign; ip.pad = 0;
-  }
-  CUtensorMap tmA, tmB, tmC;
-  std::memset(&tmA, 0, sizeof(tmA)); std::memset(&tmB, 0, sizeof(tmB)); std::memset(&tmC, 0, sizeof(tmC));
-  if (!make_map_b16_sw128(&tmA, f.A, K, f.M, f.lda, 64, kTcBM)) return FTBLAS_STATUS_NOT_SUPPORTED;
-  if (!make_map_b16_sw128(&tmB, f.B, K, f.N, f.ldb, 64, kTcBNProt)) return FTBLAS_STATUS_NOT_SUPPORTED;
-  g_last_used_tma = 1;
-  TcWorkspace w = tc_workspace_carve(ws, p.M, p.N, p.K);
-  p.rowAbsA = w.rowAbsA; p.maxAbsBe = w.maxAbsBe; p.sA = w.sA; p.absSA = w.absSA;
-  p.sa_pitch = w.kpitch; p.pend = w.pend;
-  const int64_t nNb = (f.N + kTcBNProt - 1) / kTcBNProt;
-  if (!make_map_b16_sw128(&tmC, w.chk, K, nNb * kTcChkRows, w.kpitch, 64, kTcChkRows))
-    return FTBLAS_STATUS_NOT_SUPPORTED;
-  int rc = record_cuda(launch_tc_encode(p, w, st));  // writes every workspace entry the GEMM reads
-  if (rc == 0) rc = record_cuda(launch_tc_gemm(p, &tmA, &tmB, &tmC, true, st));
-  return rc;
+  if (ws == nullptr) return FTBLAS_STATUS_WORKSPACE_LIMIT;
+  return tc_gemm_impl(layout, ta, tb, M, N, K, alpha, A, Atype, lda, B, Btype, ldb, beta, C, Ctype, ldc, ctype, a_scale,
+                      b_scale, stream, report, true, ws, ws_bytes, false);
 }
 
 }  // namespace ftk

@@ -50,16 +50,50 @@ def uniform(seed: int, matrix_id: int, count: int, chunk: int = 1 << 24) -> np.n
     return out
 
 
-def normal(seed: int, matrix_id: int, count: int) -> np.ndarray:
-    """Standard normal values by the Box-Muller transform of two uniform streams (host libm)."""
+def _chunks(count: int, threads: int, fn, chunk: int = 1 << 22) -> None:
+    """Run fn(s, e) over [0, count) in chunks, on `threads` threads (numpy releases the GIL
+    in its array loops); fn writes disjoint slices, so the result is order-independent."""
+    spans = [(s, min(count, s + chunk)) for s in range(0, count, chunk)]
+    if threads <= 1 or len(spans) <= 1:
+        for s, e in spans:
+            fn(s, e)
+        return
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda se: fn(*se), spans))
+
+
+def normal(seed: int, matrix_id: int, count: int, threads: int = 1) -> np.ndarray:
+    """Standard normal values by the Box-Muller transform of two uniform streams (host libm):
+    pair q gives values q (cosine) and n2 + q (sine), n2 = ceil(count / 2)."""
     n2 = (count + 1) // 2
-    x1 = splitmix64(seed, matrix_id, np.arange(0, n2, dtype=np.uint64))
-    x2 = splitmix64(seed, matrix_id ^ 0x55, np.arange(0, n2, dtype=np.uint64))
-    u1 = ((x1 >> np.uint64(11)).astype(np.float64) + 1.0) * (2.0 ** -53)  # (0, 1]
-    u2 = (x2 >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)          # [0, 1)
-    r = np.sqrt(-2.0 * np.log(u1))
-    z = np.concatenate([r * np.cos(2.0 * np.pi * u2), r * np.sin(2.0 * np.pi * u2)])
+    z = np.empty(2 * n2, dtype=np.float64)
+
+    def work(s, e):
+        idx = np.arange(s, e, dtype=np.uint64)
+        x1 = splitmix64(seed, matrix_id, idx)
+        x2 = splitmix64(seed, matrix_id ^ 0x55, idx)
+        u1 = ((x1 >> np.uint64(11)).astype(np.float64) + 1.0) * (2.0 ** -53)  # (0, 1]
+        u2 = (x2 >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)          # [0, 1)
+        r = np.sqrt(-2.0 * np.log(u1))
+        z[s:e] = r * np.cos(2.0 * np.pi * u2)
+        z[n2 + s:n2 + e] = r * np.sin(2.0 * np.pi * u2)
+
+    _chunks(n2, threads, work)
     return z[:count]
+
+
+def map_elementwise(fn, x: np.ndarray, out_dtype, threads: int = 1) -> np.ndarray:
+    """fn applied to the elements of x (flattened in C order, reshaped back), in chunks on
+    `threads` threads; fn must be elementwise (e.g. to_bf16_bits, to_e4m3_bits)."""
+    flat = np.ascontiguousarray(x).reshape(-1)
+    out = np.empty(flat.size, dtype=out_dtype)
+
+    def work(s, e):
+        out[s:e] = fn(flat[s:e])
+
+    _chunks(flat.size, threads, work)
+    return out.reshape(np.shape(x))
 
 
 def randint(seed: int, matrix_id: int, count: int, lo: int, hi: int) -> np.ndarray:
@@ -106,8 +140,11 @@ def uniform_matrix(seed: int, matrix_id: int, rows: int, cols: int) -> np.ndarra
     return uniform(seed, matrix_id, rows * cols).reshape(cols, rows).T
 
 
-def normal_matrix(seed: int, matrix_id: int, rows: int, cols: int, std: float = 1.0) -> np.ndarray:
-    return (std * normal(seed, matrix_id, rows * cols)).reshape(cols, rows).T
+def normal_matrix(seed: int, matrix_id: int, rows: int, cols: int, std: float = 1.0, threads: int = 1) -> np.ndarray:
+    z = normal(seed, matrix_id, rows * cols, threads)
+    if std != 1.0:
+        z *= std
+    return z.reshape(cols, rows).T
 
 
 def pow2_row_scales(seed: int, matrix_id: int, count: int, lo: int = -8, hi: int = 8) -> np.ndarray:
