@@ -290,3 +290,139 @@ def dgemm(a, b, c=None, alpha=1.0, beta=0.0, trans_a=False, trans_b=False, repor
                                  float(beta), c.data_ptr(), ldc, st)
     check(rc, "ftblas_dgemm")
     return c
+
+
+# ---------------------------------------------------------------------------------------
+# Torch-level API: gemm on tensors of any supported dtype, and a protected linear layer.
+# ---------------------------------------------------------------------------------------
+
+def _kmajor_rows(x):
+    """x (rows x K) as a row-major tensor whose rows are K-contiguous, 16-byte aligned and
+    with a 16-byte multiple pitch (what the tensor maps need); copies when x is not."""
+    import torch
+    es = x.element_size()
+    if (x.stride(1) == 1 and x.stride(0) >= max(1, x.shape[1]) and (x.stride(0) * es) % 16 == 0
+            and x.data_ptr() % 16 == 0):
+        return x, x.stride(0)
+    pitch = -(-max(1, x.shape[1]) * es // 16) * 16 // es
+    y = torch.zeros((x.shape[0], pitch), dtype=x.dtype, device=x.device)[:, :x.shape[1]]
+    y.copy_(x)
+    return y, pitch
+
+
+def gemm(a, b, c=None, alpha=1.0, beta=0.0, trans_a=False, trans_b=False, report=None, protect=True,
+         a_scale=None, b_scale=None, stream=None):
+    """c = alpha * op(a) @ op(b) + beta * c on CUDA tensors, protected by ABFT.
+
+    float64 operands run the FP64 kernel (c float64, see dgemm). bfloat16 or
+    float8_e4m3fn operands run the tensor-core kernel with FP32 accumulation and an FP32
+    c; a_scale / b_scale are 1-element float32 CUDA tensors (FP8 per-tensor scales) or
+    None. The tensor-core kernel reads K-contiguous operands: op(a) and op(b)^T are copied
+    to that form when they are not already in it. ``report``: a buffer from new_report()
+    (or None). Returns c.
+    """
+    import torch
+    if a.dtype == torch.float64:
+        return dgemm(a, b, c, alpha, beta, trans_a, trans_b, report, protect, stream)
+    fp8 = a.dtype == getattr(torch, "float8_e4m3fn", None)
+    if a.dtype != b.dtype or not (a.dtype == torch.bfloat16 or fp8):
+        raise TypeError(f"unsupported operand dtypes {a.dtype}, {b.dtype}")
+    opa = a.t() if trans_a else a          # M x K
+    opb_t = b if trans_b else b.t()        # N x K
+    M, K = opa.shape
+    N, Kb = opb_t.shape
+    if K != Kb:
+        raise ValueError(f"inner dimensions differ: {K} vs {Kb}")
+    if c is None:
+        if beta != 0.0:
+            raise ValueError("beta != 0 needs c")
+        c = torch.empty((M, N), dtype=torch.float32, device=a.device)
+    if c.dtype != torch.float32:
+        raise TypeError("c must be float32 for bfloat16 / float8 operands")
+    if c.shape != (M, N):
+        raise ValueError(f"c has shape {tuple(c.shape)}, expected {(M, N)}")
+    if c.stride(1) != 1:
+        if c.stride(0) == 1:  # column-major c: compute c^T = op(b)^T op(a)^T into its row-major view
+            return gemm(b, a, c.t(), alpha, beta, not trans_b, not trans_a, report, protect, b_scale, a_scale, stream)
+        raise ValueError("c must have a unit stride in one dimension")
+    a2, lda = _kmajor_rows(opa)
+    b2, ldb = _kmajor_rows(opb_t)
+    st = stream if stream is not None else torch.cuda.current_stream(a.device).cuda_stream
+    dt = R_8F_E4M3 if fp8 else R_16BF
+    sa = a_scale.data_ptr() if a_scale is not None else None
+    sb = b_scale.data_ptr() if b_scale is not None else None
+    args = (ROW_MAJOR, NO_TRANS, TRANS, M, N, K, float(alpha), a2.data_ptr(), dt, lda, b2.data_ptr(), dt, ldb,
+            float(beta), c.data_ptr(), R_32F, max(1, c.stride(0)), R_32F, sa, sb, st)
+    if protect:
+        rc = ftblas_gemm_ex(*args, report.data_ptr() if report is not None else None)
+    else:
+        rc = ftblas_gemm_ex_noabft(*args)
+    check(rc, "ftblas_gemm_ex")
+    return c
+
+
+class FTMonitor:
+    """Collects the report of every protected GEMM issued through it (one device buffer per
+    call); summary() synchronises and sums them."""
+
+    def __init__(self, device=None):
+        self.device = device
+        self.reports = []
+
+    def next_report(self):
+        r = new_report(self.device)
+        self.reports.append(r)
+        return r
+
+    def summary(self):
+        tot = dict(calls=len(self.reports), tiles_checked=0, detected=0, corrected=0, uncorrectable=0,
+                   checksum_only=0, status=0)
+        for buf in self.reports:
+            r = report_from_device(buf)
+            for k in ("tiles_checked", "detected", "corrected", "uncorrectable", "checksum_only"):
+                tot[k] += int(getattr(r, k))
+            tot["status"] |= int(r.status)
+        return tot
+
+
+def _ft_linear_class():
+    import torch
+
+    class FTLinearFn(torch.autograd.Function):
+        """Y = X W^T with every GEMM ABFT-protected: the forward product and, in the
+        backward pass, dX = dY W and dW = dY^T X. float64 X, W run the FP64 kernel (Y and
+        the gradients float64). bfloat16 X, W run the tensor-core kernel: Y is float32
+        (the accumulation precision), dY is rounded to bfloat16 for the two backward
+        products and the gradients are returned in bfloat16. ``monitor`` (an FTMonitor
+        or None) receives the three calls' reports."""
+
+        @staticmethod
+        def forward(ctx, x, w, monitor=None):
+            ctx.save_for_backward(x, w)
+            ctx.monitor = monitor
+            rep = monitor.next_report() if monitor is not None else None
+            return gemm(x, w, trans_b=True, report=rep)
+
+        @staticmethod
+        def backward(ctx, dy):
+            x, w = ctx.saved_tensors
+            mon = ctx.monitor
+            dyq = dy.to(x.dtype) if x.dtype != dy.dtype else dy
+            dx = dw = None
+            if ctx.needs_input_grad[0]:
+                dx = gemm(dyq, w, report=mon.next_report() if mon is not None else None)
+                dx = dx.to(x.dtype) if dx.dtype != x.dtype else dx
+            if ctx.needs_input_grad[1]:
+                dw = gemm(dyq, x, trans_a=True, report=mon.next_report() if mon is not None else None)
+                dw = dw.to(w.dtype) if dw.dtype != w.dtype else dw
+            return dx, dw, None
+
+    return FTLinearFn
+
+
+def __getattr__(name):
+    if name == "FTLinearFn":
+        cls = _ft_linear_class()
+        globals()["FTLinearFn"] = cls
+        return cls
+    raise AttributeError(name)
