@@ -59,6 +59,11 @@ def parse_args():
     ap.add_argument("--fp8-size", type=int, default=16384, help="M = N = K of the FP8 measurement")
     ap.add_argument("--bf16-only", action="store_true",
                     help="measure only the BF16 tensor-core form (for profiling); prints its own JSON line")
+    ap.add_argument("--soak", type=float, default=0.0, metavar="SECONDS",
+                    help="run only the soak (config 5a): back-to-back FT-DGEMM with Poisson-drawn injections")
+    ap.add_argument("--soak-rate", type=float, default=5.0, help="injections per second in the soak")
+    ap.add_argument("--linear-only", action="store_true", help="measure only the protected linear layer (config 4)")
+    ap.add_argument("--no-linear", action="store_true", help="skip the protected linear layer (config 4)")
     ap.add_argument("--fp8-only", action="store_true",
                     help="measure only the FP8 tensor-core form (for profiling); prints its own JSON line")
     return ap.parse_args()
@@ -297,6 +302,166 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
     }
 
 
+def run_linear(dev, steps, warmup, T=8192, n_in=4096, n_out=4096):
+    """Config 4: Y = X W^T through FTLinearFn with X (T x n_in) BF16 N(0,1), W (n_out x n_in)
+    BF16 N(0, 0.02), dY N(0,1): forward (T, n_out, n_in), dX = dY W (T, n_in, n_out) and
+    dW = dY^T X (n_out, n_in, T), all three protected, one injected output fault
+    (2^12..2^14 |C|) per GEMM pass. Reports the fwd+bwd step time as TFLOP/s (6 T n_in n_out
+    flops per step), the faults corrected, and the gradients' error against binary64
+    products of the same BF16 values on sampled rows."""
+    import torch
+
+    import paper_2104_00897_gb300 as fb
+    import synth as S
+
+    threads = max(1, min(16, os.cpu_count() or 1))
+    seed = SEED + 4
+    X = S.map_elementwise(S.to_bf16_bits, S.normal_matrix(seed, 0, T, n_in, threads=threads), np.uint16, threads)
+    W = S.map_elementwise(S.to_bf16_bits, S.normal_matrix(seed, 1, n_out, n_in, std=0.02, threads=threads), np.uint16,
+                          threads)
+    dY = S.normal_matrix(seed, 2, T, n_out, threads=threads)
+    x = torch.from_numpy(np.ascontiguousarray(X).view(np.int16)).to(dev).view(torch.bfloat16).requires_grad_(True)
+    w = torch.from_numpy(np.ascontiguousarray(W).view(np.int16)).to(dev).view(torch.bfloat16).requires_grad_(True)
+    dy = torch.from_numpy(np.ascontiguousarray(dY)).to(dev).float()
+    Fn = fb.FTLinearFn
+
+    def step(mon):
+        x.grad = None
+        w.grad = None
+        y = Fn.apply(x, w, mon)
+        y.backward(dy)
+
+    fb.ftblas_set_injection(fb.make_injection(seed=seed, site=fb.SITE_OUTPUT, mode=fb.MODE_ADD_REL, log2_lo=12,
+                                              log2_hi=14, every_n_launches=1, errors_per_launch=1))
+    for _ in range(warmup):
+        step(None)
+    torch.cuda.synchronize(dev)
+    mon = fb.FTMonitor(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step(mon)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    fb.ftblas_set_injection(None)
+    ms = e0.elapsed_time(e1) / steps
+    summ = mon.summary()
+    # gradient error on sampled rows (the faulted elements were corrected from the checksums)
+    rows = np.unique(S.randint(seed, 9, 4, 0, n_out - 1))
+    Wf = S.bf16_bits_to_f64(W)
+    dYq = S.bf16_bits_to_f64(S.to_bf16_bits(dy.double().cpu().numpy()))
+    dX = x.grad.double().cpu().numpy()[rows]
+    ref = dYq[rows] @ Wf
+    err_dx = float(np.max(np.abs(dX - ref) / (np.abs(dYq[rows]) @ np.abs(Wf))))
+    Xf = S.bf16_bits_to_f64(X)
+    dW = w.grad.double().cpu().numpy()[rows]
+    ref = dYq[:, rows].T @ Xf
+    err_dw = float(np.max(np.abs(dW - ref) / (np.abs(dYq[:, rows]).T @ np.abs(Xf))))
+    return {
+        "workload": f"FTLinearFn Y = X W^T, X {T}x{n_in} BF16 N(0,1), W {n_out}x{n_in} BF16 N(0,0.02), dY N(0,1); "
+                    "forward + backward (3 protected GEMMs, operand transposes by copy)",
+        "step_ms": ms, "tflops": 6.0 * T * n_in * n_out / ms / 1e9, "gemm_calls": summ["calls"],
+        "faults_injected": summ["calls"], "detected": summ["detected"], "corrected": summ["corrected"],
+        "uncorrectable": summ["uncorrectable"],
+        "grad_error_over_sum_abs": {"dX": err_dx, "dW": err_dw, "rows_sampled": int(len(rows)),
+                                    "note": "bfloat16 gradients vs binary64 products of the same BF16 values"},
+    }
+
+
+def run_soak(dev, n, seconds, seed=SEED + 50, rate_per_s=5.0, batch=256, bit_lo=40, bit_hi=62):
+    """Soak (config 5a): the FP64 FT-DGEMM (alpha = 1, beta = 0, U[-1,1] operands) launched
+    back to back for `seconds`. Before each launch a Poisson(rate x launch time) number of
+    accumulator bit flips (bits bit_lo..bit_hi, after BK floor(nk/2) products) is drawn on
+    distinct tiles and installed as that launch's plan. Reports come back through a ring of
+    `batch` report buffers read once per batch. Tally: a tile with an injection and a record
+    is detected (corrected or not); a record in a tile without one is a false alarm; an
+    injected tile without a record is undetected (an error at or below the threshold). The
+    final C is compared with a clean run's: bitwise equal when every injected error was
+    corrected, since the FP64 correction recomputes the element exactly."""
+    import torch
+
+    import paper_2104_00897_gb300 as fb
+
+    A, B, _ = gen_inputs(n, seed)
+    dA = torch.from_numpy(A).to(dev)
+    dB = torch.from_numpy(B).to(dev)
+    dC = torch.empty(n * n, dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    tr, tc, _ = fb.ftblas_verification_tile(fb.COL_MAJOR, fb.R_64F, n, n, n)
+    ntr, ntc = -(-n // tr), -(-n // tc)
+    reps = torch.zeros((batch, fb.REPORT_BYTES), dtype=torch.uint8, device=dev)
+
+    def call(slot):
+        fb.check(fb.ftblas_dgemm(fb.COL_MAJOR, fb.NO_TRANS, fb.NO_TRANS, n, n, n, 1.0, dA.data_ptr(), n,
+                                 dB.data_ptr(), n, 0.0, dC.data_ptr(), n, st, reps[slot].data_ptr()), "ftblas_dgemm")
+
+    fb.ftblas_set_injection(None)
+    for _ in range(3):
+        call(0)
+    torch.cuda.synchronize(dev)
+    clean = dC.clone()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        call(0)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    t_launch = e0.elapsed_time(e1) / 10 / 1e3
+    lam = rate_per_s * t_launch
+    batch = int(max(1, min(batch, seconds / t_launch / 8)))  # about 8 report read-backs over the soak
+    rng = np.random.Generator(np.random.PCG64(seed))
+    tally = dict(launches=0, injected=0, detected=0, corrected=0, uncorrectable=0, checksum_only=0, undetected=0,
+                 false_alarms=0, status=0)
+    import time
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        plans = []
+        for b in range(batch):
+            k = min(int(rng.poisson(lam)), fb.MAX_FIXED_INJECTIONS, ntr * ntc)
+            tiles = rng.choice(ntr * ntc, size=k, replace=False) if k else []
+            pts = []
+            for t in tiles:
+                r0, c0 = (int(t) % ntr) * tr, (int(t) // ntr) * tc
+                pts.append(dict(i=r0 + int(rng.integers(0, min(tr, n - r0))), j=c0 + int(rng.integers(0, min(tc, n - c0))),
+                                site=fb.SITE_ACCUM, mode=fb.MODE_BITFLIP, bit=int(rng.integers(bit_lo, bit_hi + 1))))
+            fb.ftblas_set_injection(fb.make_injection(fixed=pts) if pts else None)
+            call(b)
+            plans.append(pts)
+        host = reps.cpu().numpy()
+        for b, pts in enumerate(plans):
+            r = fb.FtReport.from_buffer_copy(host[b].tobytes())
+            inj_tiles = {(p["i"] // tr, p["j"] // tc) for p in pts}
+            rec_tiles = {}
+            for rec in r.records():
+                rec_tiles[(rec.tile_row, rec.tile_col)] = rec.kind
+            tally["launches"] += 1
+            tally["injected"] += len(pts)
+            tally["status"] |= int(r.status)
+            for key, kind in rec_tiles.items():
+                if key in inj_tiles:
+                    tally["detected"] += 1
+                    tally["corrected"] += kind == fb.KIND_CORRECTED
+                    tally["uncorrectable"] += kind == fb.KIND_UNCORRECTABLE
+                    tally["checksum_only"] += kind == fb.KIND_CHECKSUM_ONLY
+                else:
+                    tally["false_alarms"] += 1
+            tally["undetected"] += len(inj_tiles - set(rec_tiles))
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    fb.ftblas_set_injection(None)
+    last_pts = plans[-1]
+    tally.update({
+        "workload": f"ft_dgemm_{n}x{n}x{n} back to back, alpha=1, beta=0, U[-1,1]",
+        "seconds": wall, "launch_ms": 1e3 * t_launch, "poisson_lambda_per_launch": lam,
+        "injections_per_minute": 60.0 * tally["injected"] / wall,
+        "sustained_tflops": tally["launches"] * 2.0 * n ** 3 / wall / 1e12,
+        "injection": f"accumulator bit flips, bits {bit_lo}..{bit_hi}, distinct tiles",
+        "final_c_equals_clean": bool(torch.equal(dC, clean)),
+        "last_launch_injections": len(last_pts),
+    })
+    return tally
+
+
 # ------------------------------------------------------------------ reference arm (the oracle)
 def run_reference(args, rank, world):
     if rank != 0:
@@ -338,6 +503,14 @@ def run_ours(args, rank, world, dist):
     dev = torch.device("cuda", local)
     fb.load()
     n = args.size
+    if args.linear_only:
+        if rank == 0:
+            print(json.dumps({"linear_bf16": run_linear(dev, args.steps, args.warmup)}), flush=True)
+        return 0
+    if args.soak > 0:
+        if rank == 0:
+            print(json.dumps({"soak": run_soak(dev, n, args.soak, rate_per_s=args.soak_rate)}), flush=True)
+        return 0
     if args.bf16_only or args.fp8_only:
         if rank == 0:
             kind = "bf16" if args.bf16_only else "fp8"
@@ -487,6 +660,9 @@ def run_ours(args, rank, world, dist):
         bf16 = run_tc(args, dev, "bf16", n, args.steps, args.warmup, fp64_ft)
     if not args.no_fp8 and rank == 0:
         fp8 = run_tc(args, dev, "fp8", args.fp8_size, args.steps, args.warmup, fp64_ft)
+    linear = None
+    if not args.no_linear and rank == 0:
+        linear = run_linear(dev, args.steps, args.warmup)
 
     if rank != 0:
         return 0
@@ -533,6 +709,7 @@ def run_ours(args, rank, world, dist):
         "cpu_baseline": cpu,
         "bf16": bf16,
         "fp8_e4m3": fp8,
+        "linear_bf16": linear,
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clocks,
