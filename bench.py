@@ -87,8 +87,42 @@ def peaks():
     else:
         tensor = 1900.0 * 1.25 / 2250.0
         tensor_src = "fallback bf16 1900 TFLOP/s x nominal FP64/BF16 ratio 1.25/2250"
+    bf16_peak = bf16 if bf16 is not None else 1900.0
+    bf16_src = (f"measured bf16 {bf16} TFLOP/s (burst)" if bf16 is not None
+                else "fallback bf16 1900 TFLOP/s (burst)")
     return dict(alu=alu, alu_src=f"2 FP64 FMA/clk/SM x 152 SMs x {sm_max} MHz", tensor=tensor,
-                tensor_src=tensor_src)
+                tensor_src=tensor_src, bf16=bf16_peak, bf16_src=bf16_src)
+
+
+FP64_KERNEL_SOURCES = ("paper_2104_00897_gb300/csrc/ft_dgemm.cu", "paper_2104_00897_gb300/csrc/ft_device.cuh",
+                       "paper_2104_00897_gb300/csrc/ft_internal.h")
+TC_KERNEL_SOURCES = ("paper_2104_00897_gb300/csrc/ft_gemm_tc.cu", "paper_2104_00897_gb300/csrc/ft_device.cuh",
+                     "paper_2104_00897_gb300/csrc/ft_internal.h", "paper_2104_00897_gb300/csrc/ft_tc.h")
+
+
+def sources_sha256(paths):
+    import hashlib
+    h = hashlib.sha256()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profile_traffic(name, sources):
+    """DRAM bytes per launch (read + write) from the committed ncu summary profiles/<name>.md,
+    or None when the summary is missing or the kernel's sources changed since the capture
+    (the summary records their SHA-256)."""
+    import re
+    path = os.path.join(ROOT, "profiles", name + ".md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_t = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
+    m_h = re.search(r"sources_sha256:\s*([0-9a-f]{64})", text)
+    if not m_t or not m_h or m_h.group(1) != sources_sha256(sources):
+        return None
+    return int(m_t.group(1))
 
 
 def workload_config(n, engine):
@@ -228,6 +262,8 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
         else:
             fb.check(fb.ftblas_gemm_ex_noabft(*a), "ftblas_gemm_ex_noabft")
 
+    kernel_ms = {}
+
     def timed(protect, inject):
         if inject:
             # output errors of 2^p |C|, p above the rigorous threshold's reach (2^8 for BF16 at
@@ -242,11 +278,14 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
             call(protect)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fb.ftblas_kernel_timing_begin()
         e0.record()
         for s_ in range(steps):
             call(protect, reps[s_])
         e1.record()
         torch.cuda.synchronize(dev)
+        _, kms, kn = fb.ftblas_kernel_timing_end()
+        kernel_ms[(protect, inject)] = kms / kn if kn else None
         ms = e0.elapsed_time(e1) / steps
         corr = sum(int(fb.report_from_device(r).corrected) for r in reps) if protect else 0
         det = sum(int(fb.report_from_device(r).detected) for r in reps) if protect else 0
@@ -285,6 +324,19 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
         det_map[str(p)] = hits / trials
     fb.ftblas_set_injection(None)
     u = "2^-22" if fp8 else "2^-23"
+    pk = peaks()
+    peak = pk["bf16"] * (2.0 if fp8 else 1.0)
+    k_ft, k_na = kernel_ms.get((True, False)), kernel_ms.get((False, False))
+    roof = None
+    if k_ft:
+        prof = f"tc_gemm_kernel_{kind}_ft_{n}_dram"
+        roof = {"bound": "tensor", "achieved": flops / k_ft / 1e9, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / k_ft / 1e9 / peak,
+                "traffic": profile_traffic(prof, TC_KERNEL_SOURCES),
+                "peak_source": pk["bf16_src"] + (" x 2 (nominal FP8:BF16 dense ratio 4.5/2.25)" if fp8 else ""),
+                "kernel": f"tc_gemm_kernel<FT, {kind.upper()}> (protected product kernel; encode and resolve "
+                          "kernels excluded)", "kernel_ms": k_ft,
+                "noabft_kernel_frac": (flops / k_na / 1e9 / peak) if k_na else None}
     values = ("N(0,1) quantised per tensor to E4M3 (scale = amax/448)" if fp8
               else "N(0,1), A rows scaled by 2^u (u in [-8, 8])")
     return {
@@ -298,6 +350,7 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
                           "sampled": f"{len(rows)} rows x {len(cols)} columns",
                           "note": f"C - (A B computed in binary64 from the same {kind.upper()} operands)"},
         "detection_map_rel_log2": det_map,
+        "roofline": roof,
         "threshold": f"rigorous: gamma_K({u}) |alpha| (sum_k|A(i,k)|)(max_k sum_j|B(k,j)|) (1 + s) + 2^-23 (sum|C|)",
     }
 
@@ -567,6 +620,7 @@ def run_ours(args, rank, world, dist):
             sampler.__enter__()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
+        fb.ftblas_kernel_timing_begin()
         t0.record(stream)
         for s in range(steps):
             ev[s][0].record(stream)
@@ -574,6 +628,7 @@ def run_ours(args, rank, world, dist):
             ev[s][1].record(stream)
         t1.record(stream)
         barrier()
+        _, kms, kn = fb.ftblas_kernel_timing_end()
         if sampler:
             sampler.__exit__(None, None, None)
         total_ms = max_over_ranks(t0.elapsed_time(t1))
@@ -590,7 +645,8 @@ def run_ours(args, rank, world, dist):
         if protect and inject:
             injected = sum(1 for L in range(warmup, warmup + steps) if L % 10 == ((warmup + 1) % 10))
         fb.ftblas_set_injection(None)
-        return total_ms, per, rsum, injected, (sampler.summary() if sampler else None)
+        kernel_per = [kms / kn] * kn if kn == steps else per
+        return total_ms, kernel_per, rsum, injected, (sampler.summary() if sampler else None)
 
     results = {}
     engine_list = [args.engine] + ([] if args.no_second_engine else [e for e in engines if e != args.engine])
@@ -704,7 +760,8 @@ def run_ours(args, rank, world, dist):
                    "false_alarms_clean_run": h["clean_rep"]["detected"], "status": h["ft_rep"]["status"]},
         "engines": engines_out,
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "peak_source": pk["alu_src"] if bound == "alu" else pk["tensor_src"],
+                     "traffic": (profile_traffic(f"dgemm_kernel_ft_{args.engine}_{n}_dram", FP64_KERNEL_SOURCES)
+                                 if n == 8192 else None), "peak_source": pk["alu_src"] if bound == "alu" else pk["tensor_src"],
                      "kernel": "dgemm_kernel (FT, " + args.engine + ")", "kernel_ms": kernel_ms},
         "cpu_baseline": cpu,
         "bf16": bf16,

@@ -258,6 +258,17 @@ int ftblas_last_cuda_error(void);
 /* Library version, e.g. "0.1.0". */
 const char* ftblas_version(void);
 
+/* Device time of the product kernels, for measurement. After ftblas_kernel_timing_begin,
+ * every GEMM call (any entry point, protected or not) records a pair of CUDA events on its
+ * stream around its product kernel only: the encode, resolve and scaling kernels and the
+ * report clear fall outside the pair. ftblas_kernel_timing_end stops recording, waits for
+ * the recorded events, frees them, and returns in *total_ms the summed durations and in
+ * *launches the number of timed launches (either pointer may be NULL). Returns 0, or
+ * FTBLAS_STATUS_CUDA_ERROR if an event could not be created, recorded or read (those
+ * launches are left out). Process-wide; begin discards pairs not yet collected. */
+int ftblas_kernel_timing_begin(void);
+int ftblas_kernel_timing_end(double* total_ms, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

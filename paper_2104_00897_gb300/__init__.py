@@ -93,6 +93,8 @@ SIGNATURES = {
     "ftblas_last_cuda_error": (C.c_int, []),
     "ftblas_last_launch_used_tma": (C.c_int, []),
     "ftblas_version": (C.c_char_p, []),
+    "ftblas_kernel_timing_begin": (C.c_int, []),
+    "ftblas_kernel_timing_end": (C.c_int, [C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -202,6 +204,18 @@ def ftblas_version():
 
 
 # ------------------------------------------------------------------ helpers
+def ftblas_kernel_timing_begin():
+    return _call("ftblas_kernel_timing_begin")
+
+
+def ftblas_kernel_timing_end():
+    """Returns (rc, total_ms, launches) of the product kernels timed since begin."""
+    t = C.c_double(0.0)
+    n = C.c_int64(0)
+    rc = _call("ftblas_kernel_timing_end", C.byref(t), C.byref(n))
+    return rc, t.value, n.value
+
+
 def make_injection(seed=0, site=SITE_ACCUM, mode=MODE_BITFLIP, bit_lo=40, bit_hi=62, log2_lo=0, log2_hi=0,
                    every_n_launches=0, errors_per_launch=0, fixed=()):
     """Build an FtInject. ``fixed``: iterable of dicts with i, j and optional site, mode,

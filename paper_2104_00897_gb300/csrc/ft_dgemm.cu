@@ -609,7 +609,9 @@ cudaError_t launch_one(const DgemmParams& p, const CUtensorMap* tmA, const CUten
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DSmem));
   if (e != cudaSuccess) return e;
   dim3 grid((p.M + BM - 1) / BM, (p.N + BN - 1) / BN);
+  kernel_timer_start(st);
   kern<<<grid, NT, sizeof(DSmem), st>>>(*tmA, *tmB, p);
+  kernel_timer_stop(st);
   return cudaGetLastError();
 }
 

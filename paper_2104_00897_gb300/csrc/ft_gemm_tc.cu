@@ -984,7 +984,9 @@ static cudaError_t launch_gemm_kind(const TcParams& p, const CUtensorMap* tmA, c
   const int grid = (int)(tiles < sms ? tiles : sms);
   cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<FT, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  kernel_timer_start(st);
   tc_gemm_kernel<FT, KIND><<<grid, NTHREADS, smem, st>>>(*tmA, *tmB, *tmChk, p);
+  kernel_timer_stop(st);
   e = cudaGetLastError();
   if (e != cudaSuccess || !FT) return e;
   tc_resolve_kernel<KIND><<<2 * sms, kResolveWarps * 32, 0, st>>>(p);

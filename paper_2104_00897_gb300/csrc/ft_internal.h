@@ -59,6 +59,11 @@ enum Fp64Engine : int { kEngineDFMA = 0, kEngineDMMA = 1 };
 cudaError_t launch_dgemm(const DgemmParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB,
                          bool ft, int engine, cudaStream_t stream);
 
+// Product-kernel timing (ftblas_kernel_timing_begin / _end): event records on `stream`
+// immediately before and after a product kernel launch; no-ops unless timing is on.
+void kernel_timer_start(cudaStream_t stream);
+void kernel_timer_stop(cudaStream_t stream);
+
 // C = beta * C over an M x N column-major kernel-frame matrix (quick-return path).
 cudaError_t launch_scale(double* C, int64_t ldc, int32_t M, int32_t N, double beta, cudaStream_t stream);
 

@@ -7,6 +7,7 @@
 #include <atomic>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "ft_internal.h"
 #include "ft_tc.h"
@@ -377,6 +378,21 @@ cudaError_t copy_runs(double* dst, int64_t dpitch, const double* src, int64_t sp
   return cudaMemcpy2DAsync(dst, dpitch * 8, src, spitch * 8, run * 8, cnt, kind, st);
 }
 
+// product-kernel timing (ftblas_kernel_timing_begin / _end)
+std::mutex g_timer_mu;
+bool g_timer_on = false;
+bool g_timer_failed = false;
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_timer_pairs;
+thread_local cudaEvent_t g_timer_open = nullptr;
+
+void release_timer_pairs() {
+  for (auto& pr : g_timer_pairs) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  g_timer_pairs.clear();
+}
+
 std::mutex g_ws_mu;
 void* g_ws = nullptr;
 size_t g_ws_bytes = 0;
@@ -385,6 +401,33 @@ int g_ws_device = -1;
 }  // namespace
 
 namespace ftk {
+
+void kernel_timer_start(cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_timer_mu);
+  if (!g_timer_on) return;
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess || cudaEventRecord(e, st) != cudaSuccess) {
+    if (e) cudaEventDestroy(e);
+    g_timer_failed = true;
+    return;
+  }
+  g_timer_open = e;
+}
+
+void kernel_timer_stop(cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_timer_mu);
+  if (!g_timer_on || g_timer_open == nullptr) return;
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess || cudaEventRecord(e, st) != cudaSuccess) {
+    if (e) cudaEventDestroy(e);
+    cudaEventDestroy(g_timer_open);
+    g_timer_open = nullptr;
+    g_timer_failed = true;
+    return;
+  }
+  g_timer_pairs.emplace_back(g_timer_open, e);
+  g_timer_open = nullptr;
+}
 
 // The protected BF16 GEMM of ftblas_gemm_ex with the encode workspace taken from `ws`
 // (no allocation of any kind).
@@ -568,5 +611,34 @@ int ftblas_last_cuda_error(void) { return g_last_cuda_error; }
 int ftblas_last_launch_used_tma(void) { return g_last_used_tma; }
 
 const char* ftblas_version(void) { return "0.1.0"; }
+
+int ftblas_kernel_timing_begin(void) {
+  std::lock_guard<std::mutex> lk(g_timer_mu);
+  release_timer_pairs();
+  g_timer_failed = false;
+  g_timer_on = true;
+  return 0;
+}
+
+int ftblas_kernel_timing_end(double* total_ms, int64_t* launches) {
+  std::lock_guard<std::mutex> lk(g_timer_mu);
+  g_timer_on = false;
+  double t = 0.0;
+  int64_t n = 0;
+  bool failed = g_timer_failed;
+  for (auto& pr : g_timer_pairs) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(pr.second) == cudaSuccess && cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
+      t += ms;
+      ++n;
+    } else {
+      failed = true;
+    }
+  }
+  release_timer_pairs();
+  if (total_ms) *total_ms = t;
+  if (launches) *launches = n;
+  return failed ? FTBLAS_STATUS_CUDA_ERROR : 0;
+}
 
 }  // extern "C"
