@@ -133,6 +133,51 @@ def workload_config(n, engine):
             "l2": "inputs 512 MiB per operand > 129 MB L2; no flush between steps"}
 
 
+# ------------------------------------------------------------------ multi-rank host logic
+# Output problems are independent verification intervals, so N ranks run N independent
+# problems (weak scaling) with no data-path exchange; the process group carries only the
+# barrier, the maximum of the timed region and the sum of the report counters.
+
+def rank_seed(rank):
+    """Input seed of rank `rank`: every rank gets a distinct problem of the same shape."""
+    return SEED + rank
+
+
+def max_over_ranks(x, dist):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(counts, dist):
+    """Element-wise sum over ranks of a dict of integer report counters."""
+    if dist is None:
+        return dict(counts)
+    import torch
+    keys = sorted(counts)
+    t = torch.tensor([int(counts[k]) for k in keys], dtype=torch.int64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return {k: int(v) for k, v in zip(keys, t.tolist())}
+
+
+def or_over_ranks(x, dist):
+    """Bitwise OR over ranks (report status bits)."""
+    if dist is None:
+        return int(x)
+    import torch
+    t = torch.tensor([int(x)], dtype=torch.int64)
+    dist.all_reduce(t, op=dist.ReduceOp.BOR)
+    return int(t.item())
+
+
+def job_tflops(world, flops_per_rank_step, steps, max_ms):
+    """Whole-job throughput: the work of all ranks over the slowest rank's time."""
+    return world * flops_per_rank_step * steps / (max_ms / 1e3) / 1e12
+
+
 def gen_inputs(n, seed):
     import synth as S
     A = S.uniform(seed, 0, n * n)   # logical column-major index == storage index (ld = n)
@@ -571,7 +616,7 @@ def run_ours(args, rank, world, dist):
             print(json.dumps({kind: run_tc(args, dev, kind, size, args.steps, args.warmup, None)}), flush=True)
         return 0
     flops_step = 2.0 * n * n * n
-    A, B, Cin = gen_inputs(n, SEED + rank)
+    A, B, Cin = gen_inputs(n, rank_seed(rank))
     dA = torch.from_numpy(A).to(dev)
     dB = torch.from_numpy(B).to(dev)
     dCin = torch.from_numpy(Cin).to(dev)
@@ -585,18 +630,12 @@ def run_ours(args, rank, world, dist):
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     def timed(protect, inject, steps, warmup, clocks=False):
         """Per-launch device times (ms) of `steps` calls after `warmup`, with reports."""
         if protect and inject:
             # one flip per 10 launches, placed so that it falls inside the timed steps
-            seed = (SEED + rank) - ((SEED + rank) % 10) + ((warmup + 1) % 10)
+            seed = rank_seed(rank) - (rank_seed(rank) % 10) + ((warmup + 1) % 10)
             fb.ftblas_set_injection(fb.make_injection(seed=seed, site=fb.SITE_ACCUM, mode=fb.MODE_BITFLIP, bit_lo=40,
                                                       bit_hi=62, every_n_launches=10, errors_per_launch=1))
         else:
@@ -631,7 +670,7 @@ def run_ours(args, rank, world, dist):
         _, kms, kn = fb.ftblas_kernel_timing_end()
         if sampler:
             sampler.__exit__(None, None, None)
-        total_ms = max_over_ranks(t0.elapsed_time(t1))
+        total_ms = max_over_ranks(t0.elapsed_time(t1), dist)
         per = [a.elapsed_time(b) for a, b in ev]
         rsum = {"detected": 0, "corrected": 0, "uncorrectable": 0, "checksum_only": 0, "tiles_checked": 0,
                 "status": 0}
@@ -641,9 +680,13 @@ def run_ours(args, rank, world, dist):
                 for k in ("detected", "corrected", "uncorrectable", "checksum_only", "tiles_checked"):
                     rsum[k] += int(getattr(rr, k))
                 rsum["status"] |= int(rr.status)
+            status = or_over_ranks(rsum.pop("status"), dist)
+            rsum = sum_over_ranks(rsum, dist)
+            rsum["status"] = status
         injected = 0
         if protect and inject:
-            injected = sum(1 for L in range(warmup, warmup + steps) if L % 10 == ((warmup + 1) % 10))
+            # every rank injects in the same launches (its seed is shifted to the same residue)
+            injected = world * sum(1 for L in range(warmup, warmup + steps) if L % 10 == ((warmup + 1) % 10))
         fb.ftblas_set_injection(None)
         kernel_per = [kms / kn] * kn if kn == steps else per
         return total_ms, kernel_per, rsum, injected, (sampler.summary() if sampler else None)
@@ -699,8 +742,8 @@ def run_ours(args, rank, world, dist):
         for _ in range(args.steps):
             hcall()
         barrier()
-        e2e_s = max_over_ranks(time.perf_counter() - t0)
-        e2e = {"value": world * flops_step * args.steps / e2e_s / 1e12, "unit": UNIT,
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+        e2e = {"value": job_tflops(world, flops_step, args.steps, 1e3 * e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": 3 * n * n * 8, "d2h_bytes_per_step": n * n * 8 + fb.REPORT_BYTES}
 
     cpu = None
@@ -725,7 +768,7 @@ def run_ours(args, rank, world, dist):
     pk = peaks()
     h = results[args.engine]
     ft_ms = h["ft_ms"]
-    value = world * flops_step * args.steps / (ft_ms / 1e3) / 1e12
+    value = job_tflops(world, flops_step, args.steps, ft_ms)
     kernel_ms = statistics.mean(h["ft_per"])
     achieved = flops_step / (kernel_ms / 1e3) / 1e12
     bound = "alu" if args.engine == "dfma" else "tensor"

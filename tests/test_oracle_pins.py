@@ -10,6 +10,7 @@ faulty value recomputed here in plain Python floats, and exact checksum differen
 integer data.
 """
 import math
+import os
 import struct
 
 import numpy as np
@@ -458,3 +459,28 @@ def test_acc32_clean_soak_bf16_like_values():
         B = S.bf16_bits_to_f64(S.to_bf16_bits(S.normal_matrix(seed, 1, K, N)))
         _, rep = ft32(A, B, 1.0, 0.0, None, tile=(16, 32))
         assert rep.detected == 0
+
+
+# ------------------------------------------------------------------------------------
+# The generator behind the seeded draw and the inputs, pinned to its published outputs
+# ------------------------------------------------------------------------------------
+
+def _golden_splitmix():
+    path = os.path.join(os.path.dirname(__file__), "golden", "splitmix64_state0.txt")
+    vals = [int(line, 16) for line in open(path) if line.strip() and not line.startswith("#")]
+    assert len(vals) == 3
+    return vals
+
+
+def test_splitmix64_matches_published_outputs():
+    g = _golden_splitmix()
+    # synth: counter form, element idx of (seed 0, matrix 0) is output idx + 1 of state 0
+    assert [int(x) for x in S.splitmix64(0, 0, np.arange(3, dtype=np.uint64))] == g
+    # oracle draw, seed 0, launch 0 (state 0): the first point's tile, row and column come
+    # from the first three outputs (tile t = out0 mod ntiles, numbered t = tile_row +
+    # tile_col * n_tile_rows; offsets out1 mod rows, out2 mod columns of that tile)
+    M = N = 1000
+    tm = tn = 100
+    (pt,) = O.draw_injections(0, 0, 1, 1, O.SITE_ACCUM, O.MODE_BITFLIP, 40, 62, 0, 0, M, N, tm, tn)
+    t = g[0] % 100
+    assert (pt["i"], pt["j"]) == ((t % 10) * tm + g[1] % tm, (t // 10) * tn + g[2] % tn)
