@@ -62,6 +62,11 @@ def parse_args():
     ap.add_argument("--soak", type=float, default=0.0, metavar="SECONDS",
                     help="run only the soak (config 5a): back-to-back FT-DGEMM with Poisson-drawn injections")
     ap.add_argument("--soak-rate", type=float, default=5.0, help="injections per second in the soak")
+    ap.add_argument("--sweep", action="store_true",
+                    help="run only the FP64 size sweep (config 2) and print its own JSON line")
+    ap.add_argument("--unfused-only", action="store_true",
+                    help="measure only the unfused comparator (ABFT passes around cuBLAS DGEMM)")
+    ap.add_argument("--no-unfused", action="store_true", help="skip the unfused comparator")
     ap.add_argument("--linear-only", action="store_true", help="measure only the protected linear layer (config 4)")
     ap.add_argument("--no-linear", action="store_true", help="skip the protected linear layer (config 4)")
     ap.add_argument("--fp8-only", action="store_true",
@@ -400,6 +405,157 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
     }
 
 
+SWEEP_SHAPES = ((1024, 1024, 1024), (2048, 2048, 2048), (4096, 4096, 4096), (8192, 8192, 8192),
+                (16384, 16384, 16384), (8192, 8192, 256), (32768, 1024, 1024))
+
+
+def run_sweep(dev, steps, warmup, shapes=SWEEP_SHAPES):
+    """Config 2: the FP64 FT-DGEMM (DFMA engine, column-major, alpha 1.5, beta 0.5, U[-1,1])
+    against the unprotected kernel over square sizes 1024..16384 and the skinny and tall
+    shapes; the protected runs carry one accumulator flip (bits 40-62) per 10 launches,
+    placed so that a timed launch is hit. TFLOP/s from the product kernels' CUDA-event
+    time (ftblas_kernel_timing)."""
+    import torch
+
+    import paper_2104_00897_gb300 as fb
+    import synth as S
+
+    fb.ftblas_set_fp64_engine(fb.ENGINE_DFMA)
+    peak = peaks()["alu"]
+    st = torch.cuda.current_stream(dev).cuda_stream
+    rows = []
+    for (M, N, K) in shapes:
+        seed = SEED + 7
+        dA = torch.from_numpy(S.uniform(seed, 0, M * K)).to(dev)
+        dB = torch.from_numpy(S.uniform(seed, 1, K * N)).to(dev)
+        dC = torch.from_numpy(S.uniform(seed, 2, M * N)).to(dev)
+        flops = 2.0 * M * N * K
+
+        def measure(protect, inject):
+            if protect and inject:
+                fb.ftblas_set_injection(fb.make_injection(seed=seed - seed % 10 + (warmup + 1) % 10, site=fb.SITE_ACCUM,
+                                                          mode=fb.MODE_BITFLIP, bit_lo=40, bit_hi=62,
+                                                          every_n_launches=10, errors_per_launch=1))
+            else:
+                fb.ftblas_set_injection(None)
+            reps = [fb.new_report(dev) for _ in range(steps)]
+
+            def call(rep):
+                a = (fb.COL_MAJOR, fb.NO_TRANS, fb.NO_TRANS, M, N, K, 1.5, dA.data_ptr(), M, dB.data_ptr(), K, 0.5,
+                     dC.data_ptr(), M, st)
+                if protect:
+                    fb.check(fb.ftblas_dgemm(*a, rep.data_ptr() if rep is not None else None))
+                else:
+                    fb.check(fb.ftblas_dgemm_noabft(*a))
+
+            for _ in range(warmup):
+                call(None)
+            torch.cuda.synchronize(dev)
+            fb.ftblas_kernel_timing_begin()
+            for s_ in range(steps):
+                call(reps[s_])
+            torch.cuda.synchronize(dev)
+            _, kms, kn = fb.ftblas_kernel_timing_end()
+            fb.ftblas_set_injection(None)
+            det = cor = 0
+            if protect:
+                for r in reps:
+                    rr = fb.report_from_device(r)
+                    det += int(rr.detected)
+                    cor += int(rr.corrected)
+            return kms / kn, det, cor
+
+        ms_inj, det, cor = measure(True, True)
+        ms_ft, det_clean, _ = measure(True, False)
+        ms_na, _, _ = measure(False, False)
+        rows.append({"M": M, "N": N, "K": K, "ft_tflops_injected": flops / ms_inj / 1e9,
+                     "ft_tflops_clean": flops / ms_ft / 1e9, "noabft_tflops": flops / ms_na / 1e9,
+                     "pct_of_fp64_peak_ft": 100.0 * flops / ms_ft / 1e9 / peak,
+                     "abft_overhead_pct_clean": 100.0 * (ms_ft / ms_na - 1.0),
+                     "abft_overhead_pct_injected": 100.0 * (ms_inj / ms_na - 1.0),
+                     "detected": det, "corrected": cor, "false_alarms_clean": det_clean})
+        del dA, dB, dC
+        torch.cuda.empty_cache()
+    return {"workload": "ft_dgemm FP64 (DFMA), column-major, alpha 1.5, beta 0.5, U[-1,1]; one accumulator flip "
+                        "(bits 40-62) per 10 launches in the injected runs",
+            "peak_tflops": peak, "steps": steps, "warmup": warmup, "rows": rows}
+
+
+def run_unfused(dev, n, steps, warmup):
+    """NEXT-1 comparator: the same FP64 workload as the headline (8192^3, column-major, alpha
+    1.5, beta 0.5, U[-1,1]) through ftblas_dgemm_unfused: ABFT as separate bandwidth-bound
+    passes around cuBLAS's DGEMM, against cuBLAS alone. The product kernel's time comes
+    from ftblas_kernel_timing (events around the library GEMM); the passes' time is the
+    rest of the call."""
+    import torch
+
+    import paper_2104_00897_gb300 as fb
+
+    A, B, Cin = gen_inputs(n, rank_seed(0))
+    dA = torch.from_numpy(A).to(dev)
+    dB = torch.from_numpy(B).to(dev)
+    dC = torch.from_numpy(Cin).to(dev)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    flops = 2.0 * n ** 3
+
+    def timed(inject):
+        if inject:
+            fb.ftblas_set_injection(fb.make_injection(seed=SEED, site=fb.SITE_OUTPUT, mode=fb.MODE_BITFLIP, bit_lo=40,
+                                                      bit_hi=62, every_n_launches=1, errors_per_launch=1))
+        else:
+            fb.ftblas_set_injection(None)
+        reps = [fb.new_report(dev) for _ in range(steps)]
+
+        def call(rep):
+            fb.check(fb.ftblas_dgemm_unfused(fb.COL_MAJOR, fb.NO_TRANS, fb.NO_TRANS, n, n, n, 1.5, dA.data_ptr(), n,
+                                             dB.data_ptr(), n, 0.5, dC.data_ptr(), n, st,
+                                             rep.data_ptr() if rep is not None else None), "ftblas_dgemm_unfused")
+
+        for _ in range(warmup):
+            call(None)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fb.ftblas_kernel_timing_begin()
+        e0.record()
+        for s_ in range(steps):
+            call(reps[s_])
+        e1.record()
+        torch.cuda.synchronize(dev)
+        _, kms, kn = fb.ftblas_kernel_timing_end()
+        fb.ftblas_set_injection(None)
+        det = sum(int(fb.report_from_device(r).detected) for r in reps)
+        cor = sum(int(fb.report_from_device(r).corrected) for r in reps)
+        return e0.elapsed_time(e1) / steps, (kms / kn if kn else None), det, cor
+
+    ms_clean, gemm_ms, det0, _ = timed(False)
+    ms_inj, _, det, cor = timed(True)
+    # cuBLAS alone (through torch): C = A B on the column-major operands (as row-major
+    # transposes: C^T = B^T A^T), same sizes
+    a_t = dA.view(n, n)
+    b_t = dB.view(n, n)
+    for _ in range(warmup):
+        torch.mm(b_t, a_t)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        torch.mm(b_t, a_t)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms_cublas = e0.elapsed_time(e1) / steps
+    pass_ms = ms_clean - gemm_ms if gemm_ms else None
+    pass_bytes = (3 * n * n + 2 * n * n) * 8  # A, B, C_in and C read once each (+ prediction operands)
+    return {
+        "workload": f"ft_dgemm_unfused_{n}x{n}x{n}: checksum passes around cuBLAS DGEMM, alpha 1.5, beta 0.5",
+        "unfused_ft_tflops": flops / ms_clean / 1e9, "unfused_ft_tflops_injected": flops / ms_inj / 1e9,
+        "cublas_dgemm_tflops": flops / ms_cublas / 1e9,
+        "unfused_overhead_pct_vs_cublas": 100.0 * (ms_clean / ms_cublas - 1.0),
+        "checksum_passes_ms": pass_ms, "library_gemm_ms_inside_call": gemm_ms,
+        "checksum_passes_gbs": (pass_bytes / (pass_ms / 1e3) / 1e9) if pass_ms and pass_ms > 0 else None,
+        "false_alarms_clean": det0, "injected": steps, "detected": det, "corrected": cor,
+    }
+
+
 def run_linear(dev, steps, warmup, T=8192, n_in=4096, n_out=4096):
     """Config 4: Y = X W^T through FTLinearFn with X (T x n_in) BF16 N(0,1), W (n_out x n_in)
     BF16 N(0, 0.02), dY N(0,1): forward (T, n_out, n_in), dX = dY W (T, n_in, n_out) and
@@ -601,6 +757,14 @@ def run_ours(args, rank, world, dist):
     dev = torch.device("cuda", local)
     fb.load()
     n = args.size
+    if args.sweep:
+        if rank == 0:
+            print(json.dumps({"sweep_fp64": run_sweep(dev, args.steps, args.warmup)}), flush=True)
+        return 0
+    if args.unfused_only:
+        if rank == 0:
+            print(json.dumps({"unfused_fp64": run_unfused(dev, n, args.steps, args.warmup)}), flush=True)
+        return 0
     if args.linear_only:
         if rank == 0:
             print(json.dumps({"linear_bf16": run_linear(dev, args.steps, args.warmup)}), flush=True)
@@ -762,6 +926,9 @@ def run_ours(args, rank, world, dist):
     linear = None
     if not args.no_linear and rank == 0:
         linear = run_linear(dev, args.steps, args.warmup)
+    unfused = None
+    if not args.no_unfused and rank == 0:
+        unfused = run_unfused(dev, n, args.steps, args.warmup)
 
     if rank != 0:
         return 0
@@ -810,6 +977,7 @@ def run_ours(args, rank, world, dist):
         "bf16": bf16,
         "fp8_e4m3": fp8,
         "linear_bf16": linear,
+        "unfused_fp64": unfused,
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clocks,

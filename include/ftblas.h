@@ -156,6 +156,25 @@ int ftblas_dgemm_noabft(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_tr
                         const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
                         void* stream);
 
+/* The unfused comparator (no counterpart in the fused design; it reproduces the
+ * arrangement Section V improves on: ABFT as separate passes around a BLAS library call).
+ * Same arguments, checks, report and injection plan as ftblas_dgemm, and the same
+ * 128 x 128 verification tiles. The product is cuBLAS's DGEMM (loaded at run time); the
+ * checksums are formed by separate bandwidth-bound passes that read op(A), op(B), C_in
+ * (beta != 0) and the output C once each, plus two thin cuBLAS products for the predicted
+ * checksums A (B e) and (e^T A) B. The threshold is ftblas_dgemm's with the magnitude
+ * products bounded by (sum_k |A(i,k)|)(max_k sum_{j in tile} |B(k,j)|) and its transpose.
+ * A located error is corrected from the row checksum as C^r(i) - sum_{j' != j} C(i,j')
+ * (within the row threshold of the fault-free value, not bit-exact: the library's
+ * summation order is unknown). Accumulator-site injection points act on the output
+ * element (the library's accumulator is out of reach). Workspace comes from the
+ * stream-ordered allocator. Returns FTBLAS_STATUS_NOT_SUPPORTED when cuBLAS cannot be
+ * loaded or a dimension exceeds its 32-bit interface. */
+int ftblas_dgemm_unfused(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,
+                         int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+                         const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                         void* stream, ft_report_t* report);
+
 /* ftblas_dgemm on HOST buffers: copies A, B (and C when beta != 0) to library-owned
  * device workspace on `stream`, runs the protected GEMM, copies C and the report back and
  * synchronises the stream before returning. report (host memory) may be NULL. Pinned host

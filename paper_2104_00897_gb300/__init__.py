@@ -86,6 +86,7 @@ SIGNATURES = {
     "ftblas_dgemm": (C.c_int, _GEMM_ARGS + [C.c_void_p, C.c_void_p]),
     "ftblas_dgemm_noabft": (C.c_int, _GEMM_ARGS + [C.c_void_p]),
     "ftblas_dgemm_host": (C.c_int, _GEMM_ARGS + [C.c_void_p, C.c_void_p]),
+    "ftblas_dgemm_unfused": (C.c_int, _GEMM_ARGS + [C.c_void_p, C.c_void_p]),
     "ftblas_verification_tile": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64,
                                            C.c_void_p, C.c_void_p, C.c_void_p]),
     "ftblas_set_fp64_engine": (C.c_int, [C.c_int]),
@@ -131,6 +132,11 @@ def ftblas_dgemm(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C
 
 def ftblas_dgemm_noabft(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream):
     return _call("ftblas_dgemm_noabft", layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream)
+
+
+def ftblas_dgemm_unfused(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream, report):
+    return _call("ftblas_dgemm_unfused", layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream,
+                 report)
 
 
 def ftblas_dgemm_host(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream, report):

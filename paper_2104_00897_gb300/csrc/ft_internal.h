@@ -59,6 +59,21 @@ enum Fp64Engine : int { kEngineDFMA = 0, kEngineDMMA = 1 };
 cudaError_t launch_dgemm(const DgemmParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB,
                          bool ft, int engine, cudaStream_t stream);
 
+// Unfused comparator (ftblas_dgemm_unfused): checksum passes around a library DGEMM.
+struct UnfusedParams {
+  int32_t M, N, K;               // kernel frame
+  int32_t a_kmajor, b_kmajor;    // storage: op(A) k-contiguous (stored K x M)?  op(B) k-contiguous (K x N)?
+  int32_t swap_report;
+  double alpha, beta;
+  const double* A; int64_t lda;
+  const double* B; int64_t ldb;
+  double* C; int64_t ldc;
+  ft_report_t* report;           // may be null
+  InjectList inj;                // output and checksum sites (accumulator points act on the output)
+};
+// Returns 0 or an FTBLAS_STATUS_* code; on a CUDA failure *cuda_err holds the error.
+int unfused_dgemm(const UnfusedParams& p, cudaStream_t stream, cudaError_t* cuda_err);
+
 // Product-kernel timing (ftblas_kernel_timing_begin / _end): event records on `stream`
 // immediately before and after a product kernel launch; no-ops unless timing is on.
 void kernel_timer_start(cudaStream_t stream);

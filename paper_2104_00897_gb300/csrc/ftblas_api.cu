@@ -249,6 +249,48 @@ int dgemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, doub
   return record_cuda(launch_dgemm(p, &tmA, &tmB, ft, g_fp64_engine.load(), st));
 }
 
+// ------------------------------------------------------------------ unfused comparator
+int dgemm_unfused_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                       int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* stream,
+                       ft_report_t* report) {
+  const bool need_ab = (K > 0 && alpha != 0.0 && M > 0 && N > 0);
+  int v = validate(layout, ta, tb, M, N, K, A, lda, B, ldb, C, ldc, need_ab);
+  if (v != 0) return v;
+  if (M > kMaxDim || N > kMaxDim || K > kMaxDim) return FTBLAS_STATUS_NOT_SUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (report != nullptr) {
+    if (int e = record_cuda(cudaMemsetAsync(report, 0, sizeof(ft_report_t), st))) return e;
+  }
+  if (M == 0 || N == 0) return 0;
+  const Frame f = map_frame(layout, ta, tb, M, N, A, lda, B, ldb);
+  CallerPoint pts[kMaxInject];
+  const int64_t tile_rows = f.swap ? kDBN : kDBM, tile_cols = f.swap ? kDBM : kDBN;
+  const int npts = plan_injections(M, N, tile_rows, tile_cols, pts);
+  if (K == 0 || alpha == 0.0) return record_cuda(launch_scale(C, ldc, (int32_t)f.M, (int32_t)f.N, beta, st));
+  UnfusedParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.M = (int32_t)f.M; p.N = (int32_t)f.N; p.K = (int32_t)K;
+  p.a_kmajor = f.a_kmajor; p.b_kmajor = f.b_kmajor;
+  p.swap_report = f.swap;
+  p.alpha = alpha; p.beta = beta;
+  p.A = static_cast<const double*>(f.A); p.lda = f.lda;
+  p.B = static_cast<const double*>(f.B); p.ldb = f.ldb;
+  p.C = C; p.ldc = ldc;
+  p.report = report;
+  for (int q = 0; q < npts; ++q) {
+    InjectPoint& ip = p.inj.p[p.inj.n++];
+    const CallerPoint& c = pts[q];
+    ip.i = (int32_t)(f.swap ? c.j : c.i);
+    ip.j = (int32_t)(f.swap ? c.i : c.j);
+    ip.site = c.site == FT_SITE_CHECKSUM ? kSiteChecksumRow : c.site;
+    ip.mode = c.mode; ip.bit = c.bit; ip.rel_log2 = c.rel_log2; ip.sign = c.sign; ip.pad = 0;
+  }
+  cudaError_t ce = cudaSuccess;
+  const int rc = unfused_dgemm(p, st, &ce);
+  if (ce != cudaSuccess) return record_cuda(ce);
+  return rc;
+}
+
 // ------------------------------------------------------------------ mixed precision
 // The tensor-core path (A, B BF16 or FP8 E4M3; C and compute FP32) behind ftblas_gemm_ex,
 // ftblas_gemm_ex_noabft and ftblas_gemm_ex_noalloc. Workspace: from the stream-ordered
@@ -611,6 +653,12 @@ int ftblas_last_cuda_error(void) { return g_last_cuda_error; }
 int ftblas_last_launch_used_tma(void) { return g_last_used_tma; }
 
 const char* ftblas_version(void) { return "0.1.0"; }
+
+int ftblas_dgemm_unfused(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb, int64_t M, int64_t N,
+                         int64_t K, double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                         double beta, double* C, int64_t ldc, void* stream, ft_report_t* report) {
+  return dgemm_unfused_impl(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, stream, report);
+}
 
 int ftblas_kernel_timing_begin(void) {
   std::lock_guard<std::mutex> lk(g_timer_mu);
