@@ -45,6 +45,7 @@ class Problem(C.Structure):
         ("bk", C.c_int64),
         ("precision", C.c_int32), ("pad2_", C.c_int32),
         ("u_acc", C.c_double),
+        ("kc", C.c_int64),
     ]
 
 
@@ -52,7 +53,7 @@ class Injection(C.Structure):
     _fields_ = [
         ("i", C.c_int64), ("j", C.c_int64),
         ("site", C.c_int32), ("mode", C.c_int32), ("bit", C.c_int32),
-        ("rel_log2", C.c_int32), ("sign", C.c_int32), ("pad_", C.c_int32),
+        ("rel_log2", C.c_int32), ("sign", C.c_int32), ("kt", C.c_int32),
     ]
 
 
@@ -125,7 +126,7 @@ def _f64(x):
 
 
 def make_problem(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc,
-                 tile_m=128, tile_n=128, bk=16, keep=None, precision=PREC_FP64, u_acc=U_ACC32):
+                 tile_m=128, tile_n=128, bk=16, keep=None, precision=PREC_FP64, u_acc=U_ACC32, kc=0):
     """Fill a Problem; ``keep`` (a list) receives the arrays that must outlive the call."""
     A = _f64(A); B = _f64(B)
     Cin = _f64(Cin) if Cin is not None else np.zeros(1)
@@ -134,7 +135,7 @@ def make_problem(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C
     p = Problem(layout=layout, transa=transa, transb=transb, pad_=0, M=M, N=N, K=K, alpha=alpha,
                 A=A.ctypes.data, lda=lda, B=B.ctypes.data, ldb=ldb, beta=beta,
                 Cin=Cin.ctypes.data, ldc=ldc, tile_m=tile_m, tile_n=tile_n, bk=bk,
-                precision=precision, pad2_=0, u_acc=u_acc)
+                precision=precision, pad2_=0, u_acc=u_acc, kc=kc)
     return p
 
 
@@ -162,20 +163,23 @@ def gemm_rows(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin,
 
 
 def injections_array(points):
-    """``points``: iterable of dicts/tuples (i, j, site, mode, bit, rel_log2, sign)."""
+    """``points``: iterable of dicts/tuples (i, j, site, mode, bit, rel_log2, sign[, kt]);
+    kt: the accumulator flip lands after kt * bk products (0: after bk * floor(nk / 2))."""
     pts = list(points)
     arr = (Injection * max(1, len(pts)))()
     for q, pt in enumerate(pts):
         if isinstance(pt, dict):
             pt = (pt["i"], pt["j"], pt.get("site", SITE_ACCUM), pt.get("mode", MODE_BITFLIP),
-                  pt.get("bit", 0), pt.get("rel_log2", 0), pt.get("sign", 1))
-        i, j, site, mode, bit, rel, sign = pt
-        arr[q] = Injection(i=i, j=j, site=site, mode=mode, bit=bit, rel_log2=rel, sign=sign, pad_=0)
+                  pt.get("bit", 0), pt.get("rel_log2", 0), pt.get("sign", 1), pt.get("kt", 0))
+        if len(pt) == 7:
+            pt = tuple(pt) + (0,)
+        i, j, site, mode, bit, rel, sign, kt = pt
+        arr[q] = Injection(i=i, j=j, site=site, mode=mode, bit=bit, rel_log2=rel, sign=sign, kt=kt)
     return arr, len(pts)
 
 
 def ft_gemm(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc,
-            tile_m, tile_n, bk, injections=(), tiles=None, out=None, precision=PREC_FP64, u_acc=U_ACC32):
+            tile_m, tile_n, bk, injections=(), tiles=None, out=None, precision=PREC_FP64, u_acc=U_ACC32, kc=0):
     """ABFT-protected GEMM. Returns ``(Cout_buffer, Report)``.
 
     ``tiles``: None for all tiles, else tile numbers t = tile_row + tile_col * n_tile_rows
@@ -183,7 +187,7 @@ def ft_gemm(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, l
     """
     keep = []
     p = make_problem(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc,
-                     tile_m, tile_n, bk, keep=keep, precision=precision, u_acc=u_acc)
+                     tile_m, tile_n, bk, keep=keep, precision=precision, u_acc=u_acc, kc=kc)
     if out is None:
         n_store = max(1, ldc * (N if layout == COL_MAJOR else M))
         out = np.array(keep[2], copy=True) if Cin is not None and beta != 0.0 else np.zeros(n_store)

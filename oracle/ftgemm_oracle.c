@@ -93,6 +93,8 @@ typedef struct {
                                        accumulation, binary32 C) */
   int32_t pad2_;
   double u_acc;                     /* OR_PREC_ACC32: unit roundoff of the accumulation */
+  int64_t kc;                       /* OR_PREC_FP64: online verification every kc products (a
+                                       multiple of bk; 0 or >= K: only the finished tile) */
 } oracle_problem_t;
 
 typedef struct {
@@ -102,7 +104,7 @@ typedef struct {
   int32_t bit;         /* bit-flip: bit of the IEEE-754 binary64 pattern, 0 = lsb */
   int32_t rel_log2;    /* add-rel: e = sign * 2^rel_log2 * |c| */
   int32_t sign;        /* +1 or -1 */
-  int32_t pad_;
+  int32_t kt;          /* accumulator site: flip after kt * bk products (0: after bk * floor(nk / 2)) */
 } oracle_injection_t;
 
 typedef struct {
@@ -297,7 +299,7 @@ int64_t oracle_draw_injections(uint64_t seed, uint64_t launch, int32_t every_n, 
     out[n].bit = bit_lo + (int32_t)(rb % (uint64_t)(bit_hi - bit_lo + 1));
     out[n].rel_log2 = log2_lo + (int32_t)(rp % (uint64_t)(log2_hi - log2_lo + 1));
     out[n].sign = (rs & 1) ? -1 : 1;
-    out[n].pad_ = 0;
+    out[n].kt = 0;
     ++n;
   }
   return n;
@@ -314,14 +316,112 @@ static double gamma_n(double n) {
 
 static int isfinite_d(double x) { return isfinite(x) != 0; }
 
+#define OR_TILE_RECORDS 32
 typedef struct {
   uint64_t detected, corrected, uncorrectable, checksum_only, input_nonfinite;
   int32_t n_rec;
-  oracle_record_t rec[4];
+  oracle_record_t rec[OR_TILE_RECORDS];
 } tile_result_t;
 
 static void add_record(tile_result_t* res, const oracle_record_t* r) {
-  if (res->n_rec < 4) res->rec[res->n_rec++] = *r;
+  if (res->n_rec < OR_TILE_RECORDS) res->rec[res->n_rec++] = *r;
+}
+
+/* Products over the tile with online verification every kc products (Section V.A: after
+ * every rank-kc update of the outer-product formulation the checksum relation holds for
+ * the partial product, so it can be checked, and one error corrected, at each step).
+ * acc[ii + jj*nI] receives the tile's raw accumulators (alpha, beta not applied). At the
+ * end of each step but the last, the row and column sums of the accumulators are
+ * compared with the predicted partial checksums sum_{k < kh} A(i,k) (Be)(k) and
+ * sum_{k < kh} (e^T A)(k) B(k,j) against
+ *   tau = 2 [gamma_{kh + n + 3} P + gamma_n sum |acc|],  P = sum_{k < kh} |A(i,k)| (|B| e)(k)
+ * (and symmetrically for columns), the threshold reading of the finished tile with K
+ * replaced by kh and no alpha or beta. Exactly one flagged row and one flagged column
+ * locate the error, whose accumulator is recomputed over k < kh (the fault-free partial
+ * product) and recorded as corrected; other patterns are left for the check of the
+ * finished tile. Accumulator flips land after kt * bk products as in dot_row_col. */
+static void midk_products(const oracle_problem_t* p, int64_t tr, int64_t tc, int64_t i0, int64_t j0, int64_t nI,
+                          int64_t nJ, const double* Ac, const double* Br, const double* Ac_abs, const double* Br_abs,
+                          int64_t n_inj, const oracle_injection_t* inj, double* acc, tile_result_t* res) {
+  const int64_t K = p->K, nk = (K + p->bk - 1) / p->bk;
+  double* pr = (double*)calloc((size_t)nI, sizeof(double));
+  double* Pr = (double*)calloc((size_t)nI, sizeof(double));
+  double* pc = (double*)calloc((size_t)nJ, sizeof(double));
+  double* Pc = (double*)calloc((size_t)nJ, sizeof(double));
+  int64_t* kflip = (int64_t*)malloc((size_t)(nI * nJ) * sizeof(int64_t));
+  int* bflip = (int*)malloc((size_t)(nI * nJ) * sizeof(int));
+  for (int64_t e = 0; e < nI * nJ; ++e) { acc[e] = 0.0; kflip[e] = -1; bflip[e] = -1; }
+  for (int64_t q = 0; q < n_inj; ++q) {
+    if (inj[q].site != OR_SITE_ACCUM || inj[q].mode != OR_MODE_BITFLIP) continue;
+    int64_t ii = inj[q].i - i0, jj = inj[q].j - j0;
+    if (ii < 0 || ii >= nI || jj < 0 || jj >= nJ || bflip[ii + jj * nI] >= 0) continue;
+    bflip[ii + jj * nI] = inj[q].bit;
+    kflip[ii + jj * nI] = p->bk * (inj[q].kt > 0 ? inj[q].kt : nk / 2);
+  }
+  for (int64_t kl = 0; kl < K; kl += p->kc) {
+    const int64_t kh = (kl + p->kc < K) ? kl + p->kc : K;
+    for (int64_t jj = 0; jj < nJ; ++jj)
+      for (int64_t ii = 0; ii < nI; ++ii) {
+        double a_ = acc[ii + jj * nI];
+        for (int64_t k = kl; k < kh; ++k) {
+          if (bflip[ii + jj * nI] >= 0 && k == kflip[ii + jj * nI]) a_ = flip_bit(a_, bflip[ii + jj * nI]);
+          double prod = a_elem(p, i0 + ii, k) * b_elem(p, k, j0 + jj);
+          a_ = a_ + prod;
+        }
+        acc[ii + jj * nI] = a_;
+      }
+    for (int64_t ii = 0; ii < nI; ++ii)
+      for (int64_t k = kl; k < kh; ++k) {
+        double a = a_elem(p, i0 + ii, k);
+        pr[ii] = pr[ii] + a * Br[k];
+        Pr[ii] = Pr[ii] + fabs(a) * Br_abs[k];
+      }
+    for (int64_t jj = 0; jj < nJ; ++jj)
+      for (int64_t k = kl; k < kh; ++k) {
+        double b = b_elem(p, k, j0 + jj);
+        pc[jj] = pc[jj] + Ac[k] * b;
+        Pc[jj] = Pc[jj] + Ac_abs[k] * fabs(b);
+      }
+    if (kh >= K) break;
+    /* online check of the partial product */
+    const double g_row = gamma_n((double)(kh + nJ + 3)), g_rsum = gamma_n((double)nJ);
+    const double g_col = gamma_n((double)(kh + nI + 3)), g_csum = gamma_n((double)nI);
+    int64_t nr = 0, nc = 0, fr = -1, fc = -1;
+    double fr_d = 0.0, fr_t = 0.0, fc_d = 0.0, fc_t = 0.0;
+    for (int64_t ii = 0; ii < nI; ++ii) {
+      double ref = 0.0, R = 0.0;
+      for (int64_t jj = 0; jj < nJ; ++jj) { ref = ref + acc[ii + jj * nI]; R = R + fabs(acc[ii + jj * nI]); }
+      double d = ref - pr[ii], tau = 2.0 * (g_row * Pr[ii] + g_rsum * R);
+      if (!(fabs(d) <= tau) || isinf(d)) { if (fr < 0) { fr = ii; fr_d = d; fr_t = tau; } ++nr; }
+    }
+    for (int64_t jj = 0; jj < nJ; ++jj) {
+      double ref = 0.0, R = 0.0;
+      for (int64_t ii = 0; ii < nI; ++ii) { ref = ref + acc[ii + jj * nI]; R = R + fabs(acc[ii + jj * nI]); }
+      double d = ref - pc[jj], tau = 2.0 * (g_col * Pc[jj] + g_csum * R);
+      if (!(fabs(d) <= tau) || isinf(d)) { if (fc < 0) { fc = jj; fc_d = d; fc_t = tau; } ++nc; }
+    }
+    if (nr == 1 && nc == 1) {
+      double fixed = 0.0;
+      for (int64_t k = 0; k < kh; ++k) {
+        double prod = a_elem(p, i0 + fr, k) * b_elem(p, k, j0 + fc);
+        fixed = fixed + prod;
+      }
+      oracle_record_t r;
+      memset(&r, 0, sizeof(r));
+      r.tile_row = tr; r.tile_col = tc; r.i = i0 + fr; r.j = j0 + fc;
+      r.delta_row = fr_d; r.delta_col = fc_d; r.tau_row = fr_t; r.tau_col = fc_t;
+      r.value_before = acc[fr + fc * nI];
+      r.value_after = fixed;
+      r.value_subtracted = acc[fr + fc * nI] - fr_d;
+      r.kind = OR_KIND_CORRECTED;
+      r.rows_flagged = 1; r.cols_flagged = 1;
+      add_record(res, &r);
+      res->detected += 1;
+      res->corrected += 1;
+      acc[fr + fc * nI] = fixed;
+    }
+  }
+  free(pr); free(Pr); free(pc); free(Pc); free(kflip); free(bflip);
 }
 
 /* One verification interval: the tile_m x tile_n tile (tr, tc) over all of K. */
@@ -355,16 +455,27 @@ static void ft_tile(const oracle_problem_t* p, int64_t tr, int64_t tc,
   for (int64_t k = 0; k < K; ++k)
     if (!isfinite_d(Ac[k]) || !isfinite_d(Br[k])) nonfinite_input = 1;
 
-  /* Product over the tile, with the injections that fall inside it. */
+  /* Product over the tile, with the injections that fall inside it; with online
+   * verification (kc) the accumulators come from the checked rank-kc steps. */
   double* T = (double*)malloc((size_t)(nI * nJ) * sizeof(double)); /* T[ii + jj*nI] */
+  const int midk = p->kc > 0 && p->kc < K;
+  if (midk) midk_products(p, tr, tc, i0, j0, nI, nJ, Ac, Br, Ac_abs, Br_abs, n_inj, inj, T, res);
   for (int64_t jj = 0; jj < nJ; ++jj) {
     for (int64_t ii = 0; ii < nI; ++ii) {
       int64_t i = i0 + ii, j = j0 + jj;
-      int acc_bit = -1;
-      for (int64_t q = 0; q < n_inj; ++q)
-        if (inj[q].i == i && inj[q].j == j && inj[q].site == OR_SITE_ACCUM && inj[q].mode == OR_MODE_BITFLIP)
-          acc_bit = inj[q].bit;
-      double acc = dot_row_col(p, i, j, kstar, acc_bit);
+      double acc;
+      if (midk) {
+        acc = T[ii + jj * nI];
+      } else {
+        int acc_bit = -1;
+        int64_t kq = kstar;
+        for (int64_t q = 0; q < n_inj; ++q)
+          if (inj[q].i == i && inj[q].j == j && inj[q].site == OR_SITE_ACCUM && inj[q].mode == OR_MODE_BITFLIP) {
+            acc_bit = inj[q].bit;
+            if (inj[q].kt > 0) kq = p->bk * inj[q].kt;
+          }
+        acc = dot_row_col(p, i, j, kq, acc_bit);
+      }
       double v = scale_out(p, acc, i, j);
       for (int64_t q = 0; q < n_inj; ++q) {
         if (inj[q].i != i || inj[q].j != j || inj[q].site != OR_SITE_OUTPUT) continue;
@@ -455,14 +566,14 @@ static void ft_tile(const oracle_problem_t* p, int64_t tr, int64_t tc,
 
   if (nonfinite_input) {
     /* Non-finite encoded checksums: the relation cannot be checked; C is kept. */
-    res->input_nonfinite = 1;
+    res->input_nonfinite += 1;
     r.kind = OR_KIND_INPUT_NONFINITE;
     add_record(res, &r);
   } else if (nr == 0 && nc == 0) {
     /* clean */
   } else if (nr == 1 && nc == 1) {
     /* Locate at the crossing of the mismatching row and column and correct. */
-    res->detected = 1; res->corrected = 1;
+    res->detected += 1; res->corrected += 1;
     r.kind = OR_KIND_CORRECTED;
     r.value_before = T[fr + fc * nI];
     r.value_subtracted = r.value_before - r.delta_row;
@@ -471,11 +582,11 @@ static void ft_tile(const oracle_problem_t* p, int64_t tr, int64_t tc,
     r.value_after = fixed;
     add_record(res, &r);
   } else if (nr == 0 || nc == 0) {
-    res->detected = 1; res->checksum_only = 1;
+    res->detected += 1; res->checksum_only += 1;
     r.kind = OR_KIND_CHECKSUM_ONLY;
     add_record(res, &r);
   } else {
-    res->detected = 1; res->uncorrectable = 1;
+    res->detected += 1; res->uncorrectable += 1;
     r.kind = OR_KIND_UNCORRECTABLE;
     add_record(res, &r);
   }
@@ -652,7 +763,7 @@ static void ft_tile_acc32(const oracle_problem_t* p, int64_t tr, int64_t tc,
   if (nr == 0) {
     /* clean */
   } else if (located >= 0) {
-    res->detected = 1; res->corrected = 1;
+    res->detected += 1; res->corrected += 1;
     r.kind = OR_KIND_CORRECTED;
     const int64_t fcl = located;
     double before = T[fr + fcl * nI];
@@ -669,11 +780,11 @@ static void ft_tile_acc32(const oracle_problem_t* p, int64_t tr, int64_t tc,
     r.value_after = T[fr + fcl * nI];
     add_record(res, &r);
   } else if (nc == 0 && (!recompute_row || ne == 0)) {
-    res->detected = 1; res->checksum_only = 1;
+    res->detected += 1; res->checksum_only += 1;
     r.kind = OR_KIND_CHECKSUM_ONLY;
     add_record(res, &r);
   } else {
-    res->detected = 1; res->uncorrectable = 1;
+    res->detected += 1; res->uncorrectable += 1;
     r.kind = OR_KIND_UNCORRECTABLE;
     add_record(res, &r);
   }

@@ -21,6 +21,7 @@ MUTATIONS = {
     "dropped_term_in_Be": ("for (int64_t j = j0; j < j0 + nJ; ++j) { double b = b_elem(p, k, j); s = s + b;",
                            "for (int64_t j = j0 + 1; j < j0 + nJ; ++j) { double b = b_elem(p, k, j); s = s + b;"),
     "missing_alpha_in_prediction": ("double Cc = p->alpha * dotp;", "double Cc = dotp;"),
+    "online_recompute_over_all_of_K": ("for (int64_t k = 0; k < kh; ++k) {", "for (int64_t k = 0; k < K; ++k) {"),
 }
 
 

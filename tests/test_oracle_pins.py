@@ -484,3 +484,74 @@ def test_splitmix64_matches_published_outputs():
     (pt,) = O.draw_injections(0, 0, 1, 1, O.SITE_ACCUM, O.MODE_BITFLIP, 40, 62, 0, 0, M, N, tm, tn)
     t = g[0] % 100
     assert (pt["i"], pt["j"]) == ((t % 10) * tm + g[1] % tm, (t // 10) * tn + g[2] % tn)
+
+
+# ------------------------------------------------------------------------------------
+# Online verification every kc products (Section V.A's rank-kc steps)
+# ------------------------------------------------------------------------------------
+
+def _midk(A, B, kc, inj=(), tile=(4, 5), bk=2, alpha=1.0, beta=0.0, C=None):
+    M, K = A.shape
+    N = B.shape[1]
+    a, lda = stored(O.COL_MAJOR, O.NO_TRANS, A)
+    b, ldb = stored(O.COL_MAJOR, O.NO_TRANS, B)
+    c, ldc = c_store(O.COL_MAJOR, np.zeros((M, N)) if C is None else C)
+    out, rep = O.ft_gemm(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, M, N, K, alpha, a, lda, b, ldb, beta, c, ldc,
+                         tile[0], tile[1], bk, injections=inj, kc=kc)
+    return S.load(out, O.COL_MAJOR, M, N, ldc), rep
+
+
+def test_midk_two_faults_in_one_tile_both_corrected_bitwise():
+    """Brute force on 4 x 5 x 12 (one tile, bk = 2, checks after 4 and 8 products): two
+    accumulator flips in the same tile, in different rank-4 steps, are each located and
+    corrected at the check that follows them; C equals the fault-free C bit for bit.
+    Without online checks the same pair is uncorrectable."""
+    A = S.uniform_matrix(81, 0, 4, 12)
+    B = S.uniform_matrix(81, 1, 12, 5)
+    clean = A @ B  # reference only for the final comparison below
+    ref, rep0 = _midk(A, B, 4)
+    assert rep0.detected == 0
+    plain, _ = _midk(A, B, 0)
+    assert np.array_equal(ref, plain)  # the checked steps change nothing on a clean run
+    assert np.max(np.abs(ref - clean)) <= 2 * 12 * 2.0 ** -53 * np.max(np.abs(A) @ np.abs(B))
+    hits = 0
+    for (i1, j1, i2, j2) in [(0, 0, 3, 4), (1, 2, 2, 3), (3, 1, 0, 4)]:
+        for bit in (44, 52, 60, 62):
+            inj = [dict(i=i1, j=j1, site=O.SITE_ACCUM, mode=O.MODE_BITFLIP, bit=bit, kt=1),
+                   dict(i=i2, j=j2, site=O.SITE_ACCUM, mode=O.MODE_BITFLIP, bit=bit, kt=3)]
+            got, rep = _midk(A, B, 4, inj)
+            recs = sorted((r.i, r.j, r.kind) for r in rep.records())
+            if rep.corrected == 2:
+                hits += 1
+                assert recs == sorted([(i1, j1, O.KIND_CORRECTED), (i2, j2, O.KIND_CORRECTED)])
+                assert np.array_equal(got, ref)
+            _, rep_end = _midk(A, B, 0, inj)
+            if rep.corrected == 2:
+                assert rep_end.uncorrectable == 1 and rep_end.corrected == 0
+    assert hits >= 10  # a flip is undetectable only when the partial sum is tiny
+
+
+def test_midk_exact_delta_on_integer_data():
+    """Integer operands: partial checksums are exact, so at the first check after the flip
+    delta_row = delta_col = the flip's exact error, and the record carries it."""
+    A = (np.arange(4)[:, None] + np.arange(8)[None, :]).astype(np.float64)
+    B = (np.arange(8)[:, None] - np.arange(5)[None, :]).astype(np.float64)
+    i, j = 2, 3
+    acc_after_2 = sum(A[i, k] * B[k, j] for k in range(2))  # flip lands after kt * bk = 2 products
+    bit = 55
+    flipped = struct.unpack("<d", struct.pack("<Q", struct.unpack("<Q", struct.pack("<d", acc_after_2))[0] ^ (1 << bit)))[0]
+    e = flipped - acc_after_2
+    got, rep = _midk(A, B, 4, [dict(i=i, j=j, site=O.SITE_ACCUM, mode=O.MODE_BITFLIP, bit=bit, kt=1)])
+    (r,) = rep.records()
+    assert (r.i, r.j, r.kind) == (i, j, O.KIND_CORRECTED)
+    assert r.delta_row == e and r.delta_col == e
+    assert np.array_equal(got, A @ B)
+
+
+def test_midk_clean_runs_never_flag():
+    for seed in range(6):
+        M, N, K = 40, 50, 96
+        A = S.normal_matrix(seed, 0, M, K) * S.pow2_row_scales(seed, 3, M)[:, None]
+        B = S.normal_matrix(seed, 1, K, N)
+        _, rep = _midk(A, B, 16, tile=(16, 16), bk=8, alpha=1.5, beta=0.5, C=S.normal_matrix(seed, 2, M, N))
+        assert rep.detected == 0
