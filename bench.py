@@ -67,6 +67,7 @@ def parse_args():
     ap.add_argument("--unfused-only", action="store_true",
                     help="measure only the unfused comparator (ABFT passes around cuBLAS DGEMM)")
     ap.add_argument("--no-unfused", action="store_true", help="skip the unfused comparator")
+    ap.add_argument("--no-online", action="store_true", help="skip the online-verification measurement")
     ap.add_argument("--linear-only", action="store_true", help="measure only the protected linear layer (config 4)")
     ap.add_argument("--no-linear", action="store_true", help="skip the protected linear layer (config 4)")
     ap.add_argument("--fp8-only", action="store_true",
@@ -870,6 +871,32 @@ def run_ours(args, rank, world, dist):
                             clean_rep=cl_rep, noabft_ms=na_ms)
     fb.ftblas_set_fp64_engine(engines[args.engine])
 
+    # Online verification (Section V.A rank-K_c steps): checks every K/4 products; timed
+    # clean, then one call with two accumulator flips in the same tile, in different steps.
+    online = None
+    if rank == 0 and not args.no_online:
+        kc = max(1, n // 4)
+        fb.ftblas_set_verification_interval(kc)
+        on_ms, _, on_rep, _, _ = timed(True, False, args.steps, args.warmup)
+        nk = -(-n // 32)
+        pts = [dict(i=11, j=13, site=fb.SITE_ACCUM, mode=fb.MODE_BITFLIP, bit=56, kt=max(1, nk // 8)),
+               dict(i=99, j=77, site=fb.SITE_ACCUM, mode=fb.MODE_BITFLIP, bit=58, kt=max(2, 5 * nk // 8))]
+        fb.ftblas_set_injection(fb.make_injection(fixed=pts))
+        rep2 = fb.new_report(dev)
+        fb.check(fb.ftblas_dgemm(fb.COL_MAJOR, fb.NO_TRANS, fb.NO_TRANS, n, n, n, 1.5, dA.data_ptr(), n,
+                                 dB.data_ptr(), n, 0.5, dC.data_ptr(), n, st, rep2.data_ptr()))
+        torch.cuda.synchronize(dev)
+        r2 = fb.report_from_device(rep2)
+        fb.ftblas_set_injection(None)
+        fb.ftblas_set_verification_interval(0)
+        na_ms = results[args.engine]["noabft_ms"]
+        online = {"interval_products": kc, "checks_per_tile": -(-n // kc) - 1,
+                  "ft_tflops_clean": flops_step * args.steps / (on_ms / 1e3) / 1e12,
+                  "abft_overhead_pct_clean": 100.0 * (on_ms / na_ms - 1.0),
+                  "false_alarms_clean": on_rep["detected"],
+                  "two_faults_one_tile": {"injected": 2, "detected": int(r2.detected), "corrected": int(r2.corrected),
+                                          "uncorrectable": int(r2.uncorrectable)}}
+
     # Accuracy at the stated error: one more protected call from the known C_in, checked on
     # sampled rows against the oracle.
     err = None
@@ -976,6 +1003,7 @@ def run_ours(args, rank, world, dist):
         "cpu_baseline": cpu,
         "bf16": bf16,
         "fp8_e4m3": fp8,
+        "online_verification": online,
         "linear_bf16": linear,
         "unfused_fp64": unfused,
         "e2e": e2e,

@@ -108,7 +108,9 @@ typedef struct {
 
 typedef struct {
   int64_t i, j;               /* element of C, caller's coordinates */
-  int32_t site, mode, bit, rel_log2, sign, reserved;
+  int32_t site, mode, bit, rel_log2, sign;
+  int32_t k_tile;             /* FP64 accumulator site: flip after k_tile k-tiles of products
+                                 (0: after floor(nk/2)); the tensor-core paths flip after all K */
 } ft_inject_point_t;
 
 typedef struct {
@@ -262,6 +264,16 @@ int ftblas_verification_tile(ftblas_layout_t layout, ftblas_dtype_t compute_type
  * tensor-core mma.sync m8n8k4). Both run the same staging, encode and epilogue. Returns
  * the previous engine, or -1 for an unknown value. Process-wide. */
 int ftblas_set_fp64_engine(int engine);
+
+/* Online verification (Section V.A): the FP64 protected kernels also check each tile
+ * after every k_interval products (rounded up to whole k-tiles of ftblas_verification_tile's
+ * depth), on the partial product, with the finished tile's threshold for the k processed so
+ * far; exactly one mismatching row and column there are corrected at once by recomputing
+ * that accumulator over those k (bit-exact), so one error per interval per tile is
+ * correctable. Other patterns at an interval are left to the check of the finished tile.
+ * Report counters then count verification events. 0 (the default) checks only the
+ * finished tile. Process-wide; returns the previous value, or -1 for a negative argument. */
+int64_t ftblas_set_verification_interval(int64_t k_interval);
 
 /* Staging path of the calling thread's most recent GEMM launch: 1 = operands staged by
  * TMA (16-byte aligned base addresses and leading dimensions), 0 = cooperative loads (any

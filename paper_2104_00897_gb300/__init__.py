@@ -58,7 +58,7 @@ class FtReport(C.Structure):
 
 class FtInjectPoint(C.Structure):
     _fields_ = [("i", C.c_int64), ("j", C.c_int64), ("site", C.c_int32), ("mode", C.c_int32),
-                ("bit", C.c_int32), ("rel_log2", C.c_int32), ("sign", C.c_int32), ("reserved", C.c_int32)]
+                ("bit", C.c_int32), ("rel_log2", C.c_int32), ("sign", C.c_int32), ("k_tile", C.c_int32)]
 
 
 class FtInject(C.Structure):
@@ -90,6 +90,7 @@ SIGNATURES = {
     "ftblas_verification_tile": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64,
                                            C.c_void_p, C.c_void_p, C.c_void_p]),
     "ftblas_set_fp64_engine": (C.c_int, [C.c_int]),
+    "ftblas_set_verification_interval": (C.c_int64, [C.c_int64]),
     "ftblas_status_string": (C.c_char_p, [C.c_int]),
     "ftblas_last_cuda_error": (C.c_int, []),
     "ftblas_last_launch_used_tma": (C.c_int, []),
@@ -189,6 +190,10 @@ def ftblas_verification_tile(layout, compute_type, M, N, K):
     return r.value, c.value, k.value
 
 
+def ftblas_set_verification_interval(k_interval):
+    return _call("ftblas_set_verification_interval", int(k_interval))
+
+
 def ftblas_set_fp64_engine(engine):
     return _call("ftblas_set_fp64_engine", engine)
 
@@ -225,7 +230,8 @@ def ftblas_kernel_timing_end():
 def make_injection(seed=0, site=SITE_ACCUM, mode=MODE_BITFLIP, bit_lo=40, bit_hi=62, log2_lo=0, log2_hi=0,
                    every_n_launches=0, errors_per_launch=0, fixed=()):
     """Build an FtInject. ``fixed``: iterable of dicts with i, j and optional site, mode,
-    bit, rel_log2, sign; when given, those points are injected on every launch."""
+    bit, rel_log2, sign and kt (FP64 accumulator flips: after kt k-tiles, 0 = floor(nk/2));
+    when given, those points are injected on every launch."""
     cfg = FtInject(seed=seed, site=site, mode=mode, bit_lo=bit_lo, bit_hi=bit_hi, log2_lo=log2_lo, log2_hi=log2_hi,
                    every_n_launches=every_n_launches, errors_per_launch=errors_per_launch, n_fixed=0, reserved=0)
     pts = list(fixed)
@@ -234,7 +240,7 @@ def make_injection(seed=0, site=SITE_ACCUM, mode=MODE_BITFLIP, bit_lo=40, bit_hi
     for q, p in enumerate(pts):
         cfg.fixed[q] = FtInjectPoint(i=p["i"], j=p["j"], site=p.get("site", SITE_ACCUM),
                                      mode=p.get("mode", MODE_BITFLIP), bit=p.get("bit", 0),
-                                     rel_log2=p.get("rel_log2", 0), sign=p.get("sign", 1), reserved=0)
+                                     rel_log2=p.get("rel_log2", 0), sign=p.get("sign", 1), k_tile=p.get("kt", 0))
     cfg.n_fixed = len(pts)
     return cfg
 

@@ -20,6 +20,10 @@
 // one flagged column locate the error (Section V.A), which is corrected by recomputing
 // that element with the identical instruction sequence (bit-exact fault-free value);
 // other patterns are classified and reported. Then the tile is stored.
+// Online verification (optional, Section V.A): every kc_tiles k-tiles the same comparison
+// runs on the partial product (raw accumulators against the predicted partial checksums,
+// threshold for the k done so far); one flagged row and column are corrected there by
+// recomputing that accumulator over those k, so each interval tolerates one error.
 #include <climits>
 
 #include "ft_device.cuh"
@@ -48,6 +52,9 @@ struct __align__(1024) DSmem {
   double tau_row, tau_col;
   int recompute;          // 1: the located element must be recomputed
   int loc_i, loc_j;       // tile-local location
+  // online verification scratch: per-slot row / column sums of the raw accumulators
+  double mrs[8 * BM], mra[8 * BM];   // [ROW_SLOTS <= 8][BM] sums, upward sums of magnitudes
+  double mcs[4 * BN], mca[4 * BN];   // [COL_SLOTS <= 4][BN]
 };
 
 // Operand element (i, k) of the staged A tile and (k, j) of the staged B tile.
@@ -104,7 +111,7 @@ struct EngineDFMA {
   // chain in ascending k (the zero-filled padding of the last k-tile adds exact zeros).
   // Called by the owning thread only; returns true if this thread produced the value.
   __device__ static bool recompute(const DgemmParams& p, int64_t gi, int64_t gj, int t, int li, int lj,
-                                   double& out) {
+                                   double& out, int64_t kmax) {
     bool mine = false;
 #pragma unroll
     for (int r = 0; r < NR; ++r)
@@ -112,7 +119,7 @@ struct EngineDFMA {
       for (int c = 0; c < NC; ++c) mine |= (row(t, r) == li && col(t, c) == lj);
     if (!mine) return false;
     double acc = 0.0;
-    for (int64_t k = 0; k < p.K; ++k) acc = fma(ldg_a(p, gi, k), ldg_b(p, k, gj), acc);
+    for (int64_t k = 0; k < kmax; ++k) acc = fma(ldg_a(p, gi, k), ldg_b(p, k, gj), acc);
     out = acc;
     return true;
   }
@@ -159,15 +166,15 @@ struct EngineDMMA {
   }
 
   // Warp-cooperative recompute of the 8 x 8 fragment holding the element, with the same
-  // mma sequence over k in chunks of 4 (out-of-range operands are the zeros TMA filled).
+  // mma sequence over k < kmax in chunks of 4 (out-of-range operands are the zeros TMA filled).
   __device__ static bool recompute(const DgemmParams& p, int64_t gi, int64_t gj, int t, int li, int lj,
-                                   double& out) {
+                                   double& out, int64_t kmax) {
     const int w_row = li / 32, w_col = lj / 64;
     if (wm(t) != w_row || wn(t) != w_col) return false;  // warp-uniform
     const int64_t rb = gi - (li % 8), cb = gj - (lj % 8);  // fragment origin, kernel frame
     const int64_t ra = rb + g(t), cbb = cb + g(t);
     double d0 = 0.0, d1 = 0.0;
-    for (int64_t k0 = 0; k0 < p.K; k0 += 4) {
+    for (int64_t k0 = 0; k0 < kmax; k0 += 4) {
       const int64_t k = k0 + q(t);
       const double a = (ra < p.M && k < p.K) ? ldg_a(p, ra, k) : 0.0;
       const double b = (cbb < p.N && k < p.K) ? ldg_b(p, k, cbb) : 0.0;
@@ -276,6 +283,66 @@ __device__ __forceinline__ void issue_ktile(DSmem& sm, const CUtensorMap* tmA, c
   else tma_load_2d(sm.b[s], tmB, &sm.full[s], n0, k0);
 }
 
+// Online verification of the partial product over k < kp (Section V.A): reference sums of
+// the raw accumulators against the running predictions pred (C^r or C^c without alpha,
+// beta) with tau = 2 [gamma_{kp + n + 3} P + gamma_n sum |acc|], P the running magnitude
+// bound. One flagged row and one flagged column: the accumulator at their crossing is
+// recomputed over k < kp with the product's own instruction sequence and a corrected record
+// written; other patterns are left to the finished tile's check. All threads of the CTA
+// call it (it synchronises).
+template <class E>
+__device__ __forceinline__ void online_check(const DgemmParams& p, double (&acc)[E::NR][E::NC], double pred, float pmag,
+                                          DSmem& sm, int t, int m0, int n0, int nI, int nJ, int64_t kp) {
+  tile_sums<E>([&](int r, int c) { return acc[r][c]; }, t, sm.mrs, sm.mra, sm.mcs, sm.mca);
+  const bool huge = __syncthreads_or(!isfinite(pmag));  // binary32 bound overflowed: skip
+  if (huge) return;
+  const bool is_row = t < BM;
+  const int idx = is_row ? t : t - BM;
+  const int nslots = is_row ? E::ROW_SLOTS : E::COL_SLOTS;
+  const int extent = is_row ? BM : BN;
+  const double* ps = is_row ? sm.mrs : sm.mcs;
+  const double* pa = is_row ? sm.mra : sm.mca;
+  double ref = 0.0, R = 0.0;
+  for (int sl = 0; sl < nslots; ++sl) {
+    ref += ps[sl * extent + idx];
+    R = __dadd_ru(R, pa[sl * extent + idx]);
+  }
+  const double delta = ref - pred;
+  const int n_other = is_row ? nJ : nI;
+  double tau = __fma_ru(gamma_up64(kp + n_other + 3), (double)pmag, __dmul_ru(gamma_up64(n_other), R));
+  tau = __dmul_ru(2.0, tau);
+  const bool valid = idx < (is_row ? nI : nJ);
+  const bool flagged = valid && (!(fabs(delta) <= tau) || isinf(delta));
+  if (flagged) atomicMin(is_row ? &sm.first_row : &sm.first_col, idx);
+  const int nr = __syncthreads_count(is_row && flagged);
+  const int nc = __syncthreads_count(!is_row && flagged);
+  if (flagged && is_row && idx == sm.first_row) { sm.delta_row = delta; sm.tau_row = tau; }
+  if (flagged && !is_row && idx == sm.first_col) { sm.delta_col = delta; sm.tau_col = tau; }
+  __syncthreads();
+  if (nr == 1 && nc == 1 && sm.nonfinite == 0) {
+    const int li = sm.first_row, lj = sm.first_col;
+    const int64_t gi = m0 + li, gj = n0 + lj;
+    double fixed;
+    if (E::recompute(p, gi, gj, t, li, lj, fixed, kp)) {
+      double before = 0.0;
+#pragma unroll
+      for (int r = 0; r < E::NR; ++r)
+#pragma unroll
+        for (int c = 0; c < E::NC; ++c)
+          if (E::row(t, r) == li && E::col(t, c) == lj) { before = acc[r][c]; acc[r][c] = fixed; }
+      write_record(p, FT_KIND_CORRECTED, blockIdx.x, blockIdx.y, gi, gj, sm.delta_row, sm.delta_col, sm.tau_row,
+                   sm.tau_col, before, fixed, 1, 1);
+      if (p.report) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&p.report->detected), 1ull);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&p.report->corrected), 1ull);
+      }
+    }
+  }
+  __syncthreads();
+  if (t == 0) { sm.first_row = INT_MAX; sm.first_col = INT_MAX; }
+  __syncthreads();
+}
+
 template <class E, bool AK, bool BKM, bool FT>
 __global__ void __launch_bounds__(NT, 1)
     dgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -324,11 +391,13 @@ __global__ void __launch_bounds__(NT, 1)
     const double* sB = sm.b[s];
 
     if (FT) {
-      // Accumulator injection after bk * floor(nk / 2) products (test launches only).
-      if (kt == kstar_tile && p.inj.n > 0) {
+      // Accumulator injection after bk * kt products, kt = the point's k-tile or floor(nk / 2)
+      // (test launches only).
+      if (p.inj.n > 0) {
         for (int e = 0; e < p.inj.n; ++e) {
           const InjectPoint& ip = p.inj.p[e];
           if (ip.site != kSiteAccum || ip.mode != FT_MODE_BITFLIP) continue;
+          if (kt != (ip.kt > 0 ? ip.kt : kstar_tile)) continue;
           const int li = ip.i - m0, lj = ip.j - n0;
           if (li < 0 || li >= nI || lj < 0 || lj >= nJ) continue;
 #pragma unroll
@@ -394,6 +463,8 @@ __global__ void __launch_bounds__(NT, 1)
     E::template ktile<AK, BKM>(acc, sA, sB, t);
     __syncthreads();
     if (p.use_tma && t == 0 && kt + STAGES < nk) issue_ktile<AK, BKM>(sm, &tmA, &tmB, s, m0, n0, (kt + STAGES) * BK);
+    if (FT && p.kc_tiles > 0 && (kt + 1) % p.kc_tiles == 0 && kt + 1 < nk)
+      online_check<E>(p, acc, pred, pmag, sm, t, m0, n0, nI, nJ, (int64_t)(kt + 1) * BK);
   }
 
   if (sm.timeout) {
@@ -546,7 +617,7 @@ __global__ void __launch_bounds__(NT, 1)
       const int li = sm.first_row, lj = sm.first_col;
       const int64_t gi = m0 + li, gj = n0 + lj;
       double acc_fixed;
-      const bool mine = E::recompute(p, gi, gj, t, li, lj, acc_fixed);
+      const bool mine = E::recompute(p, gi, gj, t, li, lj, acc_fixed, p.K);
       if (mine) {
         const double cin = beta_nz ? p.C[gi + gj * p.ldc] : 0.0;
         const double fixed = beta_nz ? fma(p.alpha, acc_fixed, p.beta * cin) : p.alpha * acc_fixed;

@@ -20,7 +20,8 @@ enum : int32_t { kSiteAccum = 1, kSiteOutput = 2, kSiteChecksumRow = 3, kSiteChe
 struct InjectPoint {
   int32_t i, j;          // kernel-frame element
   int32_t site, mode;    // kSite*, FT_MODE_*
-  int32_t bit, rel_log2, sign, pad;
+  int32_t bit, rel_log2, sign;
+  int32_t kt;            // FP64 accumulator site: k-tile of the flip (0: floor(nk/2))
 };
 
 constexpr int kMaxInject = FTBLAS_MAX_INJECTIONS_PER_LAUNCH;
@@ -42,7 +43,7 @@ struct DgemmParams {
   int32_t a_kmajor, b_kmajor;    // storage: A k-contiguous?  B k-contiguous?
   ft_report_t* report;           // may be null
   int32_t swap_report;           // 1: records in the transposed (caller row-major) frame
-  int32_t pad_;
+  int32_t kc_tiles;              // online verification every kc_tiles k-tiles (0: finished tile only)
   InjectList inj;
 };
 

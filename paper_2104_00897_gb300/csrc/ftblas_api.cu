@@ -19,6 +19,7 @@ namespace {
 thread_local int g_last_cuda_error = 0;
 thread_local int g_last_used_tma = -1;
 std::atomic<int> g_fp64_engine{kEngineDFMA};
+std::atomic<int64_t> g_kc_interval{0};
 
 // ------------------------------------------------------------------ injection plan state
 std::mutex g_inj_mu;
@@ -43,7 +44,7 @@ uint64_t splitmix_next(uint64_t& s) {
 
 struct CallerPoint {
   int64_t i, j;
-  int32_t site, mode, bit, rel_log2, sign;
+  int32_t site, mode, bit, rel_log2, sign, kt;
 };
 
 // The points injected into this launch, in the caller's coordinates. The seeded draw is
@@ -58,7 +59,7 @@ int plan_injections(int64_t M, int64_t N, int64_t tile_rows, int64_t tile_cols, 
     for (int q = 0; q < c.n_fixed && n < kMaxInject; ++q) {
       const ft_inject_point_t& f = c.fixed[q];
       if (f.i < 0 || f.i >= M || f.j < 0 || f.j >= N) continue;
-      out[n++] = CallerPoint{f.i, f.j, f.site, f.mode, f.bit, f.rel_log2, f.sign};
+      out[n++] = CallerPoint{f.i, f.j, f.site, f.mode, f.bit, f.rel_log2, f.sign, f.k_tile};
     }
     return n;
   }
@@ -90,6 +91,7 @@ int plan_injections(int64_t M, int64_t N, int64_t tile_rows, int64_t tile_cols, 
     pnt.bit = c.bit_lo + static_cast<int32_t>(rb % static_cast<uint64_t>(c.bit_hi - c.bit_lo + 1));
     pnt.rel_log2 = c.log2_lo + static_cast<int32_t>(rp % static_cast<uint64_t>(c.log2_hi - c.log2_lo + 1));
     pnt.sign = (rs & 1) ? -1 : 1;
+    pnt.kt = 0;
   }
   return n;
 }
@@ -228,6 +230,10 @@ int dgemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, doub
   p.a_kmajor = f.a_kmajor; p.b_kmajor = f.b_kmajor;
   p.report = ft ? report : nullptr;
   p.swap_report = f.swap;
+  {
+    const int64_t kc = g_kc_interval.load();
+    p.kc_tiles = (ft && kc > 0) ? (int32_t)((kc + kDBK - 1) / kDBK) : 0;
+  }
   p.inj.n = 0;
   for (int q = 0; q < npts; ++q) {
     InjectPoint& ip = p.inj.p[p.inj.n++];
@@ -235,7 +241,7 @@ int dgemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, doub
     ip.i = (int32_t)(f.swap ? c.j : c.i);
     ip.j = (int32_t)(f.swap ? c.i : c.j);
     ip.site = c.site == FT_SITE_CHECKSUM ? (f.swap ? kSiteChecksumCol : kSiteChecksumRow) : c.site;
-    ip.mode = c.mode; ip.bit = c.bit; ip.rel_log2 = c.rel_log2; ip.sign = c.sign; ip.pad = 0;
+    ip.mode = c.mode; ip.bit = c.bit; ip.rel_log2 = c.rel_log2; ip.sign = c.sign; ip.kt = c.kt;
   }
   CUtensorMap tmA, tmB;
   std::memset(&tmA, 0, sizeof(tmA));
@@ -283,7 +289,7 @@ int dgemm_unfused_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t
     ip.i = (int32_t)(f.swap ? c.j : c.i);
     ip.j = (int32_t)(f.swap ? c.i : c.j);
     ip.site = c.site == FT_SITE_CHECKSUM ? kSiteChecksumRow : c.site;
-    ip.mode = c.mode; ip.bit = c.bit; ip.rel_log2 = c.rel_log2; ip.sign = c.sign; ip.pad = 0;
+    ip.mode = c.mode; ip.bit = c.bit; ip.rel_log2 = c.rel_log2; ip.sign = c.sign; ip.kt = c.kt;
   }
   cudaError_t ce = cudaSuccess;
   const int rc = unfused_dgemm(p, st, &ce);
@@ -358,7 +364,7 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
     ip.i = (int32_t)(f.swap ? c.j : c.i);
     ip.j = (int32_t)(f.swap ? c.i : c.j);
     ip.site = c.site == FT_SITE_CHECKSUM ? kSiteChecksumRow : c.site;
-    ip.mode = c.mode; ip.bit = c.bit; ip.rel_log2 = c.rel_log2; ip.sign = c.sign; ip.pad = 0;
+    ip.mode = c.mode; ip.bit = c.bit; ip.rel_log2 = c.rel_log2; ip.sign = c.sign; ip.kt = c.kt;
   }
   const int eb = fp8 ? 1 : 2;
   CUtensorMap tmA, tmB, tmC;
@@ -628,6 +634,11 @@ int ftblas_verification_tile(ftblas_layout_t layout, ftblas_dtype_t compute_type
   *tile_cols = swap ? bm : bn;
   *k_tile = compute_type == FTBLAS_R_64F ? kDBK : 64;
   return 0;
+}
+
+int64_t ftblas_set_verification_interval(int64_t k_interval) {
+  if (k_interval < 0) return -1;
+  return g_kc_interval.exchange(k_interval);
 }
 
 int ftblas_set_fp64_engine(int engine) {

@@ -35,10 +35,10 @@ class Problem:
         self.b, self.ldb = stored(layout, tb, self.B, pad)
         self.c, self.ldc = S.store(self.Cin, layout, ld=lead(M if layout == O.COL_MAJOR else N, pad))
 
-    def oracle_ft(self, tile_rows, tile_cols, bk, injections=(), tiles=None):
+    def oracle_ft(self, tile_rows, tile_cols, bk, injections=(), tiles=None, kc=0):
         out, rep = O.ft_gemm(self.layout, self.ta, self.tb, self.M, self.N, self.K, self.alpha, self.a, self.lda,
                              self.b, self.ldb, self.beta, self.c, self.ldc, tile_rows, tile_cols, bk,
-                             injections=injections, tiles=tiles)
+                             injections=injections, tiles=tiles, kc=kc)
         return S.load(out, self.layout, self.M, self.N, self.ldc), rep
 
     def oracle_plain(self):

@@ -319,3 +319,52 @@ def test_full_size_8192_sampled_rows_and_faulted_tile(engine):
     t = (i // tr) + (j // tc) * ((n + tr - 1) // tr)
     _, orep = P.oracle_ft(tr, tc, bk, injections=[dict(i=i, j=j, site=O.SITE_ACCUM, bit=45)], tiles=[t])
     assert record_set(orep) == record_set(rep)
+
+
+# ---------------------------------------------------------------------------------------
+# Online verification every kc products (ftblas_set_verification_interval)
+# ---------------------------------------------------------------------------------------
+
+@pytest.fixture
+def _interval_off():
+    yield
+    fb.ftblas_set_verification_interval(0)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_online_checks_leave_clean_runs_bitwise_unchanged(engine, _interval_off):
+    fb.ftblas_set_fp64_engine(engine)
+    P = Problem(300, 260, 700, O.COL_MAJOR, O.NO_TRANS, O.TRANS, alpha=1.5, beta=0.5, seed=31)
+    base, rep0 = run_gpu(P)
+    fb.ftblas_set_verification_interval(128)
+    got, rep = run_gpu(P)
+    assert np.array_equal(got, base)
+    assert rep.detected == 0 and rep.tiles_checked == rep0.tiles_checked
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("layout", [O.COL_MAJOR, O.ROW_MAJOR])
+def test_online_checks_correct_two_faults_in_one_tile(engine, layout, _interval_off):
+    """Two accumulator flips in one tile, in different intervals: with checks every 128
+    products (4 k-tiles) both are corrected where they occur, as the oracle's interval mode
+    does, and C equals the fault-free C of the same engine bit for bit; without online
+    checks the pair is uncorrectable."""
+    fb.ftblas_set_fp64_engine(engine)
+    P = Problem(256, 256, 512, layout, O.NO_TRANS, O.NO_TRANS, alpha=1.0, beta=0.0, seed=33)
+    clean, _ = run_gpu(P)
+    tr, tc, bk = tile_of(P)
+    pts = [dict(i=5, j=7, site=fb.SITE_ACCUM, mode=fb.MODE_BITFLIP, bit=55, kt=2),
+           dict(i=70, j=90, site=fb.SITE_ACCUM, mode=fb.MODE_BITFLIP, bit=58, kt=9),
+           dict(i=200, j=140, site=fb.SITE_ACCUM, mode=fb.MODE_BITFLIP, bit=52, kt=5)]
+    fb.ftblas_set_injection(fb.make_injection(fixed=pts))
+    got_end, rep_end = run_gpu(P)
+    _, orep_end = P.oracle_ft(tr, tc, bk, injections=pts)
+    assert report_summary(rep_end) == report_summary(orep_end)
+    assert rep_end.uncorrectable >= 1
+    fb.ftblas_set_verification_interval(128)
+    got, rep = run_gpu(P)
+    _, orep = P.oracle_ft(tr, tc, bk, injections=pts, kc=128)
+    assert report_summary(rep) == report_summary(orep)
+    assert record_set(rep) == record_set(orep)
+    assert (rep.corrected, rep.uncorrectable) == (3, 0)
+    assert np.array_equal(got, clean)
