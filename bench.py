@@ -68,6 +68,8 @@ def parse_args():
                     help="measure only the unfused comparator (ABFT passes around cuBLAS DGEMM)")
     ap.add_argument("--no-unfused", action="store_true", help="skip the unfused comparator")
     ap.add_argument("--no-online", action="store_true", help="skip the online-verification measurement")
+    ap.add_argument("--no-level3", action="store_true", help="skip the FT-DSYMM / FT-DTRMM measurement")
+    ap.add_argument("--level3-only", action="store_true", help="measure only FT-DSYMM / FT-DTRMM")
     ap.add_argument("--linear-only", action="store_true", help="measure only the protected linear layer (config 4)")
     ap.add_argument("--no-linear", action="store_true", help="skip the protected linear layer (config 4)")
     ap.add_argument("--fp8-only", action="store_true",
@@ -482,6 +484,52 @@ def run_sweep(dev, steps, warmup, shapes=SWEEP_SHAPES):
             "peak_tflops": peak, "steps": steps, "warmup": warmup, "rows": rows}
 
 
+def run_level3(dev, n, steps, warmup):
+    """FT-DSYMM and FT-DTRMM (side left, upper, column-major, n x n operands, U[-1,1]):
+    TFLOP/s by their own flop counts (DSYMM 2 n^3, DTRMM n^3) over the whole call (copy of
+    the symmetric / triangular operand included), one accumulator flip in the timed calls
+    (inside the faulted tile's k-range for DTRMM)."""
+    import torch
+
+    import paper_2104_00897_gb300 as fb
+    import synth as S
+
+    A = torch.from_numpy(S.uniform(SEED + 9, 0, n * n)).to(dev)
+    B = torch.from_numpy(S.uniform(SEED + 9, 1, n * n)).to(dev)
+    C = torch.from_numpy(S.uniform(SEED + 9, 2, n * n)).to(dev)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    nk = -(-n // 32)
+    out = {}
+    for name, flops in (("dsymm", 2.0 * n ** 3), ("dtrmm", 1.0 * n ** 3)):
+        def call(rep):
+            if name == "dsymm":
+                fb.check(fb.ftblas_dsymm(fb.COL_MAJOR, fb.LEFT, fb.UPPER, n, n, 1.0, A.data_ptr(), n, B.data_ptr(), n,
+                                         0.5, C.data_ptr(), n, st, rep.data_ptr() if rep is not None else None))
+            else:
+                fb.check(fb.ftblas_dtrmm(fb.COL_MAJOR, fb.LEFT, fb.UPPER, fb.NO_TRANS, fb.NON_UNIT, n, n, 1.0,
+                                         A.data_ptr(), n, B.data_ptr(), n, st,
+                                         rep.data_ptr() if rep is not None else None))
+        for _ in range(warmup):
+            call(None)
+        torch.cuda.synchronize(dev)
+        pts = [dict(i=n // 2 + 5, j=7, site=fb.SITE_ACCUM, mode=fb.MODE_BITFLIP, bit=57, kt=(3 * nk) // 4)]
+        fb.ftblas_set_injection(fb.make_injection(fixed=pts))
+        reps = [fb.new_report(dev) for _ in range(steps)]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for s_ in range(steps):
+            call(reps[s_])
+        e1.record()
+        torch.cuda.synchronize(dev)
+        fb.ftblas_set_injection(None)
+        ms = e0.elapsed_time(e1) / steps
+        rr = [fb.report_from_device(r) for r in reps]
+        out[name] = {"tflops": flops / ms / 1e9, "ms": ms, "injected": steps,
+                     "corrected": sum(int(r.corrected) for r in rr), "detected": sum(int(r.detected) for r in rr)}
+    out["workload"] = f"FT-DSYMM / FT-DTRMM {n}x{n}, side left, upper, column-major, U[-1,1]"
+    return out
+
+
 def run_unfused(dev, n, steps, warmup):
     """NEXT-1 comparator: the same FP64 workload as the headline (8192^3, column-major, alpha
     1.5, beta 0.5, U[-1,1]) through ftblas_dgemm_unfused: ABFT as separate bandwidth-bound
@@ -762,6 +810,10 @@ def run_ours(args, rank, world, dist):
         if rank == 0:
             print(json.dumps({"sweep_fp64": run_sweep(dev, args.steps, args.warmup)}), flush=True)
         return 0
+    if args.level3_only:
+        if rank == 0:
+            print(json.dumps({"level3_fp64": run_level3(dev, n, args.steps, args.warmup)}), flush=True)
+        return 0
     if args.unfused_only:
         if rank == 0:
             print(json.dumps({"unfused_fp64": run_unfused(dev, n, args.steps, args.warmup)}), flush=True)
@@ -956,6 +1008,9 @@ def run_ours(args, rank, world, dist):
     unfused = None
     if not args.no_unfused and rank == 0:
         unfused = run_unfused(dev, n, args.steps, args.warmup)
+    level3 = None
+    if not args.no_level3 and rank == 0:
+        level3 = run_level3(dev, n, max(1, args.steps // 2), max(1, args.warmup // 2))
 
     if rank != 0:
         return 0
@@ -1006,6 +1061,7 @@ def run_ours(args, rank, world, dist):
         "online_verification": online,
         "linear_bf16": linear,
         "unfused_fp64": unfused,
+        "level3_fp64": level3,
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clocks,

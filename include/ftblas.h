@@ -38,6 +38,9 @@ extern "C" {
 
 typedef enum { FTBLAS_ROW_MAJOR = 101, FTBLAS_COL_MAJOR = 102 } ftblas_layout_t;   /* CBLAS values */
 typedef enum { FTBLAS_NO_TRANS = 111, FTBLAS_TRANS = 112 } ftblas_trans_t;
+typedef enum { FTBLAS_UPPER = 121, FTBLAS_LOWER = 122 } ftblas_uplo_t;
+typedef enum { FTBLAS_NON_UNIT = 131, FTBLAS_UNIT = 132 } ftblas_diag_t;
+typedef enum { FTBLAS_LEFT = 141, FTBLAS_RIGHT = 142 } ftblas_side_t;
 
 /* Element types of ftblas_gemm_ex. */
 typedef enum {
@@ -157,6 +160,29 @@ int ftblas_dgemm_noabft(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_tr
                         int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
                         const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
                         void* stream);
+
+/* FT-DSYMM (the paper's Level-3 family beside GEMM): C = alpha A B + beta C (side LEFT, A
+ * M x M) or C = alpha B A + beta C (side RIGHT, A N x N), A symmetric with only its `uplo`
+ * triangle read. A full copy of A is formed on `stream` (workspace from the stream-ordered
+ * allocator) and the product runs through ftblas_dgemm's protected kernel: same report,
+ * tiles, thresholds, injection plan and online verification. Arguments 1-15 in CBLAS
+ * order (layout, side, uplo, M, N, alpha, A, lda, B, ldb, beta, C, ldc, stream, report);
+ * returns -p for a bad argument p, or an FTBLAS_STATUS_* code. */
+int ftblas_dsymm(ftblas_layout_t layout, ftblas_side_t side, ftblas_uplo_t uplo, int64_t M, int64_t N,
+                 double alpha, const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                 double* C, int64_t ldc, void* stream, ft_report_t* report);
+
+/* FT-DTRMM: B = alpha op(A) B (side LEFT, A M x M) or B = alpha B op(A) (side RIGHT, A N x N),
+ * A triangular (`uplo`, `diag`: FTBLAS_UNIT takes the diagonal as 1 without reading it), B
+ * overwritten. A copy of op(A) with explicit zeros and a copy of B are formed on `stream`,
+ * then ftblas_dgemm's protected kernel runs, each tile visiting only the k-tiles the
+ * triangle leaves nonzero (about half the work of the full product). Protection as for
+ * ftblas_dgemm; an accumulator injection point whose k-tile (explicit, or floor(nk/2)) falls
+ * outside its tile's range is not applied. Arguments 1-14 in CBLAS order (layout, side, uplo,
+ * transa, diag, M, N, alpha, A, lda, B, ldb, stream, report). */
+int ftblas_dtrmm(ftblas_layout_t layout, ftblas_side_t side, ftblas_uplo_t uplo, ftblas_trans_t transa,
+                 ftblas_diag_t diag, int64_t M, int64_t N, double alpha, const double* A, int64_t lda,
+                 double* B, int64_t ldb, void* stream, ft_report_t* report);
 
 /* The unfused comparator (no counterpart in the fused design; it reproduces the
  * arrangement Section V improves on: ABFT as separate passes around a BLAS library call).

@@ -16,6 +16,9 @@ from . import build as _build
 
 ROW_MAJOR, COL_MAJOR = 101, 102
 NO_TRANS, TRANS = 111, 112
+UPPER, LOWER = 121, 122
+NON_UNIT, UNIT = 131, 132
+LEFT, RIGHT = 141, 142
 R_64F, R_32F, R_16BF, R_8F_E4M3 = 0, 1, 2, 3
 SITE_ACCUM, SITE_OUTPUT, SITE_CHECKSUM = 1, 2, 3
 MODE_BITFLIP, MODE_ADD_REL = 0, 1
@@ -87,6 +90,10 @@ SIGNATURES = {
     "ftblas_dgemm_noabft": (C.c_int, _GEMM_ARGS + [C.c_void_p]),
     "ftblas_dgemm_host": (C.c_int, _GEMM_ARGS + [C.c_void_p, C.c_void_p]),
     "ftblas_dgemm_unfused": (C.c_int, _GEMM_ARGS + [C.c_void_p, C.c_void_p]),
+    "ftblas_dsymm": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_double, C.c_void_p, C.c_int64,
+                               C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "ftblas_dtrmm": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_double,
+                               C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "ftblas_verification_tile": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64,
                                            C.c_void_p, C.c_void_p, C.c_void_p]),
     "ftblas_set_fp64_engine": (C.c_int, [C.c_int]),
@@ -138,6 +145,14 @@ def ftblas_dgemm_noabft(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, 
 def ftblas_dgemm_unfused(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream, report):
     return _call("ftblas_dgemm_unfused", layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream,
                  report)
+
+
+def ftblas_dsymm(layout, side, uplo, M, N, alpha, A, lda, B, ldb, beta, C_, ldc, stream, report):
+    return _call("ftblas_dsymm", layout, side, uplo, M, N, alpha, A, lda, B, ldb, beta, C_, ldc, stream, report)
+
+
+def ftblas_dtrmm(layout, side, uplo, transa, diag, M, N, alpha, A, lda, B, ldb, stream, report):
+    return _call("ftblas_dtrmm", layout, side, uplo, transa, diag, M, N, alpha, A, lda, B, ldb, stream, report)
 
 
 def ftblas_dgemm_host(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream, report):

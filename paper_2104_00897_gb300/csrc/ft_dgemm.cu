@@ -111,7 +111,7 @@ struct EngineDFMA {
   // chain in ascending k (the zero-filled padding of the last k-tile adds exact zeros).
   // Called by the owning thread only; returns true if this thread produced the value.
   __device__ static bool recompute(const DgemmParams& p, int64_t gi, int64_t gj, int t, int li, int lj,
-                                   double& out, int64_t kmax) {
+                                   double& out, int64_t kmin, int64_t kmax) {
     bool mine = false;
 #pragma unroll
     for (int r = 0; r < NR; ++r)
@@ -119,7 +119,7 @@ struct EngineDFMA {
       for (int c = 0; c < NC; ++c) mine |= (row(t, r) == li && col(t, c) == lj);
     if (!mine) return false;
     double acc = 0.0;
-    for (int64_t k = 0; k < kmax; ++k) acc = fma(ldg_a(p, gi, k), ldg_b(p, k, gj), acc);
+    for (int64_t k = kmin; k < kmax; ++k) acc = fma(ldg_a(p, gi, k), ldg_b(p, k, gj), acc);
     out = acc;
     return true;
   }
@@ -168,13 +168,13 @@ struct EngineDMMA {
   // Warp-cooperative recompute of the 8 x 8 fragment holding the element, with the same
   // mma sequence over k < kmax in chunks of 4 (out-of-range operands are the zeros TMA filled).
   __device__ static bool recompute(const DgemmParams& p, int64_t gi, int64_t gj, int t, int li, int lj,
-                                   double& out, int64_t kmax) {
+                                   double& out, int64_t kmin, int64_t kmax) {
     const int w_row = li / 32, w_col = lj / 64;
     if (wm(t) != w_row || wn(t) != w_col) return false;  // warp-uniform
     const int64_t rb = gi - (li % 8), cb = gj - (lj % 8);  // fragment origin, kernel frame
     const int64_t ra = rb + g(t), cbb = cb + g(t);
     double d0 = 0.0, d1 = 0.0;
-    for (int64_t k0 = 0; k0 < kmax; k0 += 4) {
+    for (int64_t k0 = kmin; k0 < kmax; k0 += 4) {
       const int64_t k = k0 + q(t);
       const double a = (ra < p.M && k < p.K) ? ldg_a(p, ra, k) : 0.0;
       const double b = (cbb < p.N && k < p.K) ? ldg_b(p, k, cbb) : 0.0;
@@ -292,7 +292,8 @@ __device__ __forceinline__ void issue_ktile(DSmem& sm, const CUtensorMap* tmA, c
 // call it (it synchronises).
 template <class E>
 __device__ __forceinline__ void online_check(const DgemmParams& p, double (&acc)[E::NR][E::NC], double pred, float pmag,
-                                          DSmem& sm, int t, int m0, int n0, int nI, int nJ, int64_t kp) {
+                                          DSmem& sm, int t, int m0, int n0, int nI, int nJ, int64_t kmin,
+                                          int64_t kp) {
   tile_sums<E>([&](int r, int c) { return acc[r][c]; }, t, sm.mrs, sm.mra, sm.mcs, sm.mca);
   const bool huge = __syncthreads_or(!isfinite(pmag));  // binary32 bound overflowed: skip
   if (huge) return;
@@ -323,7 +324,7 @@ __device__ __forceinline__ void online_check(const DgemmParams& p, double (&acc)
     const int li = sm.first_row, lj = sm.first_col;
     const int64_t gi = m0 + li, gj = n0 + lj;
     double fixed;
-    if (E::recompute(p, gi, gj, t, li, lj, fixed, kp)) {
+    if (E::recompute(p, gi, gj, t, li, lj, fixed, kmin, kp)) {
       double before = 0.0;
 #pragma unroll
       for (int r = 0; r < E::NR; ++r)
@@ -353,6 +354,15 @@ __global__ void __launch_bounds__(NT, 1)
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int nk = (p.K + BK - 1) / BK;
   const int kstar_tile = nk / 2;
+  // k-tiles this tile needs: all of them, or the range a triangular operand leaves nonzero
+  // (op(A) upper: k >= i; lower: k <= i; op(B) upper: k <= j; lower: k >= j).
+  int kb = 0, ke = nk;
+  if (p.tri_a == 1) kb = m0 / BK;
+  if (p.tri_a == 2) ke = min(ke, (m0 + BM + BK - 1) / BK);
+  if (p.tri_b == 1) ke = min(ke, (n0 + BN + BK - 1) / BK);
+  if (p.tri_b == 2) kb = max(kb, n0 / BK);
+  const int nl = ke > kb ? ke - kb : 0;  // k-tiles in range
+  const int64_t k_lo = (int64_t)kb * BK, k_hi = min((int64_t)ke * BK, (int64_t)p.K);
   const int nI = min(BM, p.M - m0), nJ = min(BN, p.N - n0);
 
   if (t == 0) {
@@ -364,7 +374,7 @@ __global__ void __launch_bounds__(NT, 1)
     if (p.use_tma) {
       tma_prefetch_desc(&tmA);
       tma_prefetch_desc(&tmB);
-      for (int s = 0; s < STAGES && s < nk; ++s) issue_ktile<AK, BKM>(sm, &tmA, &tmB, s, m0, n0, s * BK);
+      for (int s = 0; s < STAGES && s < nl; ++s) issue_ktile<AK, BKM>(sm, &tmA, &tmB, s, m0, n0, (kb + s) * BK);
     }
   }
   __syncthreads();
@@ -377,11 +387,12 @@ __global__ void __launch_bounds__(NT, 1)
   double pred = 0.0;  // t < 128: alpha-free C^r(i = t) partial; t >= 128: C^c(j = t - 128)
   float pmag = 0.0f;  // upward-rounded magnitude sum for the threshold
 
-  int kt = 0;
-  for (; kt < nk; ++kt) {
-    const int s = kt % STAGES;
+  int kt = kb;
+  for (; kt < ke; ++kt) {
+    const int lt = kt - kb;  // position in this tile's k-range: stage and phase
+    const int s = lt % STAGES;
     if (p.use_tma) {
-      if (!mbar_wait_bounded(&sm.full[s], (kt / STAGES) & 1, kWaitLimitNs)) sm.timeout = 1;
+      if (!mbar_wait_bounded(&sm.full[s], (lt / STAGES) & 1, kWaitLimitNs)) sm.timeout = 1;
     } else {
       load_ktile_plain<AK, BKM>(p, sm.a[s], sm.b[s], m0, n0, kt * BK, t);
     }
@@ -462,9 +473,9 @@ __global__ void __launch_bounds__(NT, 1)
 
     E::template ktile<AK, BKM>(acc, sA, sB, t);
     __syncthreads();
-    if (p.use_tma && t == 0 && kt + STAGES < nk) issue_ktile<AK, BKM>(sm, &tmA, &tmB, s, m0, n0, (kt + STAGES) * BK);
-    if (FT && p.kc_tiles > 0 && (kt + 1) % p.kc_tiles == 0 && kt + 1 < nk)
-      online_check<E>(p, acc, pred, pmag, sm, t, m0, n0, nI, nJ, (int64_t)(kt + 1) * BK);
+    if (p.use_tma && t == 0 && lt + STAGES < nl) issue_ktile<AK, BKM>(sm, &tmA, &tmB, s, m0, n0, (kt + STAGES) * BK);
+    if (FT && p.kc_tiles > 0 && (kt + 1) % p.kc_tiles == 0 && kt + 1 < ke)
+      online_check<E>(p, acc, pred, pmag, sm, t, m0, n0, nI, nJ, k_lo, (int64_t)(kt + 1) * BK);
   }
 
   if (sm.timeout) {
@@ -472,8 +483,8 @@ __global__ void __launch_bounds__(NT, 1)
     // report. The output tile is not written.
     if (t == 0) {
       if (p.use_tma)
-        for (int k2 = kt; k2 < nk && k2 < kt + STAGES; ++k2)
-          (void)mbar_wait_bounded(&sm.full[k2 % STAGES], (k2 / STAGES) & 1, kWaitLimitNs);
+        for (int k2 = kt; k2 < ke && k2 < kt + STAGES; ++k2)
+          (void)mbar_wait_bounded(&sm.full[(k2 - kb) % STAGES], ((k2 - kb) / STAGES) & 1, kWaitLimitNs);
       if (p.report) atomicOr(&p.report->status, FT_STATUS_TIMEOUT);
     }
     return;
@@ -617,7 +628,7 @@ __global__ void __launch_bounds__(NT, 1)
       const int li = sm.first_row, lj = sm.first_col;
       const int64_t gi = m0 + li, gj = n0 + lj;
       double acc_fixed;
-      const bool mine = E::recompute(p, gi, gj, t, li, lj, acc_fixed, p.K);
+      const bool mine = E::recompute(p, gi, gj, t, li, lj, acc_fixed, k_lo, k_hi);
       if (mine) {
         const double cin = beta_nz ? p.C[gi + gj * p.ldc] : 0.0;
         const double fixed = beta_nz ? fma(p.alpha, acc_fixed, p.beta * cin) : p.alpha * acc_fixed;
@@ -661,6 +672,31 @@ __global__ void __launch_bounds__(NT, 1)
       const int li = E::row(t, r), lj = E::col(t, c);
       if (li < nI && lj < nJ) p.C[(int64_t)(m0 + li) + (int64_t)(n0 + lj) * p.ldc] = acc[r][c];
     }
+  }
+}
+
+// Full n x n copy T of a symmetric (mode 0) or triangular (mode 1) matrix stored in one
+// triangle of X (layout col/row-major, leading dimension ldx), written in the same layout
+// with leading dimension n.
+//   mode 0: T(r,c) = X(r,c) when (r,c) lies in the stored triangle, else X(c,r);
+//   mode 1: T = op(X) with the other triangle zero; unit_diag puts 1 on the diagonal.
+__global__ void expand_kernel(const double* X, int64_t ldx, int32_t row_major, int64_t n, int32_t mode,
+                              int32_t upper, int32_t trans, int32_t unit_diag, double* T) {
+  const int64_t total = n * n;
+  auto at = [&](int64_t r, int64_t c) { return row_major ? X[r * ldx + c] : X[r + c * ldx]; };
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    // e runs along the contiguous dimension of T
+    const int64_t r = row_major ? e / n : e % n, c = row_major ? e % n : e / n;
+    double v;
+    if (mode == 0) {
+      const bool stored = upper ? (r <= c) : (r >= c);
+      v = stored ? at(r, c) : at(c, r);
+    } else {
+      const int64_t p = trans ? c : r, q = trans ? r : c;  // op(X)(r,c) = X(p,q)
+      const bool in_tri = upper ? (p <= q) : (p >= q);
+      v = (r == c && unit_diag) ? 1.0 : (in_tri ? at(p, q) : 0.0);
+    }
+    T[row_major ? r * n + c : r + c * n] = v;
   }
 }
 
@@ -710,6 +746,16 @@ cudaError_t launch_scale(double* C, int64_t ldc, int32_t M, int32_t N, double be
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < 1) blocks = 1;
   scale_kernel<<<blocks, 256, 0, stream>>>(C, ldc, M, N, beta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand(const double* X, int64_t ldx, bool row_major, int64_t n, int mode, bool upper, bool trans,
+                          bool unit_diag, double* T, cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  int64_t blocks = (n * n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  expand_kernel<<<(unsigned)blocks, 256, 0, stream>>>(X, ldx, row_major ? 1 : 0, n, mode, upper ? 1 : 0,
+                                                      trans ? 1 : 0, unit_diag ? 1 : 0, T);
   return cudaGetLastError();
 }
 

@@ -44,6 +44,8 @@ struct DgemmParams {
   ft_report_t* report;           // may be null
   int32_t swap_report;           // 1: records in the transposed (caller row-major) frame
   int32_t kc_tiles;              // online verification every kc_tiles k-tiles (0: finished tile only)
+  int32_t tri_a, tri_b;          // op(A) / op(B) triangular in the kernel frame: 0 no, 1 upper, 2 lower
+                                 // (each tile then runs only the k-tiles the nonzero triangle reaches)
   InjectList inj;
 };
 
@@ -79,6 +81,11 @@ int unfused_dgemm(const UnfusedParams& p, cudaStream_t stream, cudaError_t* cuda
 // immediately before and after a product kernel launch; no-ops unless timing is on.
 void kernel_timer_start(cudaStream_t stream);
 void kernel_timer_stop(cudaStream_t stream);
+
+// Full copy of a symmetric (mode 0) or triangular (mode 1, op(X) with zeros and an optional
+// unit diagonal) n x n matrix stored in one triangle of X, in X's layout with ld = n.
+cudaError_t launch_expand(const double* X, int64_t ldx, bool row_major, int64_t n, int mode, bool upper, bool trans,
+                          bool unit_diag, double* T, cudaStream_t stream);
 
 // C = beta * C over an M x N column-major kernel-frame matrix (quick-return path).
 cudaError_t launch_scale(double* C, int64_t ldc, int32_t M, int32_t N, double beta, cudaStream_t stream);

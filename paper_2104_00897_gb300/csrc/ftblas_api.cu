@@ -199,9 +199,11 @@ Frame map_frame(int layout, int ta, int tb, int64_t M, int64_t N, const void* A,
 
 constexpr int64_t kMaxDim = (int64_t(1) << 31) - 256;
 
+// tri_a / tri_b: op(A) / op(B) triangular in the caller's frame (0 no, 1 upper, 2 lower):
+// the kernel then runs, per tile, only the k-tiles the nonzero triangle reaches.
 int dgemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
                int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* stream,
-               ft_report_t* report, bool ft) {
+               ft_report_t* report, bool ft, int tri_a = 0, int tri_b = 0) {
   const bool need_ab = (K > 0 && alpha != 0.0 && M > 0 && N > 0);
   int v = validate(layout, ta, tb, M, N, K, A, lda, B, ldb, C, ldc, need_ab);
   if (v != 0) return v;
@@ -231,6 +233,13 @@ int dgemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, doub
   p.report = ft ? report : nullptr;
   p.swap_report = f.swap;
   {
+    // row-major: the kernel frame computes C^T = op(B)^T op(A)^T, and a transpose swaps
+    // upper and lower
+    auto flip = [](int t) { return t == 1 ? 2 : (t == 2 ? 1 : 0); };
+    p.tri_a = f.swap ? flip(tri_b) : tri_a;
+    p.tri_b = f.swap ? flip(tri_a) : tri_b;
+  }
+  {
     const int64_t kc = g_kc_interval.load();
     p.kc_tiles = (ft && kc > 0) ? (int32_t)((kc + kDBK - 1) / kDBK) : 0;
   }
@@ -253,6 +262,94 @@ int dgemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, doub
   p.use_tma = ok ? 1 : 0;
   g_last_used_tma = p.use_tma;
   return record_cuda(launch_dgemm(p, &tmA, &tmB, ft, g_fp64_engine.load(), st));
+}
+
+// ------------------------------------------------------------------ FT-DSYMM, FT-DTRMM
+// Both run the protected FP64 GEMM on a full copy of the symmetric or triangular operand
+// (the analogue of the paper's symmetric / triangular packing before the Level-3 kernel).
+int dsymm_impl(int layout, int side, int uplo, int64_t M, int64_t N, double alpha, const double* A, int64_t lda,
+               const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* stream, ft_report_t* report) {
+  if (layout != FTBLAS_ROW_MAJOR && layout != FTBLAS_COL_MAJOR) return -1;
+  if (side != FTBLAS_LEFT && side != FTBLAS_RIGHT) return -2;
+  if (uplo != FTBLAS_UPPER && uplo != FTBLAS_LOWER) return -3;
+  if (M < 0) return -4;
+  if (N < 0) return -5;
+  const bool col = layout == FTBLAS_COL_MAJOR;
+  const int64_t dim = side == FTBLAS_LEFT ? M : N;
+  const bool need = M > 0 && N > 0 && alpha != 0.0;
+  if (need && A == nullptr) return -7;
+  if (lda < (dim > 1 ? dim : 1)) return -8;
+  if (need && B == nullptr) return -9;
+  const int64_t ld_mn = col ? M : N;
+  if (ldb < (ld_mn > 1 ? ld_mn : 1)) return -10;
+  if (M > 0 && N > 0 && C == nullptr) return -12;
+  if (ldc < (ld_mn > 1 ? ld_mn : 1)) return -13;
+  if (M > kMaxDim || N > kMaxDim) return FTBLAS_STATUS_NOT_SUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!need) {  // quick returns: an empty product (K = 0) gives C = beta C, or nothing
+    const int64_t l1 = ld_mn > 1 ? ld_mn : 1;
+    return dgemm_impl(layout, FTBLAS_NO_TRANS, FTBLAS_NO_TRANS, M, N, 0, 0.0, nullptr, l1, nullptr, l1, beta, C, ldc,
+                      stream, report, true);
+  }
+  double* S = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&S), (size_t)(dim * dim) * 8, st) != cudaSuccess)
+    return FTBLAS_STATUS_ALLOC_FAILED;
+  int rc = record_cuda(launch_expand(A, lda, !col, dim, 0, uplo == FTBLAS_UPPER, false, false, S, st));
+  if (rc == 0) {
+    rc = side == FTBLAS_LEFT
+             ? dgemm_impl(layout, FTBLAS_NO_TRANS, FTBLAS_NO_TRANS, M, N, M, alpha, S, dim, B, ldb, beta, C, ldc,
+                          stream, report, true)
+             : dgemm_impl(layout, FTBLAS_NO_TRANS, FTBLAS_NO_TRANS, M, N, N, alpha, B, ldb, S, dim, beta, C, ldc,
+                          stream, report, true);
+  }
+  cudaFreeAsync(S, st);
+  return rc;
+}
+
+int dtrmm_impl(int layout, int side, int uplo, int transa, int diag, int64_t M, int64_t N, double alpha,
+               const double* A, int64_t lda, double* B, int64_t ldb, void* stream, ft_report_t* report) {
+  if (layout != FTBLAS_ROW_MAJOR && layout != FTBLAS_COL_MAJOR) return -1;
+  if (side != FTBLAS_LEFT && side != FTBLAS_RIGHT) return -2;
+  if (uplo != FTBLAS_UPPER && uplo != FTBLAS_LOWER) return -3;
+  if (transa != FTBLAS_NO_TRANS && transa != FTBLAS_TRANS) return -4;
+  if (diag != FTBLAS_NON_UNIT && diag != FTBLAS_UNIT) return -5;
+  if (M < 0) return -6;
+  if (N < 0) return -7;
+  const bool col = layout == FTBLAS_COL_MAJOR;
+  const int64_t dim = side == FTBLAS_LEFT ? M : N;
+  const bool need = M > 0 && N > 0 && alpha != 0.0;
+  if (need && A == nullptr) return -9;
+  if (lda < (dim > 1 ? dim : 1)) return -10;
+  const int64_t ld_mn = col ? M : N;
+  if (M > 0 && N > 0 && B == nullptr) return -11;
+  if (ldb < (ld_mn > 1 ? ld_mn : 1)) return -12;
+  if (M > kMaxDim || N > kMaxDim) return FTBLAS_STATUS_NOT_SUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!need) {  // alpha = 0 gives B = 0 (B is not read), or an empty B
+    const int64_t l1 = ld_mn > 1 ? ld_mn : 1;
+    return dgemm_impl(layout, FTBLAS_NO_TRANS, FTBLAS_NO_TRANS, M, N, 0, 0.0, nullptr, l1, nullptr, l1, 0.0, B, ldb,
+                      stream, report, true);
+  }
+  // op(A) is upper when A is upper and not transposed, or lower and transposed
+  const bool op_upper = (uplo == FTBLAS_UPPER) == (transa == FTBLAS_NO_TRANS);
+  const int tri = op_upper ? 1 : 2;
+  const int64_t rows = col ? M : N, cols = col ? N : M;  // storage extent of B
+  double *T = nullptr, *B0 = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&T), (size_t)(dim * dim + rows * cols) * 8, st) != cudaSuccess)
+    return FTBLAS_STATUS_ALLOC_FAILED;
+  B0 = T + dim * dim;
+  int rc = record_cuda(launch_expand(A, lda, !col, dim, 1, uplo == FTBLAS_UPPER, transa == FTBLAS_TRANS,
+                                     diag == FTBLAS_UNIT, T, st));
+  if (rc == 0) rc = record_cuda(cudaMemcpy2DAsync(B0, rows * 8, B, ldb * 8, rows * 8, cols, cudaMemcpyDeviceToDevice, st));
+  if (rc == 0) {
+    rc = side == FTBLAS_LEFT
+             ? dgemm_impl(layout, FTBLAS_NO_TRANS, FTBLAS_NO_TRANS, M, N, M, alpha, T, dim, B0, rows, 0.0, B, ldb,
+                          stream, report, true, tri, 0)
+             : dgemm_impl(layout, FTBLAS_NO_TRANS, FTBLAS_NO_TRANS, M, N, N, alpha, B0, rows, T, dim, 0.0, B, ldb,
+                          stream, report, true, 0, tri);
+  }
+  cudaFreeAsync(T, st);
+  return rc;
 }
 
 // ------------------------------------------------------------------ unfused comparator
@@ -669,6 +766,18 @@ int ftblas_dgemm_unfused(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_t
                          int64_t K, double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
                          double beta, double* C, int64_t ldc, void* stream, ft_report_t* report) {
   return dgemm_unfused_impl(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, stream, report);
+}
+
+int ftblas_dsymm(ftblas_layout_t layout, ftblas_side_t side, ftblas_uplo_t uplo, int64_t M, int64_t N, double alpha,
+                 const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                 void* stream, ft_report_t* report) {
+  return dsymm_impl(layout, side, uplo, M, N, alpha, A, lda, B, ldb, beta, C, ldc, stream, report);
+}
+
+int ftblas_dtrmm(ftblas_layout_t layout, ftblas_side_t side, ftblas_uplo_t uplo, ftblas_trans_t transa,
+                 ftblas_diag_t diag, int64_t M, int64_t N, double alpha, const double* A, int64_t lda, double* B,
+                 int64_t ldb, void* stream, ft_report_t* report) {
+  return dtrmm_impl(layout, side, uplo, transa, diag, M, N, alpha, A, lda, B, ldb, stream, report);
 }
 
 int ftblas_kernel_timing_begin(void) {
