@@ -485,24 +485,33 @@ def run_sweep(dev, steps, warmup, shapes=SWEEP_SHAPES):
 
 
 def run_level3(dev, n, steps, warmup):
-    """FT-DSYMM and FT-DTRMM (side left, upper, column-major, n x n operands, U[-1,1]):
-    TFLOP/s by their own flop counts (DSYMM 2 n^3, DTRMM n^3) over the whole call (copy of
-    the symmetric / triangular operand included), one accumulator flip in the timed calls
-    (inside the faulted tile's k-range for DTRMM)."""
+    """FT-DSYMM, FT-DTRMM and FT-DTRSM (side left, upper, column-major, n x n operands,
+    U[-1,1]; DTRSM on a diagonally dominant A): TFLOP/s by their own flop counts (DSYMM
+    2 n^3, DTRMM and DTRSM n^3) over the whole call (copies of the symmetric / triangular
+    operand and of B included), one accumulator flip in the timed DSYMM / DTRMM calls
+    (inside the faulted tile's k-range for DTRMM), one flip in every internal step of the
+    timed DTRSM calls."""
     import torch
 
     import paper_2104_00897_gb300 as fb
     import synth as S
 
     A = torch.from_numpy(S.uniform(SEED + 9, 0, n * n)).to(dev)
+    Ad = A.clone().view(n, n)  # column-major storage: Ad[c, r] holds A(r, c)
+    Ad.mul_(1.0 / (2 * n))
+    Ad.diagonal().add_(1.0)
     B = torch.from_numpy(S.uniform(SEED + 9, 1, n * n)).to(dev)
     C = torch.from_numpy(S.uniform(SEED + 9, 2, n * n)).to(dev)
     st = torch.cuda.current_stream(dev).cuda_stream
     nk = -(-n // 32)
     out = {}
-    for name, flops in (("dsymm", 2.0 * n ** 3), ("dtrmm", 1.0 * n ** 3)):
+    for name, flops in (("dsymm", 2.0 * n ** 3), ("dtrmm", 1.0 * n ** 3), ("dtrsm", 1.0 * n ** 3)):
         def call(rep):
-            if name == "dsymm":
+            if name == "dtrsm":
+                fb.check(fb.ftblas_dtrsm(fb.COL_MAJOR, fb.LEFT, fb.UPPER, fb.NO_TRANS, fb.NON_UNIT, n, n, 1.0,
+                                         Ad.data_ptr(), n, B.data_ptr(), n, st,
+                                         rep.data_ptr() if rep is not None else None))
+            elif name == "dsymm":
                 fb.check(fb.ftblas_dsymm(fb.COL_MAJOR, fb.LEFT, fb.UPPER, n, n, 1.0, A.data_ptr(), n, B.data_ptr(), n,
                                          0.5, C.data_ptr(), n, st, rep.data_ptr() if rep is not None else None))
             else:
@@ -513,6 +522,8 @@ def run_level3(dev, n, steps, warmup):
             call(None)
         torch.cuda.synchronize(dev)
         pts = [dict(i=n // 2 + 5, j=7, site=fb.SITE_ACCUM, mode=fb.MODE_BITFLIP, bit=57, kt=(3 * nk) // 4)]
+        if name == "dtrsm":  # applies to every internal step, in its own coordinates
+            pts = [dict(i=5, j=7, site=fb.SITE_OUTPUT, mode=fb.MODE_BITFLIP, bit=57)]
         fb.ftblas_set_injection(fb.make_injection(fixed=pts))
         reps = [fb.new_report(dev) for _ in range(steps)]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -524,9 +535,11 @@ def run_level3(dev, n, steps, warmup):
         fb.ftblas_set_injection(None)
         ms = e0.elapsed_time(e1) / steps
         rr = [fb.report_from_device(r) for r in reps]
-        out[name] = {"tflops": flops / ms / 1e9, "ms": ms, "injected": steps,
+        out[name] = {"tflops": flops / ms / 1e9, "ms": ms,
+                     "injected": steps * ((2 * -(-n // 128) - 1) if name == "dtrsm" else 1),
                      "corrected": sum(int(r.corrected) for r in rr), "detected": sum(int(r.detected) for r in rr)}
-    out["workload"] = f"FT-DSYMM / FT-DTRMM {n}x{n}, side left, upper, column-major, U[-1,1]"
+    out["workload"] = (f"FT-DSYMM / FT-DTRMM / FT-DTRSM {n}x{n}, side left, upper, column-major, U[-1,1] "
+                       "(DTRSM: A scaled by 1/(2n) plus the identity)")
     return out
 
 

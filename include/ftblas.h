@@ -184,6 +184,21 @@ int ftblas_dtrmm(ftblas_layout_t layout, ftblas_side_t side, ftblas_uplo_t uplo,
                  ftblas_diag_t diag, int64_t M, int64_t N, double alpha, const double* A, int64_t lda,
                  double* B, int64_t ldb, void* stream, ft_report_t* report);
 
+/* FT-DTRSM: op(A) X = alpha B (side LEFT, A M x M) or X op(A) = alpha B (side RIGHT, A N x N),
+ * A triangular (`uplo`, `diag`), X overwriting B. Recursive blocked substitution on a
+ * column-major copy (workspace from the stream-ordered allocator): the off-diagonal updates
+ * run through ftblas_dgemm's protected kernel, and each 128-row diagonal block is solved by
+ * a kernel that verifies every right-hand side by its checksum, e^T (T X) = (e^T T) X
+ * against e^T R (Section II.A applied to T X = R), and solves a mismatching column again
+ * from its untouched right-hand side (bit-exact). `report` sums all internal steps; records
+ * carry B's (i, j) and, for the diagonal solves, the first row where the solved-again
+ * column differed. The injection plan applies to every internal step, in that step's own
+ * coordinates (a diagonal solve flips bit `bit` of X(i, j) as it is formed). A singular
+ * diagonal is not detected (as in BLAS). Arguments 1-14 in CBLAS order. */
+int ftblas_dtrsm(ftblas_layout_t layout, ftblas_side_t side, ftblas_uplo_t uplo, ftblas_trans_t transa,
+                 ftblas_diag_t diag, int64_t M, int64_t N, double alpha, const double* A, int64_t lda,
+                 double* B, int64_t ldb, void* stream, ft_report_t* report);
+
 /* The unfused comparator (no counterpart in the fused design; it reproduces the
  * arrangement Section V improves on: ABFT as separate passes around a BLAS library call).
  * Same arguments, checks, report and injection plan as ftblas_dgemm, and the same

@@ -110,6 +110,8 @@ def lib():
                                              C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                              C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_void_p]
         L.oracle_draw_injections.restype = C.c_int64
+        L.oracle_trsm_left.argtypes = [C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64]
+        L.oracle_trsm_left.restype = None
         L.oracle_num_threads.argtypes = []
         L.oracle_num_threads.restype = C.c_int
         _lib = L
@@ -150,6 +152,17 @@ def gemm(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc,
     if rc != 0:
         raise ValueError("oracle_gemm: bad arguments")
     return out
+
+
+def trsm_left(T, W, lower):
+    """Solve T X = W (T n x n, W n x nrhs, logical matrices) by plain substitution, reading
+    only T's lower or upper triangle. Returns X (n x nrhs)."""
+    n = T.shape[0]
+    nrhs = W.shape[1]
+    t = np.asfortranarray(np.asarray(T, dtype=np.float64))
+    w = np.array(W, dtype=np.float64, order="F", copy=True)
+    lib().oracle_trsm_left(n, nrhs, t.ctypes.data, max(1, n), 1 if lower else 0, w.ctypes.data, max(1, n))
+    return w
 
 
 def gemm_rows(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc, rows):

@@ -198,6 +198,28 @@ static double scale_out(const oracle_problem_t* p, double acc, int64_t i, int64_
   return t;
 }
 
+/* Triangular solve T X = W in place, T n x n column-major (leading dimension ldt), only
+ * its lower (lower != 0) or upper triangle read, W n x nrhs column-major (ldw): the
+ * textbook substitution for each column, x_r = (w_r - sum_c T(r,c) x_c) / T(r,r) with the
+ * sum over the already solved rows in ascending c (forward for lower, backward for upper),
+ * separate multiply and add. */
+void oracle_trsm_left(int64_t n, int64_t nrhs, const double* T, int64_t ldt, int lower, double* W, int64_t ldw) {
+#pragma omp parallel for schedule(static)
+  for (int64_t j = 0; j < nrhs; ++j) {
+    double* w = W + j * ldw;
+    for (int64_t q = 0; q < n; ++q) {
+      const int64_t r = lower ? q : n - 1 - q;
+      double s = 0.0;
+      if (lower) {
+        for (int64_t c = 0; c < r; ++c) s = s + T[r + c * ldt] * w[c];
+      } else {
+        for (int64_t c = r + 1; c < n; ++c) s = s + T[r + c * ldt] * w[c];
+      }
+      w[r] = (w[r] - s) / T[r + r * ldt];
+    }
+  }
+}
+
 /* Plain product C = alpha*op(A)*op(B) + beta*C_in into Cout (same layout and ldc as Cin).
  * Returns 0, or -1 for bad arguments. */
 int oracle_gemm(const oracle_problem_t* p, double* Cout) {

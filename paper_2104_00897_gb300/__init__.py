@@ -94,6 +94,8 @@ SIGNATURES = {
                                C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "ftblas_dtrmm": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_double,
                                C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "ftblas_dtrsm": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_double,
+                               C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "ftblas_verification_tile": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64,
                                            C.c_void_p, C.c_void_p, C.c_void_p]),
     "ftblas_set_fp64_engine": (C.c_int, [C.c_int]),
@@ -153,6 +155,10 @@ def ftblas_dsymm(layout, side, uplo, M, N, alpha, A, lda, B, ldb, beta, C_, ldc,
 
 def ftblas_dtrmm(layout, side, uplo, transa, diag, M, N, alpha, A, lda, B, ldb, stream, report):
     return _call("ftblas_dtrmm", layout, side, uplo, transa, diag, M, N, alpha, A, lda, B, ldb, stream, report)
+
+
+def ftblas_dtrsm(layout, side, uplo, transa, diag, M, N, alpha, A, lda, B, ldb, stream, report):
+    return _call("ftblas_dtrsm", layout, side, uplo, transa, diag, M, N, alpha, A, lda, B, ldb, stream, report)
 
 
 def ftblas_dgemm_host(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream, report):

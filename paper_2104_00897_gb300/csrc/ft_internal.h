@@ -87,6 +87,19 @@ void kernel_timer_stop(cudaStream_t stream);
 cudaError_t launch_expand(const double* X, int64_t ldx, bool row_major, int64_t n, int mode, bool upper, bool trans,
                           bool unit_diag, double* T, cudaStream_t stream);
 
+// FT-DTRSM blocks (ft_trsm.cu).
+constexpr int kTrsmLeaf = 128;  // diagonal block edge of the blocked substitution
+// dst(r, c) = scale * src[r * rs + c * cs] into a column-major dst (leading dimension ld)
+cudaError_t launch_copy2d(const double* src, int64_t rs, int64_t cs, double* dst, int64_t ld, int64_t rows,
+                          int64_t cols, double scale, cudaStream_t stream);
+// Solve the n x n (n <= kTrsmLeaf) lower / upper triangular block T X = W in place for
+// nrhs columns of W, each column verified by its checksum and solved again on a mismatch.
+cudaError_t launch_trsm_leaf(const double* T, int64_t ldt, double* W, int64_t ldw, int n, int64_t nrhs, bool lower,
+                             ft_report_t* report, const InjectList& inj, cudaStream_t stream);
+// Sum nparts step reports into out (records moved by row_off[p] rows, then transposed when swap).
+cudaError_t launch_report_merge(const ft_report_t* parts, const int64_t* row_off, int nparts, ft_report_t* out,
+                                bool swap, cudaStream_t stream);
+
 // C = beta * C over an M x N column-major kernel-frame matrix (quick-return path).
 cudaError_t launch_scale(double* C, int64_t ldc, int32_t M, int32_t N, double beta, cudaStream_t stream);
 

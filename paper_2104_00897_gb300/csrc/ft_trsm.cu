@@ -1,0 +1,215 @@
+// FT-DTRSM building blocks (the paper's Level-3 family beside GEMM): the strided copy that
+// brings B into the column-major solve frame, the protected diagonal-block solve, and the
+// merge of the per-step reports. The blocked substitution itself (host side) runs its
+// trailing updates through the protected FP64 GEMM.
+//
+// Diagonal-block solve with a checksum (Section II.A applied to T X = R): for an n x n
+// triangular block T and right-hand sides R, e^T (T X) = (e^T T) X must equal e^T R for
+// every column. Columns are independent, so a column whose checksum mismatches is solved
+// again from the untouched R (same instruction sequence: the fault-free result bit for
+// bit); several faulty columns are all corrected.
+#include <climits>
+
+#include "ft_device.cuh"
+#include "ft_internal.h"
+
+namespace ftk {
+
+namespace {
+
+constexpr int kLeaf = kTrsmLeaf;  // diagonal block edge (<= 128)
+constexpr int kCols = 32;         // right-hand sides per CTA (one thread each)
+
+// dst(r, c) = scale * src[r * rs + c * cs], dst column-major with leading dimension ld.
+// 32 x 32 tiles; when the source is contiguous along c the tile goes through shared memory
+// so that both the loads and the stores are coalesced.
+__global__ void copy2d_kernel(const double* src, int64_t rs, int64_t cs, double* dst, int64_t ld, int64_t rows,
+                              int64_t cols, double scale) {
+  __shared__ double tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  if (rs == 1 || cs != 1) {
+    for (int q = ty; q < 32; q += 8) {
+      const int64_t r = r0 + tx, c = c0 + q;
+      if (r < rows && c < cols) dst[r + c * ld] = scale * src[r * rs + c * cs];
+    }
+    return;
+  }
+  for (int q = ty; q < 32; q += 8) {
+    const int64_t r = r0 + q, c = c0 + tx;
+    tile[q][tx] = (r < rows && c < cols) ? src[r * rs + c] : 0.0;
+  }
+  __syncthreads();
+  for (int q = ty; q < 32; q += 8) {
+    const int64_t r = r0 + tx, c = c0 + q;
+    if (r < rows && c < cols) dst[r + c * ld] = scale * tile[tx][q];
+  }
+}
+
+__device__ __forceinline__ double gamma_up64(int64_t n) {
+  const double nu = __dmul_ru((double)n, 0x1p-53);
+  return __ddiv_ru(nu, __dsub_rd(1.0, nu));
+}
+
+struct LeafSmem {
+  double T[kLeaf][kLeaf + 1];       // the block, [row][column]
+  double w[kLeaf][kCols];           // w[row][thread]: the thread's column (right-hand side, then solution)
+  double wf[kLeaf][kCols];          // a faulty solution kept while the column is solved again
+  double tsum[kLeaf], tabs[kLeaf];  // column sums of T and of |T|
+};
+
+// Substitution for the column held in sm.w[.][t]: lower (forward) or upper (backward),
+// x_r = w_r / T(r,r) then w_s -= T(s,r) x_r for the rows still to come. An injection point
+// at row inj_r flips bit inj_bit of x_r right after it is formed (test launches only).
+__device__ void solve_column(LeafSmem& sm, int t, int n, bool lower, int inj_r, int inj_bit) {
+  for (int q = 0; q < n; ++q) {
+    const int r = lower ? q : n - 1 - q;
+    double x = sm.w[r][t] / sm.T[r][r];
+    if (r == inj_r) x = __longlong_as_double(__double_as_longlong(x) ^ (1ll << inj_bit));
+    sm.w[r][t] = x;
+    if (lower) {
+      for (int s2 = r + 1; s2 < n; ++s2) sm.w[s2][t] = fma(-sm.T[s2][r], x, sm.w[s2][t]);
+    } else {
+      for (int s2 = 0; s2 < r; ++s2) sm.w[s2][t] = fma(-sm.T[s2][r], x, sm.w[s2][t]);
+    }
+  }
+}
+
+// One CTA: kCols right-hand sides of the n x n diagonal block at T (column-major, ld ldt);
+// W (column-major, ld ldw) is overwritten with the solution. rep: this step's report.
+__global__ void __launch_bounds__(kCols) trsm_leaf_kernel(const double* T, int64_t ldt, double* W, int64_t ldw, int n,
+                                                          int64_t nrhs, int lower, ft_report_t* rep, InjectList inj) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LeafSmem& sm = *reinterpret_cast<LeafSmem*>(smem_raw);
+  const int t = threadIdx.x;
+  const int64_t j = (int64_t)blockIdx.x * kCols + t;
+  const bool jok = j < nrhs;
+  for (int e = t; e < n * n; e += kCols) {
+    const int r = e % n, c = e / n;
+    const bool in_tri = lower ? (r >= c) : (r <= c);
+    sm.T[r][c] = in_tri ? T[r + (int64_t)c * ldt] : 0.0;
+  }
+  __syncthreads();
+  for (int c = t; c < n; c += kCols) {
+    double s = 0.0, a = 0.0;
+    for (int r = 0; r < n; ++r) { s += sm.T[r][c]; a = __dadd_ru(a, fabs(sm.T[r][c])); }
+    sm.tsum[c] = s;
+    sm.tabs[c] = a;
+  }
+  double rsum = 0.0, rabs = 0.0;  // the right-hand side's sums
+  for (int r = 0; r < n; ++r) {
+    const double v = jok ? W[r + j * ldw] : 0.0;
+    sm.w[r][t] = v;
+    rsum += v;
+    rabs = __dadd_ru(rabs, fabs(v));
+  }
+  __syncthreads();
+  int inj_r = -1, inj_bit = 0;
+  for (int e = 0; e < inj.n; ++e)
+    if (inj.p[e].j == j && inj.p[e].i >= 0 && inj.p[e].i < n && inj.p[e].mode == FT_MODE_BITFLIP) {
+      inj_r = inj.p[e].i;
+      inj_bit = inj.p[e].bit;
+    }
+  if (jok) solve_column(sm, t, n, lower != 0, inj_r, inj_bit);
+  // e^T T x against e^T r: tau = 2 gamma_{2n+2} (sum_s (e^T|T|)_s |x_s| + sum |r|), a bound on
+  // the substitution's residual (componentwise backward error gamma_n |T| |x|) plus the
+  // rounding of both sums.
+  double chk = 0.0, mag = 0.0;
+  for (int s2 = 0; s2 < n; ++s2) {
+    const double x = sm.w[s2][t];
+    chk = fma(sm.tsum[s2], x, chk);
+    mag = __fma_ru(sm.tabs[s2], fabs(x), mag);
+  }
+  const double delta = chk - rsum;
+  const double tau = __dmul_ru(2.0, __dmul_ru(gamma_up64(2 * (int64_t)n + 2), __dadd_ru(mag, rabs)));
+  const bool flagged = jok && (!(fabs(delta) <= tau) || isinf(delta));
+  if (rep && t == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&rep->tiles_checked), 1ull);
+  if (flagged) {
+    // keep the faulty solution, solve again from the untouched right-hand side in W
+    for (int r = 0; r < n; ++r) { sm.wf[r][t] = sm.w[r][t]; sm.w[r][t] = W[r + j * ldw]; }
+    solve_column(sm, t, n, lower != 0, -1, 0);
+    int first = -1;  // where the fault entered: the first row, in solve order, that differs
+    for (int q = 0; q < n && first < 0; ++q) {
+      const int r = lower ? q : n - 1 - q;
+      if (__double_as_longlong(sm.wf[r][t]) != __double_as_longlong(sm.w[r][t])) first = r;
+    }
+    if (rep) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(&rep->detected), 1ull);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&rep->corrected), 1ull);
+      const unsigned slot = atomicAdd(&rep->n_records, 1u);
+      if (slot < FTBLAS_MAX_RECORDS) {
+        ft_error_record_t& rc = rep->rec[slot];
+        rc.tile_row = 0; rc.tile_col = blockIdx.x;
+        rc.i = first; rc.j = j;
+        rc.delta_row = 0.0; rc.delta_col = delta; rc.tau_row = 0.0; rc.tau_col = tau;
+        rc.value_before = first >= 0 ? sm.wf[first][t] : 0.0;
+        rc.value_after = first >= 0 ? sm.w[first][t] : 0.0;
+        rc.rows_flagged = 0; rc.cols_flagged = 1;
+        rc.kind = FT_KIND_CORRECTED;
+        rc.reserved = 0;
+      } else {
+        atomicOr(&rep->status, FT_STATUS_RECORDS_TRUNCATED);
+      }
+    }
+  }
+  if (jok)
+    for (int r = 0; r < n; ++r) W[r + j * ldw] = sm.w[r][t];
+}
+
+// Sum the step reports into `out` (zeroed by the caller): counters added, status ORed,
+// records concatenated in step order with coordinates moved from each step's frame
+// (rows + row_off[p]) to the caller's (swapped when `swap`).
+__global__ void report_merge_kernel(const ft_report_t* parts, const int64_t* row_off, int nparts, ft_report_t* out,
+                                    int swap) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  unsigned n = 0;
+  for (int q = 0; q < nparts; ++q) {
+    const ft_report_t& r = parts[q];
+    out->tiles_checked += r.tiles_checked;
+    out->detected += r.detected;
+    out->corrected += r.corrected;
+    out->uncorrectable += r.uncorrectable;
+    out->checksum_only += r.checksum_only;
+    out->input_nonfinite += r.input_nonfinite;
+    out->status |= r.status;
+    const unsigned m = r.n_records < FTBLAS_MAX_RECORDS ? r.n_records : FTBLAS_MAX_RECORDS;
+    for (unsigned k = 0; k < m; ++k) {
+      if (n >= FTBLAS_MAX_RECORDS) { out->status |= FT_STATUS_RECORDS_TRUNCATED; break; }
+      ft_error_record_t rc = r.rec[k];
+      const int64_t i = rc.i >= 0 ? rc.i + row_off[q] : -1, j = rc.j;
+      rc.i = swap ? j : i;
+      rc.j = swap ? i : j;
+      out->rec[n++] = rc;
+    }
+  }
+  out->n_records = n;
+}
+
+}  // namespace
+
+cudaError_t launch_copy2d(const double* src, int64_t rs, int64_t cs, double* dst, int64_t ld, int64_t rows,
+                          int64_t cols, double scale, cudaStream_t st) {
+  if (rows == 0 || cols == 0) return cudaSuccess;
+  dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
+  copy2d_kernel<<<grid, dim3(32, 8), 0, st>>>(src, rs, cs, dst, ld, rows, cols, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trsm_leaf(const double* T, int64_t ldt, double* W, int64_t ldw, int n, int64_t nrhs, bool lower,
+                             ft_report_t* rep, const InjectList& inj, cudaStream_t st) {
+  if (n == 0 || nrhs == 0) return cudaSuccess;
+  const size_t smem = sizeof(LeafSmem);
+  cudaError_t e = cudaFuncSetAttribute(trsm_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  trsm_leaf_kernel<<<(unsigned)((nrhs + kCols - 1) / kCols), kCols, smem, st>>>(T, ldt, W, ldw, n, nrhs,
+                                                                                   lower ? 1 : 0, rep, inj);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_report_merge(const ft_report_t* parts, const int64_t* row_off, int nparts, ft_report_t* out,
+                                bool swap, cudaStream_t st) {
+  report_merge_kernel<<<1, 32, 0, st>>>(parts, row_off, nparts, out, swap ? 1 : 0);
+  return cudaGetLastError();
+}
+
+}  // namespace ftk

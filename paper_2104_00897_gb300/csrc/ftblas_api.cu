@@ -352,6 +352,126 @@ int dtrmm_impl(int layout, int side, int uplo, int transa, int diag, int64_t M, 
   return rc;
 }
 
+// FT-DTRSM: op(A) X = alpha B (left) or X op(A) = alpha B (right), X overwriting B. The
+// system is brought to the column-major left form T W = alpha W0 (T = op(A), or op(A)^T for
+// the right side; W0 = B or B^T) and solved by recursive blocked substitution: split T into
+// halves, solve one, update the other right-hand sides with the protected GEMM
+// (W2 -= T21 X1), solve the other; diagonal blocks of kTrsmLeaf rows are solved by the
+// checksum-verified leaf kernel. Every internal step writes its own report; they are merged.
+struct TrsmCtx {
+  const double* T;
+  double* W;
+  int64_t dim, nrhs;
+  bool lower;
+  cudaStream_t st;
+  ft_report_t* parts;
+  std::vector<int64_t> row_off;
+  int rc;
+};
+
+void trsm_rec(TrsmCtx& c, int64_t i0, int64_t n) {
+  if (c.rc != 0 || n == 0) return;
+  if (n <= kTrsmLeaf) {
+    const size_t p = c.row_off.size();
+    c.row_off.push_back(i0);
+    CallerPoint pts[kMaxInject];
+    const int npts = plan_injections(n, c.nrhs, kTrsmLeaf, 32, pts);
+    InjectList inj;
+    std::memset(&inj, 0, sizeof(inj));
+    for (int q = 0; q < npts; ++q) {
+      InjectPoint& ip = inj.p[inj.n++];
+      ip.i = (int32_t)pts[q].i; ip.j = (int32_t)pts[q].j; ip.site = pts[q].site; ip.mode = pts[q].mode;
+      ip.bit = pts[q].bit; ip.rel_log2 = pts[q].rel_log2; ip.sign = pts[q].sign; ip.kt = 0;
+    }
+    c.rc = record_cuda(cudaMemsetAsync(c.parts + p, 0, sizeof(ft_report_t), c.st));
+    if (c.rc == 0)
+      c.rc = record_cuda(launch_trsm_leaf(c.T + i0 + i0 * c.dim, c.dim, c.W + i0, c.dim, (int)n, c.nrhs, c.lower,
+                                          c.parts + p, inj, c.st));
+    return;
+  }
+  const int64_t n1 = ((n / 2 + kTrsmLeaf - 1) / kTrsmLeaf) * kTrsmLeaf, n2 = n - n1;
+  auto update = [&](int64_t r_dst, int64_t m, int64_t r_src, int64_t k) {
+    // W[r_dst : r_dst + m) -= T[r_dst : r_dst + m, r_src : r_src + k) W[r_src : r_src + k)
+    const size_t p = c.row_off.size();
+    c.row_off.push_back(r_dst);
+    if (c.rc == 0)
+      c.rc = dgemm_impl(FTBLAS_COL_MAJOR, FTBLAS_NO_TRANS, FTBLAS_NO_TRANS, m, c.nrhs, k, -1.0,
+                        c.T + r_dst + r_src * c.dim, c.dim, c.W + r_src, c.dim, 1.0, c.W + r_dst, c.dim, c.st,
+                        c.parts + p, true);
+  };
+  if (c.lower) {
+    trsm_rec(c, i0, n1);
+    update(i0 + n1, n2, i0, n1);
+    trsm_rec(c, i0 + n1, n2);
+  } else {
+    trsm_rec(c, i0 + n1, n2);
+    update(i0, n1, i0 + n1, n2);
+    trsm_rec(c, i0, n1);
+  }
+}
+
+int dtrsm_impl(int layout, int side, int uplo, int transa, int diag, int64_t M, int64_t N, double alpha,
+               const double* A, int64_t lda, double* B, int64_t ldb, void* stream, ft_report_t* report) {
+  if (layout != FTBLAS_ROW_MAJOR && layout != FTBLAS_COL_MAJOR) return -1;
+  if (side != FTBLAS_LEFT && side != FTBLAS_RIGHT) return -2;
+  if (uplo != FTBLAS_UPPER && uplo != FTBLAS_LOWER) return -3;
+  if (transa != FTBLAS_NO_TRANS && transa != FTBLAS_TRANS) return -4;
+  if (diag != FTBLAS_NON_UNIT && diag != FTBLAS_UNIT) return -5;
+  if (M < 0) return -6;
+  if (N < 0) return -7;
+  const bool col = layout == FTBLAS_COL_MAJOR;
+  const int64_t dim = side == FTBLAS_LEFT ? M : N, nrhs = side == FTBLAS_LEFT ? N : M;
+  const bool need = M > 0 && N > 0 && alpha != 0.0;
+  if (need && A == nullptr) return -9;
+  if (lda < (dim > 1 ? dim : 1)) return -10;
+  const int64_t ld_mn = col ? M : N;
+  if (M > 0 && N > 0 && B == nullptr) return -11;
+  if (ldb < (ld_mn > 1 ? ld_mn : 1)) return -12;
+  if (M > kMaxDim || N > kMaxDim) return FTBLAS_STATUS_NOT_SUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!need) {  // alpha = 0 gives X = 0 (B is not read), or an empty B
+    const int64_t l1 = ld_mn > 1 ? ld_mn : 1;
+    return dgemm_impl(layout, FTBLAS_NO_TRANS, FTBLAS_NO_TRANS, M, N, 0, 0.0, nullptr, l1, nullptr, l1, 0.0, B, ldb,
+                      stream, report, true);
+  }
+  // T = op(A) (left) or op(A)^T (right), written column-major: the expansion writes in the
+  // caller's layout, and a row-major copy of X is the column-major copy of X^T.
+  const bool trans_solve = (side == FTBLAS_LEFT) == (transa == FTBLAS_TRANS);
+  const bool trans_expand = trans_solve != !col;
+  const bool upper = (uplo == FTBLAS_UPPER) == !trans_solve;
+  // B's storage read column-major is D (M x N when column-major, else N x M); W = B
+  // (left) or B^T (right) is D itself or D^T.
+  const bool w_is_d = (side == FTBLAS_LEFT) == col;
+  const int64_t d_rows = col ? M : N, d_cols = col ? N : M;
+  const int nparts = (int)(2 * ((dim + kTrsmLeaf - 1) / kTrsmLeaf) + 1);
+  double* T = nullptr;
+  const size_t bytes = (size_t)(dim * dim + dim * nrhs) * 8 + (size_t)nparts * (sizeof(ft_report_t) + 8) + 256;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&T), bytes, st) != cudaSuccess) return FTBLAS_STATUS_ALLOC_FAILED;
+  double* W = T + dim * dim;
+  char* tail = reinterpret_cast<char*>(W + dim * nrhs);
+  tail += (256 - reinterpret_cast<uintptr_t>(tail) % 256) % 256;
+  ft_report_t* parts = reinterpret_cast<ft_report_t*>(tail);
+  int64_t* row_off_dev = reinterpret_cast<int64_t*>(parts + nparts);
+  int rc = record_cuda(launch_expand(A, lda, !col, dim, 1, uplo == FTBLAS_UPPER, trans_expand, diag == FTBLAS_UNIT, T,
+                                     st));
+  if (rc == 0)
+    rc = record_cuda(launch_copy2d(B, w_is_d ? 1 : ldb, w_is_d ? ldb : 1, W, dim, dim, nrhs, alpha, st));
+  TrsmCtx c{T, W, dim, nrhs, !upper, st, parts, {}, rc};
+  trsm_rec(c, 0, dim);
+  rc = c.rc;
+  if (rc == 0)
+    rc = record_cuda(launch_copy2d(W, w_is_d ? 1 : dim, w_is_d ? dim : 1, B, ldb, d_rows, d_cols, 1.0, st));
+  if (rc == 0 && report != nullptr) {
+    rc = record_cuda(cudaMemsetAsync(report, 0, sizeof(ft_report_t), st));
+    if (rc == 0)
+      rc = record_cuda(cudaMemcpyAsync(row_off_dev, c.row_off.data(), c.row_off.size() * 8, cudaMemcpyHostToDevice, st));
+    if (rc == 0)
+      rc = record_cuda(launch_report_merge(parts, row_off_dev, (int)c.row_off.size(), report, side == FTBLAS_RIGHT, st));
+  }
+  cudaFreeAsync(T, st);
+  return rc;
+}
+
 // ------------------------------------------------------------------ unfused comparator
 int dgemm_unfused_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
                        int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* stream,
@@ -778,6 +898,12 @@ int ftblas_dtrmm(ftblas_layout_t layout, ftblas_side_t side, ftblas_uplo_t uplo,
                  ftblas_diag_t diag, int64_t M, int64_t N, double alpha, const double* A, int64_t lda, double* B,
                  int64_t ldb, void* stream, ft_report_t* report) {
   return dtrmm_impl(layout, side, uplo, transa, diag, M, N, alpha, A, lda, B, ldb, stream, report);
+}
+
+int ftblas_dtrsm(ftblas_layout_t layout, ftblas_side_t side, ftblas_uplo_t uplo, ftblas_trans_t transa,
+                 ftblas_diag_t diag, int64_t M, int64_t N, double alpha, const double* A, int64_t lda, double* B,
+                 int64_t ldb, void* stream, ft_report_t* report) {
+  return dtrsm_impl(layout, side, uplo, transa, diag, M, N, alpha, A, lda, B, ldb, stream, report);
 }
 
 int ftblas_kernel_timing_begin(void) {

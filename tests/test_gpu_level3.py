@@ -154,3 +154,76 @@ def test_dtrmm_faults_located_like_the_oracle(layout):
         assert report_summary(r) == report_summary(orep), pts
         assert record_set(r) == record_set(orep), pts
         assert r.corrected == 1, pts
+
+
+def trsm_system(layout, side, uplo, transa, diag, M, N, seed):
+    """A well-conditioned triangular A (stored triangle only, NaN elsewhere and on a unit
+    diagonal), B, and the left-form system T X = alpha W0 the definition gives."""
+    dim = M if side == fb.LEFT else N
+    R = S.uniform_matrix(seed, 0, dim, dim)
+    upper = uplo == fb.UPPER
+    r, c = np.indices((dim, dim))
+    # off-diagonal entries below 1 / (2 dim): diagonally dominant, so well conditioned
+    tri = np.where((r <= c) if upper else (r >= c), R / (2 * dim), 0.0)
+    tri[np.arange(dim), np.arange(dim)] = 1.0 if diag == fb.UNIT else 1.0 + S.uniform(seed, 3, dim) ** 2
+    opA = tri.T if transa == fb.TRANS else tri
+    B = S.uniform_matrix(seed, 1, M, N)
+    stored = stored_triangle(np.where((r <= c) if upper else (r >= c), tri, np.nan), upper,
+                             nan_diag=diag == fb.UNIT)
+    return dim, opA, B, stored
+
+
+def run_trsm(layout, side, uplo, transa, diag, M, N, alpha, stored, B, inj=None):
+    dim = M if side == fb.LEFT else N
+    a, lda = S.store(stored, layout, ld=dim + 1)
+    b, ldb = S.store(B, layout, ld=(M if layout == O.COL_MAJOR else N) + 3)
+    dA, dB = dev(a), dev(b)
+    fb.ftblas_set_injection(fb.make_injection(fixed=inj) if inj else None)
+    rep = fb.new_report()
+    fb.check(fb.ftblas_dtrsm(layout, side, uplo, transa, diag, M, N, alpha, dA.data_ptr(), lda, dB.data_ptr(), ldb,
+                             torch.cuda.current_stream().cuda_stream, rep.data_ptr()))
+    torch.cuda.synchronize()
+    fb.ftblas_set_injection(None)
+    return S.load(dB.cpu().numpy(), layout, M, N, ldb), fb.report_from_device(rep)
+
+
+@pytest.mark.parametrize("layout,side,uplo,transa,diag", list(itertools.product(
+    (O.COL_MAJOR, O.ROW_MAJOR), (fb.LEFT, fb.RIGHT), (fb.UPPER, fb.LOWER), (fb.NO_TRANS, fb.TRANS),
+    (fb.NON_UNIT, fb.UNIT))))
+def test_dtrsm_matches_oracle(layout, side, uplo, transa, diag):
+    """X against the oracle's substitution on the same system (left form: T = op(A) or
+    op(A)^T, W0 = B or B^T): |X - X_ref| within 2 gamma_{3n} of |T^-1| |alpha W0| growth,
+    bounded here through the well-conditioned T; and a small residual op(A) X - alpha B."""
+    M, N = 300, 200
+    alpha = 0.75
+    dim, opA, B, stored = trsm_system(layout, side, uplo, transa, diag, M, N, 54)
+    X, rep = run_trsm(layout, side, uplo, transa, diag, M, N, alpha, stored, B)
+    T = opA if side == fb.LEFT else opA.T
+    W0 = alpha * (B if side == fb.LEFT else B.T)
+    lower = np.allclose(np.triu(T, 1), 0.0)
+    Xref = O.trsm_left(T, W0, lower)
+    Xref = Xref if side == fb.LEFT else Xref.T
+    g = 3 * dim * 2.0 ** -53
+    assert np.max(np.abs(X - Xref)) <= 64 * g * np.max(np.abs(Xref))
+    res = (opA @ X - alpha * B) if side == fb.LEFT else (X @ opA - alpha * B)
+    mag = (np.abs(opA) @ np.abs(X)) if side == fb.LEFT else (np.abs(X) @ np.abs(opA))
+    assert np.all(np.abs(res) <= 4 * g * mag + 1e-300)
+    assert rep.detected == 0 and rep.status == 0 and rep.tiles_checked > 0
+
+
+@pytest.mark.parametrize("side", [fb.LEFT, fb.RIGHT])
+@pytest.mark.parametrize("layout", [O.COL_MAJOR, O.ROW_MAJOR])
+def test_dtrsm_faults_in_every_step_are_corrected_bitwise(layout, side):
+    """A fixed injection point applies to every internal step (each protected update GEMM
+    and each diagonal solve, in that step's coordinates): every fault is detected and
+    corrected, and X equals the fault-free X bit for bit."""
+    M, N = 520, 300
+    dim, opA, B, stored = trsm_system(layout, side, fb.LOWER, fb.NO_TRANS, fb.NON_UNIT, M, N, 55)
+    clean, rep0 = run_trsm(layout, side, fb.LOWER, fb.NO_TRANS, fb.NON_UNIT, M, N, 1.0, stored, B)
+    assert rep0.detected == 0
+    pts = [dict(i=5, j=7, site=fb.SITE_OUTPUT, mode=fb.MODE_BITFLIP, bit=54)]
+    got, rep = run_trsm(layout, side, fb.LOWER, fb.NO_TRANS, fb.NON_UNIT, M, N, 1.0, stored, B, inj=pts)
+    leaves = -(-dim // 128)
+    assert rep.detected == rep.corrected == 2 * leaves - 1  # every diagonal solve and every update
+    assert rep.uncorrectable == 0 and rep.checksum_only == 0
+    assert np.array_equal(got, clean)

@@ -555,3 +555,35 @@ def test_midk_clean_runs_never_flag():
         B = S.normal_matrix(seed, 1, K, N)
         _, rep = _midk(A, B, 16, tile=(16, 16), bk=8, alpha=1.5, beta=0.5, C=S.normal_matrix(seed, 2, M, N))
         assert rep.detected == 0
+
+
+# ------------------------------------------------------------------------------------
+# Triangular solve (the definition behind FT-DTRSM): plain substitution
+# ------------------------------------------------------------------------------------
+
+def test_trsm_identity_diagonal_and_exact_integer_solutions():
+    W = S.uniform_matrix(61, 0, 7, 5)
+    for lower in (True, False):
+        assert np.array_equal(O.trsm_left(np.eye(7), W, lower), W)
+        d = np.ldexp(1.0, S.randint(61, 1, 7, -3, 3).astype(int))
+        assert np.array_equal(O.trsm_left(np.diag(d), W, lower), W / d[:, None])
+    # unit lower bidiagonal with -1 below the diagonal: x_r = w_r + x_{r-1}, exact on integers
+    n = 9
+    T = np.eye(n) - np.eye(n, k=-1)
+    Wi = S.randint(61, 2, n * 3, -5, 5).reshape(n, 3).astype(np.float64)
+    assert np.array_equal(O.trsm_left(T, Wi, True), np.cumsum(Wi, axis=0))
+    assert np.array_equal(O.trsm_left(T.T, Wi, False), np.cumsum(Wi[::-1], axis=0)[::-1])
+
+
+def test_trsm_reads_only_its_triangle_and_has_small_residual():
+    n = 40
+    R = S.uniform_matrix(62, 0, n, n)
+    T = np.tril(R) + n * np.eye(n)
+    W = S.uniform_matrix(62, 1, n, 6)
+    junk = T + np.triu(np.full((n, n), np.nan), 1)  # the unread triangle holds NaN
+    X = O.trsm_left(junk, W, True)
+    # componentwise backward error of substitution: |T X - W| <= gamma_n |T| |X|
+    g = n * 2.0 ** -53 / (1 - n * 2.0 ** -53)
+    assert np.all(np.abs(T @ X - W) <= 2 * g * (np.abs(T) @ np.abs(X)) + 1e-300)
+    Xu = O.trsm_left(T.T + np.tril(np.full((n, n), np.nan), -1), W, False)
+    assert np.all(np.abs(T.T @ Xu - W) <= 2 * g * (np.abs(T.T) @ np.abs(Xu)) + 1e-300)
