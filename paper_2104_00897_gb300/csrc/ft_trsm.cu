@@ -18,7 +18,9 @@ namespace ftk {
 namespace {
 
 constexpr int kLeaf = kTrsmLeaf;  // diagonal block edge (<= 128)
-constexpr int kCols = 32;         // right-hand sides per CTA (one thread each)
+constexpr int kCols = 64;         // right-hand sides per CTA (one solving thread each)
+constexpr int kThreads = 256;     // all threads stage the block and the right-hand sides
+
 
 // dst(r, c) = scale * src[r * rs + c * cs], dst column-major with leading dimension ld.
 // 32 x 32 tiles; when the source is contiguous along c the tile goes through shared memory
@@ -51,109 +53,128 @@ __device__ __forceinline__ double gamma_up64(int64_t n) {
   return __ddiv_ru(nu, __dsub_rd(1.0, nu));
 }
 
+// The triangle of the block packed by columns: lower, column r holds rows r..n-1 from
+// r n - r (r - 1) / 2; upper, column r holds rows 0..r from r (r + 1) / 2.
+__device__ __forceinline__ int packed(int s, int r, int n, bool lower) {
+  return lower ? r * n - r * (r - 1) / 2 + (s - r) : r * (r + 1) / 2 + s;
+}
+
 struct LeafSmem {
-  double T[kLeaf][kLeaf + 1];       // the block, [row][column]
-  double w[kLeaf][kCols];           // w[row][thread]: the thread's column (right-hand side, then solution)
-  double wf[kLeaf][kCols];          // a faulty solution kept while the column is solved again
-  double tsum[kLeaf], tabs[kLeaf];  // column sums of T and of |T|
+  double T[kLeaf * (kLeaf + 1) / 2];  // the block's triangle, packed by columns
+  double w[kLeaf][kCols];             // w[row][column]: right-hand side, then solution
+  double wf[kLeaf][kCols];            // a faulty solution kept while its column is solved again
+  double tsum[kLeaf], tabs[kLeaf];    // column sums of T and of |T|
 };
 
-// Substitution for the column held in sm.w[.][t]: lower (forward) or upper (backward),
+// Substitution for column t held in sm.w[.][t]: lower (forward) or upper (backward),
 // x_r = w_r / T(r,r) then w_s -= T(s,r) x_r for the rows still to come. An injection point
 // at row inj_r flips bit inj_bit of x_r right after it is formed (test launches only).
 __device__ void solve_column(LeafSmem& sm, int t, int n, bool lower, int inj_r, int inj_bit) {
   for (int q = 0; q < n; ++q) {
     const int r = lower ? q : n - 1 - q;
-    double x = sm.w[r][t] / sm.T[r][r];
+    const double* col = sm.T + packed(lower ? r : 0, r, n, lower);  // column r's stored entries
+    double x = sm.w[r][t] / col[lower ? 0 : r];
     if (r == inj_r) x = __longlong_as_double(__double_as_longlong(x) ^ (1ll << inj_bit));
     sm.w[r][t] = x;
     if (lower) {
-      for (int s2 = r + 1; s2 < n; ++s2) sm.w[s2][t] = fma(-sm.T[s2][r], x, sm.w[s2][t]);
+      for (int s2 = r + 1; s2 < n; ++s2) sm.w[s2][t] = fma(-col[s2 - r], x, sm.w[s2][t]);
     } else {
-      for (int s2 = 0; s2 < r; ++s2) sm.w[s2][t] = fma(-sm.T[s2][r], x, sm.w[s2][t]);
+      for (int s2 = 0; s2 < r; ++s2) sm.w[s2][t] = fma(-col[s2], x, sm.w[s2][t]);
     }
   }
 }
 
 // One CTA: kCols right-hand sides of the n x n diagonal block at T (column-major, ld ldt);
 // W (column-major, ld ldw) is overwritten with the solution. rep: this step's report.
-__global__ void __launch_bounds__(kCols) trsm_leaf_kernel(const double* T, int64_t ldt, double* W, int64_t ldw, int n,
-                                                          int64_t nrhs, int lower, ft_report_t* rep, InjectList inj) {
+__global__ void __launch_bounds__(kThreads) trsm_leaf_kernel(const double* T, int64_t ldt, double* W, int64_t ldw,
+                                                             int n, int64_t nrhs, int lower, ft_report_t* rep,
+                                                             InjectList inj) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   LeafSmem& sm = *reinterpret_cast<LeafSmem*>(smem_raw);
-  const int t = threadIdx.x;
-  const int64_t j = (int64_t)blockIdx.x * kCols + t;
-  const bool jok = j < nrhs;
-  for (int e = t; e < n * n; e += kCols) {
+  const int tid = threadIdx.x;
+  const int64_t j0 = (int64_t)blockIdx.x * kCols;
+  const int ncols = (int)min((int64_t)kCols, nrhs - j0);
+  const bool low = lower != 0;
+  // stage the triangle (coalesced along each column) and the right-hand sides
+  for (int r = 0; r < n; ++r) {
+    const int lo = low ? r : 0, hi = low ? n : r + 1;  // stored rows of column r
+    for (int s2 = lo + tid; s2 < hi; s2 += kThreads) sm.T[packed(s2, r, n, low)] = T[s2 + (int64_t)r * ldt];
+  }
+  for (int e = tid; e < n * kCols; e += kThreads) {
     const int r = e % n, c = e / n;
-    const bool in_tri = lower ? (r >= c) : (r <= c);
-    sm.T[r][c] = in_tri ? T[r + (int64_t)c * ldt] : 0.0;
+    sm.w[r][c] = c < ncols ? W[r + (j0 + c) * ldw] : 0.0;
   }
   __syncthreads();
-  for (int c = t; c < n; c += kCols) {
+  for (int c = tid; c < n; c += kThreads) {
+    const double* col = sm.T + packed(low ? c : 0, c, n, low);
+    const int len = low ? n - c : c + 1;
     double s = 0.0, a = 0.0;
-    for (int r = 0; r < n; ++r) { s += sm.T[r][c]; a = __dadd_ru(a, fabs(sm.T[r][c])); }
+    for (int q = 0; q < len; ++q) { s += col[q]; a = __dadd_ru(a, fabs(col[q])); }
     sm.tsum[c] = s;
     sm.tabs[c] = a;
   }
-  double rsum = 0.0, rabs = 0.0;  // the right-hand side's sums
-  for (int r = 0; r < n; ++r) {
-    const double v = jok ? W[r + j * ldw] : 0.0;
-    sm.w[r][t] = v;
-    rsum += v;
-    rabs = __dadd_ru(rabs, fabs(v));
-  }
   __syncthreads();
-  int inj_r = -1, inj_bit = 0;
-  for (int e = 0; e < inj.n; ++e)
-    if (inj.p[e].j == j && inj.p[e].i >= 0 && inj.p[e].i < n && inj.p[e].mode == FT_MODE_BITFLIP) {
-      inj_r = inj.p[e].i;
-      inj_bit = inj.p[e].bit;
-    }
-  if (jok) solve_column(sm, t, n, lower != 0, inj_r, inj_bit);
-  // e^T T x against e^T r: tau = 2 gamma_{2n+2} (sum_s (e^T|T|)_s |x_s| + sum |r|), a bound on
-  // the substitution's residual (componentwise backward error gamma_n |T| |x|) plus the
-  // rounding of both sums.
-  double chk = 0.0, mag = 0.0;
-  for (int s2 = 0; s2 < n; ++s2) {
-    const double x = sm.w[s2][t];
-    chk = fma(sm.tsum[s2], x, chk);
-    mag = __fma_ru(sm.tabs[s2], fabs(x), mag);
-  }
-  const double delta = chk - rsum;
-  const double tau = __dmul_ru(2.0, __dmul_ru(gamma_up64(2 * (int64_t)n + 2), __dadd_ru(mag, rabs)));
-  const bool flagged = jok && (!(fabs(delta) <= tau) || isinf(delta));
-  if (rep && t == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&rep->tiles_checked), 1ull);
-  if (flagged) {
-    // keep the faulty solution, solve again from the untouched right-hand side in W
-    for (int r = 0; r < n; ++r) { sm.wf[r][t] = sm.w[r][t]; sm.w[r][t] = W[r + j * ldw]; }
-    solve_column(sm, t, n, lower != 0, -1, 0);
-    int first = -1;  // where the fault entered: the first row, in solve order, that differs
-    for (int q = 0; q < n && first < 0; ++q) {
-      const int r = lower ? q : n - 1 - q;
-      if (__double_as_longlong(sm.wf[r][t]) != __double_as_longlong(sm.w[r][t])) first = r;
-    }
-    if (rep) {
-      atomicAdd(reinterpret_cast<unsigned long long*>(&rep->detected), 1ull);
-      atomicAdd(reinterpret_cast<unsigned long long*>(&rep->corrected), 1ull);
-      const unsigned slot = atomicAdd(&rep->n_records, 1u);
-      if (slot < FTBLAS_MAX_RECORDS) {
-        ft_error_record_t& rc = rep->rec[slot];
-        rc.tile_row = 0; rc.tile_col = blockIdx.x;
-        rc.i = first; rc.j = j;
-        rc.delta_row = 0.0; rc.delta_col = delta; rc.tau_row = 0.0; rc.tau_col = tau;
-        rc.value_before = first >= 0 ? sm.wf[first][t] : 0.0;
-        rc.value_after = first >= 0 ? sm.w[first][t] : 0.0;
-        rc.rows_flagged = 0; rc.cols_flagged = 1;
-        rc.kind = FT_KIND_CORRECTED;
-        rc.reserved = 0;
-      } else {
-        atomicOr(&rep->status, FT_STATUS_RECORDS_TRUNCATED);
+  if (tid < kCols) {
+    const int t = tid;
+    const int64_t j = j0 + t;
+    const bool jok = t < ncols;
+    double rsum = 0.0, rabs = 0.0;  // the right-hand side's sums
+    for (int r = 0; r < n; ++r) { rsum += sm.w[r][t]; rabs = __dadd_ru(rabs, fabs(sm.w[r][t])); }
+    int inj_r = -1, inj_bit = 0;
+    for (int e = 0; e < inj.n; ++e)
+      if (inj.p[e].j == j && inj.p[e].i >= 0 && inj.p[e].i < n && inj.p[e].mode == FT_MODE_BITFLIP) {
+        inj_r = inj.p[e].i;
+        inj_bit = inj.p[e].bit;
+      }
+    if (jok) {
+      solve_column(sm, t, n, low, inj_r, inj_bit);
+      // e^T T x against e^T r: tau = 2 gamma_{2n+2} (sum_s (e^T|T|)_s |x_s| + sum |r|), a bound on
+      // the substitution's residual (componentwise backward error gamma_n |T| |x|) plus the
+      // rounding of both sums.
+      double chk = 0.0, mag = 0.0;
+      for (int s2 = 0; s2 < n; ++s2) {
+        const double x = sm.w[s2][t];
+        chk = fma(sm.tsum[s2], x, chk);
+        mag = __fma_ru(sm.tabs[s2], fabs(x), mag);
+      }
+      const double delta = chk - rsum;
+      const double tau = __dmul_ru(2.0, __dmul_ru(gamma_up64(2 * (int64_t)n + 2), __dadd_ru(mag, rabs)));
+      if (!(fabs(delta) <= tau) || isinf(delta)) {
+        // keep the faulty solution, solve again from the untouched right-hand side in W
+        for (int r = 0; r < n; ++r) { sm.wf[r][t] = sm.w[r][t]; sm.w[r][t] = W[r + j * ldw]; }
+        solve_column(sm, t, n, low, -1, 0);
+        int first = -1;  // where the fault entered: the first row, in solve order, that differs
+        for (int q = 0; q < n && first < 0; ++q) {
+          const int r = low ? q : n - 1 - q;
+          if (__double_as_longlong(sm.wf[r][t]) != __double_as_longlong(sm.w[r][t])) first = r;
+        }
+        if (rep) {
+          atomicAdd(reinterpret_cast<unsigned long long*>(&rep->detected), 1ull);
+          atomicAdd(reinterpret_cast<unsigned long long*>(&rep->corrected), 1ull);
+          const unsigned slot = atomicAdd(&rep->n_records, 1u);
+          if (slot < FTBLAS_MAX_RECORDS) {
+            ft_error_record_t& rc = rep->rec[slot];
+            rc.tile_row = 0; rc.tile_col = blockIdx.x;
+            rc.i = first; rc.j = j;
+            rc.delta_row = 0.0; rc.delta_col = delta; rc.tau_row = 0.0; rc.tau_col = tau;
+            rc.value_before = first >= 0 ? sm.wf[first][t] : 0.0;
+            rc.value_after = first >= 0 ? sm.w[first][t] : 0.0;
+            rc.rows_flagged = 0; rc.cols_flagged = 1;
+            rc.kind = FT_KIND_CORRECTED;
+            rc.reserved = 0;
+          } else {
+            atomicOr(&rep->status, FT_STATUS_RECORDS_TRUNCATED);
+          }
+        }
       }
     }
   }
-  if (jok)
-    for (int r = 0; r < n; ++r) W[r + j * ldw] = sm.w[r][t];
+  if (rep && tid == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&rep->tiles_checked), 1ull);
+  __syncthreads();
+  for (int e = tid; e < n * ncols; e += kThreads) {  // coalesced write-back
+    const int r = e % n, c = e / n;
+    W[r + (j0 + c) * ldw] = sm.w[r][c];
+  }
 }
 
 // Sum the step reports into `out` (zeroed by the caller): counters added, status ORed,
@@ -201,8 +222,8 @@ cudaError_t launch_trsm_leaf(const double* T, int64_t ldt, double* W, int64_t ld
   const size_t smem = sizeof(LeafSmem);
   cudaError_t e = cudaFuncSetAttribute(trsm_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  trsm_leaf_kernel<<<(unsigned)((nrhs + kCols - 1) / kCols), kCols, smem, st>>>(T, ldt, W, ldw, n, nrhs,
-                                                                                   lower ? 1 : 0, rep, inj);
+  trsm_leaf_kernel<<<(unsigned)((nrhs + kCols - 1) / kCols), kThreads, smem, st>>>(T, ldt, W, ldw, n, nrhs,
+                                                                                      lower ? 1 : 0, rep, inj);
   return cudaGetLastError();
 }
 
