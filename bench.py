@@ -922,14 +922,45 @@ def run_ours(args, rank, world, dist):
         return total_ms, kernel_per, rsum, injected, (sampler.summary() if sampler else None)
 
     results = {}
+    def measure_e2e():
+        """The headline metric through the host-buffer entry point, measured right after the
+        device-timed runs of the headline engine (same clocks regime), clocks sampled."""
+        hA = torch.from_numpy(A).pin_memory()
+        hB = torch.from_numpy(B).pin_memory()
+        hC = torch.from_numpy(Cin).pin_memory()
+        hrep = fb.FtReport()
+        fb.ftblas_set_injection(None)
+
+        def hcall():
+            fb.check(fb.ftblas_dgemm_host(fb.COL_MAJOR, fb.NO_TRANS, fb.NO_TRANS, n, n, n, 1.5, hA.data_ptr(), n,
+                                          hB.data_ptr(), n, 0.5, hC.data_ptr(), n, st, ctypes.addressof(hrep)))
+
+        for _ in range(max(1, min(args.warmup, 2))):
+            hcall()
+        barrier()
+        sampler = ClockSampler(local)
+        sampler.__enter__()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hcall()
+        barrier()
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+        sampler.__exit__(None, None, None)
+        return {"value": job_tflops(world, flops_step, args.steps, 1e3 * e2e_s), "unit": UNIT,
+                "h2d_bytes_per_step": 3 * n * n * 8, "d2h_bytes_per_step": n * n * 8 + fb.REPORT_BYTES,
+                "clocks": sampler.summary()}
+
     engine_list = [args.engine] + ([] if args.no_second_engine else [e for e in engines if e != args.engine])
     clocks = None
+    e2e = None
     for eng in engine_list:
         fb.ftblas_set_fp64_engine(engines[eng])
         head = eng == args.engine
         ft_ms, ft_per, ft_rep, injected, clk = timed(True, True, args.steps, args.warmup, clocks=head)
         if head:
             clocks = clk
+            if not args.no_e2e:
+                e2e = measure_e2e()
         cl_ms, _, cl_rep, _, _ = timed(True, False, args.steps, args.warmup)
         na_ms, _, _, _, _ = timed(False, False, args.steps, args.warmup)
         results[eng] = dict(ft_ms=ft_ms, ft_per=ft_per, ft_rep=ft_rep, injected=injected, clean_ms=cl_ms,
@@ -979,29 +1010,6 @@ def run_ours(args, rank, world, dist):
 
     # End to end through the public host-buffer entry point: pinned host operands, copies
     # in, protected GEMM, copies out (C and the report), synchronised per call.
-    e2e = None
-    if not args.no_e2e:
-        hA = torch.from_numpy(A).pin_memory()
-        hB = torch.from_numpy(B).pin_memory()
-        hC = torch.from_numpy(Cin).pin_memory()
-        hrep = fb.FtReport()
-        fb.ftblas_set_injection(None)
-
-        def hcall():
-            fb.check(fb.ftblas_dgemm_host(fb.COL_MAJOR, fb.NO_TRANS, fb.NO_TRANS, n, n, n, 1.5, hA.data_ptr(), n,
-                                          hB.data_ptr(), n, 0.5, hC.data_ptr(), n, st, ctypes.addressof(hrep)))
-
-        for _ in range(max(1, min(args.warmup, 2))):
-            hcall()
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            hcall()
-        barrier()
-        e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
-        e2e = {"value": job_tflops(world, flops_step, args.steps, 1e3 * e2e_s), "unit": UNIT,
-               "h2d_bytes_per_step": 3 * n * n * 8, "d2h_bytes_per_step": n * n * 8 + fb.REPORT_BYTES}
-
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         f, dt, thr = oracle_sample(n, A, B, Cin, n_tiles=16)

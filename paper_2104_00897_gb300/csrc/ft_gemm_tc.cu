@@ -783,7 +783,9 @@ __device__ __forceinline__ float reduce_scatter8_up(const float (&la)[8], int la
 struct EncArgs {
   const void* X; int64_t ld;
   int32_t nlines, K, L;
-  int32_t nclear;          // rows pass: entries of maxAbsBe to zero before the columns pass
+  int32_t nkc;             // k-chunks per line block
+  float* rowAbsA;          // rows pass: [M] upward sum_k |A(i,k)|, by the block's last k-chunk
+  unsigned* rowdone;       // rows pass: [nblocks] k-chunks finished (zeroed before the launch)
   float* sum;              // rows pass: [nblocks][pitch] e^T A per block
   float* abs_sum;          // rows pass: [nblocks][pitch] upward sum_{i in block} |A(i,k)|
   int64_t pitch;           // also the checksum operand's row pitch (elements)
@@ -793,13 +795,21 @@ struct EncArgs {
   void* chk;               // columns pass: pieces of B e in rows J*16 + p (unused rows zero)
 };
 
+// Shared memory of one encode CTA, declared once per kernel (both roles use it): the
+// float4 stores into the reduction arrays need their 16-byte alignment.
+struct __align__(16) EncSmem {
+  float red_s[ENC_WARPS][ENC_KC];
+  float red_a[ENC_WARPS][ENC_KC];
+  int last_chunk;
+};
+
 template <bool kRowsOfA, int KIND>
-__global__ void __launch_bounds__(256) encode_kernel(EncArgs g) {
+__device__ __forceinline__ void encode_block(const EncArgs& g, int blk, int kc, EncSmem& sm) {
   using E = Elem<KIND>;
-  __shared__ float red_s[ENC_WARPS][ENC_KC];
-  __shared__ float red_a[ENC_WARPS][ENC_KC];
+  auto& red_s = sm.red_s;
+  auto& red_a = sm.red_a;
+  int& last_chunk = sm.last_chunk;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int blk = blockIdx.x, kc = blockIdx.y;
   const int64_t line0 = (int64_t)blk * g.L;
   const int nI = (int)min((int64_t)g.L, (int64_t)g.nlines - line0);
   const int64_t k = (int64_t)kc * ENC_KC + lane * 8;
@@ -850,9 +860,20 @@ __global__ void __launch_bounds__(256) encode_kernel(EncArgs g) {
       g.sum[(int64_t)blk * g.pitch + kk] = S;
       g.abs_sum[(int64_t)blk * g.pitch + kk] = Aab;
     }
-    if (blk == 0 && kc == 0) {
-      for (int j = tk; j < g.nclear; j += blockDim.x) g.maxAbsBe[j] = 0.f;
-      if (tk == 0) g.pend->count = 0u;
+    if (blk == 0 && kc == 0 && tk == 0) g.pend->count = 0u;
+    // the line block's last k-chunk to finish sums the per-chunk partials of its rows
+    // (in chunk order: the result does not depend on which chunk finished last)
+    __threadfence();
+    __syncthreads();
+    if (tk == 0) last_chunk = atomicAdd(&g.rowdone[blk], 1u) == (unsigned)(g.nkc - 1);
+    __syncthreads();
+    if (last_chunk) {
+      __threadfence();
+      if (tk < nI) {
+        float a2 = 0.f;
+        for (int c2 = 0; c2 < g.nkc; ++c2) a2 = __fadd_ru(a2, __ldcg(&g.line_part[(int64_t)c2 * g.nlines + line0 + tk]));
+        g.rowAbsA[line0 + tk] = a2;
+      }
     }
   } else {
     if (kk < g.K) {
@@ -893,14 +914,13 @@ __global__ void __launch_bounds__(256) encode_kernel(EncArgs g) {
   }
 }
 
-// rowAbsA[i] = upward sum over the k-chunks of the per-chunk partial sums.
-__global__ void __launch_bounds__(256) row_abs_finalize_kernel(const float* line_part, int32_t M, int32_t nkc,
-                                                                float* rowAbsA) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M) return;
-  float a = 0.f;
-  for (int c = 0; c < nkc; ++c) a = __fadd_ru(a, line_part[(int64_t)c * M + i]);
-  rowAbsA[i] = a;
+// One launch for both operands: blocks x < nMb encode row blocks of A, the rest column
+// blocks of B, so the two reads overlap.
+template <int KIND>
+__global__ void __launch_bounds__(256) encode_kernel(EncArgs ga, EncArgs gb, int nMb) {
+  __shared__ EncSmem sm;
+  if ((int)blockIdx.x < nMb) encode_block<true, KIND>(ga, blockIdx.x, blockIdx.y, sm);
+  else encode_block<false, KIND>(gb, blockIdx.x - nMb, blockIdx.y, sm);
 }
 
 // C = beta C over an M x N column-major FP32 matrix (beta == 0 writes zeros: C is not read).
@@ -923,7 +943,7 @@ size_t tc_workspace_bytes(int32_t M, int32_t N, int32_t K, int kind) {
   const int64_t eb = kind == 0 ? 2 : 1;
   auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
   return up(nNb * CHK_ROWS * kpitch * eb) + up(nMb * kpitch * 4) + up(nMb * kpitch * 4) + up(M * 4) +
-         up(nNb * 4) + up(nkc * M * 4) + up((int64_t)sizeof(TcPending));
+         up(nNb * 4 + nMb * 4) + up(nkc * M * 4) + up((int64_t)sizeof(TcPending));
 }
 
 TcWorkspace tc_workspace_carve(void* base, int32_t M, int32_t N, int32_t K, int kind) {
@@ -938,7 +958,10 @@ TcWorkspace tc_workspace_carve(void* base, int32_t M, int32_t N, int32_t K, int 
   w.sA = reinterpret_cast<float*>(c); c += up(nMb * kpitch * 4);
   w.absSA = reinterpret_cast<float*>(c); c += up(nMb * kpitch * 4);
   w.rowAbsA = reinterpret_cast<float*>(c); c += up(M * 4);
-  w.maxAbsBe = reinterpret_cast<float*>(c); c += up(nNb * 4);
+  w.maxAbsBe = reinterpret_cast<float*>(c);
+  w.rowdone = reinterpret_cast<unsigned*>(w.maxAbsBe + nNb);
+  w.zero_bytes = (size_t)(nNb * 4 + nMb * 4);  // maxAbsBe and rowdone, cleared before the encode
+  c += up(nNb * 4 + nMb * 4);
   w.rowPart = reinterpret_cast<float*>(c); c += up(nkc * M * 4);
   w.pend = reinterpret_cast<TcPending*>(c); c += up((int64_t)sizeof(TcPending));
   w.bytes = static_cast<size_t>(c - static_cast<char*>(base));
@@ -948,20 +971,20 @@ TcWorkspace tc_workspace_carve(void* base, int32_t M, int32_t N, int32_t K, int 
 template <int KIND>
 static void launch_encode_kind(const TcParams& p, const TcWorkspace& w, cudaStream_t st) {
   const int nMb = (p.M + BM - 1) / BM, nNb = (p.N + kTcBNProt - 1) / kTcBNProt, nkc = (p.K + ENC_KC - 1) / ENC_KC;
-  EncArgs g;
-  std::memset(&g, 0, sizeof(g));
-  g.X = p.A; g.ld = p.lda; g.nlines = p.M; g.K = p.K; g.L = BM;
-  g.nclear = nNb; g.sum = w.sA; g.abs_sum = w.absSA; g.line_part = w.rowPart; g.maxAbsBe = w.maxAbsBe;
-  g.pitch = w.kpitch; g.pend = w.pend;
-  encode_kernel<true, KIND><<<dim3(nMb, nkc), ENC_WARPS * 32, 0, st>>>(g);
-  row_abs_finalize_kernel<<<(p.M + 255) / 256, 256, 0, st>>>(w.rowPart, p.M, nkc, w.rowAbsA);
-  std::memset(&g, 0, sizeof(g));
-  g.X = p.B; g.ld = p.ldb; g.nlines = p.N; g.K = p.K; g.L = kTcBNProt;
-  g.maxAbsBe = w.maxAbsBe; g.chk = w.chk; g.pitch = w.kpitch;
-  encode_kernel<false, KIND><<<dim3(nNb, nkc), ENC_WARPS * 32, 0, st>>>(g);
+  EncArgs ga, gb;
+  std::memset(&ga, 0, sizeof(ga));
+  ga.X = p.A; ga.ld = p.lda; ga.nlines = p.M; ga.K = p.K; ga.L = BM; ga.nkc = nkc;
+  ga.sum = w.sA; ga.abs_sum = w.absSA; ga.line_part = w.rowPart; ga.rowAbsA = w.rowAbsA; ga.rowdone = w.rowdone;
+  ga.pitch = w.kpitch; ga.pend = w.pend;
+  std::memset(&gb, 0, sizeof(gb));
+  gb.X = p.B; gb.ld = p.ldb; gb.nlines = p.N; gb.K = p.K; gb.L = kTcBNProt; gb.nkc = nkc;
+  gb.maxAbsBe = w.maxAbsBe; gb.chk = w.chk; gb.pitch = w.kpitch;
+  encode_kernel<KIND><<<dim3(nMb + nNb, nkc), ENC_WARPS * 32, 0, st>>>(ga, gb, nMb);
 }
 
 cudaError_t launch_tc_encode(const TcParams& p, const TcWorkspace& w, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(w.maxAbsBe, 0, w.zero_bytes, st);
+  if (e != cudaSuccess) return e;
   if (p.kind == 0) launch_encode_kind<0>(p, w, st);
   else launch_encode_kind<1>(p, w, st);
   return cudaGetLastError();

@@ -65,6 +65,8 @@ struct TcWorkspace {
   float* rowAbsA;
   float* maxAbsBe;
   float* rowPart;                // [nkc][M] per-k-chunk partial sums of |A(i,k)|
+  unsigned* rowdone;             // [nMb] k-chunks of each row block finished (follows maxAbsBe)
+  size_t zero_bytes;             // maxAbsBe and rowdone: zeroed before the encode
   TcPending* pend;
   size_t bytes;
 };
