@@ -40,7 +40,7 @@ if ROOT not in sys.path:
 METRIC = "FT-GEMM TFLOP/s, % of peak, ABFT overhead % vs unprotected, at stated error"
 UNIT = "TFLOP/s"
 SEED = 20210601
-TILE = 128
+TILE = 128  # FP64 verification tile edge at the 8192^3 workload (the oracle's geometry)
 
 
 def parse_args():
@@ -133,11 +133,11 @@ def profile_traffic(name, sources):
     return int(m_t.group(1))
 
 
-def workload_config(n, engine):
+def workload_config(n, engine, tile=TILE):
     return {"workload": f"ft_dgemm_fp64_col_major_{n}x{n}x{n}", "M": n, "N": n, "K": n, "alpha": 1.5, "beta": 0.5,
             "layout": "column-major, no transpose", "inputs": "A, B, C uniform[-1,1) from a fixed seed",
             "injection": "one seeded accumulator bit flip (bits 40-62) per 10 launches",
-            "verification_tile": f"{TILE}x{TILE}", "engine": engine,
+            "verification_tile": f"{tile}x{tile}", "engine": engine,
             "l2": "inputs 512 MiB per operand > 129 MB L2; no flush between steps"}
 
 
@@ -471,7 +471,8 @@ def run_sweep(dev, steps, warmup, shapes=SWEEP_SHAPES):
         ms_inj, det, cor = measure(True, True)
         ms_ft, det_clean, _ = measure(True, False)
         ms_na, _, _ = measure(False, False)
-        rows.append({"M": M, "N": N, "K": K, "ft_tflops_injected": flops / ms_inj / 1e9,
+        edge = fb.ftblas_verification_tile(fb.COL_MAJOR, fb.R_64F, M, N, K)[0]
+        rows.append({"M": M, "N": N, "K": K, "tile": f"{edge}x{edge}", "ft_tflops_injected": flops / ms_inj / 1e9,
                      "ft_tflops_clean": flops / ms_ft / 1e9, "noabft_tflops": flops / ms_na / 1e9,
                      "pct_of_fp64_peak_ft": 100.0 * flops / ms_ft / 1e9 / peak,
                      "abft_overhead_pct_clean": 100.0 * (ms_ft / ms_na - 1.0),
@@ -1062,7 +1063,8 @@ def run_ours(args, rank, world, dist):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ft_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(n, args.engine),
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(n, args.engine, fb.ftblas_verification_tile(fb.COL_MAJOR, fb.R_64F, n, n, n)[0]),
         "pct_of_peak": 100.0 * achieved / peak,
         "abft_overhead_pct": engines_out[args.engine]["abft_overhead_pct_injected"],
         "abft_overhead_pct_clean": engines_out[args.engine]["abft_overhead_pct_clean"],

@@ -295,16 +295,27 @@ int ftblas_gemm_ex_noalloc(ftblas_layout_t layout, ftblas_trans_t transa, ftblas
 /* Shape of the verification tile used for a call, in the caller's coordinates of C, and
  * the k-tile depth that sets the accumulator injection point (bk * floor(ceil(K/bk)/2)
  * products; for FTBLAS_R_32F the k-tile of the tensor-core path). compute_type selects the
- * kernel family: FTBLAS_R_64F (ftblas_dgemm) or FTBLAS_R_32F (BF16 tensor-core path).
+ * kernel family: FTBLAS_R_64F (ftblas_dgemm and the Level-3 routines built on it) or
+ * FTBLAS_R_32F (BF16 tensor-core path).
+ * FP64 tiles are square, 128 x 128, or 64 x 64 with the DFMA engine when 128-edge tiles
+ * would leave many of the current device's SMs idle: the choice depends on M, N, the
+ * engine (ftblas_set_fp64_engine) and the SM count (152 when no device answers). The
+ * unfused comparator ftblas_dgemm_unfused always verifies 128 x 128 tiles.
  * Returns 0, or a negative argument index. */
 int ftblas_verification_tile(ftblas_layout_t layout, ftblas_dtype_t compute_type,
                              int64_t M, int64_t N, int64_t K,
                              int64_t* tile_rows, int64_t* tile_cols, int64_t* k_tile);
 
-/* FP64 product engine: 0 = DFMA (SIMT fused multiply-add, default), 1 = DMMA (FP64
- * tensor-core mma.sync m8n8k4). Both run the same staging, encode and epilogue. Returns
- * the previous engine, or -1 for an unknown value. Process-wide. */
+/* FP64 product engine: 0 = DFMA (SIMT fused multiply-add, default; 128 or 64 tile edge),
+ * 1 = DMMA (FP64 tensor-core mma.sync m8n8k4; 128 tile edge). Both run the same staging,
+ * encode and epilogue. Returns the previous engine, or -1 for an unknown value.
+ * Process-wide. */
 int ftblas_set_fp64_engine(int engine);
+
+/* FP64 tile edge of the DFMA engine: 0 = automatic (the default; the rule described at
+ * ftblas_verification_tile), 128 or 64 = that edge for every later call. The DMMA engine
+ * always uses 128. Returns the previous setting, or -1 for another value. Process-wide. */
+int ftblas_set_fp64_tile(int edge);
 
 /* Online verification (Section V.A): the FP64 protected kernels also check each tile
  * after every k_interval products (rounded up to whole k-tiles of ftblas_verification_tile's

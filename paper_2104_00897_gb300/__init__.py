@@ -99,6 +99,7 @@ SIGNATURES = {
     "ftblas_verification_tile": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64,
                                            C.c_void_p, C.c_void_p, C.c_void_p]),
     "ftblas_set_fp64_engine": (C.c_int, [C.c_int]),
+    "ftblas_set_fp64_tile": (C.c_int, [C.c_int]),
     "ftblas_set_verification_interval": (C.c_int64, [C.c_int64]),
     "ftblas_status_string": (C.c_char_p, [C.c_int]),
     "ftblas_last_cuda_error": (C.c_int, []),
@@ -217,6 +218,10 @@ def ftblas_set_verification_interval(k_interval):
 
 def ftblas_set_fp64_engine(engine):
     return _call("ftblas_set_fp64_engine", engine)
+
+
+def ftblas_set_fp64_tile(edge):
+    return _call("ftblas_set_fp64_tile", int(edge))
 
 
 def ftblas_status_string(code):

@@ -33,13 +33,13 @@ namespace ftk {
 
 namespace {
 
-constexpr int BM = kDBM, BN = kDBN, BK = kDBK, STAGES = kDStages, NT = kDThreads;
+constexpr int BK = kDBK, STAGES = kDStages, NT = kDThreads;
 constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s per wait; a k-tile normally takes ~0.1 ms
-constexpr uint32_t kStageBytes = (BM * BK + BK * BN) * sizeof(double);
-
+// Shared memory of one CTA for engine E (tile E::BM x E::BN).
+template <class E>
 struct __align__(1024) DSmem {
-  double a[STAGES][BM * BK];
-  double b[STAGES][BK * BN];
+  double a[STAGES][E::BM * BK];
+  double b[STAGES][BK * E::BN];
   double encA[BK];        // e^T A over the tile's rows, per k of the current k-tile
   double encB[BK];        // B e over the tile's columns
   float encA_abs[BK];     // upward-rounded e^T |A|
@@ -53,18 +53,19 @@ struct __align__(1024) DSmem {
   int recompute;          // 1: the located element must be recomputed
   int loc_i, loc_j;       // tile-local location
   // online verification scratch: per-slot row / column sums of the raw accumulators
-  double mrs[8 * BM], mra[8 * BM];   // [ROW_SLOTS <= 8][BM] sums, upward sums of magnitudes
-  double mcs[4 * BN], mca[4 * BN];   // [COL_SLOTS <= 4][BN]
+  double mrs[E::ROW_SLOTS * E::BM], mra[E::ROW_SLOTS * E::BM];  // [ROW_SLOTS][BM] sums, upward sums of |.|
+  double mcs[E::COL_SLOTS * E::BN], mca[E::COL_SLOTS * E::BN];  // [COL_SLOTS][BN]
 };
 
 // Operand element (i, k) of the staged A tile and (k, j) of the staged B tile.
-template <bool AK>
+// (TBM, TBN: the tile's rows and columns, the strides of the M- and N-contiguous layouts.)
+template <bool AK, int TBM>
 __device__ __forceinline__ double lds_a(const double* sA, int i, int k) {
-  return AK ? sA[i * BK + k] : sA[k * BM + i];
+  return AK ? sA[i * BK + k] : sA[k * TBM + i];
 }
-template <bool BKM>
+template <bool BKM, int TBN>
 __device__ __forceinline__ double lds_b(const double* sB, int k, int j) {
-  return BKM ? sB[j * BK + k] : sB[k * BN + j];
+  return BKM ? sB[j * BK + k] : sB[k * TBN + j];
 }
 
 // Kernel-frame global operand access (recompute and fallback loads).
@@ -79,8 +80,11 @@ __device__ __forceinline__ double ldg_b(const DgemmParams& p, int64_t k, int64_t
 // Product engines. Each thread owns NR x NC accumulators at tile rows row(t, r) and tile
 // columns col(t, c); threads sharing a row (column) have distinct row_slot (col_slot).
 // ---------------------------------------------------------------------------------------
+// NR x NC accumulators per thread: a 16 NR x 16 NC tile (128 x 128 for 8 x 8, 64 x 64 for 4 x 4).
+template <int NR_, int NC_>
 struct EngineDFMA {
-  static constexpr int NR = 8, NC = 8;
+  static constexpr int NR = NR_, NC = NC_;
+  static constexpr int BM = 16 * NR, BN = 16 * NC;
   // Lanes l and l^16 share rows (reduced by one xor shuffle); the 8 warps then hold 8
   // partials per row. A column belongs to one half-warp (xor 1, 2, 4, 8): one partial.
   static constexpr int ROW_SLOTS = 8, COL_SLOTS = 1;
@@ -97,9 +101,9 @@ struct EngineDFMA {
     for (int k = 0; k < BK; ++k) {
       double a[NR], b[NC];
 #pragma unroll
-      for (int r = 0; r < NR; ++r) a[r] = lds_a<AK>(sA, tr + 16 * r, k);
+      for (int r = 0; r < NR; ++r) a[r] = lds_a<AK, BM>(sA, tr + 16 * r, k);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) b[c] = lds_b<BKM>(sB, k, tc + 16 * c);
+      for (int c = 0; c < NC; ++c) b[c] = lds_b<BKM, BN>(sB, k, tc + 16 * c);
 #pragma unroll
       for (int r = 0; r < NR; ++r)
 #pragma unroll
@@ -135,6 +139,7 @@ struct EngineDMMA {
   // 8 warps as 4 (rows) x 2 (columns); warp tile 32 x 64 = 4 x 8 fragments of 8 x 8.
   // m8n8k4 fragments: A(g, q), B(q, g), C(g, 2q + e) with g = lane / 4, q = lane % 4.
   static constexpr int NR = 4, NC = 16;
+  static constexpr int BM = 128, BN = 128;
   // Rows are shared by the 4 lanes with equal g (xor 1, 2) and by the 2 column warps;
   // columns by the 8 lanes with equal q (xor 4, 8, 16) and by the 4 row warps.
   static constexpr int ROW_SLOTS = 2, COL_SLOTS = 4;
@@ -155,9 +160,9 @@ struct EngineDMMA {
     for (int k = 0; k < BK; k += 4) {
       double a[NR], b[NC / 2];
 #pragma unroll
-      for (int mb = 0; mb < NR; ++mb) a[mb] = lds_a<AK>(sA, r0 + 8 * mb, k + qq);
+      for (int mb = 0; mb < NR; ++mb) a[mb] = lds_a<AK, BM>(sA, r0 + 8 * mb, k + qq);
 #pragma unroll
-      for (int nb = 0; nb < NC / 2; ++nb) b[nb] = lds_b<BKM>(sB, k + qq, c0 + 8 * nb);
+      for (int nb = 0; nb < NC / 2; ++nb) b[nb] = lds_b<BKM, BN>(sB, k + qq, c0 + 8 * nb);
 #pragma unroll
       for (int mb = 0; mb < NR; ++mb)
 #pragma unroll
@@ -206,6 +211,7 @@ __device__ __forceinline__ void xor_reduce(double& s, double& a, int mask) {
 // tile, written as per-slot partials: srow/arow[ROW_SLOTS][BM], scol/acol[COL_SLOTS][BN].
 template <class E, class F>
 __device__ __forceinline__ void tile_sums(F val, int t, double* srow, double* arow, double* scol, double* acol) {
+  constexpr int BM = E::BM, BN = E::BN;
   const int lane = t & 31;
 #pragma unroll
   for (int r = 0; r < E::NR; ++r) {
@@ -257,8 +263,9 @@ __device__ void write_record(const DgemmParams& p, int kind, int64_t tr, int64_t
 }
 
 // Cooperative (non-TMA) load of one k-tile into the same smem layout TMA produces.
-template <bool AK, bool BKM>
+template <class E, bool AK, bool BKM>
 __device__ void load_ktile_plain(const DgemmParams& p, double* sA, double* sB, int m0, int n0, int k0, int t) {
+  constexpr int BM = E::BM, BN = E::BN;
   for (int idx = t; idx < BM * BK; idx += NT) {
     int i, k;
     if (AK) { i = idx / BK; k = idx % BK; } else { k = idx / BM; i = idx % BM; }
@@ -273,9 +280,10 @@ __device__ void load_ktile_plain(const DgemmParams& p, double* sA, double* sB, i
   }
 }
 
-template <bool AK, bool BKM>
-__device__ __forceinline__ void issue_ktile(DSmem& sm, const CUtensorMap* tmA, const CUtensorMap* tmB, int s,
+template <class E, bool AK, bool BKM>
+__device__ __forceinline__ void issue_ktile(DSmem<E>& sm, const CUtensorMap* tmA, const CUtensorMap* tmB, int s,
                                             int m0, int n0, int k0) {
+  constexpr uint32_t kStageBytes = (E::BM * BK + BK * E::BN) * sizeof(double);
   mbar_arrive_expect_tx(&sm.full[s], kStageBytes);
   if (AK) tma_load_2d(sm.a[s], tmA, &sm.full[s], k0, m0);
   else tma_load_2d(sm.a[s], tmA, &sm.full[s], m0, k0);
@@ -292,13 +300,15 @@ __device__ __forceinline__ void issue_ktile(DSmem& sm, const CUtensorMap* tmA, c
 // call it (it synchronises).
 template <class E>
 __device__ __forceinline__ void online_check(const DgemmParams& p, double (&acc)[E::NR][E::NC], double pred, float pmag,
-                                          DSmem& sm, int t, int m0, int n0, int nI, int nJ, int64_t kmin,
+                                          DSmem<E>& sm, int t, int m0, int n0, int nI, int nJ, int64_t kmin,
                                           int64_t kp) {
+  constexpr int BM = E::BM, BN = E::BN;
   tile_sums<E>([&](int r, int c) { return acc[r][c]; }, t, sm.mrs, sm.mra, sm.mcs, sm.mca);
   const bool huge = __syncthreads_or(!isfinite(pmag));  // binary32 bound overflowed: skip
   if (huge) return;
-  const bool is_row = t < BM;
-  const int idx = is_row ? t : t - BM;
+  // one row (t < BM) or one column (BM <= t < BM + BN) per thread; threads beyond idle
+  const bool is_row = t < BM, active = t < BM + BN;
+  const int idx = is_row ? t : (active ? t - BM : 0);
   const int nslots = is_row ? E::ROW_SLOTS : E::COL_SLOTS;
   const int extent = is_row ? BM : BN;
   const double* ps = is_row ? sm.mrs : sm.mcs;
@@ -312,7 +322,7 @@ __device__ __forceinline__ void online_check(const DgemmParams& p, double (&acc)
   const int n_other = is_row ? nJ : nI;
   double tau = __fma_ru(gamma_up64(kp + n_other + 3), (double)pmag, __dmul_ru(gamma_up64(n_other), R));
   tau = __dmul_ru(2.0, tau);
-  const bool valid = idx < (is_row ? nI : nJ);
+  const bool valid = active && idx < (is_row ? nI : nJ);
   const bool flagged = valid && (!(fabs(delta) <= tau) || isinf(delta));
   if (flagged) atomicMin(is_row ? &sm.first_row : &sm.first_col, idx);
   const int nr = __syncthreads_count(is_row && flagged);
@@ -348,8 +358,9 @@ template <class E, bool AK, bool BKM, bool FT>
 __global__ void __launch_bounds__(NT, 1)
     dgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const __grid_constant__ DgemmParams p) {
+  constexpr int BM = E::BM, BN = E::BN;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  DSmem& sm = *reinterpret_cast<DSmem*>(smem_raw);
+  DSmem<E>& sm = *reinterpret_cast<DSmem<E>*>(smem_raw);
   const int t = threadIdx.x;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int nk = (p.K + BK - 1) / BK;
@@ -374,7 +385,7 @@ __global__ void __launch_bounds__(NT, 1)
     if (p.use_tma) {
       tma_prefetch_desc(&tmA);
       tma_prefetch_desc(&tmB);
-      for (int s = 0; s < STAGES && s < nl; ++s) issue_ktile<AK, BKM>(sm, &tmA, &tmB, s, m0, n0, (kb + s) * BK);
+      for (int s = 0; s < STAGES && s < nl; ++s) issue_ktile<E, AK, BKM>(sm, &tmA, &tmB, s, m0, n0, (kb + s) * BK);
     }
   }
   __syncthreads();
@@ -394,7 +405,7 @@ __global__ void __launch_bounds__(NT, 1)
     if (p.use_tma) {
       if (!mbar_wait_bounded(&sm.full[s], (lt / STAGES) & 1, kWaitLimitNs)) sm.timeout = 1;
     } else {
-      load_ktile_plain<AK, BKM>(p, sm.a[s], sm.b[s], m0, n0, kt * BK, t);
+      load_ktile_plain<E, AK, BKM>(p, sm.a[s], sm.b[s], m0, n0, kt * BK, t);
     }
     __syncthreads();
     if (sm.timeout) break;
@@ -426,14 +437,14 @@ __global__ void __launch_bounds__(NT, 1)
         if (sidx < BK) {
 #pragma unroll 8
           for (int qq = 0; qq < BM / 4; ++qq) {
-            const double x = lds_a<AK>(sA, part + 4 * qq, sidx);
+            const double x = lds_a<AK, BM>(sA, part + 4 * qq, sidx);
             v += x;
             va = add_up(va, abs_up(x));
           }
         } else {
 #pragma unroll 8
           for (int qq = 0; qq < BN / 4; ++qq) {
-            const double x = lds_b<BKM>(sB, sidx - BK, part + 4 * qq);
+            const double x = lds_b<BKM, BN>(sB, sidx - BK, part + 4 * qq);
             v += x;
             va = add_up(va, abs_up(x));
           }
@@ -450,21 +461,22 @@ __global__ void __launch_bounds__(NT, 1)
       }
       __syncthreads();
       // E2: C^r(i) += sum_k A(i,k) (Be)(k) for i = t; C^c(j) += sum_k (e^T A)(k) B(k,j) for
-      // j = t - 128. The k order is rotated by lane to spread shared-memory banks.
+      // j = t - BM (threads from BM + BN on are idle). The k order is rotated by lane to
+      // spread shared-memory banks.
       if (t < BM) {
 #pragma unroll 8
         for (int kk = 0; kk < BK; ++kk) {
           const int k = (kk + t) & (BK - 1);
-          const double x = lds_a<AK>(sA, t, k);
+          const double x = lds_a<AK, BM>(sA, t, k);
           pred = fma(x, sm.encB[k], pred);
           pmag = fma_up(abs_up(x), sm.encB_abs[k], pmag);
         }
-      } else {
+      } else if (t < BM + BN) {
         const int j = t - BM;
 #pragma unroll 8
         for (int kk = 0; kk < BK; ++kk) {
           const int k = (kk + t) & (BK - 1);
-          const double y = lds_b<BKM>(sB, k, j);
+          const double y = lds_b<BKM, BN>(sB, k, j);
           pred = fma(sm.encA[k], y, pred);
           pmag = fma_up(sm.encA_abs[k], abs_up(y), pmag);
         }
@@ -473,7 +485,7 @@ __global__ void __launch_bounds__(NT, 1)
 
     E::template ktile<AK, BKM>(acc, sA, sB, t);
     __syncthreads();
-    if (p.use_tma && t == 0 && lt + STAGES < nl) issue_ktile<AK, BKM>(sm, &tmA, &tmB, s, m0, n0, (kt + STAGES) * BK);
+    if (p.use_tma && t == 0 && lt + STAGES < nl) issue_ktile<E, AK, BKM>(sm, &tmA, &tmB, s, m0, n0, (kt + STAGES) * BK);
     if (FT && p.kc_tiles > 0 && (kt + 1) % p.kc_tiles == 0 && kt + 1 < ke)
       online_check<E>(p, acc, pred, pmag, sm, t, m0, n0, nI, nJ, k_lo, (int64_t)(kt + 1) * BK);
   }
@@ -547,9 +559,9 @@ __global__ void __launch_bounds__(NT, 1)
     tile_sums<E>([&](int r, int c) { return acc[r][c]; }, t, rsum, rabs, csum, cabs);
     __syncthreads();
 
-    // One row (t < 128) or one column (t >= 128) per thread.
-    const bool is_row = t < BM;
-    const int idx = is_row ? t : t - BM;
+    // One row (t < BM) or one column (BM <= t < BM + BN) per thread; threads beyond idle.
+    const bool is_row = t < BM, active = t < BM + BN;
+    const int idx = is_row ? t : (active ? t - BM : 0);
     const int nslots = is_row ? E::ROW_SLOTS : E::COL_SLOTS;
     const int extent = is_row ? BM : BN;
     const double* ps = is_row ? rsum : csum;
@@ -580,7 +592,7 @@ __global__ void __launch_bounds__(NT, 1)
           sabsA[kk] = sa;
         }
         __syncthreads();
-        if (idx < (is_row ? nI : nJ)) {
+        if (active && idx < (is_row ? nI : nJ)) {
           for (int kk = 0; kk < kc; ++kk) {
             const double x = is_row ? fabs(ldg_a(p, m0 + idx, k0 + kk)) : fabs(ldg_b(p, k0 + kk, n0 + idx));
             P = __fma_ru(x, is_row ? sabsB[kk] : sabsA[kk], P);
@@ -611,14 +623,14 @@ __global__ void __launch_bounds__(NT, 1)
     double tau = __fma_ru(fabs(p.alpha), P, __dmul_ru(fabs(p.beta), Q));
     tau = __fma_ru(g1, tau, __dmul_ru(g2, R));
     tau = __dmul_ru(2.0, tau);
-    const bool valid = idx < (is_row ? nI : nJ);
+    const bool valid = active && idx < (is_row ? nI : nJ);
     // Flagged: |delta| > tau, or delta not finite (NaN, or infinite even against tau = inf).
     const bool flagged = valid && (!(fabs(delta) <= tau) || isinf(delta));
     if (flagged) atomicMin(is_row ? &sm.first_row : &sm.first_col, idx);
     const int nr = __syncthreads_count(is_row && flagged);
     const int nc = __syncthreads_count(!is_row && flagged);
-    if (is_row && idx == sm.first_row) { sm.delta_row = delta; sm.tau_row = tau; }
-    if (!is_row && idx == sm.first_col) { sm.delta_col = delta; sm.tau_col = tau; }
+    if (valid && is_row && idx == sm.first_row) { sm.delta_row = delta; sm.tau_row = tau; }
+    if (valid && !is_row && idx == sm.first_col) { sm.delta_col = delta; sm.tau_col = tau; }
     __syncthreads();
 
     const bool nonfinite = sm.nonfinite != 0;
@@ -713,11 +725,11 @@ template <class E, bool AK, bool BKM, bool FT>
 cudaError_t launch_one(const DgemmParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, cudaStream_t st) {
   auto kern = dgemm_kernel<E, AK, BKM, FT>;
   // Set on every launch: the attribute is per device and the call costs microseconds.
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DSmem));
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DSmem<E>));
   if (e != cudaSuccess) return e;
-  dim3 grid((p.M + BM - 1) / BM, (p.N + BN - 1) / BN);
+  dim3 grid((p.M + E::BM - 1) / E::BM, (p.N + E::BN - 1) / E::BN);
   kernel_timer_start(st);
-  kern<<<grid, NT, sizeof(DSmem), st>>>(*tmA, *tmB, p);
+  kern<<<grid, NT, sizeof(DSmem<E>), st>>>(*tmA, *tmB, p);
   kernel_timer_stop(st);
   return cudaGetLastError();
 }
@@ -733,11 +745,18 @@ cudaError_t launch_layout(const DgemmParams& p, const CUtensorMap* tmA, const CU
 }  // namespace
 
 cudaError_t launch_dgemm(const DgemmParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, bool ft, int engine,
-                         cudaStream_t stream) {
+                         int tile_edge, cudaStream_t stream) {
   if (engine == kEngineDMMA) {
+    if (tile_edge != EngineDMMA::BM) return cudaErrorInvalidValue;
     return ft ? launch_layout<EngineDMMA, true>(p, tmA, tmB, stream) : launch_layout<EngineDMMA, false>(p, tmA, tmB, stream);
   }
-  return ft ? launch_layout<EngineDFMA, true>(p, tmA, tmB, stream) : launch_layout<EngineDFMA, false>(p, tmA, tmB, stream);
+  using Dfma128 = EngineDFMA<8, 8>;
+  using Dfma64 = EngineDFMA<4, 4>;
+  if (tile_edge == Dfma64::BM) {
+    return ft ? launch_layout<Dfma64, true>(p, tmA, tmB, stream) : launch_layout<Dfma64, false>(p, tmA, tmB, stream);
+  }
+  if (tile_edge != Dfma128::BM) return cudaErrorInvalidValue;
+  return ft ? launch_layout<Dfma128, true>(p, tmA, tmB, stream) : launch_layout<Dfma128, false>(p, tmA, tmB, stream);
 }
 
 cudaError_t launch_scale(double* C, int64_t ldc, int32_t M, int32_t N, double beta, cudaStream_t stream) {

@@ -49,18 +49,27 @@ struct DgemmParams {
   InjectList inj;
 };
 
-// FP64 tile geometry (all engines).
+// FP64 tile geometry. Tiles are square, kDBM x kDBN, or kDBSmall x kDBSmall (DFMA engine
+// only) when the larger tiles would leave many SMs idle (fp64_tile_edge).
 constexpr int kDBM = 128;      // tile rows (kernel frame)
 constexpr int kDBN = 128;      // tile columns
+constexpr int kDBSmall = 64;   // edge of the small tile
 constexpr int kDBK = 32;       // k-tile depth
 constexpr int kDStages = 3;    // smem ring depth
 constexpr int kDThreads = 256; // 8 warps, all compute
 
 enum Fp64Engine : int { kEngineDFMA = 0, kEngineDMMA = 1 };
 
-// Launch the FP64 kernel family. `ft` selects protection. Returns a cudaError_t.
+// Tile edge (kDBM or kDBSmall) of the FP64 kernels for a kernel-frame M x N output on
+// `engine`, given the GPU's SM count: the tile whose waves of CTAs, weighted by the checksum
+// work per product operation (about 4 / edge), keep the most SMs busy; kDBSmall only when
+// that gain is at least 3 %. DMMA: kDBM always.
+int fp64_tile_edge(int64_t M, int64_t N, int engine, int sm_count);
+
+// Launch the FP64 kernel family. `ft` selects protection; tile_edge must be
+// fp64_tile_edge's answer for p.M, p.N (the TMA boxes are cut to it). Returns a cudaError_t.
 cudaError_t launch_dgemm(const DgemmParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB,
-                         bool ft, int engine, cudaStream_t stream);
+                         bool ft, int engine, int tile_edge, cudaStream_t stream);
 
 // Unfused comparator (ftblas_dgemm_unfused): checksum passes around a library DGEMM.
 struct UnfusedParams {

@@ -19,6 +19,7 @@ namespace {
 thread_local int g_last_cuda_error = 0;
 thread_local int g_last_used_tma = -1;
 std::atomic<int> g_fp64_engine{kEngineDFMA};
+std::atomic<int> g_fp64_tile{0};  // 0: fp64_tile_edge decides; else the forced DFMA tile edge
 std::atomic<int64_t> g_kc_interval{0};
 
 // ------------------------------------------------------------------ injection plan state
@@ -31,6 +32,17 @@ int record_cuda(cudaError_t e) {
   if (e == cudaSuccess) return 0;
   g_last_cuda_error = static_cast<int>(e);
   return FTBLAS_STATUS_CUDA_ERROR;
+}
+
+// SMs of the current device; 152 (GB300) when no device answers, so that the geometry
+// queries also work on a machine without a GPU.
+int current_sm_count() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+      v > 0)
+    return v;
+  (void)cudaGetLastError();
+  return 152;
 }
 
 // SplitMix64 step (Steele, Lea and Flood, OOPSLA 2014).
@@ -199,6 +211,30 @@ Frame map_frame(int layout, int ta, int tb, int64_t M, int64_t N, const void* A,
 
 constexpr int64_t kMaxDim = (int64_t(1) << 31) - 256;
 
+}  // namespace
+
+int ftk::fp64_tile_edge(int64_t M, int64_t N, int engine, int sm_count) {
+  if (engine == kEngineDMMA || M <= 0 || N <= 0 || sm_count <= 0) return kDBM;
+  // busy fraction of the SMs over the waves of one CTA per tile, divided by the work per
+  // product operation (1 + 4 / edge: encode and predicted checksums over the tile's edges)
+  auto score = [&](int64_t e) {
+    const int64_t tiles = ((M + e - 1) / e) * ((N + e - 1) / e);
+    const int64_t waves = (tiles + sm_count - 1) / sm_count;
+    return (double)tiles / (double)(waves * sm_count) / (1.0 + 4.0 / (double)e);
+  };
+  return score(kDBSmall) > 1.03 * score(kDBM) ? kDBSmall : kDBM;
+}
+
+namespace {
+
+// The FP64 tile edge of a kernel-frame M x N call: DMMA's only edge, the forced DFMA edge
+// (ftblas_set_fp64_tile), else the rule of fp64_tile_edge.
+int chosen_fp64_edge(int64_t M, int64_t N, int engine) {
+  if (engine == kEngineDMMA) return kDBM;
+  const int forced = g_fp64_tile.load();
+  return forced != 0 ? forced : fp64_tile_edge(M, N, engine, current_sm_count());
+}
+
 // tri_a / tri_b: op(A) / op(B) triangular in the caller's frame (0 no, 1 upper, 2 lower):
 // the kernel then runs, per tile, only the k-tiles the nonzero triangle reaches.
 int dgemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
@@ -214,12 +250,11 @@ int dgemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, doub
   }
   if (M == 0 || N == 0) return 0;
   const Frame f = map_frame(layout, ta, tb, M, N, A, lda, B, ldb);
+  const int engine = g_fp64_engine.load();
+  const int edge = chosen_fp64_edge(f.M, f.N, engine);  // square tiles
   CallerPoint pts[kMaxInject];
   int npts = 0;
-  if (ft) {
-    const int64_t tile_rows = f.swap ? kDBN : kDBM, tile_cols = f.swap ? kDBM : kDBN;
-    npts = plan_injections(M, N, tile_rows, tile_cols, pts);
-  }
+  if (ft) npts = plan_injections(M, N, edge, edge, pts);
   if (K == 0 || alpha == 0.0) return record_cuda(launch_scale(C, ldc, (int32_t)f.M, (int32_t)f.N, beta, st));
 
   DgemmParams p;
@@ -255,13 +290,14 @@ int dgemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, doub
   CUtensorMap tmA, tmB;
   std::memset(&tmA, 0, sizeof(tmA));
   std::memset(&tmB, 0, sizeof(tmB));
-  bool ok = f.a_kmajor ? make_map_f64(&tmA, f.A, K, f.M, f.lda, kDBK, kDBM)
-                       : make_map_f64(&tmA, f.A, f.M, K, f.lda, kDBM, kDBK);
-  ok = ok && (f.b_kmajor ? make_map_f64(&tmB, f.B, K, f.N, f.ldb, kDBK, kDBN)
-                         : make_map_f64(&tmB, f.B, f.N, K, f.ldb, kDBN, kDBK));
+  const uint32_t be = (uint32_t)edge;
+  bool ok = f.a_kmajor ? make_map_f64(&tmA, f.A, K, f.M, f.lda, kDBK, be)
+                       : make_map_f64(&tmA, f.A, f.M, K, f.lda, be, kDBK);
+  ok = ok && (f.b_kmajor ? make_map_f64(&tmB, f.B, K, f.N, f.ldb, kDBK, be)
+                         : make_map_f64(&tmB, f.B, f.N, K, f.ldb, be, kDBK));
   p.use_tma = ok ? 1 : 0;
   g_last_used_tma = p.use_tma;
-  return record_cuda(launch_dgemm(p, &tmA, &tmB, ft, g_fp64_engine.load(), st));
+  return record_cuda(launch_dgemm(p, &tmA, &tmB, ft, engine, edge, st));
 }
 
 // ------------------------------------------------------------------ FT-DSYMM, FT-DTRMM
@@ -846,7 +882,11 @@ int ftblas_verification_tile(ftblas_layout_t layout, ftblas_dtype_t compute_type
   if (!tile_cols) return -7;
   if (!k_tile) return -8;
   const bool swap = layout == FTBLAS_ROW_MAJOR;
-  const int64_t bm = compute_type == FTBLAS_R_64F ? kDBM : kTcBM, bn = compute_type == FTBLAS_R_64F ? kDBN : kTcBNProt;
+  int64_t bm = kTcBM, bn = kTcBNProt;
+  if (compute_type == FTBLAS_R_64F) {
+    // square tiles: the kernel frame's transpose of a row-major call does not change them
+    bm = bn = chosen_fp64_edge(M, N, g_fp64_engine.load());
+  }
   *tile_rows = swap ? bn : bm;
   *tile_cols = swap ? bm : bn;
   *k_tile = compute_type == FTBLAS_R_64F ? kDBK : 64;
@@ -861,6 +901,11 @@ int64_t ftblas_set_verification_interval(int64_t k_interval) {
 int ftblas_set_fp64_engine(int engine) {
   if (engine != kEngineDFMA && engine != kEngineDMMA) return -1;
   return g_fp64_engine.exchange(engine);
+}
+
+int ftblas_set_fp64_tile(int edge) {
+  if (edge != 0 && edge != kDBM && edge != kDBSmall) return -1;
+  return g_fp64_tile.exchange(edge);
 }
 
 const char* ftblas_status_string(int code) {

@@ -71,6 +71,22 @@ def test_injection_config_validation_and_counter():
 def test_verification_tile_and_engine_switch():
     assert fb.ftblas_verification_tile(fb.COL_MAJOR, fb.R_64F, 10, 10, 10) == (128, 128, 32)
     assert fb.ftblas_verification_tile(fb.ROW_MAJOR, fb.R_64F, 10, 10, 10) == (128, 128, 32)
+    # The FP64 tile edge follows the waves of CTAs on 152 SMs (no device here): 64 where
+    # 128-edge tiles leave most SMs idle, 128 where they fill the waves.
+    expect = {(256, 256): 64, (300, 200): 64, (1024, 1024): 64, (2048, 2048): 64, (128, 8192): 64,
+              (4096, 4096): 128, (8192, 8192): 128, (16384, 16384): 128, (32768, 1024): 128}
+    for (m, n), e in expect.items():
+        for layout in (fb.COL_MAJOR, fb.ROW_MAJOR):
+            assert fb.ftblas_verification_tile(layout, fb.R_64F, m, n, 512) == (e, e, 32), (m, n)
+    assert fb.ftblas_set_fp64_tile(128) == 0
+    assert fb.ftblas_verification_tile(fb.COL_MAJOR, fb.R_64F, 1024, 1024, 1024) == (128, 128, 32)
+    assert fb.ftblas_set_fp64_tile(64) == 128
+    assert fb.ftblas_verification_tile(fb.COL_MAJOR, fb.R_64F, 8192, 8192, 8192) == (64, 64, 32)
+    prev = fb.ftblas_set_fp64_engine(fb.ENGINE_DMMA)
+    assert fb.ftblas_verification_tile(fb.COL_MAJOR, fb.R_64F, 1024, 1024, 1024) == (128, 128, 32)
+    fb.ftblas_set_fp64_engine(prev)
+    assert fb.ftblas_set_fp64_tile(96) == -1
+    assert fb.ftblas_set_fp64_tile(0) == 64
     prev = fb.ftblas_set_fp64_engine(fb.ENGINE_DMMA)
     assert fb.ftblas_set_fp64_engine(prev) == fb.ENGINE_DMMA
     assert fb.ftblas_set_fp64_engine(7) == -1

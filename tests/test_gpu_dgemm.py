@@ -19,16 +19,27 @@ import paper_2104_00897_gb300 as fb  # noqa: E402
 
 TOL = 1e-15
 COMBOS = [(l, a, b) for l in (O.COL_MAJOR, O.ROW_MAJOR) for a in (O.NO_TRANS, O.TRANS) for b in (O.NO_TRANS, O.TRANS)]
-ENGINES = [fb.ENGINE_DFMA, fb.ENGINE_DMMA]
+# kernel variants: (engine, forced tile edge or 0 for the automatic choice, which is 64 for
+# the small problems here and 128 from 4096 on)
+ENGINES = [(fb.ENGINE_DFMA, 0), (fb.ENGINE_DFMA, 128), (fb.ENGINE_DMMA, 0)]
+ENGINE_IDS = ["dfma-auto", "dfma-128", "dmma"]
+
+
+def use(variant):
+    engine, edge = variant
+    fb.ftblas_set_fp64_engine(engine)
+    fb.ftblas_set_fp64_tile(edge)
 
 
 @pytest.fixture(autouse=True)
 def _fresh_injection():
     fb.ftblas_set_injection(None)
     prev = fb.ftblas_set_fp64_engine(fb.ENGINE_DFMA)
+    prev_tile = fb.ftblas_set_fp64_tile(0)
     yield
     fb.ftblas_set_injection(None)
     fb.ftblas_set_fp64_engine(prev)
+    fb.ftblas_set_fp64_tile(prev_tile)
 
 
 def dev(x):
@@ -64,17 +75,18 @@ def seeded_point(seed, M, N):
 
 
 # ---------------------------------------------------------------------------------------
-@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
 def test_config1_256_fault_free_and_bit52_flip(engine):
     """FP64 column-major 256^3, alpha = 1, beta = 0, U[-1,1]: a fault-free run, then one
     flip of bit 52 of C(i,j) at seeded (i,j) after K/2 products."""
-    fb.ftblas_set_fp64_engine(engine)
+    use(engine)
     P = Problem(256, 256, 256, alpha=1.0, beta=0.0, seed=20210601)
     tr, tc, bk = tile_of(P)
     clean, rep = run_gpu(P)
     assert fb.ftblas_last_launch_used_tma() == 1
     oclean, orep = P.oracle_ft(tr, tc, bk)
-    assert report_summary(rep) == report_summary(orep) == (4, 0, 0, 0, 0, 0)
+    nt = (256 // tr) * (256 // tc)
+    assert report_summary(rep) == report_summary(orep) == (nt, 0, 0, 0, 0, 0)
     assert P.normalized_error(clean, oclean) <= TOL
     assert bk * ((256 // bk) // 2) == 128  # the flip happens after K/2 products
     i, j = seeded_point(20210601, 256, 256)
@@ -82,7 +94,7 @@ def test_config1_256_fault_free_and_bit52_flip(engine):
     fb.ftblas_set_injection(fb.make_injection(fixed=[pt]))
     fixed, rep = run_gpu(P)
     ofixed, orep = P.oracle_ft(tr, tc, bk, injections=[dict(pt, site=O.SITE_ACCUM)])
-    assert report_summary(rep) == report_summary(orep) == (4, 1, 1, 0, 0, 0)
+    assert report_summary(rep) == report_summary(orep) == (nt, 1, 1, 0, 0, 0)
     assert record_set(rep) == record_set(orep) == [(i, j, fb.KIND_CORRECTED)]
     r = rep.records()[0]
     assert abs(r.delta_row) > r.tau_row and abs(r.delta_col) > r.tau_col
@@ -91,11 +103,11 @@ def test_config1_256_fault_free_and_bit52_flip(engine):
     assert r.value_after == clean[i, j] and r.value_before != clean[i, j]
 
 
-@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
 @pytest.mark.parametrize("layout,ta,tb", COMBOS)
 @pytest.mark.parametrize("shape", [(300, 200, 77), (129, 257, 33), (1, 1, 1), (5, 300, 1000)])
 def test_layouts_and_ragged_shapes_match_oracle(engine, layout, ta, tb, shape):
-    fb.ftblas_set_fp64_engine(engine)
+    use(engine)
     M, N, K = shape
     P = Problem(M, N, K, layout, ta, tb, alpha=1.5, beta=0.5, seed=7 + M + N + K, pad="even")
     got, rep = run_gpu(P)
@@ -107,12 +119,12 @@ def test_layouts_and_ragged_shapes_match_oracle(engine, layout, ta, tb, shape):
     assert P.normalized_error(got, ref) <= TOL
 
 
-@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
 @pytest.mark.parametrize("layout", [O.COL_MAJOR, O.ROW_MAJOR])
 def test_seeded_draw_parity_over_launches(engine, layout):
     """The library's seeded draw and the oracle's (each its own SplitMix64) pick the same
     points; every launch detects, locates and corrects exactly what the oracle does."""
-    fb.ftblas_set_fp64_engine(engine)
+    use(engine)
     P = Problem(520, 390, 200, layout, O.NO_TRANS, O.TRANS, alpha=1.5, beta=0.5, seed=11)
     tr, tc, bk = tile_of(P)
     clean, _ = run_gpu(P)
@@ -136,9 +148,9 @@ def test_seeded_draw_parity_over_launches(engine, layout):
     assert fb.ftblas_injection_launch_count() == 4
 
 
-@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
 def test_output_checksum_and_multiple_error_sites(engine):
-    fb.ftblas_set_fp64_engine(engine)
+    use(engine)
     P = Problem(256, 256, 96, alpha=1.0, beta=1.0, seed=5)
     tr, tc, bk = tile_of(P)
     clean, _ = run_gpu(P)
@@ -163,11 +175,11 @@ def test_output_checksum_and_multiple_error_sites(engine):
             assert np.array_equal(got.view(np.uint64), clean.view(np.uint64))
 
 
-@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
 def test_infinite_output_flagged_against_infinite_threshold(engine):
     """An output flipped to +inf makes its row/column sums and thresholds infinite; it is
     still located and recomputed (same data as the oracle's pin)."""
-    fb.ftblas_set_fp64_engine(engine)
+    use(engine)
     P = Problem(8, 8, 8, alpha=1.0, beta=0.0, seed=51, pad="even")
     P.A = np.eye(8)
     P.B = S.randint(51, 0, 64, 2, 5).reshape(8, 8).astype(np.float64)
@@ -220,11 +232,11 @@ def test_quick_returns_on_gpu():
     assert P.normalized_error(got, P.oracle_plain()) <= TOL
 
 
-@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
 def test_untma_able_operands_use_the_fallback_loads(engine):
     """Odd leading dimensions and 8-byte-offset pointers cannot be described to TMA; the
     cooperative-load path must give the same answers."""
-    fb.ftblas_set_fp64_engine(engine)
+    use(engine)
     P = Problem(133, 71, 45, O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, alpha=1.5, beta=0.5, seed=9, pad=0)
     assert P.lda % 2 == 1  # 133: not a multiple of 16 bytes
     tr, tc, bk = tile_of(P)
@@ -248,9 +260,9 @@ def test_untma_able_operands_use_the_fallback_loads(engine):
     assert Q.normalized_error(got, Q.oracle_plain()) <= TOL
 
 
-@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
 def test_noabft_equals_protected_clean_output_bitwise(engine):
-    fb.ftblas_set_fp64_engine(engine)
+    use(engine)
     P = Problem(384, 256, 160, O.ROW_MAJOR, O.TRANS, O.NO_TRANS, alpha=1.5, beta=0.5, seed=12)
     ft_out, rep = run_gpu(P, protect=True)
     plain, _ = run_gpu(P, protect=False)
@@ -278,7 +290,8 @@ def test_host_buffer_entry_point_matches_device_path():
                                   ctypes.addressof(rep)))
     host_out = S.load(c, P.layout, P.M, P.N, P.ldc)
     assert np.array_equal(host_out.view(np.uint64), dev_out.view(np.uint64))
-    assert rep.tiles_checked == 2 * 2 and rep.detected == 0
+    tr, tc, _ = tile_of(P)
+    assert rep.tiles_checked == -(-P.M // tr) * -(-P.N // tc) and rep.detected == 0
     # padding between leading dimensions was not touched
     assert np.isnan(c.reshape(P.M, P.ldc)[:, P.N:]).all()
 
@@ -292,17 +305,17 @@ def test_clean_soak_no_false_alarms(seed):
     P = Problem(M, N, K, layout, ta, tb, alpha=float(rng.normal()), beta=float(rng.normal()), seed=seed,
                 dist="normal")
     for engine in ENGINES:
-        fb.ftblas_set_fp64_engine(engine)
+        use(engine)
         got, rep = run_gpu(P)
         assert rep.detected == 0 and rep.input_nonfinite == 0
     assert P.normalized_error(got, P.oracle_plain()) <= TOL
 
 
-@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("engine", [ENGINES[0], ENGINES[2]], ids=[ENGINE_IDS[0], ENGINE_IDS[2]])
 def test_full_size_8192_sampled_rows_and_faulted_tile(engine):
     """The benchmark's launch configuration (8192^3, alpha 1.5, beta 0.5) checked on sampled
     rows and on the whole faulted tile, with one accumulator flip."""
-    fb.ftblas_set_fp64_engine(engine)
+    use(engine)
     n = 8192
     P = Problem(n, n, n, alpha=1.5, beta=0.5, seed=20210602)
     tr, tc, bk = tile_of(P)
@@ -310,7 +323,7 @@ def test_full_size_8192_sampled_rows_and_faulted_tile(engine):
     fb.ftblas_set_injection(fb.make_injection(fixed=[dict(i=i, j=j, site=fb.SITE_ACCUM, bit=45)]))
     got, rep = run_gpu(P)
     assert fb.ftblas_last_launch_used_tma() == 1
-    assert report_summary(rep)[:5] == ((n // 128) ** 2, 1, 1, 0, 0)
+    assert report_summary(rep)[:5] == ((n // tr) * (n // tc), 1, 1, 0, 0)
     assert [(r.i, r.j) for r in rep.records()] == [(i, j)]
     rows = np.unique(np.concatenate([S.randint(5, 5, 6, 0, n - 1), [i]]))
     ref_rows = O.gemm_rows(P.layout, P.ta, P.tb, n, n, n, P.alpha, P.a, P.lda, P.b, P.ldb, P.beta, P.c, P.ldc, rows)
@@ -331,9 +344,9 @@ def _interval_off():
     fb.ftblas_set_verification_interval(0)
 
 
-@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
 def test_online_checks_leave_clean_runs_bitwise_unchanged(engine, _interval_off):
-    fb.ftblas_set_fp64_engine(engine)
+    use(engine)
     P = Problem(300, 260, 700, O.COL_MAJOR, O.NO_TRANS, O.TRANS, alpha=1.5, beta=0.5, seed=31)
     base, rep0 = run_gpu(P)
     fb.ftblas_set_verification_interval(128)
@@ -342,19 +355,19 @@ def test_online_checks_leave_clean_runs_bitwise_unchanged(engine, _interval_off)
     assert rep.detected == 0 and rep.tiles_checked == rep0.tiles_checked
 
 
-@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
 @pytest.mark.parametrize("layout", [O.COL_MAJOR, O.ROW_MAJOR])
 def test_online_checks_correct_two_faults_in_one_tile(engine, layout, _interval_off):
     """Two accumulator flips in one tile, in different intervals: with checks every 128
     products (4 k-tiles) both are corrected where they occur, as the oracle's interval mode
     does, and C equals the fault-free C of the same engine bit for bit; without online
     checks the pair is uncorrectable."""
-    fb.ftblas_set_fp64_engine(engine)
+    use(engine)
     P = Problem(256, 256, 512, layout, O.NO_TRANS, O.NO_TRANS, alpha=1.0, beta=0.0, seed=33)
     clean, _ = run_gpu(P)
     tr, tc, bk = tile_of(P)
     pts = [dict(i=5, j=7, site=fb.SITE_ACCUM, mode=fb.MODE_BITFLIP, bit=55, kt=2),
-           dict(i=70, j=90, site=fb.SITE_ACCUM, mode=fb.MODE_BITFLIP, bit=58, kt=9),
+           dict(i=40, j=50, site=fb.SITE_ACCUM, mode=fb.MODE_BITFLIP, bit=58, kt=9),  # same tile as (5, 7)
            dict(i=200, j=140, site=fb.SITE_ACCUM, mode=fb.MODE_BITFLIP, bit=52, kt=5)]
     fb.ftblas_set_injection(fb.make_injection(fixed=pts))
     got_end, rep_end = run_gpu(P)

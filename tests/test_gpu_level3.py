@@ -34,8 +34,8 @@ def dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-def tile(layout):
-    return fb.ftblas_verification_tile(layout, fb.R_64F, 1, 1, 1)
+def tile(layout, M, N, K):
+    return fb.ftblas_verification_tile(layout, fb.R_64F, M, N, K)
 
 
 def norm_err(got, ref, A, B, K):
@@ -47,7 +47,7 @@ def oracle_gemm(layout, M, N, K, alpha, A, B, beta, C, inj=()):
     a, lda = S.store(A, layout)
     b, ldb = S.store(B, layout)
     c, ldc = S.store(C, layout)
-    tr, tc, bk = tile(layout)
+    tr, tc, bk = tile(layout, M, N, K)
     out, rep = O.ft_gemm(layout, O.NO_TRANS, O.NO_TRANS, M, N, K, alpha, a, lda, b, ldb, beta, c, ldc, tr, tc, bk,
                          injections=inj)
     return S.load(out, layout, M, N, ldc), rep
@@ -132,7 +132,7 @@ def test_dtrmm_matches_oracle(layout, side, uplo, transa, diag):
 @pytest.mark.parametrize("layout", [O.COL_MAJOR, O.ROW_MAJOR])
 def test_dtrmm_faults_located_like_the_oracle(layout):
     """Output and accumulator faults (the latter inside the tile's k-range) in FT-DTRMM,
-    side LEFT, upper: the tile of rows [128, 256) starts at k = 128 (k-tile 4)."""
+    side LEFT, upper: a tile starts at k = its first row (the tile of rows from 128 at k-tile 4)."""
     M, N = 384, 256
     A = S.uniform_matrix(53, 0, M, M)
     T = np.triu(A)
