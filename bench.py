@@ -104,8 +104,9 @@ def peaks():
 
 FP64_KERNEL_SOURCES = ("paper_2104_00897_gb300/csrc/ft_dgemm.cu", "paper_2104_00897_gb300/csrc/ft_device.cuh",
                        "paper_2104_00897_gb300/csrc/ft_internal.h")
-TC_KERNEL_SOURCES = ("paper_2104_00897_gb300/csrc/ft_gemm_tc.cu", "paper_2104_00897_gb300/csrc/ft_device.cuh",
-                     "paper_2104_00897_gb300/csrc/ft_internal.h", "paper_2104_00897_gb300/csrc/ft_tc.h")
+TC_KERNEL_SOURCES = ("paper_2104_00897_gb300/csrc/ft_gemm_tc.cu", "paper_2104_00897_gb300/csrc/ft_tc_elem.cuh",
+                     "paper_2104_00897_gb300/csrc/ft_device.cuh", "paper_2104_00897_gb300/csrc/ft_internal.h",
+                     "paper_2104_00897_gb300/csrc/ft_tc.h")
 
 
 def sources_sha256(paths):

@@ -341,6 +341,14 @@ int ftblas_last_cuda_error(void);
 /* Library version, e.g. "0.1.0". */
 const char* ftblas_version(void);
 
+/* Decode n FP8 E4M3 codes (device memory, one byte each, 8-byte aligned) to binary32
+ * (device memory, n floats) with the unpacking that the tensor-core path's encode kernel
+ * uses (eight codes per load, two per conversion instruction). A diagnostic, so that tests
+ * can compare it code by code with the format's definition (bias 7, subnormals at exponent
+ * field 0, S.1111.111 = NaN). Asynchronous on `stream`. Returns 0, -p for an invalid
+ * argument p (null or misaligned pointer with n > 0, n < 0), or FTBLAS_STATUS_CUDA_ERROR. */
+int ftblas_decode_e4m3(const void* codes, float* out, int64_t n, void* stream);
+
 /* Device time of the product kernels, for measurement. After ftblas_kernel_timing_begin,
  * every GEMM call (any entry point, protected or not) records a pair of CUDA events on its
  * stream around its product kernel only: the encode, resolve and scaling kernels and the

@@ -105,6 +105,7 @@ SIGNATURES = {
     "ftblas_last_cuda_error": (C.c_int, []),
     "ftblas_last_launch_used_tma": (C.c_int, []),
     "ftblas_version": (C.c_char_p, []),
+    "ftblas_decode_e4m3": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "ftblas_kernel_timing_begin": (C.c_int, []),
     "ftblas_kernel_timing_end": (C.c_int, [C.c_void_p, C.c_void_p]),
 }
@@ -238,6 +239,10 @@ def ftblas_last_launch_used_tma():
 
 def ftblas_version():
     return _call("ftblas_version").decode()
+
+
+def ftblas_decode_e4m3(codes, out, n, stream=None):
+    return _call("ftblas_decode_e4m3", codes, out, int(n), stream)
 
 
 # ------------------------------------------------------------------ helpers

@@ -34,6 +34,7 @@
 #include "ft_device.cuh"
 #include "ft_internal.h"
 #include "ft_tc.h"
+#include "ft_tc_elem.cuh"
 
 namespace ftk {
 
@@ -67,81 +68,6 @@ struct __align__(1024) TcSmem {
   double pred_row;               // predicted row checksum of the first flagged row
   float cin_col[4][BNM];         // per-warp partial column sums of C_in (beta != 0)
   float cin_col_abs[4][BNM];
-};
-
-__device__ __forceinline__ float bf16_to_f32(uint16_t b) { return __uint_as_float(static_cast<uint32_t>(b) << 16); }
-
-__device__ __forceinline__ float e4m3_to_f32(uint8_t b) {
-  return __half2float(__half(__nv_cvt_fp8_to_halfraw(static_cast<__nv_fp8_storage_t>(b), __NV_E4M3)));
-}
-
-// Input element kinds of the tensor-core path.
-//   kBytes     storage bytes per element
-//   kPieces    checksum columns holding the pieces of B e (rows 0 .. kPieces-1 of a block)
-//   kPieceSum  bound of sum_p |piece_p| / |B e| (for the threshold's prediction part)
-// BF16: B e as hi + mid + lo bfloat16 (exact for a binary32 value), scale 1.
-// E4M3: B e as 16 e4m3 pieces with fixed scales 2^(9 - 4p): each piece is the nearest e4m3
-//   of what the previous ones leave (subnormals flushed and carried), so |B e| <= 240 * 448
-//   fits the first piece and the pieces hold B e to far below binary32 resolution.
-template <int KIND> struct Elem;
-template <> struct Elem<0> {
-  static constexpr int kBytes = 2, kPieces = 3;
-  static constexpr float kPieceSum = 1.0078125f;
-  // Eight consecutive elements of one K-contiguous line from k (a multiple of 8), zero
-  // at and beyond K; one 16-byte load (aligned: ld is a multiple of 8 elements, bases
-  // 16-byte aligned).
-  using Raw = uint4;
-  static __device__ __forceinline__ Raw zero() { return make_uint4(0u, 0u, 0u, 0u); }
-  static __device__ __forceinline__ Raw load_raw(const void* line, int64_t k, int32_t K) {
-    const uint16_t* l = static_cast<const uint16_t*>(line);
-    if (k + 8 <= K) return *reinterpret_cast<const uint4*>(l + k);
-    uint32_t t[4] = {0u, 0u, 0u, 0u};
-    for (int q = 0; q < 8; ++q)
-      if (k + q < K) t[q >> 1] |= (uint32_t)l[k + q] << (16 * (q & 1));
-    return make_uint4(t[0], t[1], t[2], t[3]);
-  }
-  static __device__ __forceinline__ void load8(const void* line, int64_t k, int32_t K, float (&x)[8]) {
-    unpack(load_raw(line, k, K), x);
-  }
-  static __device__ __forceinline__ void unpack(const Raw w, float (&x)[8]) {
-    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      x[2 * h] = __uint_as_float(ws[h] << 16);
-      x[2 * h + 1] = __uint_as_float(ws[h] & 0xffff0000u);
-    }
-  }
-  static __device__ __forceinline__ float at(const void* line, int64_t k) {
-    return bf16_to_f32(static_cast<const uint16_t*>(line)[k]);
-  }
-};
-template <> struct Elem<1> {
-  static constexpr int kBytes = 1, kPieces = 16;
-  static constexpr float kPieceSum = 1.25f;
-  // as above with one 8-byte load (ld a multiple of 16 elements)
-  using Raw = uint2;
-  static __device__ __forceinline__ Raw zero() { return make_uint2(0u, 0u); }
-  static __device__ __forceinline__ Raw load_raw(const void* line, int64_t k, int32_t K) {
-    const uint8_t* l = static_cast<const uint8_t*>(line);
-    if (k + 8 <= K) return *reinterpret_cast<const uint2*>(l + k);
-    uint32_t t[2] = {0u, 0u};
-    for (int q = 0; q < 8; ++q)
-      if (k + q < K) t[q >> 2] |= (uint32_t)l[k + q] << (8 * (q & 3));
-    return make_uint2(t[0], t[1]);
-  }
-  static __device__ __forceinline__ void load8(const void* line, int64_t k, int32_t K, float (&x)[8]) {
-    unpack(load_raw(line, k, K), x);
-  }
-  static __device__ __forceinline__ void unpack(const Raw w, float (&x)[8]) {
-    const uint32_t ws[2] = {w.x, w.y};
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) x[4 * h + b] = e4m3_to_f32(static_cast<uint8_t>(ws[h] >> (8 * b)));
-  }
-  static __device__ __forceinline__ float at(const void* line, int64_t k) {
-    return e4m3_to_f32(static_cast<const uint8_t*>(line)[k]);
-  }
 };
 
 // alpha times the per-tensor scales of FP8 operands (device values; absent scales are 1)
@@ -746,183 +672,6 @@ __global__ void __launch_bounds__(kResolveWarps * 32) tc_resolve_kernel(const __
   }
 }
 
-// ---------------------------------------------------------------------------------------
-// Encode pre-pass (bandwidth-bound): one read of A and one read of B. Kernel-frame A is
-// M x K and B is K x N, both K-contiguous, so each is a set of K-contiguous lines: the
-// rows of A, the columns of B. A CTA takes a block of L lines (the 128 rows of a tile of
-// A, the 240 columns of a tile of B) and ENC_KC consecutive k. Lane l of warp w loads
-// k0 + 8l .. k0 + 8l + 7 (one 16- or 8-byte load per line) of lines w, w + 8, w + 16, ...;
-// the eight warps' partial sums meet in shared memory.
-// Sums over a block are plain binary32 sums: their rounding, at most gamma_L(2^-24) times
-// the sum of magnitudes in any order, is a term of the thresholds. Sums of magnitudes round
-// upward, so they bound the exact sums.
-// ---------------------------------------------------------------------------------------
-constexpr int ENC_KC = 256;   // k per CTA: 32 lanes x 8
-constexpr int ENC_WARPS = 8;
-
-// Lane l holds la[u], a partial sum for line u of a group of 8 lines. Returns the upward
-// sum over the 32 lanes of line (l >> 2): recursive halving, 9 shuffles.
-__device__ __forceinline__ float reduce_scatter8_up(const float (&la)[8], int lane) {
-  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
-  float v4[4], v2[2];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const float keep = h16 ? la[4 + j] : la[j], send = h16 ? la[j] : la[4 + j];
-    v4[j] = __fadd_ru(keep, __shfl_xor_sync(0xffffffffu, send, 16));
-  }
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    const float keep = h8 ? v4[2 + j] : v4[j], send = h8 ? v4[j] : v4[2 + j];
-    v2[j] = __fadd_ru(keep, __shfl_xor_sync(0xffffffffu, send, 8));
-  }
-  float v = __fadd_ru(h4 ? v2[1] : v2[0], __shfl_xor_sync(0xffffffffu, h4 ? v2[0] : v2[1], 4));
-  v = __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, 2));
-  return __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, 1));
-}
-
-struct EncArgs {
-  const void* X; int64_t ld;
-  int32_t nlines, K, L;
-  int32_t nkc;             // k-chunks per line block
-  float* rowAbsA;          // rows pass: [M] upward sum_k |A(i,k)|, by the block's last k-chunk
-  unsigned* rowdone;       // rows pass: [nblocks] k-chunks finished (zeroed before the launch)
-  float* sum;              // rows pass: [nblocks][pitch] e^T A per block
-  float* abs_sum;          // rows pass: [nblocks][pitch] upward sum_{i in block} |A(i,k)|
-  int64_t pitch;           // also the checksum operand's row pitch (elements)
-  TcPending* pend;         // rows pass: its tile count is zeroed before the GEMM
-  float* line_part;        // rows pass: [nkc][M] upward sum of |A(i,k)| over one k-chunk
-  float* maxAbsBe;         // [nblocks of B]
-  void* chk;               // columns pass: pieces of B e in rows J*16 + p (unused rows zero)
-};
-
-// Shared memory of one encode CTA, declared once per kernel (both roles use it): the
-// float4 stores into the reduction arrays need their 16-byte alignment.
-struct __align__(16) EncSmem {
-  float red_s[ENC_WARPS][ENC_KC];
-  float red_a[ENC_WARPS][ENC_KC];
-  int last_chunk;
-};
-
-template <bool kRowsOfA, int KIND>
-__device__ __forceinline__ void encode_block(const EncArgs& g, int blk, int kc, EncSmem& sm) {
-  using E = Elem<KIND>;
-  auto& red_s = sm.red_s;
-  auto& red_a = sm.red_a;
-  int& last_chunk = sm.last_chunk;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t line0 = (int64_t)blk * g.L;
-  const int nI = (int)min((int64_t)g.L, (int64_t)g.nlines - line0);
-  const int64_t k = (int64_t)kc * ENC_KC + lane * 8;
-  const uint8_t* X = static_cast<const uint8_t*>(g.X);
-  float s[8], a[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) { s[q] = 0.f; a[q] = 0.f; }
-  const int T = (nI + ENC_WARPS - 1) / ENC_WARPS;  // lines per warp, rounded up
-  for (int t0 = 0; t0 < T; t0 += 8) {
-    typename E::Raw raw[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int l = warp + ENC_WARPS * (t0 + u);
-      raw[u] = (l < nI && k < g.K) ? E::load_raw(X + (line0 + l) * g.ld * E::kBytes, k, g.K) : E::zero();
-    }
-    float la[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      float x[8];
-      E::unpack(raw[u], x);
-      float lsum = 0.f;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        s[q] += x[q];
-        a[q] = __fadd_ru(a[q], fabsf(x[q]));
-        if (kRowsOfA) lsum = __fadd_ru(lsum, fabsf(x[q]));
-      }
-      la[u] = lsum;
-    }
-    if (kRowsOfA) {
-      const float v = reduce_scatter8_up(la, lane);
-      const int l = warp + ENC_WARPS * (t0 + (lane >> 2));
-      if ((lane & 3) == 0 && l < nI) g.line_part[(int64_t)kc * g.nlines + line0 + l] = v;
-    }
-  }
-  *reinterpret_cast<float4*>(&red_s[warp][lane * 8]) = make_float4(s[0], s[1], s[2], s[3]);
-  *reinterpret_cast<float4*>(&red_s[warp][lane * 8 + 4]) = make_float4(s[4], s[5], s[6], s[7]);
-  *reinterpret_cast<float4*>(&red_a[warp][lane * 8]) = make_float4(a[0], a[1], a[2], a[3]);
-  *reinterpret_cast<float4*>(&red_a[warp][lane * 8 + 4]) = make_float4(a[4], a[5], a[6], a[7]);
-  __syncthreads();
-  const int tk = threadIdx.x;
-  float S = 0.f, Aab = 0.f;
-#pragma unroll
-  for (int w = 0; w < ENC_WARPS; ++w) { S += red_s[w][tk]; Aab = __fadd_ru(Aab, red_a[w][tk]); }
-  const int64_t kk = (int64_t)kc * ENC_KC + tk;
-  if (kRowsOfA) {
-    if (kk < g.K) {
-      g.sum[(int64_t)blk * g.pitch + kk] = S;
-      g.abs_sum[(int64_t)blk * g.pitch + kk] = Aab;
-    }
-    if (blk == 0 && kc == 0 && tk == 0) g.pend->count = 0u;
-    // the line block's last k-chunk to finish sums the per-chunk partials of its rows
-    // (in chunk order: the result does not depend on which chunk finished last)
-    __threadfence();
-    __syncthreads();
-    if (tk == 0) last_chunk = atomicAdd(&g.rowdone[blk], 1u) == (unsigned)(g.nkc - 1);
-    __syncthreads();
-    if (last_chunk) {
-      __threadfence();
-      if (tk < nI) {
-        float a2 = 0.f;
-        for (int c2 = 0; c2 < g.nkc; ++c2) a2 = __fadd_ru(a2, __ldcg(&g.line_part[(int64_t)c2 * g.nlines + line0 + tk]));
-        g.rowAbsA[line0 + tk] = a2;
-      }
-    }
-  } else {
-    if (kk < g.K) {
-      if (KIND == 0) {
-        // three bfloat16 pieces, each the nearest bfloat16 of what the previous ones leave:
-        // together they hold the binary32 sum exactly (8 + 8 + 8 significand bits)
-        const __nv_bfloat16 h = __float2bfloat16_rn(S);
-        const float r1 = S - __bfloat162float(h);
-        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(m));
-        uint16_t* col = static_cast<uint16_t*>(g.chk) + (int64_t)blk * CHK_ROWS * g.pitch + kk;
-        col[0] = __bfloat16_as_ushort(h);
-        col[g.pitch] = __bfloat16_as_ushort(m);
-        col[2 * g.pitch] = __bfloat16_as_ushort(lo);
-#pragma unroll
-        for (int r = 3; r < CHK_ROWS; ++r) col[r * g.pitch] = 0;
-      } else {
-        // sixteen e4m3 pieces with scales 2^(9 - 4p): piece p is the nearest e4m3 of
-        // r / 2^(9 - 4p), r what the previous pieces leave; a subnormal piece is flushed to
-        // zero and its value carried. |S| <= 240 * 448 < 256 * 2^9, and each remainder is at
-        // most half an e4m3 unit of the piece before, so every r / 2^(9 - 4p) stays within
-        // +-256, and r - piece is exact (the two are within a factor of two).
-        uint8_t* col = static_cast<uint8_t*>(g.chk) + (int64_t)blk * CHK_ROWS * g.pitch + kk;
-        float r = S, inv = 0x1p-9f, sc = 0x1p9f;
-#pragma unroll
-        for (int pc = 0; pc < Elem<1>::kPieces; ++pc, inv *= 16.f, sc *= 0.0625f) {
-          __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(r * inv, __NV_SATFINITE, __NV_E4M3);
-          if ((q & 0x78u) == 0) q = 0;
-          col[pc * g.pitch] = q;
-          r -= e4m3_to_f32(q) * sc;
-        }
-      }
-    }
-    float mx = kk < g.K ? Aab : 0.f;
-#pragma unroll
-    for (int w = 16; w >= 1; w >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, w));
-    if (lane == 0) atomicMax(reinterpret_cast<unsigned int*>(&g.maxAbsBe[blk]), __float_as_uint(mx));
-  }
-}
-
-// One launch for both operands: blocks x < nMb encode row blocks of A, the rest column
-// blocks of B, so the two reads overlap.
-template <int KIND>
-__global__ void __launch_bounds__(256) encode_kernel(EncArgs ga, EncArgs gb, int nMb) {
-  __shared__ EncSmem sm;
-  if ((int)blockIdx.x < nMb) encode_block<true, KIND>(ga, blockIdx.x, blockIdx.y, sm);
-  else encode_block<false, KIND>(gb, blockIdx.x - nMb, blockIdx.y, sm);
-}
-
 // C = beta C over an M x N column-major FP32 matrix (beta == 0 writes zeros: C is not read).
 __global__ void scale_f32_kernel(float* C, int64_t ldc, int32_t M, int32_t N, float beta) {
   const int64_t total = (int64_t)M * N;
@@ -934,61 +683,6 @@ __global__ void scale_f32_kernel(float* C, int64_t ldc, int32_t M, int32_t N, fl
 }
 
 }  // namespace
-
-int64_t tc_kpitch(int32_t K) { return (K + 15) / 16 * 16; }
-
-size_t tc_workspace_bytes(int32_t M, int32_t N, int32_t K, int kind) {
-  const int64_t nMb = (M + BM - 1) / BM, nNb = (N + kTcBNProt - 1) / kTcBNProt;
-  const int64_t kpitch = tc_kpitch(K), nkc = (K + ENC_KC - 1) / ENC_KC;
-  const int64_t eb = kind == 0 ? 2 : 1;
-  auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
-  return up(nNb * CHK_ROWS * kpitch * eb) + up(nMb * kpitch * 4) + up(nMb * kpitch * 4) + up(M * 4) +
-         up(nNb * 4 + nMb * 4) + up(nkc * M * 4) + up((int64_t)sizeof(TcPending));
-}
-
-TcWorkspace tc_workspace_carve(void* base, int32_t M, int32_t N, int32_t K, int kind) {
-  const int64_t nMb = (M + BM - 1) / BM, nNb = (N + kTcBNProt - 1) / kTcBNProt;
-  const int64_t kpitch = tc_kpitch(K), nkc = (K + ENC_KC - 1) / ENC_KC;
-  const int64_t eb = kind == 0 ? 2 : 1;
-  auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
-  char* c = static_cast<char*>(base);
-  TcWorkspace w;
-  w.chk = c; c += up(nNb * CHK_ROWS * kpitch * eb);
-  w.kpitch = kpitch;
-  w.sA = reinterpret_cast<float*>(c); c += up(nMb * kpitch * 4);
-  w.absSA = reinterpret_cast<float*>(c); c += up(nMb * kpitch * 4);
-  w.rowAbsA = reinterpret_cast<float*>(c); c += up(M * 4);
-  w.maxAbsBe = reinterpret_cast<float*>(c);
-  w.rowdone = reinterpret_cast<unsigned*>(w.maxAbsBe + nNb);
-  w.zero_bytes = (size_t)(nNb * 4 + nMb * 4);  // maxAbsBe and rowdone, cleared before the encode
-  c += up(nNb * 4 + nMb * 4);
-  w.rowPart = reinterpret_cast<float*>(c); c += up(nkc * M * 4);
-  w.pend = reinterpret_cast<TcPending*>(c); c += up((int64_t)sizeof(TcPending));
-  w.bytes = static_cast<size_t>(c - static_cast<char*>(base));
-  return w;
-}
-
-template <int KIND>
-static void launch_encode_kind(const TcParams& p, const TcWorkspace& w, cudaStream_t st) {
-  const int nMb = (p.M + BM - 1) / BM, nNb = (p.N + kTcBNProt - 1) / kTcBNProt, nkc = (p.K + ENC_KC - 1) / ENC_KC;
-  EncArgs ga, gb;
-  std::memset(&ga, 0, sizeof(ga));
-  ga.X = p.A; ga.ld = p.lda; ga.nlines = p.M; ga.K = p.K; ga.L = BM; ga.nkc = nkc;
-  ga.sum = w.sA; ga.abs_sum = w.absSA; ga.line_part = w.rowPart; ga.rowAbsA = w.rowAbsA; ga.rowdone = w.rowdone;
-  ga.pitch = w.kpitch; ga.pend = w.pend;
-  std::memset(&gb, 0, sizeof(gb));
-  gb.X = p.B; gb.ld = p.ldb; gb.nlines = p.N; gb.K = p.K; gb.L = kTcBNProt; gb.nkc = nkc;
-  gb.maxAbsBe = w.maxAbsBe; gb.chk = w.chk; gb.pitch = w.kpitch;
-  encode_kernel<KIND><<<dim3(nMb + nNb, nkc), ENC_WARPS * 32, 0, st>>>(ga, gb, nMb);
-}
-
-cudaError_t launch_tc_encode(const TcParams& p, const TcWorkspace& w, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(w.maxAbsBe, 0, w.zero_bytes, st);
-  if (e != cudaSuccess) return e;
-  if (p.kind == 0) launch_encode_kind<0>(p, w, st);
-  else launch_encode_kind<1>(p, w, st);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_scale_f32(float* C, int64_t ldc, int64_t M, int64_t N, float beta, cudaStream_t st) {
   if (M == 0 || N == 0) return cudaSuccess;

@@ -76,6 +76,8 @@ size_t tc_workspace_bytes(int32_t M, int32_t N, int32_t K, int kind);
 TcWorkspace tc_workspace_carve(void* base, int32_t M, int32_t N, int32_t K, int kind);
 cudaError_t launch_scale_f32(float* C, int64_t ldc, int64_t M, int64_t N, float beta, cudaStream_t st);
 cudaError_t launch_tc_encode(const TcParams& p, const TcWorkspace& w, cudaStream_t st);
+// out[i] = the encode's binary32 value of E4M3 code codes[i], i < n
+cudaError_t launch_decode_e4m3(const uint8_t* codes, float* out, int64_t n, cudaStream_t st);
 cudaError_t launch_tc_gemm(const TcParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmChk,
                            bool ft, cudaStream_t st);
 

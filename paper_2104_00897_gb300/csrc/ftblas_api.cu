@@ -927,6 +927,13 @@ int ftblas_last_launch_used_tma(void) { return g_last_used_tma; }
 
 const char* ftblas_version(void) { return "0.1.0"; }
 
+int ftblas_decode_e4m3(const void* codes, float* out, int64_t n, void* stream) {
+  if (n > 0 && (codes == nullptr || reinterpret_cast<uintptr_t>(codes) % 8 != 0)) return -1;
+  if (n > 0 && out == nullptr) return -2;
+  if (n < 0) return -3;
+  return record_cuda(launch_decode_e4m3(static_cast<const uint8_t*>(codes), out, n, static_cast<cudaStream_t>(stream)));
+}
+
 int ftblas_dgemm_unfused(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb, int64_t M, int64_t N,
                          int64_t K, double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
                          double beta, double* C, int64_t ldc, void* stream, ft_report_t* report) {

@@ -173,3 +173,40 @@ def test_fp8_row_scaled_clean_runs_have_no_false_alarm():
     _, orep = P.oracle(injections=pts, tiles=[(i // 128) + (j // 240) * ((512 + 127) // 128)])
     assert (rep.detected, rep.corrected) == (1, 1)
     assert record_set(rep) == record_set(orep)
+
+
+def e4m3_from_definition(code):
+    """Value of an E4M3 code from the format's definition (OCP 8-bit floating point: sign,
+    4 exponent bits biased by 7, 3 mantissa bits; exponent field 0 subnormal; S.1111.111
+    NaN; no infinities)."""
+    s, e, m = code >> 7, (code >> 3) & 15, code & 7
+    if e == 15 and m == 7:
+        return float("nan")
+    mag = (m / 8) * 2.0 ** -6 if e == 0 else (1 + m / 8) * 2.0 ** (e - 7)
+    return -mag if s else mag
+
+
+def test_e4m3_decoder_matches_the_format_definition_for_every_code():
+    """The encode's E4M3 unpacking (paired hardware conversions) against the definition,
+    code by code, and against torch's CPU float8_e4m3fn conversion; signed zeros and NaN
+    included; a ragged count (not a multiple of 8) too."""
+    codes = torch.arange(256, dtype=torch.int32).to(torch.uint8)
+    d_codes = codes.cuda()
+    out = torch.empty(256, dtype=torch.float32, device="cuda")
+    fb.check(fb.ftblas_decode_e4m3(d_codes.data_ptr(), out.data_ptr(), 256, torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    want = np.array([e4m3_from_definition(c) for c in range(256)], dtype=np.float32)
+    via_torch = codes.view(torch.float8_e4m3fn).float().numpy()
+    nan = np.isnan(want)
+    assert nan.sum() == 2 and np.array_equal(np.isnan(got), nan) and np.array_equal(np.isnan(via_torch), nan)
+    assert np.array_equal(got[~nan].view(np.uint32), want[~nan].view(np.uint32))
+    assert np.array_equal(via_torch[~nan].view(np.uint32), want[~nan].view(np.uint32))
+    assert got[0x80] == 0.0 and np.signbit(got[0x80]) and got[0x7E] == 448.0 and got[0x01] == 2.0 ** -9
+    part = torch.full((13,), -1.0, dtype=torch.float32, device="cuda")
+    fb.check(fb.ftblas_decode_e4m3(d_codes[24:].data_ptr(), part.data_ptr(), 13, None))
+    torch.cuda.synchronize()
+    assert np.array_equal(part.cpu().numpy().view(np.uint32), want[24:37].view(np.uint32))
+    assert fb.ftblas_decode_e4m3(None, out.data_ptr(), 1, None) == -1
+    assert fb.ftblas_decode_e4m3(d_codes[3:].data_ptr(), out.data_ptr(), 1, None) == -1
+    assert fb.ftblas_decode_e4m3(d_codes.data_ptr(), out.data_ptr(), -1, None) == -3
