@@ -9,14 +9,16 @@
 // tensor-core tile is 128 x 256 and the TMEM accumulator is double-buffered):
 //   warp 0      TMA producer: A (128 x 64) and B (N_data x 64) k-tiles into a 4-stage ring,
 //               128-byte swizzled, K-major. Protected launches put the checksum column of
-//               B^r = [B, Be] (Section II.A) into rows 240..255 of the same B stage: Be over
-//               the tile's 240 data columns, split into three BF16 pieces (hi, mid, lo) by a
-//               bandwidth-bound encode pre-pass.
+//               B^r = [B, Be] (Section II.A) into the last rows of the same B stage: Be over
+//               the tile's data columns, in pieces written by a bandwidth-bound encode
+//               pre-pass (ft_tc_encode.cu): BF16, 248 data columns and three bfloat16 pieces
+//               (hi, mid, lo) in rows 248..255; E4M3, 240 data columns and sixteen pieces in
+//               rows 240..255.
 //   warp 1      TMEM allocation and MMA issue (one thread): 4 x tcgen05.mma M128 N256 K16 per
 //               k-tile into one of two 256-column TMEM buffers, so the next tile's product
 //               overlaps the previous tile's epilogue. With the checksum column appended, the
-//               tensor core produces C^r = A (B e) in columns 240..242 with the product
-//               itself, at no extra instruction (6.7 % fewer data columns per tile).
+//               tensor core produces the pieces of C^r = A (B e) in the last columns with the
+//               product itself, at no extra instruction (8 or 16 of 256 columns per tile).
 //   warps 2..5  epilogue, one TMEM lane (= output row) per thread: C = alpha acc + beta C_in
 //               stored in FP32; C^r_ref(i) = sum_j C(i,j) in compensated binary32, compared
 //               in binary64 with the predicted checksum against a rigorous bound. Only in a
@@ -45,13 +47,13 @@ constexpr int BNM = 256;             // MMA N = TMEM columns = B stage rows
 constexpr int BKB = 128;             // k-tile depth in bytes (64 BF16 or 128 E4M3)
 constexpr int STAGES = 4;
 constexpr int NTHREADS = 192;
-constexpr int CHK_ROWS = kTcChkRows;  // 16
 constexpr uint32_t TMEM_COLS = 512;   // two accumulator buffers of 256 columns
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait; a whole tile takes ~0.1 ms
 
-template <bool FT>
+template <bool FT, int KIND>
 struct TcGeom {
-  static constexpr int BN = FT ? kTcBNProt : BNM;  // data columns per tile
+  static constexpr int BN = FT ? tc_bn_prot(KIND) : BNM;  // data columns per tile
+  static constexpr int CHK = FT ? tc_chk_rows(KIND) : 0;  // checksum rows after them in a B stage
 };
 
 struct __align__(1024) TcSmem {
@@ -178,14 +180,23 @@ __device__ void count_kind(const TcParams& p, int kind) {
   atomicAdd(ctr, 1ull);
 }
 
-// Persistent-tile order: groups of kGroupM row tiles sweep all column tiles, so the CTAs
-// resident at one time share A row panels and B column panels in L2.
+// Persistent-tile order: groups of kGroupM row tiles sweep the column tiles, so the CTAs
+// resident at one time share A row panels and B column panels in L2. The last column
+// block comes after all the others: when N is not a multiple of the tile width its tiles
+// are narrower and cheaper (narrow MMAs), and placed last they fill the final round of the
+// persistent CTAs instead of adding one.
 constexpr int kGroupM = 16;
 __device__ __forceinline__ void tile_coords(int t, int nMb, int nNb, int& mt, int& nt) {
-  const int group = t / (kGroupM * nNb);
+  const int ncols = nNb - 1;  // column blocks before the last
+  if (t >= nMb * ncols) {
+    mt = t - nMb * ncols;
+    nt = ncols;
+    return;
+  }
+  const int group = t / (kGroupM * ncols);
   const int first_m = group * kGroupM;
   const int gsize = min(kGroupM, nMb - first_m);
-  const int in_group = t - group * kGroupM * nNb;
+  const int in_group = t - group * kGroupM * ncols;
   mt = first_m + in_group % gsize;
   nt = in_group / gsize;
 }
@@ -197,7 +208,7 @@ template <bool FT, int KIND>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmChk, const __grid_constant__ TcParams p) {
-  constexpr int BN = TcGeom<FT>::BN;
+  constexpr int BN = TcGeom<FT, KIND>::BN, CHK = TcGeom<FT, KIND>::CHK;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TcSmem& sm = *reinterpret_cast<TcSmem*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -228,7 +239,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tma_prefetch_desc(&tmA);
       tma_prefetch_desc(&tmB);
       if (FT) tma_prefetch_desc(&tmChk);
-      const uint32_t bytes = (BM + BN + (FT ? CHK_ROWS : 0)) * BKB;
+      const uint32_t bytes = (BM + BN + CHK) * BKB;
       uint32_t it = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
@@ -241,7 +252,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int k0 = kt * bk_elems;
           tma_load_2d(sm.a[s], &tmA, &sm.full[s], k0, mt * BM);
           tma_load_2d(sm.b[s], &tmB, &sm.full[s], k0, nt * BN);
-          if (FT) tma_load_2d(sm.b[s] + BN * BKB, &tmChk, &sm.full[s], k0, nt * CHK_ROWS);
+          if (FT) tma_load_2d(sm.b[s] + BN * BKB, &tmChk, &sm.full[s], k0, nt * CHK);
         }
       }
     }
@@ -249,10 +260,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
       // kind::f16 with BF16 operands (format 1), or kind::f8f6f4 with E4M3 operands (format 0)
-      const uint32_t idesc = KIND == 0 ? umma_idesc(1, 1, BM, BNM) : umma_idesc(0, 0, BM, BNM);
+      constexpr uint32_t fmt = KIND == 0 ? 1u : 0u;
+      const uint32_t idesc = umma_idesc(fmt, fmt, BM, BNM);
+      // A ragged last column block runs narrower MMAs: N1 (its data columns rounded up to 16)
+      // over the first stage rows, and, protected, N = 16 over stage rows 240..255, which end
+      // with the checksum rows (the data rows among them are beyond N, zero-filled by TMA),
+      // into TMEM columns 240..255. The columns in between are left as they were; the
+      // epilogue uses only data columns below the tile's width and the checksum columns.
+      const int nJ_last = p.N - (nNb - 1) * BN;
+      const int n1_last = (nJ_last + 15) / 16 * 16;
+      const bool narrow_last = n1_last + (FT ? 16 : 0) < BNM;
+      const uint32_t idesc_n1 = umma_idesc(fmt, fmt, BM, narrow_last ? n1_last : BNM);
+      const uint32_t idesc_chk = umma_idesc(fmt, fmt, BM, 16);
       uint32_t it = 0, lt = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
+        int mt, nt;
+        tile_coords(tile, nMb, nNb, mt, nt);
+        const bool narrow = narrow_last && nt == nNb - 1;
         const uint32_t b = lt & 1, ub = lt >> 1;
         if (ub > 0 && !mbar_wait_bounded(&sm.tempty[b], (ub - 1) & 1, kWaitLimitNs)) { sm.timeout = 1; break; }
         tc_fence_after();
@@ -263,13 +288,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           tc_fence_after();
           const uint32_t a0 = smem_addr(sm.a[s]), b0 = smem_addr(sm.b[s]);
 #pragma unroll
-          for (int kk = 0; kk < BKB / 32; ++kk) {  // one MMA per 32 bytes of K
-            if (KIND == 0)
-              umma_bf16(dcol, umma_desc_sw128(a0 + kk * 32), umma_desc_sw128(b0 + kk * 32), idesc,
-                        (kt > 0 || kk > 0) ? 1u : 0u);
-            else
-              umma_f8(dcol, umma_desc_sw128(a0 + kk * 32), umma_desc_sw128(b0 + kk * 32), idesc,
-                      (kt > 0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < BKB / 32; ++kk) {  // one MMA (or two narrow ones) per 32 bytes of K
+            const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
+            const uint64_t ad = umma_desc_sw128(a0 + kk * 32), bd = umma_desc_sw128(b0 + kk * 32);
+            const uint64_t bd_chk = umma_desc_sw128(b0 + (BNM - 16) * BKB + kk * 32);
+            if (KIND == 0) {
+              umma_bf16(dcol, ad, bd, narrow ? idesc_n1 : idesc, accum);
+              if (FT && narrow) umma_bf16(dcol + (BNM - 16), ad, bd_chk, idesc_chk, accum);
+            } else {
+              umma_f8(dcol, ad, bd, narrow ? idesc_n1 : idesc, accum);
+              if (FT && narrow) umma_f8(dcol + (BNM - 16), ad, bd_chk, idesc_chk, accum);
+            }
           }
           umma_commit(&sm.empty[s]);
         }
@@ -310,8 +339,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       int inj_c = INT_MAX;  // next tile column of this row holding an injection point
       if (FT && p.inj.n > 0) inj_c = next_inj_col(p, gi, n0, nJ, -1);
       if (got) {
+        const int nch = (nJ + 7) / 8;  // chunks of 8 columns holding data (warp-uniform)
 #pragma unroll 1
-        for (int ch = 0; ch < (BN + 7) / 8; ++ch) {
+        for (int ch = 0; ch < nch; ++ch) {
           uint32_t v[8];
           __syncwarp();  // reconverge after the previous chunk's per-lane branches
           tmem_ld8(trow + ch * 8, v);
@@ -390,14 +420,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         const double ref = (double)rs + (double)rc;
         delta = ref - predicted;
-        // tau = |alpha| P (gamma_K(u_acc) (1 + s) + 2^-20 + gamma_240(2^-24)) + 2 u32 (sum|C| +
+        // tau = |alpha| P (gamma_K(u_acc) (1 + s) + 2^-20 + gamma_BN(2^-24)) + 2 u32 (sum|C| +
         // |beta| sum|C_in|), P an upper bound of sum_k |A(i,k)| sum_{j in tile} |B(k,j)|, s the
         // bound of sum_p |piece_p| / |B e| (the prediction's accumulation error; the
-        // reference row sum's is gamma_K(u_acc) P); the gamma_240(2^-24) term is the
-        // rounding of B e, a binary32 sum over the tile's columns.
+        // reference row sum's is gamma_K(u_acc) P); the gamma_BN(2^-24) term is the
+        // rounding of B e, a binary32 sum over the tile's BN columns.
         const float P = __fmul_ru(p.rowAbsA[gi], p.maxAbsBe[nt]);
         const float g = gamma32_up((float)p.K, p.u_acc);
-        const float genc = gamma32_up((float)kTcBNProt, 0x1p-24f);
+        const float genc = gamma32_up((float)BN, 0x1p-24f);
         const float prod = __fmul_ru(__fmul_ru(fabsf(alpha), P),
                                      __fadd_ru(__fadd_ru(__fmul_ru(g, 1.0f + E::kPieceSum), 0x1p-20f), genc));
         const float outp = __fmul_ru(0x1p-23f, __fadd_ru(rabs, __fmul_ru(fabsf(p.beta), cabs)));
@@ -469,7 +499,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // tile's last group classifies the tile and corrects it.
 // ---------------------------------------------------------------------------------------
 constexpr int kResolveWarps = 8;
-constexpr int kResolveItems = kTcBNProt;  // one column per work item
 
 struct ResolveShared {
   int last, first_col, first_elem;
@@ -646,6 +675,7 @@ template <int KIND>
 __global__ void __launch_bounds__(kResolveWarps * 32) tc_resolve_kernel(const __grid_constant__ TcParams p) {
   __shared__ ResolveShared sh;
   const float alpha = alpha_eff(p);
+  constexpr int kResolveItems = tc_bn_prot(KIND);  // one column of a pending tile per work item
   const unsigned npend = min(*reinterpret_cast<volatile const unsigned*>(&p.pend->count), (unsigned)kTcPendCap);
   const int items = (int)npend * kResolveItems;
   const bool beta_nz = p.beta != 0.0f;
@@ -653,8 +683,8 @@ __global__ void __launch_bounds__(kResolveWarps * 32) tc_resolve_kernel(const __
     TcPendingEntry& pe = p.pend->e[item / kResolveItems];
     const int cidx = item % kResolveItems;
     const int mt = pe.mt, nt = pe.nt;
-    const int m0 = mt * BM, n0 = nt * kTcBNProt;
-    const int nI = min(BM, p.M - m0), nJ = min(kTcBNProt, p.N - n0);
+    const int m0 = mt * BM, n0 = nt * kResolveItems;
+    const int nI = min(BM, p.M - m0), nJ = min(kResolveItems, p.N - n0);
     if (cidx < nJ) {
       if (pe.nr == 1 && !beta_nz) resolve_column<true, KIND>(p, alpha, pe, sh, mt, m0, n0, nI, cidx, beta_nz);
       else resolve_column<false, KIND>(p, alpha, pe, sh, mt, m0, n0, nI, cidx, beta_nz);
@@ -696,7 +726,7 @@ template <bool FT, int KIND>
 static cudaError_t launch_gemm_kind(const TcParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB,
                                     const CUtensorMap* tmChk, int sms, cudaStream_t st) {
   const size_t smem = sizeof(TcSmem);
-  const int bn = FT ? kTcBNProt : BNM;
+  const int bn = TcGeom<FT, KIND>::BN;
   const long long tiles = (long long)((p.M + BM - 1) / BM) * ((p.N + bn - 1) / bn);
   const int grid = (int)(tiles < sms ? tiles : sms);
   cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<FT, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -12,8 +12,13 @@ namespace ftk {
 
 constexpr int kTcBM = 128;       // tile rows (TMEM lanes)
 constexpr int kTcBN = 256;       // data columns per tile, unprotected (= MMA N)
-constexpr int kTcBNProt = 240;   // data columns per tile, protected: B^r = [B, Be] fills N = 256
-constexpr int kTcChkRows = 16;   // rows of the checksum operand per column block (pieces of B e)
+// Protected tiles: B^r = [B, Be] fills the MMA's N = 256 with the tile's data columns followed
+// by the rows of the checksum operand that hold the pieces of B e: three bfloat16 pieces in 8
+// rows (248 data columns), sixteen e4m3 pieces in 16 rows (240 data columns).
+constexpr int tc_chk_rows(int kind) { return kind == 0 ? 8 : 16; }
+constexpr int tc_bn_prot(int kind) { return kTcBN - tc_chk_rows(kind); }
+constexpr int kTcBNProtMax = 248;  // the larger tc_bn_prot: per-column arrays of a pending tile
+static_assert(tc_bn_prot(0) <= kTcBNProtMax && tc_bn_prot(1) <= kTcBNProtMax, "pending-tile arrays too small");
 
 // A tile whose row checksums mismatch, handed from the GEMM's epilogue to the resolve pass
 // (lazy column side, row recompute, classification and correction), which runs after
@@ -24,12 +29,12 @@ struct TcPendingEntry {
   double delta_row, tau_row, pred_row;
   uint32_t done;                 // column groups finished (the last one classifies)
   int32_t pad_;
-  double cin_sum[kTcBNProt];     // beta != 0: sum_i C_in(i,j) over the tile (C_in is overwritten)
-  float cin_abs[kTcBNProt];      //            upward sum_i |C_in(i,j)|
-  double col_delta[kTcBNProt];   // C^c_ref - C^c per column
-  double col_tau[kTcBNProt];
-  uint8_t col_flag[kTcBNProt];   // column mismatches
-  uint8_t elem_flag[kTcBNProt];  // row recompute: element mismatches of the flagged row
+  double cin_sum[kTcBNProtMax];     // beta != 0: sum_i C_in(i,j) over the tile (C_in is overwritten)
+  float cin_abs[kTcBNProtMax];      //            upward sum_i |C_in(i,j)|
+  double col_delta[kTcBNProtMax];   // C^c_ref - C^c per column
+  double col_tau[kTcBNProtMax];
+  uint8_t col_flag[kTcBNProtMax];   // column mismatches
+  uint8_t elem_flag[kTcBNProtMax];  // row recompute: element mismatches of the flagged row
 };
 struct TcPending {
   uint32_t count;                // tiles pushed (may exceed kTcPendCap; the rest are not located)

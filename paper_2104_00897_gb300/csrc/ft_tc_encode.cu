@@ -14,13 +14,12 @@ namespace ftk {
 namespace {
 
 constexpr int BM = kTcBM;             // 128 rows of A per block (the tile's rows)
-constexpr int CHK_ROWS = kTcChkRows;  // 16 checksum-operand rows per column block of B
 
 // ---------------------------------------------------------------------------------------
 // Encode pre-pass (bandwidth-bound): one read of A and one read of B. Kernel-frame A is
 // M x K and B is K x N, both K-contiguous, so each is a set of K-contiguous lines: the
 // rows of A, the columns of B. A CTA takes a block of L lines (the 128 rows of a tile of
-// A, the 240 columns of a tile of B) and ENC_KC consecutive k. Lane l of warp w loads
+// A, the 248 (BF16) or 240 (E4M3) columns of a tile of B) and ENC_KC consecutive k. Lane l of warp w loads
 // k0 + 8l .. k0 + 8l + 7 (one 16- or 8-byte load per line) of lines w, w + 8, w + 16, ...;
 // the eight warps' partial sums meet in shared memory.
 // Sums over a block are plain binary32 sums: their rounding, at most gamma_L(2^-24) times
@@ -159,19 +158,20 @@ __device__ __forceinline__ void encode_block(const EncArgs& g, int blk, int kc, 
         const float r1 = S - __bfloat162float(h);
         const __nv_bfloat16 m = __float2bfloat16_rn(r1);
         const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(m));
-        uint16_t* col = static_cast<uint16_t*>(g.chk) + (int64_t)blk * CHK_ROWS * g.pitch + kk;
+        constexpr int kChk = tc_chk_rows(0);
+        uint16_t* col = static_cast<uint16_t*>(g.chk) + (int64_t)blk * kChk * g.pitch + kk;
         col[0] = __bfloat16_as_ushort(h);
         col[g.pitch] = __bfloat16_as_ushort(m);
         col[2 * g.pitch] = __bfloat16_as_ushort(lo);
 #pragma unroll
-        for (int r = 3; r < CHK_ROWS; ++r) col[r * g.pitch] = 0;
+        for (int r = 3; r < kChk; ++r) col[r * g.pitch] = 0;
       } else {
         // sixteen e4m3 pieces with scales 2^(9 - 4p): piece p is the nearest e4m3 of
         // r / 2^(9 - 4p), r what the previous pieces leave; a subnormal piece is flushed to
         // zero and its value carried. |S| <= 240 * 448 < 256 * 2^9, and each remainder is at
         // most half an e4m3 unit of the piece before, so every r / 2^(9 - 4p) stays within
         // +-256, and r - piece is exact (the two are within a factor of two).
-        uint8_t* col = static_cast<uint8_t*>(g.chk) + (int64_t)blk * CHK_ROWS * g.pitch + kk;
+        uint8_t* col = static_cast<uint8_t*>(g.chk) + (int64_t)blk * tc_chk_rows(1) * g.pitch + kk;
         float r = S, inv = 0x1p-9f, sc = 0x1p9f;
 #pragma unroll
         for (int pc = 0; pc < Elem<1>::kPieces; ++pc, inv *= 16.f, sc *= 0.0625f) {
@@ -223,22 +223,24 @@ cudaError_t launch_decode_e4m3(const uint8_t* codes, float* out, int64_t n, cuda
 int64_t tc_kpitch(int32_t K) { return (K + 15) / 16 * 16; }
 
 size_t tc_workspace_bytes(int32_t M, int32_t N, int32_t K, int kind) {
-  const int64_t nMb = (M + BM - 1) / BM, nNb = (N + kTcBNProt - 1) / kTcBNProt;
+  const int64_t bn = tc_bn_prot(kind), chk = tc_chk_rows(kind);
+  const int64_t nMb = (M + BM - 1) / BM, nNb = (N + bn - 1) / bn;
   const int64_t kpitch = tc_kpitch(K), nkc = (K + ENC_KC - 1) / ENC_KC;
   const int64_t eb = kind == 0 ? 2 : 1;
   auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
-  return up(nNb * CHK_ROWS * kpitch * eb) + up(nMb * kpitch * 4) + up(nMb * kpitch * 4) + up(M * 4) +
+  return up(nNb * chk * kpitch * eb) + up(nMb * kpitch * 4) + up(nMb * kpitch * 4) + up(M * 4) +
          up(nNb * 4 + nMb * 4) + up(nkc * M * 4) + up((int64_t)sizeof(TcPending));
 }
 
 TcWorkspace tc_workspace_carve(void* base, int32_t M, int32_t N, int32_t K, int kind) {
-  const int64_t nMb = (M + BM - 1) / BM, nNb = (N + kTcBNProt - 1) / kTcBNProt;
+  const int64_t bn = tc_bn_prot(kind), chk = tc_chk_rows(kind);
+  const int64_t nMb = (M + BM - 1) / BM, nNb = (N + bn - 1) / bn;
   const int64_t kpitch = tc_kpitch(K), nkc = (K + ENC_KC - 1) / ENC_KC;
   const int64_t eb = kind == 0 ? 2 : 1;
   auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
   char* c = static_cast<char*>(base);
   TcWorkspace w;
-  w.chk = c; c += up(nNb * CHK_ROWS * kpitch * eb);
+  w.chk = c; c += up(nNb * chk * kpitch * eb);
   w.kpitch = kpitch;
   w.sA = reinterpret_cast<float*>(c); c += up(nMb * kpitch * 4);
   w.absSA = reinterpret_cast<float*>(c); c += up(nMb * kpitch * 4);
@@ -255,14 +257,15 @@ TcWorkspace tc_workspace_carve(void* base, int32_t M, int32_t N, int32_t K, int 
 
 template <int KIND>
 static void launch_encode_kind(const TcParams& p, const TcWorkspace& w, cudaStream_t st) {
-  const int nMb = (p.M + BM - 1) / BM, nNb = (p.N + kTcBNProt - 1) / kTcBNProt, nkc = (p.K + ENC_KC - 1) / ENC_KC;
+  constexpr int bn = tc_bn_prot(KIND);
+  const int nMb = (p.M + BM - 1) / BM, nNb = (p.N + bn - 1) / bn, nkc = (p.K + ENC_KC - 1) / ENC_KC;
   EncArgs ga, gb;
   std::memset(&ga, 0, sizeof(ga));
   ga.X = p.A; ga.ld = p.lda; ga.nlines = p.M; ga.K = p.K; ga.L = BM; ga.nkc = nkc;
   ga.sum = w.sA; ga.abs_sum = w.absSA; ga.line_part = w.rowPart; ga.rowAbsA = w.rowAbsA; ga.rowdone = w.rowdone;
   ga.pitch = w.kpitch; ga.pend = w.pend;
   std::memset(&gb, 0, sizeof(gb));
-  gb.X = p.B; gb.ld = p.ldb; gb.nlines = p.N; gb.K = p.K; gb.L = kTcBNProt; gb.nkc = nkc;
+  gb.X = p.B; gb.ld = p.ldb; gb.nlines = p.N; gb.K = p.K; gb.L = bn; gb.nkc = nkc;
   gb.maxAbsBe = w.maxAbsBe; gb.chk = w.chk; gb.pitch = w.kpitch;
   encode_kernel<KIND><<<dim3(nMb + nNb, nkc), ENC_WARPS * 32, 0, st>>>(ga, gb, nMb);
 }

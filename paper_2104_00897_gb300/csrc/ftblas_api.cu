@@ -594,8 +594,9 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   if (!need_ab) return record_cuda(launch_scale_f32(static_cast<float*>(C), ldc, f.M, f.N, be, st));  // C = beta C
   CallerPoint pts[kMaxInject];
   int npts = 0;
+  const int64_t bnp = tc_bn_prot(kind), chk_rows = tc_chk_rows(kind);  // protected tile width, checksum rows
   if (ft) {
-    const int64_t tile_rows = f.swap ? kTcBNProt : kTcBM, tile_cols = f.swap ? kTcBM : kTcBNProt;
+    const int64_t tile_rows = f.swap ? bnp : kTcBM, tile_cols = f.swap ? kTcBM : bnp;
     npts = plan_injections(M, N, tile_rows, tile_cols, pts);
   }
   TcParams p;
@@ -623,7 +624,7 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   CUtensorMap tmA, tmB, tmC;
   std::memset(&tmA, 0, sizeof(tmA)); std::memset(&tmB, 0, sizeof(tmB)); std::memset(&tmC, 0, sizeof(tmC));
   if (!make_map_sw128(&tmA, eb, f.A, K, f.M, f.lda, kTcBM)) return FTBLAS_STATUS_NOT_SUPPORTED;
-  if (!make_map_sw128(&tmB, eb, f.B, K, f.N, f.ldb, ft ? kTcBNProt : kTcBN)) return FTBLAS_STATUS_NOT_SUPPORTED;
+  if (!make_map_sw128(&tmB, eb, f.B, K, f.N, f.ldb, ft ? (uint32_t)bnp : kTcBN)) return FTBLAS_STATUS_NOT_SUPPORTED;
   g_last_used_tma = 1;
   if (!ft) return record_cuda(launch_tc_gemm(p, &tmA, &tmB, &tmA, false, st));
   const bool own = ws == nullptr;
@@ -631,8 +632,8 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   TcWorkspace w = tc_workspace_carve(ws, p.M, p.N, p.K, kind);
   p.rowAbsA = w.rowAbsA; p.maxAbsBe = w.maxAbsBe; p.sA = w.sA; p.absSA = w.absSA;
   p.sa_pitch = w.kpitch; p.pend = w.pend;
-  const int64_t nNb = (f.N + kTcBNProt - 1) / kTcBNProt;
-  int rc = make_map_sw128(&tmC, eb, w.chk, K, nNb * kTcChkRows, w.kpitch, kTcChkRows) ? 0 : FTBLAS_STATUS_NOT_SUPPORTED;
+  const int64_t nNb = (f.N + bnp - 1) / bnp;
+  int rc = make_map_sw128(&tmC, eb, w.chk, K, nNb * chk_rows, w.kpitch, (uint32_t)chk_rows) ? 0 : FTBLAS_STATUS_NOT_SUPPORTED;
   if (rc == 0) rc = record_cuda(launch_tc_encode(p, w, st));  // writes every workspace entry the GEMM reads
   if (rc == 0) rc = record_cuda(launch_tc_gemm(p, &tmA, &tmB, &tmC, true, st));
   if (own) cudaFreeAsync(ws, st);
@@ -874,7 +875,9 @@ int ftblas_gemm_ex_noabft(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_
 int ftblas_verification_tile(ftblas_layout_t layout, ftblas_dtype_t compute_type, int64_t M, int64_t N, int64_t K,
                              int64_t* tile_rows, int64_t* tile_cols, int64_t* k_tile) {
   if (layout != FTBLAS_ROW_MAJOR && layout != FTBLAS_COL_MAJOR) return -1;
-  if (compute_type != FTBLAS_R_64F && compute_type != FTBLAS_R_32F) return -2;
+  if (compute_type != FTBLAS_R_64F && compute_type != FTBLAS_R_32F && compute_type != FTBLAS_R_16BF &&
+      compute_type != FTBLAS_R_8F_E4M3)
+    return -2;
   if (M < 0) return -3;
   if (N < 0) return -4;
   if (K < 0) return -5;
@@ -882,14 +885,16 @@ int ftblas_verification_tile(ftblas_layout_t layout, ftblas_dtype_t compute_type
   if (!tile_cols) return -7;
   if (!k_tile) return -8;
   const bool swap = layout == FTBLAS_ROW_MAJOR;
-  int64_t bm = kTcBM, bn = kTcBNProt;
+  const int tc_kind = compute_type == FTBLAS_R_8F_E4M3 ? 1 : 0;  // R_32F and R_16BF: the BF16 form
+  int64_t bm = kTcBM, bn = tc_bn_prot(tc_kind), kt = tc_kind == 1 ? 128 : 64;  // k-tile: 128 bytes
   if (compute_type == FTBLAS_R_64F) {
     // square tiles: the kernel frame's transpose of a row-major call does not change them
     bm = bn = chosen_fp64_edge(M, N, g_fp64_engine.load());
+    kt = kDBK;
   }
   *tile_rows = swap ? bn : bm;
   *tile_cols = swap ? bm : bn;
-  *k_tile = compute_type == FTBLAS_R_64F ? kDBK : 64;
+  *k_tile = kt;
   return 0;
 }
 

@@ -73,7 +73,7 @@ class Fp8Problem:
         self.c64, _ = S.store(self.Cin, layout, ld=self.ldc)
 
     def tile(self):
-        return fb.ftblas_verification_tile(self.layout, fb.R_32F, self.M, self.N, self.K)
+        return fb.ftblas_verification_tile(self.layout, fb.R_8F_E4M3, self.M, self.N, self.K)
 
     def run(self, protect=True):
         dA = torch.from_numpy(self.a8.astype(np.uint8)).cuda()
