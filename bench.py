@@ -883,12 +883,14 @@ def run_ours(args, rank, world, dist):
             else:
                 fb.check(fb.ftblas_dgemm_noabft(*args_))
 
-        for _ in range(warmup):
-            call(None)
-        barrier()
+        # the clock sampler starts before the warm-up (its start-up can stall this process's
+        # CUDA calls) and runs through the timed region
         sampler = ClockSampler(local) if clocks else None
         if sampler:
             sampler.__enter__()
+        for _ in range(warmup):
+            call(None)
+        barrier()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         fb.ftblas_kernel_timing_begin()
@@ -937,11 +939,13 @@ def run_ours(args, rank, world, dist):
             fb.check(fb.ftblas_dgemm_host(fb.COL_MAJOR, fb.NO_TRANS, fb.NO_TRANS, n, n, n, 1.5, hA.data_ptr(), n,
                                           hB.data_ptr(), n, 0.5, hC.data_ptr(), n, st, ctypes.addressof(hrep)))
 
+        # the sampler starts before the warm-up calls: its start-up (NVML initialisation) can
+        # stall this process's CUDA calls, and the host-buffer call synchronises every step
+        sampler = ClockSampler(local)
+        sampler.__enter__()
         for _ in range(max(1, min(args.warmup, 2))):
             hcall()
         barrier()
-        sampler = ClockSampler(local)
-        sampler.__enter__()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             hcall()
