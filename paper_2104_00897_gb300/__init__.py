@@ -20,7 +20,7 @@ UPPER, LOWER = 121, 122
 NON_UNIT, UNIT = 131, 132
 LEFT, RIGHT = 141, 142
 R_64F, R_32F, R_16BF, R_8F_E4M3 = 0, 1, 2, 3
-SITE_ACCUM, SITE_OUTPUT, SITE_CHECKSUM = 1, 2, 3
+SITE_ACCUM, SITE_OUTPUT, SITE_CHECKSUM, SITE_STALL = 1, 2, 3, 4
 MODE_BITFLIP, MODE_ADD_REL = 0, 1
 KIND_CORRECTED, KIND_CHECKSUM_ONLY, KIND_UNCORRECTABLE, KIND_INPUT_NONFINITE = 1, 2, 3, 4
 STATUS_TIMEOUT, STATUS_RECORDS_TRUNCATED = 1, 2

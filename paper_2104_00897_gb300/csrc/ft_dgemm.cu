@@ -34,7 +34,6 @@ namespace ftk {
 namespace {
 
 constexpr int BK = kDBK, STAGES = kDStages, NT = kDThreads;
-constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s per wait; a k-tile normally takes ~0.1 ms
 // Shared memory of one CTA for engine E (tile E::BM x E::BN).
 template <class E>
 struct __align__(1024) DSmem {
@@ -280,11 +279,25 @@ __device__ void load_ktile_plain(const DgemmParams& p, double* sA, double* sB, i
   }
 }
 
+// Bytes beyond the stage's that the staging barrier of k-tile kt of the tile at (m0, n0)
+// expects: 16 when a stall point (test launches only) names that tile and k-tile, so that the
+// barrier never completes and the waits on it give up; else 0.
+template <class E>
+__device__ __forceinline__ uint32_t stall_bytes(const DgemmParams& p, int m0, int n0, int kt, int kstar_tile) {
+  for (int e = 0; e < p.inj.n; ++e) {
+    const InjectPoint& ip = p.inj.p[e];
+    if (ip.site == kSiteStall && kt == (ip.kt > 0 ? ip.kt : kstar_tile) && ip.i >= m0 && ip.i < m0 + E::BM &&
+        ip.j >= n0 && ip.j < n0 + E::BN)
+      return 16u;
+  }
+  return 0u;
+}
+
 template <class E, bool AK, bool BKM>
 __device__ __forceinline__ void issue_ktile(DSmem<E>& sm, const CUtensorMap* tmA, const CUtensorMap* tmB, int s,
-                                            int m0, int n0, int k0) {
+                                            int m0, int n0, int k0, uint32_t extra_bytes) {
   constexpr uint32_t kStageBytes = (E::BM * BK + BK * E::BN) * sizeof(double);
-  mbar_arrive_expect_tx(&sm.full[s], kStageBytes);
+  mbar_arrive_expect_tx(&sm.full[s], kStageBytes + extra_bytes);
   if (AK) tma_load_2d(sm.a[s], tmA, &sm.full[s], k0, m0);
   else tma_load_2d(sm.a[s], tmA, &sm.full[s], m0, k0);
   if (BKM) tma_load_2d(sm.b[s], tmB, &sm.full[s], k0, n0);
@@ -385,7 +398,8 @@ __global__ void __launch_bounds__(NT, 1)
     if (p.use_tma) {
       tma_prefetch_desc(&tmA);
       tma_prefetch_desc(&tmB);
-      for (int s = 0; s < STAGES && s < nl; ++s) issue_ktile<E, AK, BKM>(sm, &tmA, &tmB, s, m0, n0, (kb + s) * BK);
+      for (int s = 0; s < STAGES && s < nl; ++s)
+        issue_ktile<E, AK, BKM>(sm, &tmA, &tmB, s, m0, n0, (kb + s) * BK, stall_bytes<E>(p, m0, n0, kb + s, kstar_tile));
     }
   }
   __syncthreads();
@@ -403,7 +417,7 @@ __global__ void __launch_bounds__(NT, 1)
     const int lt = kt - kb;  // position in this tile's k-range: stage and phase
     const int s = lt % STAGES;
     if (p.use_tma) {
-      if (!mbar_wait_bounded(&sm.full[s], (lt / STAGES) & 1, kWaitLimitNs)) sm.timeout = 1;
+      if (!mbar_wait_bounded(&sm.full[s], (lt / STAGES) & 1, p.wait_limit_ns)) sm.timeout = 1;
     } else {
       load_ktile_plain<E, AK, BKM>(p, sm.a[s], sm.b[s], m0, n0, kt * BK, t);
     }
@@ -485,7 +499,9 @@ __global__ void __launch_bounds__(NT, 1)
 
     E::template ktile<AK, BKM>(acc, sA, sB, t);
     __syncthreads();
-    if (p.use_tma && t == 0 && lt + STAGES < nl) issue_ktile<E, AK, BKM>(sm, &tmA, &tmB, s, m0, n0, (kt + STAGES) * BK);
+    if (p.use_tma && t == 0 && lt + STAGES < nl)
+      issue_ktile<E, AK, BKM>(sm, &tmA, &tmB, s, m0, n0, (kt + STAGES) * BK,
+                              stall_bytes<E>(p, m0, n0, kt + STAGES, kstar_tile));
     if (FT && p.kc_tiles > 0 && (kt + 1) % p.kc_tiles == 0 && kt + 1 < ke)
       online_check<E>(p, acc, pred, pmag, sm, t, m0, n0, nI, nJ, k_lo, (int64_t)(kt + 1) * BK);
   }
@@ -496,7 +512,7 @@ __global__ void __launch_bounds__(NT, 1)
     if (t == 0) {
       if (p.use_tma)
         for (int k2 = kt; k2 < ke && k2 < kt + STAGES; ++k2)
-          (void)mbar_wait_bounded(&sm.full[(k2 - kb) % STAGES], ((k2 - kb) / STAGES) & 1, kWaitLimitNs);
+          (void)mbar_wait_bounded(&sm.full[(k2 - kb) % STAGES], ((k2 - kb) / STAGES) & 1, p.wait_limit_ns);
       if (p.report) atomicOr(&p.report->status, FT_STATUS_TIMEOUT);
     }
     return;

@@ -15,13 +15,13 @@ namespace ftk {
 
 // Injection sites in the kernel frame (the caller's FT_SITE_CHECKSUM maps to a row or a
 // column checksum depending on the layout).
-enum : int32_t { kSiteAccum = 1, kSiteOutput = 2, kSiteChecksumRow = 3, kSiteChecksumCol = 4 };
+enum : int32_t { kSiteAccum = 1, kSiteOutput = 2, kSiteChecksumRow = 3, kSiteChecksumCol = 4, kSiteStall = 5 };
 
 struct InjectPoint {
   int32_t i, j;          // kernel-frame element
   int32_t site, mode;    // kSite*, FT_MODE_*
   int32_t bit, rel_log2, sign;
-  int32_t kt;            // FP64 accumulator site: k-tile of the flip (0: floor(nk/2))
+  int32_t kt;            // FP64 accumulator and stall sites: k-tile of the point (0: floor(nk/2))
 };
 
 constexpr int kMaxInject = FTBLAS_MAX_INJECTIONS_PER_LAUNCH;
@@ -46,6 +46,7 @@ struct DgemmParams {
   int32_t kc_tiles;              // online verification every kc_tiles k-tiles (0: finished tile only)
   int32_t tri_a, tri_b;          // op(A) / op(B) triangular in the kernel frame: 0 no, 1 upper, 2 lower
                                  // (each tile then runs only the k-tiles the nonzero triangle reaches)
+  uint64_t wait_limit_ns;        // limit of every bounded wait (short when a stall point is planned)
   InjectList inj;
 };
 

@@ -279,14 +279,21 @@ int dgemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, doub
     p.kc_tiles = (ft && kc > 0) ? (int32_t)((kc + kDBK - 1) / kDBK) : 0;
   }
   p.inj.n = 0;
+  bool stall = false;
   for (int q = 0; q < npts; ++q) {
     InjectPoint& ip = p.inj.p[p.inj.n++];
     const CallerPoint& c = pts[q];
     ip.i = (int32_t)(f.swap ? c.j : c.i);
     ip.j = (int32_t)(f.swap ? c.i : c.j);
-    ip.site = c.site == FT_SITE_CHECKSUM ? (f.swap ? kSiteChecksumCol : kSiteChecksumRow) : c.site;
+    ip.site = c.site == FT_SITE_CHECKSUM ? (f.swap ? kSiteChecksumCol : kSiteChecksumRow)
+              : c.site == FT_SITE_STALL  ? kSiteStall
+                                         : c.site;
     ip.mode = c.mode; ip.bit = c.bit; ip.rel_log2 = c.rel_log2; ip.sign = c.sign; ip.kt = c.kt;
+    stall |= c.site == FT_SITE_STALL;
   }
+  // a bounded wait normally gives up after 4 s (a k-tile takes about 0.1 ms); with a stall
+  // point planned, after 20 ms, so that its test ends quickly
+  p.wait_limit_ns = stall ? 20000000ull : 4000000000ull;
   CUtensorMap tmA, tmB;
   std::memset(&tmA, 0, sizeof(tmA));
   std::memset(&tmB, 0, sizeof(tmB));
@@ -415,6 +422,7 @@ void trsm_rec(TrsmCtx& c, int64_t i0, int64_t n) {
     InjectList inj;
     std::memset(&inj, 0, sizeof(inj));
     for (int q = 0; q < npts; ++q) {
+      if (pts[q].site == FT_SITE_STALL) continue;  // FP64 GEMM kernels only
       InjectPoint& ip = inj.p[inj.n++];
       ip.i = (int32_t)pts[q].i; ip.j = (int32_t)pts[q].j; ip.site = pts[q].site; ip.mode = pts[q].mode;
       ip.bit = pts[q].bit; ip.rel_log2 = pts[q].rel_log2; ip.sign = pts[q].sign; ip.kt = 0;
@@ -537,8 +545,9 @@ int dgemm_unfused_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t
   p.C = C; p.ldc = ldc;
   p.report = report;
   for (int q = 0; q < npts; ++q) {
-    InjectPoint& ip = p.inj.p[p.inj.n++];
     const CallerPoint& c = pts[q];
+    if (c.site == FT_SITE_STALL) continue;  // FP64 GEMM kernels only
+    InjectPoint& ip = p.inj.p[p.inj.n++];
     ip.i = (int32_t)(f.swap ? c.j : c.i);
     ip.j = (int32_t)(f.swap ? c.i : c.j);
     ip.site = c.site == FT_SITE_CHECKSUM ? kSiteChecksumRow : c.site;
@@ -613,8 +622,9 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   p.report = ft ? report : nullptr;
   p.swap_report = f.swap;
   for (int q = 0; q < npts; ++q) {
-    InjectPoint& ip = p.inj.p[p.inj.n++];
     const CallerPoint& c = pts[q];
+    if (c.site == FT_SITE_STALL) continue;  // FP64 GEMM kernels only
+    InjectPoint& ip = p.inj.p[p.inj.n++];
     ip.i = (int32_t)(f.swap ? c.j : c.i);
     ip.j = (int32_t)(f.swap ? c.i : c.j);
     ip.site = c.site == FT_SITE_CHECKSUM ? kSiteChecksumRow : c.site;
@@ -765,7 +775,7 @@ int ftblas_set_injection(const ft_inject_t* cfg) {
   }
   for (int q = 0; q < cfg->n_fixed; ++q) {
     const ft_inject_point_t& f = cfg->fixed[q];
-    if (f.site < FT_SITE_ACCUM || f.site > FT_SITE_CHECKSUM) return -1;
+    if (f.site < FT_SITE_ACCUM || f.site > FT_SITE_STALL) return -1;
     if (f.mode != FT_MODE_BITFLIP && f.mode != FT_MODE_ADD_REL) return -1;
     if (f.mode == FT_MODE_BITFLIP && (f.bit < 0 || f.bit > 63)) return -1;
   }

@@ -381,3 +381,31 @@ def test_online_checks_correct_two_faults_in_one_tile(engine, layout, _interval_
     assert record_set(rep) == record_set(orep)
     assert (rep.corrected, rep.uncorrectable) == (3, 0)
     assert np.array_equal(got, clean)
+
+
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
+def test_bounded_wait_gives_up_and_reports_timeout(engine):
+    """A staging barrier that never completes (the test-only stall point: it expects 16 bytes
+    more than TMA delivers) ends in a bounded wait, with no fault: the call returns, the
+    report carries FT_STATUS_TIMEOUT, that tile is not stored while every other tile is,
+    and the next call on the same context is clean and bit-identical."""
+    use(engine)
+    P = Problem(256, 320, 256, alpha=1.0, beta=0.0, seed=41)
+    clean, rep0 = run_gpu(P)
+    assert fb.ftblas_last_launch_used_tma() == 1 and rep0.status == 0
+    tr, tc, _ = tile_of(P)
+    i, j = 70, 200
+    fb.ftblas_set_injection(fb.make_injection(fixed=[dict(i=i, j=j, site=fb.SITE_STALL, kt=3)]))
+    got, rep = run_gpu(P)
+    fb.ftblas_set_injection(None)
+    assert rep.status & fb.STATUS_TIMEOUT
+    rows = slice((i // tr) * tr, min((i // tr + 1) * tr, P.M))
+    cols = slice((j // tc) * tc, min((j // tc + 1) * tc, P.N))
+    stalled = np.zeros_like(got, dtype=bool)
+    stalled[rows, cols] = True
+    assert np.array_equal(got[~stalled], clean[~stalled])
+    assert np.array_equal(got[stalled].view(np.uint64), P.Cin[stalled].view(np.uint64))  # not stored
+    assert rep.tiles_checked == -(-P.M // tr) * -(-P.N // tc) - 1
+    again, rep2 = run_gpu(P)
+    assert rep2.status == 0 and rep2.detected == 0
+    assert np.array_equal(again.view(np.uint64), clean.view(np.uint64))
