@@ -103,12 +103,13 @@ typedef struct {
 #define FT_SITE_ACCUM 1     /* flip a bit of the running sum of C(i,j) after bk*floor(nk/2) products */
 #define FT_SITE_OUTPUT 2    /* perturb C(i,j) after alpha/beta, before verification */
 #define FT_SITE_CHECKSUM 3  /* perturb the predicted row checksum C^r(i) of the tile holding (i,j) */
-#define FT_SITE_STALL 4     /* fixed points only, FP64 GEMM kernels staged by TMA (a test of the bounded
-                               waits): the staging barrier of k-tile k_tile (0: floor(nk/2)) of the tile
-                               holding (i,j) expects 16 bytes more than arrive, so it never completes;
-                               the call's waits give up after 20 ms instead of 4 s, that tile is not
-                               stored and the report's status gets FT_STATUS_TIMEOUT. Other kernels
-                               ignore the point. */
+#define FT_SITE_STALL 4     /* fixed points only (a test of the bounded waits), FP64 GEMM kernels
+                               staged by TMA and the tensor-core product kernel: the staging barrier of
+                               k-tile k_tile (0: the middle one) of the tile holding (i,j) expects 16
+                               bytes more than arrive, so it never completes; the call's waits give up
+                               after 20 ms instead of 4 s (2 s), the tile is not stored (the persistent
+                               tensor-core CTA also abandons its later tiles) and the report's status
+                               gets FT_STATUS_TIMEOUT. Other kernels ignore the point. */
 #define FT_MODE_BITFLIP 0   /* XOR bit `bit` (0 = lsb of the IEEE pattern of the accumulator type) */
 #define FT_MODE_ADD_REL 1   /* add sign * 2^rel_log2 * |value| */
 

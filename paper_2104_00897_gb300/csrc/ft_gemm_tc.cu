@@ -48,7 +48,6 @@ constexpr int BKB = 128;             // k-tile depth in bytes (64 BF16 or 128 E4
 constexpr int STAGES = 4;
 constexpr int NTHREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;   // two accumulator buffers of 256 columns
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait; a whole tile takes ~0.1 ms
 
 template <bool FT, int KIND>
 struct TcGeom {
@@ -180,6 +179,17 @@ __device__ void count_kind(const TcParams& p, int kind) {
   atomicAdd(ctr, 1ull);
 }
 
+// Bytes beyond the stage's that the staging barrier of k-tile kt of tile (mt, nt) expects: 16
+// when a stall point (test launches only) names that tile and k-tile (0: the middle one), so
+// that the barrier never completes and the waits on it give up; else 0.
+__device__ __forceinline__ uint32_t stall_bytes(const TcParams& p, int mt, int nt, int kt, int nk, int bn) {
+  for (int e = 0; e < p.inj.n; ++e) {
+    const InjectPoint& ip = p.inj.p[e];
+    if (ip.site == kSiteStall && kt == (ip.kt > 0 ? ip.kt : nk / 2) && ip.i / BM == mt && ip.j / bn == nt) return 16u;
+  }
+  return 0u;
+}
+
 // Persistent-tile order: groups of kGroupM row tiles sweep the column tiles, so the CTAs
 // resident at one time share A row panels and B column panels in L2. The last column
 // block comes after all the others: when N is not a multiple of the tile width its tiles
@@ -247,8 +257,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tile_coords(tile, nMb, nNb, mt, nt);
         for (int kt = 0; kt < nk; ++kt, ++it) {
           const uint32_t s = it % STAGES, u = it / STAGES;
-          if (u > 0 && !mbar_wait_bounded(&sm.empty[s], (u - 1) & 1, kWaitLimitNs)) { sm.timeout = 1; ok = false; break; }
-          mbar_arrive_expect_tx(&sm.full[s], bytes);
+          if (u > 0 && !mbar_wait_bounded(&sm.empty[s], (u - 1) & 1, p.wait_limit_ns)) { sm.timeout = 1; ok = false; break; }
+          mbar_arrive_expect_tx(&sm.full[s], bytes + stall_bytes(p, mt, nt, kt, nk, BN));
           const int k0 = kt * bk_elems;
           tma_load_2d(sm.a[s], &tmA, &sm.full[s], k0, mt * BM);
           tma_load_2d(sm.b[s], &tmB, &sm.full[s], k0, nt * BN);
@@ -279,12 +289,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tile_coords(tile, nMb, nNb, mt, nt);
         const bool narrow = narrow_last && nt == nNb - 1;
         const uint32_t b = lt & 1, ub = lt >> 1;
-        if (ub > 0 && !mbar_wait_bounded(&sm.tempty[b], (ub - 1) & 1, kWaitLimitNs)) { sm.timeout = 1; break; }
+        if (ub > 0 && !mbar_wait_bounded(&sm.tempty[b], (ub - 1) & 1, p.wait_limit_ns)) { sm.timeout = 1; break; }
         tc_fence_after();
         const uint32_t dcol = tmem + b * BNM;
         for (int kt = 0; kt < nk; ++kt, ++it) {
           const uint32_t s = it % STAGES, u = it / STAGES;
-          if (!mbar_wait_bounded(&sm.full[s], u & 1, kWaitLimitNs)) { sm.timeout = 1; ok = false; break; }
+          if (!mbar_wait_bounded(&sm.full[s], u & 1, p.wait_limit_ns)) { sm.timeout = 1; ok = false; break; }
           tc_fence_after();
           const uint32_t a0 = smem_addr(sm.a[s]), b0 = smem_addr(sm.b[s]);
 #pragma unroll
@@ -302,6 +312,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           umma_commit(&sm.empty[s]);
         }
+        // a wait gave up: the accumulator is incomplete, so the tile is never handed to the
+        // epilogue (whose own wait then gives up and leaves the tile unstored)
+        if (!ok) break;
         umma_commit(&sm.tfull[b]);
       }
     }
@@ -324,7 +337,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const uint32_t b = lt & 1, ub = lt >> 1;
       // tcgen05.ld is warp-collective (.sync.aligned): every TMEM load below is executed by
       // all 32 lanes of the warp, whatever their row; `got` is made warp-uniform for that.
-      const bool got = __all_sync(0xffffffffu, mbar_wait_bounded(&sm.tfull[b], ub & 1, kWaitLimitNs));
+      const bool got = __all_sync(0xffffffffu, mbar_wait_bounded(&sm.tfull[b], ub & 1, p.wait_limit_ns));
       if (!got) sm.timeout = 1;
       tc_fence_after();
       const uint32_t trow = tmem + b * BNM + (static_cast<uint32_t>(q * 32) << 16);
@@ -470,7 +483,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           count_kind(p, FT_KIND_UNCORRECTABLE);
         }
       }
-      if (et == 0 && p.report) atomicAdd(reinterpret_cast<unsigned long long*>(&p.report->tiles_checked), 1ull);
+      if (et == 0 && got && p.report)  // an abandoned tile (a wait gave up) is not counted
+        atomicAdd(reinterpret_cast<unsigned long long*>(&p.report->tiles_checked), 1ull);
       named_bar(1, 128);  // every epilogue thread is done with this tile's shared state
     }
   }

@@ -60,6 +60,7 @@ struct TcParams {
   int64_t sa_pitch;              // multiple of 8 (32-byte aligned rows)
   TcPending* pend;
   ft_report_t* report;
+  uint64_t wait_limit_ns;        // limit of every bounded wait (short when a stall point is planned)
   InjectList inj;
 };
 

@@ -621,15 +621,18 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   p.C = static_cast<float*>(C); p.ldc = ldc;
   p.report = ft ? report : nullptr;
   p.swap_report = f.swap;
+  bool stall = false;
   for (int q = 0; q < npts; ++q) {
     const CallerPoint& c = pts[q];
-    if (c.site == FT_SITE_STALL) continue;  // FP64 GEMM kernels only
     InjectPoint& ip = p.inj.p[p.inj.n++];
     ip.i = (int32_t)(f.swap ? c.j : c.i);
     ip.j = (int32_t)(f.swap ? c.i : c.j);
-    ip.site = c.site == FT_SITE_CHECKSUM ? kSiteChecksumRow : c.site;
+    ip.site = c.site == FT_SITE_CHECKSUM ? kSiteChecksumRow : c.site == FT_SITE_STALL ? kSiteStall : c.site;
     ip.mode = c.mode; ip.bit = c.bit; ip.rel_log2 = c.rel_log2; ip.sign = c.sign; ip.kt = c.kt;
+    stall |= c.site == FT_SITE_STALL;
   }
+  // 2 s per bounded wait (a whole tile takes about 0.1 ms); 20 ms with a stall point planned
+  p.wait_limit_ns = stall ? 20000000ull : 2000000000ull;
   const int eb = fp8 ? 1 : 2;
   CUtensorMap tmA, tmB, tmC;
   std::memset(&tmA, 0, sizeof(tmA)); std::memset(&tmB, 0, sizeof(tmB)); std::memset(&tmC, 0, sizeof(tmC));

@@ -223,3 +223,29 @@ def test_bf16_full_size_8192_sampled_rows():
     t = (i // tr) + (j // tc) * ((n + tr - 1) // tr)
     _, orep = P.oracle(injections=[pt], tiles=[t])
     assert record_set(orep) == record_set(rep)
+
+
+def test_bounded_wait_gives_up_and_reports_timeout():
+    """The tensor-core kernel's bounded waits: a staging barrier that never completes (the
+    test-only stall point) ends the stalled CTA's work after 20 ms, with no fault. With one
+    tile per persistent CTA, exactly that tile is left unwritten, the report carries
+    FT_STATUS_TIMEOUT, the other tiles are stored as in a clean call, and the next call is
+    clean."""
+    P = Bf16Problem(256, 496, 512, O.COL_MAJOR, alpha=1.0, beta=0.0, seed=43)
+    clean, rep0 = P.run()
+    assert rep0.status == 0
+    tr, tc, _ = P.tile()
+    i, j = 130, 300
+    fb.ftblas_set_injection(fb.make_injection(fixed=[dict(i=i, j=j, site=fb.SITE_STALL, kt=3)]))
+    try:
+        got, rep = P.run()
+    finally:
+        fb.ftblas_set_injection(None)
+    assert rep.status & fb.STATUS_TIMEOUT
+    stalled = np.zeros_like(got, dtype=bool)
+    stalled[(i // tr) * tr:(i // tr + 1) * tr, (j // tc) * tc:(j // tc + 1) * tc] = True
+    assert np.array_equal(got[~stalled], clean[~stalled])
+    assert np.array_equal(got[stalled], P.Cin.astype(np.float32).astype(np.float64)[stalled])  # not stored
+    assert rep.tiles_checked == -(-P.M // tr) * -(-P.N // tc) - 1
+    again, rep2 = P.run()
+    assert rep2.status == 0 and rep2.detected == 0 and np.array_equal(again, clean)
