@@ -971,10 +971,9 @@ def run_ours(args, rank, world, dist):
             fb.check(fb.ftblas_dgemm_host(fb.COL_MAJOR, fb.NO_TRANS, fb.NO_TRANS, n, n, n, 1.5, hA.data_ptr(), n,
                                           hB.data_ptr(), n, 0.5, hC.data_ptr(), n, st, ctypes.addressof(hrep)))
 
-        # the sampler starts before the warm-up calls: its start-up (NVML initialisation) can
-        # stall this process's CUDA calls, and the host-buffer call synchronises every step
-        sampler = ClockSampler(local)
-        sampler.__enter__()
+        # No nvidia-smi sampler here: its queries stall this process's CUDA calls, and the
+        # host-buffer call synchronises every step, so they would land in the wall-clock
+        # region. The device-timed runs just before carry the clock record.
         for _ in range(max(1, min(args.warmup, 2))):
             hcall()
         barrier()
@@ -983,10 +982,8 @@ def run_ours(args, rank, world, dist):
             hcall()
         barrier()
         e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
-        sampler.__exit__(None, None, None)
         return {"value": job_tflops(world, flops_step, args.steps, 1e3 * e2e_s), "unit": UNIT,
-                "h2d_bytes_per_step": 3 * n * n * 8, "d2h_bytes_per_step": n * n * 8 + fb.REPORT_BYTES,
-                "clocks": sampler.summary()}
+                "h2d_bytes_per_step": 3 * n * n * 8, "d2h_bytes_per_step": n * n * 8 + fb.REPORT_BYTES}
 
     engine_list = [args.engine] + ([] if args.no_second_engine else [e for e in engines if e != args.engine])
     clocks = None
