@@ -78,8 +78,9 @@ def parse_args():
 
 
 def peaks():
-    """Roofline denominators. The measured file holds HBM and BF16 figures; the FP64
-    pipe's peak is derived from them and the nominal figures (see the design notes)."""
+    """Roofline denominators. MEASURED_PEAKS.json holds the measured HBM copy and BF16 GEMM
+    figures (burst and sustained); the FP64 pipe's peak is derived from its unit count and the
+    maximum SM clock."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     mp = {}
     if os.path.exists(path):
