@@ -247,15 +247,15 @@ int ftblas_dgemm_host(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_tran
  * transposed), leading dimensions that are multiples of 8 elements and 16-byte aligned
  * base addresses; other combinations return FTBLAS_STATUS_NOT_SUPPORTED. Its threshold
  * assumes the tensor core accumulates in binary32 with unit roundoff 2^-23 (measured on
- * GB300: truncating accumulation). Protected tiles hold 128 x 248 outputs (BF16; 128 x 240
- * for FP8): B^r = [B, Be] (Section II.A) fills the 256-column MMA, the last 8 (16) columns
- * holding the pieces of B e. Row checksums are verified in every tile and
+ * GB300: truncating accumulation). Protected tiles hold 128 x 248 outputs: B^r = [B, Be]
+ * (Section II.A) fills the 256-column MMA, the last 8 columns holding the pieces of B e
+ * (three bfloat16 or eight e4m3 pieces). Row checksums are verified in every tile and
  * column checksums only in tiles with a row mismatch (Section V.A); when those flag no
  * column (rows of very different scale) and beta == 0, the mismatching row is recomputed
  * and compared element by element; a located error is corrected by subtracting the row mismatch
  * (Section VI.C), evaluated as C^r(i) - sum_{j' != j} C(i,j') so that a huge or
  * non-finite error does not cancel catastrophically. Workspace (about
- * 16*K*ceil(N/248) + 8*K*ceil(M/128) + 4*M*ceil(K/256) bytes for BF16, 16*K*ceil(N/240) + ...
+ * 16*K*ceil(N/248) + 8*K*ceil(M/128) + 4*M*ceil(K/256) bytes for BF16, 8*K*ceil(N/248) + ...
  * for FP8) is taken from the stream-ordered allocator and released on the same stream. */
 int ftblas_gemm_ex(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,
                    int64_t M, int64_t N, int64_t K, const void* alpha,
@@ -305,7 +305,7 @@ int ftblas_gemm_ex_noalloc(ftblas_layout_t layout, ftblas_trans_t transa, ftblas
  * products; for the tensor-core forms the k-tile of their staging, 128 bytes). compute_type
  * selects the kernel family: FTBLAS_R_64F (ftblas_dgemm and the Level-3 routines built on
  * it), FTBLAS_R_32F or FTBLAS_R_16BF (BF16 tensor-core path: 128 x 248 tiles, k-tile 64) or
- * FTBLAS_R_8F_E4M3 (FP8 tensor-core path: 128 x 240 tiles, k-tile 128).
+ * FTBLAS_R_8F_E4M3 (FP8 tensor-core path: 128 x 248 tiles, k-tile 128).
  * FP64 tiles are square, 128 x 128, or 64 x 64 with the DFMA engine when 128-edge tiles
  * would leave many of the current device's SMs idle: the choice depends on M, N, the
  * engine (ftblas_set_fp64_engine) and the SM count (152 when no device answers). The

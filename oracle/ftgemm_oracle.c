@@ -70,7 +70,7 @@
 #define OR_PREC_FP64 0
 #define OR_PREC_ACC32 1
 /* ACC32 for FP8 (E4M3) operands: the same arithmetic, with the row checksum's prediction
- * formed from B e split into sixteen e4m3 pieces instead of three bfloat16 ones, whose
+ * formed from B e split into eight e4m3 pieces instead of three bfloat16 ones, whose
  * magnitudes sum to at most 1.25 |B e| (1 + 2^-7 for the bfloat16 pieces). */
 #define OR_PREC_ACC32_E4M3 2
 #define IS_ACC32(p) ((p)->precision == OR_PREC_ACC32 || (p)->precision == OR_PREC_ACC32_E4M3)
@@ -636,7 +636,7 @@ static void ft_tile(const oracle_problem_t* p, int64_t tr, int64_t tc,
  *               rare tiles with a row mismatch)
  *     (the row side's prediction is itself a binary32 product of A with B e split into
  *     pieces whose magnitudes sum to at most s |B e|: s = 1 + 2^-7 for three bfloat16
- *     pieces, 1.25 for sixteen e4m3 pieces; the column side's is a binary32 dot product of e^T A with B; B e and
+ *     pieces, 1.25 for eight e4m3 pieces; the column side's is a binary32 dot product of e^T A with B; B e and
  *     e^T A are binary32 sums over the tile, whose rounding in any order is at most
  *     gamma_n(2^-24) times the sum of magnitudes, n the tile width);
  *   - column checksums are formed only when a row mismatches (Section V.A, lazy side);

@@ -11,14 +11,13 @@
 //               128-byte swizzled, K-major. Protected launches put the checksum column of
 //               B^r = [B, Be] (Section II.A) into the last rows of the same B stage: Be over
 //               the tile's data columns, in pieces written by a bandwidth-bound encode
-//               pre-pass (ft_tc_encode.cu): BF16, 248 data columns and three bfloat16 pieces
-//               (hi, mid, lo) in rows 248..255; E4M3, 240 data columns and sixteen pieces in
-//               rows 240..255.
+//               pre-pass (ft_tc_encode.cu): 248 data columns and, in rows 248..255, three
+//               bfloat16 pieces (hi, mid, lo) of B e, or eight e4m3 pieces.
 //   warp 1      TMEM allocation and MMA issue (one thread): 4 x tcgen05.mma M128 N256 K16 per
 //               k-tile into one of two 256-column TMEM buffers, so the next tile's product
 //               overlaps the previous tile's epilogue. With the checksum column appended, the
 //               tensor core produces the pieces of C^r = A (B e) in the last columns with the
-//               product itself, at no extra instruction (8 or 16 of 256 columns per tile).
+//               product itself, at no extra instruction (8 of 256 columns per tile).
 //   warps 2..5  epilogue, one TMEM lane (= output row) per thread: C = alpha acc + beta C_in
 //               stored in FP32; C^r_ref(i) = sum_j C(i,j) in compensated binary32, compared
 //               in binary64 with the predicted checksum against a rigorous bound. Only in a

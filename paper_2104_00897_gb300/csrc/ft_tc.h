@@ -13,9 +13,9 @@ namespace ftk {
 constexpr int kTcBM = 128;       // tile rows (TMEM lanes)
 constexpr int kTcBN = 256;       // data columns per tile, unprotected (= MMA N)
 // Protected tiles: B^r = [B, Be] fills the MMA's N = 256 with the tile's data columns followed
-// by the rows of the checksum operand that hold the pieces of B e: three bfloat16 pieces in 8
-// rows (248 data columns), sixteen e4m3 pieces in 16 rows (240 data columns).
-constexpr int tc_chk_rows(int kind) { return kind == 0 ? 8 : 16; }
+// by the rows of the checksum operand that hold the pieces of B e: three bfloat16 pieces or
+// eight e4m3 pieces, in 8 rows for both kinds (248 data columns).
+constexpr int tc_chk_rows(int /*kind*/) { return 8; }
 constexpr int tc_bn_prot(int kind) { return kTcBN - tc_chk_rows(kind); }
 constexpr int kTcBNProtMax = 248;  // the larger tc_bn_prot: per-column arrays of a pending tile
 static_assert(tc_bn_prot(0) <= kTcBNProtMax && tc_bn_prot(1) <= kTcBNProtMax, "pending-tile arrays too small");

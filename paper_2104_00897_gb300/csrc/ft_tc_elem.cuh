@@ -22,9 +22,11 @@ __device__ __forceinline__ float e4m3_to_f32(uint8_t b) {
 //   kPieces    checksum columns holding the pieces of B e (rows 0 .. kPieces-1 of a block)
 //   kPieceSum  bound of sum_p |piece_p| / |B e| (for the threshold's prediction part)
 // BF16: B e as hi + mid + lo bfloat16 (exact for a binary32 value), scale 1.
-// E4M3: B e as 16 e4m3 pieces with fixed scales 2^(9 - 4p): each piece is the nearest e4m3
-//   of what the previous ones leave (subnormals flushed and carried), so |B e| <= 240 * 448
-//   fits the first piece and the pieces hold B e to far below binary32 resolution.
+// E4M3: B e as 8 e4m3 pieces with fixed scales 2^(9 - 4p): each piece is the nearest e4m3
+//   of what the previous ones leave (subnormals flushed and carried). |B e| <= 248 * 448 fits
+//   the first piece; each piece that is not flushed takes the top 4 bits of what is left, and
+//   the scales step by 2^4, so the pieces hold the binary32 sum B e (at most 24 significant
+//   bits, a multiple of 2^-9) exactly.
 template <int KIND> struct Elem;
 template <> struct Elem<0> {
   static constexpr int kBytes = 2, kPieces = 3;
@@ -58,7 +60,7 @@ template <> struct Elem<0> {
   }
 };
 template <> struct Elem<1> {
-  static constexpr int kBytes = 1, kPieces = 16;
+  static constexpr int kBytes = 1, kPieces = 8;
   static constexpr float kPieceSum = 1.25f;
   // as above with one 8-byte load (ld a multiple of 16 elements)
   using Raw = uint2;

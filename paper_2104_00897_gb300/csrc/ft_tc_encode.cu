@@ -19,7 +19,7 @@ constexpr int BM = kTcBM;             // 128 rows of A per block (the tile's row
 // Encode pre-pass (bandwidth-bound): one read of A and one read of B. Kernel-frame A is
 // M x K and B is K x N, both K-contiguous, so each is a set of K-contiguous lines: the
 // rows of A, the columns of B. A CTA takes a block of L lines (the 128 rows of a tile of
-// A, the 248 (BF16) or 240 (E4M3) columns of a tile of B) and ENC_KC consecutive k. Lane l of warp w loads
+// A, the 248 columns of a tile of B) and ENC_KC consecutive k. Lane l of warp w loads
 // k0 + 8l .. k0 + 8l + 7 (one 16- or 8-byte load per line) of lines w, w + 8, w + 16, ...;
 // the eight warps' partial sums meet in shared memory.
 // Sums over a block are plain binary32 sums: their rounding, at most gamma_L(2^-24) times
@@ -166,11 +166,12 @@ __device__ __forceinline__ void encode_block(const EncArgs& g, int blk, int kc, 
 #pragma unroll
         for (int r = 3; r < kChk; ++r) col[r * g.pitch] = 0;
       } else {
-        // sixteen e4m3 pieces with scales 2^(9 - 4p): piece p is the nearest e4m3 of
+        // eight e4m3 pieces with scales 2^(9 - 4p): piece p is the nearest e4m3 of
         // r / 2^(9 - 4p), r what the previous pieces leave; a subnormal piece is flushed to
-        // zero and its value carried. |S| <= 240 * 448 < 256 * 2^9, and each remainder is at
+        // zero and its value carried. |S| <= 248 * 448 < 256 * 2^9, and each remainder is at
         // most half an e4m3 unit of the piece before, so every r / 2^(9 - 4p) stays within
-        // +-256, and r - piece is exact (the two are within a factor of two).
+        // +-256, and r - piece is exact (the two are within a factor of two). The last
+        // remainder is zero: the pieces take 4 bits each of S's at most 24.
         uint8_t* col = static_cast<uint8_t*>(g.chk) + (int64_t)blk * tc_chk_rows(1) * g.pitch + kk;
         float r = S, inv = 0x1p-9f, sc = 0x1p9f;
 #pragma unroll

@@ -87,11 +87,11 @@ def test_verification_tile_and_engine_switch():
     fb.ftblas_set_fp64_engine(prev)
     assert fb.ftblas_set_fp64_tile(96) == -1
     assert fb.ftblas_set_fp64_tile(0) == 64
-    # tensor-core forms: 128 x 248 (BF16: 8 checksum columns) and 128 x 240 (E4M3: 16)
+    # tensor-core forms: 128 x 248 tiles (8 checksum columns), k-tile 64 BF16 or 128 E4M3
     for ct in (fb.R_32F, fb.R_16BF):
         assert fb.ftblas_verification_tile(fb.COL_MAJOR, ct, 8192, 8192, 8192) == (128, 248, 64)
         assert fb.ftblas_verification_tile(fb.ROW_MAJOR, ct, 8192, 8192, 8192) == (248, 128, 64)
-    assert fb.ftblas_verification_tile(fb.COL_MAJOR, fb.R_8F_E4M3, 16384, 16384, 16384) == (128, 240, 128)
+    assert fb.ftblas_verification_tile(fb.COL_MAJOR, fb.R_8F_E4M3, 16384, 16384, 16384) == (128, 248, 128)
     prev = fb.ftblas_set_fp64_engine(fb.ENGINE_DMMA)
     assert fb.ftblas_set_fp64_engine(prev) == fb.ENGINE_DMMA
     assert fb.ftblas_set_fp64_engine(7) == -1

@@ -170,7 +170,8 @@ def test_fp8_row_scaled_clean_runs_have_no_false_alarm():
     pts = [dict(i=i, j=j, site=fb.SITE_OUTPUT, mode=fb.MODE_ADD_REL, rel_log2=10, sign=1)]
     fb.ftblas_set_injection(fb.make_injection(fixed=pts))
     got, rep = P.run()
-    _, orep = P.oracle(injections=pts, tiles=[(i // 128) + (j // 240) * ((512 + 127) // 128)])
+    tr, tc, _ = P.tile()
+    _, orep = P.oracle(injections=pts, tiles=[(i // tr) + (j // tc) * ((512 + tr - 1) // tr)])
     assert (rep.detected, rep.corrected) == (1, 1)
     assert record_set(rep) == record_set(orep)
 
