@@ -6,8 +6,13 @@
 // Diagonal-block solve with a checksum (Section II.A applied to T X = R): for an n x n
 // triangular block T and right-hand sides R, e^T (T X) = (e^T T) X must equal e^T R for
 // every column. Columns are independent, so a column whose checksum mismatches is solved
-// again from the untouched R (same instruction sequence: the fault-free result bit for
-// bit); several faulty columns are all corrected.
+// again from the untouched R (same arithmetic: the fault-free result bit for bit); several
+// faulty columns are all corrected.
+//
+// The substitution is blocked by kBlk rows: each diagonal kBlk x kBlk block is solved with
+// one thread per column (a short dependent chain), then the rows still to come are updated
+// by all threads, each output as a kBlk-term fused multiply-add chain in ascending k. On
+// GB300's FP64 pipe the updates, which hold almost all the work, then keep every warp busy.
 #include <climits>
 
 #include "ft_device.cuh"
@@ -18,8 +23,11 @@ namespace ftk {
 namespace {
 
 constexpr int kLeaf = kTrsmLeaf;  // diagonal block edge (<= 128)
-constexpr int kCols = 64;         // right-hand sides per CTA (one solving thread each)
-constexpr int kThreads = 256;     // all threads stage the block and the right-hand sides
+constexpr int kCols = 64;         // right-hand sides per CTA
+constexpr int kThreads = 256;     // all threads stage, update and write back
+constexpr int kBlk = 16;          // rows per diagonal block of the blocked substitution
+constexpr int kGroups = kThreads / kCols;  // threads sharing one column (its rows by residue)
+static_assert(kGroups * kCols == kThreads && 32 % kGroups == 0, "a column's threads share one warp");
 
 
 // dst(r, c) = scale * src[r * rs + c * cs], dst column-major with leading dimension ld.
@@ -64,23 +72,91 @@ struct LeafSmem {
   double w[kLeaf][kCols];             // w[row][column]: right-hand side, then solution
   double wf[kLeaf][kCols];            // a faulty solution kept while its column is solved again
   double tsum[kLeaf], tabs[kLeaf];    // column sums of T and of |T|
+  double inv_d[kLeaf];                // 1 / T(r,r)
 };
 
-// Substitution for column t held in sm.w[.][t]: lower (forward) or upper (backward),
-// x_r = w_r / T(r,r) then w_s -= T(s,r) x_r for the rows still to come. An injection point
-// at row inj_r flips bit inj_bit of x_r right after it is formed (test launches only).
-__device__ void solve_column(LeafSmem& sm, int t, int n, bool lower, int inj_r, int inj_bit) {
-  for (int q = 0; q < n; ++q) {
-    const int r = lower ? q : n - 1 - q;
-    const double* col = sm.T + packed(lower ? r : 0, r, n, lower);  // column r's stored entries
-    double x = sm.w[r][t] / col[lower ? 0 : r];
-    if (r == inj_r) x = __longlong_as_double(__double_as_longlong(x) ^ (1ll << inj_bit));
+// Element (s, r) of the block (in its stored triangle).
+__device__ __forceinline__ double tri(const LeafSmem& sm, int s, int r, int n, bool lower) {
+  return sm.T[packed(s, r, n, lower)];
+}
+
+// Rows [r0, r1) of diagonal block b in solve order: lower (forward) from the top, upper
+// (backward) from the bottom.
+__device__ __forceinline__ void block_rows(int bi, int n, bool lower, int& r0, int& r1) {
+  const int nb = (n + kBlk - 1) / kBlk;
+  const int b = lower ? bi : nb - 1 - bi;
+  r0 = b * kBlk;
+  r1 = min(n, r0 + kBlk);
+}
+
+// Substitution within diagonal block [r0, r1) for column t held in sm.w[.][t], by one thread:
+// x_r = w_r (1 / T(r,r)), then w_s -= T(s,r) x_r for the block's rows still to come, in the
+// order of the CTA-wide version below (the re-solve of a column).
+__device__ void solve_diag_block(LeafSmem& sm, int t, int r0, int r1, int n, bool lower) {
+  for (int q = r0; q < r1; ++q) {
+    const int r = lower ? q : r0 + r1 - 1 - q;
+    const double x = sm.w[r][t] * sm.inv_d[r];
     sm.w[r][t] = x;
     if (lower) {
-      for (int s2 = r + 1; s2 < n; ++s2) sm.w[s2][t] = fma(-col[s2 - r], x, sm.w[s2][t]);
+      for (int s2 = r + 1; s2 < r1; ++s2) sm.w[s2][t] = fma(-tri(sm, s2, r, n, lower), x, sm.w[s2][t]);
     } else {
-      for (int s2 = 0; s2 < r; ++s2) sm.w[s2][t] = fma(-col[s2], x, sm.w[s2][t]);
+      for (int s2 = r0; s2 < r; ++s2) sm.w[s2][t] = fma(-tri(sm, s2, r, n, lower), x, sm.w[s2][t]);
     }
+  }
+}
+
+// The same substitution by the kGroups threads of column c (lanes kGroups c .. kGroups c +
+// kGroups - 1 of one warp): thread g owns the rows r with r % kGroups == g, forms x_r for
+// those and updates only those, and each x_r reaches the others by a warp shuffle. Every
+// element receives its updates in the same order as in solve_diag_block. An injection point
+// at row inj_r flips bit inj_bit of x_r right after it is formed (test launches only).
+__device__ void solve_diag_block_par(LeafSmem& sm, int c, int g, int r0, int r1, int n, bool lower, int inj_r,
+                                     int inj_bit) {
+  const int lane = threadIdx.x & 31;
+  for (int q = r0; q < r1; ++q) {
+    const int r = lower ? q : r0 + r1 - 1 - q;
+    const int owner = r % kGroups;
+    double x = 0.0;
+    if (g == owner) {
+      x = sm.w[r][c] * sm.inv_d[r];
+      if (r == inj_r) x = __longlong_as_double(__double_as_longlong(x) ^ (1ll << inj_bit));
+      sm.w[r][c] = x;
+    }
+    x = __shfl_sync(0xffffffffu, x, (lane & ~(kGroups - 1)) | owner);
+    if (lower) {
+      for (int s2 = r + 1; s2 < r1; ++s2)
+        if (s2 % kGroups == g) sm.w[s2][c] = fma(-tri(sm, s2, r, n, lower), x, sm.w[s2][c]);
+    } else {
+      for (int s2 = r0; s2 < r; ++s2)
+        if (s2 % kGroups == g) sm.w[s2][c] = fma(-tri(sm, s2, r, n, lower), x, sm.w[s2][c]);
+    }
+  }
+}
+
+// Update of row `row` of column t by diagonal block [r0, r1): w_row -= sum_k T(row,k) x_k as
+// one fused multiply-add chain in ascending k (x_k = sm.w[k][t], already solved).
+__device__ __forceinline__ void update_row(LeafSmem& sm, int t, int row, int r0, int r1, int n, bool lower) {
+  double acc = sm.w[row][t];
+  for (int k = r0; k < r1; ++k) acc = fma(-tri(sm, row, k, n, lower), sm.w[k][t], acc);
+  sm.w[row][t] = acc;
+}
+
+// Rows a diagonal block updates: lower, those after it; upper, those before it.
+__device__ __forceinline__ void update_range(int r0, int r1, int n, bool lower, int& lo, int& hi) {
+  lo = lower ? r1 : 0;
+  hi = lower ? n : r0;
+}
+
+// The whole blocked substitution of column t by one thread, with the arithmetic of the
+// CTA-wide solve (the re-solve of a column whose checksum mismatched).
+__device__ void solve_column(LeafSmem& sm, int t, int n, bool lower) {
+  const int nb = (n + kBlk - 1) / kBlk;
+  for (int bi = 0; bi < nb; ++bi) {
+    int r0, r1, lo, hi;
+    block_rows(bi, n, lower, r0, r1);
+    solve_diag_block(sm, t, r0, r1, n, lower);
+    update_range(r0, r1, n, lower, lo, hi);
+    for (int row = lo; row < hi; ++row) update_row(sm, t, row, r0, r1, n, lower);
   }
 }
 
@@ -112,59 +188,88 @@ __global__ void __launch_bounds__(kThreads) trsm_leaf_kernel(const double* T, in
     for (int q = 0; q < len; ++q) { s += col[q]; a = __dadd_ru(a, fabs(col[q])); }
     sm.tsum[c] = s;
     sm.tabs[c] = a;
+    sm.inv_d[c] = 1.0 / tri(sm, c, c, n, low);
   }
   __syncthreads();
-  if (tid < kCols) {
-    const int t = tid;
-    const int64_t j = j0 + t;
-    const bool jok = t < ncols;
-    double rsum = 0.0, rabs = 0.0;  // the right-hand side's sums
+  // the right-hand side's sums (threads t < kCols), read before the substitution overwrites
+  // the column
+  const int t = tid;
+  const int64_t j = j0 + t;
+  const bool jok = t < kCols && t < ncols;
+  double rsum = 0.0, rabs = 0.0;
+  if (t < kCols)
     for (int r = 0; r < n; ++r) { rsum += sm.w[r][t]; rabs = __dadd_ru(rabs, fabs(sm.w[r][t])); }
-    int inj_r = -1, inj_bit = 0;
-    for (int e = 0; e < inj.n; ++e)
-      if (inj.p[e].j == j && inj.p[e].i >= 0 && inj.p[e].i < n && inj.p[e].mode == FT_MODE_BITFLIP) {
-        inj_r = inj.p[e].i;
-        inj_bit = inj.p[e].bit;
+  // this thread's column in the diagonal solves (kGroups lanes per column) and its injection
+  // point
+  const int dc = tid / kGroups, dg = tid % kGroups;
+  int inj_r = -1, inj_bit = 0;
+  for (int e = 0; e < inj.n; ++e)
+    if (dc < ncols && inj.p[e].j == j0 + dc && inj.p[e].i >= 0 && inj.p[e].i < n &&
+        inj.p[e].mode == FT_MODE_BITFLIP) {
+      inj_r = inj.p[e].i;
+      inj_bit = inj.p[e].bit;
+    }
+  __syncthreads();
+  // blocked substitution: each diagonal block by kGroups threads per column, then the updates
+  // of the rows still to come by all threads (kGroups threads per column, interleaved rows);
+  // the solved values of the block are held in registers for the updates
+  const int nb = (n + kBlk - 1) / kBlk;
+  const int uc = tid % kCols, ug = tid / kCols;
+  for (int bi = 0; bi < nb; ++bi) {
+    int r0, r1, lo, hi;
+    block_rows(bi, n, low, r0, r1);
+    solve_diag_block_par(sm, dc, dg, r0, r1, n, low, inj_r, inj_bit);
+    __syncthreads();
+    update_range(r0, r1, n, low, lo, hi);
+    double xk[kBlk];
+#pragma unroll
+    for (int k = 0; k < kBlk; ++k) xk[k] = r0 + k < r1 ? sm.w[r0 + k][uc] : 0.0;
+    for (int row = lo + ug; row < hi; row += kGroups) {
+      double acc = sm.w[row][uc];
+#pragma unroll
+      for (int k = 0; k < kBlk; ++k)
+        if (r0 + k < r1) acc = fma(-tri(sm, row, r0 + k, n, low), xk[k], acc);  // as update_row
+      sm.w[row][uc] = acc;
+    }
+    __syncthreads();
+  }
+  if (jok) {
+    // e^T T x against e^T r: tau = 2 gamma_{2n+2} (sum_s (e^T|T|)_s |x_s| + sum |r|), a bound on
+    // the substitution's residual (componentwise backward error gamma_n |T| |x|) plus the
+    // rounding of both sums.
+    double chk = 0.0, mag = 0.0;
+    for (int s2 = 0; s2 < n; ++s2) {
+      const double x = sm.w[s2][t];
+      chk = fma(sm.tsum[s2], x, chk);
+      mag = __fma_ru(sm.tabs[s2], fabs(x), mag);
+    }
+    const double delta = chk - rsum;
+    const double tau = __dmul_ru(2.0, __dmul_ru(gamma_up64(2 * (int64_t)n + 2), __dadd_ru(mag, rabs)));
+    if (!(fabs(delta) <= tau) || isinf(delta)) {
+      // keep the faulty solution, solve again from the untouched right-hand side in W
+      for (int r = 0; r < n; ++r) { sm.wf[r][t] = sm.w[r][t]; sm.w[r][t] = W[r + j * ldw]; }
+      solve_column(sm, t, n, low);
+      int first = -1;  // where the fault entered: the first row, in solve order, that differs
+      for (int q = 0; q < n && first < 0; ++q) {
+        const int r = low ? q : n - 1 - q;
+        if (__double_as_longlong(sm.wf[r][t]) != __double_as_longlong(sm.w[r][t])) first = r;
       }
-    if (jok) {
-      solve_column(sm, t, n, low, inj_r, inj_bit);
-      // e^T T x against e^T r: tau = 2 gamma_{2n+2} (sum_s (e^T|T|)_s |x_s| + sum |r|), a bound on
-      // the substitution's residual (componentwise backward error gamma_n |T| |x|) plus the
-      // rounding of both sums.
-      double chk = 0.0, mag = 0.0;
-      for (int s2 = 0; s2 < n; ++s2) {
-        const double x = sm.w[s2][t];
-        chk = fma(sm.tsum[s2], x, chk);
-        mag = __fma_ru(sm.tabs[s2], fabs(x), mag);
-      }
-      const double delta = chk - rsum;
-      const double tau = __dmul_ru(2.0, __dmul_ru(gamma_up64(2 * (int64_t)n + 2), __dadd_ru(mag, rabs)));
-      if (!(fabs(delta) <= tau) || isinf(delta)) {
-        // keep the faulty solution, solve again from the untouched right-hand side in W
-        for (int r = 0; r < n; ++r) { sm.wf[r][t] = sm.w[r][t]; sm.w[r][t] = W[r + j * ldw]; }
-        solve_column(sm, t, n, low, -1, 0);
-        int first = -1;  // where the fault entered: the first row, in solve order, that differs
-        for (int q = 0; q < n && first < 0; ++q) {
-          const int r = low ? q : n - 1 - q;
-          if (__double_as_longlong(sm.wf[r][t]) != __double_as_longlong(sm.w[r][t])) first = r;
-        }
-        if (rep) {
-          atomicAdd(reinterpret_cast<unsigned long long*>(&rep->detected), 1ull);
-          atomicAdd(reinterpret_cast<unsigned long long*>(&rep->corrected), 1ull);
-          const unsigned slot = atomicAdd(&rep->n_records, 1u);
-          if (slot < FTBLAS_MAX_RECORDS) {
-            ft_error_record_t& rc = rep->rec[slot];
-            rc.tile_row = 0; rc.tile_col = blockIdx.x;
-            rc.i = first; rc.j = j;
-            rc.delta_row = 0.0; rc.delta_col = delta; rc.tau_row = 0.0; rc.tau_col = tau;
-            rc.value_before = first >= 0 ? sm.wf[first][t] : 0.0;
-            rc.value_after = first >= 0 ? sm.w[first][t] : 0.0;
-            rc.rows_flagged = 0; rc.cols_flagged = 1;
-            rc.kind = FT_KIND_CORRECTED;
-            rc.reserved = 0;
-          } else {
-            atomicOr(&rep->status, FT_STATUS_RECORDS_TRUNCATED);
-          }
+      if (rep) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&rep->detected), 1ull);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&rep->corrected), 1ull);
+        const unsigned slot = atomicAdd(&rep->n_records, 1u);
+        if (slot < FTBLAS_MAX_RECORDS) {
+          ft_error_record_t& rc = rep->rec[slot];
+          rc.tile_row = 0; rc.tile_col = blockIdx.x;
+          rc.i = first; rc.j = j;
+          rc.delta_row = 0.0; rc.delta_col = delta; rc.tau_row = 0.0; rc.tau_col = tau;
+          rc.value_before = first >= 0 ? sm.wf[first][t] : 0.0;
+          rc.value_after = first >= 0 ? sm.w[first][t] : 0.0;
+          rc.rows_flagged = 0; rc.cols_flagged = 1;
+          rc.kind = FT_KIND_CORRECTED;
+          rc.reserved = 0;
+        } else {
+          atomicOr(&rep->status, FT_STATUS_RECORDS_TRUNCATED);
         }
       }
     }
