@@ -123,12 +123,13 @@ __device__ void solve_diag_block_par(LeafSmem& sm, int c, int g, int r0, int r1,
       sm.w[r][c] = x;
     }
     x = __shfl_sync(0xffffffffu, x, (lane & ~(kGroups - 1)) | owner);
+    // this thread's rows only (a predicated-off FMA would still take a slot of the FP64 pipe)
     if (lower) {
-      for (int s2 = r + 1; s2 < r1; ++s2)
-        if (s2 % kGroups == g) sm.w[s2][c] = fma(-tri(sm, s2, r, n, lower), x, sm.w[s2][c]);
+      const int first = r + 1 + ((g - (r + 1)) % kGroups + kGroups) % kGroups;
+      for (int s2 = first; s2 < r1; s2 += kGroups) sm.w[s2][c] = fma(-tri(sm, s2, r, n, lower), x, sm.w[s2][c]);
     } else {
-      for (int s2 = r0; s2 < r; ++s2)
-        if (s2 % kGroups == g) sm.w[s2][c] = fma(-tri(sm, s2, r, n, lower), x, sm.w[s2][c]);
+      const int first = r0 + ((g - r0) % kGroups + kGroups) % kGroups;
+      for (int s2 = first; s2 < r; s2 += kGroups) sm.w[s2][c] = fma(-tri(sm, s2, r, n, lower), x, sm.w[s2][c]);
     }
   }
 }
@@ -224,12 +225,31 @@ __global__ void __launch_bounds__(kThreads) trsm_leaf_kernel(const double* T, in
     double xk[kBlk];
 #pragma unroll
     for (int k = 0; k < kBlk; ++k) xk[k] = r0 + k < r1 ? sm.w[r0 + k][uc] : 0.0;
-    for (int row = lo + ug; row < hi; row += kGroups) {
-      double acc = sm.w[row][uc];
+    // four rows at a time: four independent chains hide the FP64 latency; each row's chain is
+    // that of update_row
+    constexpr int kRows = 4;
+    for (int row = lo + ug; row < hi; row += kGroups * kRows) {
+      double acc[kRows];
 #pragma unroll
-      for (int k = 0; k < kBlk; ++k)
-        if (r0 + k < r1) acc = fma(-tri(sm, row, r0 + k, n, low), xk[k], acc);  // as update_row
-      sm.w[row][uc] = acc;
+      for (int q = 0; q < kRows; ++q) {
+        const int rr = row + q * kGroups;
+        acc[q] = rr < hi ? sm.w[rr][uc] : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < kBlk; ++k) {
+        if (r0 + k < r1) {
+#pragma unroll
+          for (int q = 0; q < kRows; ++q) {
+            const int rr = row + q * kGroups;
+            if (rr < hi) acc[q] = fma(-tri(sm, rr, r0 + k, n, low), xk[k], acc[q]);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kRows; ++q) {
+        const int rr = row + q * kGroups;
+        if (rr < hi) sm.w[rr][uc] = acc[q];
+      }
     }
     __syncthreads();
   }
