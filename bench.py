@@ -141,7 +141,21 @@ def workload_config(n, engine, tile=TILE):
             "layout": "column-major, no transpose", "inputs": "A, B, C uniform[-1,1) from a fixed seed",
             "injection": "one seeded accumulator bit flip (bits 40-62) per 10 launches",
             "verification_tile": f"{tile}x{tile}", "engine": engine,
-            "l2": "inputs 512 MiB per operand > 129 MB L2; no flush between steps"}
+            "l2": l2_note(n * n * 8)}
+
+
+def l2_note(operand_bytes):
+    """How the timed steps stand to the 129 MB L2: inputs larger than it, or not, with no flush."""
+    mib = operand_bytes / 2**20
+    rel = "larger than" if operand_bytes > 129e6 else "within"
+    return f"inputs {mib:.0f} MiB per operand, {rel} the 129 MB L2; no flush between steps"
+
+
+def l2_note_tc(operand_bytes, c_bytes):
+    """The same for the tensor-core forms: both operands together, and the FP32 C."""
+    rel = "larger than" if operand_bytes + c_bytes > 129e6 else "within"
+    return (f"operands {operand_bytes / 2**20:.0f} MiB + C {c_bytes / 2**20:.0f} MiB, {rel} the 129 MB L2; "
+            "no flush between steps")
 
 
 # ------------------------------------------------------------------ multi-rank host logic
@@ -459,8 +473,7 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
         "method": "ft_tflops, noabft_tflops and the overhead from unprotected and protected calls alternated in "
                   "one region (per-call CUDA events); ft_tflops_injected from a region of injected calls; the "
                   "roofline from the product-kernel events of a region of protected calls",
-        "l2": f"operands {2 * n * n * (1 if fp8 else 2) / 2**20:.0f} MiB + C {n * n * 4 / 2**20:.0f} MiB > 129 MB L2; "
-              "no flush between steps",
+        "l2": l2_note_tc(2 * n * n * (1 if fp8 else 2), n * n * 4),
         "error_vs_fp64": {"max_over_sum_abs_ab": err_norm, "median_rel": err_rel,
                           "sampled": f"{len(rows)} rows x {len(cols)} columns",
                           "note": f"C - (A B computed in binary64 from the same {kind.upper()} operands)"},
