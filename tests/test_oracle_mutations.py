@@ -22,6 +22,19 @@ MUTATIONS = {
                            "for (int64_t j = j0 + 1; j < j0 + nJ; ++j) { double b = b_elem(p, k, j); s = s + b;"),
     "missing_alpha_in_prediction": ("double Cc = p->alpha * dotp;", "double Cc = dotp;"),
     "online_recompute_over_all_of_K": ("for (int64_t k = 0; k < kh; ++k) {", "for (int64_t k = 0; k < K; ++k) {"),
+    "column_prediction_from_magnitude_sums": ("dotp = dotp + Ac[k] * b;", "dotp = dotp + Ac_abs[k] * b;"),
+    # binary32-accumulation model of the tensor-core forms
+    "acc32_output_not_rounded": ("double v = round32(scale_out(p, acc, i, j));", "double v = scale_out(p, acc, i, j);"),
+    "acc32_correction_keeps_faulty_element": ("if (jj != fcl) rest = rest + T[fr + jj * nI];",
+                                              "rest = rest + T[fr + jj * nI];"),
+    "acc32_accumulator_flip_in_binary64": ("acc = flip_bit32(acc, inj[q].bit);", "acc = flip_bit(acc, inj[q].bit);"),
+    "acc32_row_recompute_with_beta": ("const int recompute_row = (nr == 1 && nc == 0 && p->beta == 0.0);",
+                                      "const int recompute_row = (nr == 1 && nc == 0);"),
+    # triangular solve
+    "trsm_lower_sums_the_diagonal": ("for (int64_t c = 0; c < r; ++c) s = s + T[r + c * ldt] * w[c];",
+                                     "for (int64_t c = 0; c <= r; ++c) s = s + T[r + c * ldt] * w[c];"),
+    "trsm_upper_reads_the_diagonal": ("for (int64_t c = r + 1; c < n; ++c) s = s + T[r + c * ldt] * w[c];",
+                                      "for (int64_t c = r; c < n; ++c) s = s + T[r + c * ldt] * w[c];"),
 }
 
 
