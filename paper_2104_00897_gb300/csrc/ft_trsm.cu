@@ -336,9 +336,16 @@ __global__ void report_merge_kernel(const ft_report_t* parts, const int64_t* row
 cudaError_t launch_copy2d(const double* src, int64_t rs, int64_t cs, double* dst, int64_t ld, int64_t rows,
                           int64_t cols, double scale, cudaStream_t st) {
   if (rows == 0 || cols == 0) return cudaSuccess;
-  dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
-  copy2d_kernel<<<grid, dim3(32, 8), 0, st>>>(src, rs, cs, dst, ld, rows, cols, scale);
-  return cudaGetLastError();
+  // gridDim.y is at most 65535: wider copies go in column chunks of 65535 x 32
+  constexpr int64_t kChunk = 65535 * 32;
+  for (int64_t c0 = 0; c0 < cols; c0 += kChunk) {
+    const int64_t nc = cols - c0 < kChunk ? cols - c0 : kChunk;
+    dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((nc + 31) / 32));
+    copy2d_kernel<<<grid, dim3(32, 8), 0, st>>>(src + c0 * cs, rs, cs, dst + c0 * ld, ld, rows, nc, scale);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_trsm_leaf(const double* T, int64_t ldt, double* W, int64_t ldw, int n, int64_t nrhs, bool lower,

@@ -349,6 +349,56 @@ int dsymm_impl(int layout, int side, int uplo, int64_t M, int64_t N, double alph
   return rc;
 }
 
+// FT-DTRMM's tiles do unequal work: each visits only the k-tiles its triangle leaves
+// nonzero, from all of K down to one. The kernel's launch order, which the block scheduler
+// follows, runs row tiles fastest and column tiles slowest. So the heaviest tiles come
+// first, and the lightest fill the last wave, exactly when the triangular operand is the
+// kernel frame's op(B) and is lower (column tile j needs k >= j). With the triangular
+// operand as the kernel's op(A), heavy and light tiles alternate. As op(B) upper, the
+// heaviest come last. Running the product in the other storage layout transposes the
+// kernel frame: op(A) becomes op(B) and upper becomes lower. Each element keeps the same
+// products in the same k order, so the values are unchanged. The cost is a transposing
+// copy of B in and of the result out.
+// Placement score: 2 for op(B) lower, 1 for op(A), 0 for op(B) upper.
+int tri_placement_score(bool on_a, int t) { return on_a ? 1 : (t == 2 ? 2 : 0); }
+
+bool use_other_layout(bool col, bool left, int tri) {
+  auto flip = [](int t) { return t == 1 ? 2 : 1; };
+  // in the caller's layout: column-major puts op(A) of a left product in the kernel's op(A);
+  // row-major swaps the kernel's operands and transposes them
+  const bool on_a = col == left;
+  const int t = col ? tri : flip(tri);
+  return tri_placement_score(!on_a, flip(t)) > tri_placement_score(on_a, t);
+}
+
+int dtrmm_other_layout(bool col, int side, int uplo, int transa, int diag, int64_t M, int64_t N, double alpha,
+                       const double* A, int64_t lda, double* B, int64_t ldb, cudaStream_t st, ft_report_t* report,
+                       int tri, int64_t rows, int64_t cols) {
+  // B's storage holds `cols` lines of `rows` contiguous elements; in the other layout the
+  // copies Bt (the operand) and Ct (the product) hold `rows` lines of `cols`, ld = cols.
+  const int64_t dim = side == FTBLAS_LEFT ? M : N;
+  double* T = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&T), (size_t)(dim * dim + 2 * rows * cols) * 8, st) != cudaSuccess)
+    return FTBLAS_STATUS_ALLOC_FAILED;
+  double* Bt = T + dim * dim;
+  double* Ct = Bt + rows * cols;
+  // op(A)^T in the caller's layout is op(A) in the other one
+  int rc = record_cuda(launch_expand(A, lda, !col, dim, 1, uplo == FTBLAS_UPPER, transa != FTBLAS_TRANS,
+                                     diag == FTBLAS_UNIT, T, st));
+  if (rc == 0) rc = record_cuda(launch_copy2d(B, ldb, 1, Bt, cols, cols, rows, 1.0, st));
+  if (rc == 0) {
+    const int other = col ? FTBLAS_ROW_MAJOR : FTBLAS_COL_MAJOR;
+    rc = side == FTBLAS_LEFT
+             ? dgemm_impl(other, FTBLAS_NO_TRANS, FTBLAS_NO_TRANS, M, N, M, alpha, T, dim, Bt, cols, 0.0, Ct, cols,
+                          st, report, true, tri, 0)
+             : dgemm_impl(other, FTBLAS_NO_TRANS, FTBLAS_NO_TRANS, M, N, N, alpha, Bt, cols, T, dim, 0.0, Ct, cols,
+                          st, report, true, 0, tri);
+  }
+  if (rc == 0) rc = record_cuda(launch_copy2d(Ct, cols, 1, B, ldb, rows, cols, 1.0, st));
+  cudaFreeAsync(T, st);
+  return rc;
+}
+
 int dtrmm_impl(int layout, int side, int uplo, int transa, int diag, int64_t M, int64_t N, double alpha,
                const double* A, int64_t lda, double* B, int64_t ldb, void* stream, ft_report_t* report) {
   if (layout != FTBLAS_ROW_MAJOR && layout != FTBLAS_COL_MAJOR) return -1;
@@ -377,6 +427,9 @@ int dtrmm_impl(int layout, int side, int uplo, int transa, int diag, int64_t M, 
   const bool op_upper = (uplo == FTBLAS_UPPER) == (transa == FTBLAS_NO_TRANS);
   const int tri = op_upper ? 1 : 2;
   const int64_t rows = col ? M : N, cols = col ? N : M;  // storage extent of B
+  if (use_other_layout(col, side == FTBLAS_LEFT, tri))
+    return dtrmm_other_layout(col, side, uplo, transa, diag, M, N, alpha, A, lda, B, ldb, st, report, tri, rows,
+                              cols);
   double *T = nullptr, *B0 = nullptr;
   if (cudaMallocAsync(reinterpret_cast<void**>(&T), (size_t)(dim * dim + rows * cols) * 8, st) != cudaSuccess)
     return FTBLAS_STATUS_ALLOC_FAILED;
