@@ -140,7 +140,8 @@ def workload_config(n, engine, tile=TILE):
     return {"workload": f"ft_dgemm_fp64_col_major_{n}x{n}x{n}", "M": n, "N": n, "K": n, "alpha": 1.5, "beta": 0.5,
             "layout": "column-major, no transpose", "inputs": "A, B, C uniform[-1,1) from a fixed seed",
             "injection": "one seeded accumulator bit flip (bits 40-62) per 10 launches",
-            "verification_tile": f"{tile}x{tile}", "engine": engine,
+            "verification_tile": f"{tile}x{tile}", "engine": engine, "seed": SEED,
+            "seed_per_rank": "seed + rank (each rank solves its own problem)",
             "l2": l2_note(n * n * 8)}
 
 
@@ -473,6 +474,7 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
         "method": "ft_tflops, noabft_tflops and the overhead from unprotected and protected calls alternated in "
                   "one region (per-call CUDA events); ft_tflops_injected from a region of injected calls; the "
                   "roofline from the product-kernel events of a region of protected calls",
+        "seed": seed,
         "l2": l2_note_tc(2 * n * n * (1 if fp8 else 2), n * n * 4),
         "error_vs_fp64": {"max_over_sum_abs_ab": err_norm, "median_rel": err_rel,
                           "sampled": f"{len(rows)} rows x {len(cols)} columns",
