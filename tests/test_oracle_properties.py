@@ -1,0 +1,125 @@
+"""Randomised properties of the oracle (CPU only; hypothesis draws the cases).
+
+Shapes, layouts, transposes, alpha, beta, verification-tile geometries and k-tile depths
+are drawn at random. Each example checks facts that hold independently of the oracle's
+code:
+
+- Section II.A's checksum relations, e^T C = alpha (e^T op(A)) op(B) + beta e^T C_in and
+  C e = alpha op(A) (op(B) e) + beta C_in e, summed here without rounding (math.fsum over
+  the individual products) and compared within the rounding bound of the product;
+- the product against a library matmul within the standard bound 2 gamma_{K+2}
+  (|alpha| |A||B| + |beta| |C_in|);
+- a clean protected run flags nothing and checks every tile;
+- on integer operands, where every checksum is exact, one output error of any size and sign
+  at any element (Section VI.C) is located at that element. Its row and column mismatches
+  both equal the error exactly, and the recomputed C equals the fault-free C bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth as S
+from tests.helpers import stored
+
+hypothesis = pytest.importorskip("hypothesis")
+from hypothesis import HealthCheck, assume, given, settings  # noqa: E402
+from hypothesis import strategies as st  # noqa: E402
+
+U = 2.0 ** -53
+SETTINGS = settings(max_examples=120, deadline=None, suppress_health_check=[HealthCheck.too_slow])
+
+
+def gamma(n):
+    return n * U / (1 - n * U)
+
+
+def c_store(layout, C_log, pad):
+    ld = (C_log.shape[0] if layout == O.COL_MAJOR else C_log.shape[1]) + pad
+    return S.store(C_log, layout, ld=max(1, ld))
+
+
+def run(case, A, B, Cin, protected, inj=()):
+    layout, ta, tb, alpha, beta, tm, tn, bk, pad = (case[k] for k in
+                                                    ("layout", "ta", "tb", "alpha", "beta", "tm", "tn", "bk", "pad"))
+    M, K = A.shape
+    N = B.shape[1]
+    a, lda = stored(layout, ta, A, pad=pad)
+    b, ldb = stored(layout, tb, B, pad=pad)
+    c, ldc = c_store(layout, Cin, pad)
+    if not protected:
+        return S.load(O.gemm(layout, ta, tb, M, N, K, alpha, a, lda, b, ldb, beta, c, ldc), layout, M, N, ldc)
+    out, rep = O.ft_gemm(layout, ta, tb, M, N, K, alpha, a, lda, b, ldb, beta, c, ldc, tm, tn, bk, injections=inj)
+    return S.load(out, layout, M, N, ldc), rep
+
+
+def cases(alphas, betas):
+    return st.fixed_dictionaries({
+        "M": st.integers(1, 20), "N": st.integers(1, 20), "K": st.integers(1, 24),
+        "layout": st.sampled_from([O.COL_MAJOR, O.ROW_MAJOR]),
+        "ta": st.sampled_from([O.NO_TRANS, O.TRANS]), "tb": st.sampled_from([O.NO_TRANS, O.TRANS]),
+        "alpha": st.sampled_from(alphas), "beta": st.sampled_from(betas),
+        "tm": st.integers(1, 8), "tn": st.integers(1, 8), "bk": st.integers(1, 6),
+        "pad": st.integers(0, 3), "seed": st.integers(0, 10 ** 6),
+    })
+
+
+@SETTINGS
+@given(cases([1.0, -0.75, 1.5, 2.0], [0.0, 0.5, -1.0]))
+def test_product_checksum_relations_and_library_bound(case):
+    M, N, K, seed = case["M"], case["N"], case["K"], case["seed"]
+    alpha, beta = case["alpha"], case["beta"]
+    A = S.uniform_matrix(seed, 0, M, K)
+    B = S.uniform_matrix(seed, 1, K, N)
+    Cin = S.uniform_matrix(seed, 2, M, N)
+    C = run(case, A, B, Cin, protected=False)
+    mag = abs(alpha) * (np.abs(A) @ np.abs(B)) + abs(beta) * np.abs(Cin)
+    # library cross-check
+    lib = alpha * (A @ B) + beta * Cin
+    assert np.all(np.abs(C - lib) <= 2 * gamma(K + 2) * mag + 1e-300)
+    # Section II.A relations, right-hand sides summed without intermediate rounding
+    g = gamma(K + 3)
+    for j in range(N):
+        rhs = math.fsum([alpha * A[i, k] * B[k, j] for i in range(M) for k in range(K)] +
+                        [beta * Cin[i, j] for i in range(M)])
+        assert abs(math.fsum(C[:, j]) - rhs) <= 2 * g * mag[:, j].sum() + 1e-300
+    for i in range(M):
+        rhs = math.fsum([alpha * A[i, k] * B[k, j] for j in range(N) for k in range(K)] +
+                        [beta * Cin[i, j] for j in range(N)])
+        assert abs(math.fsum(C[i, :]) - rhs) <= 2 * g * mag[i, :].sum() + 1e-300
+
+
+@SETTINGS
+@given(cases([1.0, -0.75, 1.5], [0.0, 0.5, -1.0]))
+def test_clean_protected_run_checks_every_tile_and_flags_nothing(case):
+    M, N, K, seed = case["M"], case["N"], case["K"], case["seed"]
+    A = S.uniform_matrix(seed, 0, M, K)
+    B = S.uniform_matrix(seed, 1, K, N)
+    Cin = S.uniform_matrix(seed, 2, M, N)
+    got, rep = run(case, A, B, Cin, protected=True)
+    assert rep.detected == 0 and rep.input_nonfinite == 0 and rep.n_records == 0
+    assert rep.tiles_checked == math.ceil(M / case["tm"]) * math.ceil(N / case["tn"])
+    assert np.array_equal(got, run(case, A, B, Cin, protected=False))
+
+
+@SETTINGS
+@given(cases([1.0, 2.0, -1.0], [0.0, 1.0, -2.0]), st.integers(0, 10 ** 6), st.integers(-3, 6),
+       st.sampled_from([1, -1]))
+def test_one_output_error_anywhere_is_located_and_removed_exactly(case, where, p, sign):
+    M, N, K, seed = case["M"], case["N"], case["K"], case["seed"]
+    A = S.randint(seed, 0, M * K, -4, 4).reshape(M, K).astype(np.float64)
+    B = S.randint(seed, 1, K * N, -4, 4).reshape(K, N).astype(np.float64)
+    Cin = S.randint(seed, 2, M * N, -9, 9).reshape(M, N).astype(np.float64)
+    clean = run(case, A, B, Cin, protected=False)
+    i, j = (where // N) % M, where % N
+    assume(clean[i, j] != 0)
+    e = sign * 2.0 ** p * abs(clean[i, j])
+    got, rep = run(case, A, B, Cin, protected=True,
+                   inj=[dict(i=i, j=j, site=O.SITE_OUTPUT, mode=O.MODE_ADD_REL, rel_log2=p, sign=sign)])
+    assert (rep.detected, rep.corrected, rep.uncorrectable, rep.checksum_only) == (1, 1, 0, 0)
+    r = rep.records()[0]
+    assert (r.i, r.j) == (i, j)
+    assert (r.tile_row, r.tile_col) == (i // case["tm"], j // case["tn"])
+    assert r.delta_row == e and r.delta_col == e
+    assert np.array_equal(got, clean)
