@@ -123,3 +123,84 @@ def test_one_output_error_anywhere_is_located_and_removed_exactly(case, where, p
     assert (r.tile_row, r.tile_col) == (i // case["tm"], j // case["tn"])
     assert r.delta_row == e and r.delta_col == e
     assert np.array_equal(got, clean)
+
+
+# ------------------------------------------------------------------------------------
+# The binary32-accumulation model of the tensor-core forms (ACC32)
+# ------------------------------------------------------------------------------------
+
+def bf16_exact(X):
+    return S.bf16_bits_to_f64(S.to_bf16_bits(X))
+
+
+@SETTINGS
+@given(cases([1.0, 2.0], [0.0, 1.0, -2.0]))
+def test_acc32_output_is_the_exact_product_rounded_once_to_binary32(case):
+    """A on the grid 2^-8 Z and B, C_in bfloat16 of magnitude 0 or at least 2^-12 in
+    [-1, 1): every product is a multiple of 2^-27 below 1, so with K <= 24 and alpha, beta
+    powers of two, alpha acc + beta C_in has at most 33 significant bits and is exact in
+    binary64 in any order. C must be that value rounded to nearest binary32 (a real
+    rounding: up to 33 bits into 24), and a clean run must flag nothing."""
+    M, N, K, seed = case["M"], case["N"], case["K"], case["seed"]
+
+    def bf16_not_tiny(X):
+        X = bf16_exact(X)
+        return np.where(np.abs(X) < 2.0 ** -12, 0.0, X)
+
+    A = np.round(S.uniform_matrix(seed, 0, M, K) * 256.0) / 256.0
+    B = bf16_not_tiny(S.uniform_matrix(seed, 1, K, N))
+    Cin = bf16_not_tiny(S.uniform_matrix(seed, 2, M, N))
+    exact = case["alpha"] * (A @ B) + case["beta"] * Cin  # every step exact here
+    a, lda = stored(case["layout"], case["ta"], A, pad=case["pad"])
+    b, ldb = stored(case["layout"], case["tb"], B, pad=case["pad"])
+    c, ldc = c_store(case["layout"], Cin, case["pad"])
+    out, rep = O.ft_gemm(case["layout"], case["ta"], case["tb"], M, N, K, case["alpha"], a, lda, b, ldb,
+                         case["beta"], c, ldc, case["tm"], case["tn"], case["bk"], precision=O.PREC_ACC32)
+    got = S.load(out, case["layout"], M, N, ldc)
+    assert np.array_equal(got, exact.astype(np.float32).astype(np.float64))
+    assert rep.detected == 0 and rep.tiles_checked == math.ceil(M / case["tm"]) * math.ceil(N / case["tn"])
+
+
+@SETTINGS
+@given(cases([1.0, -0.75, 1.5], [0.0, 0.5]), st.integers(-8, 8))
+def test_acc32_clean_runs_never_flag_under_row_scaling(case, shift):
+    M, N, K, seed = case["M"], case["N"], case["K"], case["seed"]
+    A = bf16_exact(S.normal_matrix(seed, 0, M, K) * S.pow2_row_scales(seed, 5, M)[:, None] * 2.0 ** shift)
+    B = bf16_exact(S.normal_matrix(seed, 1, K, N))
+    Cin = S.normal_matrix(seed, 2, M, N)
+    a, lda = stored(case["layout"], case["ta"], A, pad=case["pad"])
+    b, ldb = stored(case["layout"], case["tb"], B, pad=case["pad"])
+    c, ldc = c_store(case["layout"], Cin, case["pad"])
+    _, rep = O.ft_gemm(case["layout"], case["ta"], case["tb"], M, N, K, case["alpha"], a, lda, b, ldb,
+                       case["beta"], c, ldc, case["tm"], case["tn"], case["bk"], precision=O.PREC_ACC32)
+    assert rep.detected == 0
+
+
+@SETTINGS
+@given(cases([1.0, 2.0, -1.0], [0.0, 1.0]), st.integers(0, 10 ** 6), st.integers(0, 6), st.sampled_from([1, -1]))
+def test_acc32_one_output_error_anywhere_is_located_and_removed_exactly(case, where, p, sign):
+    M, N, K, seed = case["M"], case["N"], case["K"], case["seed"]
+    A = S.randint(seed, 0, M * K, -4, 4).reshape(M, K).astype(np.float64)
+    B = S.randint(seed, 1, K * N, -4, 4).reshape(K, N).astype(np.float64)
+    Cin = S.randint(seed, 2, M * N, -9, 9).reshape(M, N).astype(np.float64)
+    a, lda = stored(case["layout"], case["ta"], A, pad=case["pad"])
+    b, ldb = stored(case["layout"], case["tb"], B, pad=case["pad"])
+    c, ldc = c_store(case["layout"], Cin, case["pad"])
+
+    def call(inj):
+        out, rep = O.ft_gemm(case["layout"], case["ta"], case["tb"], M, N, K, case["alpha"], a, lda, b, ldb,
+                             case["beta"], c, ldc, case["tm"], case["tn"], case["bk"], injections=inj,
+                             precision=O.PREC_ACC32)
+        return S.load(out, case["layout"], M, N, ldc), rep
+
+    clean, rep0 = call(())
+    assert rep0.detected == 0
+    assert np.array_equal(clean, case["alpha"] * (A @ B) + case["beta"] * Cin)  # small integers: exact
+    i, j = (where // N) % M, where % N
+    assume(clean[i, j] != 0)
+    got, rep = call([dict(i=i, j=j, site=O.SITE_OUTPUT, mode=O.MODE_ADD_REL, rel_log2=p, sign=sign)])
+    assert (rep.detected, rep.corrected) == (1, 1)
+    r = rep.records()[0]
+    assert (r.i, r.j) == (i, j)
+    assert r.delta_row == sign * 2.0 ** p * abs(clean[i, j])
+    assert np.array_equal(got, clean)
