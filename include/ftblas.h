@@ -183,13 +183,14 @@ int ftblas_dsymm(ftblas_layout_t layout, ftblas_side_t side, ftblas_uplo_t uplo,
  * A triangular (`uplo`, `diag`: FTBLAS_UNIT takes the diagonal as 1 without reading it), B
  * overwritten. A copy of op(A) with explicit zeros and a copy of B are formed on `stream`,
  * then ftblas_dgemm's protected kernel runs, each tile visiting only the k-tiles the
- * triangle leaves nonzero (about half the work of the full product). Where that puts the
- * heaviest tiles first in launch order, the copies and the product are made in the other
- * storage layout and the product is copied back: the values are the same, and the
- * workspace is then n^2 + 2 M N doubles instead of n^2 + M N (n = M or N, A's order). Protection as for
- * ftblas_dgemm; an accumulator injection point whose k-tile (explicit, or floor(nk/2)) falls
- * outside its tile's range is not applied. Arguments 1-14 in CBLAS order (layout, side, uplo,
- * transa, diag, M, N, alpha, A, lda, B, ldb, stream, report). */
+ * triangle leaves nonzero (about half the work of the full product). When the other
+ * storage layout gives a better launch order of these unequal tiles (heaviest first, or
+ * no longer heaviest last), the copies and the product are made in that layout and the
+ * product is copied back. The values are the same. The workspace is then n^2 + 2 M N
+ * doubles instead of n^2 + M N (n = M or N, A's order). Protection as for ftblas_dgemm; an
+ * accumulator injection point whose k-tile (explicit, or floor(nk/2)) falls outside its
+ * tile's range is not applied. Arguments 1-14 in CBLAS order (layout, side, uplo, transa,
+ * diag, M, N, alpha, A, lda, B, ldb, stream, report). */
 int ftblas_dtrmm(ftblas_layout_t layout, ftblas_side_t side, ftblas_uplo_t uplo, ftblas_trans_t transa,
                  ftblas_diag_t diag, int64_t M, int64_t N, double alpha, const double* A, int64_t lda,
                  double* B, int64_t ldb, void* stream, ft_report_t* report);
