@@ -290,7 +290,6 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
     the fraction of injected output errors 2^p |C| corrected per p."""
     import torch
 
-    import oracle as O
     import paper_2104_00897_gb300 as fb
     import synth as S
 
@@ -326,7 +325,7 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
     flops = 2.0 * n ** 3
 
     def call(protect, rep=None):
-        a = (O.COL_MAJOR, O.TRANS, O.NO_TRANS, n, n, n, 1.0, dA.data_ptr(), dtype, n, dB.data_ptr(), dtype, n,
+        a = (fb.COL_MAJOR, fb.TRANS, fb.NO_TRANS, n, n, n, 1.0, dA.data_ptr(), dtype, n, dB.data_ptr(), dtype, n,
              0.0, dC.data_ptr(), fb.R_32F, n, fb.R_32F, sa_ptr, sb_ptr, st)
         if protect:
             fb.check(fb.ftblas_gemm_ex(*a, rep.data_ptr() if rep is not None else None), "ftblas_gemm_ex")
@@ -1079,10 +1078,9 @@ def run_ours(args, rank, world, dist):
                                           "uncorrectable": int(r2.uncorrectable)}}
 
     # Accuracy at the stated error: one more protected call from the known C_in, checked on
-    # sampled rows against the oracle.
+    # sampled rows against the binary64 product of the same operands (a library matmul).
     err = None
     if rank == 0:
-        import oracle as O
         import synth as S
         dC.copy_(dCin)
         fb.check(fb.ftblas_dgemm(fb.COL_MAJOR, fb.NO_TRANS, fb.NO_TRANS, n, n, n, 1.5, dA.data_ptr(), n,
@@ -1090,7 +1088,8 @@ def run_ours(args, rank, world, dist):
         torch.cuda.synchronize(dev)
         rows = np.unique(S.randint(SEED, 9, 4, 0, n - 1))
         got = dC.view(n, n).t()[torch.as_tensor(rows, device=dev)].cpu().numpy()  # column-major: C[i, :]
-        ref = O.gemm_rows(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, n, n, n, 1.5, A, n, B, n, 0.5, Cin, n, rows)
+        Am, Bm, Cm = (X.reshape(n, n, order="F") for X in (A, B, Cin))  # column-major storage
+        ref = 1.5 * (Am[rows, :] @ Bm) + 0.5 * Cm[rows, :]
         err = float(np.abs(got - ref).max() / (np.abs(A).max() * np.abs(B).max() * n))
 
     # End to end through the public host-buffer entry point: pinned host operands, copies
@@ -1152,8 +1151,8 @@ def run_ours(args, rank, world, dist):
         "pct_of_peak": 100.0 * achieved / peak,
         "abft_overhead_pct": engines_out[args.engine]["abft_overhead_pct_injected"],
         "abft_overhead_pct_clean": engines_out[args.engine]["abft_overhead_pct_clean"],
-        "error_vs_oracle": {"normalized_max": err, "criterion": "max|C-C_ref|/(max|A| max|B| K) <= 1e-15",
-                            "rows_sampled": 4},
+        "error_vs_fp64": {"normalized_max": err, "criterion": "max|C-C_ref|/(max|A| max|B| K) <= 1e-15",
+                          "rows_sampled": 4, "reference": "binary64 product of the same operands (library matmul)"},
         "faults": {"injected": h["injected"], "detected": h["ft_rep"]["detected"],
                    "corrected": h["ft_rep"]["corrected"], "uncorrectable": h["ft_rep"]["uncorrectable"],
                    "false_alarms_clean_run": h["clean_rep"]["detected"], "status": h["ft_rep"]["status"]},
