@@ -61,7 +61,7 @@ struct EncArgs {
   TcPending* pend;         // rows pass: its tile count is zeroed before the GEMM
   float* line_part;        // rows pass: [nkc][M] upward sum of |A(i,k)| over one k-chunk
   float* maxAbsBe;         // [nblocks of B]
-  void* chk;               // columns pass: pieces of B e in rows J*16 + p (unused rows zero)
+  void* chk;               // columns pass: pieces of B e in rows J*8 + p (unused rows zero)
 };
 
 // Shared memory of one encode CTA, declared once per kernel (both roles use it): the
