@@ -112,11 +112,21 @@ TC_KERNEL_SOURCES = ("paper_2104_00897_gb300/csrc/ft_gemm_tc.cu", "paper_2104_00
 
 
 def sources_sha256(paths):
+    """SHA-256 of the kernel's code: its sources without comments and blank lines, each
+    line stripped. An edit of comments or layout alone keeps a capture's counters valid;
+    any change of code voids them."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for rel in paths:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for line in src.split("\n"):
+            line = line.strip()
+            if line:
+                h.update(line.encode() + b"\n")
     return h.hexdigest()
 
 

@@ -1,5 +1,6 @@
 // Reduced-precision ABFT-protected GEMM on the fifth-generation tensor cores (sm_103a):
-// BF16 operands, FP32 accumulation in TMEM, FP32 output, FP64 checksum comparison.
+// BF16 or FP8 E4M3 operands, FP32 accumulation in TMEM, FP32 output, FP64 checksum
+// comparison.
 //
 // FT-BLAS (Zhai et al., ICS '21) has no reduced precision; the checksum relations are those
 // of Section II.A, the lazy second side that of Section V.A, and C = beta*C is folded into
@@ -20,12 +21,13 @@
 //               product itself, at no extra instruction (8 of 256 columns per tile).
 //   warps 2..5  epilogue, one TMEM lane (= output row) per thread: C = alpha acc + beta C_in
 //               stored in FP32; C^r_ref(i) = sum_j C(i,j) in compensated binary32, compared
-//               in binary64 with the predicted checksum against a rigorous bound. Only in a
-//               tile with a mismatching row are the column checksums formed (C^c_ref from
-//               the stored tile, C^c = (e^T A) B from global memory in binary32)
-//               to locate the error; when the columns cannot locate it (rows of very
-//               different scale), the mismatching row is recomputed and compared element by
-//               element. The located element is corrected from the row checksum.
+//               in binary64 with the predicted checksum against a rigorous bound. A tile
+//               with a mismatching row is entered in a pending list.
+// After the GEMM, tc_resolve_kernel takes the pending tiles (the lazy second side): it forms
+// their column checksums (C^c_ref from the stored tile, C^c = (e^T A) B from global memory
+// in binary32) to locate the error. When the columns cannot locate it (rows of very
+// different scale), it recomputes the mismatching row and compares element by element. The
+// located element is corrected from the row checksum.
 #include <climits>
 #include <cstring>
 

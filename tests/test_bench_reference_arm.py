@@ -4,6 +4,7 @@
 prints one line with the same metric, unit and config keys as the GPU arm, plus the
 `cpu_baseline` and a zero-copy `e2e`. Under a multi-rank launch rank 0 alone runs and prints;
 the other ranks exit 0 without work. Both launches run on the CPU here, at a small size.
+Also the fingerprint that ties a committed DRAM capture to the kernel code it measured.
 """
 import json
 import os
@@ -76,3 +77,19 @@ def test_reference_arm_two_ranks_rank0_prints_once():
     lines = _json_lines(r.stdout)
     assert len(lines) == 1
     _check_line(lines[0], 512, 1, 3, 2)
+
+
+def test_profile_fingerprint_ignores_comments_and_catches_code_changes(tmp_path, monkeypatch):
+    """A committed DRAM capture stays valid while only comments or layout change, and is
+    voided by any change of code."""
+    monkeypatch.syspath_prepend(ROOT)
+    import bench
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    src = tmp_path / "k.cu"
+    src.write_text("// header\n__global__ void k(float* x) {\n  x[0] = 1.0f;  // store\n}\n")
+    h0 = bench.sources_sha256(["k.cu"])
+    src.write_text("/* a new\n   block comment */\n// header, reworded\n\n__global__ void k(float* x) {\n"
+                   "    x[0] = 1.0f;\n}\n")
+    assert bench.sources_sha256(["k.cu"]) == h0
+    src.write_text("// header\n__global__ void k(float* x) {\n  x[0] = 2.0f;  // store\n}\n")
+    assert bench.sources_sha256(["k.cu"]) != h0
