@@ -1,7 +1,7 @@
 // FP64 ABFT-protected GEMM for sm_103a (FT-BLAS, Zhai et al., ICS '21, Sections II.A, V).
 //
-// One CTA computes one 128 x 128 output tile over all of K; that tile is the verification
-// interval. Per k-tile (32 deep) the operand tiles are staged in shared memory by TMA
+// One CTA computes one output tile over all of K, 128 x 128 (or 64 x 64 where 128-edge
+// tiles would leave SMs idle); that tile is the verification interval. Per k-tile (32 deep) the operand tiles are staged in shared memory by TMA
 // (3-stage mbarrier ring; a cooperative-load fallback covers pointers or leading dimensions
 // TMA cannot address). While staged they are reused, as the paper's fused packing reuses
 // each loaded element (Section V.B):
@@ -13,7 +13,9 @@
 //   MMA the product, by one of two FP64 engines sharing this code: DFMA (8x8 register
 //       micro-tile of fused multiply-adds per thread) or DMMA (mma.sync.m8n8k4.f64 tensor
 //       core fragments). On GB300 both issue to the same FP64 pipe, so checksum work costs
-//       exactly its operation count: (3/128) of the product here.
+//       exactly its operation count: 2 (BM + BN) FP64 operations per k (E1's two sums, E2's
+//       two fused multiply-adds) against BM BN for the product, 1/32 at 128 x 128 and 1/16
+//       at 64 x 64.
 // Epilogue: C = alpha*acc + beta*C_in in registers; reference checksums C^r_ref, C^c_ref
 // from those registers (Section V.B reuses C at register level); compare with the
 // predicted ones against the rigorous round-off threshold; exactly one flagged row and

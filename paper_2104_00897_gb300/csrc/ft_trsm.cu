@@ -9,10 +9,15 @@
 // again from the untouched R (same arithmetic: the fault-free result bit for bit); several
 // faulty columns are all corrected.
 //
-// The substitution is blocked by kBlk rows: each diagonal kBlk x kBlk block is solved with
-// one thread per column (a short dependent chain), then the rows still to come are updated
-// by all threads, each output as a kBlk-term fused multiply-add chain in ascending k. On
-// GB300's FP64 pipe the updates, which hold almost all the work, then keep every warp busy.
+// The substitution is blocked by kBlk rows. Each diagonal kBlk x kBlk block is solved by
+// kGroups threads per column: the owner of row r forms x_r = w_r / T(r,r) (as w_r times the
+// reciprocal, one rounding more than a division, inside the checksum's bound), broadcasts it
+// by warp shuffle, and each thread eliminates it from its own rows of the block. Then the
+// rows still to come are updated by all threads, each output as a kBlk-term fused
+// multiply-add chain in ascending k, four rows per thread at a time so that four
+// independent chains hide the FP64 latency. On GB300's FP64 pipe the updates, which hold
+// almost all the work, then keep every warp busy. The one-thread re-solve of a column uses
+// exactly the same arithmetic, so its result is the fault-free one bit for bit.
 #include <climits>
 
 #include "ft_device.cuh"
