@@ -1063,8 +1063,9 @@ def run_ours(args, rank, world, dist):
 
     # Online verification (Section V.A rank-K_c steps): checks every K/4 products; timed
     # clean, then one call with two accumulator flips in the same tile, in different steps.
+    # Every rank runs it: timed() synchronises the ranks around its timed region.
     online = None
-    if rank == 0 and not args.no_online:
+    if not args.no_online:
         kc = max(1, n // 4)
         fb.ftblas_set_verification_interval(kc)
         on_ms, _, on_rep, _, _ = timed(True, False, args.steps, args.warmup)

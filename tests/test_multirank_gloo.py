@@ -60,3 +60,30 @@ def test_two_gloo_ranks_shard_and_combine(tmp_path):
     assert slowest == 11.0 and status == 3
     import bench
     assert bench.job_tflops(2, 2.0e12, 3, 1000.0) == pytest.approx(12.0)  # 2 ranks x 3 steps x 2 TFLOP / 1 s
+
+
+def test_collectives_in_the_gpu_arm_are_reached_by_every_rank():
+    """Every call in bench.run_ours that synchronises the ranks (directly or through the
+    timed helpers) must sit outside any branch that depends on the rank; a rank-0-only
+    section that reached a barrier would leave the others gone and rank 0 waiting."""
+    import ast
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py")).read()
+    run_ours = next(n for n in ast.parse(src).body if isinstance(n, ast.FunctionDef) and n.name == "run_ours")
+    syncing = {"barrier", "timed", "measure_e2e", "max_over_ranks", "sum_over_ranks", "or_over_ranks"}
+    # nested helpers that synchronise must not be called under a rank test either
+    bad = []
+
+    def visit(node, under_rank):
+        if isinstance(node, ast.If):
+            names = {x.id for x in ast.walk(node.test) if isinstance(x, ast.Name)}
+            for child in node.body + node.orelse:
+                visit(child, under_rank or "rank" in names)
+            return
+        if isinstance(node, ast.Call) and isinstance(node.func, ast.Name) and node.func.id in syncing and under_rank:
+            bad.append(node.lineno)
+        for child in ast.iter_child_nodes(node):
+            visit(child, under_rank)
+
+    for stmt in run_ours.body:
+        visit(stmt, False)
+    assert not bad, f"rank-dependent synchronising calls at bench.py lines {bad}"
