@@ -7,6 +7,7 @@ header is newer than the library.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import glob
 import os
 import shutil
@@ -47,10 +48,24 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every CUDA source for sm_103a and link libftblas.so. Returns its path."""
+    """Compile every CUDA source for sm_103a and link libftblas.so. Returns its path.
+
+    Processes that build at the same time (one per rank) take turns on a lock file; each
+    checks again, once it holds the lock, whether the library is still out of date."""
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and up_to_date():
+                return LIB
+            return _build_locked(verbose)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose: bool) -> str:
     cc = nvcc()
 
     def compile_one(src: str) -> str:
