@@ -912,6 +912,12 @@ def run_ours(args, rank, world, dist):
     dev = torch.device("cuda", local)
     fb.load()
     n = args.size
+    if world > 1:
+        # At N > 1 the line carries the scaled headline (and its end-to-end figure) only: the
+        # single-GPU sections are reported by the N = 1 run, and running them on rank 0
+        # alone would hold the other GPUs idle.
+        for flag in ("no_bf16", "no_fp8", "no_linear", "no_unfused", "no_level3", "no_online", "no_second_engine"):
+            setattr(args, flag, True)
     if args.sweep:
         if rank == 0:
             print(json.dumps({"sweep_fp64": run_sweep(dev, args.steps, args.warmup)}), flush=True)
