@@ -1186,7 +1186,7 @@ def run_ours(args, rank, world, dist):
         "unfused_fp64": unfused,
         "level3_fp64": level3,
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        "gpu_launches": world * args.steps,  # one protected product kernel per step on every rank
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
