@@ -214,7 +214,9 @@ def to_e4m3_bits(x: np.ndarray) -> np.ndarray:
     q = np.where(carry, 8.0, q)
     eb = np.where(carry, eb + 1, eb)
     bits_n = (eb.astype(np.int64) << 3) | (q.astype(np.int64) - 8)
-    sub = (mag > 0) & (eb < 1)
+    # subnormal range by the exponent before rounding (a carry may lift it to the smallest
+    # normal, and qs == 8 is then the smallest normal's bit pattern)
+    sub = (mag > 0) & ~normal_
     qs = np.rint(np.ldexp(np.where(sub, mag, 0.0), 9))  # subnormal step 2**-9
     out = np.where(normal_, bits_n, 0)
     out = np.where(sub, qs.astype(np.int64), out)
