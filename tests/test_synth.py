@@ -86,3 +86,14 @@ def test_threaded_normal_equals_serial_bitwise():
     z4 = S.normal(11, 0, count, threads=4)
     assert np.array_equal(z1, z4)
     assert abs(z1.mean()) < 0.01 and abs(z1.std() - 1.0) < 0.01
+
+
+def test_randint_and_pow2_scales_cover_their_stated_ranges():
+    r = S.randint(5, 1, 200000, -4, 4)
+    assert r.min() == -4 and r.max() == 4 and set(np.unique(r)) == set(range(-4, 5))
+    counts = np.bincount(r + 4)
+    assert counts.min() > 0.9 * counts.mean()  # roughly uniform
+    p = S.pow2_row_scales(5, 2, 100000)
+    m, e = np.frexp(p)
+    assert np.all(m == 0.5)  # exact powers of two
+    assert set(np.unique(e - 1)) == set(range(-8, 9))
