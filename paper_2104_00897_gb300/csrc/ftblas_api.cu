@@ -901,23 +901,30 @@ int ftblas_dgemm_host(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_tran
   double* dB = reinterpret_cast<double*>(base + up(bytesA));
   double* dC = reinterpret_cast<double*>(base + up(bytesA) + up(bytesB));
   ft_report_t* dR = reinterpret_cast<ft_report_t*>(base + up(bytesA) + up(bytesB) + up(bytesC));
+  // Every return below waits for the stream first, failures included: copies already
+  // enqueued read or write the caller's host buffers, which are the caller's again on return.
+  auto done = [&](int rc) {
+    const cudaError_t e = cudaStreamSynchronize(st);
+    return rc != 0 ? rc : record_cuda(e);
+  };
   if (need_ab) {
-    if (int e = record_cuda(copy_runs(dA, dlda, A, lda, a_run, a_cnt, cudaMemcpyHostToDevice, st))) return e;
-    if (int e = record_cuda(copy_runs(dB, dldb, B, ldb, b_run, b_cnt, cudaMemcpyHostToDevice, st))) return e;
+    if (int e = record_cuda(copy_runs(dA, dlda, A, lda, a_run, a_cnt, cudaMemcpyHostToDevice, st))) return done(e);
+    if (int e = record_cuda(copy_runs(dB, dldb, B, ldb, b_run, b_cnt, cudaMemcpyHostToDevice, st))) return done(e);
   }
   if (beta != 0.0 && M > 0 && N > 0) {
-    if (int e = record_cuda(copy_runs(dC, dldc, C, ldc, c_run, c_cnt, cudaMemcpyHostToDevice, st))) return e;
+    if (int e = record_cuda(copy_runs(dC, dldc, C, ldc, c_run, c_cnt, cudaMemcpyHostToDevice, st))) return done(e);
   }
   int rc = dgemm_impl(layout, transa, transb, M, N, K, alpha, dA, dlda, dB, dldb, beta, dC, dldc, stream,
                       report ? dR : nullptr, true);
-  if (rc != 0) return rc;
+  if (rc != 0) return done(rc);
   if (M > 0 && N > 0) {
-    if (int e = record_cuda(copy_runs(C, ldc, dC, dldc, c_run, c_cnt, cudaMemcpyDeviceToHost, st))) return e;
+    if (int e = record_cuda(copy_runs(C, ldc, dC, dldc, c_run, c_cnt, cudaMemcpyDeviceToHost, st))) return done(e);
   }
   if (report) {
-    if (int e = record_cuda(cudaMemcpyAsync(report, dR, sizeof(ft_report_t), cudaMemcpyDeviceToHost, st))) return e;
+    if (int e = record_cuda(cudaMemcpyAsync(report, dR, sizeof(ft_report_t), cudaMemcpyDeviceToHost, st)))
+      return done(e);
   }
-  return record_cuda(cudaStreamSynchronize(st));
+  return done(0);
 }
 
 int ftblas_gemm_ex(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb, int64_t M, int64_t N, int64_t K,
