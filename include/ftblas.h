@@ -258,7 +258,9 @@ int ftblas_dgemm_host(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_tran
  * column (rows of very different scale) and beta == 0, the mismatching row is recomputed
  * and compared element by element; a located error is corrected by subtracting the row mismatch
  * (Section VI.C), evaluated as C^r(i) - sum_{j' != j} C(i,j') so that a huge or
- * non-finite error does not cancel catastrophically. Workspace (about
+ * non-finite error does not cancel catastrophically. Locating runs after the product, for
+ * at most 64 mismatching tiles per call; further mismatching tiles of the same call are
+ * reported as FT_KIND_UNCORRECTABLE (detected, C left as computed). Workspace (about
  * 16*K*ceil(N/248) + 8*K*ceil(M/128) + 4*M*ceil(K/256) bytes for BF16, 8*K*ceil(N/248) + ...
  * for FP8) is taken from the stream-ordered allocator and released on the same stream. */
 int ftblas_gemm_ex(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,
