@@ -135,12 +135,13 @@ typedef struct {
   ft_inject_point_t fixed[FTBLAS_MAX_FIXED_INJECTIONS];
 } ft_inject_t;
 
-/* Install (cfg != NULL) or remove (cfg == NULL) the process-wide injection plan and reset
- * the launch counter to 0. Every protected call with M, N > 0 that passes validation
- * counts as one launch. For launch n the seeded draw takes, per injection, six SplitMix64
- * outputs in the order tile, row offset, column offset, bit, rel_log2, sign; tiles are
- * numbered t = tile_row + tile_col * n_tile_rows in the caller's coordinates and drawn
- * without replacement. Returns 0, or -1 when cfg is malformed (ranges, counts). */
+/* Fault injection of Section VI.C's experiment. Install (cfg != NULL) or remove (cfg == NULL)
+ * the process-wide injection plan and reset the launch counter to 0. Every protected call with
+ * M, N > 0 that passes validation counts as one launch. For launch n the seeded draw takes,
+ * per injection, six SplitMix64 outputs in the order tile, row offset, column offset, bit,
+ * rel_log2, sign; tiles are numbered t = tile_row + tile_col * n_tile_rows in the caller's
+ * coordinates and drawn without replacement. Returns 0, or -1 when cfg is malformed (ranges,
+ * counts). */
 int ftblas_set_injection(const ft_inject_t* cfg);
 
 /* Protected launches counted since the last ftblas_set_injection. */
@@ -161,14 +162,15 @@ int ftblas_dgemm(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t t
                  void* stream, ft_report_t* report);
 
 /* The same kernel with the protection compiled out (no encode, verify or correction, no
- * injection): the baseline the ABFT overhead is measured against. Same arguments; no
+ * injection): the baseline the ABFT overhead is measured against, as Section VI.B compares
+ * FT-BLAS with its own implementation without FT capability. Same arguments; no
  * report. */
 int ftblas_dgemm_noabft(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,
                         int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
                         const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
                         void* stream);
 
-/* FT-DSYMM (the paper's Level-3 family beside GEMM): C = alpha A B + beta C (side LEFT, A
+/* FT-DSYMM (the Level-3 routines beside GEMM, Sections III.C and VI.B): C = alpha A B + beta C (side LEFT, A
  * M x M) or C = alpha B A + beta C (side RIGHT, A N x N), A symmetric with only its `uplo`
  * triangle read. A full copy of A is formed on `stream` (workspace from the stream-ordered
  * allocator) and the product runs through ftblas_dgemm's protected kernel: same report,
@@ -179,18 +181,18 @@ int ftblas_dsymm(ftblas_layout_t layout, ftblas_side_t side, ftblas_uplo_t uplo,
                  double alpha, const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                  double* C, int64_t ldc, void* stream, ft_report_t* report);
 
-/* FT-DTRMM: B = alpha op(A) B (side LEFT, A M x M) or B = alpha B op(A) (side RIGHT, A N x N),
- * A triangular (`uplo`, `diag`: FTBLAS_UNIT takes the diagonal as 1 without reading it), B
- * overwritten. A copy of op(A) with explicit zeros and a copy of B are formed on `stream`,
- * then ftblas_dgemm's protected kernel runs, each tile visiting only the k-tiles the
- * triangle leaves nonzero (about half the work of the full product). When the other
- * storage layout gives a better launch order of these unequal tiles (heaviest first, or
- * no longer heaviest last), the copies and the product are made in that layout and the
- * product is copied back. The values are the same. The workspace is then n^2 + 2 M N
- * doubles instead of n^2 + M N (n = M or N, A's order). Protection as for ftblas_dgemm; an
- * accumulator injection point whose k-tile (explicit, or floor(nk/2)) falls outside its
- * tile's range is not applied. Arguments 1-14 in CBLAS order (layout, side, uplo, transa,
- * diag, M, N, alpha, A, lda, B, ldb, stream, report). */
+/* FT-DTRMM (the Level-3 routines beside GEMM, Sections III.C and VI.B): B = alpha op(A) B
+ * (side LEFT, A M x M) or B = alpha B op(A) (side RIGHT, A N x N), A triangular (`uplo`,
+ * `diag`: FTBLAS_UNIT takes the diagonal as 1 without reading it), B overwritten. A copy of
+ * op(A) with explicit zeros and a copy of B are formed on `stream`, then ftblas_dgemm's
+ * protected kernel runs, each tile visiting only the k-tiles the triangle leaves nonzero
+ * (about half the work of the full product). When the other storage layout gives a better
+ * launch order of these unequal tiles (heaviest first, or no longer heaviest last), the copies
+ * and the product are made in that layout and the product is copied back. The values are the
+ * same. The workspace is then n^2 + 2 M N doubles instead of n^2 + M N (n = M or N, A's
+ * order). Protection as for ftblas_dgemm; an accumulator injection point whose k-tile
+ * (explicit, or floor(nk/2)) falls outside its tile's range is not applied. Arguments 1-14 in
+ * CBLAS order (layout, side, uplo, transa, diag, M, N, alpha, A, lda, B, ldb, stream, report). */
 int ftblas_dtrmm(ftblas_layout_t layout, ftblas_side_t side, ftblas_uplo_t uplo, ftblas_trans_t transa,
                  ftblas_diag_t diag, int64_t M, int64_t N, double alpha, const double* A, int64_t lda,
                  double* B, int64_t ldb, void* stream, ft_report_t* report);
@@ -229,10 +231,11 @@ int ftblas_dgemm_unfused(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_t
                          const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
                          void* stream, ft_report_t* report);
 
-/* ftblas_dgemm on HOST buffers: copies A, B (and C when beta != 0) to library-owned
- * device workspace on `stream`, runs the protected GEMM, copies C and the report back and
- * synchronises the stream before returning. report (host memory) may be NULL. Pinned host
- * memory gives the fastest copies. Workspace grows to the largest call and is kept. */
+/* ftblas_dgemm (Sections II.A, V) on HOST buffers: copies A, B (and C when beta != 0) to
+ * library-owned device workspace on `stream`, runs the protected GEMM, copies C and the report
+ * back and synchronises the stream before returning (on failures too, so no copy outlives
+ * the call). report (host memory) may be NULL. Pinned
+ * host memory gives the fastest copies. Workspace grows to the largest call and is kept. */
 int ftblas_dgemm_host(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,
                       int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
                       const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
@@ -270,8 +273,9 @@ int ftblas_gemm_ex(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t
                    void* C, ftblas_dtype_t Ctype, int64_t ldc, ftblas_dtype_t compute_type,
                    const float* a_scale, const float* b_scale, void* stream, ft_report_t* report);
 
-/* ftblas_gemm_ex with the protection compiled out (no encode pre-pass, no checksum MMA,
- * no verification): the baseline for the overhead. Same arguments without the report. */
+/* ftblas_gemm_ex with the protection compiled out (no encode pre-pass, no checksum MMA, no
+ * verification): the baseline for the overhead (Section VI.B's comparison). Same arguments
+ * without the report. */
 int ftblas_gemm_ex_noabft(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,
                           int64_t M, int64_t N, int64_t K, const void* alpha,
                           const void* A, ftblas_dtype_t Atype, int64_t lda,
@@ -306,30 +310,31 @@ int ftblas_gemm_ex_noalloc(ftblas_layout_t layout, ftblas_trans_t transa, ftblas
                            void* C, ftblas_dtype_t Ctype, int64_t ldc, ftblas_dtype_t compute_type,
                            const float* a_scale, const float* b_scale, void* stream, ft_report_t* report);
 
-/* Shape of the verification tile used for a call, in the caller's coordinates of C, and
- * the k-tile depth that sets the accumulator injection point (bk * floor(ceil(K/bk)/2)
- * products; for the tensor-core forms the k-tile of their staging, 128 bytes). compute_type
- * selects the kernel family: FTBLAS_R_64F (ftblas_dgemm and the Level-3 routines built on
- * it), FTBLAS_R_32F or FTBLAS_R_16BF (BF16 tensor-core path: 128 x 248 tiles, k-tile 64) or
- * FTBLAS_R_8F_E4M3 (FP8 tensor-core path: 128 x 248 tiles, k-tile 128).
- * FP64 tiles are square, 128 x 128, or 64 x 64 with the DFMA engine when 128-edge tiles
- * would leave many of the current device's SMs idle: the choice depends on M, N, the
- * engine (ftblas_set_fp64_engine) and the SM count (152 when no device answers). The
- * unfused comparator ftblas_dgemm_unfused always verifies 128 x 128 tiles.
- * Returns 0, or a negative argument index. */
+/* The verification interval of Section II.A (one error correctable in each): the shape of the
+ * verification tile used for a call, in the caller's coordinates of C, and the k-tile depth
+ * that sets the accumulator injection point (bk * floor(ceil(K/bk)/2) products; for the
+ * tensor-core forms the k-tile of their staging, 128 bytes). compute_type selects the kernel
+ * family: FTBLAS_R_64F (ftblas_dgemm and the Level-3 routines built on it), FTBLAS_R_32F or
+ * FTBLAS_R_16BF (BF16 tensor-core path: 128 x 248 tiles, k-tile 64) or FTBLAS_R_8F_E4M3 (FP8
+ * tensor-core path: 128 x 248 tiles, k-tile 128). FP64 tiles are square, 128 x 128, or 64 x 64
+ * with the DFMA engine when 128-edge tiles would leave many of the current device's SMs idle:
+ * the choice depends on M, N, the engine (ftblas_set_fp64_engine) and the SM count (152 when
+ * no device answers). The unfused comparator ftblas_dgemm_unfused always verifies 128 x 128
+ * tiles. Returns 0, or a negative argument index. */
 int ftblas_verification_tile(ftblas_layout_t layout, ftblas_dtype_t compute_type,
                              int64_t M, int64_t N, int64_t K,
                              int64_t* tile_rows, int64_t* tile_cols, int64_t* k_tile);
 
-/* FP64 product engine: 0 = DFMA (SIMT fused multiply-add, default; 128 or 64 tile edge),
- * 1 = DMMA (FP64 tensor-core mma.sync m8n8k4; 128 tile edge). Both run the same staging,
- * encode and epilogue. Returns the previous engine, or -1 for an unknown value.
- * Process-wide. */
+/* Library control, no counterpart in the paper. FP64 product engine: 0 = DFMA (SIMT fused
+ * multiply-add, default; 128 or 64 tile edge), 1 = DMMA (FP64 tensor-core mma.sync m8n8k4; 128
+ * tile edge). Both run the same staging, encode and epilogue. Returns the previous engine, or
+ * -1 for an unknown value. Process-wide. */
 int ftblas_set_fp64_engine(int engine);
 
-/* FP64 tile edge of the DFMA engine: 0 = automatic (the default; the rule described at
- * ftblas_verification_tile), 128 or 64 = that edge for every later call. The DMMA engine
- * always uses 128. Returns the previous setting, or -1 for another value. Process-wide. */
+/* Library control, no counterpart in the paper. FP64 tile edge of the DFMA engine: 0 =
+ * automatic (the default; the rule described at ftblas_verification_tile), 128 or 64 = that
+ * edge for every later call. The DMMA engine always uses 128. Returns the previous setting, or
+ * -1 for another value. Process-wide. */
 int ftblas_set_fp64_tile(int edge);
 
 /* Online verification (Section V.A): the FP64 protected kernels also check each tile
@@ -342,36 +347,39 @@ int ftblas_set_fp64_tile(int edge);
  * finished tile. Process-wide; returns the previous value, or -1 for a negative argument. */
 int64_t ftblas_set_verification_interval(int64_t k_interval);
 
-/* Staging path of the calling thread's most recent GEMM launch: 1 = operands staged by
- * TMA (16-byte aligned base addresses and leading dimensions), 0 = cooperative loads (any
- * other alignment), -1 = no kernel launched yet on this thread. For tests and tuning. */
+/* Diagnostics (no counterpart in the paper). Staging path of the calling thread's most recent
+ * GEMM launch: 1 = operands staged by TMA (16-byte aligned base addresses and leading
+ * dimensions), 0 = cooperative loads (any other alignment), -1 = no kernel launched yet on
+ * this thread. For tests and tuning. */
 int ftblas_last_launch_used_tma(void);
 
-/* Human-readable text of a return code. */
+/* Diagnostics (no counterpart in the paper): human-readable text of a return code. */
 const char* ftblas_status_string(int code);
 
-/* cudaError_t of the last failing CUDA call made by the library on this thread (0: none). */
+/* Diagnostics (no counterpart in the paper): cudaError_t of the last failing CUDA call made by
+ * the library on this thread (0: none). */
 int ftblas_last_cuda_error(void);
 
-/* Library version, e.g. "0.1.0". */
+/* Diagnostics (no counterpart in the paper): library version, e.g. "0.1.0". */
 const char* ftblas_version(void);
 
-/* Decode n FP8 E4M3 codes (device memory, one byte each, 8-byte aligned) to binary32
- * (device memory, n floats) with the unpacking that the tensor-core path's encode kernel
- * uses (eight codes per load, two per conversion instruction). A diagnostic, so that tests
- * can compare it code by code with the format's definition (bias 7, subnormals at exponent
- * field 0, S.1111.111 = NaN). Asynchronous on `stream`. Returns 0, -p for an invalid
- * argument p (null or misaligned pointer with n > 0, n < 0), or FTBLAS_STATUS_CUDA_ERROR. */
+/* Test support (no counterpart in the paper). Decode n FP8 E4M3 codes (device memory, one byte
+ * each, 8-byte aligned) to binary32 (device memory, n floats) with the unpacking that the
+ * tensor-core path's encode kernel uses (eight codes per load, two per conversion
+ * instruction). A diagnostic, so that tests can compare it code by code with the format's
+ * definition (bias 7, subnormals at exponent field 0, S.1111.111 = NaN). Asynchronous on
+ * `stream`. Returns 0, -p for an invalid argument p (null or misaligned pointer with n > 0, n
+ * < 0), or FTBLAS_STATUS_CUDA_ERROR. */
 int ftblas_decode_e4m3(const void* codes, float* out, int64_t n, void* stream);
 
-/* Device time of the product kernels, for measurement. After ftblas_kernel_timing_begin,
- * every GEMM call (any entry point, protected or not) records a pair of CUDA events on its
- * stream around its product kernel only: the encode, resolve and scaling kernels and the
- * report clear fall outside the pair. ftblas_kernel_timing_end stops recording, waits for
- * the recorded events, frees them, and returns in *total_ms the summed durations and in
- * *launches the number of timed launches (either pointer may be NULL). Returns 0, or
- * FTBLAS_STATUS_CUDA_ERROR if an event could not be created, recorded or read (those
- * launches are left out). Process-wide; begin discards pairs not yet collected. */
+/* Measurement support, no counterpart in the paper. Device time of the product kernels. After
+ * ftblas_kernel_timing_begin, every GEMM call (any entry point, protected or not) records a
+ * pair of CUDA events on its stream around its product kernel only: the encode, resolve and
+ * scaling kernels and the report clear fall outside the pair. ftblas_kernel_timing_end stops
+ * recording, waits for the recorded events, frees them, and returns in *total_ms the summed
+ * durations and in *launches the number of timed launches (either pointer may be NULL).
+ * Returns 0, or FTBLAS_STATUS_CUDA_ERROR if an event could not be created, recorded or read
+ * (those launches are left out). Process-wide; begin discards pairs not yet collected. */
 int ftblas_kernel_timing_begin(void);
 int ftblas_kernel_timing_end(double* total_ms, int64_t* launches);
 

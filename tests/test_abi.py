@@ -95,3 +95,15 @@ def test_verification_tile_and_engine_switch():
     prev = fb.ftblas_set_fp64_engine(fb.ENGINE_DMMA)
     assert fb.ftblas_set_fp64_engine(prev) == fb.ENGINE_DMMA
     assert fb.ftblas_set_fp64_engine(7) == -1
+
+
+def test_every_declaration_cites_its_passage():
+    """Each entry point's comment in the header names the passage of the paper that defines
+    its operation, or says that the paper has no counterpart (controls, diagnostics)."""
+    src = open(os.path.join(ROOT, "include", "ftblas.h")).read()
+    decls = list(re.finditer(r"(/\*(?:(?!\*/).)*?\*/)\s*\n(?:int|const char\s*\*|void|int64_t)\s+(ftblas_\w+)\s*\(",
+                             src, flags=re.S))
+    assert len(decls) >= 20
+    missing = [m.group(2) for m in decls
+               if not re.search(r"Section|no counterpart", " ".join(re.sub(r"\n\s*\*", " ", m.group(1)).split()))]
+    assert not missing, missing
