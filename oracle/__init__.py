@@ -1,7 +1,9 @@
 """CPU oracle for the ABFT-protected GEMM (FT-BLAS, Zhai et al., ICS '21, Sections II.A and V).
 
 TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU-baseline
-leg may import this package; the library itself never does. The C source next to this
+leg and reference arm may import this package; the library itself never does. Parity
+unpinned: the ACC32 model's values against the hardware beyond the stated bound, and one
+threshold term (both named in the C source's header). The C source next to this
 file (``ftgemm_oracle.c``) is plain binary64 code compiled with ``-ffp-contract=off``; it
 shares no code with the CUDA path. Buffers are flat numpy float64 arrays in BLAS storage
 with explicit leading dimensions, exactly as the C ABI takes them.
