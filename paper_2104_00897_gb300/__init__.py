@@ -305,6 +305,20 @@ def _layout_of(t):
     return None, None
 
 
+def _require_cuda(name, t, dtype=None, device=None, numel=None):
+    """Raise unless t is a CUDA tensor (of the given dtype, on the given device, with the
+    given number of elements): the C ABI takes raw device pointers, so a host tensor or a
+    wrong element type must be refused before any launch."""
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{name} must be a CUDA tensor (got {getattr(t, 'device', type(t))})")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, the operands on {device}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} element(s), has {t.numel()}")
+
+
 def dgemm(a, b, c=None, alpha=1.0, beta=0.0, trans_a=False, trans_b=False, report=None, protect=True,
           stream=None):
     """c = alpha * op(a) @ op(b) + beta * c on float64 CUDA tensors, protected by ABFT.
@@ -314,6 +328,12 @@ def dgemm(a, b, c=None, alpha=1.0, beta=0.0, trans_a=False, trans_b=False, repor
     copies when they differ. ``report``: a buffer from new_report() (or None). Returns c.
     """
     import torch
+    _require_cuda("a", a, torch.float64)
+    _require_cuda("b", b, torch.float64, a.device)
+    if c is not None:
+        _require_cuda("c", c, torch.float64, a.device)
+    if report is not None:
+        _require_cuda("report", report, device=a.device)
     Ma, Ka = (a.shape[1], a.shape[0]) if trans_a else (a.shape[0], a.shape[1])
     Kb, Nb = (b.shape[1], b.shape[0]) if trans_b else (b.shape[0], b.shape[1])
     if Ka != Kb:
@@ -384,6 +404,15 @@ def gemm(a, b, c=None, alpha=1.0, beta=0.0, trans_a=False, trans_b=False, report
     fp8 = a.dtype == getattr(torch, "float8_e4m3fn", None)
     if a.dtype != b.dtype or not (a.dtype == torch.bfloat16 or fp8):
         raise TypeError(f"unsupported operand dtypes {a.dtype}, {b.dtype}")
+    _require_cuda("a", a)
+    _require_cuda("b", b, device=a.device)
+    if c is not None:
+        _require_cuda("c", c, device=a.device)
+    if report is not None:
+        _require_cuda("report", report, device=a.device)
+    for name, sc in (("a_scale", a_scale), ("b_scale", b_scale)):
+        if sc is not None:
+            _require_cuda(name, sc, torch.float32, a.device, numel=1)
     opa = a.t() if trans_a else a          # M x K
     opb_t = b if trans_b else b.t()        # N x K
     M, K = opa.shape

@@ -53,3 +53,18 @@ def test_missing_library_raises(monkeypatch, tmp_path):
     monkeypatch.setattr(fb._build, "LIB", str(tmp_path / "libftblas.so"))
     with pytest.raises(RuntimeError, match="not found"):
         fb.load(build_if_needed=False)
+
+
+def test_torch_helpers_refuse_host_tensors_before_any_launch():
+    """The C ABI takes raw device pointers: the torch helpers refuse host tensors up front
+    (here, with no GPU, before any CUDA call is made)."""
+    torch = pytest.importorskip("torch")
+    import paper_2104_00897_gb300 as fb
+    a = torch.zeros((4, 3), dtype=torch.float64)
+    b = torch.zeros((3, 5), dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        fb.gemm(a, b)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        fb.dgemm(a, b)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        fb.gemm(a.to(torch.bfloat16), b.to(torch.bfloat16))
