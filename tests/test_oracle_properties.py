@@ -15,6 +15,7 @@ code:
   both equal the error exactly, and the recomputed C equals the fault-free C bit for bit.
 """
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -204,3 +205,30 @@ def test_acc32_one_output_error_anywhere_is_located_and_removed_exactly(case, wh
     assert (r.i, r.j) == (i, j)
     assert r.delta_row == sign * 2.0 ** p * abs(clean[i, j])
     assert np.array_equal(got, clean)
+
+
+# ------------------------------------------------------------------------------------
+# The triangular solve behind FT-DTRSM's reference
+# ------------------------------------------------------------------------------------
+
+@SETTINGS
+@given(st.integers(1, 24), st.integers(1, 10), st.booleans(), st.integers(0, 10 ** 6))
+def test_substitution_meets_its_componentwise_backward_error_bound(n, nrhs, lower, seed):
+    """Substitution is componentwise backward stable: the computed X satisfies
+    |T X - W| <= gamma_n |T| |X| (a textbook bound for forward and back substitution with
+    any summation order). The unread triangle holds NaN, so reading it would show."""
+    R = S.uniform_matrix(seed, 0, n, n)
+    d = 0.5 + S.uniform(seed, 1, n) ** 2                      # diagonal away from zero
+    T = np.tril(R, -1) if lower else np.triu(R, 1)
+    T = T + np.diag(d * np.where(S.uniform(seed, 2, n) < 0, -1.0, 1.0))
+    W = S.uniform_matrix(seed, 3, n, nrhs)
+    Tn = np.where(np.tril(np.ones((n, n))) if lower else np.triu(np.ones((n, n))), T, np.nan)
+    X = O.trsm_left(Tn, W, lower)
+    # the residual formed exactly (rational arithmetic), so that only the solve's rounding shows
+    Tf = [[Fraction(float(v)) for v in row] for row in T]
+    bound = gamma(n) * (np.abs(T) @ np.abs(X)) * (1 + 1e-9)
+    for j in range(nrhs):
+        xj = [Fraction(float(v)) for v in X[:, j]]
+        for i in range(n):
+            res = sum((Tf[i][k] * xj[k] for k in range(n)), Fraction(0)) - Fraction(float(W[i, j]))
+            assert abs(res) <= Fraction(float(bound[i, j])), (i, j, float(res), bound[i, j])
