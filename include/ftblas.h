@@ -120,7 +120,11 @@ typedef struct {
   int64_t i, j;               /* element of C, caller's coordinates */
   int32_t site, mode, bit, rel_log2, sign;
   int32_t k_tile;             /* FP64 accumulator site: flip after k_tile k-tiles of products
-                                 (0: after floor(nk/2)); the tensor-core paths flip after all K */
+                                 (0: after floor(nk/2)); the tensor-core paths flip after all K.
+                                 The injection model holds one FP64 accumulator point per element
+                                 and launch: the oracle applies only the first point at an element,
+                                 so a plan with two there has no reference (the seeded draw never
+                                 makes one: its points fall in distinct tiles) */
 } ft_inject_point_t;
 
 typedef struct {

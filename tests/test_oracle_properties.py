@@ -232,3 +232,53 @@ def test_substitution_meets_its_componentwise_backward_error_bound(n, nrhs, lowe
         for i in range(n):
             res = sum((Tf[i][k] * xj[k] for k in range(n)), Fraction(0)) - Fraction(float(W[i, j]))
             assert abs(res) <= Fraction(float(bound[i, j])), (i, j, float(res), bound[i, j])
+
+
+# ------------------------------------------------------------------------------------
+# Online (mid-K) verification: one correctable error per interval
+# ------------------------------------------------------------------------------------
+
+@SETTINGS
+@given(st.data())
+def test_online_checks_correct_one_flip_per_interval(data):
+    """Integer operands (exact partial checksums); checks every kc products. Two accumulator
+    flips of an exponent bit in one tile, strictly inside two different intervals, are each
+    corrected at the check that follows them (Section V.A's rank-K_c steps), and C equals
+    the fault-free C bit for bit. Without online checks the pair is uncorrectable."""
+    bk = data.draw(st.integers(1, 3))
+    kc = bk * data.draw(st.integers(2, 3))
+    K = kc * data.draw(st.integers(3, 4))
+    M, N = data.draw(st.integers(1, 10)), data.draw(st.integers(2, 10))
+    tm, tn = data.draw(st.integers(1, 6)), data.draw(st.integers(2, 6))
+    seed = data.draw(st.integers(0, 10 ** 6))
+    A = S.randint(seed, 0, M * K, 1, 4).reshape(M, K).astype(np.float64)   # positive: partial sums > 0
+    B = S.randint(seed, 1, K * N, 1, 4).reshape(K, N).astype(np.float64)
+    inside = [kt for kt in range(1, K // bk) if (kt * bk) % kc != 0]
+    last = (K // bk - 1) * bk // kc
+    kt1 = data.draw(st.sampled_from([kt for kt in inside if (kt * bk) // kc < last]))
+    kt2 = data.draw(st.sampled_from([kt for kt in inside if (kt * bk) // kc > (kt1 * bk) // kc]))
+    hi, hj = min(tm, M), min(tn, N)  # both flips in tile (0, 0), which has at least 2 elements
+    e1 = data.draw(st.integers(0, hi * hj - 1))
+    e2 = data.draw(st.integers(0, hi * hj - 2))
+    e2 += e2 >= e1  # a different element: the injection model holds one accumulator point per element
+    (i1, j1), (i2, j2) = divmod(e1, hj), divmod(e2, hj)
+    bit = data.draw(st.integers(55, 60))
+    a, lda = stored(O.COL_MAJOR, O.NO_TRANS, A)
+    b, ldb = stored(O.COL_MAJOR, O.NO_TRANS, B)
+    c, ldc = c_store(O.COL_MAJOR, np.zeros((M, N)), 0)
+
+    def call(kc_, inj):
+        out, rep = O.ft_gemm(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, M, N, K, 1.0, a, lda, b, ldb, 0.0, c, ldc,
+                             tm, tn, bk, injections=inj, kc=kc_)
+        return S.load(out, O.COL_MAJOR, M, N, ldc), rep
+
+    clean, rep0 = call(kc, ())
+    assert rep0.detected == 0 and np.array_equal(clean, A @ B)  # small integers: exact
+    pts = [dict(i=i1, j=j1, site=O.SITE_ACCUM, mode=O.MODE_BITFLIP, bit=bit, kt=kt1),
+           dict(i=i2, j=j2, site=O.SITE_ACCUM, mode=O.MODE_BITFLIP, bit=bit, kt=kt2)]
+    got, rep = call(kc, pts)
+    assert rep.corrected == 2 and rep.uncorrectable == 0
+    assert sorted((r.i, r.j) for r in rep.records()) == sorted([(i1, j1), (i2, j2)])
+    assert np.array_equal(got, clean)
+    _, rep_end = call(0, pts)
+    assert rep_end.corrected == 0 and rep_end.uncorrectable == 1
