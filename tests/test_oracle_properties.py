@@ -282,3 +282,42 @@ def test_online_checks_correct_one_flip_per_interval(data):
     assert np.array_equal(got, clean)
     _, rep_end = call(0, pts)
     assert rep_end.corrected == 0 and rep_end.uncorrectable == 1
+
+
+# ------------------------------------------------------------------------------------
+# Classification of several errors (G4)
+# ------------------------------------------------------------------------------------
+
+@SETTINGS
+@given(st.data())
+def test_two_errors_in_one_tile_are_uncorrectable_and_in_two_tiles_corrected(data):
+    """Integer operands, so each flagged row and column carries the exact error. Two errors
+    at different elements of one tile flag two rows and/or two columns: uncorrectable, with
+    C left as computed (both errors stay). Two errors in different tiles: both corrected."""
+    M, N, K = data.draw(st.integers(2, 12)), data.draw(st.integers(2, 12)), data.draw(st.integers(1, 12))
+    tm, tn = data.draw(st.integers(1, 6)), data.draw(st.integers(1, 6))
+    seed = data.draw(st.integers(0, 10 ** 6))
+    A = S.randint(seed, 0, M * K, 1, 4).reshape(M, K).astype(np.float64)  # positive: C >= 1
+    B = S.randint(seed, 1, K * N, 1, 4).reshape(K, N).astype(np.float64)
+    case = dict(layout=O.COL_MAJOR, ta=O.NO_TRANS, tb=O.NO_TRANS, alpha=1.0, beta=0.0, tm=tm, tn=tn,
+                bk=data.draw(st.integers(1, 4)), pad=0)
+    Cin = np.zeros((M, N))
+    clean = run(case, A, B, Cin, protected=False)
+    err = lambda i, j: dict(i=i, j=j, site=O.SITE_OUTPUT, mode=O.MODE_ADD_REL, rel_log2=3, sign=1)
+    tiles = [(r, c) for r in range(-(-M // tm)) for c in range(-(-N // tn))]
+    tr, tc = data.draw(st.sampled_from(tiles))
+    cells = [(i, j) for i in range(tr * tm, min(M, tr * tm + tm)) for j in range(tc * tn, min(N, tc * tn + tn))]
+    if len(cells) >= 2:
+        (i1, j1), (i2, j2) = data.draw(st.lists(st.sampled_from(cells), min_size=2, max_size=2, unique=True))
+        got, rep = run(case, A, B, Cin, protected=True, inj=[err(i1, j1), err(i2, j2)])
+        assert (rep.detected, rep.uncorrectable, rep.corrected) == (1, 1, 0)
+        (r,) = rep.records()
+        assert (r.rows_flagged, r.cols_flagged) == (len({i1, i2}), len({j1, j2}))
+        assert got[i1, j1] == 9 * clean[i1, j1] and got[i2, j2] == 9 * clean[i2, j2]
+    if len(tiles) >= 2:
+        (ta_, tb_) = data.draw(st.lists(st.sampled_from(tiles), min_size=2, max_size=2, unique=True))
+        pick = lambda t: (t[0] * tm, t[1] * tn)
+        (i1, j1), (i2, j2) = pick(ta_), pick(tb_)
+        got, rep = run(case, A, B, Cin, protected=True, inj=[err(i1, j1), err(i2, j2)])
+        assert (rep.detected, rep.corrected, rep.uncorrectable) == (2, 2, 0)
+        assert np.array_equal(got, clean)
