@@ -321,3 +321,24 @@ def test_two_errors_in_one_tile_are_uncorrectable_and_in_two_tiles_corrected(dat
         got, rep = run(case, A, B, Cin, protected=True, inj=[err(i1, j1), err(i2, j2)])
         assert (rep.detected, rep.corrected, rep.uncorrectable) == (2, 2, 0)
         assert np.array_equal(got, clean)
+
+
+@SETTINGS
+@given(st.data())
+def test_a_fault_in_a_predicted_checksum_alone_is_checksum_only(data):
+    """A fault in the predicted checksum and nowhere in C flags one side only: reported as
+    checksum-only, and C is left exactly as the fault-free product (G4)."""
+    M, N, K = data.draw(st.integers(1, 12)), data.draw(st.integers(1, 12)), data.draw(st.integers(1, 12))
+    layout = data.draw(st.sampled_from([O.COL_MAJOR, O.ROW_MAJOR]))
+    case = dict(layout=layout, ta=O.NO_TRANS, tb=O.NO_TRANS, alpha=1.0, beta=0.0,
+                tm=data.draw(st.integers(1, 6)), tn=data.draw(st.integers(1, 6)), bk=data.draw(st.integers(1, 4)), pad=0)
+    seed = data.draw(st.integers(0, 10 ** 6))
+    A = S.randint(seed, 0, M * K, 1, 4).reshape(M, K).astype(np.float64)
+    B = S.randint(seed, 1, K * N, 1, 4).reshape(K, N).astype(np.float64)
+    Cin = np.zeros((M, N))
+    clean = run(case, A, B, Cin, protected=False)
+    i, j = data.draw(st.integers(0, M - 1)), data.draw(st.integers(0, N - 1))
+    got, rep = run(case, A, B, Cin, protected=True,
+                   inj=[dict(i=i, j=j, site=O.SITE_CHECKSUM, mode=O.MODE_ADD_REL, rel_log2=2, sign=1)])
+    assert (rep.detected, rep.checksum_only, rep.corrected, rep.uncorrectable) == (1, 1, 0, 0)
+    assert np.array_equal(got, clean)
