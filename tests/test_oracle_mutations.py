@@ -1,7 +1,8 @@
 """The oracle's pins must catch plausible mistakes.
 
 Each case plants one mistake in a copy of the oracle's C source (never in the real one),
-builds it, and runs the pin tests against that build; they must fail.
+builds it, and runs the pin tests and the randomised properties against that build; they
+must fail.
 """
 import os
 import subprocess
@@ -30,6 +31,8 @@ MUTATIONS = {
     "acc32_accumulator_flip_in_binary64": ("acc = flip_bit32(acc, inj[q].bit);", "acc = flip_bit(acc, inj[q].bit);"),
     "acc32_row_recompute_with_beta": ("const int recompute_row = (nr == 1 && nc == 0 && p->beta == 0.0);",
                                       "const int recompute_row = (nr == 1 && nc == 0);"),
+    "acc32_row_recompute_never_used": ("const int recompute_row = (nr == 1 && nc == 0 && p->beta == 0.0);",
+                                       "const int recompute_row = 0;"),
     # triangular solve
     "trsm_lower_sums_the_diagonal": ("for (int64_t c = 0; c < r; ++c) s = s + T[r + c * ldt] * w[c];",
                                      "for (int64_t c = 0; c <= r; ++c) s = s + T[r + c * ldt] * w[c];"),
@@ -49,7 +52,12 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
                     "-o", str(lib), str(mutated), "-lm"], check=True, capture_output=True)
     env = dict(os.environ, ORACLE_LIB=str(lib))
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+    tests = [os.path.join(ROOT, "tests", "test_oracle_pins.py")]
+    try:
+        import hypothesis  # noqa: F401  (the randomised properties need it)
+        tests.append(os.path.join(ROOT, "tests", "test_oracle_properties.py"))
+    except ImportError:
+        pass
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *tests],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch mutation {name}:\n{r.stdout[-2000:]}"

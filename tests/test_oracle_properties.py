@@ -342,3 +342,37 @@ def test_a_fault_in_a_predicted_checksum_alone_is_checksum_only(data):
                    inj=[dict(i=i, j=j, site=O.SITE_CHECKSUM, mode=O.MODE_ADD_REL, rel_log2=2, sign=1)])
     assert (rep.detected, rep.checksum_only, rep.corrected, rep.uncorrectable) == (1, 1, 0, 0)
     assert np.array_equal(got, clean)
+
+
+@SETTINGS
+@given(st.data())
+def test_acc32_error_in_the_smallest_row_is_located_and_removed_exactly(data):
+    """Rows of A scaled by 2^u, u in [-8, 8] (config 3's structure), with small integer
+    entries: every value is dyadic and exact in binary32. An output error 2^-4 |C(i,j)| in
+    the row of smallest scale is far above that row's threshold (positive entries make
+    C(i,j) at least the row's sum of |A|) but usually below the column thresholds, which the
+    large rows of the tile dominate; the row-recompute locator (beta = 0) then finds it.
+    Either way it is located, and the correction from the row checksum restores C exactly."""
+    M, N, K = data.draw(st.integers(8, 16)), data.draw(st.integers(1, 16)), data.draw(st.integers(32, 64))
+    seed = data.draw(st.integers(0, 10 ** 6))
+    A = S.randint(seed, 0, M * K, 1, 3).reshape(M, K).astype(np.float64) * S.pow2_row_scales(seed, 5, M)[:, None]
+    B = S.randint(seed, 1, K * N, 1, 3).reshape(K, N).astype(np.float64)
+    case = dict(layout=O.COL_MAJOR, ta=O.TRANS, tb=O.NO_TRANS, alpha=1.0, beta=0.0,
+                tm=16, tn=data.draw(st.integers(1, 16)), bk=64, pad=0)
+    a, lda = stored(case["layout"], case["ta"], A)
+    b, ldb = stored(case["layout"], case["tb"], B)
+    c, ldc = c_store(case["layout"], np.zeros((M, N)), 0)
+
+    def call(inj):
+        out, rep = O.ft_gemm(case["layout"], case["ta"], case["tb"], M, N, K, 1.0, a, lda, b, ldb, 0.0, c, ldc,
+                             case["tm"], case["tn"], case["bk"], injections=inj, precision=O.PREC_ACC32)
+        return S.load(out, case["layout"], M, N, ldc), rep
+
+    clean, rep0 = call(())
+    assert rep0.detected == 0 and np.array_equal(clean, A @ B)
+    i = int(np.argmin(np.abs(A).sum(axis=1)))
+    j = data.draw(st.integers(0, N - 1))
+    got, rep = call([dict(i=i, j=j, site=O.SITE_OUTPUT, mode=O.MODE_ADD_REL, rel_log2=-4, sign=1)])
+    assert (rep.detected, rep.corrected) == (1, 1)
+    assert (rep.records()[0].i, rep.records()[0].j) == (i, j)
+    assert np.array_equal(got, clean)
