@@ -107,3 +107,50 @@ def test_every_declaration_cites_its_passage():
     missing = [m.group(2) for m in decls
                if not re.search(r"Section|no counterpart", " ".join(re.sub(r"\n\s*\*", " ", m.group(1)).split()))]
     assert not missing, missing
+
+
+C_CONSUMER = r"""
+#include <stdio.h>
+#include <string.h>
+#include "ftblas.h"
+
+int main(void) {
+  int64_t tr = 0, tc = 0, bk = 0;
+  /* argument validation returns -p (xerbla style) before any device work */
+  int bad = ftblas_dgemm(FTBLAS_COL_MAJOR, FTBLAS_NO_TRANS, FTBLAS_NO_TRANS, -1, 4, 4, 1.0, 0, 1, 0, 4, 0.0, 0, 1,
+                         0, 0);
+  int rc = ftblas_verification_tile(FTBLAS_COL_MAJOR, FTBLAS_R_16BF, 256, 256, 256, &tr, &tc, &bk);
+  printf("%s|%d|%d|%lld|%lld|%lld|%s\n", ftblas_version(), bad, rc, (long long)tr, (long long)tc, (long long)bk,
+         ftblas_status_string(FTBLAS_STATUS_NOT_SUPPORTED));
+  return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_a_c_program_links_and_calls_the_library(tmp_path):
+    """The boundary is a C ABI: the header compiles as C99 on its own, and a plain C program
+    links against libftblas.so and calls entry points that need no GPU."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    inc = os.path.join(ROOT, "include")
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-fsyntax-only", "-x", "c",
+                        os.path.join(inc, "ftblas.h")], capture_output=True, text=True)
+    assert r.returncode == 0 and not r.stderr.strip(), r.stderr
+    fb.load()
+    lib = fb.library_path()
+    src = tmp_path / "consumer.c"
+    src.write_text(C_CONSUMER)
+    exe = tmp_path / "consumer"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-I", inc, str(src), "-o", str(exe), lib,
+                        "-Wl,-rpath," + os.path.dirname(lib)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stderr
+    version, bad, rc, tr, tc, bk, msg = r.stdout.strip().split("|")
+    expected = fb.ftblas_version()
+    assert version == (expected.decode() if isinstance(expected, bytes) else expected)
+    assert int(bad) == -4  # M is argument 4
+    assert int(rc) == 0 and (int(tr), int(tc), int(bk)) == (128, 248, 64)
+    assert msg
