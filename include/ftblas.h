@@ -293,20 +293,24 @@ int ftblas_gemm_ex_noabft(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_
  * while work is being issued. Examples are a runtime whose memory is fully reserved up
  * front by another framework's caching allocator, a real-time or certification setting
  * that forbids allocation after initialisation, and a caller holding a lock under which
- * allocation could block. The protected BF16 GEMM (the same argument list and the same
- * supported combination as ftblas_gemm_ex: A, B FTBLAS_R_16BF, C and compute
- * FTBLAS_R_32F) takes its encode scratch from one static device array of 16 MiB that
- * every GPU loading this library holds until the process exits; nothing else is
- * allocated (no cudaMalloc, cudaFree, stream-ordered or library allocation).
+ * allocation could block. The protected BF16 GEMM (the argument list of ftblas_gemm_ex,
+ * and only its BF16 combination: A, B FTBLAS_R_16BF, C and compute FTBLAS_R_32F; FP64 and
+ * FP8 E4M3 return FTBLAS_STATUS_NOT_SUPPORTED) takes its encode scratch from one static
+ * device array of 16 MiB that every GPU loading this library holds until the process
+ * exits; nothing else is allocated (no cudaMalloc, cudaFree, stream-ordered or library
+ * allocation).
  *   - Size limit: problems whose scratch, about 16*K*ceil(N/248) + 8*K*ceil(M/128) +
  *     4*M*ceil(K/256) bytes, exceeds 16 MiB are rejected with
  *     FTBLAS_STATUS_WORKSPACE_LIMIT before any device work (M = N = K = 8192 fits).
- *   - First call per device: it looks up the device address of the static array with
- *     the device current; make that first call before any stream capture.
+ *   - First call per device: the first call that launches the protected product looks
+ *     up the device address of the static array, with the device current (argument,
+ *     type and size checks and the quick returns come before and need no lookup); make
+ *     that first call before any stream capture. A failed lookup returns
+ *     FTBLAS_STATUS_CUDA_ERROR, its code readable with ftblas_last_cuda_error.
  *   - Sharing: every call on a device uses the same array and its encode pass writes
  *     every scratch entry its GEMM reads. Calls whose device work overlaps (different streams, or other
  *     threads) race on it and must be serialised by the caller.
- * Other combinations return FTBLAS_STATUS_NOT_SUPPORTED. */
+ * Argument errors return -p as ftblas_gemm_ex does. */
 int ftblas_gemm_ex_noalloc(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,
                            int64_t M, int64_t N, int64_t K, const void* alpha,
                            const void* A, ftblas_dtype_t Atype, int64_t lda,

@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU-baseline
 leg and reference arm may import this package; the library itself never does. Parity
-unpinned: the ACC32 model's values against the hardware beyond the stated bound, and one
-threshold term (both named in the C source's header). The C source next to this
+unpinned: the ACC32 model's values against the hardware beyond the stated bound (named
+in the C source's header). The C source next to this
 file (``ftgemm_oracle.c``) is plain binary64 code compiled with ``-ffp-contract=off``; it
 shares no code with the CUDA path. Buffers are flat numpy float64 arrays in BLAS storage
 with explicit leading dimensions, exactly as the C ABI takes them.

@@ -32,14 +32,12 @@
  *     bk * floor(nk / 2) products, nk = ceil(K / bk); output injection perturbs C(i, j)
  *     after alpha/beta and before verification.
  *
- * Parity unpinned, in two places, both in the binary32-accumulation model (ACC32) of the
- * tensor-core forms:
- *   - the values of those forms against binary64 are checked only within the stated
- *     accumulation bound; its unit roundoff u_acc is a property of the hardware, not a
- *     figure of the paper;
- *   - the row threshold's term s gamma_K(u_acc), which bounds the rounding of the tensor
- *     core's binary32 product of A with the pieces of B e, is exercised by no error this
- *     oracle can show, since it forms that prediction in binary64.
+ * Parity unpinned, in one place, the binary32-accumulation model (ACC32) of the
+ * tensor-core forms: the values of those forms against binary64 are checked only within
+ * the stated accumulation bound; its unit roundoff u_acc is a property of the hardware,
+ * not a figure of the paper. (The row threshold's term s gamma_K(u_acc), which this oracle's
+ * own binary64 prediction never exercises, is pinned by a test that builds the extreme
+ * binary32 accumulations the threshold must cover.)
  *
  * Arithmetic: binary64, products and sums as separate operations in ascending k. Build
  * with -ffp-contract=off so no multiply-add is contracted. OpenMP may split rows or
@@ -635,22 +633,43 @@ static void ft_tile(const oracle_problem_t* p, int64_t tr, int64_t tc,
  * the differences are the ones a binary32 accumulation brings:
  *   - C(i,j) = fl32(alpha * acc + beta * C_in), acc the binary64 inner product;
  *   - an accumulator injection flips bit b of the binary32 accumulator after all K products;
- *   - tau uses gamma_K(u_acc) for the product part, with sum_k |A(i,k)| sum_j |B(k,j)|
- *     bounded by (sum_k |A(i,k)|) (max_k sum_j |B(k,j)|) over the tile:
+ *   - tau bounds, for any run whose binary32 accumulation steps each err by at most u_acc
+ *     (either direction), the mismatch a clean tile can show. With P = (sum_k |A(i,k)|)
+ *     (max_k sum_j |B(k,j)|) over the tile (an upper bound of sum_k |A(i,k)| sum_j |B(k,j)|):
  *       row:    |alpha| P (gamma_K(u_acc) (1 + s) + 2^-20 + gamma_{tile_n}(2^-24))
- *               + 2^-23 (sum_j |C| + |beta| sum_j |C_in|)
+ *               + 2^-23 sum_j |C| + 2^-21 |beta| sum_j |C_in|
+ *       term by term: gamma_K(u_acc) P, the K-term accumulations of the row's outputs;
+ *       gamma_K(u_acc) s P, the accumulations of A times the pieces of B e that form the
+ *       prediction, the pieces' magnitudes summing to at most s |B e| (s = 1 + 2^-7 for
+ *       three bfloat16 pieces, 1.25 for eight e4m3 pieces); gamma_{tile_n}(2^-24) P, the
+ *       binary32 sum B e over the tile's columns in any order; 2^-23 sum_j |C|, the
+ *       compensated binary32 sum of the row (2 x 2^-24 of its value); 2^-21 |beta| sum_j
+ *       |C_in|, the beta side of four roundings of 2^-24: beta C_in and the output's
+ *       multiply-add, both binary32, and the compensated sum of C_in (2 x 2^-24), with a
+ *       factor two to spare; 2^-20 P collects the alpha side of the output rounding
+ *       (2^-24 (1 + gamma_K) P), the cross term gamma_K s gamma_{tile_n} (below 2^-24 for
+ *       K <= 2^15) and the binary64 operations of the comparison (a few 2^-53), with a
+ *       factor four to spare;
  *       column: |alpha| P_c (gamma_K(u_acc) + gamma_K(2^-24) + 2^-22 + gamma_{tile_m}(2^-24))
  *               + 2^-23 (sum_i |C| + 34 |beta| sum_i |C_in|),
  *               P_c = sum_k (sum_{i in tile} |A(i,k)|) |B(k,j)| (exact: it is formed only in the
  *               rare tiles with a row mismatch)
- *     (the row side's prediction is itself a binary32 product of A with B e split into
- *     pieces whose magnitudes sum to at most s |B e|: s = 1 + 2^-7 for three bfloat16
- *     pieces, 1.25 for eight e4m3 pieces; the column side's is a binary32 dot product of e^T A with B; B e and
- *     e^T A are binary32 sums over the tile, whose rounding in any order is at most
- *     gamma_n(2^-24) times the sum of magnitudes, n the tile width);
+ *       term by term: gamma_K(u_acc) P_c, the column's outputs; gamma_K(2^-24) P_c, the
+ *       prediction (e^T A) B as a binary32 dot product (round to nearest);
+ *       gamma_{tile_m}(2^-24) P_c, e^T A as a binary32 sum over the tile's rows; 2^-23 sum_i
+ *       |C|, the compensated column sum; 34 x 2^-23 |beta| sum_i |C_in|, the beta side:
+ *       gamma_31(2^-24) for the binary32 sums of C_in over each group of 32 rows in any
+ *       order (31 x 2^-24), beta C_in and the output's multiply-add (2 x 2^-24), 33 x 2^-24
+ *       in all, with a factor two to spare; 2^-22 P_c collects the alpha side of the output
+ *       rounding, the cross terms (gamma_K(2^-24) gamma_{tile_m}(2^-24), below 2^-26) and
+ *       the binary64 operations;
  *   - column checksums are formed only when a row mismatches (Section V.A, lazy side);
  *     when they flag no column and beta == 0, the mismatching row is recomputed and each
- *     element compared with its own bound (locates errors in rows of small scale);
+ *     element compared with its own bound (locates errors in rows of small scale):
+ *       |alpha| S (gamma_K(u_acc) + gamma_K(2^-24) + 2^-30) + 2^-23 |C(i,j)|,
+ *       S = sum_k |A(i,k)| |B(k,j)|: the output's accumulation, the recomputation as a
+ *       binary32 dot product (round to nearest), the output's rounding (2^-24, a factor two
+ *       to spare) and 2^-30 S for the cross term and the binary64 operations;
  *   - a located error is corrected by subtracting the row mismatch (Section VI.C),
  *     evaluated as C(i,j) = C^r(i) - sum_{j' != j} C(i,j') (equal in exact arithmetic,
  *     stable for huge or non-finite errors); the result is rounded to binary32. */
@@ -724,7 +743,7 @@ static void ft_tile_acc32(const oracle_problem_t* p, int64_t tr, int64_t tc,
     for (int64_t jj = 0; jj < nJ; ++jj) { Cr_ref = Cr_ref + T[ii + jj * nI]; R = R + fabs(T[ii + jj * nI]); }
     double P = rowAbsA * maxAbsBe;
     double tau = fabs(p->alpha) * P * (gK * (1.0 + piece_sum) + 9.5367431640625e-07 + genc_r) +
-                 1.1920928955078125e-07 * (R + fabs(p->beta) * Q);
+                 1.1920928955078125e-07 * R + 4.76837158203125e-07 * fabs(p->beta) * Q;
     double d = Cr_ref - Cr;
     if (!(fabs(d) <= tau) || isinf(d)) {
       if (fr < 0) { fr = ii; fr_delta = d; fr_tau = tau; fr_pred = Cr; }

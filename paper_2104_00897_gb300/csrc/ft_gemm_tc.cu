@@ -434,17 +434,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         const double ref = (double)rs + (double)rc;
         delta = ref - predicted;
-        // tau = |alpha| P (gamma_K(u_acc) (1 + s) + 2^-20 + gamma_BN(2^-24)) + 2 u32 (sum|C| +
-        // |beta| sum|C_in|), P an upper bound of sum_k |A(i,k)| sum_{j in tile} |B(k,j)|, s the
-        // bound of sum_p |piece_p| / |B e| (the prediction's accumulation error; the
-        // reference row sum's is gamma_K(u_acc) P); the gamma_BN(2^-24) term is the
-        // rounding of B e, a binary32 sum over the tile's BN columns.
+        // tau = |alpha| P (gamma_K(u_acc) (1 + s) + 2^-20 + gamma_BN(2^-24)) + 2^-23 sum|C| +
+        // 2^-21 |beta| sum|C_in|, P an upper bound of sum_k |A(i,k)| sum_{j in tile} |B(k,j)|:
+        // gamma_K(u_acc) P bounds the accumulations of the row's outputs, gamma_K(u_acc) s P
+        // those of the prediction (s bounds sum_p |piece_p| / |B e|), gamma_BN(2^-24) P the
+        // binary32 sum B e over the tile's BN columns, 2^-23 sum|C| the compensated row sum,
+        // 2^-21 |beta| sum|C_in| the beta side of the roundings of beta C_in, of the output's
+        // multiply-add and of the compensated C_in sum (four times 2^-24, doubled), and
+        // 2^-20 P the alpha side of the output rounding, the cross terms and the binary64
+        // operations (about 2^-23 P, quadrupled).
         const float P = __fmul_ru(p.rowAbsA[gi], p.maxAbsBe[nt]);
         const float g = gamma32_up((float)p.K, p.u_acc);
         const float genc = gamma32_up((float)BN, 0x1p-24f);
         const float prod = __fmul_ru(__fmul_ru(fabsf(alpha), P),
                                      __fadd_ru(__fadd_ru(__fmul_ru(g, 1.0f + E::kPieceSum), 0x1p-20f), genc));
-        const float outp = __fmul_ru(0x1p-23f, __fadd_ru(rabs, __fmul_ru(fabsf(p.beta), cabs)));
+        const float outp = __fadd_ru(__fmul_ru(0x1p-23f, rabs), __fmul_ru(0x1p-21f, __fmul_ru(fabsf(p.beta), cabs)));
         tau = (double)__fadd_ru(prod, outp);
         if (!(fabs(delta) <= tau) || isinf(delta)) {
           atomicAdd(&sm.nflag_rows, 1);
@@ -610,8 +614,12 @@ __device__ void resolve_column(const TcParams& p, float alpha, TcPendingEntry& p
   }
   const double dcol = sh.cref - cpred;
   // C^c_ref carries the accumulation error gamma_K(u_acc) P_c; C^c (binary32 dot of e^T A
-  // with B) adds gamma_K(2^-24) P_c + 2^-22 P_c, and e^T A itself, a binary32 sum,
-  // gamma_128(2^-24) P_c; the per-warp C_in partial sums carry gamma_31 (binary32).
+  // with B) adds gamma_K(2^-24) P_c, and e^T A itself, a binary32 sum, gamma_128(2^-24)
+  // P_c; 2^-22 P_c covers the alpha side of the output rounding, the cross terms and the
+  // binary64 operations. 2^-23 sum|C| is the compensated column sum; the beta side, 34 x
+  // 2^-23 |beta| sum|C_in|, covers the per-warp binary32 C_in sums over 32 rows
+  // (gamma_31(2^-24)), beta C_in and the output's multiply-add (2 x 2^-24): 33 x 2^-24,
+  // doubled.
   const float prod = __fmul_ru(__fmul_ru(fabsf(alpha), Pc), __fadd_ru(__fadd_ru(__fadd_ru(g, g24), 0x1p-22f), genc));
   const float outp = __fmul_ru(0x1p-23f, __fadd_ru(sh.cref_abs, __fmul_ru(__fmul_ru(fabsf(p.beta), cin_abs), 34.0f)));
   const double tauc = (double)__fadd_ru(prod, outp);
@@ -622,7 +630,8 @@ __device__ void resolve_column(const TcParams& p, float alpha, TcPendingEntry& p
     const double rec = (double)alpha * rsum;
     const double cij = (double)p.C[gi + gj * p.ldc];
     // the recomputation is a binary32 dot product: its rounding, gamma_K(2^-24) S, joins the
-    // accumulation's gamma_K(u_acc) S
+    // accumulation's gamma_K(u_acc) S; 2^-23 |C| covers the output's rounding (2^-24,
+    // doubled) and 2^-30 S the cross term and the binary64 operations
     const float te = __fadd_ru(__fmul_ru(__fmul_ru(fabsf(alpha), Sx), __fadd_ru(__fadd_ru(g, g24), 0x1p-30f)),
                                __fmul_ru(0x1p-23f, (float)fabs(cij)));
     const double dd = cij - rec;

@@ -87,12 +87,20 @@ cudaError_t launch_decode_e4m3(const uint8_t* codes, float* out, int64_t n, cuda
 cudaError_t launch_tc_gemm(const TcParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmChk,
                            bool ft, cudaStream_t st);
 
-// The protected BF16 GEMM of ftblas_gemm_ex run on caller-supplied device scratch of
-// ws_bytes bytes instead of stream-ordered allocations. Returns
-// FTBLAS_STATUS_WORKSPACE_LIMIT, before any device work, when the problem needs more.
-int gemm_bf16_ft_with_workspace(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, const void* alpha,
-                                const void* A, int Atype, int64_t lda, const void* B, int Btype, int64_t ldb,
-                                const void* beta, void* C, int Ctype, int64_t ldc, int ctype, const float* a_scale,
-                                const float* b_scale, void* stream, ft_report_t* report, void* ws, size_t ws_bytes);
+// Device address of a fixed scratch area, looked up only when a call needs it; returns null
+// and sets *err on failure.
+using ScratchResolver = void* (*)(cudaError_t* err);
+
+// The protected BF16 GEMM of ftblas_gemm_ex run on a fixed scratch area of scratch_bytes
+// bytes instead of stream-ordered allocations. Arguments are checked first, then the
+// problem's scratch size (FTBLAS_STATUS_WORKSPACE_LIMIT before any device work); the
+// scratch address is resolved only after that, and only when the call launches the
+// protected product (quick returns never resolve it). A failed lookup returns
+// FTBLAS_STATUS_CUDA_ERROR with the CUDA error recorded for ftblas_last_cuda_error.
+int gemm_bf16_ft_with_scratch(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, const void* alpha,
+                              const void* A, int Atype, int64_t lda, const void* B, int Btype, int64_t ldb,
+                              const void* beta, void* C, int Ctype, int64_t ldc, int ctype, const float* a_scale,
+                              const float* b_scale, void* stream, ft_report_t* report, ScratchResolver resolve,
+                              size_t scratch_bytes);
 
 }  // namespace ftk

@@ -620,7 +620,7 @@ int dgemm_unfused_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t
 int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, const void* alpha, const void* A,
                  int Atype, int64_t lda, const void* B, int Btype, int64_t ldb, const void* beta, void* C, int Ctype,
                  int64_t ldc, int ctype, const float* a_scale, const float* b_scale, void* stream, ft_report_t* report,
-                 bool ft, void* ws, size_t ws_bytes, bool allow_fp8) {
+                 bool ft, ScratchResolver resolve, size_t ws_bytes, bool allow_fp8) {
   if (layout != FTBLAS_ROW_MAJOR && layout != FTBLAS_COL_MAJOR) return -1;
   if (ta != FTBLAS_NO_TRANS && ta != FTBLAS_TRANS) return -2;
   if (tb != FTBLAS_NO_TRANS && tb != FTBLAS_TRANS) return -3;
@@ -647,7 +647,7 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   const Frame f = map_frame(layout, ta, tb, M, N, A, lda, B, ldb);
   if (need_ab && (!f.a_kmajor || !f.b_kmajor)) return FTBLAS_STATUS_NOT_SUPPORTED;
   const size_t wsb = (ft && need_ab) ? tc_workspace_bytes((int32_t)f.M, (int32_t)f.N, (int32_t)K, kind) : 0;
-  if (ws != nullptr && wsb > ws_bytes) return FTBLAS_STATUS_WORKSPACE_LIMIT;
+  if (resolve != nullptr && wsb > ws_bytes) return FTBLAS_STATUS_WORKSPACE_LIMIT;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (ft && report != nullptr) {
     if (int e = record_cuda(cudaMemsetAsync(report, 0, sizeof(ft_report_t), st))) return e;
@@ -693,8 +693,15 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   if (!make_map_sw128(&tmB, eb, f.B, K, f.N, f.ldb, ft ? (uint32_t)bnp : kTcBN)) return FTBLAS_STATUS_NOT_SUPPORTED;
   g_last_used_tma = 1;
   if (!ft) return record_cuda(launch_tc_gemm(p, &tmA, &tmB, &tmA, false, st));
-  const bool own = ws == nullptr;
-  if (own && cudaMallocAsync(&ws, wsb, st) != cudaSuccess) return FTBLAS_STATUS_ALLOC_FAILED;
+  const bool own = resolve == nullptr;
+  void* ws = nullptr;
+  if (own) {
+    if (cudaMallocAsync(&ws, wsb, st) != cudaSuccess) return FTBLAS_STATUS_ALLOC_FAILED;
+  } else {
+    cudaError_t ce = cudaSuccess;
+    ws = resolve(&ce);
+    if (ws == nullptr) return record_cuda(ce != cudaSuccess ? ce : cudaErrorInvalidDevicePointer);
+  }
   TcWorkspace w = tc_workspace_carve(ws, p.M, p.N, p.K, kind);
   p.rowAbsA = w.rowAbsA; p.maxAbsBe = w.maxAbsBe; p.sA = w.sA; p.absSA = w.absSA;
   p.sa_pitch = w.kpitch; p.pend = w.pend;
@@ -797,15 +804,16 @@ void kernel_timer_stop(cudaStream_t st) {
   g_timer_open = nullptr;
 }
 
-// The protected BF16 GEMM of ftblas_gemm_ex with the encode workspace taken from `ws`
-// (no allocation of any kind).
-int gemm_bf16_ft_with_workspace(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, const void* alpha,
-                                const void* A, int Atype, int64_t lda, const void* B, int Btype, int64_t ldb,
-                                const void* beta, void* C, int Ctype, int64_t ldc, int ctype, const float* a_scale,
-                                const float* b_scale, void* stream, ft_report_t* report, void* ws, size_t ws_bytes) {
-  if (ws == nullptr) return FTBLAS_STATUS_WORKSPACE_LIMIT;
+// The protected BF16 GEMM of ftblas_gemm_ex with the encode workspace in a fixed scratch
+// area (no allocation of any kind).
+int gemm_bf16_ft_with_scratch(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, const void* alpha,
+                              const void* A, int Atype, int64_t lda, const void* B, int Btype, int64_t ldb,
+                              const void* beta, void* C, int Ctype, int64_t ldc, int ctype, const float* a_scale,
+                              const float* b_scale, void* stream, ft_report_t* report, ScratchResolver resolve,
+                              size_t scratch_bytes) {
+  if (resolve == nullptr) return FTBLAS_STATUS_WORKSPACE_LIMIT;
   return tc_gemm_impl(layout, ta, tb, M, N, K, alpha, A, Atype, lda, B, Btype, ldb, beta, C, Ctype, ldc, ctype, a_scale,
-                      b_scale, stream, report, true, ws, ws_bytes, false);
+                      b_scale, stream, report, true, resolve, scratch_bytes, false);
 }
 
 }  // namespace ftk

@@ -19,12 +19,13 @@ std::mutex g_scratch_mu;
 void* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the static scratch on the current device, looked up once per device
-// (with that device current). Returns null on failure and records the CUDA error code.
-void* scratch_for_current_device(int* cuda_error) {
+// (with that device current). Returns null on failure with the CUDA error in *err; the
+// caller records it for ftblas_last_cuda_error.
+void* scratch_for_current_device(cudaError_t* err) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    *cuda_error = static_cast<int>(e != cudaSuccess ? e : cudaErrorInvalidDevice);
+    *err = e != cudaSuccess ? e : cudaErrorInvalidDevice;
     return nullptr;
   }
   std::lock_guard<std::mutex> lk(g_scratch_mu);
@@ -32,7 +33,7 @@ void* scratch_for_current_device(int* cuda_error) {
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_static_scratch);
     if (e != cudaSuccess || ptr == nullptr) {
-      *cuda_error = static_cast<int>(e);
+      *err = e != cudaSuccess ? e : cudaErrorInvalidSymbol;
       return nullptr;
     }
     g_scratch_addr[dev] = ptr;
@@ -47,10 +48,9 @@ extern "C" int ftblas_gemm_ex_noalloc(ftblas_layout_t layout, ftblas_trans_t tra
                                       int64_t lda, const void* B, ftblas_dtype_t Btype, int64_t ldb, const void* beta,
                                       void* C, ftblas_dtype_t Ctype, int64_t ldc, ftblas_dtype_t compute_type,
                                       const float* a_scale, const float* b_scale, void* stream, ft_report_t* report) {
-  int err = 0;
-  void* scratch = scratch_for_current_device(&err);
-  if (scratch == nullptr) return FTBLAS_STATUS_CUDA_ERROR;
-  return ftk::gemm_bf16_ft_with_workspace(layout, transa, transb, M, N, K, alpha, A, Atype, lda, B, Btype, ldb, beta, C,
-                                          Ctype, ldc, compute_type, a_scale, b_scale, stream, report, scratch,
-                                          kStaticScratchBytes);
+  // The address lookup runs inside, after the argument, type and size checks and only when
+  // the protected product is launched.
+  return ftk::gemm_bf16_ft_with_scratch(layout, transa, transb, M, N, K, alpha, A, Atype, lda, B, Btype, ldb, beta, C,
+                                        Ctype, ldc, compute_type, a_scale, b_scale, stream, report,
+                                        scratch_for_current_device, kStaticScratchBytes);
 }

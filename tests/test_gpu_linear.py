@@ -2,7 +2,8 @@
 (Y = X W^T, whose backward runs dX = dY W and dW = dY^T X as two more protected GEMMs).
 
 - FP64: central finite differences (torch.autograd.gradcheck) at X 64 x 48, W 32 x 48,
-  i.e. the GEMM (M, N, K) = (64, 32, 48), pin the backward.
+  i.e. the GEMM (M, N, K) = (64, 32, 48), pin the backward; forward and gradients equal
+  the oracle's products within the FP64 criterion, with one corrected fault per pass.
 - BF16: forward and gradients against the oracle's products of the same BF16 values
   (binary32 accumulation) within the accumulation bound plus the bfloat16 rounding of the
   returned gradients; one injected output fault per GEMM pass is corrected in all three.
@@ -43,6 +44,16 @@ def ref_gemm(A, B):
     return S.load(out, O.COL_MAJOR, M, N, M)
 
 
+def ref_gemm64(A, B):
+    """Oracle product A @ B in binary64 (the GEMM definition, ascending k)."""
+    M, K = A.shape
+    N = B.shape[1]
+    a, lda = S.store(np.ascontiguousarray(A), O.COL_MAJOR)
+    b, ldb = S.store(np.ascontiguousarray(B), O.COL_MAJOR)
+    out = O.gemm(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, M, N, K, 1.0, a, lda, b, ldb, 0.0, None, M)
+    return S.load(out, O.COL_MAJOR, M, N, M)
+
+
 def test_fp64_linear_gradcheck():
     x = torch.from_numpy(S.uniform_matrix(41, 0, 64, 48)).cuda().requires_grad_(True)
     w = torch.from_numpy(S.uniform_matrix(41, 1, 32, 48)).cuda().requires_grad_(True)
@@ -66,10 +77,15 @@ def test_fp64_linear_matches_oracle_and_corrects_one_fault_per_pass():
     s = mon.summary()
     assert (s["calls"], s["detected"], s["corrected"], s["uncorrectable"]) == (3, 3, 3, 0)
     fb.ftblas_set_injection(None)
+    # the oracle's reference products Y = X W^T, dX = dY W, dW = dY^T X: within the FP64
+    # criterion max|C - C_ref| / (max|A| max|B| K) <= 1e-15, and within the rounding bound
     for got, A, B in ((y, X, W.T), (x.grad, dY, W), (w.grad, dY.T, X)):
-        ref = A @ B
-        bound = 2 * gamma(A.shape[1], 2.0 ** -53) * (np.abs(A) @ np.abs(B)) + 1e-300
-        assert np.all(np.abs(got.detach().cpu().numpy() - ref) <= bound)
+        ref = ref_gemm64(A, B)
+        g = got.detach().cpu().numpy()
+        K = A.shape[1]
+        assert np.abs(g - ref).max() / (np.abs(A).max() * np.abs(B).max() * K) <= 1e-15
+        bound = 2 * gamma(K, 2.0 ** -53) * (np.abs(A) @ np.abs(B)) + 1e-300
+        assert np.all(np.abs(g - ref) <= bound)
 
 
 def test_bf16_linear_forward_backward_with_faults():

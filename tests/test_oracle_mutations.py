@@ -33,6 +33,11 @@ MUTATIONS = {
                                       "const int recompute_row = (nr == 1 && nc == 0);"),
     "acc32_row_recompute_never_used": ("const int recompute_row = (nr == 1 && nc == 0 && p->beta == 0.0);",
                                        "const int recompute_row = 0;"),
+    "acc32_row_threshold_without_the_prediction_term": ("P * (gK * (1.0 + piece_sum) +", "P * (gK * (1.0) +"),
+    # sampled rows of the plain product
+    "gemm_rows_without_beta": ("v = scale_out(p, dot_row_col(p, i, j, 0, -1), i, j);",
+                               "v = p->alpha * dot_row_col(p, i, j, 0, -1);"),
+    "gemm_rows_shifted_row": ("int64_t i = rows[r];", "int64_t i = rows[(r + 1) % nrows];"),
     # triangular solve
     "trsm_lower_sums_the_diagonal": ("for (int64_t c = 0; c < r; ++c) s = s + T[r + c * ldt] * w[c];",
                                      "for (int64_t c = 0; c <= r; ++c) s = s + T[r + c * ldt] * w[c];"),

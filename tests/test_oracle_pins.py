@@ -369,7 +369,8 @@ def test_seeded_draw_properties():
 # ACC32 precision (binary32 accumulation and output): pins on exact integer data
 # ------------------------------------------------------------------------------------
 
-def ft32(A_log, B_log, alpha=1.0, beta=0.0, C_log=None, tile=(8, 16), inj=()):
+def ft32(A_log, B_log, alpha=1.0, beta=0.0, C_log=None, tile=(8, 16), inj=(), precision=O.PREC_ACC32,
+         u_acc=O.U_ACC32):
     M, K = A_log.shape
     N = B_log.shape[1]
     a, lda = stored(O.COL_MAJOR, O.TRANS, A_log)   # A k-contiguous
@@ -378,7 +379,7 @@ def ft32(A_log, B_log, alpha=1.0, beta=0.0, C_log=None, tile=(8, 16), inj=()):
         C_log = np.zeros((M, N))
     c, ldc = c_store(O.COL_MAJOR, C_log)
     out, rep = O.ft_gemm(O.COL_MAJOR, O.TRANS, O.NO_TRANS, M, N, K, alpha, a, lda, b, ldb, beta, c, ldc,
-                         tile[0], tile[1], 64, injections=inj, precision=O.PREC_ACC32)
+                         tile[0], tile[1], 64, injections=inj, precision=precision, u_acc=u_acc)
     return S.load(out, O.COL_MAJOR, M, N, ldc), rep
 
 
@@ -459,6 +460,106 @@ def test_acc32_clean_soak_bf16_like_values():
         B = S.bf16_bits_to_f64(S.to_bf16_bits(S.normal_matrix(seed, 1, K, N)))
         _, rep = ft32(A, B, 1.0, 0.0, None, tile=(16, 32))
         assert rep.detected == 0
+
+
+def _extreme_accumulation(terms, u, direction):
+    """The sum of `terms` in ascending order with every step rounded at the extreme that a
+    unit roundoff u allows (standard model fl(s + x) = (s + x)(1 + d), |d| <= u), all in
+    one direction: d = -u (direction -1) or d = +u (direction +1). Binary64 carries the
+    model; its own rounding (2^-53 per step) is far below u."""
+    s = 0.0
+    for x in terms:
+        s = (s + x) * (1.0 + direction * u)
+    return s
+
+
+@pytest.mark.parametrize("precision,u_acc", [(O.PREC_ACC32, 2.0 ** -23), (O.PREC_ACC32_E4M3, 2.0 ** -22)])
+def test_acc32_row_threshold_covers_the_extreme_accumulations(precision, u_acc):
+    """The ACC32 row threshold claims to bound the row mismatch of every tensor-core run in
+    which each binary32 accumulation step errs by at most u_acc in either direction: the
+    K-term accumulations of the tile's outputs C(i, j) (the reference side) and those of A
+    times the pieces of B e that the checksum columns hold (the prediction side). This
+    builds the worst such run by hand: outputs accumulated with every step rounded down,
+    the checksum products with every step rounded up, on data whose partial sums stay at
+    their final size from the first product on (A(i, 0) = 1, later A(i, k) = 2^-16, B all
+    ones). Here B e = 8 exactly, so each of its pieces (three bfloat16 or eight e4m3) is
+    8 or 0. The mismatch then uses most of the threshold: it must stay within it, and it
+    is well above the 0.44 to 0.5 of it that a threshold without the prediction side's
+    term would be."""
+    M, N, K = 1, 8, 2048
+    A = np.full((M, K), 2.0 ** -16)
+    A[:, 0] = 1.0
+    B = np.ones((K, N))
+    # the reference side: sum_j C(i, j), each C(i, j) an extreme accumulation of its products
+    C = [_extreme_accumulation(A[0] * B[:, j], u_acc, -1) for j in range(N)]
+    ref = math.fsum(C)
+    # the prediction side: B e = 8 in every k, held as one nonzero piece (8) in either format
+    Be = B.sum(axis=1)
+    assert np.all(Be == 8.0)
+    pred = _extreme_accumulation(A[0] * Be, u_acc, +1)
+    delta = ref - pred
+    # the oracle's threshold for row 0, read from the record of a flagged row (a checksum
+    # fault far above any threshold; the threshold does not depend on it)
+    _, rep = ft32(A, B, tile=(4, N), precision=precision, u_acc=u_acc,
+                  inj=[dict(i=0, j=0, site=O.SITE_CHECKSUM, mode=O.MODE_ADD_REL, rel_log2=30, sign=1)])
+    (r,) = rep.records()
+    assert r.i == 0 and r.kind == O.KIND_CHECKSUM_ONLY
+    tau = r.tau_row
+    assert abs(delta) <= tau
+    # the data is adversarial enough to need every term of it (0.97 of the threshold with
+    # the bfloat16 pieces, 0.87 with the e4m3 pieces, whose magnitude bound is looser)
+    assert abs(delta) > 0.8 * tau
+    # and a clean run of the oracle itself never flags
+    _, rep0 = ft32(A, B, tile=(4, N), precision=precision, u_acc=u_acc)
+    assert rep0.detected == 0
+
+
+# ------------------------------------------------------------------------------------
+# Sampled rows of the plain product (the reference of the full-size GPU tests)
+# ------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("layout,ta,tb", COMBOS)
+def test_gemm_rows_equals_the_full_product_row_by_row(layout, ta, tb):
+    """oracle_gemm_rows gives, bit for bit, the rows of oracle_gemm, whatever rows are
+    asked for (repeated, unordered, the last one), with alpha, beta and C_in."""
+    M, N, K = 23, 17, 31
+    A = S.uniform_matrix(61, 0, M, K)
+    B = S.uniform_matrix(61, 1, K, N)
+    Cin = S.uniform_matrix(61, 2, M, N)
+    a, lda = stored(layout, ta, A)
+    b, ldb = stored(layout, tb, B)
+    c, ldc = c_store(layout, Cin)
+    full = S.load(O.gemm(layout, ta, tb, M, N, K, 1.5, a, lda, b, ldb, 0.5, c, ldc), layout, M, N, ldc)
+    rows = np.array([22, 0, 7, 7, 13])
+    got = O.gemm_rows(layout, ta, tb, M, N, K, 1.5, a, lda, b, ldb, 0.5, c, ldc, rows)
+    assert np.array_equal(got, full[rows, :])
+    # quick returns: alpha = 0 gives beta C_in; K = 0 likewise
+    got0 = O.gemm_rows(layout, ta, tb, M, N, K, 0.0, a, lda, b, ldb, 0.5, c, ldc, rows)
+    assert np.array_equal(got0, 0.5 * Cin[rows, :])
+    got_k0 = O.gemm_rows(layout, ta, tb, M, N, 0, 1.5, a, lda, b, ldb, -2.0, c, ldc, rows)
+    assert np.array_equal(got_k0, -2.0 * Cin[rows, :])
+
+
+@pytest.mark.parametrize("layout,ta,tb", COMBOS)
+def test_gemm_rows_closed_form_linear_operands(layout, ta, tb):
+    """A(i,k) = i + k, B(k,j) = k + j: row i of C is K i j + (i + j) S1 + S2 exactly, and
+    with alpha = 0.5, beta = -2, C_in(i,j) = i - 2 j, 0.5 of that minus 2 C_in."""
+    M, N, K = 40, 9, 57
+    k = np.arange(K)
+    A = (np.arange(M)[:, None] + k[None, :]).astype(np.float64)
+    B = (k[:, None] + np.arange(N)[None, :]).astype(np.float64)
+    i = np.arange(M)[:, None]
+    j = np.arange(N)[None, :]
+    S1 = K * (K - 1) // 2
+    S2 = (K - 1) * K * (2 * K - 1) // 6
+    expect = (K * i * j + (i + j) * S1 + S2).astype(np.float64)
+    Cin = (i - 2 * j).astype(np.float64)
+    a, lda = stored(layout, ta, A)
+    b, ldb = stored(layout, tb, B)
+    c, ldc = c_store(layout, Cin)
+    rows = np.array([0, 39, 5])
+    got = O.gemm_rows(layout, ta, tb, M, N, K, 0.5, a, lda, b, ldb, -2.0, c, ldc, rows)
+    assert np.array_equal(got, (0.5 * expect - 2.0 * Cin)[rows, :])
 
 
 # ------------------------------------------------------------------------------------
