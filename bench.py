@@ -88,8 +88,15 @@ def peaks():
             mp = json.load(f)
     bf16 = mp.get("bf16_tflops")
     sm_max = mp.get("sm_max_mhz", 2070.0)
-    # FP64 FMA pipe: 2 FMA / clock / SM (GB300 nominal 1.25 TFLOP/s at 2070 MHz) x 152 SMs.
-    alu = 2 * 2 * 152 * sm_max * 1e6 / 1e12
+    sms = 152  # GB300; the device's own count when one answers
+    try:
+        import torch
+        if torch.cuda.is_available():
+            sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    except Exception:
+        pass
+    # FP64 FMA pipe: 2 FMA / clock / SM (GB300 nominal 1.25 TFLOP/s at 2070 MHz) x the SMs.
+    alu = 2 * 2 * sms * sm_max * 1e6 / 1e12
     if bf16 is not None:
         tensor = bf16 * 1.25 / 2250.0
         tensor_src = f"measured bf16 {bf16} TFLOP/s x nominal FP64/BF16 ratio 1.25/2250"
@@ -100,7 +107,7 @@ def peaks():
     bf16_src = (f"measured bf16 {bf16} TFLOP/s (burst)" if bf16 is not None
                 else "fallback bf16 1900 TFLOP/s (burst)")
     bf16_sus = mp.get("bf16_tflops_sustained") or 1700.0
-    return dict(alu=alu, alu_src=f"2 FP64 FMA/clk/SM x 152 SMs x {sm_max} MHz", tensor=tensor,
+    return dict(alu=alu, alu_src=f"2 FP64 FMA/clk/SM x {sms} SMs x {sm_max} MHz", tensor=tensor,
                 tensor_src=tensor_src, bf16=bf16_peak, bf16_src=bf16_src, bf16_sustained=bf16_sus)
 
 

@@ -28,6 +28,7 @@ MAX_RECORDS = 256
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ftgemm_oracle.c")
+_SRCS = (_SRC, os.path.join(_HERE, "emu_oracle.c"))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -48,6 +49,19 @@ class Problem(C.Structure):
         ("precision", C.c_int32), ("pad2_", C.c_int32),
         ("u_acc", C.c_double),
         ("kc", C.c_int64),
+    ]
+
+
+class EmuProblem(C.Structure):
+    _fields_ = [
+        ("layout", C.c_int32), ("transa", C.c_int32), ("transb", C.c_int32), ("slices", C.c_int32),
+        ("M", C.c_int64), ("N", C.c_int64), ("K", C.c_int64),
+        ("alpha", C.c_double),
+        ("A", C.c_void_p), ("lda", C.c_int64),
+        ("B", C.c_void_p), ("ldb", C.c_int64),
+        ("beta", C.c_double),
+        ("Cin", C.c_void_p), ("ldc", C.c_int64),
+        ("tile_m", C.c_int64), ("tile_n", C.c_int64),
     ]
 
 
@@ -84,12 +98,13 @@ class Report(C.Structure):
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C, -ffp-contract=off). Returns the library path."""
     with _lock:
-        if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        if not force and os.path.exists(_LIB_PATH) and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(x)
+                                                           for x in _SRCS):
             return _LIB_PATH
         os.makedirs(_BUILD, exist_ok=True)
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
-               "-fopenmp", "-Wall", "-o", tmp, _SRC, "-lm"]
+               "-fopenmp", "-Wall", "-o", tmp, *_SRCS, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
         return _LIB_PATH
@@ -114,6 +129,17 @@ def lib():
         L.oracle_draw_injections.restype = C.c_int64
         L.oracle_trsm_left.argtypes = [C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64]
         L.oracle_trsm_left.restype = None
+        L.oracle_emu_gemm.argtypes = [C.POINTER(EmuProblem), C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                                      C.c_void_p, C.POINTER(Report)]
+        L.oracle_emu_gemm.restype = C.c_int
+        L.oracle_emu_split.argtypes = [C.c_double, C.c_int, C.c_void_p]
+        L.oracle_emu_split.restype = None
+        L.oracle_emu_digits.argtypes = [C.c_int64, C.c_void_p]
+        L.oracle_emu_digits.restype = None
+        L.oracle_emu_i128_to_double.argtypes = [C.c_int64, C.c_uint64]
+        L.oracle_emu_i128_to_double.restype = C.c_double
+        L.oracle_emu_max_k.argtypes = [C.c_int]
+        L.oracle_emu_max_k.restype = C.c_int64
         L.oracle_num_threads.argtypes = []
         L.oracle_num_threads.restype = C.c_int
         _lib = L
@@ -227,3 +253,63 @@ def draw_injections(seed, launch, every_n, per_launch, site, mode, bit_lo, bit_h
                                      log2_lo, log2_hi, M, N, tile_m, tile_n, cap, C.addressof(arr))
     return [dict(i=arr[q].i, j=arr[q].j, site=arr[q].site, mode=arr[q].mode, bit=arr[q].bit,
                  rel_log2=arr[q].rel_log2, sign=arr[q].sign) for q in range(n)]
+
+
+# ------------------------------------------------------------------------------------
+# The emulated FP64 product (emu_oracle.c): binary64 operands as integer slices with
+# exact group products and exact integer checksums.
+# ------------------------------------------------------------------------------------
+EMU_SLICES = 14
+EMU_TILE_M, EMU_TILE_N = 128, 248
+
+
+def emu_gemm(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldc, slices=EMU_SLICES,
+             injections=(), tiles=None, out=None, tile_m=EMU_TILE_M, tile_n=EMU_TILE_N):
+    """The emulated protected GEMM. Returns ``(Cout_buffer, Report)``; ``tiles`` as in
+    ``ft_gemm`` (caller tile numbering; tiles are tile_n x tile_m for row-major calls)."""
+    A = _f64(A); B = _f64(B)
+    Cin_ = _f64(Cin) if Cin is not None else np.zeros(1)
+    p = EmuProblem(layout=layout, transa=transa, transb=transb, slices=slices, M=M, N=N, K=K, alpha=alpha,
+                   A=A.ctypes.data, lda=lda, B=B.ctypes.data, ldb=ldb, beta=beta, Cin=Cin_.ctypes.data, ldc=ldc,
+                   tile_m=tile_m, tile_n=tile_n)
+    if out is None:
+        n_store = max(1, ldc * (N if layout == COL_MAJOR else M))
+        out = np.array(Cin_, copy=True) if Cin is not None and beta != 0.0 else np.zeros(n_store)
+    inj, n_inj = injections_array(injections)
+    rep = Report()
+    if tiles is None:
+        rc = lib().oracle_emu_gemm(C.byref(p), n_inj, C.addressof(inj), 0, None, out.ctypes.data, C.byref(rep))
+    else:
+        t = np.ascontiguousarray(tiles, dtype=np.int64)
+        rc = lib().oracle_emu_gemm(C.byref(p), n_inj, C.addressof(inj), len(t), t.ctypes.data, out.ctypes.data,
+                                   C.byref(rep))
+    if rc != 0:
+        raise ValueError(f"oracle_emu_gemm: rc {rc}")
+    return out, rep
+
+
+def emu_split(x, slices=EMU_SLICES):
+    """The integer slices of x in (-1, 1)."""
+    out = (C.c_int32 * slices)()
+    lib().oracle_emu_split(float(x), slices, out)
+    return [int(v) for v in out]
+
+
+def emu_digits(v):
+    """The four base-16 digits (each in [-8, 8]) of the integer v."""
+    out = (C.c_int32 * 4)()
+    lib().oracle_emu_digits(int(v), out)
+    return [int(d) for d in out]
+
+
+def emu_i128_to_double(x):
+    """The oracle's rounded-to-nearest conversion of a 128-bit integer x."""
+    x = int(x) & ((1 << 128) - 1)
+    hi = x >> 64
+    if hi >= 1 << 63:
+        hi -= 1 << 64
+    return lib().oracle_emu_i128_to_double(hi, x & ((1 << 64) - 1))
+
+
+def emu_max_k(slices=EMU_SLICES):
+    return int(lib().oracle_emu_max_k(slices))

@@ -1,6 +1,6 @@
 """The oracle's pins must catch plausible mistakes.
 
-Each case plants one mistake in a copy of the oracle's C source (never in the real one),
+Each case plants one mistake in a copy of the oracle's C sources (never in the real ones),
 builds it, and runs the pin tests and the randomised properties against that build; they
 must fail.
 """
@@ -46,18 +46,40 @@ MUTATIONS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
+# the emulated FP64 product (emu_oracle.c)
+EMU_MUTATIONS = {
+    "emu_slices_truncated_not_rounded": ("double a = nearbyint(r);", "double a = floor(r);"),
+    "emu_group_pairs_shifted": ("const int32_t* b = &bs[(jj * s + (g - pp)) * K];",
+                                "const int32_t* b = &bs[(jj * s + (g - pp + 1) % s) * K];"),
+    "emu_group_weight": ("S[jj] = S[jj] * 16 + gi;", "S[jj] = S[jj] * 8 + gi;"),
+    "emu_scale_shift_off_by_one_slice": ("const int shift = -4 * (s + 1);", "const int shift = -4 * s;"),
+    "emu_checksum_digit_weight": ("for (int t = 0; t < EO_DIGITS; ++t, w *= 16) {",
+                                  "for (int t = 0; t < EO_DIGITS; ++t, w *= 8) {"),
+    "emu_location_never_recorded": ("if (bits64(before) != bits64(after))", "if (0)"),
+    "emu_conversion_drops_high_bits": ("return (double)x;", "return (double)(int64_t)x;"),
+    "emu_binary64_stage_without_threshold": ("double tauC = 2.0 * gamma_u(", "double tauC = 0.0 * gamma_u("),
+    "emu_more_flagged_rows_accepted": ("#define EO_MAX_FLAGGED_ROWS 4", "#define EO_MAX_FLAGGED_ROWS 5"),
+}
+EMU_SRC = os.path.join(ROOT, "oracle", "emu_oracle.c")
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS) + sorted(EMU_MUTATIONS))
 def test_pins_catch_planted_mistake(name, tmp_path):
-    old, new = MUTATIONS[name]
-    src = open(SRC).read()
-    assert src.count(old) >= 1, f"mutation anchor for {name} not found"
-    mutated = tmp_path / "mutant.c"
-    mutated.write_text(src.replace(old, new))
+    target, (old, new) = (SRC, MUTATIONS[name]) if name in MUTATIONS else (EMU_SRC, EMU_MUTATIONS[name])
+    srcs = []
+    for path in (SRC, EMU_SRC):
+        text = open(path).read()
+        if path == target:
+            assert text.count(old) >= 1, f"mutation anchor for {name} not found"
+            text = text.replace(old, new)
+        out = tmp_path / os.path.basename(path)
+        out.write_text(text)
+        srcs.append(str(out))
     lib = tmp_path / "libmutant.so"
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
-                    "-o", str(lib), str(mutated), "-lm"], check=True, capture_output=True)
+                    "-o", str(lib), *srcs, "-lm"], check=True, capture_output=True)
     env = dict(os.environ, ORACLE_LIB=str(lib))
-    tests = [os.path.join(ROOT, "tests", "test_oracle_pins.py")]
+    tests = [os.path.join(ROOT, "tests", "test_oracle_pins.py"), os.path.join(ROOT, "tests", "test_emu_oracle.py")]
     try:
         import hypothesis  # noqa: F401  (the randomised properties need it)
         tests.append(os.path.join(ROOT, "tests", "test_oracle_properties.py"))
