@@ -318,6 +318,68 @@ int ftblas_gemm_ex_noalloc(ftblas_layout_t layout, ftblas_trans_t transa, ftblas
                            void* C, ftblas_dtype_t Ctype, int64_t ldc, ftblas_dtype_t compute_type,
                            const float* a_scale, const float* b_scale, void* stream, ft_report_t* report);
 
+/* Emulated FP64 ABFT-protected GEMM (Section II.A checksums, Section V.A's argument for
+ * cheap checksums carried over to the product itself): the binary64 GEMM of ftblas_dgemm
+ * (same arguments 1-16, same quick returns) formed on the E4M3 tensor cores from integer
+ * slices.
+ *   - Scales and slices: row i of op(A) is scaled by 2^-e_i, e_i the binary exponent of
+ *     max_k |A(i,k)|, and column j of op(B) likewise; each scaled value x in (-1, 1) is
+ *     split into s slices a_p = rint(r_p), r_0 = 16 x, r_{p+1} = 16 (r_p - a_p), integers of
+ *     magnitude <= 16 (s = ftblas_set_emulation_slices, 14 by default).
+ *   - Product: the groups G_g = sum_{p+q=g} A_p B_q, g < s, are formed exactly on the tensor
+ *     cores (every partial sum an integer below 2^24: K <= ftblas_emulation_max_k(s), 16384
+ *     for s = 14, else FTBLAS_STATUS_NOT_SUPPORTED), combined exactly in 128-bit integers,
+ *     and C = alpha 2^(e_i + f_j - 4(s+1)) S + beta C_in in binary64 (S converted with one
+ *     rounding). The error against the exact product is at most |alpha| 2^(e_i + f_j) K
+ *     16^-s (s + 3) / 4 plus a few units of the last place of C: with s = 14, at most 3.3e-16
+ *     of max|A| max|B| K.
+ *   - Checks: in every tile of 128 x 248 outputs (ftblas_verification_tile with
+ *     FTBLAS_R_8F_E4M3) each group's row sums are compared exactly with A_p (B_q e), B e
+ *     held as four base-16 digits in the MMA's last columns: zero threshold, so every
+ *     change of a group value is detected; C's row sums are compared with alpha sum_j v +
+ *     beta sum_j C_in within the rounding of the binary64 stage.
+ *   - Correction: a flagged row is recomputed exactly from the slices and stored, so C is
+ *     the fault-free result bit for bit; records name the elements that differed
+ *     (FT_KIND_CORRECTED, delta_row the integer mismatch or the binary64 stage's, tau_row 0
+ *     for an integer check), or FT_KIND_CHECKSUM_ONLY when none did. More than 4 flagged
+ *     rows in a tile, or more than 64 flagged tiles in a call: FT_KIND_UNCORRECTABLE, C as
+ *     computed. A row or column holding a non-finite value gives NaN there, and its tiles
+ *     are reported FT_KIND_INPUT_NONFINITE.
+ *   - Injection: the accumulator site flips bit (bit & 31) of the binary32 value of G_g(i,j)
+ *     with g = the point's k_tile (0: the leading group); the output and checksum sites
+ *     act on C(i,j) and on group 0's predicted row checksum (adding sign max(1,
+ *     floor(2^rel_log2 |P|))); the stall site as for the tensor-core product kernel.
+ * Workspace (about 2 s (M + N) K bytes) from the stream-ordered allocator, released on the
+ * same stream. Row-major calls compute C^T in the column-major frame, whose rows are the
+ * caller's columns; the values are identical. */
+int ftblas_dgemm_emulated(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,
+                          int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+                          const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                          void* stream, ft_report_t* report);
+
+/* ftblas_dgemm_emulated with the protection compiled out (no checksum digits, no checks;
+ * 256-column tiles): the baseline of its overhead, as Section VI.B compares FT-BLAS with its
+ * own implementation without FT capability. Same arguments without the report. */
+int ftblas_dgemm_emulated_noabft(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,
+                                 int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+                                 const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                                 void* stream);
+
+/* Library control, no counterpart in the paper: slices per operand of the emulated FP64 GEMM,
+ * 2 .. 15 (default 14). Fewer slices run faster with a larger error bound (above).
+ * Returns the previous value, or -1 for another value. Process-wide. */
+int ftblas_set_emulation_slices(int slices);
+
+/* Library control, no counterpart in the paper: the largest K the emulated FP64 GEMM accepts
+ * with `slices` slices, 2^18 / (slices + 2); -1 for slices outside 2 .. 15. */
+int64_t ftblas_emulation_max_k(int slices);
+
+/* Test support (no counterpart in the paper): the emulated GEMM's conversion of n 128-bit
+ * integers (words[2i] low, words[2i+1] high, two's complement; device memory) to binary64
+ * rounded to nearest, ties to even, into out (device memory). Asynchronous on stream.
+ * Returns 0, -p for an invalid argument p, or FTBLAS_STATUS_CUDA_ERROR. */
+int ftblas_emu_convert_i128(const int64_t* words, double* out, int64_t n, void* stream);
+
 /* The verification interval of Section II.A (one error correctable in each): the shape of the
  * verification tile used for a call, in the caller's coordinates of C, and the k-tile depth
  * that sets the accumulator injection point (bk * floor(ceil(K/bk)/2) products; for the

@@ -288,12 +288,14 @@ static void emu_tile(const frame_t* f, int64_t tr, int64_t tc, int64_t npts, con
   /* slices of the tile's rows of op(A) and columns of op(B) (step 2) */
   int32_t* as = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nI * s * K));   /* as[(ii*s + p)*K + k] */
   int32_t* bs = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nJ * s * K));   /* bs[(jj*s + q)*K + k] */
+#pragma omp parallel for schedule(static)
   for (int64_t ii = 0; ii < nI; ++ii)
     for (int64_t k = 0; k < K; ++k) {
       int32_t sl[32];
       oracle_emu_split(fin_row[i0 + ii] ? ldexp(fa(f, i0 + ii, k), -erow[i0 + ii]) : 0.0, s, sl);
       for (int q = 0; q < s; ++q) as[(ii * s + q) * K + k] = sl[q];
     }
+#pragma omp parallel for schedule(static)
   for (int64_t jj = 0; jj < nJ; ++jj)
     for (int64_t k = 0; k < K; ++k) {
       int32_t sl[32];
@@ -320,12 +322,15 @@ static void emu_tile(const frame_t* f, int64_t tr, int64_t tc, int64_t npts, con
   int* flagged = (int*)calloc((size_t)nI, sizeof(int));
   double* fdelta = (double*)calloc((size_t)nI, sizeof(double));
   double* ftau = (double*)calloc((size_t)nI, sizeof(double));
-  i128* S = (i128*)malloc(sizeof(i128) * (size_t)nJ);
-  i128* St = (i128*)malloc(sizeof(i128) * (size_t)nJ);
   const int shift = -4 * (s + 1);
 
+  /* rows are independent: OpenMP may split them across threads (every sum below is exact
+   * or taken in the order written within one row) */
+#pragma omp parallel for schedule(dynamic, 1)
   for (int64_t ii = 0; ii < nI; ++ii) {
     const int64_t i = i0 + ii;
+    i128* S = (i128*)malloc(sizeof(i128) * (size_t)nJ);
+    i128* St = (i128*)malloc(sizeof(i128) * (size_t)nJ);
     for (int64_t jj = 0; jj < nJ; ++jj) { S[jj] = 0; St[jj] = 0; }
     for (int g = 0; g < s; ++g) {
       /* step 3: group values as the accumulators hold them, and the reference row sum */
@@ -407,6 +412,8 @@ static void emu_tile(const frame_t* f, int64_t tr, int64_t tc, int64_t npts, con
     double tauC = 2.0 * gamma_u((double)(nJ + 2)) * ((fabs(p->alpha) * aV + fabs(p->beta) * aQ) + aC);
     double d = RC - Pi;
     if (!flagged[ii] && (!(fabs(d) <= tauC) || isinf(d))) { flagged[ii] = 1; fdelta[ii] = d; ftau[ii] = tauC; }
+    free(S);
+    free(St);
   }
 
   /* step 7: classification, location by recomputation, correction */
@@ -447,7 +454,7 @@ static void emu_tile(const frame_t* f, int64_t tr, int64_t tc, int64_t npts, con
   for (int64_t ii = 0; ii < nI; ++ii)
     for (int64_t jj = 0; jj < nJ; ++jj) Cout[fc_index(f, i0 + ii, j0 + jj)] = Cc[ii * nJ + jj];
 
-  free(as); free(bs); free(dg); free(Cc); free(Ct); free(flagged); free(fdelta); free(ftau); free(S); free(St);
+  free(as); free(bs); free(dg); free(Cc); free(Ct); free(flagged); free(fdelta); free(ftau);
 }
 
 /* ---------------------------------------------------------------------------------- */
@@ -501,7 +508,6 @@ int oracle_emu_gemm(const emu_problem_t* p, int64_t n_inj, const emu_injection_t
   const int64_t ctr = f.swap ? ftc : ftr;  /* tile rows in the caller's coordinates */
   const int64_t nsel = sel_tiles ? n_sel : ftr * ftc;
   emu_tile_result_t* res = (emu_tile_result_t*)calloc((size_t)(nsel > 0 ? nsel : 1), sizeof(emu_tile_result_t));
-#pragma omp parallel for schedule(dynamic, 1)
   for (int64_t q = 0; q < nsel; ++q) {
     int64_t tr, tc;
     if (sel_tiles) {

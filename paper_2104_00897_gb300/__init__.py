@@ -90,6 +90,11 @@ SIGNATURES = {
     "ftblas_dgemm_noabft": (C.c_int, _GEMM_ARGS + [C.c_void_p]),
     "ftblas_dgemm_host": (C.c_int, _GEMM_ARGS + [C.c_void_p, C.c_void_p]),
     "ftblas_dgemm_unfused": (C.c_int, _GEMM_ARGS + [C.c_void_p, C.c_void_p]),
+    "ftblas_dgemm_emulated": (C.c_int, _GEMM_ARGS + [C.c_void_p, C.c_void_p]),
+    "ftblas_dgemm_emulated_noabft": (C.c_int, _GEMM_ARGS + [C.c_void_p]),
+    "ftblas_set_emulation_slices": (C.c_int, [C.c_int]),
+    "ftblas_emulation_max_k": (C.c_int64, [C.c_int]),
+    "ftblas_emu_convert_i128": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "ftblas_dsymm": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_double, C.c_void_p, C.c_int64,
                                C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "ftblas_dtrmm": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_double,
@@ -149,6 +154,28 @@ def ftblas_dgemm_noabft(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, 
 def ftblas_dgemm_unfused(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream, report):
     return _call("ftblas_dgemm_unfused", layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream,
                  report)
+
+
+def ftblas_dgemm_emulated(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream, report):
+    return _call("ftblas_dgemm_emulated", layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc,
+                 stream, report)
+
+
+def ftblas_dgemm_emulated_noabft(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_, ldc, stream):
+    return _call("ftblas_dgemm_emulated_noabft", layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C_,
+                 ldc, stream)
+
+
+def ftblas_set_emulation_slices(slices):
+    return _call("ftblas_set_emulation_slices", slices)
+
+
+def ftblas_emulation_max_k(slices):
+    return _call("ftblas_emulation_max_k", slices)
+
+
+def ftblas_emu_convert_i128(words, out, n, stream=None):
+    return _call("ftblas_emu_convert_i128", words, out, n, stream)
 
 
 def ftblas_dsymm(layout, side, uplo, M, N, alpha, A, lda, B, ldb, beta, C_, ldc, stream, report):

@@ -9,6 +9,7 @@
 #include <mutex>
 #include <vector>
 
+#include "ft_emu.h"
 #include "ft_internal.h"
 #include "ft_tc.h"
 
@@ -21,6 +22,7 @@ thread_local int g_last_used_tma = -1;
 std::atomic<int> g_fp64_engine{kEngineDFMA};
 std::atomic<int> g_fp64_tile{0};  // 0: fp64_tile_edge decides; else the forced DFMA tile edge
 std::atomic<int64_t> g_kc_interval{0};
+std::atomic<int> g_emu_slices{kEmuSlicesDefault};
 
 // ------------------------------------------------------------------ injection plan state
 std::mutex g_inj_mu;
@@ -713,6 +715,80 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   return rc;
 }
 
+// ------------------------------------------------------------------ emulated FP64
+// The binary64 GEMM formed from E4M3 integer slices on the tensor cores (ft_emu.cu).
+// Workspace from the stream-ordered allocator, released on the same stream.
+int emu_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+             const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* stream, ft_report_t* report,
+             bool ft) {
+  const bool need_ab = (K > 0 && alpha != 0.0 && M > 0 && N > 0);
+  int v = validate(layout, ta, tb, M, N, K, A, lda, B, ldb, C, ldc, need_ab);
+  if (v != 0) return v;
+  const int s = g_emu_slices.load();
+  if (K > emu_max_k(s) || M > (int64_t(1) << 26) || N > (int64_t(1) << 26)) return FTBLAS_STATUS_NOT_SUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (ft && report != nullptr) {
+    if (int e = record_cuda(cudaMemsetAsync(report, 0, sizeof(ft_report_t), st))) return e;
+  }
+  if (M == 0 || N == 0) return 0;
+  const Frame f = map_frame(layout, ta, tb, M, N, A, lda, B, ldb);
+  const int bn = ft ? kEmuBNProt : kEmuBNPlain;
+  CallerPoint pts[kMaxInject];
+  int npts = 0;
+  if (ft) {
+    const int64_t tile_rows = f.swap ? bn : kEmuBM, tile_cols = f.swap ? kEmuBM : bn;
+    npts = plan_injections(M, N, tile_rows, tile_cols, pts);
+  }
+  if (K == 0 || alpha == 0.0) return record_cuda(launch_scale(C, ldc, (int32_t)f.M, (int32_t)f.N, beta, st));
+  EmuParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.M = (int32_t)f.M; p.N = (int32_t)f.N; p.K = (int32_t)K;
+  p.s = s;
+  p.bn = bn;
+  p.nMb = (int32_t)((f.M + kEmuBM - 1) / kEmuBM);
+  p.nNb = (int32_t)((f.N + bn - 1) / bn);
+  p.m_pad = (int64_t)p.nMb * kEmuBM;
+  p.n_pad = (int64_t)p.nNb * bn;
+  p.kpitch = (K + 15) / 16 * 16;
+  p.swap_report = f.swap;
+  p.alpha = alpha; p.beta = beta;
+  p.C = C; p.ldc = ldc;
+  p.report = ft ? report : nullptr;
+  bool stall = false;
+  for (int q = 0; q < npts; ++q) {
+    const CallerPoint& c = pts[q];
+    InjectPoint& ip = p.inj.p[p.inj.n++];
+    ip.i = (int32_t)(f.swap ? c.j : c.i);
+    ip.j = (int32_t)(f.swap ? c.i : c.j);
+    ip.site = c.site == FT_SITE_CHECKSUM ? kSiteChecksumRow : c.site == FT_SITE_STALL ? kSiteStall : c.site;
+    ip.mode = c.mode; ip.bit = c.bit; ip.rel_log2 = c.rel_log2; ip.sign = c.sign; ip.kt = c.kt;
+    stall |= c.site == FT_SITE_STALL;
+  }
+  p.wait_limit_ns = stall ? 20000000ull : 2000000000ull;
+  // sources of the split: line i of op(A) and line j of op(B)^T in the kernel frame
+  const EmuSource sa{static_cast<const double*>(f.A), f.a_kmajor ? f.lda : 1, f.a_kmajor ? 1 : f.lda, f.M};
+  const EmuSource sb{static_cast<const double*>(f.B), f.b_kmajor ? f.ldb : 1, f.b_kmajor ? 1 : f.ldb, f.N};
+  const int64_t tiles = (int64_t)p.nMb * p.nNb;
+  const int sms = current_sm_count();
+  const int grid = (int)(tiles < sms ? tiles : sms);
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, emu_workspace_bytes(p, grid), st) != cudaSuccess) return FTBLAS_STATUS_ALLOC_FAILED;
+  uint8_t* chk = nullptr;
+  emu_workspace_carve(p, ws, grid, &chk);
+  CUtensorMap tmA, tmB, tmC;
+  std::memset(&tmA, 0, sizeof(tmA)); std::memset(&tmB, 0, sizeof(tmB)); std::memset(&tmC, 0, sizeof(tmC));
+  int rc = 0;
+  if (!make_map_sw128(&tmA, 1, p.aslices, K, (int64_t)s * p.m_pad, p.kpitch, kEmuBM) ||
+      !make_map_sw128(&tmB, 1, p.bslices, K, (int64_t)s * p.n_pad, p.kpitch, (uint32_t)bn) ||
+      (ft && !make_map_sw128(&tmC, 1, chk, K, (int64_t)s * p.nNb * kEmuChkRows, p.kpitch, kEmuChkRows)))
+    rc = FTBLAS_STATUS_NOT_SUPPORTED;
+  if (rc == 0) rc = record_cuda(launch_emu_split(p, sa, sb, chk, ft, st));
+  if (rc == 0) rc = record_cuda(launch_emu_gemm(p, &tmA, &tmB, &tmC, ft, grid, st));
+  g_last_used_tma = 1;
+  cudaFreeAsync(ws, st);
+  return rc;
+}
+
 int gemm_ex_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, const void* alpha, const void* A,
                  int Atype, int64_t lda, const void* B, int Btype, int64_t ldb, const void* beta, void* C, int Ctype,
                  int64_t ldc, int ctype, const float* a_scale, const float* b_scale, void* stream,
@@ -977,6 +1053,35 @@ int ftblas_verification_tile(ftblas_layout_t layout, ftblas_dtype_t compute_type
   *tile_cols = swap ? bm : bn;
   *k_tile = kt;
   return 0;
+}
+
+int ftblas_dgemm_emulated(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb, int64_t M, int64_t N,
+                          int64_t K, double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                          double beta, double* C, int64_t ldc, void* stream, ft_report_t* report) {
+  return emu_impl(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, stream, report, true);
+}
+
+int ftblas_dgemm_emulated_noabft(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb, int64_t M,
+                                 int64_t N, int64_t K, double alpha, const double* A, int64_t lda, const double* B,
+                                 int64_t ldb, double beta, double* C, int64_t ldc, void* stream) {
+  return emu_impl(layout, transa, transb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, stream, nullptr, false);
+}
+
+int ftblas_set_emulation_slices(int slices) {
+  if (slices < 2 || slices > kEmuSlicesMax) return -1;
+  return g_emu_slices.exchange(slices);
+}
+
+int64_t ftblas_emulation_max_k(int slices) {
+  if (slices < 2 || slices > kEmuSlicesMax) return -1;
+  return emu_max_k(slices);
+}
+
+int ftblas_emu_convert_i128(const int64_t* words, double* out, int64_t n, void* stream) {
+  if (n < 0) return -3;
+  if (n > 0 && words == nullptr) return -1;
+  if (n > 0 && out == nullptr) return -2;
+  return record_cuda(launch_emu_convert(words, out, n, static_cast<cudaStream_t>(stream)));
 }
 
 int64_t ftblas_set_verification_interval(int64_t k_interval) {
