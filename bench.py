@@ -68,6 +68,10 @@ def parse_args():
                     help="measure only the unfused comparator (ABFT passes around cuBLAS DGEMM)")
     ap.add_argument("--no-unfused", action="store_true", help="skip the unfused comparator")
     ap.add_argument("--no-online", action="store_true", help="skip the online-verification measurement")
+    ap.add_argument("--no-emulated", action="store_true", help="skip the emulated FP64 measurement")
+    ap.add_argument("--no-large", action="store_true", help="skip the FP64 16384^3 point of the default line")
+    ap.add_argument("--no-soak-default", action="store_true", help="skip the 60 s soak of the default line")
+    ap.add_argument("--emulated-only", action="store_true", help="measure only the emulated FP64 GEMM")
     ap.add_argument("--no-level3", action="store_true", help="skip the FT-DSYMM / FT-DTRMM measurement")
     ap.add_argument("--level3-only", action="store_true", help="measure only FT-DSYMM / FT-DTRMM")
     ap.add_argument("--linear-only", action="store_true", help="measure only the protected linear layer (config 4)")
@@ -405,7 +409,9 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
         call(True)
         e1.record()
         torch.cuda.synchronize(dev)
-        npairs = max(steps, min(256, int(40.0 / max(e0.elapsed_time(e1), 1e-3)) + 1))
+        # pairs covering at least 4.5 s, so that the clock sampler (every 200 ms) records
+        # twenty and more samples through the region
+        npairs = max(steps, min(8192, int(4500.0 / max(e0.elapsed_time(e1), 1e-3)) + 1))
         ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(npairs)]
         reps = [fb.new_report(dev) for _ in range(npairs)]
         for i in range(npairs):
@@ -501,6 +507,131 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
     }
 
 
+# ------------------------------------------------------------------ emulated FP64 (NEXT-3)
+def run_emulated(dev, n, steps, warmup, fp64_tflops, slices=14):
+    """FP64 GEMM formed from E4M3 integer slices on the tensor cores (ftblas_dgemm_emulated)
+    on config 2's workload: column-major n^3, alpha 1.5, beta 0.5, A, B, C uniform[-1,1].
+    Protected and unprotected calls alternated in one region (whole calls: the split passes,
+    the product kernel and the resolve pass), then a region with one seeded accumulator flip
+    per call (a group value's bit 0-31, detected exactly). Reports TFLOP/s (2 n^3 per call),
+    the overhead, the speedup over the native FP64 FT-DGEMM, the error against the binary64
+    product on sampled rows, and the product kernel's tensor-pipe roofline (its E4M3 work is
+    s (s+1) / 2 slice products of 2 n^3)."""
+    import torch
+
+    import paper_2104_00897_gb300 as fb
+    import synth as S
+
+    prev = fb.ftblas_set_emulation_slices(slices)
+    A, B, Cin = gen_inputs(n, SEED)
+    dA = torch.from_numpy(A).to(dev)
+    dB = torch.from_numpy(B).to(dev)
+    dC0 = torch.from_numpy(Cin).to(dev)
+    dC = dC0.clone()
+    st = torch.cuda.current_stream(dev).cuda_stream
+    flops = 2.0 * n ** 3
+
+    def call(protect, rep=None):
+        a = (fb.COL_MAJOR, fb.NO_TRANS, fb.NO_TRANS, n, n, n, 1.5, dA.data_ptr(), n, dB.data_ptr(), n, 0.5,
+             dC.data_ptr(), n, st)
+        if protect:
+            fb.check(fb.ftblas_dgemm_emulated(*a, rep.data_ptr() if rep is not None else None), "ftblas_dgemm_emulated")
+        else:
+            fb.check(fb.ftblas_dgemm_emulated_noabft(*a), "ftblas_dgemm_emulated_noabft")
+
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    sampler.__enter__()
+    fb.ftblas_set_injection(None)
+    for _ in range(warmup):
+        call(False)
+        call(True)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    call(False)
+    call(True)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    # pairs covering at least 4.5 s: twenty and more clock samples through the region
+    npairs = max(steps, 4, int(4500.0 / max(e0.elapsed_time(e1), 1e-3)) + 1)
+    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(npairs)]
+    reps = [fb.new_report(dev) for _ in range(npairs)]
+    fb.ftblas_kernel_timing_begin()
+    for i in range(npairs):
+        ev[i][0].record()
+        call(False)
+        ev[i][1].record()
+        call(True, reps[i])
+        ev[i][2].record()
+    torch.cuda.synchronize(dev)
+    _, kms, kn = fb.ftblas_kernel_timing_end()  # product kernels: unprotected and protected alternate
+    ms_na = sum(a.elapsed_time(b) for a, b, _ in ev) / npairs
+    ms_ft = sum(b.elapsed_time(c) for _, b, c in ev) / npairs
+    false_alarms = sum(int(fb.report_from_device(r).detected) for r in reps)
+    # protected product-kernel time alone, for the roofline
+    nreg = max(steps, 4)
+    fb.ftblas_kernel_timing_begin()
+    for i in range(nreg):
+        call(True)
+    torch.cuda.synchronize(dev)
+    _, kms_ft, kn_ft = fb.ftblas_kernel_timing_end()
+    # one seeded accumulator flip per call: bits 0-31 of a leading group value
+    fb.ftblas_set_injection(fb.make_injection(seed=SEED + 60, site=fb.SITE_ACCUM, mode=fb.MODE_BITFLIP, bit_lo=0,
+                                              bit_hi=31, every_n_launches=1, errors_per_launch=1))
+    irep = [fb.new_report(dev) for _ in range(nreg)]
+    e0.record()
+    for i in range(nreg):
+        call(True, irep[i])
+    e1.record()
+    torch.cuda.synchronize(dev)
+    fb.ftblas_set_injection(None)
+    ms_inj = e0.elapsed_time(e1) / nreg
+    sampler.__exit__(None, None, None)
+    ir = [fb.report_from_device(r) for r in irep]
+    # accuracy: one clean call from C_in, sampled rows against the binary64 library product
+    dC.copy_(dC0)
+    call(True)
+    torch.cuda.synchronize(dev)
+    rows = np.unique(S.randint(SEED, 9, 4, 0, n - 1))
+    got = dC.view(n, n).t()[torch.as_tensor(rows, device=dev)].cpu().numpy()
+    Am, Bm, Cm = (X.reshape(n, n, order="F") for X in (A, B, Cin))
+    ref = 1.5 * (Am[rows, :] @ Bm) + 0.5 * Cm[rows, :]
+    err = float(np.abs(got - ref).max() / (np.abs(A).max() * np.abs(B).max() * n))
+    fb.ftblas_set_emulation_slices(prev)
+    pk = peaks()
+    peak8 = 2.0 * pk["bf16"]
+    k_ft = kms_ft / kn_ft if kn_ft else None
+    pairs = slices * (slices + 1) // 2
+    roof = None
+    if k_ft:
+        tensor = pairs * flops / k_ft / 1e9
+        roof = {"bound": "tensor", "achieved": tensor, "peak": peak8, "unit": "TFLOP/s", "frac": tensor / peak8,
+                "peak_sustained": 2.0 * pk["bf16_sustained"], "frac_sustained": tensor / (2.0 * pk["bf16_sustained"]),
+                "traffic": None, "peak_source": pk["bf16_src"] + " x 2 (nominal FP8:BF16 dense ratio 4.5/2.25)",
+                "kernel": f"emu_gemm_kernel<FT> ({pairs} E4M3 slice products of 2 n^3 each per call)",
+                "kernel_ms": k_ft}
+    return {
+        "workload": f"ft_dgemm_emulated_{n}x{n}x{n}, column-major, alpha 1.5, beta 0.5, U[-1,1], {slices} slices",
+        "ft_tflops": flops / ms_ft / 1e9, "ft_tflops_injected": flops / ms_inj / 1e9,
+        "noabft_tflops": flops / ms_na / 1e9, "abft_overhead_pct": 100.0 * (ms_ft / ms_na - 1.0),
+        "product_kernel_ms": k_ft,
+        "speedup_over_native_fp64_ft": (flops / ms_ft / 1e9) / fp64_tflops if fp64_tflops else None,
+        "error_vs_fp64": {"normalized_max": err, "criterion": "max|C-C_ref|/(max|A| max|B| K) <= 1e-15",
+                          "bound": f"(s+3) 16^-s + 3u = {(slices + 3) * 16.0 ** -slices + 3 * 2.0 ** -53:.2e}",
+                          "rows_sampled": len(rows), "reference": "binary64 product of the same operands (library matmul)"},
+        "faults": {"injected": nreg, "detected": sum(int(r.detected) for r in ir),
+                   "corrected": sum(int(r.corrected) for r in ir), "checksum_only": sum(int(r.checksum_only) for r in ir),
+                   "uncorrectable": sum(int(r.uncorrectable) for r in ir), "false_alarms_clean": false_alarms,
+                   "note": "a flip that leaves C unchanged (a fraction bit of a small group value, rounded away) "
+                           "is detected and classified checksum-only"},
+        "roofline": roof,
+        "clocks": sampler.summary(),
+        "timed_calls": {"alternating_pairs": npairs, "product_kernel_region": nreg, "injected_region": nreg},
+        "method": "protected and unprotected whole calls alternated in one region of at least 4.5 s (per-call "
+                  "CUDA events); the product kernel timed in a region of protected calls",
+    }
+
+
 SWEEP_SHAPES = ((1024, 1024, 1024), (2048, 2048, 2048), (4096, 4096, 4096), (8192, 8192, 8192),
                 (16384, 16384, 16384), (8192, 8192, 256), (32768, 1024, 1024))
 
@@ -576,6 +707,55 @@ def run_sweep(dev, steps, warmup, shapes=SWEEP_SHAPES):
     return {"workload": "ft_dgemm FP64 (DFMA), column-major, alpha 1.5, beta 0.5, U[-1,1]; one accumulator flip "
                         "(bits 40-62) per 10 launches in the injected runs",
             "peak_tflops": peak, "steps": steps, "warmup": warmup, "rows": rows}
+
+
+def run_fp64_large(dev, n=16384):
+    """Config 2's largest square point in the default line: FP64 FT-DGEMM (DFMA) n^3,
+    column-major, alpha 1.5, beta 0.5, U[-1,1]; after one warm-up each, one protected call
+    with one fixed accumulator flip (bit 52, middle of the matrix), one clean protected call
+    and one unprotected call, timed by the product kernels' CUDA events."""
+    import torch
+
+    import paper_2104_00897_gb300 as fb
+    import synth as S
+
+    fb.ftblas_set_fp64_engine(fb.ENGINE_DFMA)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    seed = SEED + 7
+    dA = torch.from_numpy(S.uniform(seed, 0, n * n)).to(dev)
+    dB = torch.from_numpy(S.uniform(seed, 1, n * n)).to(dev)
+    dC = torch.from_numpy(S.uniform(seed, 2, n * n)).to(dev)
+    flops = 2.0 * n ** 3
+    rep = fb.new_report(dev)
+
+    def timed(protect, pts):
+        fb.ftblas_set_injection(fb.make_injection(fixed=pts) if pts else None)
+        a = (fb.COL_MAJOR, fb.NO_TRANS, fb.NO_TRANS, n, n, n, 1.5, dA.data_ptr(), n, dB.data_ptr(), n, 0.5,
+             dC.data_ptr(), n, st)
+        fb.ftblas_kernel_timing_begin()
+        fb.check(fb.ftblas_dgemm(*a, rep.data_ptr()) if protect else fb.ftblas_dgemm_noabft(*a))
+        torch.cuda.synchronize(dev)
+        _, kms, _ = fb.ftblas_kernel_timing_end()
+        fb.ftblas_set_injection(None)
+        return kms, (fb.report_from_device(rep) if protect else None)
+
+    timed(True, None)   # warm-up
+    timed(False, None)
+    pt = [dict(i=n // 2 + 17, j=n // 3 + 5, site=fb.SITE_ACCUM, mode=fb.MODE_BITFLIP, bit=52)]
+    ms_inj, r_inj = timed(True, pt)
+    ms_ft, r_ft = timed(True, None)
+    ms_na, _ = timed(False, None)
+    peak = peaks()["alu"]
+    del dA, dB, dC
+    torch.cuda.empty_cache()
+    return {"workload": f"ft_dgemm FP64 (DFMA) {n}x{n}x{n}, column-major, alpha 1.5, beta 0.5, U[-1,1]",
+            "ft_tflops_injected": flops / ms_inj / 1e9, "ft_tflops_clean": flops / ms_ft / 1e9,
+            "noabft_tflops": flops / ms_na / 1e9, "pct_of_fp64_peak_clean": 100.0 * flops / ms_ft / 1e9 / peak,
+            "abft_overhead_pct_clean": 100.0 * (ms_ft / ms_na - 1.0),
+            "abft_overhead_pct_injected": 100.0 * (ms_inj / ms_na - 1.0),
+            "injected": 1, "detected": int(r_inj.detected), "corrected": int(r_inj.corrected),
+            "located": [(int(r.i), int(r.j)) for r in r_inj.records()], "false_alarms_clean": int(r_ft.detected),
+            "method": "one timed call each (7 s per call), after one warm-up each"}
 
 
 def run_level3(dev, n, steps, warmup):
@@ -923,7 +1103,8 @@ def run_ours(args, rank, world, dist):
         # At N > 1 the line carries the scaled headline (and its end-to-end figure) only: the
         # single-GPU sections are reported by the N = 1 run, and running them on rank 0
         # alone would hold the other GPUs idle.
-        for flag in ("no_bf16", "no_fp8", "no_linear", "no_unfused", "no_level3", "no_online", "no_second_engine"):
+        for flag in ("no_bf16", "no_fp8", "no_linear", "no_unfused", "no_level3", "no_online", "no_second_engine",
+                     "no_emulated", "no_large", "no_soak_default"):
             setattr(args, flag, True)
     if args.sweep:
         if rank == 0:
@@ -944,6 +1125,10 @@ def run_ours(args, rank, world, dist):
     if args.soak > 0:
         if rank == 0:
             print(json.dumps({"soak": run_soak(dev, n, args.soak, rate_per_s=args.soak_rate)}), flush=True)
+        return 0
+    if args.emulated_only:
+        if rank == 0:
+            print(json.dumps({"fp64_emulated": run_emulated(dev, n, args.steps, args.warmup, None)}), flush=True)
         return 0
     if args.bf16_only or args.fp8_only:
         if rank == 0:
@@ -1134,12 +1319,21 @@ def run_ours(args, rank, world, dist):
     linear = None
     if not args.no_linear and rank == 0:
         linear = run_linear(dev, args.steps, args.warmup)
+    emulated = None
+    if not args.no_emulated and rank == 0:
+        emulated = run_emulated(dev, n, args.steps, args.warmup, fp64_ft)
     unfused = None
     if not args.no_unfused and rank == 0:
         unfused = run_unfused(dev, n, args.steps, args.warmup)
     level3 = None
     if not args.no_level3 and rank == 0:
         level3 = run_level3(dev, n, max(1, args.steps // 2), max(1, args.warmup // 2))
+    large = None
+    if not args.no_large and rank == 0 and n == 8192:
+        large = run_fp64_large(dev, 16384)
+    soak = None
+    if not args.no_soak_default and rank == 0:
+        soak = run_soak(dev, n, 60.0, rate_per_s=args.soak_rate)
 
     if rank != 0:
         return 0
@@ -1188,10 +1382,13 @@ def run_ours(args, rank, world, dist):
         "cpu_baseline": cpu,
         "bf16": bf16,
         "fp8_e4m3": fp8,
+        "fp64_emulated": emulated,
         "online_verification": online,
         "linear_bf16": linear,
         "unfused_fp64": unfused,
         "level3_fp64": level3,
+        "fp64_16384": large,
+        "soak": soak,
         "e2e": e2e,
         "gpu_launches": world * args.steps,  # one protected product kernel per step on every rank
         "clocks": clocks,
