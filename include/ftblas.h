@@ -11,6 +11,11 @@
  * (Section V.A) and corrected (Section VI.C). One verification interval is one output
  * tile over all of K in one call; ftblas_verification_tile() reports its shape.
  *
+ * Workspace: the calls that need workspace take it stream-ordered from a memory pool the
+ * library creates per device, and release it on the same stream; the pool keeps the memory
+ * it has reserved (up to the largest call's need) until the process exits, so that calls do
+ * not map and unmap device memory each time.
+ *
  * Storage follows BLAS/CBLAS: column-major (element (r, c) of X at X[r + c*ld], ld >=
  * max(1, rows)) or row-major (X[r*ld + c], ld >= max(1, cols)), selected per call.
  *
@@ -203,7 +208,7 @@ int ftblas_dtrmm(ftblas_layout_t layout, ftblas_side_t side, ftblas_uplo_t uplo,
 
 /* FT-DTRSM: op(A) X = alpha B (side LEFT, A M x M) or X op(A) = alpha B (side RIGHT, A N x N),
  * A triangular (`uplo`, `diag`), X overwriting B. Recursive blocked substitution on a
- * column-major copy (workspace from the stream-ordered allocator): the off-diagonal updates
+ * column-major copy (workspace from the library's workspace pool): the off-diagonal updates
  * run through ftblas_dgemm's protected kernel, and each 128-row diagonal block is solved by
  * a kernel that verifies every right-hand side by its checksum, e^T (T X) = (e^T T) X
  * against e^T R (Section II.A applied to T X = R), and solves a mismatching column again
@@ -228,7 +233,7 @@ int ftblas_dtrsm(ftblas_layout_t layout, ftblas_side_t side, ftblas_uplo_t uplo,
  * (within the row threshold of the fault-free value, not bit-exact: the library's
  * summation order is unknown). Accumulator-site injection points act on the output
  * element (the library's accumulator is out of reach). Workspace comes from the
- * stream-ordered allocator. Returns FTBLAS_STATUS_NOT_SUPPORTED when cuBLAS cannot be
+ * library's workspace pool. Returns FTBLAS_STATUS_NOT_SUPPORTED when cuBLAS cannot be
  * loaded or a dimension exceeds its 32-bit interface. */
 int ftblas_dgemm_unfused(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,
                          int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
@@ -253,10 +258,12 @@ int ftblas_dgemm_host(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_tran
  *   A, B, C, compute all FTBLAS_R_64F            -> the same path as ftblas_dgemm;
  *   A, B FTBLAS_R_16BF, C and compute FTBLAS_R_32F -> tcgen05 BF16 GEMM, C stored in FP32.
  * a_scale / b_scale (device pointers to one float each) scale FP8 operands and must be
- * NULL otherwise. The BF16 path needs both operands K-contiguous in the column-major
- * kernel frame (column-major: A transposed and B not; row-major: A not transposed and B
- * transposed), leading dimensions that are multiples of 8 elements and 16-byte aligned
- * base addresses; other combinations return FTBLAS_STATUS_NOT_SUPPORTED. Its threshold
+ * NULL otherwise. The tensor-core kernel reads both operands K-contiguous in the
+ * column-major kernel frame (column-major: A transposed and B not; row-major: A not
+ * transposed and B transposed), through tensor maps that need 16-byte aligned base
+ * addresses and leading dimensions. Every transpose combination and alignment is accepted:
+ * an operand stored the other way, or misaligned, is first copied K-major and aligned into
+ * workspace from the library's workspace pool (one read and one write of it). Its threshold
  * assumes the tensor core accumulates in binary32 with unit roundoff 2^-23 (measured on
  * GB300: truncating accumulation). Protected tiles hold 128 x 248 outputs: B^r = [B, Be]
  * (Section II.A) fills the 256-column MMA, the last 8 columns holding the pieces of B e
@@ -269,7 +276,7 @@ int ftblas_dgemm_host(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_tran
  * at most 64 mismatching tiles per call; further mismatching tiles of the same call are
  * reported as FT_KIND_UNCORRECTABLE (detected, C left as computed). Workspace (about
  * 16*K*ceil(N/248) + 8*K*ceil(M/128) + 4*M*ceil(K/256) bytes for BF16, 8*K*ceil(N/248) + ...
- * for FP8) is taken from the stream-ordered allocator and released on the same stream. */
+ * for FP8) is taken from the library's workspace pool and released on the same stream. */
 int ftblas_gemm_ex(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,
                    int64_t M, int64_t N, int64_t K, const void* alpha,
                    const void* A, ftblas_dtype_t Atype, int64_t lda,
@@ -295,7 +302,9 @@ int ftblas_gemm_ex_noabft(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_
  * that forbids allocation after initialisation, and a caller holding a lock under which
  * allocation could block. The protected BF16 GEMM (the argument list of ftblas_gemm_ex,
  * and only its BF16 combination: A, B FTBLAS_R_16BF, C and compute FTBLAS_R_32F; FP64 and
- * FP8 E4M3 return FTBLAS_STATUS_NOT_SUPPORTED) takes its encode scratch from one static
+ * FP8 E4M3 return FTBLAS_STATUS_NOT_SUPPORTED; both operands K-contiguous in the kernel
+ * frame with 16-byte aligned bases and leading dimensions, since this entry point makes no
+ * copies: other operands return FTBLAS_STATUS_NOT_SUPPORTED) takes its encode scratch from one static
  * device array of 16 MiB that every GPU loading this library holds until the process
  * exits; nothing else is allocated (no cudaMalloc, cudaFree, stream-ordered or library
  * allocation).
@@ -349,7 +358,7 @@ int ftblas_gemm_ex_noalloc(ftblas_layout_t layout, ftblas_trans_t transa, ftblas
  *     with g = the point's k_tile (0: the leading group); the output and checksum sites
  *     act on C(i,j) and on group 0's predicted row checksum (adding sign max(1,
  *     floor(2^rel_log2 |P|))); the stall site as for the tensor-core product kernel.
- * Workspace (about 2 s (M + N) K bytes) from the stream-ordered allocator, released on the
+ * Workspace (about 2 s (M + N) K bytes) from the library's workspace pool, released on the
  * same stream. Row-major calls compute C^T in the column-major frame, whose rows are the
  * caller's columns; the values are identical. */
 int ftblas_dgemm_emulated(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_trans_t transb,

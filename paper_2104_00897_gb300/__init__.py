@@ -414,6 +414,20 @@ def _kmajor_rows(x):
     return y, pitch
 
 
+def _row_major_operand(x):
+    """How a (rows x K) tensor x enters a row-major call: (NO_TRANS, x, ld) when its rows
+    of K are contiguous (copied first when the base or pitch is not 16-byte aligned), or
+    (TRANS, x, ld) when its columns are, x then being read as the transpose of a row-major
+    K x rows array (the library copies it K-major itself)."""
+    if x.stride(1) == 1 and (x.shape[0] <= 1 or x.stride(0) >= max(1, x.shape[1])):
+        y, ld = _kmajor_rows(x)
+        return NO_TRANS, y, ld
+    if x.stride(0) == 1 and (x.shape[1] <= 1 or x.stride(1) >= max(1, x.shape[0])):
+        return TRANS, x, max(1, x.stride(1) if x.shape[1] > 1 else x.shape[0])
+    y, ld = _kmajor_rows(x)
+    return NO_TRANS, y, ld
+
+
 def gemm(a, b, c=None, alpha=1.0, beta=0.0, trans_a=False, trans_b=False, report=None, protect=True,
          a_scale=None, b_scale=None, stream=None):
     """c = alpha * op(a) @ op(b) + beta * c on CUDA tensors, protected by ABFT.
@@ -421,9 +435,9 @@ def gemm(a, b, c=None, alpha=1.0, beta=0.0, trans_a=False, trans_b=False, report
     float64 operands run the FP64 kernel (c float64, see dgemm). bfloat16 or
     float8_e4m3fn operands run the tensor-core kernel with FP32 accumulation and an FP32
     c; a_scale / b_scale are 1-element float32 CUDA tensors (FP8 per-tensor scales) or
-    None. The tensor-core kernel reads K-contiguous operands: op(a) and op(b)^T are copied
-    to that form when they are not already in it. ``report``: a buffer from new_report()
-    (or None). Returns c.
+    None. Operands are passed through in either storage order (the library copies an
+    MN-major operand K-major for the tensor-core kernel). ``report``: a buffer from
+    new_report() (or None). Returns c.
     """
     import torch
     if a.dtype == torch.float64:
@@ -458,13 +472,18 @@ def gemm(a, b, c=None, alpha=1.0, beta=0.0, trans_a=False, trans_b=False, report
         if c.stride(0) == 1:  # column-major c: compute c^T = op(b)^T op(a)^T into its row-major view
             return gemm(b, a, c.t(), alpha, beta, not trans_b, not trans_a, report, protect, b_scale, a_scale, stream)
         raise ValueError("c must have a unit stride in one dimension")
-    a2, lda = _kmajor_rows(opa)
-    b2, ldb = _kmajor_rows(opb_t)
+    # Row-major call. An operand whose rows of K are contiguous is passed as it is (the
+    # tensor maps want a 16-byte aligned base and pitch; otherwise it is copied into that
+    # form); one stored the other way is passed transposed, and the library makes its own
+    # K-major copy.
+    ta_, a2, lda = _row_major_operand(opa)
+    tb_k, b2, ldb = _row_major_operand(opb_t)
+    tb_ = TRANS if tb_k == NO_TRANS else NO_TRANS   # op(B) = opb_t^T
     st = stream if stream is not None else torch.cuda.current_stream(a.device).cuda_stream
     dt = R_8F_E4M3 if fp8 else R_16BF
     sa = a_scale.data_ptr() if a_scale is not None else None
     sb = b_scale.data_ptr() if b_scale is not None else None
-    args = (ROW_MAJOR, NO_TRANS, TRANS, M, N, K, float(alpha), a2.data_ptr(), dt, lda, b2.data_ptr(), dt, ldb,
+    args = (ROW_MAJOR, ta_, tb_, M, N, K, float(alpha), a2.data_ptr(), dt, lda, b2.data_ptr(), dt, ldb,
             float(beta), c.data_ptr(), R_32F, max(1, c.stride(0)), R_32F, sa, sb, st)
     if protect:
         rc = ftblas_gemm_ex(*args, report.data_ptr() if report is not None else None)

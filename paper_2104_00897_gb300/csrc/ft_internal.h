@@ -87,6 +87,11 @@ struct UnfusedParams {
 // Returns 0 or an FTBLAS_STATUS_* code; on a CUDA failure *cuda_err holds the error.
 int unfused_dgemm(const UnfusedParams& p, cudaStream_t stream, cudaError_t* cuda_err);
 
+// Stream-ordered workspace (released with cudaFreeAsync on the same stream) from a memory
+// pool the library owns for the current device, which keeps what it has reserved between
+// calls instead of returning it to the driver at every synchronisation.
+cudaError_t ws_alloc(void** ptr, size_t bytes, cudaStream_t stream);
+
 // Product-kernel timing (ftblas_kernel_timing_begin / _end): event records on `stream`
 // immediately before and after a product kernel launch; no-ops unless timing is on.
 void kernel_timer_start(cudaStream_t stream);

@@ -87,6 +87,13 @@ cudaError_t launch_decode_e4m3(const uint8_t* codes, float* out, int64_t n, cuda
 cudaError_t launch_tc_gemm(const TcParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmChk,
                            bool ft, cudaStream_t st);
 
+// K-major copy of an MN-major operand: dst[r * pitch + k] = src[r + k * ld] for r < R,
+// k < K, elem_bytes 1 or 2 (asynchronous on st). pitch: tc_kmajor_pitch(K, elem_bytes), K
+// rounded up to 16 bytes.
+int64_t tc_kmajor_pitch(int64_t K, int elem_bytes);
+cudaError_t launch_kmajor_copy(const void* src, int64_t R, int64_t K, int64_t ld, int elem_bytes, void* dst,
+                               int64_t pitch, cudaStream_t st);
+
 // Device address of a fixed scratch area, looked up only when a call needs it; returns null
 // and sets *err on failure.
 using ScratchResolver = void* (*)(cudaError_t* err);

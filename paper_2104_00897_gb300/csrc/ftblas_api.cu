@@ -337,7 +337,7 @@ int dsymm_impl(int layout, int side, int uplo, int64_t M, int64_t N, double alph
                       stream, report, true);
   }
   double* S = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&S), (size_t)(dim * dim) * 8, st) != cudaSuccess)
+  if (ws_alloc(reinterpret_cast<void**>(&S), (size_t)(dim * dim) * 8, st) != cudaSuccess)
     return FTBLAS_STATUS_ALLOC_FAILED;
   int rc = record_cuda(launch_expand(A, lda, !col, dim, 0, uplo == FTBLAS_UPPER, false, false, S, st));
   if (rc == 0) {
@@ -380,7 +380,7 @@ int dtrmm_other_layout(bool col, int side, int uplo, int transa, int diag, int64
   // copies Bt (the operand) and Ct (the product) hold `rows` lines of `cols`, ld = cols.
   const int64_t dim = side == FTBLAS_LEFT ? M : N;
   double* T = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&T), (size_t)(dim * dim + 2 * rows * cols) * 8, st) != cudaSuccess)
+  if (ws_alloc(reinterpret_cast<void**>(&T), (size_t)(dim * dim + 2 * rows * cols) * 8, st) != cudaSuccess)
     return FTBLAS_STATUS_ALLOC_FAILED;
   double* Bt = T + dim * dim;
   double* Ct = Bt + rows * cols;
@@ -433,7 +433,7 @@ int dtrmm_impl(int layout, int side, int uplo, int transa, int diag, int64_t M, 
     return dtrmm_other_layout(col, side, uplo, transa, diag, M, N, alpha, A, lda, B, ldb, st, report, tri, rows,
                               cols);
   double *T = nullptr, *B0 = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&T), (size_t)(dim * dim + rows * cols) * 8, st) != cudaSuccess)
+  if (ws_alloc(reinterpret_cast<void**>(&T), (size_t)(dim * dim + rows * cols) * 8, st) != cudaSuccess)
     return FTBLAS_STATUS_ALLOC_FAILED;
   B0 = T + dim * dim;
   int rc = record_cuda(launch_expand(A, lda, !col, dim, 1, uplo == FTBLAS_UPPER, transa == FTBLAS_TRANS,
@@ -545,7 +545,7 @@ int dtrsm_impl(int layout, int side, int uplo, int transa, int diag, int64_t M, 
   const int nparts = (int)(2 * ((dim + kTrsmLeaf - 1) / kTrsmLeaf) + 1);
   double* T = nullptr;
   const size_t bytes = (size_t)(dim * dim + dim * nrhs) * 8 + (size_t)nparts * (sizeof(ft_report_t) + 8) + 256;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&T), bytes, st) != cudaSuccess) return FTBLAS_STATUS_ALLOC_FAILED;
+  if (ws_alloc(reinterpret_cast<void**>(&T), bytes, st) != cudaSuccess) return FTBLAS_STATUS_ALLOC_FAILED;
   double* W = T + dim * dim;
   char* tail = reinterpret_cast<char*>(W + dim * nrhs);
   tail += (256 - reinterpret_cast<uintptr_t>(tail) % 256) % 256;
@@ -646,8 +646,18 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
     return -pos[-v];
   }
   if (M > kMaxDim || N > kMaxDim || K > kMaxDim) return FTBLAS_STATUS_NOT_SUPPORTED;
-  const Frame f = map_frame(layout, ta, tb, M, N, A, lda, B, ldb);
-  if (need_ab && (!f.a_kmajor || !f.b_kmajor)) return FTBLAS_STATUS_NOT_SUPPORTED;
+  Frame f = map_frame(layout, ta, tb, M, N, A, lda, B, ldb);
+  const int eb = (Atype == FTBLAS_R_8F_E4M3) ? 1 : 2;
+  // K-major operands the tensor maps cannot address (base or pitch not 16-byte aligned) are
+  // copied too, into aligned rows
+  auto aligned = [&](const void* x, int64_t ld) {
+    return (reinterpret_cast<uintptr_t>(x) & 15u) == 0 && ((ld * eb) & 15) == 0;
+  };
+  const bool copy_a = need_ab && (!f.a_kmajor || !aligned(f.A, f.lda));
+  const bool copy_b = need_ab && (!f.b_kmajor || !aligned(f.B, f.ldb));
+  // such operands are copied into workspace below; the entry point without allocation has
+  // no room for copies
+  if (resolve != nullptr && (copy_a || copy_b)) return FTBLAS_STATUS_NOT_SUPPORTED;
   const size_t wsb = (ft && need_ab) ? tc_workspace_bytes((int32_t)f.M, (int32_t)f.N, (int32_t)K, kind) : 0;
   if (resolve != nullptr && wsb > ws_bytes) return FTBLAS_STATUS_WORKSPACE_LIMIT;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -672,6 +682,39 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   p.kind = kind;
   p.a_scale = fp8 ? (f.swap ? b_scale : a_scale) : nullptr;
   p.b_scale = fp8 ? (f.swap ? a_scale : b_scale) : nullptr;
+  // K-major, aligned copies of MN-major or misaligned operands (stream-ordered workspace,
+  // released at the end)
+  void* tws = nullptr;
+  if (copy_a || copy_b) {
+    const int64_t pitch = tc_kmajor_pitch(K, eb);
+    const size_t abytes = copy_a ? (size_t(f.M * pitch * eb) + 255) & ~size_t(255) : 0;
+    const size_t bbytes = copy_b ? size_t(f.N * pitch * eb) : 0;
+    if (ws_alloc(&tws, abytes + bbytes, st) != cudaSuccess) return FTBLAS_STATUS_ALLOC_FAILED;
+    uint8_t* base = static_cast<uint8_t*>(tws);
+    auto copy = [&](const void* src, int64_t rows, int64_t ld, bool kmajor, uint8_t* dst) {
+      if (kmajor)  // rows of K already contiguous: a pitched copy
+        return cudaMemcpy2DAsync(dst, size_t(pitch * eb), src, size_t(ld * eb), size_t(K * eb), size_t(rows),
+                                 cudaMemcpyDeviceToDevice, st);
+      return launch_kmajor_copy(src, rows, K, ld, eb, dst, pitch, st);
+    };
+    cudaError_t ce = cudaSuccess;
+    if (copy_a) {
+      ce = copy(f.A, f.M, f.lda, f.a_kmajor, base);
+      f.A = base; f.lda = pitch; f.a_kmajor = true;
+    }
+    if (ce == cudaSuccess && copy_b) {
+      ce = copy(f.B, f.N, f.ldb, f.b_kmajor, base + abytes);
+      f.B = base + abytes; f.ldb = pitch; f.b_kmajor = true;
+    }
+    if (ce != cudaSuccess) {
+      cudaFreeAsync(tws, st);
+      return record_cuda(ce);
+    }
+  }
+  auto release = [&](int rc) {
+    if (tws != nullptr) cudaFreeAsync(tws, st);
+    return rc;
+  };
   p.A = f.A; p.lda = f.lda; p.B = f.B; p.ldb = f.ldb;
   p.C = static_cast<float*>(C); p.ldc = ldc;
   p.report = ft ? report : nullptr;
@@ -688,21 +731,21 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   }
   // 2 s per bounded wait (a whole tile takes about 0.1 ms); 20 ms with a stall point planned
   p.wait_limit_ns = stall ? 20000000ull : 2000000000ull;
-  const int eb = fp8 ? 1 : 2;
   CUtensorMap tmA, tmB, tmC;
   std::memset(&tmA, 0, sizeof(tmA)); std::memset(&tmB, 0, sizeof(tmB)); std::memset(&tmC, 0, sizeof(tmC));
-  if (!make_map_sw128(&tmA, eb, f.A, K, f.M, f.lda, kTcBM)) return FTBLAS_STATUS_NOT_SUPPORTED;
-  if (!make_map_sw128(&tmB, eb, f.B, K, f.N, f.ldb, ft ? (uint32_t)bnp : kTcBN)) return FTBLAS_STATUS_NOT_SUPPORTED;
+  if (!make_map_sw128(&tmA, eb, f.A, K, f.M, f.lda, kTcBM)) return release(FTBLAS_STATUS_NOT_SUPPORTED);
+  if (!make_map_sw128(&tmB, eb, f.B, K, f.N, f.ldb, ft ? (uint32_t)bnp : kTcBN))
+    return release(FTBLAS_STATUS_NOT_SUPPORTED);
   g_last_used_tma = 1;
-  if (!ft) return record_cuda(launch_tc_gemm(p, &tmA, &tmB, &tmA, false, st));
+  if (!ft) return release(record_cuda(launch_tc_gemm(p, &tmA, &tmB, &tmA, false, st)));
   const bool own = resolve == nullptr;
   void* ws = nullptr;
   if (own) {
-    if (cudaMallocAsync(&ws, wsb, st) != cudaSuccess) return FTBLAS_STATUS_ALLOC_FAILED;
+    if (ws_alloc(&ws, wsb, st) != cudaSuccess) return release(FTBLAS_STATUS_ALLOC_FAILED);
   } else {
     cudaError_t ce = cudaSuccess;
     ws = resolve(&ce);
-    if (ws == nullptr) return record_cuda(ce != cudaSuccess ? ce : cudaErrorInvalidDevicePointer);
+    if (ws == nullptr) return release(record_cuda(ce != cudaSuccess ? ce : cudaErrorInvalidDevicePointer));
   }
   TcWorkspace w = tc_workspace_carve(ws, p.M, p.N, p.K, kind);
   p.rowAbsA = w.rowAbsA; p.maxAbsBe = w.maxAbsBe; p.sA = w.sA; p.absSA = w.absSA;
@@ -712,7 +755,7 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   if (rc == 0) rc = record_cuda(launch_tc_encode(p, w, st));  // writes every workspace entry the GEMM reads
   if (rc == 0) rc = record_cuda(launch_tc_gemm(p, &tmA, &tmB, &tmC, true, st));
   if (own) cudaFreeAsync(ws, st);
-  return rc;
+  return release(rc);
 }
 
 // ------------------------------------------------------------------ emulated FP64
@@ -772,7 +815,7 @@ int emu_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, double
   const int sms = current_sm_count();
   const int grid = (int)(tiles < sms ? tiles : sms);
   void* ws = nullptr;
-  if (cudaMallocAsync(&ws, emu_workspace_bytes(p, grid), st) != cudaSuccess) return FTBLAS_STATUS_ALLOC_FAILED;
+  if (ws_alloc(&ws, emu_workspace_bytes(p, grid), st) != cudaSuccess) return FTBLAS_STATUS_ALLOC_FAILED;
   uint8_t* chk = nullptr;
   emu_workspace_carve(p, ws, grid, &chk);
   CUtensorMap tmA, tmB, tmC;
@@ -852,6 +895,40 @@ int g_ws_device = -1;
 }  // namespace
 
 namespace ftk {
+
+cudaError_t ws_alloc(void** ptr, size_t bytes, cudaStream_t st) {
+  constexpr int kMaxPoolDevices = 64;
+  static std::mutex mu;
+  static cudaMemPool_t pools[kMaxPoolDevices] = {};
+  static bool tried[kMaxPoolDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxPoolDevices) {
+    (void)cudaGetLastError();
+    return cudaMallocAsync(ptr, bytes, st);
+  }
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!tried[dev]) {
+      tried[dev] = true;
+      cudaMemPoolProps props;
+      std::memset(&props, 0, sizeof(props));
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      if (cudaMemPoolCreate(&pools[dev], &props) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        (void)cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+      } else {
+        pools[dev] = nullptr;
+        (void)cudaGetLastError();
+      }
+    }
+    pool = pools[dev];
+  }
+  if (pool == nullptr) return cudaMallocAsync(ptr, bytes, st);
+  return cudaMallocFromPoolAsync(ptr, bytes, pool, st);
+}
 
 void kernel_timer_start(cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_timer_mu);

@@ -314,7 +314,7 @@ int unfused_dgemm(const UnfusedParams& p, cudaStream_t st, cudaError_t* cuda_err
                      up256(8 * (size_t)(M * nNb)) + up256(8 * (size_t)(nMb * N));
   const size_t total = szA + szB + szC * (beta_nz ? 2 : 1) + szX;
   char* ws = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), total, st);
+  cudaError_t e = ws_alloc(reinterpret_cast<void**>(&ws), total, st);
   if (e != cudaSuccess) return FTBLAS_STATUS_ALLOC_FAILED;
   char* c = ws;
   auto take = [&](size_t bytes) { double* q = reinterpret_cast<double*>(c); c += up256(bytes); return q; };

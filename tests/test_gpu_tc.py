@@ -185,18 +185,6 @@ def test_bf16_detection_threshold_sweep_agrees_with_oracle():
     assert first is not None and first <= 8
 
 
-def test_bf16_non_k_contiguous_is_not_supported():
-    P = Bf16Problem(128, 256, 64, O.COL_MAJOR)
-    dA = torch.zeros(128 * 64, dtype=torch.int16, device="cuda")
-    dB = torch.zeros(256 * 64, dtype=torch.int16, device="cuda")
-    dC = torch.zeros(128 * 256, dtype=torch.float32, device="cuda")
-    rc = fb.ftblas_gemm_ex(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, 128, 256, 64, 1.0, dA.data_ptr(), fb.R_16BF, 128,
-                           dB.data_ptr(), fb.R_16BF, 64, 0.0, dC.data_ptr(), fb.R_32F, 128, fb.R_32F, None, None,
-                           None, None)
-    assert rc == 2  # FTBLAS_STATUS_NOT_SUPPORTED
-    assert P.M == 128
-
-
 def test_bf16_full_size_8192_sampled_rows():
     """8192^3 BF16 with an injected output error: sampled rows within the bound, the faulted
     tile's detection equal to the oracle's."""

@@ -126,6 +126,21 @@ def test_noalloc_detects_and_corrects_like_the_allocating_entry_point(layout):
     assert abs(got_l[i, j] - Cl[i, j]) <= r.tau_row + 2.0 ** -22 * abs(Cl[i, j])
 
 
+def test_noalloc_rejects_mn_major_operands():
+    """The allocating entry point copies an MN-major operand K-major in workspace; this one
+    makes no copies, so such a call is refused before any device work."""
+    M, N, K = 128, 256, 64
+    dA = torch.zeros(M * K, dtype=torch.int16, device="cuda")
+    dB = torch.zeros(N * K, dtype=torch.int16, device="cuda")
+    dC = torch.full((M * N,), 7.0, dtype=torch.float32, device="cuda")
+    rc = fb.ftblas_gemm_ex_noalloc(O.COL_MAJOR, O.NO_TRANS, O.NO_TRANS, M, N, K, 1.0, dA.data_ptr(), fb.R_16BF, M,
+                                   dB.data_ptr(), fb.R_16BF, K, 0.0, dC.data_ptr(), fb.R_32F, M, fb.R_32F, None, None,
+                                   None, None)
+    assert rc == 2  # FTBLAS_STATUS_NOT_SUPPORTED
+    torch.cuda.synchronize()
+    assert bool((dC == 7.0).all())
+
+
 def test_noalloc_rejects_problems_beyond_its_scratch():
     # M = N = 128, K = 2^20: the encode scratch (about 40 MiB) exceeds the 16 MiB array.
     M, N, K = 128, 256, 1 << 20
