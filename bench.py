@@ -78,6 +78,8 @@ def parse_args():
     ap.add_argument("--no-linear", action="store_true", help="skip the protected linear layer (config 4)")
     ap.add_argument("--fp8-only", action="store_true",
                     help="measure only the FP8 tensor-core form (for profiling); prints its own JSON line")
+    ap.add_argument("--tc-cta-group", type=int, choices=[1, 2], default=None,
+                    help="tensor-core product kernel: 1 CTA per tile or a CTA pair (default: the library's)")
     return ap.parse_args()
 
 
@@ -477,8 +479,9 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
                 "peak_sustained": peak_sus, "frac_sustained": flops / k_ft / 1e9 / peak_sus,
                 "traffic": profile_traffic(prof, TC_KERNEL_SOURCES),
                 "peak_source": pk["bf16_src"] + (" x 2 (nominal FP8:BF16 dense ratio 4.5/2.25)" if fp8 else ""),
-                "kernel": f"tc_gemm_kernel<FT, {kind.upper()}> (protected product kernel; encode and resolve "
-                          "kernels excluded)", "kernel_ms": k_ft,
+                "kernel": f"tc_gemm_kernel<FT, {kind.upper()}> (protected product kernel, "
+                          + ("CTA pairs, cta_group::2" if fb.tc_cta_group(True) == 2 else "one CTA per tile")
+                          + "; encode and resolve kernels excluded)", "kernel_ms": k_ft,
                 "noabft_kernel_frac": (flops / k_na / 1e9 / peak) if k_na else None}
     values = ("N(0,1) quantised per tensor to E4M3 (scale = amax/448)" if fp8
               else "N(0,1), A rows scaled by 2^u (u in [-8, 8])")
@@ -1099,6 +1102,8 @@ def run_ours(args, rank, world, dist):
     dev = torch.device("cuda", local)
     fb.load()
     n = args.size
+    if args.tc_cta_group is not None:
+        fb.ftblas_set_tc_cta_group(args.tc_cta_group)
     if world > 1:
         # At N > 1 the line carries the scaled headline (and its end-to-end figure) only: the
         # single-GPU sections are reported by the N = 1 run, and running them on rank 0

@@ -104,6 +104,7 @@ SIGNATURES = {
     "ftblas_verification_tile": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int64,
                                            C.c_void_p, C.c_void_p, C.c_void_p]),
     "ftblas_set_fp64_engine": (C.c_int, [C.c_int]),
+    "ftblas_set_tc_cta_group": (C.c_int, [C.c_int]),
     "ftblas_set_fp64_tile": (C.c_int, [C.c_int]),
     "ftblas_set_verification_interval": (C.c_int64, [C.c_int64]),
     "ftblas_status_string": (C.c_char_p, [C.c_int]),
@@ -246,6 +247,17 @@ def ftblas_set_verification_interval(k_interval):
 
 def ftblas_set_fp64_engine(engine):
     return _call("ftblas_set_fp64_engine", engine)
+
+
+def ftblas_set_tc_cta_group(cta_group):
+    return _call("ftblas_set_tc_cta_group", cta_group)
+
+
+def tc_cta_group(protected=True):
+    """The tensor-core kernel form a call takes (1: one CTA per tile, 2: CTA pairs)."""
+    cur = ftblas_set_tc_cta_group(0)
+    ftblas_set_tc_cta_group(cur)
+    return cur if cur != 0 else (1 if protected else 2)
 
 
 def ftblas_set_fp64_tile(edge):

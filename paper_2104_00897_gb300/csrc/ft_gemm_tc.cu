@@ -28,6 +28,12 @@
 // in binary32) to locate the error. When the columns cannot locate it (rows of very
 // different scale), it recomputes the mismatching row and compares element by element. The
 // located element is corrected from the row checksum.
+//
+// Two forms of the product kernel share this structure: tc_gemm_kernel, one CTA per 128-row
+// tile as above, and tc_gemm_pair_kernel, a CTA pair (cta_group::2) per 256-row unit with
+// each CTA staging its own 128 rows of A and half of B^r in a 6-stage ring, so that a CTA's
+// shared-memory traffic per MMA carries half the B operand. Both verify, hand over and
+// correct per 128 x BN tile. ftblas_set_tc_cta_group selects the form.
 #include <climits>
 #include <cstring>
 
@@ -44,9 +50,8 @@ namespace ftk {
 namespace {
 
 constexpr int BM = kTcBM;            // 128 tile rows (TMEM lanes)
-constexpr int BNM = 256;             // MMA N = TMEM columns = B stage rows
+constexpr int BNM = 256;             // MMA N = TMEM columns of one accumulator buffer
 constexpr int BKB = 128;             // k-tile depth in bytes (64 BF16 or 128 E4M3)
-constexpr int STAGES = 4;
 constexpr int NTHREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;   // two accumulator buffers of 256 columns
 
@@ -56,13 +61,23 @@ struct TcGeom {
   static constexpr int CHK = FT ? tc_chk_rows(KIND) : 0;  // checksum rows after them in a B stage
 };
 
+// Staging of one CTA. CG = 1: a CTA per 128-row tile, B stages of 256 rows, 4 stages.
+// CG = 2: a CTA pair per 256-row unit (cta_group::2); each CTA stages its own 128 rows of A
+// and half of B^r (128 rows), 6 stages in the same shared memory.
+template <int CG>
+struct TcStage {
+  static constexpr int kStages = CG == 2 ? 6 : 4;
+  static constexpr int kBRows = BNM / CG;
+};
+
+template <int CG>
 struct __align__(1024) TcSmem {
-  uint8_t a[STAGES][BM * BKB];
-  uint8_t b[STAGES][BNM * BKB];
-  uint64_t full[STAGES];
-  uint64_t empty[STAGES];
+  uint8_t a[TcStage<CG>::kStages][BM * BKB];
+  uint8_t b[TcStage<CG>::kStages][TcStage<CG>::kBRows * BKB];
+  uint64_t full[TcStage<CG>::kStages];
+  uint64_t empty[TcStage<CG>::kStages];
   uint64_t tfull[2];             // accumulator buffer b holds a finished tile
-  uint64_t tempty[2];            // accumulator buffer b has been read by the 4 epilogue warps
+  uint64_t tempty[2];            // accumulator buffer b has been read by the epilogue warps (of both CTAs)
   uint32_t tmem_base;
   int timeout;
   int nflag_rows, first_row, pend_slot;
@@ -71,6 +86,39 @@ struct __align__(1024) TcSmem {
   float cin_col[4][BNM];         // per-warp partial column sums of C_in (beta != 0)
   float cin_col_abs[4][BNM];
 };
+
+// MMA shape of a CTA-pair unit whose column block holds nJ data columns. D columns [0, n/2)
+// come from the even CTA's B stage rows [0, n/2), D columns [n/2, n) from the odd CTA's.
+//   protected, nJ > 120:  n = 256; the even CTA stages data columns 0..127, the odd one
+//                         columns 128..247 in rows 0..119 and the checksum rows in 120..127
+//                         (D columns 248..255);
+//   protected, nJ <= 120 (a ragged last column block): n = 2h, h = nJ rounded up to 8; the
+//                         even CTA stages the data columns, the odd one only the checksum rows,
+//                         in rows 0..7 (D columns h..h+7; D columns h+8..2h are not used);
+//   unprotected:          n = nJ rounded up to 16 (256 for a full block); the odd CTA stages
+//                         data columns n/2.. .
+struct PairShape {
+  int n;        // MMA N
+  int chk_col;  // first D column of the checksum pieces (protected)
+  int b1_row;   // first data column staged by the odd CTA
+  bool b1_data; // the odd CTA stages data columns
+};
+template <bool FT>
+__device__ __forceinline__ PairShape pair_shape(int nJ) {
+  PairShape g;
+  if (FT) {
+    if (nJ <= 120) {
+      const int h = (nJ + 7) / 8 * 8;
+      g.n = 2 * h; g.chk_col = h; g.b1_row = 0; g.b1_data = false;
+    } else {
+      g.n = BNM; g.chk_col = BNM - 8; g.b1_row = BNM / 2; g.b1_data = true;
+    }
+  } else {
+    g.n = nJ >= BNM ? BNM : (nJ + 15) / 16 * 16;
+    g.chk_col = 0; g.b1_row = g.n / 2; g.b1_data = true;
+  }
+  return g;
+}
 
 // alpha times the per-tensor scales of FP8 operands (device values; absent scales are 1)
 __device__ __forceinline__ float alpha_eff(const TcParams& p) {
@@ -180,35 +228,37 @@ __device__ void count_kind(const TcParams& p, int kind) {
   atomicAdd(ctr, 1ull);
 }
 
-// Bytes beyond the stage's that the staging barrier of k-tile kt of tile (mt, nt) expects: 16
-// when a stall point (test launches only) names that tile and k-tile (0: the middle one), so
-// that the barrier never completes and the waits on it give up; else 0.
-__device__ __forceinline__ uint32_t stall_bytes(const TcParams& p, int mt, int nt, int kt, int nk, int bn) {
+// Bytes beyond the stage's that the staging barrier of k-tile kt of unit (mu, nt) expects
+// (a unit: `rows` rows, one tile or the two tiles of a CTA pair): 16 when a stall point (test
+// launches only) names a tile of that unit and k-tile (0: the middle one), so that the barrier
+// never completes and the waits on it give up; else 0.
+__device__ __forceinline__ uint32_t stall_bytes(const TcParams& p, int mu, int rows, int nt, int kt, int nk, int bn) {
   for (int e = 0; e < p.inj.n; ++e) {
     const InjectPoint& ip = p.inj.p[e];
-    if (ip.site == kSiteStall && kt == (ip.kt > 0 ? ip.kt : nk / 2) && ip.i / BM == mt && ip.j / bn == nt) return 16u;
+    if (ip.site == kSiteStall && kt == (ip.kt > 0 ? ip.kt : nk / 2) && ip.i / rows == mu && ip.j / bn == nt)
+      return 16u;
   }
   return 0u;
 }
 
-// Persistent-tile order: groups of kGroupM row tiles sweep the column tiles, so the CTAs
-// resident at one time share A row panels and B column panels in L2. The last column
-// block comes after all the others: when N is not a multiple of the tile width its tiles
-// are narrower and cheaper (narrow MMAs), and placed last they fill the final round of the
-// persistent CTAs instead of adding one.
-constexpr int kGroupM = 16;
-__device__ __forceinline__ void tile_coords(int t, int nMb, int nNb, int& mt, int& nt) {
+// Persistent order of the units (row unit mu, column block nt): groups of kGroupRows rows
+// sweep the column blocks, so the CTAs resident at one time share A row panels and B column
+// panels in L2. The last column block comes after all the others: when N is not a multiple
+// of the tile width its units are narrower and cheaper (narrow MMAs), and placed last they
+// fill the final round of the persistent CTAs instead of adding one.
+constexpr int kGroupRows = 2048;
+__device__ __forceinline__ void tile_coords(int t, int nUb, int nNb, int group_units, int& mu, int& nt) {
   const int ncols = nNb - 1;  // column blocks before the last
-  if (t >= nMb * ncols) {
-    mt = t - nMb * ncols;
+  if (t >= nUb * ncols) {
+    mu = t - nUb * ncols;
     nt = ncols;
     return;
   }
-  const int group = t / (kGroupM * ncols);
-  const int first_m = group * kGroupM;
-  const int gsize = min(kGroupM, nMb - first_m);
-  const int in_group = t - group * kGroupM * ncols;
-  mt = first_m + in_group % gsize;
+  const int group = t / (group_units * ncols);
+  const int first_m = group * group_units;
+  const int gsize = min(group_units, nUb - first_m);
+  const int in_group = t - group * group_units * ncols;
+  mu = first_m + in_group % gsize;
   nt = in_group / gsize;
 }
 
@@ -221,7 +271,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                    const __grid_constant__ CUtensorMap tmChk, const __grid_constant__ TcParams p) {
   constexpr int BN = TcGeom<FT, KIND>::BN, CHK = TcGeom<FT, KIND>::CHK;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  TcSmem& sm = *reinterpret_cast<TcSmem*>(smem_raw);
+  constexpr int STAGES = TcStage<1>::kStages;
+  TcSmem<1>& sm = *reinterpret_cast<TcSmem<1>*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   using E = Elem<KIND>;
   const int bk_elems = BKB / E::kBytes;
@@ -255,11 +306,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         int mt, nt;
-        tile_coords(tile, nMb, nNb, mt, nt);
+        tile_coords(tile, nMb, nNb, kGroupRows / BM, mt, nt);
         for (int kt = 0; kt < nk; ++kt, ++it) {
           const uint32_t s = it % STAGES, u = it / STAGES;
           if (u > 0 && !mbar_wait_bounded(&sm.empty[s], (u - 1) & 1, p.wait_limit_ns)) { sm.timeout = 1; ok = false; break; }
-          mbar_arrive_expect_tx(&sm.full[s], bytes + stall_bytes(p, mt, nt, kt, nk, BN));
+          mbar_arrive_expect_tx(&sm.full[s], bytes + stall_bytes(p, mt, BM, nt, kt, nk, BN));
           const int k0 = kt * bk_elems;
           tma_load_2d(sm.a[s], &tmA, &sm.full[s], k0, mt * BM);
           tma_load_2d(sm.b[s], &tmB, &sm.full[s], k0, nt * BN);
@@ -287,7 +338,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
         int mt, nt;
-        tile_coords(tile, nMb, nNb, mt, nt);
+        tile_coords(tile, nMb, nNb, kGroupRows / BM, mt, nt);
         const bool narrow = narrow_last && nt == nNb - 1;
         const uint32_t b = lt & 1, ub = lt >> 1;
         if (ub > 0 && !mbar_wait_bounded(&sm.tempty[b], (ub - 1) & 1, p.wait_limit_ns)) { sm.timeout = 1; break; }
@@ -330,7 +381,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t lt = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
       int mt, nt;
-      tile_coords(tile, nMb, nNb, mt, nt);
+      tile_coords(tile, nMb, nNb, kGroupRows / BM, mt, nt);
       const int m0 = mt * BM, n0 = nt * BN;
       const int nI = min(BM, p.M - m0), nJ = min(BN, p.N - n0);
       const int64_t gi = m0 + row;
@@ -502,6 +553,313 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncwarp();  // tcgen05.dealloc is warp-collective: reconverge after the divergent MMA issue
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// CTA-pair kernel (cta_group::2): a thread-block cluster of two CTAs on one TPC computes each
+// 256 x 256 product. Each CTA stages its own 128 rows of A and half of B^r (128 rows: the even
+// CTA data columns 0..127, the odd CTA the rest and the checksum rows, as pair_shape gives),
+// so a CTA's shared-memory traffic per MMA is half the B operand of the one-CTA kernel. Both
+// CTAs' TMA loads complete on the even CTA's staging barrier; the even CTA's MMA warp issues
+// M = 256 MMAs over both CTAs' stages and its commits arrive on the barriers of both. Each
+// CTA's epilogue verifies and stores its own 128-row tile, so the verification interval, the
+// pending list and the resolve pass are those of the one-CTA kernel. The pair loops over units
+// (256-row block, column block) in the order of tile_coords.
+template <bool FT, int KIND>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                        const __grid_constant__ CUtensorMap tmB2, const __grid_constant__ CUtensorMap tmChk,
+                        const __grid_constant__ TcParams p) {
+  constexpr int BN = TcGeom<FT, KIND>::BN, CHK = TcGeom<FT, KIND>::CHK;
+  constexpr int STAGES = TcStage<2>::kStages, BROWS = TcStage<2>::kBRows;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  TcSmem<2>& sm = *reinterpret_cast<TcSmem<2>*>(smem_raw);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  using E = Elem<KIND>;
+  const int bk_elems = BKB / E::kBytes;
+  const int nk = (p.K + bk_elems - 1) / bk_elems;
+  const int nMb = (p.M + BM - 1) / BM, nNb = (p.N + BN - 1) / BN;
+  const int nUb = (nMb + 1) / 2;  // 256-row blocks
+  const int nunits = nUb * nNb;
+  const int rank = static_cast<int>(cluster_ctarank());
+  const int unit0 = static_cast<int>(blockIdx.x) / 2, ustep = static_cast<int>(gridDim.x) / 2;
+
+  if (t == 0) {
+    for (int s = 0; s < STAGES; ++s) { mbar_init(&sm.full[s], 1); mbar_init(&sm.empty[s], 1); }
+    // tempty: the four epilogue warps of each CTA (the odd CTA's arrive remotely)
+    for (int b = 0; b < 2; ++b) { mbar_init(&sm.tfull[b], 1); mbar_init(&sm.tempty[b], 8); }
+    sm.timeout = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    __syncwarp();
+    tmem_alloc_pair(&sm.tmem_base, TMEM_COLS);
+  }
+  tc_fence_before();
+  cluster_sync();  // the peer's barriers are initialised before any TMA or commit signals them
+  tc_fence_after();
+  const uint32_t tmem = sm.tmem_base;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      tma_prefetch_desc(&tmA);
+      tma_prefetch_desc(&tmB);
+      if (FT) { tma_prefetch_desc(&tmB2); tma_prefetch_desc(&tmChk); }
+      uint32_t it = 0;
+      bool ok = true;
+      for (int unit = unit0; unit < nunits && ok; unit += ustep) {
+        int mu, nt;
+        tile_coords(unit, nUb, nNb, kGroupRows / (2 * BM), mu, nt);
+        const int mt = 2 * mu + rank;
+        const int n0 = nt * BN;
+        const PairShape g = pair_shape<FT>(min(BN, p.N - n0));
+        // bytes of both CTAs' loads, expected on the even CTA's barrier
+        const uint32_t bytes = (2 * BM + BROWS + (FT ? (g.b1_data ? BROWS : CHK) : BROWS)) * BKB;
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const uint32_t s = it % STAGES, u = it / STAGES;
+          if (u > 0 && !mbar_wait_bounded(&sm.empty[s], (u - 1) & 1, p.wait_limit_ns)) { sm.timeout = 1; ok = false; break; }
+          const int k0 = kt * bk_elems;
+          const uint32_t fbar = mapa_shared(smem_addr(&sm.full[s]), 0);
+          if (rank == 0) mbar_arrive_expect_tx(&sm.full[s], bytes + stall_bytes(p, mu, 2 * BM, nt, kt, nk, BN));
+          // rows beyond M (an odd CTA past the last row tile) read the fill value, zero
+          tma_load_2d_pair(sm.a[s], &tmA, fbar, k0, mt * BM);
+          if (rank == 0) {
+            tma_load_2d_pair(sm.b[s], &tmB, fbar, k0, n0);
+          } else {
+            if (g.b1_data) tma_load_2d_pair(sm.b[s], FT ? &tmB2 : &tmB, fbar, k0, n0 + g.b1_row);
+            if (FT) tma_load_2d_pair(sm.b[s] + (g.b1_data ? BROWS - CHK : 0) * BKB, &tmChk, fbar, k0, nt * CHK);
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issue (even CTA)
+    if (lane == 0 && rank == 0) {
+      // kind::f16 with BF16 operands (format 1), or kind::f8f6f4 with E4M3 operands (format 0)
+      constexpr uint32_t fmt = KIND == 0 ? 1u : 0u;
+      uint32_t it = 0, lt = 0;
+      bool ok = true;
+      for (int unit = unit0; unit < nunits && ok; unit += ustep, ++lt) {
+        int mu, nt;
+        tile_coords(unit, nUb, nNb, kGroupRows / (2 * BM), mu, nt);
+        const uint32_t idesc = umma_idesc(fmt, fmt, 2 * BM, pair_shape<FT>(min(BN, p.N - nt * BN)).n);
+        const uint32_t b = lt & 1, ub = lt >> 1;
+        if (ub > 0 && !mbar_wait_bounded(&sm.tempty[b], (ub - 1) & 1, p.wait_limit_ns)) { sm.timeout = 1; break; }
+        tc_fence_after();
+        const uint32_t dcol = tmem + b * BNM;
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const uint32_t s = it % STAGES, u = it / STAGES;
+          if (!mbar_wait_bounded(&sm.full[s], u & 1, p.wait_limit_ns)) { sm.timeout = 1; ok = false; break; }
+          tc_fence_after();
+          const uint32_t a0 = smem_addr(sm.a[s]), b0 = smem_addr(sm.b[s]);
+#pragma unroll
+          for (int kk = 0; kk < BKB / 32; ++kk) {  // one MMA per 32 bytes of K
+            const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
+            const uint64_t ad = umma_desc_sw128(a0 + kk * 32), bd = umma_desc_sw128(b0 + kk * 32);
+            if (KIND == 0) umma_bf16_pair(dcol, ad, bd, idesc, accum);
+            else umma_f8_pair(dcol, ad, bd, idesc, accum);
+          }
+          umma_commit_pair(&sm.empty[s]);
+        }
+        // a wait gave up: the accumulator is incomplete, so the unit is never handed to the
+        // epilogues (whose own waits then give up and leave the tiles unstored)
+        if (!ok) break;
+        umma_commit_pair(&sm.tfull[b]);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue (warps 2..5)
+    const int q = warp & 3;                 // TMEM lane quarter of this warp
+    const int row = q * 32 + lane;          // tile row = TMEM lane
+    const int ew = warp - 2;                // epilogue warp index 0..3
+    const int et = t - 64;                  // epilogue thread index 0..127
+    const bool beta_nz = p.beta != 0.0f;
+    const float alpha = alpha_eff(p);
+    uint32_t lt = 0;
+    for (int unit = unit0; unit < nunits; unit += ustep, ++lt) {
+      int mu, nt;
+      tile_coords(unit, nUb, nNb, kGroupRows / (2 * BM), mu, nt);
+      const int mt = 2 * mu + rank;
+      const int m0 = mt * BM, n0 = nt * BN;
+      const int nI = min(BM, p.M - m0), nJ = min(BN, p.N - n0);  // nI <= 0: an odd CTA past the last row tile
+      const int chk_col = pair_shape<FT>(nJ).chk_col;  // first checksum column in TMEM
+      const int64_t gi = m0 + row;
+      const bool row_ok = row < nI;
+      const uint32_t b = lt & 1, ub = lt >> 1;
+      // tcgen05.ld is warp-collective (.sync.aligned): every TMEM load below is executed by
+      // all 32 lanes of the warp, whatever their row; `got` is made warp-uniform for that.
+      const bool got = __all_sync(0xffffffffu, mbar_wait_bounded(&sm.tfull[b], ub & 1, p.wait_limit_ns));
+      if (!got) sm.timeout = 1;
+      tc_fence_after();
+      const uint32_t trow = tmem + b * BNM + (static_cast<uint32_t>(q * 32) << 16);
+      float rs = 0.f, rc = 0.f, rabs = 0.f;   // compensated sum of C over the row, upward |C| sum
+      float cs = 0.f, cc = 0.f, cabs = 0.f;   // same for C_in
+      uint32_t wp[16];  // checksum columns: the pieces' products
+#pragma unroll
+      for (int q2 = 0; q2 < 16; ++q2) wp[q2] = 0u;
+      // Injection points in this tile (test launches only): the per-element injection code
+      // is kept out of the hot loop so the epilogue stays small in the instruction cache,
+      // which it shares with the producer and MMA warps.
+      int inj_c = INT_MAX;  // next tile column of this row holding an injection point
+      if (FT && p.inj.n > 0) inj_c = next_inj_col(p, gi, n0, nJ, -1);
+      if (got) {
+        const int nch = (nJ + 7) / 8;  // chunks of 8 columns holding data (warp-uniform)
+#pragma unroll 1
+        for (int ch = 0; ch < nch; ++ch) {
+          uint32_t v[8];
+          __syncwarp();  // reconverge after the previous chunk's per-lane branches
+          tmem_ld8(trow + ch * 8, v);
+          tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int col = ch * 8 + j;
+            const int64_t gj = n0 + col;
+            const bool ok = row_ok && col < nJ;
+            float acc = __uint_as_float(v[j]);
+            float cin = 0.f;
+            if (beta_nz && ok) cin = p.C[gi + gj * p.ldc];
+            float out;
+            if (FT && col == inj_c) {
+              out = inject_element(p, alpha, gi, gj, acc, cin, beta_nz);
+              inj_c = next_inj_col(p, gi, n0, nJ, col);
+            } else {
+              out = beta_nz ? fmaf(alpha, acc, p.beta * cin) : alpha * acc;
+            }
+            if (ok) p.C[gi + gj * p.ldc] = out;
+            if (FT) {
+              const float o = ok ? out : 0.f;
+              neumaier(rs, rc, o);
+              rabs = __fadd_ru(rabs, fabsf(o));
+              if (beta_nz) {
+                neumaier(cs, cc, cin);
+                cabs = __fadd_ru(cabs, fabsf(cin));
+                // column sums of C_in over this warp's 32 rows, for the lazy column side
+                const float csum = warp_sum_plain(ok ? cin : 0.f);
+                const float cabsum = warp_sum_up(fabsf(ok ? cin : 0.f));
+                if (lane == 0 && col < BNM) { sm.cin_col[ew][col] = csum; sm.cin_col_abs[ew][col] = cabsum; }
+              }
+            }
+          }
+        }
+        if (FT) {  // C^r pieces from the checksum columns of B^r
+#pragma unroll
+          for (int h = 0; h < (E::kPieces + 7) / 8; ++h) {
+            uint32_t v8[8];
+            __syncwarp();
+            tmem_ld8(trow + chk_col + 8 * h, v8);
+            tmem_ld_wait();
+#pragma unroll
+            for (int q2 = 0; q2 < 8; ++q2) wp[8 * h + q2] = v8[q2];
+          }
+        }
+      }
+      // The accumulator buffer is free for the MMA warp's next-but-one unit (the barrier is the
+      // even CTA's, which issues the MMAs).
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        if (rank != 0) mbar_arrive_cluster(mapa_shared(smem_addr(&sm.tempty[b]), 0));
+        else mbar_arrive(&sm.tempty[b]);
+      }
+      if (!FT) continue;
+
+      // -------------------------------------------------------- row verification
+      if (et == 0) { sm.nflag_rows = 0; sm.first_row = INT_MAX; }
+      named_bar(1, 128);
+      double delta = 0.0, tau = 0.0, predicted = 0.0;
+      if (got && row_ok) {
+        double pr;
+        if (KIND == 0) {
+          pr = (double)__uint_as_float(wp[0]) + (double)__uint_as_float(wp[1]) + (double)__uint_as_float(wp[2]);
+        } else {
+          pr = 0.0;
+          double sc = 512.0;  // piece scale 2^(9 - 4p)
+#pragma unroll
+          for (int q2 = 0; q2 < E::kPieces; ++q2, sc *= 0.0625) pr += sc * (double)__uint_as_float(wp[q2]);
+        }
+        const double cin_sum = (double)cs + (double)cc;
+        predicted = (double)alpha * pr + (beta_nz ? (double)p.beta * cin_sum : 0.0);
+        for (int e = 0; e < p.inj.n; ++e) {
+          const InjectPoint& ip = p.inj.p[e];
+          if (ip.site == kSiteChecksumRow && ip.i == gi && ip.j >= n0 && ip.j < n0 + nJ) {
+            const double em = ldexp(fabs(predicted), ip.rel_log2);
+            predicted = ip.sign < 0 ? predicted - em : predicted + em;
+          }
+        }
+        const double ref = (double)rs + (double)rc;
+        delta = ref - predicted;
+        // tau = |alpha| P (gamma_K(u_acc) (1 + s) + 2^-20 + gamma_BN(2^-24)) + 2^-23 sum|C| +
+        // 2^-21 |beta| sum|C_in|, P an upper bound of sum_k |A(i,k)| sum_{j in tile} |B(k,j)|:
+        // gamma_K(u_acc) P bounds the accumulations of the row's outputs, gamma_K(u_acc) s P
+        // those of the prediction (s bounds sum_p |piece_p| / |B e|), gamma_BN(2^-24) P the
+        // binary32 sum B e over the tile's BN columns, 2^-23 sum|C| the compensated row sum,
+        // 2^-21 |beta| sum|C_in| the beta side of the roundings of beta C_in, of the output's
+        // multiply-add and of the compensated C_in sum (four times 2^-24, doubled), and
+        // 2^-20 P the alpha side of the output rounding, the cross terms and the binary64
+        // operations (about 2^-23 P, quadrupled).
+        const float P = __fmul_ru(p.rowAbsA[gi], p.maxAbsBe[nt]);
+        const float g = gamma32_up((float)p.K, p.u_acc);
+        const float genc = gamma32_up((float)BN, 0x1p-24f);
+        const float prod = __fmul_ru(__fmul_ru(fabsf(alpha), P),
+                                     __fadd_ru(__fadd_ru(__fmul_ru(g, 1.0f + E::kPieceSum), 0x1p-20f), genc));
+        const float outp = __fadd_ru(__fmul_ru(0x1p-23f, rabs), __fmul_ru(0x1p-21f, __fmul_ru(fabsf(p.beta), cabs)));
+        tau = (double)__fadd_ru(prod, outp);
+        if (!(fabs(delta) <= tau) || isinf(delta)) {
+          atomicAdd(&sm.nflag_rows, 1);
+          atomicMin(&sm.first_row, row);
+        }
+      }
+      named_bar(1, 128);
+      if (row_ok && row == sm.first_row) { sm.delta_row = delta; sm.tau_row = tau; sm.pred_row = predicted; }
+      __threadfence_block();
+      named_bar(1, 128);
+      const int nr = sm.nflag_rows;
+      if (nr > 0) {
+        // A row mismatch. The column checksums that locate it (Section V.A, lazy side) are
+        // formed by the resolve pass after every tile is stored, spread over many CTAs; this
+        // CTA only hands the tile over (with the column sums of C_in, which it overwrote).
+        if (et == 0) sm.pend_slot = (int)atomicAdd(&p.pend->count, 1u);
+        named_bar(1, 128);
+        const int slot = sm.pend_slot;
+        if (slot < kTcPendCap) {
+          TcPendingEntry& pe = p.pend->e[slot];
+          if (et == 0) {
+            pe.mt = mt; pe.nt = nt; pe.nr = nr; pe.first_row = sm.first_row;
+            pe.delta_row = sm.delta_row; pe.tau_row = sm.tau_row; pe.pred_row = sm.pred_row; pe.done = 0u;
+          }
+          if (beta_nz)
+            for (int c = et; c < nJ; c += 128) {
+              double cs2 = 0.0;
+              float ca = 0.f;
+              for (int w = 0; w < 4; ++w) { cs2 += (double)sm.cin_col[w][c]; ca = __fadd_ru(ca, sm.cin_col_abs[w][c]); }
+              pe.cin_sum[c] = cs2;
+              pe.cin_abs[c] = ca;
+            }
+        } else if (et == 0) {
+          // more mismatching tiles in this call than the resolve pass holds: detected, not located
+          tc_record(p, FT_KIND_UNCORRECTABLE, mt, nt, m0 + sm.first_row, -1, sm.delta_row, 0.0, sm.tau_row, 0.0,
+                    0.0, 0.0, nr, 0);
+          count_kind(p, FT_KIND_UNCORRECTABLE);
+        }
+      }
+      if (et == 0 && got && nI > 0 && p.report)  // an abandoned tile (a wait gave up) is not counted
+        atomicAdd(reinterpret_cast<unsigned long long*>(&p.report->tiles_checked), 1ull);
+      named_bar(1, 128);  // every epilogue thread is done with this tile's shared state
+    }
+  }
+
+  // ------------------------------------------------------------ teardown
+  // neither CTA leaves (nor frees the pair's TMEM) while the other may still signal its
+  // barriers or read its TMEM
+  tc_fence_before();
+  __syncwarp();
+  cluster_sync();
+  if (t == 0 && sm.timeout && p.report) atomicOr(&p.report->status, FT_STATUS_TIMEOUT);
+  if (warp == 1) {
+    __syncwarp();  // tcgen05.dealloc is warp-collective: reconverge after the divergent MMA issue
+    tc_fence_after();
+    tmem_dealloc_pair(tmem, TMEM_COLS);
   }
 }
 
@@ -747,34 +1105,64 @@ cudaError_t launch_scale_f32(float* C, int64_t ldc, int64_t M, int64_t N, float 
 }
 
 template <bool FT, int KIND>
-static cudaError_t launch_gemm_kind(const TcParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB,
-                                    const CUtensorMap* tmChk, int sms, cudaStream_t st) {
-  const size_t smem = sizeof(TcSmem);
+static cudaError_t launch_gemm_kind(const TcParams& p, const TcMaps& m, int cg, int sms, cudaStream_t st) {
   const int bn = TcGeom<FT, KIND>::BN;
-  const long long tiles = (long long)((p.M + BM - 1) / BM) * ((p.N + bn - 1) / bn);
-  const int grid = (int)(tiles < sms ? tiles : sms);
-  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<FT, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  kernel_timer_start(st);
-  tc_gemm_kernel<FT, KIND><<<grid, NTHREADS, smem, st>>>(*tmA, *tmB, *tmChk, p);
-  kernel_timer_stop(st);
-  e = cudaGetLastError();
+  const long long nMb = (p.M + BM - 1) / BM, nNb = (p.N + bn - 1) / bn;
+  cudaError_t e;
+  if (cg == 2) {
+    auto kern = tc_gemm_pair_kernel<FT, KIND>;
+    const size_t smem = sizeof(TcSmem<2>);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)(sms / 2 * 2), 1, 1);
+    cfg.blockDim = dim3(NTHREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // CTA pairs resident at once (one per TPC when nothing else occupies the GPU)
+    static int max_clusters[2][2] = {{0, 0}, {0, 0}};
+    int& mc = max_clusters[FT ? 1 : 0][KIND];
+    if (mc == 0) {
+      e = cudaOccupancyMaxActiveClusters(&mc, kern, &cfg);
+      if (e != cudaSuccess) return e;
+      if (mc <= 0) return cudaErrorInvalidConfiguration;
+    }
+    const long long units = (nMb + 1) / 2 * nNb;
+    cfg.gridDim = dim3((unsigned)(2 * (units < mc ? units : mc)), 1, 1);
+    kernel_timer_start(st);
+    e = cudaLaunchKernelEx(&cfg, kern, m.a, m.b, m.b2, m.chk, p);
+    kernel_timer_stop(st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+  } else {
+    const size_t smem = sizeof(TcSmem<1>);
+    const long long tiles = nMb * nNb;
+    const int grid = (int)(tiles < sms ? tiles : sms);
+    e = cudaFuncSetAttribute(tc_gemm_kernel<FT, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kernel_timer_start(st);
+    tc_gemm_kernel<FT, KIND><<<grid, NTHREADS, smem, st>>>(m.a, m.b, m.chk, p);
+    kernel_timer_stop(st);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess || !FT) return e;
   tc_resolve_kernel<KIND><<<2 * sms, kResolveWarps * 32, 0, st>>>(p);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_gemm(const TcParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmChk,
-                           bool ft, cudaStream_t st) {
+cudaError_t launch_tc_gemm(const TcParams& p, const TcMaps& m, bool ft, int cg, cudaStream_t st) {
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  if (p.kind == 0) return ft ? launch_gemm_kind<true, 0>(p, tmA, tmB, tmChk, sms, st)
-                             : launch_gemm_kind<false, 0>(p, tmA, tmB, tmChk, sms, st);
-  return ft ? launch_gemm_kind<true, 1>(p, tmA, tmB, tmChk, sms, st)
-            : launch_gemm_kind<false, 1>(p, tmA, tmB, tmChk, sms, st);
+  if (p.kind == 0) return ft ? launch_gemm_kind<true, 0>(p, m, cg, sms, st) : launch_gemm_kind<false, 0>(p, m, cg, sms, st);
+  return ft ? launch_gemm_kind<true, 1>(p, m, cg, sms, st) : launch_gemm_kind<false, 1>(p, m, cg, sms, st);
 }
 
 }  // namespace ftk

@@ -84,8 +84,14 @@ cudaError_t launch_scale_f32(float* C, int64_t ldc, int64_t M, int64_t N, float 
 cudaError_t launch_tc_encode(const TcParams& p, const TcWorkspace& w, cudaStream_t st);
 // out[i] = the encode's binary32 value of E4M3 code codes[i], i < n
 cudaError_t launch_decode_e4m3(const uint8_t* codes, float* out, int64_t n, cudaStream_t st);
-cudaError_t launch_tc_gemm(const TcParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmChk,
-                           bool ft, cudaStream_t st);
+// Tensor maps of one call, all K-major with 128-byte boxes along K: a (128 rows per box),
+// b (data rows of B: BN per box for one CTA per tile, 128 for a CTA pair), b2 (a CTA pair's
+// odd CTA, protected: 120 rows) and chk (the checksum operand, 8 rows).
+struct TcMaps {
+  CUtensorMap a, b, b2, chk;
+};
+// cg: 1 (one CTA per 128-row tile) or 2 (a CTA pair per 256 rows, cta_group::2).
+cudaError_t launch_tc_gemm(const TcParams& p, const TcMaps& m, bool ft, int cg, cudaStream_t st);
 
 // K-major copy of an MN-major operand: dst[r * pitch + k] = src[r + k * ld] for r < R,
 // k < K, elem_bytes 1 or 2 (asynchronous on st). pitch: tc_kmajor_pitch(K, elem_bytes), K

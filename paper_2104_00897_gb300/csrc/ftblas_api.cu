@@ -20,6 +20,7 @@ namespace {
 thread_local int g_last_cuda_error = 0;
 thread_local int g_last_used_tma = -1;
 std::atomic<int> g_fp64_engine{kEngineDFMA};
+std::atomic<int> g_tc_cta_group{0};  // 0: by call (protected: one CTA per tile; unprotected: CTA pairs)
 std::atomic<int> g_fp64_tile{0};  // 0: fp64_tile_edge decides; else the forced DFMA tile edge
 std::atomic<int64_t> g_kc_interval{0};
 std::atomic<int> g_emu_slices{kEmuSlicesDefault};
@@ -731,13 +732,21 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   }
   // 2 s per bounded wait (a whole tile takes about 0.1 ms); 20 ms with a stall point planned
   p.wait_limit_ns = stall ? 20000000ull : 2000000000ull;
-  CUtensorMap tmA, tmB, tmC;
-  std::memset(&tmA, 0, sizeof(tmA)); std::memset(&tmB, 0, sizeof(tmB)); std::memset(&tmC, 0, sizeof(tmC));
-  if (!make_map_sw128(&tmA, eb, f.A, K, f.M, f.lda, kTcBM)) return release(FTBLAS_STATUS_NOT_SUPPORTED);
-  if (!make_map_sw128(&tmB, eb, f.B, K, f.N, f.ldb, ft ? (uint32_t)bnp : kTcBN))
+  // one CTA per 128-row tile, or a CTA pair per 256 rows (B staged half in each CTA); by
+  // default the faster form measured for each (protected: one CTA; unprotected: pairs)
+  const int cg_set = g_tc_cta_group.load();
+  const int cg = cg_set != 0 ? cg_set : (ft ? 1 : 2);
+  TcMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  const uint32_t b_rows = cg == 2 ? kTcBN / 2 : (ft ? (uint32_t)bnp : kTcBN);
+  if (!make_map_sw128(&maps.a, eb, f.A, K, f.M, f.lda, kTcBM)) return release(FTBLAS_STATUS_NOT_SUPPORTED);
+  if (!make_map_sw128(&maps.b, eb, f.B, K, f.N, f.ldb, b_rows)) return release(FTBLAS_STATUS_NOT_SUPPORTED);
+  maps.b2 = maps.b;
+  if (cg == 2 && ft && !make_map_sw128(&maps.b2, eb, f.B, K, f.N, f.ldb, (uint32_t)(bnp - kTcBN / 2)))
     return release(FTBLAS_STATUS_NOT_SUPPORTED);
+  maps.chk = maps.a;
   g_last_used_tma = 1;
-  if (!ft) return release(record_cuda(launch_tc_gemm(p, &tmA, &tmB, &tmA, false, st)));
+  if (!ft) return release(record_cuda(launch_tc_gemm(p, maps, false, cg, st)));
   const bool own = resolve == nullptr;
   void* ws = nullptr;
   if (own) {
@@ -751,9 +760,10 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   p.rowAbsA = w.rowAbsA; p.maxAbsBe = w.maxAbsBe; p.sA = w.sA; p.absSA = w.absSA;
   p.sa_pitch = w.kpitch; p.pend = w.pend;
   const int64_t nNb = (f.N + bnp - 1) / bnp;
-  int rc = make_map_sw128(&tmC, eb, w.chk, K, nNb * chk_rows, w.kpitch, (uint32_t)chk_rows) ? 0 : FTBLAS_STATUS_NOT_SUPPORTED;
+  int rc = make_map_sw128(&maps.chk, eb, w.chk, K, nNb * chk_rows, w.kpitch, (uint32_t)chk_rows) ? 0
+                                                                                              : FTBLAS_STATUS_NOT_SUPPORTED;
   if (rc == 0) rc = record_cuda(launch_tc_encode(p, w, st));  // writes every workspace entry the GEMM reads
-  if (rc == 0) rc = record_cuda(launch_tc_gemm(p, &tmA, &tmB, &tmC, true, st));
+  if (rc == 0) rc = record_cuda(launch_tc_gemm(p, maps, true, cg, st));
   if (own) cudaFreeAsync(ws, st);
   return release(rc);
 }
@@ -1164,6 +1174,11 @@ int ftblas_emu_convert_i128(const int64_t* words, double* out, int64_t n, void* 
 int64_t ftblas_set_verification_interval(int64_t k_interval) {
   if (k_interval < 0) return -1;
   return g_kc_interval.exchange(k_interval);
+}
+
+int ftblas_set_tc_cta_group(int cta_group) {
+  if (cta_group < 0 || cta_group > 2) return -1;
+  return g_tc_cta_group.exchange(cta_group);
 }
 
 int ftblas_set_fp64_engine(int engine) {

@@ -95,6 +95,13 @@ def test_verification_tile_and_engine_switch():
     prev = fb.ftblas_set_fp64_engine(fb.ENGINE_DMMA)
     assert fb.ftblas_set_fp64_engine(prev) == fb.ENGINE_DMMA
     assert fb.ftblas_set_fp64_engine(7) == -1
+    # tensor-core kernel form: 0 (by call), 1 or 2; the verification tile does not depend on it
+    assert fb.ftblas_set_tc_cta_group(3) == -1 and fb.ftblas_set_tc_cta_group(-1) == -1
+    prev = fb.ftblas_set_tc_cta_group(2)
+    assert prev == 0 and fb.tc_cta_group(True) == 2
+    assert fb.ftblas_verification_tile(fb.COL_MAJOR, fb.R_16BF, 8192, 8192, 8192) == (128, 248, 64)
+    assert fb.ftblas_set_tc_cta_group(prev) == 2
+    assert fb.tc_cta_group(True) == 1 and fb.tc_cta_group(False) == 2
 
 
 def test_every_declaration_cites_its_passage():

@@ -213,27 +213,34 @@ def test_bf16_full_size_8192_sampled_rows():
     assert record_set(orep) == record_set(rep)
 
 
-def test_bounded_wait_gives_up_and_reports_timeout():
+@pytest.mark.parametrize("cta_group", [1, 2])
+def test_bounded_wait_gives_up_and_reports_timeout(cta_group):
     """The tensor-core kernel's bounded waits: a staging barrier that never completes (the
-    test-only stall point) ends the stalled CTA's work after 20 ms, with no fault. With one
-    tile per persistent CTA, exactly that tile is left unwritten, the report carries
-    FT_STATUS_TIMEOUT, the other tiles are stored as in a clean call, and the next call is
-    clean."""
-    P = Bf16Problem(256, 496, 512, O.COL_MAJOR, alpha=1.0, beta=0.0, seed=43)
-    clean, rep0 = P.run()
-    assert rep0.status == 0
-    tr, tc, _ = P.tile()
-    i, j = 130, 300
-    fb.ftblas_set_injection(fb.make_injection(fixed=[dict(i=i, j=j, site=fb.SITE_STALL, kt=3)]))
+    test-only stall point) ends the stalled CTA's (or CTA pair's) work after 20 ms, with no
+    fault. With one unit per persistent CTA (pair), exactly that unit is left unwritten: the
+    stalled tile, or with CTA pairs the two 128-row tiles that share the pair's staging
+    barrier. The report carries FT_STATUS_TIMEOUT, the other tiles are stored as in a clean
+    call, and the next call is clean."""
+    prev = fb.ftblas_set_tc_cta_group(cta_group)
     try:
-        got, rep = P.run()
+        P = Bf16Problem(256, 496, 512, O.COL_MAJOR, alpha=1.0, beta=0.0, seed=43)
+        clean, rep0 = P.run()
+        assert rep0.status == 0
+        tr, tc, _ = P.tile()
+        i, j = 130, 300
+        fb.ftblas_set_injection(fb.make_injection(fixed=[dict(i=i, j=j, site=fb.SITE_STALL, kt=3)]))
+        try:
+            got, rep = P.run()
+        finally:
+            fb.ftblas_set_injection(None)
+        assert rep.status & fb.STATUS_TIMEOUT
+        ur = tr * cta_group  # rows of a unit
+        stalled = np.zeros_like(got, dtype=bool)
+        stalled[(i // ur) * ur:(i // ur + 1) * ur, (j // tc) * tc:(j // tc + 1) * tc] = True
+        assert np.array_equal(got[~stalled], clean[~stalled])
+        assert np.array_equal(got[stalled], P.Cin.astype(np.float32).astype(np.float64)[stalled])  # not stored
+        assert rep.tiles_checked == -(-P.M // tr) * -(-P.N // tc) - cta_group
+        again, rep2 = P.run()
+        assert rep2.status == 0 and rep2.detected == 0 and np.array_equal(again, clean)
     finally:
-        fb.ftblas_set_injection(None)
-    assert rep.status & fb.STATUS_TIMEOUT
-    stalled = np.zeros_like(got, dtype=bool)
-    stalled[(i // tr) * tr:(i // tr + 1) * tr, (j // tc) * tc:(j // tc + 1) * tc] = True
-    assert np.array_equal(got[~stalled], clean[~stalled])
-    assert np.array_equal(got[stalled], P.Cin.astype(np.float32).astype(np.float64)[stalled])  # not stored
-    assert rep.tiles_checked == -(-P.M // tr) * -(-P.N // tc) - 1
-    again, rep2 = P.run()
-    assert rep2.status == 0 and rep2.detected == 0 and np.array_equal(again, clean)
+        fb.ftblas_set_tc_cta_group(prev)

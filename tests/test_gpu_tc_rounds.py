@@ -56,9 +56,17 @@ def _largest_in_tile(clean, P, tile_row, tile_col):
     return tile_row * tr + int(a), tile_col * tc + int(b)
 
 
+@pytest.fixture
+def cta_group(request):
+    prev = fb.ftblas_set_tc_cta_group(request.param)
+    yield request.param
+    fb.ftblas_set_tc_cta_group(prev)
+
+
+@pytest.mark.parametrize("cta_group", [1, 2], indirect=True)
 @pytest.mark.parametrize("kind", ["bf16", "fp8"])
 @pytest.mark.parametrize("layout", [O.COL_MAJOR, O.ROW_MAJOR])
-def test_multi_round_parity_with_one_fault_per_call(kind, layout):
+def test_multi_round_parity_with_one_fault_per_call(kind, layout, cta_group):
     M, N, K = 2304, 4100, 520
     cls = Bf16Problem if kind == "bf16" else Fp8Problem
     P = cls(M, N, K, layout, alpha=1.25, beta=0.5, seed=2304 + layout)
@@ -91,6 +99,46 @@ def test_multi_round_parity_with_one_fault_per_call(kind, layout):
         others = np.ones_like(got, dtype=bool)
         others[i, j] = False
         assert np.array_equal(got[others], clean[others])  # nothing else moved
+
+
+@pytest.mark.parametrize("kind", ["bf16", "fp8"])
+@pytest.mark.parametrize("N", [256, 368, 369, 500])
+def test_cta_pair_shapes_match_the_oracle(kind, N):
+    """The CTA-pair kernel's unit shapes: an odd number of 128-row tiles (the last pair's odd
+    CTA reads rows past M as zeros and stores nothing), and last column blocks of 8 and 120
+    data columns (the narrow pair MMA with the checksum pieces staged by the odd CTA), 121
+    (full width, rows past N zero), and 248. Protected and unprotected calls, with one CTA per
+    tile and with CTA pairs: values within the accumulation bound of the oracle, reports equal
+    to its clean report, and with a fault in the last tile of the ragged corner the oracle's
+    record."""
+    M, K = 300, 200
+    cls = Bf16Problem if kind == "bf16" else Fp8Problem
+    P = cls(M, N, K, O.COL_MAJOR, alpha=0.75, beta=-0.5, seed=300 + N)
+    ref, orep = P.oracle()
+    bound = P.bound(ref)
+    tr, tc, _ = P.tile()
+    i, j = _largest_in_tile(ref, P, -(-M // tr) - 1, -(-N // tc) - 1)
+    pt = dict(i=i, j=j, site=fb.SITE_OUTPUT, mode=fb.MODE_ADD_REL, rel_log2=14, sign=-1)
+    _, orep_f = P.oracle(injections=[pt], tiles=[_tile_of(P, i, j)])
+    prev = fb.ftblas_set_tc_cta_group(2)
+    try:
+        for cg in (1, 2):
+            fb.ftblas_set_tc_cta_group(cg)
+            got, rep = P.run()
+            assert np.all(np.abs(got - ref) <= bound), cg
+            assert report_summary(rep) == report_summary(orep) and rep.detected == 0 and rep.status == 0, cg
+            plain, _ = P.run(protect=False)
+            assert np.all(np.abs(plain - ref) <= bound), cg
+            fb.ftblas_set_injection(fb.make_injection(fixed=[pt]))
+            fgot, frep = P.run()
+            fb.ftblas_set_injection(None)
+            assert report_summary(frep)[1:] == report_summary(orep_f)[1:] == (1, 1, 0, 0, 0), cg
+            assert record_set(frep) == record_set(orep_f) == [(i, j, fb.KIND_CORRECTED)], cg
+            (r,) = frep.records()
+            assert abs(fgot[i, j] - ref[i, j]) <= bound[i, j] + r.tau_row + 2.0 ** -21 * abs(ref[i, j]), cg
+    finally:
+        fb.ftblas_set_injection(None)
+        fb.ftblas_set_tc_cta_group(prev)
 
 
 def test_fp8_full_size_16384_sampled_rows():
