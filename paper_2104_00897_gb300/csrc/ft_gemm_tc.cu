@@ -877,6 +877,51 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // ---------------------------------------------------------------------------------------
 constexpr int kResolveWarps = 8;
 
+// The lazy side's row-block sums, formed only for the row blocks of pending tiles (after the
+// GEMM, before the resolve pass; with no pending tile every CTA returns at once): for the
+// 128-row block of each pending tile, e^T A(k) = sum_i A(i,k) (binary32, any order) and
+// sum_i |A(i,k)| (upward), into sA / absSA. CTA x takes k = 256 x .. 256 x + 255; lane l of
+// warp w loads k .. k + 7 of rows w, w + 8, ...; the eight warps' partials meet in shared
+// memory. Two pending tiles of one row block write the same values.
+constexpr int kColsumK = 256;
+template <int KIND>
+__global__ void __launch_bounds__(256) tc_colsum_kernel(const __grid_constant__ TcParams p) {
+  using E = Elem<KIND>;
+  __shared__ __align__(16) float red_s[8][kColsumK];
+  __shared__ __align__(16) float red_a[8][kColsumK];
+  const unsigned npend = min(*reinterpret_cast<volatile const unsigned*>(&p.pend->count), (unsigned)kTcPendCap);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tk = threadIdx.x;
+  const int64_t k = (int64_t)blockIdx.x * kColsumK + lane * 8;
+  const uint8_t* A = static_cast<const uint8_t*>(p.A);
+  for (unsigned e = 0; e < npend; ++e) {
+    const int mt = p.pend->e[e].mt;
+    const int m0 = mt * BM, nI = min(BM, p.M - m0);
+    float s[8], a[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { s[q] = 0.f; a[q] = 0.f; }
+    for (int i = warp; i < nI; i += 8) {
+      float x[8];
+      E::unpack(k < p.K ? E::load_raw(A + (int64_t)(m0 + i) * p.lda * E::kBytes, k, p.K) : E::zero(), x);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { s[q] += x[q]; a[q] = __fadd_ru(a[q], fabsf(x[q])); }
+    }
+    *reinterpret_cast<float4*>(&red_s[warp][lane * 8]) = make_float4(s[0], s[1], s[2], s[3]);
+    *reinterpret_cast<float4*>(&red_s[warp][lane * 8 + 4]) = make_float4(s[4], s[5], s[6], s[7]);
+    *reinterpret_cast<float4*>(&red_a[warp][lane * 8]) = make_float4(a[0], a[1], a[2], a[3]);
+    *reinterpret_cast<float4*>(&red_a[warp][lane * 8 + 4]) = make_float4(a[4], a[5], a[6], a[7]);
+    __syncthreads();
+    float S = 0.f, Aab = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) { S += red_s[w][tk]; Aab = __fadd_ru(Aab, red_a[w][tk]); }
+    const int64_t kk = (int64_t)blockIdx.x * kColsumK + tk;
+    if (kk < p.K) {
+      p.sA[(int64_t)mt * p.sa_pitch + kk] = S;
+      p.absSA[(int64_t)mt * p.sa_pitch + kk] = Aab;
+    }
+    __syncthreads();  // the reduction arrays are reused by the next pending tile
+  }
+}
+
 struct ResolveShared {
   int last, first_col, first_elem;
   double part_d[kResolveWarps], part_r[kResolveWarps];
@@ -1151,6 +1196,9 @@ static cudaError_t launch_gemm_kind(const TcParams& p, const TcMaps& m, int cg, 
     e = cudaGetLastError();
   }
   if (e != cudaSuccess || !FT) return e;
+  tc_colsum_kernel<KIND><<<(unsigned)((p.K + kColsumK - 1) / kColsumK), 256, 0, st>>>(p);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   tc_resolve_kernel<KIND><<<2 * sms, kResolveWarps * 32, 0, st>>>(p);
   return cudaGetLastError();
 }

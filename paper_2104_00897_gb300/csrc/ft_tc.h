@@ -55,8 +55,9 @@ struct TcParams {
   float* C; int64_t ldc;
   const float* rowAbsA;          // [M]        upward sum_k |A(i,k)|
   const float* maxAbsBe;         // [nNb]      max_k upward sum_{j in block} |B(k,j)|
-  const float* sA;               // [nMb][sa_pitch] e^T A per 128-row block (binary32 sum)
-  const float* absSA;            // [nMb][sa_pitch] upward sum_{i in block} |A(i,k)|
+  float* sA;                     // [nMb][sa_pitch] e^T A per 128-row block (binary32 sum), formed after
+                                 // the GEMM for the row blocks of pending tiles only
+  float* absSA;                  // [nMb][sa_pitch] upward sum_{i in block} |A(i,k)|, likewise
   int64_t sa_pitch;              // multiple of 8 (32-byte aligned rows)
   TcPending* pend;
   ft_report_t* report;

@@ -21,7 +21,10 @@ constexpr int BM = kTcBM;             // 128 rows of A per block (the tile's row
 // rows of A, the columns of B. A CTA takes a block of L lines (the 128 rows of a tile of
 // A, the 248 columns of a tile of B) and ENC_KC consecutive k. Lane l of warp w loads
 // k0 + 8l .. k0 + 8l + 7 (one 16- or 8-byte load per line) of lines w, w + 8, w + 16, ...;
-// the eight warps' partial sums meet in shared memory.
+// the eight warps' partial sums meet in shared memory. From A it forms only what every
+// tile's row check needs, sum_k |A(i,k)| per row; e^T A per row block, which only the
+// lazy column side of a mismatching tile uses, is formed after the GEMM for those tiles'
+// row blocks alone (tc_colsum_kernel).
 // Sums over a block are plain binary32 sums: their rounding, at most gamma_L(2^-24) times
 // the sum of magnitudes in any order, is a term of the thresholds. Sums of magnitudes round
 // upward, so they bound the exact sums.
@@ -47,6 +50,20 @@ __device__ __forceinline__ float reduce_scatter8_up(const float (&la)[8], int la
   float v = __fadd_ru(h4 ? v2[1] : v2[0], __shfl_xor_sync(0xffffffffu, h4 ? v2[0] : v2[1], 4));
   v = __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, 2));
   return __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, 1));
+}
+
+// s[q] += x[q] for q < 8, two lanes of binary32 per instruction (add.rn.f32x2): each sum
+// takes the same values in the same order as eight scalar additions.
+__device__ __forceinline__ void add_f32x8(float (&s)[8], const float (&x)[8]) {
+#pragma unroll
+  for (int q = 0; q < 8; q += 2) {
+    unsigned long long a = (static_cast<unsigned long long>(__float_as_uint(s[q + 1])) << 32) | __float_as_uint(s[q]);
+    const unsigned long long b =
+        (static_cast<unsigned long long>(__float_as_uint(x[q + 1])) << 32) | __float_as_uint(x[q]);
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(a) : "l"(a), "l"(b));
+    s[q] = __uint_as_float(static_cast<uint32_t>(a));
+    s[q + 1] = __uint_as_float(static_cast<uint32_t>(a >> 32));
+  }
 }
 
 struct EncArgs {
@@ -106,10 +123,13 @@ __device__ __forceinline__ void encode_block(const EncArgs& g, int blk, int kc, 
         float lsum = 0.f;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          s[q] += x[q];
-          a[q] = __fadd_ru(a[q], fabsf(x[q]));
-          if (kRowsOfA) lsum = __fadd_ru(lsum, fabsf(x[q]));
+          if (kRowsOfA) {
+            lsum = __fadd_ru(lsum, fabsf(x[q]));
+          } else {
+            a[q] = __fadd_ru(a[q], fabsf(x[q]));
+          }
         }
+        if (!kRowsOfA) add_f32x8(s, x);
         la[u] = lsum;
       }
       if (kRowsOfA) {
@@ -119,21 +139,11 @@ __device__ __forceinline__ void encode_block(const EncArgs& g, int blk, int kc, 
       }
     }
   }
-  *reinterpret_cast<float4*>(&red_s[warp][lane * 8]) = make_float4(s[0], s[1], s[2], s[3]);
-  *reinterpret_cast<float4*>(&red_s[warp][lane * 8 + 4]) = make_float4(s[4], s[5], s[6], s[7]);
-  *reinterpret_cast<float4*>(&red_a[warp][lane * 8]) = make_float4(a[0], a[1], a[2], a[3]);
-  *reinterpret_cast<float4*>(&red_a[warp][lane * 8 + 4]) = make_float4(a[4], a[5], a[6], a[7]);
-  __syncthreads();
   const int tk = threadIdx.x;
-  float S = 0.f, Aab = 0.f;
-#pragma unroll
-  for (int w = 0; w < ENC_WARPS; ++w) { S += red_s[w][tk]; Aab = __fadd_ru(Aab, red_a[w][tk]); }
   const int64_t kk = (int64_t)kc * ENC_KC + tk;
   if (kRowsOfA) {
-    if (kk < g.K) {
-      g.sum[(int64_t)blk * g.pitch + kk] = S;
-      g.abs_sum[(int64_t)blk * g.pitch + kk] = Aab;
-    }
+    // (e^T A and sum_i |A(i,k)| per row block are formed only for the row blocks of tiles
+    // that reach the resolve pass: tc_colsum_kernel)
     if (blk == 0 && kc == 0 && tk == 0) g.pend->count = 0u;
     // the line block's last k-chunk to finish sums the per-chunk partials of its rows
     // (in chunk order: the result does not depend on which chunk finished last)
@@ -150,6 +160,14 @@ __device__ __forceinline__ void encode_block(const EncArgs& g, int blk, int kc, 
       }
     }
   } else {
+    *reinterpret_cast<float4*>(&red_s[warp][lane * 8]) = make_float4(s[0], s[1], s[2], s[3]);
+    *reinterpret_cast<float4*>(&red_s[warp][lane * 8 + 4]) = make_float4(s[4], s[5], s[6], s[7]);
+    *reinterpret_cast<float4*>(&red_a[warp][lane * 8]) = make_float4(a[0], a[1], a[2], a[3]);
+    *reinterpret_cast<float4*>(&red_a[warp][lane * 8 + 4]) = make_float4(a[4], a[5], a[6], a[7]);
+    __syncthreads();
+    float S = 0.f, Aab = 0.f;
+#pragma unroll
+    for (int w = 0; w < ENC_WARPS; ++w) { S += red_s[w][tk]; Aab = __fadd_ru(Aab, red_a[w][tk]); }
     if (kk < g.K) {
       if (KIND == 0) {
         // three bfloat16 pieces, each the nearest bfloat16 of what the previous ones leave:
