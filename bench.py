@@ -414,23 +414,31 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
         # pairs covering at least 4.5 s, so that the clock sampler (every 200 ms) records
         # twenty and more samples through the region
         npairs = max(steps, min(8192, int(4500.0 / max(e0.elapsed_time(e1), 1e-3)) + 1))
-        ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(npairs)]
+        # each step: unprotected (the library's fastest form), protected, and unprotected in
+        # the protected call's kernel form (the same-kernel overhead)
+        ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4)) for _ in range(npairs)]
         reps = [fb.new_report(dev) for _ in range(npairs)]
+        ft_form = fb.tc_cta_group(True)
         for i in range(npairs):
             ev[i][0].record()
             call(False)
             ev[i][1].record()
             call(True, reps[i])
             ev[i][2].record()
+            prev = fb.ftblas_set_tc_cta_group(ft_form)
+            call(False)
+            fb.ftblas_set_tc_cta_group(prev)
+            ev[i][3].record()
         torch.cuda.synchronize(dev)
-        na = sum(a.elapsed_time(b) for a, b, _ in ev) / npairs
-        ft = sum(b.elapsed_time(c) for _, b, c in ev) / npairs
+        na = sum(a.elapsed_time(b) for a, b, _, _ in ev) / npairs
+        ft = sum(b.elapsed_time(c) for _, b, c, _ in ev) / npairs
+        na_same = sum(c.elapsed_time(d) for _, _, c, d in ev) / npairs
         det = sum(int(fb.report_from_device(r).detected) for r in reps)
-        return na, ft, det, npairs
+        return na, ft, det, npairs, na_same
 
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     sampler.__enter__()  # started before the first warm-up; runs through the timed regions
-    ms_na, ms_ft, det_pair, npairs = timed_pair()
+    ms_na, ms_ft, det_pair, npairs, ms_na_same = timed_pair()
     _, _, _ = timed(False, False)  # unprotected product-kernel time for the roofline note
     _, det0, _ = timed(True, False)  # protected product-kernel time for the roofline
     ms_inj, det_inj, corr_inj = timed(True, True)
@@ -490,15 +498,22 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
         "ft_tflops": flops / ms_ft / 1e9, "ft_tflops_injected": flops / ms_inj / 1e9,
         "noabft_tflops": flops / ms_na / 1e9,
         "abft_overhead_pct": 100.0 * (ms_ft / ms_na - 1.0),
+        "noabft_tflops_same_form": flops / ms_na_same / 1e9,
+        "abft_overhead_pct_same_form": 100.0 * (ms_ft / ms_na_same - 1.0),
+        "kernel_forms": {"protected": "one CTA per tile" if fb.tc_cta_group(True) == 1 else "CTA pairs",
+                         "unprotected": "one CTA per tile" if fb.tc_cta_group(False) == 1 else "CTA pairs",
+                         "note": "abft_overhead_pct: protected call vs the fastest unprotected call; "
+                                 "_same_form: vs the unprotected call of the protected call's kernel form"},
         "speedup_over_fp64_ft": (flops / ms_ft / 1e9) / fp64_tflops if fp64_tflops else None,
         "false_alarms_clean": det0, "injected": timed_steps[(True, True)], "corrected": corr_inj, "detected": det_inj,
         "undetected_below_threshold": timed_steps[(True, True)] - det_inj,
         "injected_magnitude": f"2^{18 if fp8 else 16}..2^{22 if fp8 else 20} |C(i,j)| at a seeded element per call",
         "clocks": sampler.summary(),
-        "timed_steps": {"alternating_pairs": npairs, "ft_injected": timed_steps[(True, True)]},
-        "method": "ft_tflops, noabft_tflops and the overhead from unprotected and protected calls alternated in "
-                  "one region (per-call CUDA events); ft_tflops_injected from a region of injected calls; the "
-                  "roofline from the product-kernel events of a region of protected calls",
+        "timed_steps": {"alternating_triplets": npairs, "ft_injected": timed_steps[(True, True)]},
+        "method": "ft_tflops, noabft_tflops and the overheads from unprotected, protected and same-form "
+                  "unprotected calls alternated in one region (per-call CUDA events); ft_tflops_injected from a "
+                  "region of injected calls; the roofline from the product-kernel events of a region of "
+                  "protected calls",
         "seed": seed,
         "l2": l2_note_tc(2 * n * n * (1 if fp8 else 2), n * n * 4),
         "error_vs_fp64": {"max_over_sum_abs_ab": err_norm, "median_rel": err_rel,
@@ -915,7 +930,7 @@ def run_linear(dev, steps, warmup, T=8192, n_in=4096, n_out=4096):
     dY = S.normal_matrix(seed, 2, T, n_out, threads=threads)
     x = torch.from_numpy(np.ascontiguousarray(X).view(np.int16)).to(dev).view(torch.bfloat16).requires_grad_(True)
     w = torch.from_numpy(np.ascontiguousarray(W).view(np.int16)).to(dev).view(torch.bfloat16).requires_grad_(True)
-    dy = torch.from_numpy(np.ascontiguousarray(dY)).to(dev).float()
+    dy = torch.from_numpy(np.ascontiguousarray(dY)).to(dev).to(torch.bfloat16)  # Y is bfloat16
     Fn = fb.FTLinearFn
 
     def step(mon):
@@ -929,13 +944,18 @@ def run_linear(dev, steps, warmup, T=8192, n_in=4096, n_out=4096):
     for _ in range(warmup):
         step(None)
     torch.cuda.synchronize(dev)
-    # as many timed steps as cover at least 40 ms (a step takes about a millisecond)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     step(None)
     e1.record()
     torch.cuda.synchronize(dev)
-    nsteps = max(steps, min(256, int(40.0 / max(e0.elapsed_time(e1), 1e-3)) + 1))
+    step_ms = max(e0.elapsed_time(e1), 1e-3)
+    # at least 0.3 s of further warm-up (clocks settle after the process starts), then as
+    # many timed steps as cover at least 1 s (a step takes about a millisecond)
+    for _ in range(int(300.0 / step_ms)):
+        step(None)
+    torch.cuda.synchronize(dev)
+    nsteps = max(steps, min(4096, int(1000.0 / step_ms) + 1))
     mon = fb.FTMonitor(dev)
     e0.record()
     for _ in range(nsteps):
@@ -958,7 +978,8 @@ def run_linear(dev, steps, warmup, T=8192, n_in=4096, n_out=4096):
     err_dw = float(np.max(np.abs(dW - ref) / (np.abs(dYq[:, rows]).T @ np.abs(Xf))))
     return {
         "workload": f"FTLinearFn Y = X W^T, X {T}x{n_in} BF16 N(0,1), W {n_out}x{n_in} BF16 N(0,0.02), dY N(0,1); "
-                    "forward + backward (3 protected GEMMs, operand transposes by copy)",
+                    "forward + backward (3 protected GEMMs with bfloat16 Y, dX, dW rounded from the verified "
+                    "FP32 products; MN-major operands copied K-major by the library)",
         "step_ms": ms, "timed_steps": nsteps, "tflops": 6.0 * T * n_in * n_out / ms / 1e9, "gemm_calls": summ["calls"],
         "faults_injected": summ["calls"], "detected": summ["detected"], "corrected": summ["corrected"],
         "uncorrectable": summ["uncorrectable"],

@@ -256,7 +256,12 @@ int ftblas_dgemm_host(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_tran
  * a_scale, b_scale, stream, report. alpha and beta point to HOST scalars of the compute
  * type (double for FTBLAS_R_64F, float for FTBLAS_R_32F). Supported combinations:
  *   A, B, C, compute all FTBLAS_R_64F            -> the same path as ftblas_dgemm;
- *   A, B FTBLAS_R_16BF, C and compute FTBLAS_R_32F -> tcgen05 BF16 GEMM, C stored in FP32.
+ *   A, B FTBLAS_R_16BF or both FTBLAS_R_8F_E4M3, compute FTBLAS_R_32F, C FTBLAS_R_32F
+ *                                                 -> tcgen05 GEMM, C stored in FP32;
+ *   the same with C FTBLAS_R_16BF                  -> the product runs into an FP32 buffer
+ *       from the workspace pool (filled from C first when beta != 0), where it is verified,
+ *       located and corrected exactly as above; C is then rounded to nearest bfloat16 in
+ *       one pass. The checks cover the FP32 values; the final rounding is not checked.
  * a_scale / b_scale (device pointers to one float each) scale FP8 operands and must be
  * NULL otherwise. The tensor-core kernel reads both operands K-contiguous in the
  * column-major kernel frame (column-major: A transposed and B not; row-major: A not
@@ -301,8 +306,8 @@ int ftblas_gemm_ex_noabft(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_
  * front by another framework's caching allocator, a real-time or certification setting
  * that forbids allocation after initialisation, and a caller holding a lock under which
  * allocation could block. The protected BF16 GEMM (the argument list of ftblas_gemm_ex,
- * and only its BF16 combination: A, B FTBLAS_R_16BF, C and compute FTBLAS_R_32F; FP64 and
- * FP8 E4M3 return FTBLAS_STATUS_NOT_SUPPORTED; both operands K-contiguous in the kernel
+ * and only its BF16 combination: A, B FTBLAS_R_16BF, C and compute FTBLAS_R_32F; FP64,
+ * FP8 E4M3 and a bfloat16 C return FTBLAS_STATUS_NOT_SUPPORTED; both operands K-contiguous in the kernel
  * frame with 16-byte aligned bases and leading dimensions, since this entry point makes no
  * copies: other operands return FTBLAS_STATUS_NOT_SUPPORTED) takes its encode scratch from one static
  * device array of 16 MiB that every GPU loading this library holds until the process

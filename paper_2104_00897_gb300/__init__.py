@@ -441,15 +441,16 @@ def _row_major_operand(x):
 
 
 def gemm(a, b, c=None, alpha=1.0, beta=0.0, trans_a=False, trans_b=False, report=None, protect=True,
-         a_scale=None, b_scale=None, stream=None):
+         a_scale=None, b_scale=None, stream=None, out_dtype=None):
     """c = alpha * op(a) @ op(b) + beta * c on CUDA tensors, protected by ABFT.
 
     float64 operands run the FP64 kernel (c float64, see dgemm). bfloat16 or
-    float8_e4m3fn operands run the tensor-core kernel with FP32 accumulation and an FP32
-    c; a_scale / b_scale are 1-element float32 CUDA tensors (FP8 per-tensor scales) or
-    None. Operands are passed through in either storage order (the library copies an
-    MN-major operand K-major for the tensor-core kernel). ``report``: a buffer from
-    new_report() (or None). Returns c.
+    float8_e4m3fn operands run the tensor-core kernel with FP32 accumulation and a float32
+    or bfloat16 c (``out_dtype`` when c is None, float32 by default; a bfloat16 c is
+    verified and corrected in FP32 and rounded once); a_scale / b_scale are 1-element
+    float32 CUDA tensors (FP8 per-tensor scales) or None. Operands are passed through in
+    either storage order (the library copies an MN-major operand K-major for the
+    tensor-core kernel). ``report``: a buffer from new_report() (or None). Returns c.
     """
     import torch
     if a.dtype == torch.float64:
@@ -475,14 +476,15 @@ def gemm(a, b, c=None, alpha=1.0, beta=0.0, trans_a=False, trans_b=False, report
     if c is None:
         if beta != 0.0:
             raise ValueError("beta != 0 needs c")
-        c = torch.empty((M, N), dtype=torch.float32, device=a.device)
-    if c.dtype != torch.float32:
-        raise TypeError("c must be float32 for bfloat16 / float8 operands")
+        c = torch.empty((M, N), dtype=out_dtype if out_dtype is not None else torch.float32, device=a.device)
+    if c.dtype not in (torch.float32, torch.bfloat16):
+        raise TypeError("c must be float32 or bfloat16 for bfloat16 / float8 operands")
     if c.shape != (M, N):
         raise ValueError(f"c has shape {tuple(c.shape)}, expected {(M, N)}")
     if c.stride(1) != 1:
         if c.stride(0) == 1:  # column-major c: compute c^T = op(b)^T op(a)^T into its row-major view
-            return gemm(b, a, c.t(), alpha, beta, not trans_b, not trans_a, report, protect, b_scale, a_scale, stream)
+            return gemm(b, a, c.t(), alpha, beta, not trans_b, not trans_a, report, protect, b_scale, a_scale, stream,
+                        out_dtype)
         raise ValueError("c must have a unit stride in one dimension")
     # Row-major call. An operand whose rows of K are contiguous is passed as it is (the
     # tensor maps want a 16-byte aligned base and pitch; otherwise it is copied into that
@@ -495,8 +497,9 @@ def gemm(a, b, c=None, alpha=1.0, beta=0.0, trans_a=False, trans_b=False, report
     dt = R_8F_E4M3 if fp8 else R_16BF
     sa = a_scale.data_ptr() if a_scale is not None else None
     sb = b_scale.data_ptr() if b_scale is not None else None
+    ct = R_16BF if c.dtype == torch.bfloat16 else R_32F
     args = (ROW_MAJOR, ta_, tb_, M, N, K, float(alpha), a2.data_ptr(), dt, lda, b2.data_ptr(), dt, ldb,
-            float(beta), c.data_ptr(), R_32F, max(1, c.stride(0)), R_32F, sa, sb, st)
+            float(beta), c.data_ptr(), ct, max(1, c.stride(0)), R_32F, sa, sb, st)
     if protect:
         rc = ftblas_gemm_ex(*args, report.data_ptr() if report is not None else None)
     else:
@@ -514,7 +517,10 @@ class FTMonitor:
         self.reports = []
 
     def next_report(self):
-        r = new_report(self.device)
+        # every protected call zeroes its report on the stream before anything else, so the
+        # monitor's buffers need no fill of their own
+        import torch
+        r = torch.empty(REPORT_BYTES, dtype=torch.uint8, device=self.device or "cuda")
         self.reports.append(r)
         return r
 
@@ -535,17 +541,17 @@ def _ft_linear_class():
     class FTLinearFn(torch.autograd.Function):
         """Y = X W^T with every GEMM ABFT-protected: the forward product and, in the
         backward pass, dX = dY W and dW = dY^T X. float64 X, W run the FP64 kernel (Y and
-        the gradients float64). bfloat16 X, W run the tensor-core kernel: Y is float32
-        (the accumulation precision), dY is rounded to bfloat16 for the two backward
-        products and the gradients are returned in bfloat16. ``monitor`` (an FTMonitor
-        or None) receives the three calls' reports."""
+        the gradients float64). bfloat16 X, W run the tensor-core kernel with FP32
+        accumulation: Y and the gradients are bfloat16, each verified and corrected in FP32
+        and rounded once by the library (a dY of another dtype is rounded to bfloat16 first).
+        ``monitor`` (an FTMonitor or None) receives the three calls' reports."""
 
         @staticmethod
         def forward(ctx, x, w, monitor=None):
             ctx.save_for_backward(x, w)
             ctx.monitor = monitor
             rep = monitor.next_report() if monitor is not None else None
-            return gemm(x, w, trans_b=True, report=rep)
+            return gemm(x, w, trans_b=True, report=rep, out_dtype=x.dtype)
 
         @staticmethod
         def backward(ctx, dy):
@@ -554,11 +560,10 @@ def _ft_linear_class():
             dyq = dy.to(x.dtype) if x.dtype != dy.dtype else dy
             dx = dw = None
             if ctx.needs_input_grad[0]:
-                dx = gemm(dyq, w, report=mon.next_report() if mon is not None else None)
-                dx = dx.to(x.dtype) if dx.dtype != x.dtype else dx
+                dx = gemm(dyq, w, report=mon.next_report() if mon is not None else None, out_dtype=x.dtype)
             if ctx.needs_input_grad[1]:
-                dw = gemm(dyq, x, trans_a=True, report=mon.next_report() if mon is not None else None)
-                dw = dw.to(w.dtype) if dw.dtype != w.dtype else dw
+                dw = gemm(dyq, x, trans_a=True, report=mon.next_report() if mon is not None else None,
+                          out_dtype=w.dtype)
             return dx, dw, None
 
     return FTLinearFn

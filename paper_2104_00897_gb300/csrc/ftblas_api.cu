@@ -632,7 +632,10 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   if (K < 0) return -6;
   if (alpha == nullptr) return -7;
   if (beta == nullptr) return -14;
-  const bool c32 = Ctype == FTBLAS_R_32F && ctype == FTBLAS_R_32F;
+  // C in FP32, or in bfloat16 (the product then runs into an FP32 buffer, verified,
+  // located and corrected there, and is rounded to bfloat16 once at the end)
+  const bool c_bf16 = Ctype == FTBLAS_R_16BF && resolve == nullptr;
+  const bool c32 = (Ctype == FTBLAS_R_32F || c_bf16) && ctype == FTBLAS_R_32F;
   const bool bf16 = c32 && Atype == FTBLAS_R_16BF && Btype == FTBLAS_R_16BF;
   const bool fp8 = c32 && allow_fp8 && Atype == FTBLAS_R_8F_E4M3 && Btype == FTBLAS_R_8F_E4M3;
   if (!bf16 && !fp8) return FTBLAS_STATUS_NOT_SUPPORTED;
@@ -666,7 +669,10 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
     if (int e = record_cuda(cudaMemsetAsync(report, 0, sizeof(ft_report_t), st))) return e;
   }
   if (M == 0 || N == 0) return 0;
-  if (!need_ab) return record_cuda(launch_scale_f32(static_cast<float*>(C), ldc, f.M, f.N, be, st));  // C = beta C
+  if (!need_ab) {  // C = beta C
+    if (c_bf16) return record_cuda(launch_scale_bf16(static_cast<uint16_t*>(C), ldc, f.M, f.N, be, st));
+    return record_cuda(launch_scale_f32(static_cast<float*>(C), ldc, f.M, f.N, be, st));
+  }
   CallerPoint pts[kMaxInject];
   int npts = 0;
   const int64_t bnp = tc_bn_prot(kind), chk_rows = tc_chk_rows(kind);  // protected tile width, checksum rows
@@ -686,11 +692,15 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   // K-major, aligned copies of MN-major or misaligned operands (stream-ordered workspace,
   // released at the end)
   void* tws = nullptr;
-  if (copy_a || copy_b) {
+  // FP32 product buffer of a bfloat16 C (kernel frame, column-major, leading dimension M)
+  const size_t cbytes = c_bf16 ? (size_t(f.M) * size_t(f.N) * 4 + 255) & ~size_t(255) : 0;
+  float* cf = nullptr;
+  if (copy_a || copy_b || c_bf16) {
     const int64_t pitch = tc_kmajor_pitch(K, eb);
     const size_t abytes = copy_a ? (size_t(f.M * pitch * eb) + 255) & ~size_t(255) : 0;
-    const size_t bbytes = copy_b ? size_t(f.N * pitch * eb) : 0;
-    if (ws_alloc(&tws, abytes + bbytes, st) != cudaSuccess) return FTBLAS_STATUS_ALLOC_FAILED;
+    const size_t bbytes = copy_b ? (size_t(f.N * pitch * eb) + 255) & ~size_t(255) : 0;
+    if (ws_alloc(&tws, abytes + bbytes + cbytes, st) != cudaSuccess) return FTBLAS_STATUS_ALLOC_FAILED;
+    if (c_bf16) cf = reinterpret_cast<float*>(static_cast<uint8_t*>(tws) + abytes + bbytes);
     uint8_t* base = static_cast<uint8_t*>(tws);
     auto copy = [&](const void* src, int64_t rows, int64_t ld, bool kmajor, uint8_t* dst) {
       if (kmajor)  // rows of K already contiguous: a pitched copy
@@ -717,7 +727,20 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
     return rc;
   };
   p.A = f.A; p.lda = f.lda; p.B = f.B; p.ldb = f.ldb;
-  p.C = static_cast<float*>(C); p.ldc = ldc;
+  if (c_bf16) {
+    p.C = cf; p.ldc = f.M;
+    if (be != 0.0f) {
+      if (int e = record_cuda(launch_bf16_to_f32(static_cast<const uint16_t*>(C), ldc, cf, f.M, f.M, f.N, st)))
+        return release(e);
+    }
+  } else {
+    p.C = static_cast<float*>(C); p.ldc = ldc;
+  }
+  // the bfloat16 C rounded from the FP32 buffer once every pass over it has finished
+  auto finish = [&](int rc) {
+    if (rc == 0 && c_bf16) rc = record_cuda(launch_f32_to_bf16(cf, f.M, static_cast<uint16_t*>(C), ldc, f.M, f.N, st));
+    return release(rc);
+  };
   p.report = ft ? report : nullptr;
   p.swap_report = f.swap;
   bool stall = false;
@@ -746,7 +769,7 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
     return release(FTBLAS_STATUS_NOT_SUPPORTED);
   maps.chk = maps.a;
   g_last_used_tma = 1;
-  if (!ft) return release(record_cuda(launch_tc_gemm(p, maps, false, cg, st)));
+  if (!ft) return finish(record_cuda(launch_tc_gemm(p, maps, false, cg, st)));
   const bool own = resolve == nullptr;
   void* ws = nullptr;
   if (own) {
@@ -765,7 +788,7 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   if (rc == 0) rc = record_cuda(launch_tc_encode(p, w, st));  // writes every workspace entry the GEMM reads
   if (rc == 0) rc = record_cuda(launch_tc_gemm(p, maps, true, cg, st));
   if (own) cudaFreeAsync(ws, st);
-  return release(rc);
+  return finish(rc);
 }
 
 // ------------------------------------------------------------------ emulated FP64

@@ -4,9 +4,10 @@
 - FP64: central finite differences (torch.autograd.gradcheck) at X 64 x 48, W 32 x 48,
   i.e. the GEMM (M, N, K) = (64, 32, 48), pin the backward; forward and gradients equal
   the oracle's products within the FP64 criterion, with one corrected fault per pass.
-- BF16: forward and gradients against the oracle's products of the same BF16 values
-  (binary32 accumulation) within the accumulation bound plus the bfloat16 rounding of the
-  returned gradients; one injected output fault per GEMM pass is corrected in all three.
+- BF16: forward and gradients (bfloat16, rounded once by the library from the verified
+  FP32 products) against the oracle's products of the same BF16 values (binary32
+  accumulation) within the accumulation bound plus the bfloat16 rounding; one injected
+  output fault per GEMM pass is corrected in all three.
 """
 import numpy as np
 import pytest
@@ -99,16 +100,17 @@ def test_bf16_linear_forward_backward_with_faults():
                                               log2_hi=14, every_n_launches=1, errors_per_launch=1))
     mon = fb.FTMonitor()
     y = fb.FTLinearFn.apply(x, w, mon)
-    assert y.dtype == torch.float32
+    assert y.dtype == torch.bfloat16
     dy = torch.from_numpy(dY).cuda().float()
-    y.backward(dy)
+    y.backward(dy.to(torch.bfloat16))
     s = mon.summary()
     assert (s["calls"], s["detected"], s["corrected"], s["uncorrectable"], s["status"]) == (3, 3, 3, 0, 0)
     fb.ftblas_set_injection(None)
     dYq = S.bf16_bits_to_f64(S.to_bf16_bits(dy.double().cpu().numpy()))  # dY rounded to bfloat16, as the layer does
-    # forward (FP32) and gradients (bfloat16: one more rounding, 2^-8 relative). A corrected
-    # element comes from the row checksum: within its record's row threshold instead.
-    calls = ((y.detach(), X, W.T, 2.0 ** -22), (x.grad, dYq, W, 2.0 ** -8), (w.grad, dYq.T, X, 2.0 ** -8))
+    # forward and gradients in bfloat16 (the FP32 result rounded once: 2^-8 relative covers
+    # it with the FP32 rounding). A corrected element comes from the row checksum: within
+    # its record's row threshold instead.
+    calls = ((y.detach(), X, W.T, 2.0 ** -8), (x.grad, dYq, W, 2.0 ** -8), (w.grad, dYq.T, X, 2.0 ** -8))
     for (got, A, B, out_round), buf in zip(calls, mon.reports):
         ref = ref_gemm(A, B)
         bound = 2 * gamma(A.shape[1], U32) * (np.abs(A) @ np.abs(B)) + out_round * np.abs(ref) + 1e-30
