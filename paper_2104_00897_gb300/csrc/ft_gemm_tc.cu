@@ -880,18 +880,19 @@ constexpr int kResolveWarps = 8;
 // The lazy side's row-block sums, formed only for the row blocks of pending tiles (after the
 // GEMM, before the resolve pass; with no pending tile every CTA returns at once): for the
 // 128-row block of each pending tile, e^T A(k) = sum_i A(i,k) (binary32, any order) and
-// sum_i |A(i,k)| (upward), into sA / absSA. CTA x takes k = 256 x .. 256 x + 255; lane l of
-// warp w loads k .. k + 7 of rows w, w + 8, ...; the eight warps' partials meet in shared
-// memory. Two pending tiles of one row block write the same values.
-constexpr int kColsumK = 256;
+// sum_i |A(i,k)| (upward), into sA / absSA. CTA x takes k = 64 x .. 64 x + 63: thread t loads
+// k = 64 x + 8 (t & 7) .. + 7 of rows t >> 3, (t >> 3) + 32, ...; the 32 row groups' partials
+// meet in shared memory and are summed in a fixed order. Two pending tiles of one row block
+// write the same values.
+constexpr int kColsumK = 64;
 template <int KIND>
 __global__ void __launch_bounds__(256) tc_colsum_kernel(const __grid_constant__ TcParams p) {
   using E = Elem<KIND>;
-  __shared__ __align__(16) float red_s[8][kColsumK];
-  __shared__ __align__(16) float red_a[8][kColsumK];
+  __shared__ __align__(16) float red_s[32][kColsumK];
+  __shared__ __align__(16) float red_a[32][kColsumK];
   const unsigned npend = min(*reinterpret_cast<volatile const unsigned*>(&p.pend->count), (unsigned)kTcPendCap);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tk = threadIdx.x;
-  const int64_t k = (int64_t)blockIdx.x * kColsumK + lane * 8;
+  const int t = threadIdx.x, oct = t & 7, rg = t >> 3;
+  const int64_t k = (int64_t)blockIdx.x * kColsumK + oct * 8;
   const uint8_t* A = static_cast<const uint8_t*>(p.A);
   for (unsigned e = 0; e < npend; ++e) {
     const int mt = p.pend->e[e].mt;
@@ -899,24 +900,27 @@ __global__ void __launch_bounds__(256) tc_colsum_kernel(const __grid_constant__ 
     float s[8], a[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) { s[q] = 0.f; a[q] = 0.f; }
-    for (int i = warp; i < nI; i += 8) {
+#pragma unroll
+    for (int u = 0; u < BM / 32; ++u) {
+      const int i = rg + 32 * u;
       float x[8];
-      E::unpack(k < p.K ? E::load_raw(A + (int64_t)(m0 + i) * p.lda * E::kBytes, k, p.K) : E::zero(), x);
+      E::unpack((i < nI && k < p.K) ? E::load_raw(A + (int64_t)(m0 + i) * p.lda * E::kBytes, k, p.K) : E::zero(), x);
 #pragma unroll
       for (int q = 0; q < 8; ++q) { s[q] += x[q]; a[q] = __fadd_ru(a[q], fabsf(x[q])); }
     }
-    *reinterpret_cast<float4*>(&red_s[warp][lane * 8]) = make_float4(s[0], s[1], s[2], s[3]);
-    *reinterpret_cast<float4*>(&red_s[warp][lane * 8 + 4]) = make_float4(s[4], s[5], s[6], s[7]);
-    *reinterpret_cast<float4*>(&red_a[warp][lane * 8]) = make_float4(a[0], a[1], a[2], a[3]);
-    *reinterpret_cast<float4*>(&red_a[warp][lane * 8 + 4]) = make_float4(a[4], a[5], a[6], a[7]);
+    *reinterpret_cast<float4*>(&red_s[rg][oct * 8]) = make_float4(s[0], s[1], s[2], s[3]);
+    *reinterpret_cast<float4*>(&red_s[rg][oct * 8 + 4]) = make_float4(s[4], s[5], s[6], s[7]);
+    *reinterpret_cast<float4*>(&red_a[rg][oct * 8]) = make_float4(a[0], a[1], a[2], a[3]);
+    *reinterpret_cast<float4*>(&red_a[rg][oct * 8 + 4]) = make_float4(a[4], a[5], a[6], a[7]);
     __syncthreads();
-    float S = 0.f, Aab = 0.f;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) { S += red_s[w][tk]; Aab = __fadd_ru(Aab, red_a[w][tk]); }
-    const int64_t kk = (int64_t)blockIdx.x * kColsumK + tk;
-    if (kk < p.K) {
-      p.sA[(int64_t)mt * p.sa_pitch + kk] = S;
-      p.absSA[(int64_t)mt * p.sa_pitch + kk] = Aab;
+    if (t < kColsumK) {
+      float S = 0.f, Aab = 0.f;
+      for (int g = 0; g < 32; ++g) { S += red_s[g][t]; Aab = __fadd_ru(Aab, red_a[g][t]); }
+      const int64_t kk = (int64_t)blockIdx.x * kColsumK + t;
+      if (kk < p.K) {
+        p.sA[(int64_t)mt * p.sa_pitch + kk] = S;
+        p.absSA[(int64_t)mt * p.sa_pitch + kk] = Aab;
+      }
     }
     __syncthreads();  // the reduction arrays are reused by the next pending tile
   }
