@@ -41,6 +41,7 @@
 #include <cuda_fp8.h>
 
 #include "ft_device.cuh"
+#include "ft_pair.cuh"
 #include "ft_internal.h"
 #include "ft_tc.h"
 #include "ft_tc_elem.cuh"

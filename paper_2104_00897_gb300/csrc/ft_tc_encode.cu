@@ -19,8 +19,8 @@ constexpr int BM = kTcBM;             // 128 rows of A per block (the tile's row
 // Encode pre-pass (bandwidth-bound): one read of A and one read of B. Kernel-frame A is
 // M x K and B is K x N, both K-contiguous, so each is a set of K-contiguous lines: the
 // rows of A, the columns of B. A CTA takes a block of L lines (the 128 rows of a tile of
-// A, the 248 columns of a tile of B) and ENC_KC consecutive k. Lane l of warp w loads
-// k0 + 8l .. k0 + 8l + 7 (one 16- or 8-byte load per line) of lines w, w + 8, w + 16, ...;
+// A, the 248 columns of a tile of B) and 256 (BF16) or 512 (E4M3) consecutive k. Lane l of
+// warp w loads 16 bytes of k per line (8 BF16 or 16 E4M3 elements) of lines w, w + 8, ...;
 // the eight warps' partial sums meet in shared memory. From A it forms only what every
 // tile's row check needs, sum_k |A(i,k)| per row; e^T A per row block, which only the
 // lazy column side of a mismatching tile uses, is formed after the GEMM for those tiles'
@@ -29,8 +29,14 @@ constexpr int BM = kTcBM;             // 128 rows of A per block (the tile's row
 // the sum of magnitudes in any order, is a term of the thresholds. Sums of magnitudes round
 // upward, so they bound the exact sums.
 // ---------------------------------------------------------------------------------------
-constexpr int ENC_KC = 256;   // k per CTA: 32 lanes x 8
 constexpr int ENC_WARPS = 8;
+// Elements per lane and line (one 16-byte load: 8 BF16 or 16 E4M3 codes) and k per CTA.
+template <int KIND>
+struct EncVec {
+  static constexpr int kV = KIND == 1 ? 16 : 8;
+  static constexpr int kKC = 32 * kV;
+};
+constexpr int enc_kc(int kind) { return kind == 1 ? EncVec<1>::kKC : EncVec<0>::kKC; }
 
 // Lane l holds la[u], a partial sum for line u of a group of 8 lines. Returns the upward
 // sum over the 32 lanes of line (l >> 2): recursive halving, 9 shuffles.
@@ -52,11 +58,12 @@ __device__ __forceinline__ float reduce_scatter8_up(const float (&la)[8], int la
   return __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, 1));
 }
 
-// s[q] += x[q] for q < 8, two lanes of binary32 per instruction (add.rn.f32x2): each sum
-// takes the same values in the same order as eight scalar additions.
-__device__ __forceinline__ void add_f32x8(float (&s)[8], const float (&x)[8]) {
+// s[q] += x[q] for q < N, two lanes of binary32 per instruction (add.rn.f32x2): each sum
+// takes the same values in the same order as N scalar additions.
+template <int N>
+__device__ __forceinline__ void add_f32x2n(float (&s)[N], const float (&x)[N]) {
 #pragma unroll
-  for (int q = 0; q < 8; q += 2) {
+  for (int q = 0; q < N; q += 2) {
     unsigned long long a = (static_cast<unsigned long long>(__float_as_uint(s[q + 1])) << 32) | __float_as_uint(s[q]);
     const unsigned long long b =
         (static_cast<unsigned long long>(__float_as_uint(x[q + 1])) << 32) | __float_as_uint(x[q]);
@@ -83,64 +90,93 @@ struct EncArgs {
 
 // Shared memory of one encode CTA, declared once per kernel (both roles use it): the
 // float4 stores into the reduction arrays need their 16-byte alignment.
+template <int KC>
 struct __align__(16) EncSmem {
-  float red_s[ENC_WARPS][ENC_KC];
-  float red_a[ENC_WARPS][ENC_KC];
+  float red_s[ENC_WARPS][KC];
+  float red_a[ENC_WARPS][KC];
   int last_chunk;
 };
 
+// kV consecutive elements of one K-contiguous line from k (a multiple of kV), zero at and
+// beyond K: one 16-byte load (ld a multiple of 16 bytes, base 16-byte aligned).
+template <int KIND>
+__device__ __forceinline__ uint4 load_line16(const uint8_t* line, int64_t k, int32_t K) {
+  constexpr int V = EncVec<KIND>::kV, EB = Elem<KIND>::kBytes;
+  if (k + V <= K) return *reinterpret_cast<const uint4*>(line + k * EB);
+  uint32_t t[4] = {0u, 0u, 0u, 0u};
+  for (int q = 0; q < V; ++q)
+    if (k + q < K) {
+      const uint32_t v = EB == 2 ? reinterpret_cast<const uint16_t*>(line)[k + q] : line[k + q];
+      t[(q * EB) >> 2] |= v << (8 * ((q * EB) & 3));
+    }
+  return make_uint4(t[0], t[1], t[2], t[3]);
+}
+template <int KIND>
+__device__ __forceinline__ void unpack16(const uint4 w, float (&x)[EncVec<KIND>::kV]) {
+  if constexpr (KIND == 0) {
+    float y[8];
+    Elem<0>::unpack(w, y);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = y[q];
+  } else {
+    float y[8];
+    Elem<1>::unpack(make_uint2(w.x, w.y), y);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = y[q];
+    Elem<1>::unpack(make_uint2(w.z, w.w), y);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[8 + q] = y[q];
+  }
+}
+
 template <bool kRowsOfA, int KIND>
-__device__ __forceinline__ void encode_block(const EncArgs& g, int blk, int kc, EncSmem& sm) {
-  using E = Elem<KIND>;
+__device__ __forceinline__ void encode_block(const EncArgs& g, int blk, int kc, EncSmem<EncVec<KIND>::kKC>& sm) {
+  constexpr int V = EncVec<KIND>::kV, KC = EncVec<KIND>::kKC;
   auto& red_s = sm.red_s;
   auto& red_a = sm.red_a;
   int& last_chunk = sm.last_chunk;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t line0 = (int64_t)blk * g.L;
   const int nI = (int)min((int64_t)g.L, (int64_t)g.nlines - line0);
-  const int64_t k = (int64_t)kc * ENC_KC + lane * 8;
+  const int64_t k = (int64_t)kc * KC + lane * V;
   const uint8_t* X = static_cast<const uint8_t*>(g.X);
-  float s[8], a[8];
+  constexpr int EB = Elem<KIND>::kBytes;
+  float s[V], a[V];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) { s[q] = 0.f; a[q] = 0.f; }
+  for (int q = 0; q < V; ++q) { s[q] = 0.f; a[q] = 0.f; }
   const int T = (nI + ENC_WARPS - 1) / ENC_WARPS;  // lines per warp, rounded up
-  // 8-line groups loaded per iteration: 128 bytes in flight per lane for both kinds
-  constexpr int kGroups = 2 / E::kBytes;
-  for (int t0 = 0; t0 < T; t0 += 8 * kGroups) {
-    typename E::Raw raw[8 * kGroups];
+  // 8 lines loaded per iteration: 128 bytes in flight per lane
+  for (int t0 = 0; t0 < T; t0 += 8) {
+    uint4 raw[8];
 #pragma unroll
-    for (int u = 0; u < 8 * kGroups; ++u) {
+    for (int u = 0; u < 8; ++u) {
       const int l = warp + ENC_WARPS * (t0 + u);
-      raw[u] = (l < nI && k < g.K) ? E::load_raw(X + (line0 + l) * g.ld * E::kBytes, k, g.K) : E::zero();
+      raw[u] = (l < nI && k < g.K) ? load_line16<KIND>(X + (line0 + l) * g.ld * EB, k, g.K) : make_uint4(0u, 0u, 0u, 0u);
     }
+    float la[8];
 #pragma unroll
-    for (int gq = 0; gq < kGroups; ++gq) {
-      float la[8];
+    for (int u = 0; u < 8; ++u) {
+      float x[V];
+      unpack16<KIND>(raw[u], x);
+      float lsum = 0.f;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        float x[8];
-        E::unpack(raw[8 * gq + u], x);
-        float lsum = 0.f;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          if (kRowsOfA) {
-            lsum = __fadd_ru(lsum, fabsf(x[q]));
-          } else {
-            a[q] = __fadd_ru(a[q], fabsf(x[q]));
-          }
+      for (int q = 0; q < V; ++q) {
+        if (kRowsOfA) {
+          lsum = __fadd_ru(lsum, fabsf(x[q]));
+        } else {
+          a[q] = __fadd_ru(a[q], fabsf(x[q]));
         }
-        if (!kRowsOfA) add_f32x8(s, x);
-        la[u] = lsum;
       }
-      if (kRowsOfA) {
-        const float v = reduce_scatter8_up(la, lane);
-        const int l = warp + ENC_WARPS * (t0 + 8 * gq + (lane >> 2));
-        if ((lane & 3) == 0 && l < nI) g.line_part[(int64_t)kc * g.nlines + line0 + l] = v;
-      }
+      if (!kRowsOfA) add_f32x2n(s, x);
+      la[u] = lsum;
+    }
+    if (kRowsOfA) {
+      const float v = reduce_scatter8_up(la, lane);
+      const int l = warp + ENC_WARPS * (t0 + (lane >> 2));
+      if ((lane & 3) == 0 && l < nI) g.line_part[(int64_t)kc * g.nlines + line0 + l] = v;
     }
   }
   const int tk = threadIdx.x;
-  const int64_t kk = (int64_t)kc * ENC_KC + tk;
   if (kRowsOfA) {
     // (e^T A and sum_i |A(i,k)| per row block are formed only for the row blocks of tiles
     // that reach the resolve pass: tc_colsum_kernel)
@@ -160,15 +196,21 @@ __device__ __forceinline__ void encode_block(const EncArgs& g, int blk, int kc, 
       }
     }
   } else {
-    *reinterpret_cast<float4*>(&red_s[warp][lane * 8]) = make_float4(s[0], s[1], s[2], s[3]);
-    *reinterpret_cast<float4*>(&red_s[warp][lane * 8 + 4]) = make_float4(s[4], s[5], s[6], s[7]);
-    *reinterpret_cast<float4*>(&red_a[warp][lane * 8]) = make_float4(a[0], a[1], a[2], a[3]);
-    *reinterpret_cast<float4*>(&red_a[warp][lane * 8 + 4]) = make_float4(a[4], a[5], a[6], a[7]);
-    __syncthreads();
-    float S = 0.f, Aab = 0.f;
 #pragma unroll
-    for (int w = 0; w < ENC_WARPS; ++w) { S += red_s[w][tk]; Aab = __fadd_ru(Aab, red_a[w][tk]); }
-    if (kk < g.K) {
+    for (int q = 0; q < V; q += 4) {
+      *reinterpret_cast<float4*>(&red_s[warp][lane * V + q]) = make_float4(s[q], s[q + 1], s[q + 2], s[q + 3]);
+      *reinterpret_cast<float4*>(&red_a[warp][lane * V + q]) = make_float4(a[q], a[q + 1], a[q + 2], a[q + 3]);
+    }
+    __syncthreads();
+    float mx = 0.f;
+#pragma unroll
+    for (int t2 = tk; t2 < KC; t2 += ENC_WARPS * 32) {  // one or two k per thread
+      const int64_t kk = (int64_t)kc * KC + t2;
+      float S = 0.f, Aab = 0.f;
+#pragma unroll
+      for (int w = 0; w < ENC_WARPS; ++w) { S += red_s[w][t2]; Aab = __fadd_ru(Aab, red_a[w][t2]); }
+      if (kk >= g.K) continue;
+      mx = fmaxf(mx, Aab);
       if (KIND == 0) {
         // three bfloat16 pieces, each the nearest bfloat16 of what the previous ones leave:
         // together they hold the binary32 sum exactly (8 + 8 + 8 significand bits)
@@ -201,7 +243,6 @@ __device__ __forceinline__ void encode_block(const EncArgs& g, int blk, int kc, 
         }
       }
     }
-    float mx = kk < g.K ? Aab : 0.f;
 #pragma unroll
     for (int w = 16; w >= 1; w >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, w));
     if (lane == 0) atomicMax(reinterpret_cast<unsigned int*>(&g.maxAbsBe[blk]), __float_as_uint(mx));
@@ -211,8 +252,8 @@ __device__ __forceinline__ void encode_block(const EncArgs& g, int blk, int kc, 
 // One launch for both operands: blocks x < nMb encode row blocks of A, the rest column
 // blocks of B, so the two reads overlap.
 template <int KIND>
-__global__ void __launch_bounds__(256) encode_kernel(EncArgs ga, EncArgs gb, int nMb) {
-  __shared__ EncSmem sm;
+__global__ void __launch_bounds__(256, 3) encode_kernel(EncArgs ga, EncArgs gb, int nMb) {
+  __shared__ EncSmem<EncVec<KIND>::kKC> sm;
   if ((int)blockIdx.x < nMb) encode_block<true, KIND>(ga, blockIdx.x, blockIdx.y, sm);
   else encode_block<false, KIND>(gb, blockIdx.x - nMb, blockIdx.y, sm);
 }
@@ -244,7 +285,7 @@ int64_t tc_kpitch(int32_t K) { return (K + 15) / 16 * 16; }
 size_t tc_workspace_bytes(int32_t M, int32_t N, int32_t K, int kind) {
   const int64_t bn = tc_bn_prot(kind), chk = tc_chk_rows(kind);
   const int64_t nMb = (M + BM - 1) / BM, nNb = (N + bn - 1) / bn;
-  const int64_t kpitch = tc_kpitch(K), nkc = (K + ENC_KC - 1) / ENC_KC;
+  const int64_t kpitch = tc_kpitch(K), nkc = (K + enc_kc(kind) - 1) / enc_kc(kind);
   const int64_t eb = kind == 0 ? 2 : 1;
   auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
   return up(nNb * chk * kpitch * eb) + up(nMb * kpitch * 4) + up(nMb * kpitch * 4) + up(M * 4) +
@@ -254,7 +295,7 @@ size_t tc_workspace_bytes(int32_t M, int32_t N, int32_t K, int kind) {
 TcWorkspace tc_workspace_carve(void* base, int32_t M, int32_t N, int32_t K, int kind) {
   const int64_t bn = tc_bn_prot(kind), chk = tc_chk_rows(kind);
   const int64_t nMb = (M + BM - 1) / BM, nNb = (N + bn - 1) / bn;
-  const int64_t kpitch = tc_kpitch(K), nkc = (K + ENC_KC - 1) / ENC_KC;
+  const int64_t kpitch = tc_kpitch(K), nkc = (K + enc_kc(kind) - 1) / enc_kc(kind);
   const int64_t eb = kind == 0 ? 2 : 1;
   auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
   char* c = static_cast<char*>(base);
@@ -277,7 +318,7 @@ TcWorkspace tc_workspace_carve(void* base, int32_t M, int32_t N, int32_t K, int 
 template <int KIND>
 static void launch_encode_kind(const TcParams& p, const TcWorkspace& w, cudaStream_t st) {
   constexpr int bn = tc_bn_prot(KIND);
-  const int nMb = (p.M + BM - 1) / BM, nNb = (p.N + bn - 1) / bn, nkc = (p.K + ENC_KC - 1) / ENC_KC;
+  const int nMb = (p.M + BM - 1) / BM, nNb = (p.N + bn - 1) / bn, nkc = (p.K + EncVec<KIND>::kKC - 1) / EncVec<KIND>::kKC;
   EncArgs ga, gb;
   std::memset(&ga, 0, sizeof(ga));
   ga.X = p.A; ga.ld = p.lda; ga.nlines = p.M; ga.K = p.K; ga.L = BM; ga.nkc = nkc;
