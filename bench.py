@@ -478,7 +478,9 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
     k_ft, k_na = kernel_ms.get((True, False)), kernel_ms.get((False, False))
     roof = None
     if k_ft:
-        prof = f"tc_gemm_kernel_{kind}_ft_{n}_dram"
+        pair = fb.tc_cta_group(True) == 2
+        kname = "tc_gemm_pair_kernel" if pair else "tc_gemm_kernel"
+        prof = f"{kname}_{kind}_ft_{n}_dram"
         peak_sus = pk["bf16_sustained"] * (2.0 if fp8 else 1.0)
         roof = {"bound": "tensor", "achieved": flops / k_ft / 1e9, "peak": peak, "unit": "TFLOP/s",
                 "frac": flops / k_ft / 1e9 / peak,
@@ -487,8 +489,8 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
                 "peak_sustained": peak_sus, "frac_sustained": flops / k_ft / 1e9 / peak_sus,
                 "traffic": profile_traffic(prof, TC_KERNEL_SOURCES),
                 "peak_source": pk["bf16_src"] + (" x 2 (nominal FP8:BF16 dense ratio 4.5/2.25)" if fp8 else ""),
-                "kernel": f"tc_gemm_kernel<FT, {kind.upper()}> (protected product kernel, "
-                          + ("CTA pairs, cta_group::2" if fb.tc_cta_group(True) == 2 else "one CTA per tile")
+                "kernel": f"{kname}<FT, {kind.upper()}> (protected product kernel, "
+                          + ("CTA pairs, cta_group::2" if pair else "one CTA per tile")
                           + "; encode and resolve kernels excluded)", "kernel_ms": k_ft,
                 "noabft_kernel_frac": (flops / k_na / 1e9 / peak) if k_na else None}
     values = ("N(0,1) quantised per tensor to E4M3 (scale = amax/448)" if fp8

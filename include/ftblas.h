@@ -418,8 +418,8 @@ int ftblas_set_fp64_engine(int engine);
 /* Library control, no counterpart in the paper. Tensor-core (BF16, FP8) product kernel: 2 =
  * a pair of CTAs on one TPC computes each 256 x 256 product with cta_group::2 MMAs, each CTA
  * staging its own 128 rows of A and half of the B columns; 1 = one CTA per 128 x 256
- * product; 0 = the faster form measured on GB300 for each call (the default: one CTA for
- * protected calls, CTA pairs for unprotected ones). Both verify, locate and correct per
+ * product; 0 = the faster form measured on GB300 (the default: CTA pairs, for protected and
+ * unprotected calls). Both verify, locate and correct per
  * 128 x 248 tile (the verification interval of ftblas_verification_tile is the same), so
  * reports do not depend on the form; values agree within the accumulation bound. Returns the
  * previous setting, or -1 for a value other than 0, 1 or 2. Process-wide. */

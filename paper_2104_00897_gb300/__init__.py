@@ -257,7 +257,7 @@ def tc_cta_group(protected=True):
     """The tensor-core kernel form a call takes (1: one CTA per tile, 2: CTA pairs)."""
     cur = ftblas_set_tc_cta_group(0)
     ftblas_set_tc_cta_group(cur)
-    return cur if cur != 0 else (1 if protected else 2)
+    return cur if cur != 0 else 2
 
 
 def ftblas_set_fp64_tile(edge):

@@ -557,6 +557,85 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
+// The CTA pair's single-thread loops, the MMA issue (even CTA) and the TMA producer (each
+// CTA), are kept out of line (__noinline__). The loops themselves are unchanged; measured, the
+// pair kernel then runs 3-10% faster for BF16 and FP8 operands, protected or not, which we
+// attribute to instruction fetch (the epilogue warps' verification code is long).
+//
+// The MMA issue loop.
+template <bool FT, int KIND>
+__device__ __noinline__ void pair_mma_loop(const TcParams& p, TcSmem<2>& sm, uint32_t tmem, int unit0, int ustep, int nunits, int nUb, int nNb, int nk) {
+  constexpr int BN = TcGeom<FT, KIND>::BN;
+  constexpr int STAGES = TcStage<2>::kStages;
+  // kind::f16 with BF16 operands (format 1), or kind::f8f6f4 with E4M3 operands (format 0)
+  constexpr uint32_t fmt = KIND == 0 ? 1u : 0u;
+  uint32_t it = 0, lt = 0;
+  bool ok = true;
+  for (int unit = unit0; unit < nunits && ok; unit += ustep, ++lt) {
+    int mu, nt;
+    tile_coords(unit, nUb, nNb, kGroupRows / (2 * BM), mu, nt);
+    const uint32_t idesc = umma_idesc(fmt, fmt, 2 * BM, pair_shape<FT>(min(BN, p.N - nt * BN)).n);
+    const uint32_t b = lt & 1, ub = lt >> 1;
+    if (ub > 0 && !mbar_wait_bounded(&sm.tempty[b], (ub - 1) & 1, p.wait_limit_ns)) { sm.timeout = 1; break; }
+    tc_fence_after();
+    const uint32_t dcol = tmem + b * BNM;
+    for (int kt = 0; kt < nk; ++kt, ++it) {
+      const uint32_t s = it % STAGES, u = it / STAGES;
+      if (!mbar_wait_bounded(&sm.full[s], u & 1, p.wait_limit_ns)) { sm.timeout = 1; ok = false; break; }
+      tc_fence_after();
+      const uint32_t a0 = smem_addr(sm.a[s]), b0 = smem_addr(sm.b[s]);
+#pragma unroll
+      for (int kk = 0; kk < BKB / 32; ++kk) {  // one MMA per 32 bytes of K
+        const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
+        const uint64_t ad = umma_desc_sw128(a0 + kk * 32), bd = umma_desc_sw128(b0 + kk * 32);
+        if (KIND == 0) umma_bf16_pair(dcol, ad, bd, idesc, accum);
+        else umma_f8_pair(dcol, ad, bd, idesc, accum);
+      }
+      umma_commit_pair(&sm.empty[s]);
+    }
+    // a wait gave up: the accumulator is incomplete, so the unit is never handed to the
+    // epilogues (whose own waits then give up and leave the tiles unstored)
+    if (!ok) break;
+    umma_commit_pair(&sm.tfull[b]);
+  }
+}
+
+// The TMA producer loop (one thread per CTA).
+template <bool FT, int KIND>
+__device__ __noinline__ void pair_tma_loop(const TcParams& p, TcSmem<2>& sm, const CUtensorMap* pA, const CUtensorMap* pB, const CUtensorMap* pB2, const CUtensorMap* pChk, int rank, int unit0, int ustep, int nunits, int nUb, int nNb, int nk, int bk_elems) {
+  constexpr int BN = TcGeom<FT, KIND>::BN, CHK = TcGeom<FT, KIND>::CHK;
+  constexpr int STAGES = TcStage<2>::kStages, BROWS = TcStage<2>::kBRows;
+  tma_prefetch_desc(pA);
+  tma_prefetch_desc(pB);
+  if (FT) { tma_prefetch_desc(pB2); tma_prefetch_desc(pChk); }
+  uint32_t it = 0;
+  bool ok = true;
+  for (int unit = unit0; unit < nunits && ok; unit += ustep) {
+    int mu, nt;
+    tile_coords(unit, nUb, nNb, kGroupRows / (2 * BM), mu, nt);
+    const int mt = 2 * mu + rank;
+    const int n0 = nt * BN;
+    const PairShape g = pair_shape<FT>(min(BN, p.N - n0));
+    // bytes of both CTAs' loads, expected on the even CTA's barrier
+    const uint32_t bytes = (2 * BM + BROWS + (FT ? (g.b1_data ? BROWS : CHK) : BROWS)) * BKB;
+    for (int kt = 0; kt < nk; ++kt, ++it) {
+      const uint32_t s = it % STAGES, u = it / STAGES;
+      if (u > 0 && !mbar_wait_bounded(&sm.empty[s], (u - 1) & 1, p.wait_limit_ns)) { sm.timeout = 1; ok = false; break; }
+      const int k0 = kt * bk_elems;
+      const uint32_t fbar = mapa_shared(smem_addr(&sm.full[s]), 0);
+      if (rank == 0) mbar_arrive_expect_tx(&sm.full[s], bytes + stall_bytes(p, mu, 2 * BM, nt, kt, nk, BN));
+      // rows beyond M (an odd CTA past the last row tile) read the fill value, zero
+      tma_load_2d_pair(sm.a[s], pA, fbar, k0, mt * BM);
+      if (rank == 0) {
+        tma_load_2d_pair(sm.b[s], pB, fbar, k0, n0);
+      } else {
+        if (g.b1_data) tma_load_2d_pair(sm.b[s], FT ? pB2 : pB, fbar, k0, n0 + g.b1_row);
+        if (FT) tma_load_2d_pair(sm.b[s] + (g.b1_data ? BROWS - CHK : 0) * BKB, pChk, fbar, k0, nt * CHK);
+      }
+    }
+  }
+}
+
 // CTA-pair kernel (cta_group::2): a thread-block cluster of two CTAs on one TPC computes each
 // 256 x 256 product. Each CTA stages its own 128 rows of A and half of B^r (128 rows: the even
 // CTA data columns 0..127, the odd CTA the rest and the checksum rows, as pair_shape gives),
@@ -603,72 +682,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
-    if (lane == 0) {
-      tma_prefetch_desc(&tmA);
-      tma_prefetch_desc(&tmB);
-      if (FT) { tma_prefetch_desc(&tmB2); tma_prefetch_desc(&tmChk); }
-      uint32_t it = 0;
-      bool ok = true;
-      for (int unit = unit0; unit < nunits && ok; unit += ustep) {
-        int mu, nt;
-        tile_coords(unit, nUb, nNb, kGroupRows / (2 * BM), mu, nt);
-        const int mt = 2 * mu + rank;
-        const int n0 = nt * BN;
-        const PairShape g = pair_shape<FT>(min(BN, p.N - n0));
-        // bytes of both CTAs' loads, expected on the even CTA's barrier
-        const uint32_t bytes = (2 * BM + BROWS + (FT ? (g.b1_data ? BROWS : CHK) : BROWS)) * BKB;
-        for (int kt = 0; kt < nk; ++kt, ++it) {
-          const uint32_t s = it % STAGES, u = it / STAGES;
-          if (u > 0 && !mbar_wait_bounded(&sm.empty[s], (u - 1) & 1, p.wait_limit_ns)) { sm.timeout = 1; ok = false; break; }
-          const int k0 = kt * bk_elems;
-          const uint32_t fbar = mapa_shared(smem_addr(&sm.full[s]), 0);
-          if (rank == 0) mbar_arrive_expect_tx(&sm.full[s], bytes + stall_bytes(p, mu, 2 * BM, nt, kt, nk, BN));
-          // rows beyond M (an odd CTA past the last row tile) read the fill value, zero
-          tma_load_2d_pair(sm.a[s], &tmA, fbar, k0, mt * BM);
-          if (rank == 0) {
-            tma_load_2d_pair(sm.b[s], &tmB, fbar, k0, n0);
-          } else {
-            if (g.b1_data) tma_load_2d_pair(sm.b[s], FT ? &tmB2 : &tmB, fbar, k0, n0 + g.b1_row);
-            if (FT) tma_load_2d_pair(sm.b[s] + (g.b1_data ? BROWS - CHK : 0) * BKB, &tmChk, fbar, k0, nt * CHK);
-          }
-        }
-      }
-    }
+    if (lane == 0) pair_tma_loop<FT, KIND>(p, sm, &tmA, &tmB, &tmB2, &tmChk, rank, unit0, ustep, nunits, nUb, nNb, nk, bk_elems);
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issue (even CTA)
-    if (lane == 0 && rank == 0) {
-      // kind::f16 with BF16 operands (format 1), or kind::f8f6f4 with E4M3 operands (format 0)
-      constexpr uint32_t fmt = KIND == 0 ? 1u : 0u;
-      uint32_t it = 0, lt = 0;
-      bool ok = true;
-      for (int unit = unit0; unit < nunits && ok; unit += ustep, ++lt) {
-        int mu, nt;
-        tile_coords(unit, nUb, nNb, kGroupRows / (2 * BM), mu, nt);
-        const uint32_t idesc = umma_idesc(fmt, fmt, 2 * BM, pair_shape<FT>(min(BN, p.N - nt * BN)).n);
-        const uint32_t b = lt & 1, ub = lt >> 1;
-        if (ub > 0 && !mbar_wait_bounded(&sm.tempty[b], (ub - 1) & 1, p.wait_limit_ns)) { sm.timeout = 1; break; }
-        tc_fence_after();
-        const uint32_t dcol = tmem + b * BNM;
-        for (int kt = 0; kt < nk; ++kt, ++it) {
-          const uint32_t s = it % STAGES, u = it / STAGES;
-          if (!mbar_wait_bounded(&sm.full[s], u & 1, p.wait_limit_ns)) { sm.timeout = 1; ok = false; break; }
-          tc_fence_after();
-          const uint32_t a0 = smem_addr(sm.a[s]), b0 = smem_addr(sm.b[s]);
-#pragma unroll
-          for (int kk = 0; kk < BKB / 32; ++kk) {  // one MMA per 32 bytes of K
-            const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
-            const uint64_t ad = umma_desc_sw128(a0 + kk * 32), bd = umma_desc_sw128(b0 + kk * 32);
-            if (KIND == 0) umma_bf16_pair(dcol, ad, bd, idesc, accum);
-            else umma_f8_pair(dcol, ad, bd, idesc, accum);
-          }
-          umma_commit_pair(&sm.empty[s]);
-        }
-        // a wait gave up: the accumulator is incomplete, so the unit is never handed to the
-        // epilogues (whose own waits then give up and leave the tiles unstored)
-        if (!ok) break;
-        umma_commit_pair(&sm.tfull[b]);
-      }
-    }
+    if (lane == 0 && rank == 0) pair_mma_loop<FT, KIND>(p, sm, tmem, unit0, ustep, nunits, nUb, nNb, nk);
   } else {
     // ------------------------------------------------------------ epilogue (warps 2..5)
     const int q = warp & 3;                 // TMEM lane quarter of this warp

@@ -756,9 +756,9 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   // 2 s per bounded wait (a whole tile takes about 0.1 ms); 20 ms with a stall point planned
   p.wait_limit_ns = stall ? 20000000ull : 2000000000ull;
   // one CTA per 128-row tile, or a CTA pair per 256 rows (B staged half in each CTA); by
-  // default the faster form measured for each (protected: one CTA; unprotected: pairs)
+  // default the pairs, the faster form measured for protected and unprotected calls alike
   const int cg_set = g_tc_cta_group.load();
-  const int cg = cg_set != 0 ? cg_set : (ft ? 1 : 2);
+  const int cg = cg_set != 0 ? cg_set : 2;
   TcMaps maps;
   std::memset(&maps, 0, sizeof(maps));
   const uint32_t b_rows = cg == 2 ? kTcBN / 2 : (ft ? (uint32_t)bnp : kTcBN);

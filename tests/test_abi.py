@@ -101,7 +101,7 @@ def test_verification_tile_and_engine_switch():
     assert prev == 0 and fb.tc_cta_group(True) == 2
     assert fb.ftblas_verification_tile(fb.COL_MAJOR, fb.R_16BF, 8192, 8192, 8192) == (128, 248, 64)
     assert fb.ftblas_set_tc_cta_group(prev) == 2
-    assert fb.tc_cta_group(True) == 1 and fb.tc_cta_group(False) == 2
+    assert fb.tc_cta_group(True) == 2 and fb.tc_cta_group(False) == 2
 
 
 def test_every_declaration_cites_its_passage():
