@@ -416,25 +416,42 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
         npairs = max(steps, min(8192, int(4500.0 / max(e0.elapsed_time(e1), 1e-3)) + 1))
         # each step: unprotected (the library's fastest form), protected, and unprotected in
         # the protected call's kernel form (the same-kernel overhead)
+        # (when both calls take the same form by default, the third call is left out)
         ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4)) for _ in range(npairs)]
         reps = [fb.new_report(dev) for _ in range(npairs)]
         ft_form = fb.tc_cta_group(True)
+        same = ft_form == fb.tc_cta_group(False)
         for i in range(npairs):
             ev[i][0].record()
             call(False)
             ev[i][1].record()
             call(True, reps[i])
             ev[i][2].record()
-            prev = fb.ftblas_set_tc_cta_group(ft_form)
-            call(False)
-            fb.ftblas_set_tc_cta_group(prev)
-            ev[i][3].record()
+            if not same:
+                prev = fb.ftblas_set_tc_cta_group(ft_form)
+                call(False)
+                fb.ftblas_set_tc_cta_group(prev)
+                ev[i][3].record()
         torch.cuda.synchronize(dev)
         na = sum(a.elapsed_time(b) for a, b, _, _ in ev) / npairs
         ft = sum(b.elapsed_time(c) for _, b, c, _ in ev) / npairs
-        na_same = sum(c.elapsed_time(d) for _, _, c, d in ev) / npairs
+        na_same = na if same else sum(c.elapsed_time(d) for _, _, c, d in ev) / npairs
         det = sum(int(fb.report_from_device(r).detected) for r in reps)
         return na, ft, det, npairs, na_same
+
+    def burst(protect, calls=10):
+        """Mean product-kernel time of a short burst of calls after an idle second: the
+        conditions of the measured burst peak (the best of 10 single GEMMs), before power
+        capping sets in. The long regions above run at the power cap."""
+        fb.ftblas_set_injection(None)
+        torch.cuda.synchronize(dev)
+        time.sleep(1.0)
+        fb.ftblas_kernel_timing_begin()
+        for _ in range(calls):
+            call(protect)
+        torch.cuda.synchronize(dev)
+        _, kms, kn = fb.ftblas_kernel_timing_end()
+        return kms / kn if kn else None
 
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     sampler.__enter__()  # started before the first warm-up; runs through the timed regions
@@ -444,6 +461,7 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
     ms_inj, det_inj, corr_inj = timed(True, True)
     det0 += det_pair
     sampler.__exit__(None, None, None)
+    kb_na, kb_ft = burst(False), burst(True)
     # accuracy against the FP64 product of the same operands, on a sampled 4 x 64 block
     call(True)
     torch.cuda.synchronize(dev)
@@ -477,22 +495,26 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
     peak = pk["bf16"] * (2.0 if fp8 else 1.0)
     k_ft, k_na = kernel_ms.get((True, False)), kernel_ms.get((False, False))
     roof = None
-    if k_ft:
+    if k_ft and kb_ft:
         pair = fb.tc_cta_group(True) == 2
         kname = "tc_gemm_pair_kernel" if pair else "tc_gemm_kernel"
         prof = f"{kname}_{kind}_ft_{n}_dram"
         peak_sus = pk["bf16_sustained"] * (2.0 if fp8 else 1.0)
-        roof = {"bound": "tensor", "achieved": flops / k_ft / 1e9, "peak": peak, "unit": "TFLOP/s",
-                "frac": flops / k_ft / 1e9 / peak,
-                # the timed region runs tens of calls back to back: the seconds-long measured
-                # figure (power-capped) is the other bound of the denominator
-                "peak_sustained": peak_sus, "frac_sustained": flops / k_ft / 1e9 / peak_sus,
+        # each kernel time against the peak measured under the same conditions: a short burst
+        # against the burst peak, the long power-capped region against the sustained peak
+        roof = {"bound": "tensor", "achieved": flops / kb_ft / 1e9, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / kb_ft / 1e9 / peak, "kernel_ms": kb_ft,
+                "timing": "mean product-kernel time of 10 protected calls after 1 s idle (burst, as the peak)",
+                "achieved_sustained": flops / k_ft / 1e9, "peak_sustained": peak_sus,
+                "frac_sustained": flops / k_ft / 1e9 / peak_sus, "kernel_ms_sustained": k_ft,
+                "timing_sustained": "mean product-kernel time over a region of protected calls following "
+                                    "seconds of back-to-back calls (power-capped)",
                 "traffic": profile_traffic(prof, TC_KERNEL_SOURCES),
                 "peak_source": pk["bf16_src"] + (" x 2 (nominal FP8:BF16 dense ratio 4.5/2.25)" if fp8 else ""),
                 "kernel": f"{kname}<FT, {kind.upper()}> (protected product kernel, "
                           + ("CTA pairs, cta_group::2" if pair else "one CTA per tile")
-                          + "; encode and resolve kernels excluded)", "kernel_ms": k_ft,
-                "noabft_kernel_frac": (flops / k_na / 1e9 / peak) if k_na else None}
+                          + "; encode and resolve kernels excluded)",
+                "noabft_kernel_frac": (flops / kb_na / 1e9 / peak) if kb_na else None}
     values = ("N(0,1) quantised per tensor to E4M3 (scale = amax/448)" if fp8
               else "N(0,1), A rows scaled by 2^u (u in [-8, 8])")
     return {
@@ -511,11 +533,12 @@ def run_tc(args, dev, kind, n, steps, warmup, fp64_tflops):
         "undetected_below_threshold": timed_steps[(True, True)] - det_inj,
         "injected_magnitude": f"2^{18 if fp8 else 16}..2^{22 if fp8 else 20} |C(i,j)| at a seeded element per call",
         "clocks": sampler.summary(),
-        "timed_steps": {"alternating_triplets": npairs, "ft_injected": timed_steps[(True, True)]},
-        "method": "ft_tflops, noabft_tflops and the overheads from unprotected, protected and same-form "
-                  "unprotected calls alternated in one region (per-call CUDA events); ft_tflops_injected from a "
-                  "region of injected calls; the roofline from the product-kernel events of a region of "
-                  "protected calls",
+        "timed_steps": {"alternating_steps": npairs, "ft_injected": timed_steps[(True, True)]},
+        "method": "ft_tflops, noabft_tflops and the overheads from unprotected and protected calls (and "
+                  "same-form unprotected calls when the forms differ) alternated in one region (per-call CUDA "
+                  "events); ft_tflops_injected from a region of injected calls; the roofline from the "
+                  "product-kernel events of a short burst after an idle second (burst peak) and of a region "
+                  "of protected calls (sustained peak)",
         "seed": seed,
         "l2": l2_note_tc(2 * n * n * (1 if fp8 else 2), n * n * 4),
         "error_vs_fp64": {"max_over_sum_abs_ab": err_norm, "median_rel": err_rel,
