@@ -258,10 +258,15 @@ int ftblas_dgemm_host(ftblas_layout_t layout, ftblas_trans_t transa, ftblas_tran
  *   A, B, C, compute all FTBLAS_R_64F            -> the same path as ftblas_dgemm;
  *   A, B FTBLAS_R_16BF or both FTBLAS_R_8F_E4M3, compute FTBLAS_R_32F, C FTBLAS_R_32F
  *                                                 -> tcgen05 GEMM, C stored in FP32;
- *   the same with C FTBLAS_R_16BF                  -> the product runs into an FP32 buffer
- *       from the workspace pool (filled from C first when beta != 0), where it is verified,
- *       located and corrected exactly as above; C is then rounded to nearest bfloat16 in
- *       one pass. The checks cover the FP32 values; the final rounding is not checked.
+ *   the same with C FTBLAS_R_16BF                  -> the product is verified, located and
+ *       corrected in FP32 exactly as above, and each element of C is rounded to nearest
+ *       bfloat16 once. With the CTA-pair kernel (the default form) the epilogue reads C_in
+ *       from the bfloat16 C and stores the rounded value there, and a protected call keeps
+ *       the FP32 values in a buffer from the workspace pool for the resolve pass, which
+ *       stores a corrected element in both; with one CTA per tile the product runs into
+ *       that buffer (filled from C first when beta != 0) and C is rounded in one pass at the
+ *       end. Either way C equals the rounding of the FP32 result. The checks cover the FP32
+ *       values; the rounding itself is not checked.
  * a_scale / b_scale (device pointers to one float each) scale FP8 operands and must be
  * NULL otherwise. The tensor-core kernel reads both operands K-contiguous in the
  * column-major kernel frame (column-major: A transposed and B not; row-major: A not

@@ -645,7 +645,7 @@ __device__ __noinline__ void pair_tma_loop(const TcParams& p, TcSmem<2>& sm, con
 // CTA's epilogue verifies and stores its own 128-row tile, so the verification interval, the
 // pending list and the resolve pass are those of the one-CTA kernel. The pair loops over units
 // (256-row block, column block) in the order of tile_coords.
-template <bool FT, int KIND>
+template <bool FT, int KIND, bool CB>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                         const __grid_constant__ CUtensorMap tmB2, const __grid_constant__ CUtensorMap tmChk,
@@ -736,7 +736,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const bool ok = row_ok && col < nJ;
             float acc = __uint_as_float(v[j]);
             float cin = 0.f;
-            if (beta_nz && ok) cin = p.C[gi + gj * p.ldc];
+            if (beta_nz && ok) {
+              if constexpr (CB) cin = __uint_as_float(static_cast<uint32_t>(p.Cb[gi + gj * p.ldcb]) << 16);
+              else cin = p.C[gi + gj * p.ldc];
+            }
             float out;
             if (FT && col == inj_c) {
               out = inject_element(p, alpha, gi, gj, acc, cin, beta_nz);
@@ -744,7 +747,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             } else {
               out = beta_nz ? fmaf(alpha, acc, p.beta * cin) : alpha * acc;
             }
-            if (ok) p.C[gi + gj * p.ldc] = out;
+            if (ok) {
+              if constexpr (CB) {
+                // the bfloat16 C, rounded to nearest once; a protected call also keeps the
+                // FP32 value, which the resolve pass reads and corrects
+                p.Cb[gi + gj * p.ldcb] = __bfloat16_as_ushort(__float2bfloat16_rn(out));
+                if (FT) p.C[gi + gj * p.ldc] = out;
+              } else {
+                p.C[gi + gj * p.ldc] = out;
+              }
+            }
             if (FT) {
               const float o = ok ? out : 0.f;
               neumaier(rs, rc, o);
@@ -1109,6 +1121,7 @@ __device__ void resolve_tile(const TcParams& p, TcPendingEntry& pe, ResolveShare
     before = (double)__ldcg(cp);
     const float fixed = (float)(pe.pred_row - rest);
     *cp = fixed;
+    if (p.Cb != nullptr) p.Cb[gi + gj * p.ldcb] = __bfloat16_as_ushort(__float2bfloat16_rn(fixed));
     after = (double)fixed;
   } else if (nc == 0 && (!recompute_row || ne == 0)) {
     kind = FT_KIND_CHECKSUM_ONLY;
@@ -1175,9 +1188,11 @@ template <bool FT, int KIND>
 static cudaError_t launch_gemm_kind(const TcParams& p, const TcMaps& m, int cg, int sms, cudaStream_t st) {
   const int bn = TcGeom<FT, KIND>::BN;
   const long long nMb = (p.M + BM - 1) / BM, nNb = (p.N + bn - 1) / bn;
+  const bool cb = p.Cb != nullptr;
+  if (cb && cg != 2) return cudaErrorInvalidValue;
   cudaError_t e;
   if (cg == 2) {
-    auto kern = tc_gemm_pair_kernel<FT, KIND>;
+    auto kern = cb ? tc_gemm_pair_kernel<FT, KIND, true> : tc_gemm_pair_kernel<FT, KIND, false>;
     const size_t smem = sizeof(TcSmem<2>);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1193,8 +1208,8 @@ static cudaError_t launch_gemm_kind(const TcParams& p, const TcMaps& m, int cg, 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     // CTA pairs resident at once (one per TPC when nothing else occupies the GPU)
-    static int max_clusters[2][2] = {{0, 0}, {0, 0}};
-    int& mc = max_clusters[FT ? 1 : 0][KIND];
+    static int max_clusters[2][2][2] = {};
+    int& mc = max_clusters[FT ? 1 : 0][KIND][cb ? 1 : 0];
     if (mc == 0) {
       e = cudaOccupancyMaxActiveClusters(&mc, kern, &cfg);
       if (e != cudaSuccess) return e;

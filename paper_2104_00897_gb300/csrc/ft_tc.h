@@ -52,7 +52,9 @@ struct TcParams {
   const float* b_scale;
   const void* A; int64_t lda;
   const void* B; int64_t ldb;
-  float* C; int64_t ldc;
+  float* C; int64_t ldc;          // FP32 C (protected calls with a bfloat16 C: the verified FP32 copy)
+  uint16_t* Cb; int64_t ldcb;     // bfloat16 C (bits) written by the CTA-pair kernel's epilogue and
+                                  // the resolve pass, which also read C_in from it; null for an FP32 C
   const float* rowAbsA;          // [M]        upward sum_k |A(i,k)|
   const float* maxAbsBe;         // [nNb]      max_k upward sum_{j in block} |B(k,j)|
   float* sA;                     // [nMb][sa_pitch] e^T A per 128-row block (binary32 sum), formed after
@@ -91,7 +93,8 @@ cudaError_t launch_decode_e4m3(const uint8_t* codes, float* out, int64_t n, cuda
 struct TcMaps {
   CUtensorMap a, b, b2, chk;
 };
-// cg: 1 (one CTA per 128-row tile) or 2 (a CTA pair per 256 rows, cta_group::2).
+// cg: 1 (one CTA per 128-row tile) or 2 (a CTA pair per 256 rows, cta_group::2). A bfloat16 C
+// (p.Cb) needs cg 2; the one-CTA kernel writes only the FP32 C.
 cudaError_t launch_tc_gemm(const TcParams& p, const TcMaps& m, bool ft, int cg, cudaStream_t st);
 
 // K-major copy of an MN-major operand: dst[r * pitch + k] = src[r + k * ld] for r < R,

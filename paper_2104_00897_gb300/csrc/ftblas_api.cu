@@ -20,7 +20,7 @@ namespace {
 thread_local int g_last_cuda_error = 0;
 thread_local int g_last_used_tma = -1;
 std::atomic<int> g_fp64_engine{kEngineDFMA};
-std::atomic<int> g_tc_cta_group{0};  // 0: by call (protected: one CTA per tile; unprotected: CTA pairs)
+std::atomic<int> g_tc_cta_group{0};  // 0: the library's choice (CTA pairs); 1 or 2 forced
 std::atomic<int> g_fp64_tile{0};  // 0: fp64_tile_edge decides; else the forced DFMA tile edge
 std::atomic<int64_t> g_kc_interval{0};
 std::atomic<int> g_emu_slices{kEmuSlicesDefault};
@@ -632,8 +632,9 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   if (K < 0) return -6;
   if (alpha == nullptr) return -7;
   if (beta == nullptr) return -14;
-  // C in FP32, or in bfloat16 (the product then runs into an FP32 buffer, verified,
-  // located and corrected there, and is rounded to bfloat16 once at the end)
+  // C in FP32, or in bfloat16: the product is verified, located and corrected in FP32 and
+  // rounded to bfloat16 once (by the CTA-pair kernel's epilogue and the resolve pass, or, for
+  // the one-CTA kernel, by a pass over an FP32 buffer at the end)
   const bool c_bf16 = Ctype == FTBLAS_R_16BF && resolve == nullptr;
   const bool c32 = (Ctype == FTBLAS_R_32F || c_bf16) && ctype == FTBLAS_R_32F;
   const bool bf16 = c32 && Atype == FTBLAS_R_16BF && Btype == FTBLAS_R_16BF;
@@ -689,18 +690,27 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   p.kind = kind;
   p.a_scale = fp8 ? (f.swap ? b_scale : a_scale) : nullptr;
   p.b_scale = fp8 ? (f.swap ? a_scale : b_scale) : nullptr;
+  // one CTA per 128-row tile, or a CTA pair per 256 rows (B staged half in each CTA); by
+  // default the pairs, the faster form measured for protected and unprotected calls alike
+  const int cg_set = g_tc_cta_group.load();
+  const int cg = cg_set != 0 ? cg_set : 2;
+  // a bfloat16 C written by the pair kernel itself (the one-CTA kernel writes FP32 only)
+  const bool cb_direct = c_bf16 && cg == 2;
   // K-major, aligned copies of MN-major or misaligned operands (stream-ordered workspace,
   // released at the end)
   void* tws = nullptr;
-  // FP32 product buffer of a bfloat16 C (kernel frame, column-major, leading dimension M)
-  const size_t cbytes = c_bf16 ? (size_t(f.M) * size_t(f.N) * 4 + 255) & ~size_t(255) : 0;
+  // FP32 product buffer of a bfloat16 C (kernel frame, column-major, leading dimension M):
+  // the verified copy the resolve pass reads and corrects; none for an unprotected call
+  // that writes the bfloat16 C directly
+  const bool need_cf = c_bf16 && (ft || !cb_direct);
+  const size_t cbytes = need_cf ? (size_t(f.M) * size_t(f.N) * 4 + 255) & ~size_t(255) : 0;
   float* cf = nullptr;
-  if (copy_a || copy_b || c_bf16) {
+  if (copy_a || copy_b || need_cf) {
     const int64_t pitch = tc_kmajor_pitch(K, eb);
     const size_t abytes = copy_a ? (size_t(f.M * pitch * eb) + 255) & ~size_t(255) : 0;
     const size_t bbytes = copy_b ? (size_t(f.N * pitch * eb) + 255) & ~size_t(255) : 0;
     if (ws_alloc(&tws, abytes + bbytes + cbytes, st) != cudaSuccess) return FTBLAS_STATUS_ALLOC_FAILED;
-    if (c_bf16) cf = reinterpret_cast<float*>(static_cast<uint8_t*>(tws) + abytes + bbytes);
+    if (need_cf) cf = reinterpret_cast<float*>(static_cast<uint8_t*>(tws) + abytes + bbytes);
     uint8_t* base = static_cast<uint8_t*>(tws);
     auto copy = [&](const void* src, int64_t rows, int64_t ld, bool kmajor, uint8_t* dst) {
       if (kmajor)  // rows of K already contiguous: a pitched copy
@@ -727,7 +737,12 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
     return rc;
   };
   p.A = f.A; p.lda = f.lda; p.B = f.B; p.ldb = f.ldb;
-  if (c_bf16) {
+  if (cb_direct) {
+    // the kernel reads C_in from the bfloat16 C and writes it there (and the FP32 copy into
+    // cf when protected)
+    p.C = cf; p.ldc = f.M;
+    p.Cb = static_cast<uint16_t*>(C); p.ldcb = ldc;
+  } else if (c_bf16) {
     p.C = cf; p.ldc = f.M;
     if (be != 0.0f) {
       if (int e = record_cuda(launch_bf16_to_f32(static_cast<const uint16_t*>(C), ldc, cf, f.M, f.M, f.N, st)))
@@ -738,7 +753,8 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   }
   // the bfloat16 C rounded from the FP32 buffer once every pass over it has finished
   auto finish = [&](int rc) {
-    if (rc == 0 && c_bf16) rc = record_cuda(launch_f32_to_bf16(cf, f.M, static_cast<uint16_t*>(C), ldc, f.M, f.N, st));
+    if (rc == 0 && c_bf16 && !cb_direct)
+      rc = record_cuda(launch_f32_to_bf16(cf, f.M, static_cast<uint16_t*>(C), ldc, f.M, f.N, st));
     return release(rc);
   };
   p.report = ft ? report : nullptr;
@@ -755,10 +771,6 @@ int tc_gemm_impl(int layout, int ta, int tb, int64_t M, int64_t N, int64_t K, co
   }
   // 2 s per bounded wait (a whole tile takes about 0.1 ms); 20 ms with a stall point planned
   p.wait_limit_ns = stall ? 20000000ull : 2000000000ull;
-  // one CTA per 128-row tile, or a CTA pair per 256 rows (B staged half in each CTA); by
-  // default the pairs, the faster form measured for protected and unprotected calls alike
-  const int cg_set = g_tc_cta_group.load();
-  const int cg = cg_set != 0 ? cg_set : 2;
   TcMaps maps;
   std::memset(&maps, 0, sizeof(maps));
   const uint32_t b_rows = cg == 2 ? kTcBN / 2 : (ft ? (uint32_t)bnp : kTcBN);

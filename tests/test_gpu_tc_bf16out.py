@@ -1,6 +1,8 @@
 """GPU tests of a bfloat16 C on the tensor-core path (ftblas_gemm_ex with Ctype
-FTBLAS_R_16BF): the product runs into an FP32 buffer where it is verified, located and
-corrected as for an FP32 C, and is rounded to nearest bfloat16 once at the end.
+FTBLAS_R_16BF): the product is verified, located and corrected in FP32 as for an FP32 C, and
+rounded to nearest bfloat16 once: by the CTA-pair kernel's epilogue as it stores each element
+(and by the resolve pass for a corrected one), or, with one CTA per tile, by a pass over an
+FP32 buffer at the end. Each test runs with both kernel forms.
 
 So a bfloat16-C call must give, bit for bit, the nearest bfloat16 of the FP32-C call on the
 same operands (and, for beta != 0, on the same bfloat16 C_in), with the same report and
@@ -27,6 +29,13 @@ def gamma(n, u):
 def bf16_round(x):
     """Nearest bfloat16 of binary32 values (ties to even), as float64."""
     return S.bf16_bits_to_f64(S.to_bf16_bits(np.asarray(x, dtype=np.float32).astype(np.float64)))
+
+
+@pytest.fixture(params=[1, 2], ids=["one_cta", "cta_pair"])
+def cta_group(request):
+    prev = fb.ftblas_set_tc_cta_group(request.param)
+    yield request.param
+    fb.ftblas_set_tc_cta_group(prev)
 
 
 @pytest.fixture(autouse=True)
@@ -118,7 +127,7 @@ CASES = [("bf16", O.COL_MAJOR, 0.0), ("bf16", O.ROW_MAJOR, 0.5), ("fp8", O.COL_M
 
 
 @pytest.mark.parametrize("kind,layout,beta", CASES)
-def test_bf16_c_is_the_rounded_fp32_c(kind, layout, beta):
+def test_bf16_c_is_the_rounded_fp32_c(kind, layout, beta, cta_group):
     P = Problem(kind, 300, 517, 260, layout, beta=beta, seed=31 + layout)
     c32, r32 = P.run(False)
     c16, r16 = P.run(True)
@@ -134,7 +143,7 @@ def test_bf16_c_is_the_rounded_fp32_c(kind, layout, beta):
 
 
 @pytest.mark.parametrize("kind,layout,beta", CASES)
-def test_bf16_c_fault_corrected_in_fp32(kind, layout, beta):
+def test_bf16_c_fault_corrected_in_fp32(kind, layout, beta, cta_group):
     P = Problem(kind, 300, 517, 260, layout, beta=beta, seed=41 + layout)
     clean32, _ = P.run(False)
     i, j = (int(x) for x in np.unravel_index(np.argmax(np.abs(clean32)), clean32.shape))
@@ -148,6 +157,35 @@ def test_bf16_c_fault_corrected_in_fp32(kind, layout, beta):
     assert np.array_equal(g16, bf16_round(g32))
     _, orep = P.oracle(injections=[pt])
     assert record_set(orep) == [(i, j, fb.KIND_CORRECTED)]
+
+
+@pytest.mark.parametrize("kind", ["bf16", "fp8"])
+def test_bf16_c_over_several_rounds(kind, cta_group):
+    """More tiles than one persistent round, a ragged last column block, beta != 0 and one
+    fault: the bfloat16 C is the rounded FP32 C of the same call form, bit for bit."""
+    P = Problem(kind, 2304, 4100, 520, O.COL_MAJOR, beta=0.5, seed=57)
+    clean32, _ = P.run(False)
+    # the largest element of a tile of the ragged last column block (columns 3968..4099)
+    blk = np.abs(clean32[1408:1536, 3968:])
+    di, dj = np.unravel_index(np.argmax(blk), blk.shape)
+    i, j = 1408 + int(di), 3968 + int(dj)
+    pt = dict(i=i, j=j, site=fb.SITE_OUTPUT, mode=fb.MODE_ADD_REL, rel_log2=14, sign=-1)
+    fb.ftblas_set_injection(fb.make_injection(fixed=[pt]))
+    g32, r32 = P.run(False)
+    g16, r16 = P.run(True)
+    fb.ftblas_set_injection(None)
+    assert record_set(r16) == record_set(r32) == [(i, j, fb.KIND_CORRECTED)]
+    assert np.array_equal(g16, bf16_round(g32))
+    others = np.ones_like(g32, dtype=bool)
+    others[i, j] = False
+    assert np.array_equal(g32[others], clean32[others])
+    (r,) = r32.records()
+    assert abs(g32[i, j] - clean32[i, j]) <= r.tau_row + 2.0 ** -21 * abs(clean32[i, j])
+    c16, r = P.run(True)
+    assert np.array_equal(c16, bf16_round(clean32)) and r.detected == 0
+    u32, _ = P.run(False, protect=False)
+    u16, _ = P.run(True, protect=False)
+    assert np.array_equal(u16, bf16_round(u32))
 
 
 def test_bf16_c_scaled_when_there_is_no_product():
