@@ -242,6 +242,21 @@ __device__ __forceinline__ uint32_t stall_bytes(const TcParams& p, int mu, int r
   return 0u;
 }
 
+// The k-tile of unit (mu, nt) at which a stall point (test launches only) makes the staging
+// barrier expect 16 bytes more than arrive, as stall_bytes does, formed once per unit: the
+// earliest k-tile named for the unit, or -1. It keeps the per-k-tile work of the producer
+// thread at one comparison when injection is on.
+__device__ __forceinline__ int stall_ktile(const TcParams& p, int mu, int rows, int nt, int nk, int bn) {
+  int kt_min = -1;
+  for (int e = 0; e < p.inj.n; ++e) {
+    const InjectPoint& ip = p.inj.p[e];
+    if (ip.site != kSiteStall || ip.i / rows != mu || ip.j / bn != nt) continue;
+    const int kt = ip.kt > 0 ? ip.kt : nk / 2;
+    if (kt_min < 0 || kt < kt_min) kt_min = kt;
+  }
+  return kt_min;
+}
+
 // Persistent order of the units (row unit mu, column block nt): groups of kGroupRows rows
 // sweep the column blocks, so the CTAs resident at one time share A row panels and B column
 // panels in L2. The last column block comes after all the others: when N is not a multiple
@@ -618,12 +633,13 @@ __device__ __noinline__ void pair_tma_loop(const TcParams& p, TcSmem<2>& sm, con
     const PairShape g = pair_shape<FT>(min(BN, p.N - n0));
     // bytes of both CTAs' loads, expected on the even CTA's barrier
     const uint32_t bytes = (2 * BM + BROWS + (FT ? (g.b1_data ? BROWS : CHK) : BROWS)) * BKB;
+    const int skt = p.inj.n > 0 ? stall_ktile(p, mu, 2 * BM, nt, nk, BN) : -1;
     for (int kt = 0; kt < nk; ++kt, ++it) {
       const uint32_t s = it % STAGES, u = it / STAGES;
       if (u > 0 && !mbar_wait_bounded(&sm.empty[s], (u - 1) & 1, p.wait_limit_ns)) { sm.timeout = 1; ok = false; break; }
       const int k0 = kt * bk_elems;
       const uint32_t fbar = mapa_shared(smem_addr(&sm.full[s]), 0);
-      if (rank == 0) mbar_arrive_expect_tx(&sm.full[s], bytes + stall_bytes(p, mu, 2 * BM, nt, kt, nk, BN));
+      if (rank == 0) mbar_arrive_expect_tx(&sm.full[s], bytes + (kt == skt ? 16u : 0u));
       // rows beyond M (an odd CTA past the last row tile) read the fill value, zero
       tma_load_2d_pair(sm.a[s], pA, fbar, k0, mt * BM);
       if (rank == 0) {
