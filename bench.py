@@ -1288,6 +1288,7 @@ def run_ours(args, rank, world, dist):
         # CUDA events around each call (they bracket the copies and the kernels on the stream)
         # split the wall time into the device's share and the host's
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        fb.ftblas_kernel_timing_begin()
         t0 = time.perf_counter()
         for s_ in range(args.steps):
             evs[s_][0].record()
@@ -1295,10 +1296,12 @@ def run_ours(args, rank, world, dist):
             evs[s_][1].record()
         barrier()
         e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+        _, kms, kn = fb.ftblas_kernel_timing_end()
         dev_ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
         return {"value": job_tflops(world, flops_step, args.steps, 1e3 * e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": 3 * n * n * 8, "d2h_bytes_per_step": n * n * 8 + fb.REPORT_BYTES,
-                "wall_ms_per_call": 1e3 * e2e_s / args.steps, "stream_ms_per_call": dev_ms}
+                "wall_ms_per_call": 1e3 * e2e_s / args.steps, "stream_ms_per_call": dev_ms,
+                "kernel_ms_per_call": kms / kn if kn else None}
 
     engine_list = [args.engine] + ([] if args.no_second_engine else [e for e in engines if e != args.engine])
     clocks = None
