@@ -53,8 +53,9 @@ struct TcParams {
   const void* A; int64_t lda;
   const void* B; int64_t ldb;
   float* C; int64_t ldc;          // FP32 C (protected calls with a bfloat16 C: the verified FP32 copy)
-  uint16_t* Cb; int64_t ldcb;     // bfloat16 C (bits) written by the CTA-pair kernel's epilogue and
-                                  // the resolve pass, which also read C_in from it; null for an FP32 C
+  uint16_t* Cb; int64_t ldcb;     // bfloat16 C (bits): the CTA-pair kernel's epilogue reads C_in from
+                                  // it and stores the rounded output there, the resolve pass a corrected
+                                  // element; null for an FP32 C
   const float* rowAbsA;          // [M]        upward sum_k |A(i,k)|
   const float* maxAbsBe;         // [nNb]      max_k upward sum_{j in block} |B(k,j)|
   float* sA;                     // [nMb][sa_pitch] e^T A per 128-row block (binary32 sum), formed after
