@@ -105,9 +105,10 @@ int64_t tc_kmajor_pitch(int64_t K, int elem_bytes);
 cudaError_t launch_kmajor_copy(const void* src, int64_t R, int64_t K, int64_t ld, int elem_bytes, void* dst,
                                int64_t pitch, cudaStream_t st);
 
-// Column-major R x Cc format conversions for bfloat16 outputs (asynchronous on st): the
-// product runs into an FP32 buffer that the library rounds to bfloat16 at the end (and, for
-// beta != 0, fills from the bfloat16 C first); C = beta C directly on a bfloat16 matrix.
+// Column-major R x Cc format conversions for bfloat16 outputs (asynchronous on st): with one
+// CTA per tile the product runs into an FP32 buffer that the library rounds to bfloat16 at the
+// end (and, for beta != 0, fills from the bfloat16 C first); C = beta C directly on a bfloat16
+// matrix.
 cudaError_t launch_f32_to_bf16(const float* src, int64_t sld, uint16_t* dst, int64_t dld, int64_t R, int64_t Cc,
                                cudaStream_t st);
 cudaError_t launch_bf16_to_f32(const uint16_t* src, int64_t sld, float* dst, int64_t dld, int64_t R, int64_t Cc,
