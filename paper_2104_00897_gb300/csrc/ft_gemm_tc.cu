@@ -1,6 +1,6 @@
 // Reduced-precision ABFT-protected GEMM on the fifth-generation tensor cores (sm_103a):
-// BF16 or FP8 E4M3 operands, FP32 accumulation in TMEM, FP32 output, FP64 checksum
-// comparison.
+// BF16 or FP8 E4M3 operands, FP32 accumulation in TMEM, FP32 output (or bfloat16, rounded
+// once from the verified FP32 value), FP64 checksum comparison.
 //
 // FT-BLAS (Zhai et al., ICS '21) has no reduced precision; the checksum relations are those
 // of Section II.A, the lazy second side that of Section V.A, and C = beta*C is folded into

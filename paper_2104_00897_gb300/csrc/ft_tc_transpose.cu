@@ -2,8 +2,9 @@
 // bfloat16 outputs. The tcgen05 product kernel and the checksum encode read every operand
 // K-contiguous (rows of K elements, 128-byte swizzled TMA boxes); an operand stored the other
 // way (op(A) with its rows contiguous, or op(B) with its columns contiguous) is transposed
-// once into library workspace through shared memory, with 16-byte loads and stores on both
-// sides where alignment allows.
+// once into library workspace: each thread loads a block of 8 x 8 16-bit or 16 x 16 8-bit
+// elements with 16-byte loads, transposes it in registers by byte permutes and stores it
+// with 16-byte stores.
 #include <cstdint>
 #include <type_traits>
 
